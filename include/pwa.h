@@ -1,0 +1,209 @@
+/*
+ * pwa.h -- libpwa: the unbinned extended negative log-likelihood of a
+ * partial-wave analysis, its gradient, its Hessian-vector products and the
+ * Newton-conjugate-gradient fit they drive, evaluated on one B300 GPU.
+ *
+ * The method is that of PWACG (arXiv:2403.09225):
+ *   Eq. 1  omega(xi) ~ sum_mu |A^mu|^2 with A^mu = sum_m Lambda_m U_m^mu
+ *          (here: I(e) = sum_s |A_s(e)|^2, A_s = sum_k c_k(e) F_{k,s}(e),
+ *           c_k = g_k BW_k(e), g_k = rho_k e^{i phi_k},
+ *           BW_k = 1 / (M_k^2 - m^2_{ch(k)}(e) - i M_k Gamma_k));
+ *   Eq. 2  normalisation by the phase-space MC sample (efficiency folded in);
+ *   Eq. 3  ln L = sum_data w ln I - N_d ln((1/N_mc) sum_mc I), N_d = sum_data w;
+ *   Eqs. 4-7  the decomposition of ln L, its gradient and its Hessian into
+ *          per-shard sums F_m, G_m and their derivatives.
+ * The library minimises NLL = -ln L.  F (the parameter-free projections U of
+ * Eq. 1) is precomputed by the caller and kept resident on the device (the
+ * paper's Sec. 2.2 does the same).
+ *
+ * Conventions for every call:
+ *  - Return value is a pwa_status; no C++ exception crosses this boundary.
+ *  - Calls are synchronous with respect to the handle's CUDA stream: results
+ *    are valid on return.  The *_device variants are asynchronous (enqueued on
+ *    the handle's stream) and read/write device memory only.
+ *  - Pointers marked "host" are ordinary host memory, "device" is CUDA device
+ *    memory; "either" is resolved by the on_device flag of the struct.
+ *  - The caller keeps ownership of every buffer it passes; the library copies
+ *    what it needs during pwa_create and never retains caller pointers.
+ *  - On error, pwa_last_error(handle) describes the first failure of the last
+ *    call (for pwa_create, the message is returned through *out when a handle
+ *    could be allocated, otherwise via pwa_last_create_error()).
+ *
+ * Parameter vector theta (host or device FP64, length P = pwa_num_params):
+ *   the free magnitudes rho_k, then the free phases phi_k, then the free masses
+ *   M_k, then the free widths Gamma_k, each block in resonance order.  With the
+ *   usual choice (resonance 0's coupling fixed to 1, everything else free)
+ *   P = 4K - 2 and theta = (rho_1..rho_{K-1}, phi_1..phi_{K-1}, M_0..M_{K-1},
+ *   Gamma_0..Gamma_{K-1}).
+ */
+#ifndef LIBPWA_PWA_H
+#define LIBPWA_PWA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pwa_handle pwa_handle; /* opaque; owned by the library */
+
+typedef enum {
+    PWA_OK = 0,
+    PWA_EINVAL = 1,      /* bad argument (shape, range, NULL, non-finite input)   */
+    PWA_ENOMEM = 2,      /* device or pinned host allocation failed               */
+    PWA_ECUDA = 3,       /* a CUDA runtime call failed (message has the details)  */
+    PWA_ENONFINITE = 4,  /* an event's intensity is not finite, or not positive for
+                            data; pwa_last_error names the first such event index
+                            (data events 0..N_d-1, MC events N_d..N_d+N_mc-1)      */
+    PWA_ENOCONV = 5,     /* the fit stopped without converging (see result.status) */
+    PWA_ETIMEOUT = 6     /* a bounded device-side wait ran out; the handle must be
+                            destroyed (its device state is no longer consistent)  */
+} pwa_status;
+
+/* One event sample (paper Eq. 3: data; Eq. 2: phase-space MC).
+ *   n          number of events (>= 1)
+ *   m2         [3][n] FP32, channel-major: m12^2, m13^2, m23^2 in GeV^2
+ *   w          [n] FP32 data weights, or NULL for unit weights; must be NULL
+ *              for the MC sample (its events enter G = sum I unweighted)
+ *   F          [n][K][S] complex FP32, interleaved (re, im): F_{k,s}(e)
+ *   on_device  0: the three pointers are host memory; 1: device memory      */
+typedef struct {
+    int64_t n;
+    const float* m2;
+    const float* w;
+    const float* F;
+    int on_device;
+} pwa_events;
+
+/* One resonance k.  channel: 0 = m12, 1 = m13, 2 = m23 (which m^2 enters
+ * BW_k); spin is informational (the angular part is inside F).  mass, width
+ * in GeV; mag, phase: the coupling g_k = mag e^{i phase}.  A fixed parameter
+ * keeps the value given here and is left out of theta; fix_coupling fixes
+ * both mag and phase. */
+typedef struct {
+    int channel;
+    int spin;
+    double mass, width;
+    double mag, phase;
+    int fix_coupling, fix_mass, fix_width;
+} pwa_resonance;
+
+/* Options of pwa_newton_cg_fit (paper Sec. 3: scipy's Newton-CG with xtol,
+ * default 1e-8, and early stopping after 500 s). */
+typedef struct {
+    double xtol;          /* stop when mean |delta theta| of a step <= xtol (1e-8) */
+    double gtol;          /* stop when max |grad| <= gtol (0: off)                 */
+    int maxiter;          /* outer iterations (0: 200 P)                            */
+    int cg_maxiter;       /* inner CG iterations per outer step (0: 20 P)           */
+    double time_limit_s;  /* wall-clock limit, 0: none (the paper uses 500 s)       */
+} pwa_fit_opts;
+
+typedef enum {
+    PWA_FIT_XTOL = 0,        /* converged: step below xtol                         */
+    PWA_FIT_GTOL = 1,        /* converged: gradient below gtol                     */
+    PWA_FIT_MAXITER = 2,     /* outer iteration limit reached                      */
+    PWA_FIT_TIME_LIMIT = 3,  /* time_limit_s reached (early stopping)              */
+    PWA_FIT_LINESEARCH = 4,  /* no step satisfied the Wolfe conditions             */
+    PWA_FIT_PRECISION = 5    /* converged: predicted decrease below the NLL's
+                                resolution, no further step can be resolved        */
+} pwa_fit_status;
+
+typedef struct {
+    double nll;       /* NLL at theta_out                                  */
+    double grad_max;  /* max |grad| at theta_out                           */
+    int iters;        /* outer Newton iterations                           */
+    int n_hvp;        /* Hessian-vector products (one pass over F each)    */
+    int n_fev;        /* NLL+gradient evaluations (one pass over F each)   */
+    int status;       /* pwa_fit_status                                    */
+    double elapsed_s; /* wall-clock seconds inside the call                */
+} pwa_fit_result;
+
+/* Build a likelihood handle.  Copies data and MC events to the device and
+ * re-lays F out in event tiles for the streaming kernel; validates that
+ * K >= 1, 1 <= S <= 4, both samples are non-empty, channels are 0..2, every
+ * m2, F and w value is finite, weights are >= 0, masses and widths are finite
+ * and positive.  cuda_stream: a cudaStream_t, or NULL for the default stream.
+ * Errors: PWA_EINVAL, PWA_ENOMEM, PWA_ECUDA.  On error *out is set to NULL. */
+pwa_status pwa_create(pwa_handle** out, const pwa_events* data, const pwa_events* mc,
+                      const pwa_resonance* table, int K, int S, void* cuda_stream);
+
+/* Message of the last pwa_create failure in this thread ("" if none). */
+const char* pwa_last_create_error(void);
+
+/* Number of free parameters P (length of theta, grad, v, hv). */
+int pwa_num_params(const pwa_handle* h);
+
+/* NLL = -ln L at theta (Eq. 3, negated).  theta: host [P]; nll: host. */
+pwa_status pwa_nll(pwa_handle* h, const double* theta, double* nll);
+
+/* Gradient of NLL at theta (Eq. 6, negated); nll_or_null also receives NLL.
+ * theta: host [P]; grad: host [P]. */
+pwa_status pwa_grad(pwa_handle* h, const double* theta, double* nll_or_null, double* grad);
+
+/* Hessian-vector product H v of NLL at theta (Eq. 7 contracted with v).
+ * theta, v, hv: host [P]. */
+pwa_status pwa_hvp(pwa_handle* h, const double* theta, const double* v, double* hv);
+
+/* The fused pass: NLL, gradient and H v from one read of F.  Any of grad,
+ * hv may be NULL (then the cheaper pass without them runs); v is required
+ * when hv is not NULL.  All pointers host. */
+pwa_status pwa_eval(pwa_handle* h, const double* theta, const double* v,
+                    double* nll, double* grad, double* hv);
+
+/* Asynchronous fused pass on device buffers, enqueued on the handle's stream.
+ * d_theta [P], d_v [P] (may be NULL when hv is not wanted), d_out [1 + 2P]
+ * receives (NLL, grad[P], hv[P]); with want_hv == 0 the hv part is left
+ * untouched and v is not read; with want_grad == 0 only NLL is written.
+ * Errors detected on the device (non-finite intensity, wait timeout) are
+ * reported by the next synchronous call or by pwa_sync(). */
+pwa_status pwa_eval_device(pwa_handle* h, const double* d_theta, const double* d_v,
+                           double* d_out, int want_grad, int want_hv);
+
+/* Wait for the handle's stream and report device-side errors of earlier
+ * asynchronous calls. */
+pwa_status pwa_sync(pwa_handle* h);
+
+/* Per-event intensity I(e) = sum_s |A_s(e)|^2 (Eq. 1) of the handle's data
+ * (sample = 0) or MC (sample = 1) events at theta (host [P]), in event order.
+ * out: [n] FP32, host (out_on_device = 0) or device (1). */
+pwa_status pwa_event_intensity(pwa_handle* h, int sample, const double* theta,
+                               float* out, int out_on_device);
+
+/* Newton-CG fit from theta0 (host [P]); theta_out (host [P]) receives the
+ * final point (it may alias theta0).  opts may be NULL (defaults).  Returns
+ * PWA_OK when the fit converged or hit its time limit (result->status says
+ * which), PWA_ENOCONV when it stopped otherwise, or an error status. */
+pwa_status pwa_newton_cg_fit(pwa_handle* h, const double* theta0, const pwa_fit_opts* opts,
+                             double* theta_out, pwa_fit_result* result);
+
+/* Default options: xtol 1e-8, gtol 0, maxiter 0 (= 200 P), cg_maxiter 0
+ * (= 20 P), no time limit. */
+void pwa_fit_opts_default(pwa_fit_opts* opts);
+
+/* Use another CUDA stream (cudaStream_t, NULL = default) for later calls. */
+pwa_status pwa_set_stream(pwa_handle* h, void* cuda_stream);
+
+/* Tiling of the streaming kernel (the autotuner's knobs).  warps: warps per
+ * block (1, 2, 4, 8 or 16); lanes_per_event: lanes that share one event in
+ * the coherent-sum sweep (1, 2, 4 or 8, at most 32 * warps / 32); stages:
+ * tiles in flight per block (2..4); blocks_per_sm: 0 = as many as fit.  The
+ * tile size is 32 * warps / lanes_per_event events.  Re-lays the events out
+ * on the device.  Errors: PWA_EINVAL when the combination does not fit. */
+pwa_status pwa_set_tiling(pwa_handle* h, int warps, int lanes_per_event, int stages,
+                          int blocks_per_sm);
+
+/* Current tiling and geometry: fills (warps, lanes_per_event, stages,
+ * blocks_per_sm, events_per_tile, grid_blocks, smem_bytes_per_block). */
+pwa_status pwa_get_tiling(const pwa_handle* h, int out7[7]);
+
+/* Message describing the first failure of the handle's last call. */
+const char* pwa_last_error(const pwa_handle* h);
+
+/* Free every resource of the handle (NULL is allowed). */
+void pwa_destroy(pwa_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBPWA_PWA_H */

@@ -1,0 +1,286 @@
+"""ctypes binding of libpwa (include/pwa.h): argument marshalling only.
+
+Every function of the C ABI is exposed under its own name; ``Likelihood`` is a
+thin owner of one handle.  All arithmetic of the likelihood runs in the CUDA
+library; there is no Python or CPU fallback: importing this module on a
+machine without the built library raises, and every call checks the status
+the library returns.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpwa.so")
+
+PWA_OK, PWA_EINVAL, PWA_ENOMEM, PWA_ECUDA, PWA_ENONFINITE, PWA_ENOCONV, PWA_ETIMEOUT = range(7)
+STATUS_NAMES = {0: "PWA_OK", 1: "PWA_EINVAL", 2: "PWA_ENOMEM", 3: "PWA_ECUDA", 4: "PWA_ENONFINITE",
+                5: "PWA_ENOCONV", 6: "PWA_ETIMEOUT"}
+FIT_STATUS_NAMES = ("xtol", "gtol", "maxiter", "time_limit", "linesearch_failed", "precision_limit")
+
+
+class pwa_events(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m2", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("F", ctypes.c_void_p), ("on_device", ctypes.c_int)]
+
+
+class pwa_resonance(ctypes.Structure):
+    _fields_ = [("channel", ctypes.c_int), ("spin", ctypes.c_int), ("mass", ctypes.c_double),
+                ("width", ctypes.c_double), ("mag", ctypes.c_double), ("phase", ctypes.c_double),
+                ("fix_coupling", ctypes.c_int), ("fix_mass", ctypes.c_int), ("fix_width", ctypes.c_int)]
+
+
+class pwa_fit_opts(ctypes.Structure):
+    _fields_ = [("xtol", ctypes.c_double), ("gtol", ctypes.c_double), ("maxiter", ctypes.c_int),
+                ("cg_maxiter", ctypes.c_int), ("time_limit_s", ctypes.c_double)]
+
+
+class pwa_fit_result(ctypes.Structure):
+    _fields_ = [("nll", ctypes.c_double), ("grad_max", ctypes.c_double), ("iters", ctypes.c_int),
+                ("n_hvp", ctypes.c_int), ("n_fev", ctypes.c_int), ("status", ctypes.c_int),
+                ("elapsed_s", ctypes.c_double)]
+
+
+class PwaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+#: every symbol include/pwa.h declares
+EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "pwa_grad", "pwa_hvp",
+           "pwa_eval", "pwa_eval_device", "pwa_sync", "pwa_event_intensity", "pwa_newton_cg_fit",
+           "pwa_fit_opts_default", "pwa_set_stream", "pwa_set_tiling", "pwa_get_tiling", "pwa_last_error",
+           "pwa_destroy")
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise RuntimeError("libpwa is not built (%s missing); run paper_2403_09225_b300/build.py" % path)
+    lib = ctypes.CDLL(path)
+    H, vp, dp, ip, i = ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), \
+        ctypes.POINTER(ctypes.c_int), ctypes.c_int
+    st = ctypes.c_int
+    sig = {
+        "pwa_create": (st, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(pwa_events),
+                            ctypes.POINTER(pwa_events), ctypes.POINTER(pwa_resonance), i, i, vp]),
+        "pwa_last_create_error": (ctypes.c_char_p, []),
+        "pwa_num_params": (i, [H]),
+        "pwa_nll": (st, [H, dp, dp]),
+        "pwa_grad": (st, [H, dp, dp, dp]),
+        "pwa_hvp": (st, [H, dp, dp, dp]),
+        "pwa_eval": (st, [H, dp, dp, dp, dp, dp]),
+        "pwa_eval_device": (st, [H, vp, vp, vp, i, i]),
+        "pwa_sync": (st, [H]),
+        "pwa_event_intensity": (st, [H, i, dp, vp, i]),
+        "pwa_newton_cg_fit": (st, [H, dp, ctypes.POINTER(pwa_fit_opts), dp, ctypes.POINTER(pwa_fit_result)]),
+        "pwa_fit_opts_default": (None, [ctypes.POINTER(pwa_fit_opts)]),
+        "pwa_set_stream": (st, [H, vp]),
+        "pwa_set_tiling": (st, [H, i, i, i, i]),
+        "pwa_get_tiling": (st, [H, ip]),
+        "pwa_last_error": (ctypes.c_char_p, [H]),
+        "pwa_destroy": (None, [H]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(x, n: Optional[int] = None) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    if n is not None and a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _events(m2, F, w, keep: list) -> pwa_events:
+    """pwa_events for numpy arrays (host) or torch CUDA tensors (device)."""
+    if _is_torch(m2):
+        import torch
+        m2 = m2.contiguous().to(torch.float32)
+        Fr = torch.view_as_real(F.contiguous()) if F.is_complex() else F.contiguous()
+        Fr = Fr.to(torch.float32)
+        wt = None if w is None else w.contiguous().to(torch.float32)
+        keep.extend([m2, Fr, wt])
+        dev = 1 if m2.is_cuda else 0
+        return pwa_events(int(m2.shape[1]), m2.data_ptr(), 0 if wt is None else wt.data_ptr(), Fr.data_ptr(), dev)
+    m2 = np.ascontiguousarray(m2, dtype=np.float32)
+    Fv = np.ascontiguousarray(F)
+    Fv = Fv.view(np.float32) if np.iscomplexobj(Fv) else np.ascontiguousarray(Fv, dtype=np.float32)
+    wv = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+    keep.extend([m2, Fv, wv])
+    return pwa_events(int(m2.shape[1]), m2.ctypes.data, 0 if wv is None else wv.ctypes.data, Fv.ctypes.data, 0)
+
+
+def resonance_table(table: Sequence) -> ctypes.Array:
+    """pwa_resonance[K] from objects with channel, spin, mass, width, mag,
+    phase, fix_coupling, fix_mass, fix_width attributes."""
+    arr = (pwa_resonance * len(table))()
+    for k, r in enumerate(table):
+        arr[k] = pwa_resonance(int(r.channel), int(r.spin), float(r.mass), float(r.width), float(r.mag),
+                               float(r.phase), int(bool(r.fix_coupling)), int(bool(r.fix_mass)),
+                               int(bool(r.fix_width)))
+    return arr
+
+
+class Likelihood:
+    """One libpwa handle: data + MC events and a resonance table."""
+
+    def __init__(self, data, mc, table, K: int, S: int, stream: int = 0):
+        """data, mc: objects with m2 [3, n], F [n, K, S] complex and w ([n] or
+        None) as numpy arrays or torch CUDA tensors."""
+        keep: list = []
+        de = _events(data.m2, data.F, getattr(data, "w", None), keep)
+        me = _events(mc.m2, mc.F, None, keep)
+        tab = resonance_table(table)
+        h = ctypes.c_void_p()
+        st = lib().pwa_create(ctypes.byref(h), ctypes.byref(de), ctypes.byref(me), tab, int(K), int(S),
+                              ctypes.c_void_p(stream))
+        if st != PWA_OK:
+            raise PwaError(st, lib().pwa_last_create_error().decode())
+        self._h = h
+        self.K, self.S = int(K), int(S)
+        self.P = lib().pwa_num_params(h)
+        self._n = (int(de.n), int(me.n))
+
+    # -- plumbing --
+    def _check(self, st: int):
+        if st != PWA_OK:
+            raise PwaError(st, lib().pwa_last_error(self._h).decode())
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pwa_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- evaluation (host vectors) --
+    def nll(self, theta) -> float:
+        th = _f64(theta, self.P)
+        f = ctypes.c_double()
+        self._check(lib().pwa_nll(self._h, _dptr(th), ctypes.byref(f)))
+        return f.value
+
+    def grad(self, theta):
+        th = _f64(theta, self.P)
+        f = ctypes.c_double()
+        g = np.empty(self.P)
+        self._check(lib().pwa_grad(self._h, _dptr(th), ctypes.byref(f), _dptr(g)))
+        return f.value, g
+
+    def hvp(self, theta, v) -> np.ndarray:
+        th, vv = _f64(theta, self.P), _f64(v, self.P)
+        hv = np.empty(self.P)
+        self._check(lib().pwa_hvp(self._h, _dptr(th), _dptr(vv), _dptr(hv)))
+        return hv
+
+    def eval(self, theta, v=None):
+        """(NLL, grad, H v) from one fused pass; H v is None when v is None."""
+        th = _f64(theta, self.P)
+        f = ctypes.c_double()
+        g = np.empty(self.P)
+        if v is None:
+            self._check(lib().pwa_eval(self._h, _dptr(th), None, ctypes.byref(f), _dptr(g), None))
+            return f.value, g, None
+        vv = _f64(v, self.P)
+        hv = np.empty(self.P)
+        self._check(lib().pwa_eval(self._h, _dptr(th), _dptr(vv), ctypes.byref(f), _dptr(g), _dptr(hv)))
+        return f.value, g, hv
+
+    def eval_device(self, d_theta: int, d_v: int, d_out: int, want_grad: bool = True, want_hv: bool = True):
+        """Asynchronous fused pass on device pointers (theta [P], v [P], out [1 + 2P])."""
+        self._check(lib().pwa_eval_device(self._h, ctypes.c_void_p(d_theta), ctypes.c_void_p(d_v),
+                                          ctypes.c_void_p(d_out), int(want_grad), int(want_hv)))
+
+    def sync(self):
+        self._check(lib().pwa_sync(self._h))
+
+    def set_stream(self, stream: int):
+        self._check(lib().pwa_set_stream(self._h, ctypes.c_void_p(stream)))
+
+    def intensity(self, theta, sample: int = 1, out=None) -> np.ndarray:
+        """I(e) of the data (sample 0) or MC (sample 1) events, FP32.  With out
+        a torch CUDA tensor the result is written there on the device."""
+        th = _f64(theta, self.P)
+        if out is not None and _is_torch(out):
+            self._check(lib().pwa_event_intensity(self._h, int(sample), _dptr(th), ctypes.c_void_p(out.data_ptr()), 1))
+            return out
+        n = self.n_events(sample)
+        res = np.empty(n, dtype=np.float32)
+        self._check(lib().pwa_event_intensity(self._h, int(sample), _dptr(th), ctypes.c_void_p(res.ctypes.data), 0))
+        return res
+
+    def n_events(self, sample: int) -> int:
+        return self._n[sample]
+
+    # -- fitting --
+    def fit(self, theta0, xtol: float = 1e-8, gtol: float = 0.0, maxiter: int = 0, cg_maxiter: int = 0,
+            time_limit_s: float = 0.0):
+        th = _f64(theta0, self.P)
+        out = np.empty(self.P)
+        opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s)
+        res = pwa_fit_result()
+        st = lib().pwa_newton_cg_fit(self._h, _dptr(th), ctypes.byref(opts), _dptr(out), ctypes.byref(res))
+        if st not in (PWA_OK, PWA_ENOCONV):
+            self._check(st)
+        return out, {"nll": res.nll, "grad_max": res.grad_max, "iters": res.iters, "n_hvp": res.n_hvp,
+                     "n_fev": res.n_fev, "status": FIT_STATUS_NAMES[res.status], "elapsed_s": res.elapsed_s,
+                     "converged": st == PWA_OK}
+
+    # -- tiling --
+    def set_tiling(self, warps: int, lanes_per_event: int, stages: int, blocks_per_sm: int = 0):
+        self._check(lib().pwa_set_tiling(self._h, warps, lanes_per_event, stages, blocks_per_sm))
+
+    def get_tiling(self) -> dict:
+        out = (ctypes.c_int * 7)()
+        self._check(lib().pwa_get_tiling(self._h, out))
+        keys = ("warps", "lanes_per_event", "stages", "blocks_per_sm", "events_per_tile", "grid_blocks",
+                "smem_bytes")
+        return dict(zip(keys, list(out)))
+
+
+def make_likelihood(workload, stream: int = 0, device_inputs: bool = False) -> Likelihood:
+    """Likelihood for a workload.Workload (host inputs, or torch CUDA tensors
+    when device_inputs is True)."""
+    data, mc = workload.data, workload.mc
+    if device_inputs:
+        import torch
+        from types import SimpleNamespace
+        dev = torch.device("cuda")
+        data = SimpleNamespace(m2=torch.from_numpy(data.m2).to(dev), F=torch.from_numpy(data.F).to(dev),
+                               w=None if data.w is None else torch.from_numpy(data.w).to(dev))
+        mc = SimpleNamespace(m2=torch.from_numpy(mc.m2).to(dev), F=torch.from_numpy(mc.F).to(dev), w=None)
+    return Likelihood(data, mc, workload.table, workload.K, workload.S, stream)

@@ -1,0 +1,655 @@
+// pass_kernel.cuh -- the fused streaming pass of libpwa (sm_103a).
+//
+// One launch reads every event tile of F exactly once and produces the NLL,
+// its gradient and a Hessian-vector product (paper Eqs. 3, 6, 7).  Per event
+// e and resonance k (all FP32, in registers):
+//   BW_k   = 1 / (M_k^2 - m^2_{ch(k)}(e) - i M_k Gamma_k)           (a-3)
+//   c_k    = g_k BW_k,   cdot_k = BW_k (alpha_k + BW_k beta_k)       (a-3, a-6)
+//   A_s    = sum_k c_k F_{k,s},  Adot_s = sum_k cdot_k F_{k,s}       (sweep 1, Eq. 1)
+//   I      = sum_s |A_s|^2,      Idot = 2 Re sum_s conj(A_s) Adot_s
+//   D_k    = sum_s conj(A_s) F_{k,s},  Ddot_k = sum_s conj(Adot_s) F_{k,s}   (sweep 2)
+// and the event's contribution to five complex sums per resonance,
+//   Q1 += Dh B, Q2 += Dh B^2, Q3 += Dh B^3, P1 += Dt B, P2 += Dt B^2,
+// with Dh = a D, Dt = a Ddot - b D, (a, b) = (w/I, w Idot/I^2) for data and
+// (1, 0) for MC.  Every derivative of the NLL with respect to resonance k's
+// (rho, phi, M, Gamma) is a fixed complex combination of these sums, applied
+// once per pass in FP64 (see combine()); no per-event intermediate is stored.
+//
+// Data layout (built by pwa_create): events are cut into tiles of E events;
+// one tile record is contiguous in HBM:
+//   F   float2 [K][S][E]   position p = (e + shift_k) mod E   (shift: bank-conflict
+//                          free sweeps when several lanes share an event)
+//   m2  float  [3][E]
+//   w   float  [E]         (data tiles only)
+// A block streams whole tile records into shared memory with the TMA bulk
+// copy engine (cp.async.bulk + mbarrier transaction counts), NST tiles in
+// flight, and works on them in two phases:
+//   phase 1: H lanes per event (butterfly-reduced) build A, Adot, I, Idot;
+//   phase 2: each warp owns KPW resonances and sweeps the tile's events.
+// Per-lane FP32 sums are folded into FP64 every kWindow tiles; each block
+// writes FP64 partials; a two-level "last block done" reduction (fixed order,
+// hence run-to-run bit-identical) adds them and the final block evaluates the
+// combination of Eqs. 4, 6, 7 in FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pwa {
+
+constexpr int kNV = 10;        // FP64 values per resonance and sample set
+constexpr int kNScal = 3;      // per-set scalars: data (sum w ln I, -, -), MC (G, Gdot, -)
+constexpr int kWindow = 16;    // tiles between FP32 -> FP64 folds
+constexpr int kMaxThreads = 512;
+
+enum { MODE_NLL = 0, MODE_GRAD = 1, MODE_HVP = 2 };
+enum { ERR_TIMEOUT = 1, ERR_NONFINITE = 2 };
+
+struct ResParam {       // parameter map of one resonance
+    int idx[4];         // theta index of rho, phi, M, Gamma; -1 when fixed
+    int channel;
+    int pad;
+    double fixed[4];    // values of fixed parameters
+};
+
+struct __align__(16) KConst {  // FP32 per-resonance constants (48 bytes)
+    float m2hi, m2lo, mg;      // M^2 = m2hi + m2lo (FP32 pair), M Gamma
+    int ch;                    // channel of m^2
+    float gre, gim;            // g = rho e^{i phi}
+    float are, aim;            // alpha = v_rho e^{i phi} + i v_phi g
+    float bre, bim;            // beta = g (v_M (-2M + i Gamma) + v_Gamma (i M))
+    int shift;                 // rotation of the event position in the tile
+    int pad;
+};
+
+struct PassArgs {
+    const unsigned char* tiles[2];  // data, MC tile records
+    uint32_t tile_bytes[2];
+    int ntiles[2];
+    long long nev[2];
+    int K, E, H, W, NST;
+    uint32_t stage_bytes;
+    int P;
+    const ResParam* res;
+    const double* theta;
+    const double* v;
+    double Nd, Nmc;
+    double* block_rec;
+    double* group_rec;
+    unsigned* group_count;
+    unsigned* top_count;
+    int group_size, ngroups, rec_len;
+    double* out;
+    unsigned long long* bad;
+    int* err;
+    long long timeout_cycles;
+};
+
+// ---------------------------------------------------------------------------
+// small PTX helpers: mbarrier, TMA bulk copy
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Arm the barrier for `bytes` of transactions and start one bulk copy of a
+// contiguous tile record from global into shared memory.
+__device__ __forceinline__ void tma_load_tile(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Wait for the barrier phase with the given parity; gives up after `budget`
+// SM cycles and returns false (the caller reports ERR_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget)
+{
+    const uint32_t a = smem_addr(bar);
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > budget) return false;
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// ---------------------------------------------------------------------------
+// per-resonance constants (a-1): FP64 in, FP32 out
+// ---------------------------------------------------------------------------
+
+struct ResValues {
+    double rho, phi, M, G;     // parameter values
+    double vr, vp, vm, vg;     // direction components (0 for fixed parameters)
+};
+
+__device__ __forceinline__ ResValues res_values(const PassArgs& a, int k, bool with_v)
+{
+    const ResParam r = a.res[k];
+    double p[4], d[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        p[j] = r.idx[j] >= 0 ? a.theta[r.idx[j]] : r.fixed[j];
+        d[j] = (with_v && r.idx[j] >= 0) ? a.v[r.idx[j]] : 0.0;
+    }
+    return ResValues{p[0], p[1], p[2], p[3], d[0], d[1], d[2], d[3]};
+}
+
+__device__ __forceinline__ KConst make_kconst(const PassArgs& a, int k, bool with_v, int ev)
+{
+    const ResValues rv = res_values(a, k, with_v);
+    double s, c;
+    sincos(rv.phi, &s, &c);
+    const double gre = rv.rho * c, gim = rv.rho * s;
+    const double M2 = rv.M * rv.M;
+    KConst kc;
+    kc.m2hi = (float)M2;
+    kc.m2lo = (float)(M2 - (double)kc.m2hi);
+    kc.mg = (float)(rv.M * rv.G);
+    kc.ch = a.res[k].channel;
+    kc.gre = (float)gre;
+    kc.gim = (float)gim;
+    // alpha = v_rho E + i v_phi g
+    kc.are = (float)(rv.vr * c - rv.vp * gim);
+    kc.aim = (float)(rv.vr * s + rv.vp * gre);
+    // u = v_M a1 + v_G a2, a1 = -2M + i G, a2 = i M;  beta = g u
+    const double ure = -2.0 * rv.M * rv.vm, uim = rv.G * rv.vm + rv.M * rv.vg;
+    kc.bre = (float)(gre * ure - gim * uim);
+    kc.bim = (float)(gre * uim + gim * ure);
+    kc.shift = ev < 16 ? (k % (16 / ev)) * ev : 0;
+    kc.pad = 0;
+    return kc;
+}
+
+// BW_k(e) = 1/(M^2 - m^2 - i M Gamma) = (d + i mg) / (d^2 + mg^2), d = M^2 - m^2
+// with M^2 carried as an FP32 (hi, lo) pair so that narrow peaks keep their shape.
+__device__ __forceinline__ void breit_wigner(const KConst& kc, float m2, float& br, float& bi)
+{
+    const float d = (kc.m2hi - m2) + kc.m2lo;
+    const float r = __fdividef(1.0f, fmaf(d, d, kc.mg * kc.mg));
+    br = d * r;
+    bi = kc.mg * r;
+}
+
+__device__ __forceinline__ float pick3(int ch, float a0, float a1, float a2)
+{
+    return ch == 0 ? a0 : (ch == 1 ? a1 : a2);
+}
+
+// ---------------------------------------------------------------------------
+// the fused pass
+// ---------------------------------------------------------------------------
+
+template <int MODE, int S, int KPW>
+__global__ void __launch_bounds__(kMaxThreads) pass_kernel(const PassArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr bool HV = MODE == MODE_HVP;
+    constexpr bool GR = MODE >= MODE_GRAD;
+    constexpr int NVM = HV ? kNV : 4;          // accumulated reals per resonance
+    constexpr int V = GR ? NVM * KPW : 1;       // per-warp accumulated reals
+    constexpr int SLOTS = (V + 31) / 32;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int K = a.K, E = a.E, H = a.H, W = a.W, NST = a.NST;
+    const int ev = 32 / H;
+    const int nthreads = blockDim.x;
+
+    unsigned char* stages = smem;
+    KConst* kc = reinterpret_cast<KConst*>(smem + (size_t)NST * a.stage_bytes);
+    float4* abuf = reinterpret_cast<float4*>(kc + K);   // [S][E] (A_s, Adot_s)
+    float2* ab = reinterpret_cast<float2*>(abuf + S * E); // [E] (a, b)
+    double* red = reinterpret_cast<double*>(ab + E);      // [W][4]
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(red + 4 * W);
+    __shared__ int s_flag;
+
+    const long long T = (long long)a.ntiles[0] + a.ntiles[1];
+    const long long G = gridDim.x;
+
+    if (tid == 0) {
+        for (int s = 0; s < NST; ++s) mbar_init(&mbar[s], 1);
+        fence_mbar_init();
+        for (int i = 0; i < NST; ++i) {
+            const long long t = blockIdx.x + i * G;
+            if (t < T) {
+                const int smp = t < a.ntiles[0] ? 0 : 1;
+                const long long lt = smp ? t - a.ntiles[0] : t;
+                tma_load_tile(stages + (size_t)i * a.stage_bytes,
+                              a.tiles[smp] + (size_t)lt * a.tile_bytes[smp], a.tile_bytes[smp], &mbar[i]);
+            }
+        }
+    }
+    for (int k = tid; k < K; k += nthreads) kc[k] = make_kconst(a, k, HV, ev);
+    __syncthreads();
+
+    // FP32 accumulators (phase 2: per owned resonance; phase 1: per-event scalars)
+    float acc[GR ? KPW : 1][GR ? NVM : 1];
+#pragma unroll
+    for (int j = 0; j < (GR ? KPW : 1); ++j)
+#pragma unroll
+        for (int q = 0; q < (GR ? NVM : 1); ++q) acc[j][q] = 0.f;
+    float sc0 = 0.f, sc1 = 0.f;
+    double dacc[SLOTS];
+#pragma unroll
+    for (int t = 0; t < SLOTS; ++t) dacc[t] = 0.0;
+    double dsc0 = 0.0, dsc1 = 0.0;
+
+    const int k0 = warp * KPW;
+    const int h = lane / ev, el = lane % ev;
+    int cur_set = -1;
+    bool set_written[2] = {false, false};
+    long long i_fail = -1;  // loop iteration whose tile never arrived
+
+    // fold the per-lane FP32 sums into per-lane FP64 slots (fixed order)
+    auto fold = [&]() {
+        if constexpr (GR) {
+#pragma unroll
+            for (int j = 0; j < KPW; ++j)
+#pragma unroll
+                for (int q = 0; q < NVM; ++q) {
+                    const float s = warp_sum(acc[j][q]);
+                    acc[j][q] = 0.f;
+                    const int vi = j * NVM + q;
+                    if ((vi & 31) == lane) dacc[vi >> 5] += (double)s;
+                }
+        }
+        const float t0 = warp_sum(sc0), t1 = warp_sum(sc1);
+        sc0 = sc1 = 0.f;
+        if (lane == 0) {
+            dsc0 += (double)t0;
+            dsc1 += (double)t1;
+        }
+    };
+
+    // write this block's FP64 partials of one sample set
+    auto write_set = [&](int set) {
+        double* rec = a.block_rec + (size_t)blockIdx.x * a.rec_len + (size_t)set * (K * kNV + kNScal);
+        if constexpr (GR) {
+#pragma unroll
+            for (int t = 0; t < SLOTS; ++t) {
+                const int vi = lane + 32 * t;
+                if (vi < V) {
+                    const int k = k0 + vi / NVM;
+                    if (k < K) rec[k * kNV + vi % NVM] = dacc[t];
+                }
+                dacc[t] = 0.0;
+            }
+        }
+        if (lane == 0) {
+            red[warp * 4 + 0] = dsc0;
+            red[warp * 4 + 1] = dsc1;
+        }
+        dsc0 = dsc1 = 0.0;
+        __syncthreads();
+        if (tid == 0) {
+            double s0 = 0.0, s1 = 0.0;
+            for (int w = 0; w < W; ++w) {
+                s0 += red[w * 4 + 0];
+                s1 += red[w * 4 + 1];
+            }
+            rec[K * kNV + 0] = s0;
+            rec[K * kNV + 1] = s1;
+            rec[K * kNV + 2] = 0.0;
+        }
+        __syncthreads();
+        set_written[set] = true;
+    };
+
+    int win = 0;
+    for (long long i = 0;; ++i) {
+        const long long t = blockIdx.x + i * G;
+        if (t >= T) break;
+        const int smp = t < a.ntiles[0] ? 0 : 1;
+        const long long lt = smp ? t - a.ntiles[0] : t;
+        if (smp != cur_set) {
+            if (cur_set >= 0) {
+                fold();
+                write_set(cur_set);
+            }
+            cur_set = smp;
+            win = 0;
+        }
+        const int st = (int)(i % NST);
+        const uint32_t parity = (uint32_t)((i / NST) & 1);
+        const bool ok = mbar_wait(&mbar[st], parity, a.timeout_cycles);
+        if (__syncthreads_or(!ok)) {
+            i_fail = i;
+            break;
+        }
+        const float2* Fs = reinterpret_cast<const float2*>(stages + (size_t)st * a.stage_bytes);
+        const float* m2s = reinterpret_cast<const float*>(Fs + (size_t)K * S * E);
+        const float* ws = m2s + 3 * E;
+        const long long e_base = lt * E;
+        const int nvalid = (int)min((long long)E, a.nev[smp] - e_base);
+
+        // ---- phase 1: coherent sums, intensity, per-event weights ----
+        for (int item = warp; item < E / ev; item += W) {
+            const int e = item * ev + el;
+            const float m20 = m2s[e], m21 = m2s[E + e], m22 = m2s[2 * E + e];
+            float Ar[S], Ai[S], Dr[S], Di[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) Ar[s] = Ai[s] = Dr[s] = Di[s] = 0.f;
+#pragma unroll 2
+            for (int k = h; k < K; k += H) {
+                const KConst c = kc[k];
+                float br, bi;
+                breit_wigner(c, pick3(c.ch, m20, m21, m22), br, bi);
+                const float cr = c.gre * br - c.gim * bi, ci = c.gre * bi + c.gim * br;
+                float dr = 0.f, di = 0.f;
+                if constexpr (HV) {
+                    const float tr = c.are + (br * c.bre - bi * c.bim);
+                    const float ti = c.aim + (br * c.bim + bi * c.bre);
+                    dr = br * tr - bi * ti;
+                    di = br * ti + bi * tr;
+                }
+                int p = e + c.shift;
+                p = p >= E ? p - E : p;
+                const float2* Fk = Fs + (size_t)k * S * E + p;
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    const float2 f = Fk[s * E];
+                    Ar[s] = fmaf(cr, f.x, fmaf(-ci, f.y, Ar[s]));
+                    Ai[s] = fmaf(cr, f.y, fmaf(ci, f.x, Ai[s]));
+                    if constexpr (HV) {
+                        Dr[s] = fmaf(dr, f.x, fmaf(-di, f.y, Dr[s]));
+                        Di[s] = fmaf(dr, f.y, fmaf(di, f.x, Di[s]));
+                    }
+                }
+            }
+            for (int off = ev; off < 32; off <<= 1) {
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    Ar[s] += __shfl_xor_sync(0xffffffffu, Ar[s], off);
+                    Ai[s] += __shfl_xor_sync(0xffffffffu, Ai[s], off);
+                    if constexpr (HV) {
+                        Dr[s] += __shfl_xor_sync(0xffffffffu, Dr[s], off);
+                        Di[s] += __shfl_xor_sync(0xffffffffu, Di[s], off);
+                    }
+                }
+            }
+            if (h == 0) {
+                float I = 0.f, Id = 0.f;
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    I = fmaf(Ar[s], Ar[s], fmaf(Ai[s], Ai[s], I));
+                    if constexpr (HV) Id = fmaf(Ar[s], Dr[s], fmaf(Ai[s], Di[s], Id));
+                }
+                Id *= 2.f;
+                const bool valid = e < nvalid;
+                float wa = 0.f, wb = 0.f;
+                if (smp == 0) {
+                    const float w = ws[e];
+                    const bool good = I > 0.f && I < INFINITY;
+                    if (valid && !good) {
+                        atomicMin(a.bad, (unsigned long long)(e_base + e));
+                        atomicOr(a.err, ERR_NONFINITE);
+                    }
+                    if (valid && good) {
+                        const float rI = 1.0f / I;
+                        wa = w * rI;
+                        wb = wa * Id * rI;
+                        sc0 += w * logf(I);
+                    }
+                } else {
+                    if (valid && !(I < INFINITY)) {
+                        atomicMin(a.bad, (unsigned long long)(a.nev[0] + e_base + e));
+                        atomicOr(a.err, ERR_NONFINITE);
+                    }
+                    if (valid) {
+                        wa = 1.f;
+                        sc0 += I;
+                        sc1 += Id;
+                    }
+                }
+                if constexpr (GR) {
+#pragma unroll
+                    for (int s = 0; s < S; ++s) abuf[s * E + e] = make_float4(Ar[s], Ai[s], Dr[s], Di[s]);
+                    ab[e] = make_float2(wa, wb);
+                }
+            }
+        }
+
+        if constexpr (GR) {
+            __syncthreads();
+            // ---- phase 2: second sweep, per-resonance sums ----
+            if (k0 < K) {
+                for (int c0 = 0; c0 < E; c0 += 32) {
+                    const int e = c0 + lane;
+                    float Ar[S], Ai[S], Dr[S], Di[S];
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+                        const float4 q = abuf[s * E + e];
+                        Ar[s] = q.x;
+                        Ai[s] = q.y;
+                        Dr[s] = q.z;
+                        Di[s] = q.w;
+                    }
+                    const float2 wab = ab[e];
+                    const float m20 = m2s[e], m21 = m2s[E + e], m22 = m2s[2 * E + e];
+#pragma unroll
+                    for (int j = 0; j < KPW; ++j) {
+                        const int k = k0 + j;
+                        if (k >= K) break;
+                        const KConst c = kc[k];
+                        float br, bi;
+                        breit_wigner(c, pick3(c.ch, m20, m21, m22), br, bi);
+                        int p = e + c.shift;
+                        p = p >= E ? p - E : p;
+                        const float2* Fk = Fs + (size_t)k * S * E + p;
+                        float xr = 0.f, xi = 0.f, yr = 0.f, yi = 0.f;   // D, Ddot
+#pragma unroll
+                        for (int s = 0; s < S; ++s) {
+                            const float2 f = Fk[s * E];
+                            xr = fmaf(Ar[s], f.x, fmaf(Ai[s], f.y, xr));
+                            xi = fmaf(Ar[s], f.y, fmaf(-Ai[s], f.x, xi));
+                            if constexpr (HV) {
+                                yr = fmaf(Dr[s], f.x, fmaf(Di[s], f.y, yr));
+                                yi = fmaf(Dr[s], f.y, fmaf(-Di[s], f.x, yi));
+                            }
+                        }
+                        // Dh = a D
+                        const float hr = wab.x * xr, hi = wab.x * xi;
+                        // B^2
+                        const float b2r = br * br - bi * bi, b2i = 2.f * br * bi;
+                        acc[j][0] = fmaf(hr, br, fmaf(-hi, bi, acc[j][0]));
+                        acc[j][1] = fmaf(hr, bi, fmaf(hi, br, acc[j][1]));
+                        acc[j][2] = fmaf(hr, b2r, fmaf(-hi, b2i, acc[j][2]));
+                        acc[j][3] = fmaf(hr, b2i, fmaf(hi, b2r, acc[j][3]));
+                        if constexpr (HV) {
+                            const float b3r = b2r * br - b2i * bi, b3i = b2r * bi + b2i * br;
+                            // Dt = a Ddot - b D
+                            const float tr = fmaf(wab.x, yr, -wab.y * xr), ti = fmaf(wab.x, yi, -wab.y * xi);
+                            acc[j][4] = fmaf(hr, b3r, fmaf(-hi, b3i, acc[j][4]));
+                            acc[j][5] = fmaf(hr, b3i, fmaf(hi, b3r, acc[j][5]));
+                            acc[j][6] = fmaf(tr, br, fmaf(-ti, bi, acc[j][6]));
+                            acc[j][7] = fmaf(tr, bi, fmaf(ti, br, acc[j][7]));
+                            acc[j][8] = fmaf(tr, b2r, fmaf(-ti, b2i, acc[j][8]));
+                            acc[j][9] = fmaf(tr, b2i, fmaf(ti, b2r, acc[j][9]));
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();  // the stage and abuf may now be overwritten
+        if (tid == 0) {
+            const long long tn = t + (long long)NST * G;
+            if (tn < T) {
+                fence_proxy_async();
+                const int s2 = tn < a.ntiles[0] ? 0 : 1;
+                const long long lt2 = s2 ? tn - a.ntiles[0] : tn;
+                tma_load_tile(stages + (size_t)st * a.stage_bytes, a.tiles[s2] + (size_t)lt2 * a.tile_bytes[s2],
+                              a.tile_bytes[s2], &mbar[st]);
+            }
+        }
+        if (++win == kWindow) {
+            fold();
+            win = 0;
+        }
+    }
+
+    if (i_fail >= 0) {
+        // A tile never arrived.  Report it, then wait (bounded) for the copies
+        // this block still has in flight -- those of iterations i_fail ..
+        // i_fail + NST - 1 -- so that no copy lands in a freed shared buffer.
+        if (tid == 0) {
+            atomicOr(a.err, ERR_TIMEOUT);
+            for (long long j = i_fail; j < i_fail + NST; ++j) {
+                if (blockIdx.x + j * G >= T) break;
+                (void)mbar_wait(&mbar[j % NST], (uint32_t)((j / NST) & 1), a.timeout_cycles);
+            }
+        }
+        __syncthreads();
+        return;
+    }
+
+    if (cur_set >= 0) {
+        fold();
+        write_set(cur_set);
+    }
+    for (int s = 0; s < 2; ++s) {
+        if (!set_written[s]) {
+            double* rec = a.block_rec + (size_t)blockIdx.x * a.rec_len + (size_t)s * (K * kNV + kNScal);
+            for (int i = tid; i < K * kNV + kNScal; i += nthreads) rec[i] = 0.0;
+        }
+    }
+
+    // ---- two-level last-block-done reduction (fixed order) ----
+    __threadfence();  // every thread's record writes are visible device-wide ...
+    __syncthreads();  // ... before thread 0 announces the block as done
+    const int g = blockIdx.x / a.group_size;
+    if (tid == 0) {
+        const int members = min(a.group_size, (int)gridDim.x - g * a.group_size);
+        const unsigned prev = atomicAdd(&a.group_count[g], 1u);
+        s_flag = prev == (unsigned)(members - 1);
+    }
+    __syncthreads();
+    if (!s_flag) return;
+    __threadfence();
+    {
+        const int b0 = g * a.group_size, b1 = min((int)gridDim.x, b0 + a.group_size);
+        for (int i = tid; i < a.rec_len; i += nthreads) {
+            double s = 0.0;
+            for (int b = b0; b < b1; ++b) s += __ldcg(a.block_rec + (size_t)b * a.rec_len + i);
+            a.group_rec[(size_t)g * a.rec_len + i] = s;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        a.group_count[g] = 0;
+        const unsigned prev = atomicAdd(a.top_count, 1u);
+        s_flag = prev == (unsigned)(a.ngroups - 1);
+    }
+    __syncthreads();
+    if (!s_flag) return;
+    __threadfence();
+    // the last group: totals into shared memory (reuse the stage area)
+    double* tot = reinterpret_cast<double*>(stages);
+    for (int i = tid; i < a.rec_len; i += nthreads) {
+        double s = 0.0;
+        for (int gg = 0; gg < a.ngroups; ++gg) s += __ldcg(a.group_rec + (size_t)gg * a.rec_len + i);
+        tot[i] = s;
+    }
+    __syncthreads();
+    if (tid == 0) *a.top_count = 0;
+
+    // ---- combine (a-8, Eqs. 4, 6, 7) in FP64 ----
+    const int L = K * kNV + kNScal;
+    const double SlnI = tot[K * kNV + 0];
+    const double Gm = tot[L + K * kNV + 0], Gdot = tot[L + K * kNV + 1];
+    if (tid == 0) a.out[0] = -SlnI + a.Nd * log(Gm / a.Nmc);
+    if constexpr (GR) {
+        for (int k = tid; k < K; k += nthreads) {
+            const ResValues rv = res_values(a, k, HV);
+            const ResParam rp = a.res[k];
+            double sn, cs;
+            sincos(rv.phi, &sn, &cs);
+            const double2 E1 = make_double2(cs, sn);
+            const double2 g1 = make_double2(rv.rho * cs, rv.rho * sn);
+            const double2 a1 = make_double2(-2.0 * rv.M, rv.G), a2 = make_double2(0.0, rv.M);
+            auto mul = [](double2 x, double2 y) { return make_double2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x); };
+            auto add = [](double2 x, double2 y) { return make_double2(x.x + y.x, x.y + y.y); };
+            auto scl = [](double s, double2 x) { return make_double2(s * x.x, s * x.y); };
+            auto ii = [](double2 x) { return make_double2(-x.y, x.x); };  // i x
+            const double* td = tot + k * kNV;
+            const double* tm = tot + L + k * kNV;
+            const double2 Q1d = make_double2(td[0], td[1]), Q2d = make_double2(td[2], td[3]);
+            const double2 Q1m = make_double2(tm[0], tm[1]), Q2m = make_double2(tm[2], tm[3]);
+            // kappa_{j1}, kappa_{j2}: dc/dtheta_j = kappa1 B + kappa2 B^2
+            const double2 zero = make_double2(0.0, 0.0);
+            const double2 kap1[4] = {E1, ii(g1), zero, zero};
+            const double2 kap2[4] = {zero, zero, mul(g1, a1), mul(g1, a2)};
+            double2 lam1[4], lam2[4], lam3[4];
+            if constexpr (HV) {
+                const double2 al = add(scl(rv.vr, E1), scl(rv.vp, ii(g1)));
+                const double2 u = add(scl(rv.vm, a1), scl(rv.vg, a2));
+                const double2 be = mul(g1, u);
+                lam1[0] = scl(rv.vp, ii(E1));
+                lam2[0] = mul(E1, u);
+                lam3[0] = zero;
+                lam1[1] = add(scl(rv.vr, ii(E1)), scl(-rv.vp, g1));
+                lam2[1] = ii(be);
+                lam3[1] = zero;
+                lam1[2] = zero;
+                lam2[2] = add(mul(g1, make_double2(-2.0 * rv.vm, rv.vg)), mul(al, a1));
+                lam3[2] = scl(2.0, mul(be, a1));
+                lam1[3] = zero;
+                lam2[3] = add(mul(g1, make_double2(0.0, rv.vm)), mul(al, a2));
+                lam3[3] = scl(2.0, mul(be, a2));
+            }
+            for (int j = 0; j < 4; ++j) {
+                const int idx = rp.idx[j];
+                if (idx < 0) continue;
+                const double gD = 2.0 * (mul(kap1[j], Q1d).x + mul(kap2[j], Q2d).x);
+                const double gM = 2.0 * (mul(kap1[j], Q1m).x + mul(kap2[j], Q2m).x);
+                a.out[1 + idx] = -gD + a.Nd * gM / Gm;
+                if constexpr (HV) {
+                    const double2 Q3d = make_double2(td[4], td[5]), P1d = make_double2(td[6], td[7]),
+                                  P2d = make_double2(td[8], td[9]);
+                    const double2 Q3m = make_double2(tm[4], tm[5]), P1m = make_double2(tm[6], tm[7]),
+                                  P2m = make_double2(tm[8], tm[9]);
+                    const double hD = 2.0 * (mul(kap1[j], P1d).x + mul(kap2[j], P2d).x + mul(lam1[j], Q1d).x +
+                                             mul(lam2[j], Q2d).x + mul(lam3[j], Q3d).x);
+                    const double hM = 2.0 * (mul(kap1[j], P1m).x + mul(kap2[j], P2m).x + mul(lam1[j], Q1m).x +
+                                             mul(lam2[j], Q2m).x + mul(lam3[j], Q3m).x);
+                    a.out[1 + a.P + idx] = -hD + a.Nd * (hM / Gm - gM * Gdot / (Gm * Gm));
+                }
+            }
+        }
+    }
+}
+
+}  // namespace pwa

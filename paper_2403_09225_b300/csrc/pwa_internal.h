@@ -1,0 +1,86 @@
+// pwa_internal.h -- handle layout shared by the libpwa translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pwa.h"
+#include "pass_kernel.cuh"
+
+namespace pwa {
+
+struct Tiling {
+    int W = 4;        // warps per block
+    int H = 2;        // lanes per event in the coherent-sum sweep
+    int NST = 2;      // tiles in flight per block
+    int bps = 0;      // blocks per SM requested (0 = as many as fit)
+    int E = 64;       // events per tile = 32 W / H
+    int KPW = 5;      // resonances owned by a warp in the second sweep
+    int grid = 0;     // blocks launched
+    int blocks_per_sm = 0;
+    size_t smem = 0;  // dynamic shared memory per block
+    uint32_t stage_bytes = 0;
+};
+
+// Rotation of resonance k's event positions inside a tile: with ev = 32/H
+// events per warp, the H lanes of one event read different resonances; the
+// rotation puts the rows those lanes read at the same step on different
+// shared-memory banks.
+__host__ __device__ inline int tile_shift(int k, int ev)
+{
+    return ev < 16 ? (k % (16 / ev)) * ev : 0;
+}
+
+}  // namespace pwa
+
+struct pwa_handle {
+    int K = 0, S = 0, P = 0;
+    cudaStream_t stream = nullptr;
+    long long n[2] = {0, 0};
+    double Nd = 0.0, Nmc = 0.0;
+    std::vector<pwa::ResParam> res;
+    pwa::ResParam* d_res = nullptr;
+    // device copies of the caller's events in the ABI layout (kept for re-tiling)
+    float* d_F[2] = {nullptr, nullptr};
+    float* d_m2[2] = {nullptr, nullptr};
+    float* d_w = nullptr;
+    // tiled layout streamed by the pass
+    unsigned char* d_tiles[2] = {nullptr, nullptr};
+    uint32_t tile_bytes[2] = {0, 0};
+    int ntiles[2] = {0, 0};
+    pwa::Tiling tiling;
+    int num_sms = 0;
+    // reduction scratch and results
+    double* d_block_rec = nullptr;
+    double* d_group_rec = nullptr;
+    unsigned* d_counts = nullptr;  // [ngroups] group counters, then the top counter
+    int group_size = 16, ngroups = 0, rec_len = 0;
+    double* d_theta = nullptr;
+    double* d_v = nullptr;
+    double* d_out = nullptr;        // [1 + 2P]
+    unsigned long long* d_bad = nullptr;
+    int* d_err = nullptr;
+    double* h_pin = nullptr;        // pinned staging: theta[P], v[P], out[1 + 2P], status
+    long long timeout_cycles = 0;
+    bool broken = false;
+    std::string err;
+};
+
+namespace pwa {
+
+using KernelFn = void (*)(const PassArgs);
+// kernel instance for (S, resonances per warp), one function per mode
+KernelFn pick_pass_nll(int S, int kpw);
+KernelFn pick_pass_grad(int S, int kpw);
+KernelFn pick_pass_hvp(int S, int kpw);
+
+// Enqueue one fused pass on device buffers (theta, v: device [P]; out: device [1+2P]).
+pwa_status launch_pass(pwa_handle* h, const double* d_theta, const double* d_v, double* d_out, int mode);
+// Read back and clear the device error flags; turns them into a status + message.
+pwa_status check_device_errors(pwa_handle* h);
+pwa_status set_error(pwa_handle* h, pwa_status st, const std::string& msg);
+pwa_status cuda_error(pwa_handle* h, cudaError_t e, const char* what);
+
+}  // namespace pwa

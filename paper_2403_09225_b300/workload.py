@@ -264,16 +264,23 @@ def blatt_weisskopf(J: int, q: np.ndarray) -> np.ndarray:
 
 def amplitudes(kin: Kinematics, table: list[Resonance], S: int) -> np.ndarray:
     """F[n, K, S] complex64 (interleaved re/im when viewed as float32)."""
-    n, K = kin.n, len(table)
-    F = np.empty((n, K, S), dtype=np.complex64)
-    radial = {}
-    for k, r in enumerate(table):
-        key = (r.channel, r.spin)
-        if key not in radial:
-            radial[key] = legendre(r.spin, kin.cos[r.channel]) * blatt_weisskopf(r.spin, kin.q[r.channel])
+    n = kin.n
+    spins = sorted({r.spin for r in table})
+    # radial part P_J(cos) B_J(q) per (channel, spin), phase e^{i s phi} per (channel, s)
+    radial = np.empty((n, 3, max(spins) + 1), dtype=np.float32)
+    for ch in range(3):
+        for J in spins:
+            radial[:, ch, J] = legendre(J, kin.cos[ch]) * blatt_weisskopf(J, kin.q[ch])
+    phase = np.empty((n, 3, S), dtype=np.complex64)
+    for ch in range(3):
+        e1 = np.exp(1j * kin.phi[ch])
+        p = np.ones(n, dtype=np.complex128)
         for s in range(S):
-            F[:, k, s] = (radial[key] * np.exp(1j * s * kin.phi[r.channel])).astype(np.complex64)
-    return F
+            phase[:, ch, s] = p
+            p = p * e1
+    ch = np.array([r.channel for r in table])
+    J = np.array([r.spin for r in table])
+    return radial[:, ch, J][:, :, None] * phase[:, ch, :]
 
 
 # ---------------------------------------------------------------------------
@@ -292,17 +299,34 @@ class Sample:
         return self.m2.shape[1]
 
 
+def _phase_space_chunk(args):
+    seed, n, table, S = args
+    rng = np.random.Generator(np.random.Philox(seed))
+    x, y = uniform_dalitz(rng, n)
+    kin = kinematics(rng, x, y)
+    return kin.m2.astype(np.float32), amplitudes(kin, table, S)
+
+
 def phase_space_sample(rng: np.random.Generator, n: int, table: list[Resonance], S: int,
-                       chunk: int = 1 << 20) -> Sample:
-    """n phase-space events (the MC sample; efficiency = 1, paper Eq. 2)."""
+                       chunk: int = 1 << 17, threads: int = 8) -> Sample:
+    """n phase-space events (the MC sample; efficiency = 1, paper Eq. 2).
+    Chunks draw from their own Philox streams seeded from rng, so the result
+    does not depend on the number of threads."""
+    from concurrent.futures import ThreadPoolExecutor
     m2 = np.empty((3, n), dtype=np.float32)
     F = np.empty((n, len(table), S), dtype=np.complex64)
-    for a in range(0, n, chunk):
-        b = min(n, a + chunk)
-        x, y = uniform_dalitz(rng, b - a)
-        kin = kinematics(rng, x, y)
-        m2[:, a:b] = kin.m2.astype(np.float32)
-        F[a:b] = amplitudes(kin, table, S)
+    starts = list(range(0, n, chunk))
+    seeds = rng.integers(0, 2 ** 63 - 1, size=len(starts))
+    jobs = [(int(sd), min(n, a + chunk) - a, table, S) for sd, a in zip(seeds, starts)]
+
+    def run(i):
+        a = starts[i]
+        cm2, cF = _phase_space_chunk(jobs[i])
+        m2[:, a:a + cm2.shape[1]] = cm2
+        F[a:a + cm2.shape[1]] = cF
+
+    with ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
+        list(ex.map(run, range(len(jobs))))
     return Sample(m2=m2, F=F)
 
 
