@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the fused NLL + gradient + HVP pass.
+
+Workload: the paper-scale configuration -- a three-body decay (parent
+3.097 GeV; daughters 0.1396, 0.1396, 1.0195 GeV) with K = 20 Breit-Wigner
+resonances over the three channels (spins 0..4), S = 4 complex FP32 amplitude
+projections per resonance, 1e6 data events drawn from I(theta_true) by
+accept-reject and 5e6 phase-space MC events; 78 real parameters.  All inputs
+are synthetic and seeded (the paper's psi(3686) -> phi K+ K- sample is not
+available).
+
+One step = one fused pass over all events (parameter unpack, Breit-Wigner,
+coherent sums, adjoint gradient sweep, forward-over-reverse HVP, FP64
+reductions and the Eq. 4-7 combination), i.e. one Newton-CG inner iteration.
+Metric: event-amplitude evaluations per second, (N_data + N_MC) * K / time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(the path is not sharded: replicas only); value = all ranks' units / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NLL+grad+HVP event-amplitude evaluations/s (fused pass)"
+UNIT = "event*amp/s"
+CONFIG_NAME = "paper"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def bytes_per_pass(nd, nm, K, S):
+    """Algorithmic HBM bytes of one pass: F (8 S bytes per event-amplitude),
+    three m^2 values per event, one weight per data event."""
+    return nd * (8 * K * S + 12 + 4) + nm * (8 * K * S + 12)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during a timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        time.sleep(0.2)
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_intensity_fn(table, K, S):
+    """I(e) at the table's parameter values computed by the library (used to
+    accept-reject the data sample)."""
+    from types import SimpleNamespace
+    from paper_2403_09225_b300 import binding
+    from paper_2403_09225_b300 import workload as W
+    theta = W.free_parameter_vector(table)
+    one = SimpleNamespace(m2=np.full((3, 1), 1.0, np.float32), F=np.ones((1, K, S), np.complex64), w=None)
+
+    def fn(m2, F):
+        L = binding.Likelihood(one, SimpleNamespace(m2=m2, F=F, w=None), table, K, S)
+        try:
+            return L.intensity(theta, sample=1).astype(np.float64)
+        finally:
+            L.close()
+    return fn
+
+
+def build_workload(scale: float = 1.0):
+    from paper_2403_09225_b300 import workload as W
+    cfg = W.CONFIGS[CONFIG_NAME]
+    table = W.make_table(cfg)
+    return W.make_workload(cfg, intensity=gpu_intensity_fn(table, cfg.K, cfg.S),
+                           n_data=int(round(cfg.n_data * scale)), n_mc=int(round(cfg.n_mc * scale)))
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle (FP64, one thread) on a bounded sample of the workload."""
+    if rank != 0:
+        return None
+    import oracle
+    from paper_2403_09225_b300 import workload as W
+    cfg = W.CONFIGS[CONFIG_NAME]
+    table = W.make_table(cfg)
+    model = oracle.Model.from_table(table, cfg.S)
+    frac = 1.0 / 60.0
+    nd, nm = int(cfg.n_data * frac), int(cfg.n_mc * frac)
+    wl = W.make_workload(cfg, intensity=None, n_data=nd, n_mc=nm)
+    th = W.random_starts(wl, 1)[0]
+    v = np.linspace(-1.0, 1.0, model.P)
+    for _ in range(min(args.warmup, 1)):
+        oracle.nll_grad_hvp(model, th, v, wl.data, wl.mc)
+    steps = max(1, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.nll_grad_hvp(model, th, v, wl.data, wl.mc)
+    dt = time.perf_counter() - t0
+    value = steps * (nd + nm) * cfg.K / dt
+    sample = ("%d data + %d MC phase-space events (1/60 of the workload), K=%d, S=%d, %d steps"
+              % (nd, nm, cfg.K, cfg.S, steps))
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": min(args.warmup, 1), "ms_per_step": dt / steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": "paper-scale K=20 S=4 (bounded CPU sample)",
+                                        "n_data": nd, "n_mc": nm, "K": cfg.K, "S": cfg.S},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def cpu_baseline_leg():
+    """The oracle as it stands, single-threaded, on a bounded sample."""
+    import oracle
+    from paper_2403_09225_b300 import workload as W
+    cfg = W.CONFIGS[CONFIG_NAME]
+    table = W.make_table(cfg)
+    model = oracle.Model.from_table(table, cfg.S)
+    nd, nm = cfg.n_data // 60, cfg.n_mc // 60
+    wl = W.make_workload(cfg, intensity=None, n_data=nd, n_mc=nm)
+    th = W.random_starts(wl, 1)[0]
+    v = np.linspace(-1.0, 1.0, model.P)
+    reps = 8
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.nll_grad_hvp(model, th, v, wl.data, wl.mc)
+    dt = time.perf_counter() - t0
+    return {"value": reps * (nd + nm) * cfg.K / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d data + %d MC events (1/60 of the workload), K=%d, S=%d, %d fused evaluations, "
+                      "%.1f s" % (nd, nm, cfg.K, cfg.S, reps, dt)}
+
+
+def fit_metric(L, wl, n_starts: int, time_limit: float):
+    """Newton-CG fits from random starts; a fit reaches the global minimum when
+    its NLL is within 0.01 of the best NLL over all fits (including one from
+    theta_true)."""
+    from paper_2403_09225_b300 import workload as W
+    starts = W.random_starts(wl, n_starts)
+    ref, ref_info = L.fit(wl.theta_true, xtol=1e-8, time_limit_s=time_limit)
+    results = []
+    t0 = time.perf_counter()
+    for s in starts:
+        _, info = L.fit(s, xtol=1e-8, time_limit_s=time_limit)
+        results.append(info)
+    total = time.perf_counter() - t0
+    best = min([ref_info["nll"]] + [r["nll"] for r in results])
+    ok = sum(1 for r in results if r["nll"] <= best + 0.01)
+    return {"starts": n_starts, "reached_global_min": ok, "gpu_seconds": total,
+            "fits_to_global_min_per_s": ok / total if total > 0 else 0.0,
+            "best_nll": best, "passes": int(sum(r["n_fev"] + r["n_hvp"] for r in results)),
+            "statuses": sorted({r["status"] for r in results}), "xtol": 1e-8,
+            "time_limit_s": time_limit}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fits", type=int, default=2, help="random-start fits for the fit metric (0: skip)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tiling", default="", help="warps,lanes_per_event,stages[,blocks_per_sm] (default: library's)")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="event counts relative to the workload (profiling captures only; default 1)")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res))
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_2403_09225_b300 import binding
+    wl = build_workload(args.scale)
+    K, S, nd, nm = wl.K, wl.S, wl.data.n, wl.mc.n
+    stream = torch.cuda.current_stream()
+    L = binding.make_likelihood(wl, stream=stream.cuda_stream)
+    if args.tiling:
+        L.set_tiling(*[int(x) for x in args.tiling.split(",")])
+    P = L.P
+    rng = np.random.default_rng(1)
+    th = wl.theta_true + 0.01 * rng.standard_normal(P)
+    v = rng.standard_normal(P)
+    d_th = torch.tensor(th, dtype=torch.float64, device="cuda")
+    d_v = torch.tensor(v, dtype=torch.float64, device="cuda")
+    d_out = torch.empty(1 + 2 * P, dtype=torch.float64, device="cuda")
+
+    # ---- device-resident timing: K back-to-back fused passes ----
+    for _ in range(max(3, args.warmup)):
+        L.eval_device(d_th.data_ptr(), d_v.data_ptr(), d_out.data_ptr(), True, True)
+    torch.cuda.synchronize()
+    L.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            L.eval_device(d_th.data_ptr(), d_v.data_ptr(), d_out.data_ptr(), True, True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    L.sync()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = (nd + nm) * K
+    value = world * units / (ms * 1e-3)
+    bpp = bytes_per_pass(nd, nm, K, S)
+    peak, peak_kind = peaks()
+    achieved = bpp / (ms * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with host vectors (pinned staging inside) ----
+    e2e_steps = max(1, args.steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        L.eval(th, v)
+    e2e_dt = time.perf_counter() - t0
+    e2e_ms = e2e_dt / e2e_steps * 1e3
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * units / (e2e_ms * 1e-3)
+
+    fit = None
+    if args.fits > 0 and rank == 0:
+        fit = fit_metric(L, wl, args.fits, time_limit=20.0)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_leg()
+
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic_paper_hvp.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                traffic = json.load(f).get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    til = L.get_tiling()
+    if rank == 0:
+        res = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "paper-scale: K=20, S=4, 1e6 data (accept-reject from I) + 5e6 MC, P=78"
+                       + ("" if args.scale == 1.0 else " (scaled x%g for profiling)" % args.scale),
+                       "n_data": nd, "n_mc": nm, "K": K, "S": S, "P": P, "parallelism": "replicas" if world > 1
+                       else "single", "l2": "inputs (%.2f GB) larger than L2, no flush" % (bpp / 1e9),
+                       "tiling": til},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": bpp},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * P * 8,
+                    "d2h_bytes_per_step": (1 + 2 * P) * 8 + 12, "ms_per_step": e2e_ms},
+            "gpu_launches": args.steps,
+            "clocks": clk.summary(),
+        }
+        if cpu is not None:
+            res["cpu_baseline"] = cpu
+        if fit is not None:
+            res["fit"] = fit
+        print(json.dumps(res))
+    L.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -183,18 +183,18 @@ void pwa_fit_opts_default(pwa_fit_opts* opts);
 /* Use another CUDA stream (cudaStream_t, NULL = default) for later calls. */
 pwa_status pwa_set_stream(pwa_handle* h, void* cuda_stream);
 
-/* Tiling of the streaming kernel (the autotuner's knobs).  warps: warps per
- * block (1, 2, 4, 8 or 16); lanes_per_event: lanes that share one event in
- * the coherent-sum sweep (1, 2, 4 or 8, at most 32 * warps / 32); stages:
- * tiles in flight per block (2..4); blocks_per_sm: 0 = as many as fit.  The
- * tile size is 32 * warps / lanes_per_event events.  Re-lays the events out
- * on the device.  Errors: PWA_EINVAL when the combination does not fit. */
-pwa_status pwa_set_tiling(pwa_handle* h, int warps, int lanes_per_event, int stages,
-                          int blocks_per_sm);
+/* Tiling of the streaming kernel (the autotuner's knobs).  Events are cut
+ * into tiles of 32; warps: warps per block (1, 2, 4 or 8) -- the block shares
+ * one tile, W lanes share an event in the coherent-sum sweep and each warp
+ * owns ceil(K / warps) <= 8 resonances in the second sweep; stages: tiles in
+ * flight per block (2..4); blocks_per_sm: 0 = as many as fit.  Re-lays the
+ * events out on the device.  Errors: PWA_EINVAL when the combination is not
+ * compiled or does not fit in shared memory (the previous tiling stays). */
+pwa_status pwa_set_tiling(pwa_handle* h, int warps, int stages, int blocks_per_sm);
 
-/* Current tiling and geometry: fills (warps, lanes_per_event, stages,
- * blocks_per_sm, events_per_tile, grid_blocks, smem_bytes_per_block). */
-pwa_status pwa_get_tiling(const pwa_handle* h, int out7[7]);
+/* Current tiling and geometry: fills (warps, stages, blocks_per_sm,
+ * events_per_tile, grid_blocks, smem_bytes_per_block). */
+pwa_status pwa_get_tiling(const pwa_handle* h, int out6[6]);
 
 /* Message describing the first failure of the handle's last call. */
 const char* pwa_last_error(const pwa_handle* h);

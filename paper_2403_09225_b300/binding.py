@@ -80,7 +80,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pwa_newton_cg_fit": (st, [H, dp, ctypes.POINTER(pwa_fit_opts), dp, ctypes.POINTER(pwa_fit_result)]),
         "pwa_fit_opts_default": (None, [ctypes.POINTER(pwa_fit_opts)]),
         "pwa_set_stream": (st, [H, vp]),
-        "pwa_set_tiling": (st, [H, i, i, i, i]),
+        "pwa_set_tiling": (st, [H, i, i, i]),
         "pwa_get_tiling": (st, [H, ip]),
         "pwa_last_error": (ctypes.c_char_p, [H]),
         "pwa_destroy": (None, [H]),
@@ -261,14 +261,13 @@ class Likelihood:
                      "converged": st == PWA_OK}
 
     # -- tiling --
-    def set_tiling(self, warps: int, lanes_per_event: int, stages: int, blocks_per_sm: int = 0):
-        self._check(lib().pwa_set_tiling(self._h, warps, lanes_per_event, stages, blocks_per_sm))
+    def set_tiling(self, warps: int, stages: int = 2, blocks_per_sm: int = 0):
+        self._check(lib().pwa_set_tiling(self._h, warps, stages, blocks_per_sm))
 
     def get_tiling(self) -> dict:
-        out = (ctypes.c_int * 7)()
+        out = (ctypes.c_int * 6)()
         self._check(lib().pwa_get_tiling(self._h, out))
-        keys = ("warps", "lanes_per_event", "stages", "blocks_per_sm", "events_per_tile", "grid_blocks",
-                "smem_bytes")
+        keys = ("warps", "stages", "blocks_per_sm", "events_per_tile", "grid_blocks", "smem_bytes")
         return dict(zip(keys, list(out)))
 
 

@@ -35,6 +35,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace pwa {
 
 constexpr int kNV = 10;        // FP64 values per resonance and sample set
@@ -213,26 +215,36 @@ __device__ __forceinline__ float pick3(int ch, float a0, float a1, float a2)
 // the fused pass
 // ---------------------------------------------------------------------------
 
-template <int MODE, int S, int KPW>
-__global__ void __launch_bounds__(kMaxThreads) pass_kernel(const PassArgs a)
+// Tile shape: kTileE = 32 events per tile; a block has W warps and W lanes
+// share one event in the coherent-sum sweep (each takes every W-th resonance),
+// so a warp covers 32/W events and the block covers the tile; in the second
+// sweep lane l handles event l and warp w owns resonances [w KPW, (w+1) KPW).
+constexpr int kTileE = 32;
+
+template <int MODE, int S, int W, int KPW>
+__global__ void __launch_bounds__(32 * W) pass_kernel(const PassArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr bool HV = MODE == MODE_HVP;
     constexpr bool GR = MODE >= MODE_GRAD;
+    constexpr int E = kTileE;
+    constexpr int H = W;                       // lanes per event in sweep 1
+    constexpr int EV = 32 / H;                 // events per warp in sweep 1
     constexpr int NVM = HV ? kNV : 4;          // accumulated reals per resonance
-    constexpr int V = GR ? NVM * KPW : 1;       // per-warp accumulated reals
+    constexpr int V = GR ? NVM * KPW : 1;      // per-warp accumulated reals
     constexpr int SLOTS = (V + 31) / 32;
+    constexpr int NT = 32 * W;
+    using AVec = typename std::conditional<HV, float4, float2>::type;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int K = a.K, E = a.E, H = a.H, W = a.W, NST = a.NST;
-    const int ev = 32 / H;
-    const int nthreads = blockDim.x;
+    const int K = a.K, NST = a.NST;
 
     unsigned char* stages = smem;
     KConst* kc = reinterpret_cast<KConst*>(smem + (size_t)NST * a.stage_bytes);
-    float4* abuf = reinterpret_cast<float4*>(kc + K);   // [S][E] (A_s, Adot_s)
-    float2* ab = reinterpret_cast<float2*>(abuf + S * E); // [E] (a, b)
-    double* red = reinterpret_cast<double*>(ab + E);      // [W][4]
+    // sweep-2 inputs per (s, event): a A_s (and a Adot_s - b A_s for HVP)
+    AVec* abuf = reinterpret_cast<AVec*>(kc + K);
+    float2* Bs = reinterpret_cast<float2*>(reinterpret_cast<float4*>(kc + K) + S * E);  // [K][E] rotated
+    double* red = reinterpret_cast<double*>(Bs + K * E);                                 // [W][4]
     uint64_t* mbar = reinterpret_cast<uint64_t*>(red + 4 * W);
     __shared__ int s_flag;
 
@@ -252,10 +264,10 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const PassArgs a)
             }
         }
     }
-    for (int k = tid; k < K; k += nthreads) kc[k] = make_kconst(a, k, HV, ev);
+    for (int k = tid; k < K; k += NT) kc[k] = make_kconst(a, k, HV, EV);
     __syncthreads();
 
-    // FP32 accumulators (phase 2: per owned resonance; phase 1: per-event scalars)
+    // FP32 accumulators (sweep 2: per owned resonance; sweep 1: per-event scalars)
     float acc[GR ? KPW : 1][GR ? NVM : 1];
 #pragma unroll
     for (int j = 0; j < (GR ? KPW : 1); ++j)
@@ -268,7 +280,15 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const PassArgs a)
     double dsc0 = 0.0, dsc1 = 0.0;
 
     const int k0 = warp * KPW;
-    const int h = lane / ev, el = lane % ev;
+    const int h = lane / EV, el = lane % EV;
+    const int e1 = warp * EV + el;  // this lane's event in sweep 1
+    // sweep 1 visits k = h, h + H, ...: they share one rotation (it depends on
+    // k mod (H/2)), so the lane's F and BW offsets advance by constants
+    const int p1 = (e1 + (h < K ? kc[h].shift : 0)) & (E - 1);
+    // sweep 2: the rotated position of this lane's event in each owned row
+    int p2[GR ? KPW : 1];
+#pragma unroll
+    for (int j = 0; j < (GR ? KPW : 1); ++j) p2[j] = (lane + (k0 + j < K ? kc[k0 + j].shift : 0)) & (E - 1);
     int cur_set = -1;
     bool set_written[2] = {false, false};
     long long i_fail = -1;  // loop iteration whose tile never arrived
@@ -276,6 +296,11 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const PassArgs a)
     // fold the per-lane FP32 sums into per-lane FP64 slots (fixed order)
     auto fold = [&]() {
         if constexpr (GR) {
+            // lane l keeps value l + 32 t of the warp's V sums (FP32 select,
+            // then one FP64 add per slot: the FP64 pipe is narrow)
+            float mine[SLOTS];
+#pragma unroll
+            for (int t = 0; t < SLOTS; ++t) mine[t] = 0.f;
 #pragma unroll
             for (int j = 0; j < KPW; ++j)
 #pragma unroll
@@ -283,8 +308,10 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const PassArgs a)
                     const float s = warp_sum(acc[j][q]);
                     acc[j][q] = 0.f;
                     const int vi = j * NVM + q;
-                    if ((vi & 31) == lane) dacc[vi >> 5] += (double)s;
+                    mine[vi >> 5] = (vi & 31) == lane ? s : mine[vi >> 5];
                 }
+#pragma unroll
+            for (int t = 0; t < SLOTS; ++t) dacc[t] += (double)mine[t];
         }
         const float t0 = warp_sum(sc0), t1 = warp_sum(sc1);
         sc0 = sc1 = 0.f;
@@ -350,23 +377,25 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const PassArgs a)
             break;
         }
         const float2* Fs = reinterpret_cast<const float2*>(stages + (size_t)st * a.stage_bytes);
-        const float* m2s = reinterpret_cast<const float*>(Fs + (size_t)K * S * E);
-        const float* ws = m2s + 3 * E;
+        const float* m2s = reinterpret_cast<const float*>(Fs + K * S * E);
         const long long e_base = lt * E;
         const int nvalid = (int)min((long long)E, a.nev[smp] - e_base);
 
-        // ---- phase 1: coherent sums, intensity, per-event weights ----
-        for (int item = warp; item < E / ev; item += W) {
-            const int e = item * ev + el;
+        // ---- sweep 1: BW, coherent sums, intensity, per-event weights ----
+        {
+            const int e = e1;
             const float m20 = m2s[e], m21 = m2s[E + e], m22 = m2s[2 * E + e];
             float Ar[S], Ai[S], Dr[S], Di[S];
 #pragma unroll
             for (int s = 0; s < S; ++s) Ar[s] = Ai[s] = Dr[s] = Di[s] = 0.f;
+            const float2* Fk = Fs + h * S * E + p1;
+            float2* Bk = Bs + h * E + p1;
 #pragma unroll 2
-            for (int k = h; k < K; k += H) {
+            for (int k = h; k < K; k += H, Fk += H * S * E, Bk += H * E) {
                 const KConst c = kc[k];
                 float br, bi;
                 breit_wigner(c, pick3(c.ch, m20, m21, m22), br, bi);
+                if constexpr (GR) *Bk = make_float2(br, bi);
                 const float cr = c.gre * br - c.gim * bi, ci = c.gre * bi + c.gim * br;
                 float dr = 0.f, di = 0.f;
                 if constexpr (HV) {
@@ -375,9 +404,6 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const PassArgs a)
                     dr = br * tr - bi * ti;
                     di = br * ti + bi * tr;
                 }
-                int p = e + c.shift;
-                p = p >= E ? p - E : p;
-                const float2* Fk = Fs + (size_t)k * S * E + p;
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
                     const float2 f = Fk[s * E];
@@ -389,7 +415,8 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const PassArgs a)
                     }
                 }
             }
-            for (int off = ev; off < 32; off <<= 1) {
+#pragma unroll
+            for (int off = EV; off < 32; off <<= 1) {
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
                     Ar[s] += __shfl_xor_sync(0xffffffffu, Ar[s], off);
@@ -400,110 +427,113 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const PassArgs a)
                     }
                 }
             }
-            if (h == 0) {
-                float I = 0.f, Id = 0.f;
+            // every lane of the event now holds A and Adot
+            float I = 0.f, Id = 0.f;
 #pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    I = fmaf(Ar[s], Ar[s], fmaf(Ai[s], Ai[s], I));
-                    if constexpr (HV) Id = fmaf(Ar[s], Dr[s], fmaf(Ai[s], Di[s], Id));
+            for (int s = 0; s < S; ++s) {
+                I = fmaf(Ar[s], Ar[s], fmaf(Ai[s], Ai[s], I));
+                if constexpr (HV) Id = fmaf(Ar[s], Dr[s], fmaf(Ai[s], Di[s], Id));
+            }
+            Id *= 2.f;
+            const bool valid = e < nvalid;
+            float wa = 0.f, wb = 0.f;  // (a, b) = (w/I, w Idot/I^2) for data, (1, 0) for MC
+            if (smp == 0) {
+                const float w = m2s[3 * E + e];
+                const bool good = I > 0.f && I < INFINITY;
+                if (valid && good) {
+                    const float rI = __fdividef(1.0f, I);
+                    wa = w * rI;
+                    wb = wa * Id * rI;
                 }
-                Id *= 2.f;
-                const bool valid = e < nvalid;
-                float wa = 0.f, wb = 0.f;
-                if (smp == 0) {
-                    const float w = ws[e];
-                    const bool good = I > 0.f && I < INFINITY;
+                if (h == 0) {
                     if (valid && !good) {
                         atomicMin(a.bad, (unsigned long long)(e_base + e));
                         atomicOr(a.err, ERR_NONFINITE);
                     }
-                    if (valid && good) {
-                        const float rI = 1.0f / I;
-                        wa = w * rI;
-                        wb = wa * Id * rI;
-                        sc0 += w * logf(I);
-                    }
-                } else {
+                    if (valid && good) sc0 += w * logf(I);
+                }
+            } else {
+                if (valid) wa = 1.f;
+                if (h == 0) {
                     if (valid && !(I < INFINITY)) {
                         atomicMin(a.bad, (unsigned long long)(a.nev[0] + e_base + e));
                         atomicOr(a.err, ERR_NONFINITE);
                     }
                     if (valid) {
-                        wa = 1.f;
                         sc0 += I;
                         sc1 += Id;
                     }
                 }
-                if constexpr (GR) {
+            }
+            if constexpr (GR) {
+                // lane h of the event stores the components s = h, h + H, ...
 #pragma unroll
-                    for (int s = 0; s < S; ++s) abuf[s * E + e] = make_float4(Ar[s], Ai[s], Dr[s], Di[s]);
-                    ab[e] = make_float2(wa, wb);
+                for (int s = 0; s < S; ++s) {
+                    if ((s % H) != h) continue;
+                    if constexpr (HV)
+                        abuf[s * E + e] = make_float4(wa * Ar[s], wa * Ai[s], fmaf(wa, Dr[s], -wb * Ar[s]),
+                                                      fmaf(wa, Di[s], -wb * Ai[s]));
+                    else
+                        abuf[s * E + e] = make_float2(wa * Ar[s], wa * Ai[s]);
                 }
             }
         }
 
         if constexpr (GR) {
             __syncthreads();
-            // ---- phase 2: second sweep, per-resonance sums ----
+            // ---- sweep 2: per-resonance sums for event `lane` ----
             if (k0 < K) {
-                for (int c0 = 0; c0 < E; c0 += 32) {
-                    const int e = c0 + lane;
-                    float Ar[S], Ai[S], Dr[S], Di[S];
+                float Ar[S], Ai[S], Dr[S], Di[S];  // a A_s and (a Adot_s - b A_s)
 #pragma unroll
-                    for (int s = 0; s < S; ++s) {
-                        const float4 q = abuf[s * E + e];
-                        Ar[s] = q.x;
-                        Ai[s] = q.y;
+                for (int s = 0; s < S; ++s) {
+                    const AVec q = abuf[s * E + lane];
+                    Ar[s] = q.x;
+                    Ai[s] = q.y;
+                    if constexpr (HV) {
                         Dr[s] = q.z;
                         Di[s] = q.w;
                     }
-                    const float2 wab = ab[e];
-                    const float m20 = m2s[e], m21 = m2s[E + e], m22 = m2s[2 * E + e];
+                }
 #pragma unroll
-                    for (int j = 0; j < KPW; ++j) {
-                        const int k = k0 + j;
-                        if (k >= K) break;
-                        const KConst c = kc[k];
-                        float br, bi;
-                        breit_wigner(c, pick3(c.ch, m20, m21, m22), br, bi);
-                        int p = e + c.shift;
-                        p = p >= E ? p - E : p;
-                        const float2* Fk = Fs + (size_t)k * S * E + p;
-                        float xr = 0.f, xi = 0.f, yr = 0.f, yi = 0.f;   // D, Ddot
+                for (int j = 0; j < KPW; ++j) {
+                    const int k = k0 + j;
+                    if (k >= K) break;
+                    const float2 B = Bs[k * E + p2[j]];
+                    const float br = B.x, bi = B.y;
+                    const float2* Fk = Fs + k * S * E + p2[j];
+                    // Dh = sum_s conj(a A_s) F, Dt = sum_s conj(a Adot_s - b A_s) F (two chains each)
+                    float xr[2] = {0.f, 0.f}, xi[2] = {0.f, 0.f}, yr[2] = {0.f, 0.f}, yi[2] = {0.f, 0.f};
 #pragma unroll
-                        for (int s = 0; s < S; ++s) {
-                            const float2 f = Fk[s * E];
-                            xr = fmaf(Ar[s], f.x, fmaf(Ai[s], f.y, xr));
-                            xi = fmaf(Ar[s], f.y, fmaf(-Ai[s], f.x, xi));
-                            if constexpr (HV) {
-                                yr = fmaf(Dr[s], f.x, fmaf(Di[s], f.y, yr));
-                                yi = fmaf(Dr[s], f.y, fmaf(-Di[s], f.x, yi));
-                            }
-                        }
-                        // Dh = a D
-                        const float hr = wab.x * xr, hi = wab.x * xi;
-                        // B^2
-                        const float b2r = br * br - bi * bi, b2i = 2.f * br * bi;
-                        acc[j][0] = fmaf(hr, br, fmaf(-hi, bi, acc[j][0]));
-                        acc[j][1] = fmaf(hr, bi, fmaf(hi, br, acc[j][1]));
-                        acc[j][2] = fmaf(hr, b2r, fmaf(-hi, b2i, acc[j][2]));
-                        acc[j][3] = fmaf(hr, b2i, fmaf(hi, b2r, acc[j][3]));
+                    for (int s = 0; s < S; ++s) {
+                        const float2 f = Fk[s * E];
+                        const int q = s & 1;
+                        xr[q] = fmaf(Ar[s], f.x, fmaf(Ai[s], f.y, xr[q]));
+                        xi[q] = fmaf(Ar[s], f.y, fmaf(-Ai[s], f.x, xi[q]));
                         if constexpr (HV) {
-                            const float b3r = b2r * br - b2i * bi, b3i = b2r * bi + b2i * br;
-                            // Dt = a Ddot - b D
-                            const float tr = fmaf(wab.x, yr, -wab.y * xr), ti = fmaf(wab.x, yi, -wab.y * xi);
-                            acc[j][4] = fmaf(hr, b3r, fmaf(-hi, b3i, acc[j][4]));
-                            acc[j][5] = fmaf(hr, b3i, fmaf(hi, b3r, acc[j][5]));
-                            acc[j][6] = fmaf(tr, br, fmaf(-ti, bi, acc[j][6]));
-                            acc[j][7] = fmaf(tr, bi, fmaf(ti, br, acc[j][7]));
-                            acc[j][8] = fmaf(tr, b2r, fmaf(-ti, b2i, acc[j][8]));
-                            acc[j][9] = fmaf(tr, b2i, fmaf(ti, b2r, acc[j][9]));
+                            yr[q] = fmaf(Dr[s], f.x, fmaf(Di[s], f.y, yr[q]));
+                            yi[q] = fmaf(Dr[s], f.y, fmaf(-Di[s], f.x, yi[q]));
                         }
+                    }
+                    const float hr = xr[0] + xr[1], hi = xi[0] + xi[1];
+                    const float b2r = fmaf(br, br, -bi * bi), b2i = 2.f * br * bi;
+                    acc[j][0] = fmaf(hr, br, fmaf(-hi, bi, acc[j][0]));
+                    acc[j][1] = fmaf(hr, bi, fmaf(hi, br, acc[j][1]));
+                    acc[j][2] = fmaf(hr, b2r, fmaf(-hi, b2i, acc[j][2]));
+                    acc[j][3] = fmaf(hr, b2i, fmaf(hi, b2r, acc[j][3]));
+                    if constexpr (HV) {
+                        const float tr = yr[0] + yr[1], ti = yi[0] + yi[1];
+                        const float b3r = fmaf(b2r, br, -b2i * bi), b3i = fmaf(b2r, bi, b2i * br);
+                        acc[j][4] = fmaf(hr, b3r, fmaf(-hi, b3i, acc[j][4]));
+                        acc[j][5] = fmaf(hr, b3i, fmaf(hi, b3r, acc[j][5]));
+                        acc[j][6] = fmaf(tr, br, fmaf(-ti, bi, acc[j][6]));
+                        acc[j][7] = fmaf(tr, bi, fmaf(ti, br, acc[j][7]));
+                        acc[j][8] = fmaf(tr, b2r, fmaf(-ti, b2i, acc[j][8]));
+                        acc[j][9] = fmaf(tr, b2i, fmaf(ti, b2r, acc[j][9]));
                     }
                 }
             }
         }
-        __syncthreads();  // the stage and abuf may now be overwritten
+        __syncthreads();  // the stage, abuf and Bs may now be overwritten
         if (tid == 0) {
             const long long tn = t + (long long)NST * G;
             if (tn < T) {
@@ -542,7 +572,7 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const PassArgs a)
     for (int s = 0; s < 2; ++s) {
         if (!set_written[s]) {
             double* rec = a.block_rec + (size_t)blockIdx.x * a.rec_len + (size_t)s * (K * kNV + kNScal);
-            for (int i = tid; i < K * kNV + kNScal; i += nthreads) rec[i] = 0.0;
+            for (int i = tid; i < K * kNV + kNScal; i += NT) rec[i] = 0.0;
         }
     }
 
@@ -560,7 +590,7 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const PassArgs a)
     __threadfence();
     {
         const int b0 = g * a.group_size, b1 = min((int)gridDim.x, b0 + a.group_size);
-        for (int i = tid; i < a.rec_len; i += nthreads) {
+        for (int i = tid; i < a.rec_len; i += NT) {
             double s = 0.0;
             for (int b = b0; b < b1; ++b) s += __ldcg(a.block_rec + (size_t)b * a.rec_len + i);
             a.group_rec[(size_t)g * a.rec_len + i] = s;
@@ -578,7 +608,7 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const PassArgs a)
     __threadfence();
     // the last group: totals into shared memory (reuse the stage area)
     double* tot = reinterpret_cast<double*>(stages);
-    for (int i = tid; i < a.rec_len; i += nthreads) {
+    for (int i = tid; i < a.rec_len; i += NT) {
         double s = 0.0;
         for (int gg = 0; gg < a.ngroups; ++gg) s += __ldcg(a.group_rec + (size_t)gg * a.rec_len + i);
         tot[i] = s;
@@ -592,7 +622,7 @@ __global__ void __launch_bounds__(kMaxThreads) pass_kernel(const PassArgs a)
     const double Gm = tot[L + K * kNV + 0], Gdot = tot[L + K * kNV + 1];
     if (tid == 0) a.out[0] = -SlnI + a.Nd * log(Gm / a.Nmc);
     if constexpr (GR) {
-        for (int k = tid; k < K; k += nthreads) {
+        for (int k = tid; k < K; k += NT) {
             const ResValues rv = res_values(a, k, HV);
             const ResParam rp = a.res[k];
             double sn, cs;

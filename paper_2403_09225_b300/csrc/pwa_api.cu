@@ -90,7 +90,7 @@ __global__ void intensity_kernel(pwa::PassArgs a, int smp, int S, float* __restr
     extern __shared__ __align__(16) unsigned char smem_i[];
     pwa::KConst* kc = reinterpret_cast<pwa::KConst*>(smem_i);
     const int K = a.K, E = a.E;
-    const int ev = 32 / a.H;
+    const int ev = 32 / a.W;
     for (int k = threadIdx.x; k < K; k += blockDim.x) kc[k] = pwa::make_kconst(a, k, false, ev);
     __syncthreads();
     const long long n = a.nev[smp];
@@ -128,25 +128,30 @@ __global__ void intensity_kernel(pwa::PassArgs a, int smp, int S, float* __restr
 
 using pwa::KernelFn;
 
-KernelFn pick_kernel(int mode, int S, int kpw)
+KernelFn pick_kernel(int mode, int S, int W, int kpw)
 {
+#define PWA_PICK(m)                                       \
+    switch (S) {                                          \
+        case 1: return pwa::pick_pass_##m##_s1(W, kpw);   \
+        case 2: return pwa::pick_pass_##m##_s2(W, kpw);   \
+        case 3: return pwa::pick_pass_##m##_s3(W, kpw);   \
+        case 4: return pwa::pick_pass_##m##_s4(W, kpw);   \
+        default: return nullptr;                          \
+    }
     switch (mode) {
-        case pwa::MODE_NLL: return pwa::pick_pass_nll(S, kpw);
-        case pwa::MODE_GRAD: return pwa::pick_pass_grad(S, kpw);
-        case pwa::MODE_HVP: return pwa::pick_pass_hvp(S, kpw);
+        case pwa::MODE_NLL: PWA_PICK(nll)
+        case pwa::MODE_GRAD: PWA_PICK(grad)
+        case pwa::MODE_HVP: PWA_PICK(hvp)
         default: return nullptr;
     }
-}
-
-int kpw_supported(int kpw)
-{
-    return kpw == 7 ? 8 : (kpw >= 1 && kpw <= 8 ? kpw : -1);
+#undef PWA_PICK
 }
 
 size_t smem_bytes(const Tiling& t, int K, int S)
 {
+    // stages | KConst[K] | sweep-2 vectors [S][E] float4 | BW cache [K][E] float2 | [W][4] doubles | mbarriers
     return (size_t)t.NST * t.stage_bytes + (size_t)K * sizeof(pwa::KConst) + (size_t)S * t.E * 16 +
-           (size_t)t.E * 8 + (size_t)t.W * 32 + (size_t)t.NST * 8;
+           (size_t)K * t.E * 8 + (size_t)t.W * 32 + (size_t)t.NST * 8;
 }
 
 pwa_status alloc(pwa_handle* h, void** p, size_t bytes, const char* what)
@@ -172,40 +177,36 @@ pwa_status alloc(pwa_handle* h, void** p, size_t bytes, const char* what)
         if (s_ != PWA_OK) return s_;   \
     } while (0)
 
-// Fill t.E, t.KPW, stage bytes, smem and occupancy for (W, H, NST, bps).
+// Fill t.E, t.H, t.KPW, stage bytes, smem and occupancy for (W, NST, bps).
 pwa_status finish_tiling(pwa_handle* h, Tiling& t)
 {
     const int K = h->K, S = h->S;
-    if (!(t.W == 1 || t.W == 2 || t.W == 4 || t.W == 8 || t.W == 16))
-        return pwa::set_error(h, PWA_EINVAL, "warps must be 1, 2, 4, 8 or 16");
-    if (!(t.H == 1 || t.H == 2 || t.H == 4 || t.H == 8) || t.H > t.W)
-        return pwa::set_error(h, PWA_EINVAL, "lanes_per_event must be 1, 2, 4 or 8 and at most warps");
+    if (!(t.W == 1 || t.W == 2 || t.W == 4 || t.W == 8))
+        return pwa::set_error(h, PWA_EINVAL, "warps must be 1, 2, 4 or 8");
     if (t.NST < 2 || t.NST > 4) return pwa::set_error(h, PWA_EINVAL, "stages must be 2..4");
-    t.E = 32 * t.W / t.H;
-    t.KPW = kpw_supported((K + t.W - 1) / t.W);
-    if (t.KPW < 0) return pwa::set_error(h, PWA_EINVAL, "too many resonances per warp (K > 8 * warps)");
+    t.E = pwa::kTileE;
+    t.H = t.W;
+    t.KPW = (K + t.W - 1) / t.W;
+    if (t.KPW > 8) return pwa::set_error(h, PWA_EINVAL, "too many resonances per warp (K > 8 * warps)");
     const size_t rec_data = (size_t)t.E * (8ull * K * S + 16);
     t.stage_bytes = (uint32_t)((rec_data + 127) / 128 * 128);
     if (rec_data >= (1u << 20)) return pwa::set_error(h, PWA_EINVAL, "tile record too large");
     t.smem = smem_bytes(t, K, S);
-    KernelFn fn = pick_kernel(pwa::MODE_HVP, S, t.KPW);
-    if (!fn) return pwa::set_error(h, PWA_EINVAL, "unsupported S/KPW combination");
     int dev = 0;
     PWA_CUDA(h, cudaGetDevice(&dev));
     int max_optin = 0;
     PWA_CUDA(h, cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if (t.smem > (size_t)max_optin)
-        return pwa::set_error(h, PWA_EINVAL, "tiling needs " + std::to_string(t.smem) +
-                                                 " bytes of shared memory per block (max " +
-                                                 std::to_string(max_optin) + ")");
     int occ = 1 << 30;
     for (int mode = 0; mode < 3; ++mode) {
-        KernelFn f = pick_kernel(mode, S, t.KPW);
+        KernelFn f = pick_kernel(mode, S, t.W, t.KPW);
+        if (!f) return pwa::set_error(h, PWA_EINVAL, "no compiled kernel for this S / warps / K combination");
         cudaFuncAttributes fa;
         PWA_CUDA(h, cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(f)));
         const int dyn_max = max_optin - (int)fa.sharedSizeBytes;
         if ((int)t.smem > dyn_max)
-            return pwa::set_error(h, PWA_EINVAL, "tiling needs more shared memory than a block may use");
+            return pwa::set_error(h, PWA_EINVAL, "tiling needs " + std::to_string(t.smem) +
+                                                     " bytes of shared memory per block (max " +
+                                                     std::to_string(dyn_max) + ")");
         // permit the largest size (another handle may launch the same instance
         // with a larger tiling); occupancy below uses this handle's size
         PWA_CUDA(h, cudaFuncSetAttribute(reinterpret_cast<const void*>(f),
@@ -222,41 +223,28 @@ pwa_status finish_tiling(pwa_handle* h, Tiling& t)
 
 Tiling default_tiling(int K, int S)
 {
-    // Prefer few idle resonance slots in the second sweep (K close to W * KPW),
-    // then tiles of 16..48 KB so that 2 blocks x 2 stages stay in flight per SM.
-    Tiling best;
-    double best_score = -1e30;
-    const int Ws[] = {1, 2, 4, 8, 16};
-    const int Hs[] = {1, 2, 4, 8};
+    // The fewest warps per block whose second sweep leaves few resonance slots
+    // idle (K close to W * KPW, KPW <= 8): small K runs one warp per event
+    // (no cross-lane reduction in the first sweep), larger K splits each
+    // event over W lanes.  Two stages; three when tile records are small.
+    Tiling t;
+    const int Ws[] = {1, 2, 4, 8};
     for (int W : Ws) {
-        const int kpw = kpw_supported((K + W - 1) / W);
-        if (kpw < 0) continue;
-        for (int H : Hs) {
-            if (H > W) continue;
-            const int E = 32 * W / H;
-            const double rec = (double)E * (8.0 * K * S + 16);
-            if (rec > 60 * 1024) continue;
-            const double balance = (double)K / (W * kpw);
-            double score = 4.0 * balance;
-            score -= std::fabs(std::log2(std::max(rec, 1.0) / (32 * 1024.0))) * 0.25;  // aim near 32 KB
-            score -= 0.05 * std::log2((double)H);                                    // shuffle cost
-            if (W >= 4) score += 0.2;                                                // enough warps per block
-            if (score > best_score) {
-                best_score = score;
-                best.W = W;
-                best.H = H;
-                best.NST = rec < 16 * 1024 ? 4 : (rec < 32 * 1024 ? 3 : 2);
-            }
-        }
+        const int kpw = (K + W - 1) / W;
+        if (kpw > 8) continue;
+        t.W = W;
+        if ((double)K / (W * kpw) >= 0.8) break;
     }
-    return best;
+    const double rec = (double)pwa::kTileE * (8.0 * K * S + 16);
+    t.NST = rec < 8 * 1024 ? 3 : 2;
+    return t;
 }
 
 pwa_status build_tiles(pwa_handle* h)
 {
     Tiling& t = h->tiling;
     PWA_TRY(finish_tiling(h, t));  // sets t.E first: everything below depends on it
-    const int ev = 32 / t.H;
+    const int ev = 32 / t.W;
     for (int smp = 0; smp < 2; ++smp) {
         const int with_w = smp == 0;
         const size_t rec = (size_t)t.E * (8ull * h->K * h->S + 12 + 4 * with_w);
@@ -482,7 +470,7 @@ pwa_status cuda_error(pwa_handle* h, cudaError_t e, const char* what)
 pwa_status launch_pass(pwa_handle* h, const double* d_theta, const double* d_v, double* d_out, int mode)
 {
     if (h->broken) return set_error(h, PWA_ETIMEOUT, "handle is unusable after a device-side timeout");
-    KernelFn fn = pick_kernel(mode, h->S, h->tiling.KPW);
+    KernelFn fn = pick_kernel(mode, h->S, h->tiling.W, h->tiling.KPW);
     if (!fn) return set_error(h, PWA_EINVAL, "no kernel for this shape");
     // the geometry the kernel relies on: every tile record fits a stage and
     // the tiles cover every event
@@ -662,13 +650,12 @@ pwa_status pwa_set_stream(pwa_handle* h, void* cuda_stream)
     return PWA_OK;
 }
 
-pwa_status pwa_set_tiling(pwa_handle* h, int warps, int lanes_per_event, int stages, int blocks_per_sm)
+pwa_status pwa_set_tiling(pwa_handle* h, int warps, int stages, int blocks_per_sm)
 {
     if (!h) return PWA_EINVAL;
     h->err.clear();
     Tiling t;
     t.W = warps;
-    t.H = lanes_per_event;
     t.NST = stages;
     t.bps = blocks_per_sm;
     const Tiling old = h->tiling;
@@ -683,16 +670,15 @@ pwa_status pwa_set_tiling(pwa_handle* h, int warps, int lanes_per_event, int sta
     return st;
 }
 
-pwa_status pwa_get_tiling(const pwa_handle* h, int out7[7])
+pwa_status pwa_get_tiling(const pwa_handle* h, int out6[6])
 {
-    if (!h || !out7) return PWA_EINVAL;
-    out7[0] = h->tiling.W;
-    out7[1] = h->tiling.H;
-    out7[2] = h->tiling.NST;
-    out7[3] = h->tiling.blocks_per_sm;
-    out7[4] = h->tiling.E;
-    out7[5] = h->tiling.grid;
-    out7[6] = (int)h->tiling.smem;
+    if (!h || !out6) return PWA_EINVAL;
+    out6[0] = h->tiling.W;
+    out6[1] = h->tiling.NST;
+    out6[2] = h->tiling.blocks_per_sm;
+    out6[3] = h->tiling.E;
+    out6[4] = h->tiling.grid;
+    out6[5] = (int)h->tiling.smem;
     return PWA_OK;
 }
 

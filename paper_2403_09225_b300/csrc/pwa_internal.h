@@ -6,17 +6,17 @@
 #include <string>
 #include <vector>
 
-#include "../../include/pwa.h"
+#include "pwa.h"  // include/ is on the include path
 #include "pass_kernel.cuh"
 
 namespace pwa {
 
 struct Tiling {
-    int W = 4;        // warps per block
-    int H = 2;        // lanes per event in the coherent-sum sweep
+    int W = 4;        // warps per block (= lanes per event in the coherent-sum sweep)
+    int H = 4;        // lanes per event, always W
     int NST = 2;      // tiles in flight per block
     int bps = 0;      // blocks per SM requested (0 = as many as fit)
-    int E = 64;       // events per tile = 32 W / H
+    int E = kTileE;   // events per tile
     int KPW = 5;      // resonances owned by a warp in the second sweep
     int grid = 0;     // blocks launched
     int blocks_per_sm = 0;
@@ -71,10 +71,17 @@ struct pwa_handle {
 namespace pwa {
 
 using KernelFn = void (*)(const PassArgs);
-// kernel instance for (S, resonances per warp), one function per mode
-KernelFn pick_pass_nll(int S, int kpw);
-KernelFn pick_pass_grad(int S, int kpw);
-KernelFn pick_pass_hvp(int S, int kpw);
+// compiled instances of the fused pass for (warps per block, resonances per
+// warp), one function per mode and S (generated by build.py)
+#define PWA_DECLARE_PICK(mode)                 \
+    KernelFn pick_pass_##mode##_s1(int W, int kpw); \
+    KernelFn pick_pass_##mode##_s2(int W, int kpw); \
+    KernelFn pick_pass_##mode##_s3(int W, int kpw); \
+    KernelFn pick_pass_##mode##_s4(int W, int kpw);
+PWA_DECLARE_PICK(nll)
+PWA_DECLARE_PICK(grad)
+PWA_DECLARE_PICK(hvp)
+#undef PWA_DECLARE_PICK
 
 // Enqueue one fused pass on device buffers (theta, v: device [P]; out: device [1+2P]).
 pwa_status launch_pass(pwa_handle* h, const double* d_theta, const double* d_v, double* d_out, int mode);
