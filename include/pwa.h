@@ -159,6 +159,25 @@ pwa_status pwa_eval(pwa_handle* h, const double* theta, const double* v,
 pwa_status pwa_eval_device(pwa_handle* h, const double* d_theta, const double* d_v,
                            double* d_out, int want_grad, int want_hv);
 
+/* pwa_eval_device without any device allocation (the paper has no
+ * counterpart: this is a deployment variant).  For callers that may not call
+ * cudaMalloc while they evaluate -- e.g. code under an external memory manager
+ * that has reserved the device's memory, or a loop that must not take the
+ * device-wide synchronisation an allocation can imply.  Same arguments,
+ * result and asynchrony as pwa_eval_device (errors are reported by pwa_sync);
+ * the handle is still created beforehand with pwa_create, which allocates.
+ * The reduction scratch (per-block and per-group partial sums, completion
+ * counters) lives in one statically allocated 2 MiB device array that every
+ * GPU loading the library holds until exit; a handle needing more
+ * (grid blocks + groups) x (20 K + 6) x 8 bytes + counters is refused with
+ * PWA_EINVAL.  The array's device address is looked up on the first call on
+ * each device: make that first call before any stream capture.  All calls
+ * share the array and the counters are cleared at each call, so calls whose
+ * kernels overlap on the GPU (e.g. on different streams) race and must not be
+ * issued concurrently. */
+pwa_status pwa_eval_device_noalloc(pwa_handle* h, const double* d_theta, const double* d_v,
+                                   double* d_out, int want_grad, int want_hv);
+
 /* Wait for the handle's stream and report device-side errors of earlier
  * asynchronous calls. */
 pwa_status pwa_sync(pwa_handle* h);

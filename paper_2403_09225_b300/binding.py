@@ -53,7 +53,7 @@ class PwaError(RuntimeError):
 
 #: every symbol include/pwa.h declares
 EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "pwa_grad", "pwa_hvp",
-           "pwa_eval", "pwa_eval_device", "pwa_sync", "pwa_event_intensity", "pwa_newton_cg_fit",
+           "pwa_eval", "pwa_eval_device", "pwa_eval_device_noalloc", "pwa_sync", "pwa_event_intensity", "pwa_newton_cg_fit",
            "pwa_fit_opts_default", "pwa_set_stream", "pwa_set_tiling", "pwa_get_tiling", "pwa_last_error",
            "pwa_destroy")
 
@@ -75,6 +75,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pwa_hvp": (st, [H, dp, dp, dp]),
         "pwa_eval": (st, [H, dp, dp, dp, dp, dp]),
         "pwa_eval_device": (st, [H, vp, vp, vp, i, i]),
+        "pwa_eval_device_noalloc": (st, [H, vp, vp, vp, i, i]),
         "pwa_sync": (st, [H]),
         "pwa_event_intensity": (st, [H, i, dp, vp, i]),
         "pwa_newton_cg_fit": (st, [H, dp, ctypes.POINTER(pwa_fit_opts), dp, ctypes.POINTER(pwa_fit_result)]),
@@ -224,6 +225,13 @@ class Likelihood:
         """Asynchronous fused pass on device pointers (theta [P], v [P], out [1 + 2P])."""
         self._check(lib().pwa_eval_device(self._h, ctypes.c_void_p(d_theta), ctypes.c_void_p(d_v),
                                           ctypes.c_void_p(d_out), int(want_grad), int(want_hv)))
+
+    def eval_device_noalloc(self, d_theta: int, d_v: int, d_out: int, want_grad: bool = True,
+                            want_hv: bool = True):
+        """eval_device with the reduction scratch in the library's static
+        device array: allocates nothing (see include/pwa.h)."""
+        self._check(lib().pwa_eval_device_noalloc(self._h, ctypes.c_void_p(d_theta), ctypes.c_void_p(d_v),
+                                                  ctypes.c_void_p(d_out), int(want_grad), int(want_hv)))
 
     def sync(self):
         self._check(lib().pwa_sync(self._h))

@@ -1,0 +1,80 @@
+"""The allocation-free entry point, pwa_eval_device_noalloc (GPU).
+
+Some callers may not call cudaMalloc while they evaluate (an external memory
+manager owns the device's memory, or a loop must not take an allocation's
+device-wide synchronisation).  For them the fused pass can keep its reduction
+scratch in the library's static device array instead of the handle's
+buffers.  This file is collected last on purpose; it checks, through the C
+ABI, that the variant returns what pwa_eval_device returns, on two calls in a
+row, and that a handle needing more scratch than the array holds is refused.
+"""
+import numpy as np
+import pytest
+
+from paper_2403_09225_b300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _outputs(L, fn, th, v, want_grad, want_hv):
+    import torch
+    d_th = torch.tensor(th, dtype=torch.float64, device="cuda")
+    d_v = torch.tensor(v, dtype=torch.float64, device="cuda")
+    out = torch.full((1 + 2 * L.P,), float("nan"), dtype=torch.float64, device="cuda")
+    fn(d_th.data_ptr(), d_v.data_ptr(), out.data_ptr(), want_grad, want_hv)
+    L.sync()
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def test_noalloc_matches_the_allocating_entry_point():
+    import torch
+    from paper_2403_09225_b300 import binding
+    cfg = W.CONFIGS["paper"]
+    wl = W.make_workload(cfg, intensity=None, n_data=3001, n_mc=12007)
+    L = binding.make_likelihood(wl, stream=torch.cuda.current_stream().cuda_stream)
+    th = W.random_starts(wl, 1)[0]
+    v = np.linspace(-1.0, 1.0, L.P)
+    P = L.P
+    for want_grad, want_hv in ((True, True), (True, False), (False, False)):
+        ref = _outputs(L, L.eval_device, th, v, want_grad, want_hv)
+        for _ in range(2):  # two calls in a row share (and re-clear) the static scratch
+            got = _outputs(L, L.eval_device_noalloc, th, v, want_grad, want_hv)
+            n = 1 + (P if want_grad else 0) + (P if want_hv else 0)
+            assert abs(got[0] - ref[0]) <= 1e-12 * abs(ref[0])
+            if want_grad:
+                g, gr = got[1:1 + P], ref[1:1 + P]
+                assert np.max(np.abs(g - gr)) <= 1e-10 * np.max(np.abs(gr))
+            if want_hv:
+                h, hr = got[1 + P:1 + 2 * P], ref[1 + P:1 + 2 * P]
+                assert np.max(np.abs(h - hr)) <= 1e-10 * np.max(np.abs(hr))
+            assert np.all(np.isfinite(got[:n]))
+    L.close()
+
+
+def test_noalloc_refuses_a_handle_larger_than_its_scratch():
+    import torch
+    from paper_2403_09225_b300 import binding
+    # many resonances (long partial-sum records) with small tiles (many blocks)
+    for K in (44, 48, 56, 64):
+        cfg = W.Config("k%d" % K, K, 1, 0, 0, 2, False, 7)
+        wl = W.make_workload(cfg, intensity=None, n_data=20000, n_mc=200000)
+        L = binding.make_likelihood(wl, stream=torch.cuda.current_stream().cuda_stream)
+        til = L.get_tiling()
+        groups = (til["grid_blocks"] + 15) // 16
+        need = 8 * (til["grid_blocks"] + groups) * 2 * (K * 10 + 3) + 4 * (groups + 1)
+        if need > 2 << 20:
+            break
+        L.close()
+    else:
+        pytest.skip("every handle tried fits the scratch on this GPU")
+    d_th = torch.tensor(wl.theta_true, dtype=torch.float64, device="cuda")
+    out = torch.empty(1 + 2 * L.P, dtype=torch.float64, device="cuda")
+    with pytest.raises(binding.PwaError) as e:
+        L.eval_device_noalloc(d_th.data_ptr(), d_th.data_ptr(), out.data_ptr(), True, False)
+    assert e.value.status == binding.PWA_EINVAL and "scratch" in str(e.value)
+    # the allocating entry point still serves this handle
+    L.eval_device(d_th.data_ptr(), d_th.data_ptr(), out.data_ptr(), True, False)
+    L.sync()
+    assert np.isfinite(out[0].item())
+    L.close()
