@@ -41,7 +41,7 @@ namespace pwa {
 
 constexpr int kNV = 10;        // FP64 values per resonance and sample set
 constexpr int kNScal = 3;      // per-set scalars: data (sum w ln I, -, -), MC (G, Gdot, -)
-constexpr int kWindow = 16;    // tiles between FP32 -> FP64 folds
+constexpr int kWindow = 64;    // tiles between FP32 -> FP64 folds
 constexpr int kMaxThreads = 512;
 
 enum { MODE_NLL = 0, MODE_GRAD = 1, MODE_HVP = 2 };
@@ -61,8 +61,16 @@ struct __align__(16) KConst {  // FP32 per-resonance constants (48 bytes)
     float are, aim;            // alpha = v_rho e^{i phi} + i v_phi g
     float bre, bim;            // beta = g (v_M (-2M + i Gamma) + v_Gamma (i M))
     int shift;                 // rotation of the event position in the tile
-    int pad;
+    float mg2;                 // (M Gamma)^2
 };
+
+// Position of F_{k,s} of the event at tile position p inside a tile's F block
+// (float2 units).  Even S stores the projections in pairs, (s, s+1) adjacent,
+// so that one 16-byte load fetches two of them; odd S stores [k][s][p].
+__host__ __device__ inline int f_slot(int k, int s, int p, int S, int E)
+{
+    return (S % 2 == 0) ? ((k * (S / 2) + s / 2) * E + p) * 2 + (s & 1) : (k * S + s) * E + p;
+}
 
 struct PassArgs {
     const unsigned char* tiles[2];  // data, MC tile records
@@ -192,7 +200,7 @@ __device__ __forceinline__ KConst make_kconst(const PassArgs& a, int k, bool wit
     kc.bre = (float)(gre * ure - gim * uim);
     kc.bim = (float)(gre * uim + gim * ure);
     kc.shift = ev < 16 ? (k % (16 / ev)) * ev : 0;
-    kc.pad = 0;
+    kc.mg2 = (float)((rv.M * rv.G) * (rv.M * rv.G));
     return kc;
 }
 
@@ -201,7 +209,7 @@ __device__ __forceinline__ KConst make_kconst(const PassArgs& a, int k, bool wit
 __device__ __forceinline__ void breit_wigner(const KConst& kc, float m2, float& br, float& bi)
 {
     const float d = (kc.m2hi - m2) + kc.m2lo;
-    const float r = __fdividef(1.0f, fmaf(d, d, kc.mg * kc.mg));
+    const float r = __fdividef(1.0f, fmaf(d, d, kc.mg2));
     br = d * r;
     bi = kc.mg * r;
 }
@@ -209,6 +217,24 @@ __device__ __forceinline__ void breit_wigner(const KConst& kc, float m2, float& 
 __device__ __forceinline__ float pick3(int ch, float a0, float a1, float a2)
 {
     return ch == 0 ? a0 : (ch == 1 ? a1 : a2);
+}
+
+// The S projections of one (resonance, event) from the tile's F block; row
+// points at s = 0 (see f_slot): 16-byte loads for pairs when S is even.
+template <int S, int E>
+__device__ __forceinline__ void load_row(const float2* row, float2 (&fv)[S])
+{
+    if constexpr (S % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < S / 2; ++q) {
+            const float4 v = *reinterpret_cast<const float4*>(row + 2 * E * q);
+            fv[2 * q] = make_float2(v.x, v.y);
+            fv[2 * q + 1] = make_float2(v.z, v.w);
+        }
+    } else {
+#pragma unroll
+        for (int s = 0; s < S; ++s) fv[s] = row[s * E];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -222,37 +248,43 @@ __device__ __forceinline__ float pick3(int ch, float a0, float a1, float a2)
 constexpr int kTileE = 32;
 
 template <int MODE, int S, int W, int KPW>
-__global__ void __launch_bounds__(32 * W) pass_kernel(const PassArgs a)
+__global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr bool HV = MODE == MODE_HVP;
     constexpr bool GR = MODE >= MODE_GRAD;
     constexpr int E = kTileE;
-    constexpr int H = W;                       // lanes per event in sweep 1
-    constexpr int EV = 32 / H;                 // events per warp in sweep 1
+    constexpr int H = W;                       // lanes per event
+    constexpr int EV = 32 / H;                 // events per warp (one tile = W x EV events)
     constexpr int NVM = HV ? kNV : 4;          // accumulated reals per resonance
-    constexpr int V = GR ? NVM * KPW : 1;      // per-warp accumulated reals
-    constexpr int SLOTS = (V + 31) / 32;
     constexpr int NT = 32 * W;
     using AVec = typename std::conditional<HV, float4, float2>::type;
+    (void)sizeof(AVec);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = a.K, NST = a.NST;
 
+    // shared memory: stages | KConst[K] | per-warp FP64 sums [W][K*kNV + 2] | stage counters | mbarriers
     unsigned char* stages = smem;
     KConst* kc = reinterpret_cast<KConst*>(smem + (size_t)NST * a.stage_bytes);
-    // sweep-2 inputs per (s, event): a A_s (and a Adot_s - b A_s for HVP)
-    AVec* abuf = reinterpret_cast<AVec*>(kc + K);
-    float2* Bs = reinterpret_cast<float2*>(reinterpret_cast<float4*>(kc + K) + S * E);  // [K][E] rotated
-    double* red = reinterpret_cast<double*>(Bs + K * E);                                 // [W][4]
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(red + 4 * W);
+    const int wlen = K * kNV + 2;
+    double* wacc = reinterpret_cast<double*>(kc + K);
+    unsigned* stage_cnt = reinterpret_cast<unsigned*>(wacc + W * wlen);
+    long long* issued = reinterpret_cast<long long*>(stage_cnt + 4);  // last iteration issued per stage
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(issued + 4);
     __shared__ int s_flag;
+    __shared__ volatile int s_abort;
 
     const long long T = (long long)a.ntiles[0] + a.ntiles[1];
     const long long G = gridDim.x;
 
     if (tid == 0) {
-        for (int s = 0; s < NST; ++s) mbar_init(&mbar[s], 1);
+        s_abort = 0;
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&mbar[s], 1);
+            stage_cnt[s] = 0;
+            issued[s] = -1;
+        }
         fence_mbar_init();
         for (int i = 0; i < NST; ++i) {
             const long long t = blockIdx.x + i * G;
@@ -261,141 +293,105 @@ __global__ void __launch_bounds__(32 * W) pass_kernel(const PassArgs a)
                 const long long lt = smp ? t - a.ntiles[0] : t;
                 tma_load_tile(stages + (size_t)i * a.stage_bytes,
                               a.tiles[smp] + (size_t)lt * a.tile_bytes[smp], a.tile_bytes[smp], &mbar[i]);
+                issued[i] = i;
             }
         }
     }
     for (int k = tid; k < K; k += NT) kc[k] = make_kconst(a, k, HV, EV);
+    for (int i = tid; i < W * wlen; i += NT) wacc[i] = 0.0;
     __syncthreads();
 
-    // FP32 accumulators (sweep 2: per owned resonance; sweep 1: per-event scalars)
+    // lane (h, el): event e = warp * EV + el of every tile, resonances k = h + i H
+    const int h = lane / EV, el = lane % EV;
+    const int e = warp * EV + el;
+    // all resonances of a lane share one rotation (it depends on k mod (H/2))
+    const int p = (e + (h < K ? kc[h].shift : 0)) & (E - 1);
+    const int kcount = h < K ? (K - 1 - h) / H + 1 : 0;  // resonances of this lane (<= KPW in GRAD/HVP)
+
+    // FP32 per-lane sums of the current fold window
     float acc[GR ? KPW : 1][GR ? NVM : 1];
 #pragma unroll
     for (int j = 0; j < (GR ? KPW : 1); ++j)
 #pragma unroll
         for (int q = 0; q < (GR ? NVM : 1); ++q) acc[j][q] = 0.f;
     float sc0 = 0.f, sc1 = 0.f;
-    double dacc[SLOTS];
-#pragma unroll
-    for (int t = 0; t < SLOTS; ++t) dacc[t] = 0.0;
-    double dsc0 = 0.0, dsc1 = 0.0;
 
-    const int k0 = warp * KPW;
-    const int h = lane / EV, el = lane % EV;
-    const int e1 = warp * EV + el;  // this lane's event in sweep 1
-    // sweep 1 visits k = h, h + H, ...: they share one rotation (it depends on
-    // k mod (H/2)), so the lane's F and BW offsets advance by constants
-    const int p1 = (e1 + (h < K ? kc[h].shift : 0)) & (E - 1);
-    // sweep 2: the rotated position of this lane's event in each owned row
-    int p2[GR ? KPW : 1];
-#pragma unroll
-    for (int j = 0; j < (GR ? KPW : 1); ++j) p2[j] = (lane + (k0 + j < K ? kc[k0 + j].shift : 0)) & (E - 1);
-    int cur_set = -1;
-    bool set_written[2] = {false, false};
-    long long i_fail = -1;  // loop iteration whose tile never arrived
-
-    // fold the per-lane FP32 sums into per-lane FP64 slots (fixed order)
+    // fold the warp's FP32 sums into its FP64 sums in shared memory: reduce over
+    // the EV lanes of each resonance group, lane el == 0 adds (fixed order)
     auto fold = [&]() {
+        double* wa = wacc + warp * wlen;
         if constexpr (GR) {
-            // lane l keeps value l + 32 t of the warp's V sums (FP32 select,
-            // then one FP64 add per slot: the FP64 pipe is narrow)
-            float mine[SLOTS];
-#pragma unroll
-            for (int t = 0; t < SLOTS; ++t) mine[t] = 0.f;
 #pragma unroll
             for (int j = 0; j < KPW; ++j)
 #pragma unroll
                 for (int q = 0; q < NVM; ++q) {
-                    const float s = warp_sum(acc[j][q]);
+                    float v = acc[j][q];
                     acc[j][q] = 0.f;
-                    const int vi = j * NVM + q;
-                    mine[vi >> 5] = (vi & 31) == lane ? s : mine[vi >> 5];
-                }
 #pragma unroll
-            for (int t = 0; t < SLOTS; ++t) dacc[t] += (double)mine[t];
+                    for (int o = 1; o < EV; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (el == 0 && j < kcount) wa[(h + j * H) * kNV + q] += (double)v;
+                }
         }
         const float t0 = warp_sum(sc0), t1 = warp_sum(sc1);
         sc0 = sc1 = 0.f;
         if (lane == 0) {
-            dsc0 += (double)t0;
-            dsc1 += (double)t1;
+            wa[K * kNV + 0] += (double)t0;
+            wa[K * kNV + 1] += (double)t1;
         }
     };
 
-    // write this block's FP64 partials of one sample set
+    // the block's FP64 partials of one sample set: sum the warps in order
     auto write_set = [&](int set) {
+        __syncthreads();
         double* rec = a.block_rec + (size_t)blockIdx.x * a.rec_len + (size_t)set * (K * kNV + kNScal);
-        if constexpr (GR) {
-#pragma unroll
-            for (int t = 0; t < SLOTS; ++t) {
-                const int vi = lane + 32 * t;
-                if (vi < V) {
-                    const int k = k0 + vi / NVM;
-                    if (k < K) rec[k * kNV + vi % NVM] = dacc[t];
-                }
-                dacc[t] = 0.0;
-            }
-        }
-        if (lane == 0) {
-            red[warp * 4 + 0] = dsc0;
-            red[warp * 4 + 1] = dsc1;
-        }
-        dsc0 = dsc1 = 0.0;
-        __syncthreads();
-        if (tid == 0) {
-            double s0 = 0.0, s1 = 0.0;
-            for (int w = 0; w < W; ++w) {
-                s0 += red[w * 4 + 0];
-                s1 += red[w * 4 + 1];
-            }
-            rec[K * kNV + 0] = s0;
-            rec[K * kNV + 1] = s1;
-            rec[K * kNV + 2] = 0.0;
+        for (int i = tid; i < K * kNV + kNScal; i += NT) {
+            double v = 0.0;
+            if (i < wlen)
+                for (int w = 0; w < W; ++w) v += wacc[w * wlen + i];
+            rec[i] = v;
         }
         __syncthreads();
-        set_written[set] = true;
+        for (int i = tid; i < W * wlen; i += NT) wacc[i] = 0.0;
+        __syncthreads();
     };
 
+    int cur_set = -1;
+    bool set_written[2] = {false, false};
     int win = 0;
-    for (long long i = 0;; ++i) {
-        const long long t = blockIdx.x + i * G;
-        if (t >= T) break;
+    int st = 0;         // stage of iteration i (i mod NST), kept without 64-bit division
+    uint32_t ph = 0;    // barrier phase parity of iteration i ((i / NST) & 1)
+    for (long long i = 0, t = blockIdx.x; t < T; ++i, t += G) {
         const int smp = t < a.ntiles[0] ? 0 : 1;
         const long long lt = smp ? t - a.ntiles[0] : t;
-        if (smp != cur_set) {
+        if (smp != cur_set) {  // every warp reaches this tile index: a block barrier is safe
             if (cur_set >= 0) {
                 fold();
                 write_set(cur_set);
+                set_written[cur_set] = true;
             }
             cur_set = smp;
             win = 0;
         }
-        const int st = (int)(i % NST);
-        const uint32_t parity = (uint32_t)((i / NST) & 1);
-        const bool ok = mbar_wait(&mbar[st], parity, a.timeout_cycles);
-        if (__syncthreads_or(!ok)) {
-            i_fail = i;
-            break;
+        bool ok = false;
+        if (!s_abort) {
+            ok = __all_sync(0xffffffffu, mbar_wait(&mbar[st], ph, a.timeout_cycles));
+            if (!ok && lane == 0) s_abort = 1;
         }
-        const float2* Fs = reinterpret_cast<const float2*>(stages + (size_t)st * a.stage_bytes);
-        const float* m2s = reinterpret_cast<const float*>(Fs + K * S * E);
-        const long long e_base = lt * E;
-        const int nvalid = (int)min((long long)E, a.nev[smp] - e_base);
+        if (ok) {
+            const float2* Fs = reinterpret_cast<const float2*>(stages + (size_t)st * a.stage_bytes);
+            const float* m2s = reinterpret_cast<const float*>(Fs + K * S * E);
+            const long long e_base = lt * E;
+            const bool valid = e < (int)min((long long)E, a.nev[smp] - e_base);
+            const float2* Frow = Fs + f_slot(h, 0, p, S, E);  // F_{k,.}(e) for k = h; + i H S E for k = h + i H
 
-        // ---- sweep 1: BW, coherent sums, intensity, per-event weights ----
-        {
-            const int e = e1;
-            const float m20 = m2s[e], m21 = m2s[E + e], m22 = m2s[2 * E + e];
+            // ---- sweep 1: BW, couplings, coherent sums over this lane's resonances ----
             float Ar[S], Ai[S], Dr[S], Di[S];
 #pragma unroll
             for (int s = 0; s < S; ++s) Ar[s] = Ai[s] = Dr[s] = Di[s] = 0.f;
-            const float2* Fk = Fs + h * S * E + p1;
-            float2* Bk = Bs + h * E + p1;
-#pragma unroll 2
-            for (int k = h; k < K; k += H, Fk += H * S * E, Bk += H * E) {
+            float2 Bk[GR ? KPW : 1];
+            auto visit = [&](int k, const float2* Fk, float& br, float& bi) {
                 const KConst c = kc[k];
-                float br, bi;
-                breit_wigner(c, pick3(c.ch, m20, m21, m22), br, bi);
-                if constexpr (GR) *Bk = make_float2(br, bi);
+                breit_wigner(c, m2s[c.ch * E + e], br, bi);
                 const float cr = c.gre * br - c.gim * bi, ci = c.gre * bi + c.gim * br;
                 float dr = 0.f, di = 0.f;
                 if constexpr (HV) {
@@ -404,9 +400,11 @@ __global__ void __launch_bounds__(32 * W) pass_kernel(const PassArgs a)
                     dr = br * tr - bi * ti;
                     di = br * ti + bi * tr;
                 }
+                float2 fv[S];
+                load_row<S, E>(Fk, fv);
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
-                    const float2 f = Fk[s * E];
+                    const float2 f = fv[s];
                     Ar[s] = fmaf(cr, f.x, fmaf(-ci, f.y, Ar[s]));
                     Ai[s] = fmaf(cr, f.y, fmaf(ci, f.x, Ai[s]));
                     if constexpr (HV) {
@@ -414,7 +412,22 @@ __global__ void __launch_bounds__(32 * W) pass_kernel(const PassArgs a)
                         Di[s] = fmaf(dr, f.y, fmaf(di, f.x, Di[s]));
                     }
                 }
+            };
+            if constexpr (GR) {
+#pragma unroll
+                for (int j = 0; j < KPW; ++j) {
+                    if (j >= kcount) break;
+                    visit(h + j * H, Frow + j * H * S * E, Bk[j].x, Bk[j].y);
+                }
+            } else {
+                // the NLL-only pass is compiled once per W: the trip count is runtime
+#pragma unroll 2
+                for (int j = 0; j < kcount; ++j) {
+                    float br, bi;
+                    visit(h + j * H, Frow + j * H * S * E, br, bi);
+                }
             }
+            // ---- the H lanes of the event combine their partial sums ----
 #pragma unroll
             for (int off = EV; off < 32; off <<= 1) {
 #pragma unroll
@@ -427,7 +440,6 @@ __global__ void __launch_bounds__(32 * W) pass_kernel(const PassArgs a)
                     }
                 }
             }
-            // every lane of the event now holds A and Adot
             float I = 0.f, Id = 0.f;
 #pragma unroll
             for (int s = 0; s < S; ++s) {
@@ -435,7 +447,6 @@ __global__ void __launch_bounds__(32 * W) pass_kernel(const PassArgs a)
                 if constexpr (HV) Id = fmaf(Ar[s], Dr[s], fmaf(Ai[s], Di[s], Id));
             }
             Id *= 2.f;
-            const bool valid = e < nvalid;
             float wa = 0.f, wb = 0.f;  // (a, b) = (w/I, w Idot/I^2) for data, (1, 0) for MC
             if (smp == 0) {
                 const float w = m2s[3 * E + e];
@@ -465,47 +476,30 @@ __global__ void __launch_bounds__(32 * W) pass_kernel(const PassArgs a)
                     }
                 }
             }
-            if constexpr (GR) {
-                // lane h of the event stores the components s = h, h + H, ...
-#pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    if ((s % H) != h) continue;
-                    if constexpr (HV)
-                        abuf[s * E + e] = make_float4(wa * Ar[s], wa * Ai[s], fmaf(wa, Dr[s], -wb * Ar[s]),
-                                                      fmaf(wa, Di[s], -wb * Ai[s]));
-                    else
-                        abuf[s * E + e] = make_float2(wa * Ar[s], wa * Ai[s]);
-                }
-            }
-        }
 
-        if constexpr (GR) {
-            __syncthreads();
-            // ---- sweep 2: per-resonance sums for event `lane` ----
-            if (k0 < K) {
-                float Ar[S], Ai[S], Dr[S], Di[S];  // a A_s and (a Adot_s - b A_s)
+            if constexpr (GR) {
+                // ---- sweep 2 over the same resonances: Dh = sum_s conj(a A_s) F,
+                //      Dt = sum_s conj(a Adot_s - b A_s) F, then the five sums ----
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
-                    const AVec q = abuf[s * E + lane];
-                    Ar[s] = q.x;
-                    Ai[s] = q.y;
+                    const float ar = wa * Ar[s], ai = wa * Ai[s];
                     if constexpr (HV) {
-                        Dr[s] = q.z;
-                        Di[s] = q.w;
+                        Dr[s] = fmaf(wa, Dr[s], -wb * Ar[s]);
+                        Di[s] = fmaf(wa, Di[s], -wb * Ai[s]);
                     }
+                    Ar[s] = ar;
+                    Ai[s] = ai;
                 }
 #pragma unroll
                 for (int j = 0; j < KPW; ++j) {
-                    const int k = k0 + j;
-                    if (k >= K) break;
-                    const float2 B = Bs[k * E + p2[j]];
-                    const float br = B.x, bi = B.y;
-                    const float2* Fk = Fs + k * S * E + p2[j];
-                    // Dh = sum_s conj(a A_s) F, Dt = sum_s conj(a Adot_s - b A_s) F (two chains each)
+                    if (j >= kcount) break;
+                    const float br = Bk[j].x, bi = Bk[j].y;
+                    float2 fv[S];
+                    load_row<S, E>(Frow + j * H * S * E, fv);
                     float xr[2] = {0.f, 0.f}, xi[2] = {0.f, 0.f}, yr[2] = {0.f, 0.f}, yi[2] = {0.f, 0.f};
 #pragma unroll
                     for (int s = 0; s < S; ++s) {
-                        const float2 f = Fk[s * E];
+                        const float2 f = fv[s];
                         const int q = s & 1;
                         xr[q] = fmaf(Ar[s], f.x, fmaf(Ai[s], f.y, xr[q]));
                         xi[q] = fmaf(Ar[s], f.y, fmaf(-Ai[s], f.x, xi[q]));
@@ -533,32 +527,42 @@ __global__ void __launch_bounds__(32 * W) pass_kernel(const PassArgs a)
                 }
             }
         }
-        __syncthreads();  // the stage, abuf and Bs may now be overwritten
-        if (tid == 0) {
-            const long long tn = t + (long long)NST * G;
-            if (tn < T) {
-                fence_proxy_async();
-                const int s2 = tn < a.ntiles[0] ? 0 : 1;
-                const long long lt2 = s2 ? tn - a.ntiles[0] : tn;
-                tma_load_tile(stages + (size_t)st * a.stage_bytes, a.tiles[s2] + (size_t)lt2 * a.tile_bytes[s2],
-                              a.tile_bytes[s2], &mbar[st]);
+        // ---- release the stage; the last warp to do so refills it ----
+        __syncwarp();
+        if (lane == 0) {
+            const unsigned prev = atomicAdd(&stage_cnt[st], 1u);
+            if (prev == (unsigned)(W - 1)) {
+                stage_cnt[st] = 0;
+                const long long tn = t + (long long)NST * G;
+                if (tn < T && !s_abort) {
+                    fence_proxy_async();
+                    const int s2 = tn < a.ntiles[0] ? 0 : 1;
+                    const long long lt2 = s2 ? tn - a.ntiles[0] : tn;
+                    issued[st] = i + NST;
+                    tma_load_tile(stages + (size_t)st * a.stage_bytes,
+                                  a.tiles[s2] + (size_t)lt2 * a.tile_bytes[s2], a.tile_bytes[s2], &mbar[st]);
+                }
             }
         }
         if (++win == kWindow) {
             fold();
             win = 0;
         }
+        if (++st == NST) {
+            st = 0;
+            ph ^= 1u;
+        }
     }
+    __syncthreads();
 
-    if (i_fail >= 0) {
+    if (s_abort) {
         // A tile never arrived.  Report it, then wait (bounded) for the copies
-        // this block still has in flight -- those of iterations i_fail ..
-        // i_fail + NST - 1 -- so that no copy lands in a freed shared buffer.
+        // still in flight so that none lands in a freed shared buffer.
         if (tid == 0) {
             atomicOr(a.err, ERR_TIMEOUT);
-            for (long long j = i_fail; j < i_fail + NST; ++j) {
-                if (blockIdx.x + j * G >= T) break;
-                (void)mbar_wait(&mbar[j % NST], (uint32_t)((j / NST) & 1), a.timeout_cycles);
+            for (int s = 0; s < NST; ++s) {
+                const long long j = issued[s];
+                if (j >= 0) (void)mbar_wait(&mbar[s], (uint32_t)((j / NST) & 1), a.timeout_cycles);
             }
         }
         __syncthreads();
@@ -568,6 +572,7 @@ __global__ void __launch_bounds__(32 * W) pass_kernel(const PassArgs a)
     if (cur_set >= 0) {
         fold();
         write_set(cur_set);
+        set_written[cur_set] = true;
     }
     for (int s = 0; s < 2; ++s) {
         if (!set_written[s]) {

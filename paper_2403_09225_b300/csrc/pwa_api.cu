@@ -58,6 +58,7 @@ __global__ void layout_kernel(const float2* __restrict__ F, const float* __restr
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total_F + total_x;
          i += (long long)gridDim.x * blockDim.x) {
         if (i < total_F) {
+            // i enumerates (tile, k, s, p); the destination follows f_slot
             const long long t = i / per_tile_F;
             const long long r = i % per_tile_F;
             const int k = (int)(r / ((long long)S * E));
@@ -67,7 +68,7 @@ __global__ void layout_kernel(const float2* __restrict__ F, const float* __restr
             const long long e = t * E + el;
             float2 val = make_float2(0.f, 0.f);
             if (e < n) val = F[(e * K + k) * S + s];
-            reinterpret_cast<float2*>(tiles + (size_t)t * tile_bytes)[r] = val;
+            reinterpret_cast<float2*>(tiles + (size_t)t * tile_bytes)[pwa::f_slot(k, s, p, S, E)] = val;
         } else {
             const long long j = i - total_F;
             const long long t = j / extra;
@@ -101,18 +102,17 @@ __global__ void intensity_kernel(pwa::PassArgs a, int smp, int S, float* __restr
         const unsigned char* rec = a.tiles[smp] + (size_t)t * a.tile_bytes[smp];
         const float2* Fs = reinterpret_cast<const float2*>(rec);
         const float* m2s = reinterpret_cast<const float*>(Fs + (size_t)K * S * E);
-        const float m20 = m2s[el], m21 = m2s[E + el], m22 = m2s[2 * E + el];
         float I = 0.f;
         for (int s = 0; s < S; ++s) {
             float Ar = 0.f, Ai = 0.f;
             for (int k = 0; k < K; ++k) {
                 const pwa::KConst c = kc[k];
                 float br, bi;
-                pwa::breit_wigner(c, pwa::pick3(c.ch, m20, m21, m22), br, bi);
+                pwa::breit_wigner(c, m2s[c.ch * E + el], br, bi);
                 const float cr = c.gre * br - c.gim * bi, ci = c.gre * bi + c.gim * br;
                 int p = el + c.shift;
                 p = p >= E ? p - E : p;
-                const float2 f = Fs[((size_t)k * S + s) * E + p];
+                const float2 f = Fs[pwa::f_slot(k, s, p, S, E)];
                 Ar = fmaf(cr, f.x, fmaf(-ci, f.y, Ar));
                 Ai = fmaf(cr, f.y, fmaf(ci, f.x, Ai));
             }
@@ -149,9 +149,10 @@ KernelFn pick_kernel(int mode, int S, int W, int kpw)
 
 size_t smem_bytes(const Tiling& t, int K, int S)
 {
-    // stages | KConst[K] | sweep-2 vectors [S][E] float4 | BW cache [K][E] float2 | [W][4] doubles | mbarriers
-    return (size_t)t.NST * t.stage_bytes + (size_t)K * sizeof(pwa::KConst) + (size_t)S * t.E * 16 +
-           (size_t)K * t.E * 8 + (size_t)t.W * 32 + (size_t)t.NST * 8;
+    // stages | KConst[K] | per-warp FP64 sums [W][10 K + 2] | stage counters[4] | issued[4] | mbarriers[NST]
+    (void)S;
+    return (size_t)t.NST * t.stage_bytes + (size_t)K * sizeof(pwa::KConst) +
+           (size_t)t.W * (K * pwa::kNV + 2) * 8 + 16 + 32 + (size_t)t.NST * 8;
 }
 
 pwa_status alloc(pwa_handle* h, void** p, size_t bytes, const char* what)
