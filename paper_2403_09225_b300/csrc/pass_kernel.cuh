@@ -496,26 +496,23 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
                     const float br = Bk[j].x, bi = Bk[j].y;
                     float2 fv[S];
                     load_row<S, E>(Frow + j * H * S * E, fv);
-                    float xr[2] = {0.f, 0.f}, xi[2] = {0.f, 0.f}, yr[2] = {0.f, 0.f}, yi[2] = {0.f, 0.f};
+                    float hr = 0.f, hi = 0.f, tr = 0.f, ti = 0.f;
 #pragma unroll
                     for (int s = 0; s < S; ++s) {
                         const float2 f = fv[s];
-                        const int q = s & 1;
-                        xr[q] = fmaf(Ar[s], f.x, fmaf(Ai[s], f.y, xr[q]));
-                        xi[q] = fmaf(Ar[s], f.y, fmaf(-Ai[s], f.x, xi[q]));
+                        hr = fmaf(Ar[s], f.x, fmaf(Ai[s], f.y, hr));
+                        hi = fmaf(Ar[s], f.y, fmaf(-Ai[s], f.x, hi));
                         if constexpr (HV) {
-                            yr[q] = fmaf(Dr[s], f.x, fmaf(Di[s], f.y, yr[q]));
-                            yi[q] = fmaf(Dr[s], f.y, fmaf(-Di[s], f.x, yi[q]));
+                            tr = fmaf(Dr[s], f.x, fmaf(Di[s], f.y, tr));
+                            ti = fmaf(Dr[s], f.y, fmaf(-Di[s], f.x, ti));
                         }
                     }
-                    const float hr = xr[0] + xr[1], hi = xi[0] + xi[1];
                     const float b2r = fmaf(br, br, -bi * bi), b2i = 2.f * br * bi;
                     acc[j][0] = fmaf(hr, br, fmaf(-hi, bi, acc[j][0]));
                     acc[j][1] = fmaf(hr, bi, fmaf(hi, br, acc[j][1]));
                     acc[j][2] = fmaf(hr, b2r, fmaf(-hi, b2i, acc[j][2]));
                     acc[j][3] = fmaf(hr, b2i, fmaf(hi, b2r, acc[j][3]));
                     if constexpr (HV) {
-                        const float tr = yr[0] + yr[1], ti = yi[0] + yi[1];
                         const float b3r = fmaf(b2r, br, -b2i * bi), b3i = fmaf(b2r, bi, b2i * br);
                         acc[j][4] = fmaf(hr, b3r, fmaf(-hi, b3i, acc[j][4]));
                         acc[j][5] = fmaf(hr, b3i, fmaf(hi, b3r, acc[j][5]));
