@@ -385,9 +385,11 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
             const float2* Frow = Fs + f_slot(h, 0, p, S, E);  // F_{k,.}(e) for k = h; + i H S E for k = h + i H
 
             // ---- sweep 1: BW, couplings, coherent sums over this lane's resonances ----
-            float Ar[S], Ai[S], Dr[S], Di[S];
+            // packed FP32 pairs: A_s += Re(F) c + Im(F) (i c), two paired FMAs per
+            // complex product (and the same for Adot with cdot)
+            float2 A2[S], D2[S];
 #pragma unroll
-            for (int s = 0; s < S; ++s) Ar[s] = Ai[s] = Dr[s] = Di[s] = 0.f;
+            for (int s = 0; s < S; ++s) A2[s] = D2[s] = make_float2(0.f, 0.f);
             float2 Bk[GR ? KPW : 1];
             auto visit = [&](int k, const float2* Fk, float& br, float& bi) {
                 const KConst c = kc[k];
@@ -402,15 +404,13 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
                 }
                 float2 fv[S];
                 load_row<S, E>(Fk, fv);
+                const float2 c2 = make_float2(cr, ci), ic2 = make_float2(-ci, cr);
+                const float2 d2 = make_float2(dr, di), id2 = make_float2(-di, dr);
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
-                    const float2 f = fv[s];
-                    Ar[s] = fmaf(cr, f.x, fmaf(-ci, f.y, Ar[s]));
-                    Ai[s] = fmaf(cr, f.y, fmaf(ci, f.x, Ai[s]));
-                    if constexpr (HV) {
-                        Dr[s] = fmaf(dr, f.x, fmaf(-di, f.y, Dr[s]));
-                        Di[s] = fmaf(dr, f.y, fmaf(di, f.x, Di[s]));
-                    }
+                    const float2 fxx = make_float2(fv[s].x, fv[s].x), fyy = make_float2(fv[s].y, fv[s].y);
+                    A2[s] = __ffma2_rn(fyy, ic2, __ffma2_rn(fxx, c2, A2[s]));
+                    if constexpr (HV) D2[s] = __ffma2_rn(fyy, id2, __ffma2_rn(fxx, d2, D2[s]));
                 }
             };
             if constexpr (GR) {
@@ -426,6 +426,14 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
                     float br, bi;
                     visit(h + j * H, Frow + j * H * S * E, br, bi);
                 }
+            }
+            float Ar[S], Ai[S], Dr[S], Di[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                Ar[s] = A2[s].x;
+                Ai[s] = A2[s].y;
+                Dr[s] = D2[s].x;
+                Di[s] = D2[s].y;
             }
             // ---- the H lanes of the event combine their partial sums ----
 #pragma unroll
