@@ -208,6 +208,19 @@ def fit_metric(L, wl, n_starts: int, time_limit: float):
             "time_limit_s": time_limit}
 
 
+def aggregate_replicas(ms: float, units: float, dist=None, device="cuda"):
+    """Whole-job throughput of independent replicas: every rank processed
+    `units` in `ms` milliseconds; the job takes the slowest rank's time."""
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * units / (ms * 1e-3), ms
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -271,13 +284,8 @@ def main():
         if dist:
             dist.barrier()
     L.sync()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     units = (nd + nm) * K
-    value = world * units / (ms * 1e-3)
+    value, ms = aggregate_replicas(e0.elapsed_time(e1) / args.steps, units, dist)
     bpp = bytes_per_pass(nd, nm, K, S)
     peak, peak_kind = peaks()
     achieved = bpp / (ms * 1e-3) / 1e9
@@ -289,12 +297,7 @@ def main():
     for _ in range(e2e_steps):
         L.eval(th, v)
     e2e_dt = time.perf_counter() - t0
-    e2e_ms = e2e_dt / e2e_steps * 1e3
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * units / (e2e_ms * 1e-3)
+    e2e_value, e2e_ms = aggregate_replicas(e2e_dt / e2e_steps * 1e3, units, dist)
 
     fit = None
     if args.fits > 0 and rank == 0:

@@ -215,6 +215,15 @@ pwa_status pwa_set_tiling(pwa_handle* h, int warps, int stages, int blocks_per_s
  * events_per_tile, grid_blocks, smem_bytes_per_block). */
 pwa_status pwa_get_tiling(const pwa_handle* h, int out6[6]);
 
+/* Diagnostic of the device-side failure detection (no counterpart in the
+ * paper).  Launches one block that waits on an mbarrier which nothing ever
+ * completes, using the same bounded wait the streaming kernel applies to its
+ * tile copies, limited to `seconds` (0 < seconds <= 10) of SM clock.  Returns
+ * PWA_ETIMEOUT when the wait ran out -- the expected outcome -- with the CUDA
+ * context still usable; PWA_OK would mean the wait completed, PWA_EINVAL a
+ * bad argument, PWA_ECUDA / PWA_ENOMEM a runtime failure. */
+pwa_status pwa_selftest_bounded_wait(double seconds);
+
 /* Message describing the first failure of the handle's last call. */
 const char* pwa_last_error(const pwa_handle* h);
 

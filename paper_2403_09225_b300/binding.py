@@ -54,8 +54,8 @@ class PwaError(RuntimeError):
 #: every symbol include/pwa.h declares
 EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "pwa_grad", "pwa_hvp",
            "pwa_eval", "pwa_eval_device", "pwa_eval_device_noalloc", "pwa_sync", "pwa_event_intensity", "pwa_newton_cg_fit",
-           "pwa_fit_opts_default", "pwa_set_stream", "pwa_set_tiling", "pwa_get_tiling", "pwa_last_error",
-           "pwa_destroy")
+           "pwa_fit_opts_default", "pwa_set_stream", "pwa_set_tiling", "pwa_get_tiling",
+           "pwa_selftest_bounded_wait", "pwa_last_error", "pwa_destroy")
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pwa_set_stream": (st, [H, vp]),
         "pwa_set_tiling": (st, [H, i, i, i]),
         "pwa_get_tiling": (st, [H, ip]),
+        "pwa_selftest_bounded_wait": (st, [ctypes.c_double]),
         "pwa_last_error": (ctypes.c_char_p, [H]),
         "pwa_destroy": (None, [H]),
     }

@@ -122,6 +122,20 @@ __global__ void intensity_kernel(pwa::PassArgs a, int smp, int S, float* __restr
     }
 }
 
+// One block waits on an mbarrier that nothing completes, with the bounded
+// wait of the streaming kernel; records whether the wait ran out.
+__global__ void bounded_wait_kernel(long long budget, int* out)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        pwa::mbar_init(&bar, 1);
+        pwa::fence_mbar_init();
+    }
+    __syncthreads();
+    const bool done = pwa::mbar_wait(&bar, 0, budget);
+    if (threadIdx.x == 0) *out = done ? 1 : 2;
+}
+
 // ---------------------------------------------------------------------------
 // dispatch over the compile-time shapes (instances live in pass_*.cu)
 // ---------------------------------------------------------------------------
@@ -681,6 +695,35 @@ pwa_status pwa_get_tiling(const pwa_handle* h, int out6[6])
     out6[4] = h->tiling.grid;
     out6[5] = (int)h->tiling.smem;
     return PWA_OK;
+}
+
+pwa_status pwa_selftest_bounded_wait(double seconds)
+{
+    if (!(seconds > 0 && seconds <= 10)) return PWA_EINVAL;
+    int dev = 0, clock_khz = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev) != cudaSuccess || clock_khz <= 0) {
+        cudaGetLastError();
+        return PWA_ECUDA;
+    }
+    int* d_out = nullptr;
+    if (cudaMalloc(&d_out, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return PWA_ENOMEM;
+    }
+    int h_out = 0;
+    cudaError_t e = cudaMemset(d_out, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        bounded_wait_kernel<<<1, 32>>>((long long)(seconds * clock_khz * 1000.0), d_out);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h_out, d_out, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d_out);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return PWA_ECUDA;
+    }
+    return h_out == 2 ? PWA_ETIMEOUT : (h_out == 1 ? PWA_OK : PWA_ECUDA);
 }
 
 const char* pwa_last_error(const pwa_handle* h) { return h ? h->err.c_str() : "NULL handle"; }
