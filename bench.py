@@ -34,6 +34,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "NLL+grad+HVP event-amplitude evaluations/s (fused pass)"
+#: identifies the kernel version the committed DRAM-traffic summary was taken on
+KERNEL_REVISION = "lane-owned-k ffma2-sweep1"
 UNIT = "event*amp/s"
 CONFIG_NAME = "paper"
 
@@ -176,11 +178,12 @@ def cpu_baseline_leg():
     wl = W.make_workload(cfg, intensity=None, n_data=nd, n_mc=nm)
     th = W.random_starts(wl, 1)[0]
     v = np.linspace(-1.0, 1.0, model.P)
-    reps = 8
+    reps, dt = 0, 0.0
     t0 = time.perf_counter()
-    for _ in range(reps):
+    while reps < 2 or dt < 12.0:  # about 12 s of single-core work
         oracle.nll_grad_hvp(model, th, v, wl.data, wl.mc)
-    dt = time.perf_counter() - t0
+        reps += 1
+        dt = time.perf_counter() - t0
     return {"value": reps * (nd + nm) * cfg.K / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d data + %d MC events (1/60 of the workload), K=%d, S=%d, %d fused evaluations, "
                       "%.1f s" % (nd, nm, cfg.K, cfg.S, reps, dt)}
@@ -208,6 +211,25 @@ def fit_metric(L, wl, n_starts: int, time_limit: float):
             "time_limit_s": time_limit}
 
 
+def measured_traffic(tiling: dict):
+    """DRAM bytes per launch of the fused HVP pass from the committed ncu
+    summary, when it was taken with the tiling in use (else None)."""
+    path = os.path.join(ROOT, "profiles", "pass_kernel_hvp_paper_traffic.txt")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_revision") != KERNEL_REVISION or kv.get("tiling") != "%d,%d" % (
+                tiling["warps"], tiling["stages"]):
+            return None
+        return float(kv["dram_bytes_per_launch_full"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def aggregate_replicas(ms: float, units: float, dist=None, device="cuda"):
     """Whole-job throughput of independent replicas: every rank processed
     `units` in `ms` milliseconds; the job takes the slowest rank's time."""
@@ -228,6 +250,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fits", type=int, default=2, help="random-start fits for the fit metric (0: skip)")
+    ap.add_argument("--fit-time-limit", type=float, default=10.0, help="seconds per fit (early stopping)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tiling", default="", help="warps,lanes_per_event,stages[,blocks_per_sm] (default: library's)")
     ap.add_argument("--scale", type=float, default=1.0,
@@ -301,22 +324,15 @@ def main():
 
     fit = None
     if args.fits > 0 and rank == 0:
-        fit = fit_metric(L, wl, args.fits, time_limit=20.0)
+        fit = fit_metric(L, wl, args.fits, time_limit=args.fit_time_limit)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_leg()
 
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic_paper_hvp.json")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as f:
-                traffic = json.load(f).get("dram_bytes_per_launch")
-        except Exception:
-            traffic = None
-
     til = L.get_tiling()
+    traffic = measured_traffic(til)
+
     if rank == 0:
         res = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
