@@ -189,12 +189,8 @@ def cpu_baseline_leg():
                       "%.1f s" % (nd, nm, cfg.K, cfg.S, reps, dt)}
 
 
-def fit_metric(L, wl, n_starts: int, time_limit: float):
-    """Newton-CG fits from random starts; a fit reaches the global minimum when
-    its NLL is within 0.01 of the best NLL over all fits (including one from
-    theta_true)."""
+def _fit_runs(L, wl, starts, time_limit: float):
     from paper_2403_09225_b300 import workload as W
-    starts = W.random_starts(wl, n_starts)
     ref, ref_info = L.fit(wl.theta_true, xtol=1e-8, time_limit_s=time_limit)
     results = []
     t0 = time.perf_counter()
@@ -204,11 +200,31 @@ def fit_metric(L, wl, n_starts: int, time_limit: float):
     total = time.perf_counter() - t0
     best = min([ref_info["nll"]] + [r["nll"] for r in results])
     ok = sum(1 for r in results if r["nll"] <= best + 0.01)
-    return {"starts": n_starts, "reached_global_min": ok, "gpu_seconds": total,
-            "fits_to_global_min_per_s": ok / total if total > 0 else 0.0,
-            "best_nll": best, "passes": int(sum(r["n_fev"] + r["n_hvp"] for r in results)),
-            "statuses": sorted({r["status"] for r in results}), "xtol": 1e-8,
-            "time_limit_s": time_limit}
+    return {"starts": len(starts), "reached_global_min": ok, "gpu_seconds": total,
+            "fits_to_global_min_per_s": ok / total if total > 0 else 0.0, "best_nll": best,
+            "passes": int(sum(r["n_fev"] + r["n_hvp"] for r in results)),
+            "statuses": sorted({r["status"] for r in results}), "time_limit_s": time_limit}
+
+
+def fit_metric(L, wl, n_starts: int, time_limit: float):
+    """Newton-CG fits (xtol 1e-8) from random starts of the prior.  A fit
+    reaches the global minimum when its NLL is within 0.01 of the best NLL
+    seen over all fits of that workload (including one from theta_true).
+    The paper-scale fits are bounded by an early-stopping time limit; the
+    tiny configuration (K = 3, 2e4 + 1e5 events) shows the rate on a model
+    whose fits finish."""
+    from paper_2403_09225_b300 import binding
+    from paper_2403_09225_b300 import workload as W
+    out = {"xtol": 1e-8, "paper": _fit_runs(L, wl, W.random_starts(wl, n_starts), time_limit)}
+    cfg = W.CONFIGS["tiny"]
+    table = W.make_table(cfg)
+    tiny = W.make_workload(cfg, intensity=gpu_intensity_fn(table, cfg.K, cfg.S))
+    Lt = binding.make_likelihood(tiny)
+    try:
+        out["tiny"] = _fit_runs(Lt, tiny, W.random_starts(tiny, 32), time_limit)
+    finally:
+        Lt.close()
+    return out
 
 
 def measured_traffic(tiling: dict):
