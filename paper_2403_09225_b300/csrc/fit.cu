@@ -5,8 +5,9 @@
 // a line search for the strong Wolfe conditions (their Algorithms 3.5/3.6).
 // This is an independent C++ restatement of those textbook steps driving the
 // fused GPU pass: every gradient is one pass over F, every inner CG step is
-// one Hessian-vector pass.  The CG scalars (dot products, curvature, step
-// lengths) and all vectors are FP64.
+// one Hessian-vector pass.  The inner CG runs on the device (FP64 vectors and
+// scalars: dot products, curvature, step lengths), replayed as a CUDA graph
+// in batches of iterations; the outer loop and the line search run on the host.
 //
 // Differences from the textbook statement, all because the NLL is summed
 // from FP32 per-event terms (its value carries rounding noise far above
@@ -24,6 +25,209 @@
 
 namespace {
 
+// ---------------------------------------------------------------------------
+// inner CG on the device: every iteration is one fused HVP pass plus one
+// single-block FP64 update; batches of iterations are replayed as a CUDA
+// graph and only the termination word returns to the host
+// ---------------------------------------------------------------------------
+
+constexpr int kCgThreads = 256;
+constexpr int kCgBatch = 8;  // CG iterations per graph launch
+
+struct DevCG {
+    double* x;      // [P] point of the Newton step
+    double* g;      // [P] gradient at x
+    double* z;      // [P] CG iterate (the step on exit)
+    double* r;      // [P] residual
+    double* d;      // [P] search direction
+    double* out;    // [1 + 2P] pass output; H d at out + 1 + P
+    double* scal;   // rr, eps
+    int* flags;     // done (0 running, 1 negative curvature, 2 converged, 3 iteration limit), j, passes
+};
+
+// fixed-order block sum of one FP64 value per thread
+__device__ double block_sum(double v, double* sh)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = kCgThreads / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double s = sh[0];
+    __syncthreads();
+    return s;
+}
+
+__global__ void __launch_bounds__(kCgThreads) cg_init_kernel(DevCG c, int P, double eps)
+{
+    __shared__ double sh[kCgThreads];
+    double rr = 0.0;
+    for (int i = threadIdx.x; i < P; i += kCgThreads) {
+        const double gi = c.g[i];
+        c.z[i] = 0.0;
+        c.r[i] = gi;
+        c.d[i] = -gi;
+        rr += gi * gi;
+    }
+    rr = block_sum(rr, sh);
+    if (threadIdx.x == 0) {
+        c.scal[0] = rr;
+        c.scal[1] = eps;
+        c.flags[0] = 0;
+        c.flags[1] = 0;
+        c.flags[2] = 0;
+    }
+}
+
+// one CG iteration (N&W Algorithm 7.1, inner loop) after H d is in c.out
+__global__ void __launch_bounds__(kCgThreads) cg_step_kernel(DevCG c, int P, int maxiter)
+{
+    __shared__ double sh[kCgThreads];
+    __shared__ int s_done;
+    if (threadIdx.x == 0) s_done = c.flags[0];
+    __syncthreads();
+    if (s_done) return;
+    const double* Bd = c.out + 1 + P;
+    double curv = 0.0;
+    for (int i = threadIdx.x; i < P; i += kCgThreads) curv += c.d[i] * Bd[i];
+    curv = block_sum(curv, sh);
+    const int j = c.flags[1];
+    if (threadIdx.x == 0) c.flags[2] += 1;
+    if (!(curv > 0.0)) {
+        // negative curvature: steepest descent on the first iteration, else the current iterate
+        if (j == 0)
+            for (int i = threadIdx.x; i < P; i += kCgThreads) c.z[i] = -c.g[i];
+        if (threadIdx.x == 0) c.flags[0] = 1;
+        return;
+    }
+    const double rr = c.scal[0];
+    const double alpha = rr / curv;
+    double rr_new = 0.0;
+    for (int i = threadIdx.x; i < P; i += kCgThreads) {
+        c.z[i] += alpha * c.d[i];
+        const double ri = c.r[i] + alpha * Bd[i];
+        c.r[i] = ri;
+        rr_new += ri * ri;
+    }
+    rr_new = block_sum(rr_new, sh);
+    if (sqrt(rr_new) < c.scal[1]) {
+        if (threadIdx.x == 0) {
+            c.flags[0] = 2;
+            c.flags[1] = j + 1;
+        }
+        return;
+    }
+    if (j + 1 >= maxiter) {
+        if (threadIdx.x == 0) {
+            c.flags[0] = 3;
+            c.flags[1] = j + 1;
+        }
+        return;
+    }
+    const double beta = rr_new / rr;
+    for (int i = threadIdx.x; i < P; i += kCgThreads) c.d[i] = -c.r[i] + beta * c.d[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        c.scal[0] = rr_new;
+        c.flags[1] = j + 1;
+    }
+}
+
+struct DeviceCG {
+    pwa_handle* h = nullptr;
+    int P = 0;
+    double* block = nullptr;
+    DevCG c{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+
+    pwa_status init(pwa_handle* hh)
+    {
+        h = hh;
+        P = h->P;
+        const size_t n = 5 * (size_t)P + (1 + 2 * (size_t)P) + 2 + 2;
+        if (cudaMalloc(&block, n * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return pwa::set_error(h, PWA_ENOMEM, "cudaMalloc failed for the CG state");
+        }
+        c.x = block;
+        c.g = c.x + P;
+        c.z = c.g + P;
+        c.r = c.z + P;
+        c.d = c.r + P;
+        c.out = c.d + P;
+        c.scal = c.out + 1 + 2 * P;
+        c.flags = reinterpret_cast<int*>(c.scal + 2);
+        return PWA_OK;
+    }
+
+    // capture kCgBatch iterations (HVP pass at x along d, then the update) once
+    pwa_status capture(int maxiter)
+    {
+        cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return pwa::cuda_error(h, e, "cudaStreamBeginCapture");
+        pwa_status st = PWA_OK;
+        for (int b = 0; b < kCgBatch && st == PWA_OK; ++b) {
+            st = pwa::launch_pass(h, c.x, c.d, c.out, pwa::MODE_HVP, c.flags);
+            if (st == PWA_OK) {
+                cg_step_kernel<<<1, kCgThreads, 0, h->stream>>>(c, P, maxiter);
+                e = cudaGetLastError();
+                if (e != cudaSuccess) st = pwa::cuda_error(h, e, "cg_step launch");
+            }
+        }
+        e = cudaStreamEndCapture(h->stream, &graph);
+        if (st != PWA_OK) return st;
+        if (e != cudaSuccess) return pwa::cuda_error(h, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) return pwa::cuda_error(h, e, "cudaGraphInstantiate");
+        return PWA_OK;
+    }
+
+    // p = approximate solution of H p = -g at x (inner loop of Algorithm 7.1)
+    pwa_status solve(const std::vector<double>& x, const std::vector<double>& g, double eps, int maxiter,
+                     std::vector<double>& p, int& n_hvp)
+    {
+        if (!exec) {
+            pwa_status st = capture(maxiter);
+            if (st != PWA_OK) return st;
+        }
+        double* pin = h->h_pin;  // 4P + 8 doubles of pinned staging
+        std::memcpy(pin, x.data(), sizeof(double) * P);
+        std::memcpy(pin + P, g.data(), sizeof(double) * P);
+        cudaError_t e = cudaMemcpyAsync(c.x, pin, sizeof(double) * 2 * P, cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) return pwa::cuda_error(h, e, "CG upload");
+        cg_init_kernel<<<1, kCgThreads, 0, h->stream>>>(c, P, eps);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return pwa::cuda_error(h, e, "cg_init launch");
+        int flags[3] = {0, 0, 0};
+        for (int done_batches = 0;; ++done_batches) {
+            e = cudaGraphLaunch(exec, h->stream);
+            if (e != cudaSuccess) return pwa::cuda_error(h, e, "cudaGraphLaunch");
+            e = cudaMemcpyAsync(pin + 2 * P, c.flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) return pwa::cuda_error(h, e, "CG flags");
+            std::memcpy(flags, pin + 2 * P, sizeof(int) * 3);
+            if (flags[0]) break;
+            if ((done_batches + 1) * kCgBatch > maxiter + kCgBatch) break;  // guard; the step sets flag 3 first
+        }
+        n_hvp += flags[2];
+        e = cudaMemcpyAsync(pin, c.z, sizeof(double) * P, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return pwa::cuda_error(h, e, "CG download");
+        p.assign(pin, pin + P);
+        return pwa::check_device_errors(h);
+    }
+
+    ~DeviceCG()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (block) cudaFree(block);
+        cudaGetLastError();
+    }
+};
+
 struct Evaluator {
     pwa_handle* h;
     int n_fev = 0, n_hvp = 0;
@@ -32,13 +236,6 @@ struct Evaluator {
     {
         ++n_fev;
         return pwa_eval(h, x.data(), nullptr, &f, g.data(), nullptr);
-    }
-    pwa_status hessp(const std::vector<double>& x, const std::vector<double>& d, std::vector<double>& out)
-    {
-        ++n_hvp;
-        double f;
-        std::vector<double> g(x.size());
-        return pwa_eval(h, x.data(), d.data(), &f, g.data(), out.data());
     }
 };
 
@@ -96,10 +293,34 @@ extern "C" pwa_status pwa_newton_cg_fit(pwa_handle* h, const double* theta0, con
     const int cg_maxiter = o.cg_maxiter > 0 ? o.cg_maxiter : 20 * n;
     const double c1 = 1e-4, c2 = 0.9;
 
+    // the CG graph is captured on a private non-default stream
+    cudaStream_t user_stream = h->stream, fit_stream = nullptr;
+    if (cudaStreamCreateWithFlags(&fit_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return pwa::set_error(h, PWA_ECUDA, "cannot create the fit stream");
+    }
+    if (user_stream) cudaStreamSynchronize(user_stream);
+    else cudaDeviceSynchronize();
+    h->stream = fit_stream;
+    struct Restore {
+        pwa_handle* h;
+        cudaStream_t user, own;
+        ~Restore()
+        {
+            cudaStreamSynchronize(own);
+            h->stream = user;
+            cudaStreamDestroy(own);
+            cudaGetLastError();
+        }
+    } restore{h, user_stream, fit_stream};
+    DeviceCG cg;
+    pwa_status st = cg.init(h);
+    if (st != PWA_OK) return st;
+
     Evaluator ev{h};
-    std::vector<double> x(theta0, theta0 + n), g(n), p(n), z(n), r(n), d(n), Bd(n);
+    std::vector<double> x(theta0, theta0 + n), g(n), p(n);
     double f = 0.0;
-    pwa_status st = ev.fg(x, f, g);
+    st = ev.fg(x, f, g);
     if (st != PWA_OK) return st;
 
     int status = PWA_FIT_MAXITER;
@@ -111,40 +332,11 @@ extern "C" pwa_status pwa_newton_cg_fit(pwa_handle* h, const double* theta0, con
             status = PWA_FIT_GTOL;
             break;
         }
-        // ---- inner CG on H p = -g (N&W Algorithm 7.1) ----
+        // ---- inner CG on H p = -g (N&W Algorithm 7.1), on the device ----
         const double gnorm = std::sqrt(dot(g, g));
         const double eps = std::min(0.5, std::sqrt(gnorm)) * gnorm;
-        std::fill(z.begin(), z.end(), 0.0);
-        r = g;
-        for (int i = 0; i < n; ++i) d[i] = -r[i];
-        double rr = dot(r, r);
-        bool have_p = false;
-        for (int j = 0; j < cg_maxiter; ++j) {
-            st = ev.hessp(x, d, Bd);
-            if (st != PWA_OK) return st;
-            const double curv = dot(d, Bd);
-            if (curv <= 0) {
-                if (j == 0) for (int i = 0; i < n; ++i) p[i] = -g[i];
-                else p = z;
-                have_p = true;
-                break;
-            }
-            const double alpha = rr / curv;
-            for (int i = 0; i < n; ++i) {
-                z[i] += alpha * d[i];
-                r[i] += alpha * Bd[i];
-            }
-            const double rr_new = dot(r, r);
-            if (std::sqrt(rr_new) < eps) {
-                p = z;
-                have_p = true;
-                break;
-            }
-            const double beta = rr_new / rr;
-            for (int i = 0; i < n; ++i) d[i] = -r[i] + beta * d[i];
-            rr = rr_new;
-        }
-        if (!have_p) p = z;
+        st = cg.solve(x, g, eps, cg_maxiter, p, ev.n_hvp);
+        if (st != PWA_OK) break;
         ++k;
         double pmean = 0.0;
         for (double v : p) pmean += std::fabs(v);

@@ -93,6 +93,7 @@ struct PassArgs {
     unsigned long long* bad;
     int* err;
     long long timeout_cycles;
+    const int* skip = nullptr;  // when set and non-zero at launch, the pass does nothing
 };
 
 // ---------------------------------------------------------------------------
@@ -180,27 +181,35 @@ __device__ __forceinline__ ResValues res_values(const PassArgs& a, int k, bool w
 
 __device__ __forceinline__ KConst make_kconst(const PassArgs& a, int k, bool with_v, int ev)
 {
+    // FP64 only where FP32 would lose the narrow peaks (M^2 as an FP32 pair,
+    // M Gamma) and for the phase's range reduction; the FP32 constants are
+    // otherwise computed in FP32 (the FP64 pipe is narrow on this GPU)
     const ResValues rv = res_values(a, k, with_v);
-    double s, c;
-    sincos(rv.phi, &s, &c);
-    const double gre = rv.rho * c, gim = rv.rho * s;
+    const double phr = rv.phi - 6.283185307179586 * rint(rv.phi * 0.15915494309189535);
+    float s, c;
+    sincosf((float)phr, &s, &c);
+    const float rho = (float)rv.rho;
+    const float gre = rho * c, gim = rho * s;
     const double M2 = rv.M * rv.M;
+    const double MG = rv.M * rv.G;
     KConst kc;
     kc.m2hi = (float)M2;
     kc.m2lo = (float)(M2 - (double)kc.m2hi);
-    kc.mg = (float)(rv.M * rv.G);
+    kc.mg = (float)MG;
+    kc.mg2 = (float)(MG * MG);
     kc.ch = a.res[k].channel;
-    kc.gre = (float)gre;
-    kc.gim = (float)gim;
+    kc.gre = gre;
+    kc.gim = gim;
     // alpha = v_rho E + i v_phi g
-    kc.are = (float)(rv.vr * c - rv.vp * gim);
-    kc.aim = (float)(rv.vr * s + rv.vp * gre);
+    const float vr = (float)rv.vr, vp = (float)rv.vp, vm = (float)rv.vm, vg = (float)rv.vg;
+    const float M = (float)rv.M, G = (float)rv.G;
+    kc.are = vr * c - vp * gim;
+    kc.aim = vr * s + vp * gre;
     // u = v_M a1 + v_G a2, a1 = -2M + i G, a2 = i M;  beta = g u
-    const double ure = -2.0 * rv.M * rv.vm, uim = rv.G * rv.vm + rv.M * rv.vg;
-    kc.bre = (float)(gre * ure - gim * uim);
-    kc.bim = (float)(gre * uim + gim * ure);
+    const float ure = -2.f * M * vm, uim = G * vm + M * vg;
+    kc.bre = gre * ure - gim * uim;
+    kc.bim = gre * uim + gim * ure;
     kc.shift = ev < 16 ? (k % (16 / ev)) * ev : 0;
-    kc.mg2 = (float)((rv.M * rv.G) * (rv.M * rv.G));
     return kc;
 }
 
@@ -275,6 +284,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
     __shared__ int s_flag;
     __shared__ volatile int s_abort;
 
+    if (a.skip && *a.skip) return;  // a device-side loop has already finished (uniform for the grid)
     const long long T = (long long)a.ntiles[0] + a.ntiles[1];
     const long long G = gridDim.x;
 

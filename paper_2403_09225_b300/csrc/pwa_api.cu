@@ -425,13 +425,16 @@ pwa_status create_impl(pwa_handle* h, const pwa_events* data, const pwa_events* 
 
     PWA_TRY(alloc(h, reinterpret_cast<void**>(&h->d_res), sizeof(ResParam) * K, "parameter map"));
     PWA_CUDA(h, cudaMemcpyAsync(h->d_res, h->res.data(), sizeof(ResParam) * K, cudaMemcpyHostToDevice, h->stream));
-    PWA_TRY(alloc(h, reinterpret_cast<void**>(&h->d_theta), sizeof(double) * std::max(P, 1), "theta"));
-    PWA_TRY(alloc(h, reinterpret_cast<void**>(&h->d_v), sizeof(double) * std::max(P, 1), "v"));
-    PWA_TRY(alloc(h, reinterpret_cast<void**>(&h->d_out), sizeof(double) * (1 + 2 * P), "output"));
-    PWA_TRY(alloc(h, reinterpret_cast<void**>(&h->d_bad), sizeof(unsigned long long), "status"));
-    PWA_TRY(alloc(h, reinterpret_cast<void**>(&h->d_err), sizeof(int), "status"));
-    PWA_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
-    if (cudaMallocHost(reinterpret_cast<void**>(&h->h_pin), sizeof(double) * (4 + 4 * P)) != cudaSuccess) {
+    // one device block for a call's inputs and results, so that a host call
+    // needs one copy each way: theta[P] | v[P] | err (8 B) | bad (8 B) | out[1 + 2P]
+    PWA_TRY(alloc(h, reinterpret_cast<void**>(&h->d_theta), sizeof(double) * (2 * (size_t)P + 3 + 2 * P),
+                  "call buffers"));
+    h->d_v = h->d_theta + P;
+    h->d_err = reinterpret_cast<int*>(h->d_theta + 2 * P);
+    h->d_bad = reinterpret_cast<unsigned long long*>(h->d_theta + 2 * P + 1);
+    h->d_out = h->d_theta + 2 * P + 2;
+    PWA_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(double), h->stream));
+    if (cudaMallocHost(reinterpret_cast<void**>(&h->h_pin), sizeof(double) * (8 + 4 * P)) != cudaSuccess) {
         cudaGetLastError();
         return pwa::set_error(h, PWA_ENOMEM, "pinned host allocation failed");
     }
@@ -482,7 +485,8 @@ pwa_status cuda_error(pwa_handle* h, cudaError_t e, const char* what)
     return set_error(h, PWA_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-pwa_status launch_pass(pwa_handle* h, const double* d_theta, const double* d_v, double* d_out, int mode)
+pwa_status launch_pass(pwa_handle* h, const double* d_theta, const double* d_v, double* d_out, int mode,
+                       const int* skip)
 {
     if (h->broken) return set_error(h, PWA_ETIMEOUT, "handle is unusable after a device-side timeout");
     KernelFn fn = pick_kernel(mode, h->S, h->tiling.W, h->tiling.KPW);
@@ -494,7 +498,8 @@ pwa_status launch_pass(pwa_handle* h, const double* d_theta, const double* d_v, 
         if (h->tile_bytes[s] > t.stage_bytes || (long long)h->ntiles[s] * t.E < h->n[s] ||
             h->tile_bytes[s] % 16 != 0)
             return set_error(h, PWA_EINVAL, "inconsistent tile geometry");
-    const PassArgs a = make_args(h, d_theta, d_v, d_out);
+    PassArgs a = make_args(h, d_theta, d_v, d_out);
+    a.skip = skip;
     fn<<<h->tiling.grid, 32 * h->tiling.W, h->tiling.smem, h->stream>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(h, e, "pass kernel launch");
@@ -576,12 +581,17 @@ pwa_status pwa_eval(pwa_handle* h, const double* theta, const double* v, double*
     double* pin = h->h_pin;
     std::memcpy(pin, theta, sizeof(double) * P);
     if (hv) std::memcpy(pin + P, v, sizeof(double) * P);
-    PWA_CUDA(h, cudaMemcpyAsync(h->d_theta, pin, sizeof(double) * P, cudaMemcpyHostToDevice, h->stream));
-    if (hv) PWA_CUDA(h, cudaMemcpyAsync(h->d_v, pin + P, sizeof(double) * P, cudaMemcpyHostToDevice, h->stream));
+    PWA_CUDA(h, cudaMemcpyAsync(h->d_theta, pin, sizeof(double) * (hv ? 2 * P : P), cudaMemcpyHostToDevice,
+                                h->stream));
     PWA_TRY(pwa::launch_pass(h, h->d_theta, hv ? h->d_v : nullptr, h->d_out, mode));
-    double* res = pin + 2 * P;
-    PWA_CUDA(h, cudaMemcpyAsync(res, h->d_out, sizeof(double) * (1 + 2 * P), cudaMemcpyDeviceToHost, h->stream));
-    PWA_TRY(pwa::check_device_errors(h));
+    // error word, first bad event and the results in one copy
+    double* st = pin + 2 * P;
+    PWA_CUDA(h, cudaMemcpyAsync(st, h->d_err, sizeof(double) * (3 + 2 * P), cudaMemcpyDeviceToHost, h->stream));
+    PWA_CUDA(h, cudaStreamSynchronize(h->stream));
+    int err_word = 0;
+    std::memcpy(&err_word, st, sizeof(int));
+    if (err_word) PWA_TRY(pwa::check_device_errors(h));
+    const double* res = st + 2;
     *nll = res[0];
     if (grad) std::memcpy(grad, res + 1, sizeof(double) * P);
     if (hv) std::memcpy(hv, res + 1 + P, sizeof(double) * P);
@@ -733,9 +743,9 @@ void pwa_destroy(pwa_handle* h)
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
-    void* ptrs[] = {h->d_res,   h->d_F[0],      h->d_F[1],      h->d_m2[0], h->d_m2[1],  h->d_w,
-                    h->d_tiles[0], h->d_tiles[1], h->d_block_rec, h->d_group_rec, h->d_counts, h->d_theta,
-                    h->d_v,     h->d_out,       h->d_bad,       h->d_err};
+    // d_v, d_err, d_bad and d_out live inside the d_theta block
+    void* ptrs[] = {h->d_res,      h->d_F[0],     h->d_F[1],      h->d_m2[0],     h->d_m2[1], h->d_w,
+                    h->d_tiles[0], h->d_tiles[1], h->d_block_rec, h->d_group_rec, h->d_counts, h->d_theta};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_pin) cudaFreeHost(h->h_pin);

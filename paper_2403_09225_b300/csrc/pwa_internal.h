@@ -84,7 +84,9 @@ PWA_DECLARE_PICK(hvp)
 #undef PWA_DECLARE_PICK
 
 // Enqueue one fused pass on device buffers (theta, v: device [P]; out: device [1+2P]).
-pwa_status launch_pass(pwa_handle* h, const double* d_theta, const double* d_v, double* d_out, int mode);
+// skip: optional device flag; the pass does nothing when it is non-zero at launch.
+pwa_status launch_pass(pwa_handle* h, const double* d_theta, const double* d_v, double* d_out, int mode,
+                       const int* skip = nullptr);
 // Read back and clear the device error flags; turns them into a status + message.
 pwa_status check_device_errors(pwa_handle* h);
 pwa_status set_error(pwa_handle* h, pwa_status st, const std::string& msg);
