@@ -64,13 +64,21 @@ struct __align__(16) KConst {  // FP32 per-resonance constants (48 bytes)
     float mg2;                 // (M Gamma)^2
 };
 
-// Position of F_{k,s} of the event at tile position p inside a tile's F block
-// (float2 units).  Even S stores the projections in pairs, (s, s+1) adjacent,
-// so that one 16-byte load fetches two of them; odd S stores [k][s][p].
+// Layout of a tile's F block.  Even S: for each (k, projection pair q = s/2, tile
+// position p) one 16-byte group holds (Re F_{2q}, Re F_{2q+1}, Im F_{2q}, Im F_{2q+1}),
+// so that the real parts and the imaginary parts of two projections load as packed
+// FP32 pairs; the groups are ordered [k][q][p].  Odd S: (Re F, Im F) at [k][s][p].
+// f_slot: float2 index of the group of (k, s, p) (even S) or of its (Re, Im) pair (odd S).
 __host__ __device__ inline int f_slot(int k, int s, int p, int S, int E)
 {
-    return (S % 2 == 0) ? ((k * (S / 2) + s / 2) * E + p) * 2 + (s & 1) : (k * S + s) * E + p;
+    return (S % 2 == 0) ? ((k * (S / 2) + s / 2) * E + p) * 2 : (k * S + s) * E + p;
 }
+// f_re: float index of Re F_{k,s} at tile position p; Im F is f_im_off(S) floats further.
+__host__ __device__ inline int f_re(int k, int s, int p, int S, int E)
+{
+    return (S % 2 == 0) ? ((k * (S / 2) + s / 2) * E + p) * 4 + (s & 1) : ((k * S + s) * E + p) * 2;
+}
+__host__ __device__ inline int f_im_off(int S) { return S % 2 == 0 ? 2 : 1; }
 
 struct PassArgs {
     const unsigned char* tiles[2];  // data, MC tile records
@@ -138,7 +146,7 @@ __device__ __forceinline__ void tma_load_tile(void* dst, const void* src, uint32
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget)
 {
     const uint32_t a = smem_addr(bar);
-    const long long t0 = clock64();
+    long long t0 = -1;  // the clock is read only once the first try has failed
     while (true) {
         uint32_t done;
         asm volatile(
@@ -147,8 +155,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > budget) return false;
+        const long long now = clock64();
+        if (t0 < 0) t0 = now;
+        else if (now - t0 > budget) return false;
     }
+}
+
+// acc = (hi, lo) += x with Knuth's TwoSum: hi + lo stays the exact sum up to the
+// rounding of lo (about 2^-48 relative), without the FP64 pipe
+__device__ __forceinline__ void two_sum_add(float2& acc, float x)
+{
+    const float s = __fadd_rn(acc.x, x);
+    const float bp = __fsub_rn(s, acc.x);
+    const float ap = __fsub_rn(s, bp);
+    const float err = __fadd_rn(__fsub_rn(acc.x, ap), __fsub_rn(x, bp));
+    acc = make_float2(s, __fadd_rn(acc.y, err));
 }
 
 __device__ __forceinline__ float warp_sum(float x)
@@ -223,13 +244,10 @@ __device__ __forceinline__ void breit_wigner(const KConst& kc, float m2, float& 
     bi = kc.mg * r;
 }
 
-__device__ __forceinline__ float pick3(int ch, float a0, float a1, float a2)
-{
-    return ch == 0 ? a0 : (ch == 1 ? a1 : a2);
-}
-
 // The S projections of one (resonance, event) from the tile's F block; row
-// points at s = 0 (see f_slot): 16-byte loads for pairs when S is even.
+// points at s = 0 (see f_slot).  Even S: one 16-byte load per projection pair q,
+// fv[2q] = (Re F_2q, Re F_2q+1) and fv[2q+1] = (Im F_2q, Im F_2q+1).  Odd S:
+// fv[s] = (Re F_s, Im F_s).
 template <int S, int E>
 __device__ __forceinline__ void load_row(const float2* row, float2 (&fv)[S])
 {
@@ -273,11 +291,11 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = a.K, NST = a.NST;
 
-    // shared memory: stages | KConst[K] | per-warp FP64 sums [W][K*kNV + 2] | stage counters | mbarriers
+    // shared memory: stages | KConst[K] | per-warp (hi, lo) FP32 sums [W][K*kNV + 2] | stage counters | mbarriers
     unsigned char* stages = smem;
     KConst* kc = reinterpret_cast<KConst*>(smem + (size_t)NST * a.stage_bytes);
     const int wlen = K * kNV + 2;
-    double* wacc = reinterpret_cast<double*>(kc + K);
+    float2* wacc = reinterpret_cast<float2*>(kc + K);  // (hi, lo) FP32 pairs: hi + lo is the exact running sum
     unsigned* stage_cnt = reinterpret_cast<unsigned*>(wacc + W * wlen);
     long long* issued = reinterpret_cast<long long*>(stage_cnt + 4);  // last iteration issued per stage
     uint64_t* mbar = reinterpret_cast<uint64_t*>(issued + 4);
@@ -308,7 +326,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
         }
     }
     for (int k = tid; k < K; k += NT) kc[k] = make_kconst(a, k, HV, EV);
-    for (int i = tid; i < W * wlen; i += NT) wacc[i] = 0.0;
+    for (int i = tid; i < W * wlen; i += NT) wacc[i] = make_float2(0.f, 0.f);
     __syncthreads();
 
     // lane (h, el): event e = warp * EV + el of every tile, resonances k = h + i H
@@ -317,6 +335,13 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
     // all resonances of a lane share one rotation (it depends on k mod (H/2))
     const int p = (e + (h < K ? kc[h].shift : 0)) & (E - 1);
     const int kcount = h < K ? (K - 1 - h) / H + 1 : 0;  // resonances of this lane (<= KPW in GRAD/HVP)
+    // channels of this lane's resonances, 2 bits each, so that the m^2 loads need no KConst load
+    uint32_t chbits = 0;
+    if constexpr (GR) {
+#pragma unroll
+        for (int j = 0; j < KPW; ++j)
+            if (j < kcount) chbits |= (uint32_t)kc[h + j * H].ch << (2 * j);
+    }
 
     // FP32 per-lane sums of the current fold window
     float acc[GR ? KPW : 1][GR ? NVM : 1];
@@ -326,10 +351,12 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
         for (int q = 0; q < (GR ? NVM : 1); ++q) acc[j][q] = 0.f;
     float sc0 = 0.f, sc1 = 0.f;
 
-    // fold the warp's FP32 sums into its FP64 sums in shared memory: reduce over
-    // the EV lanes of each resonance group, lane el == 0 adds (fixed order)
+    // fold the warp's FP32 sums into its compensated (hi, lo) sums in shared memory:
+    // reduce over the EV lanes of each resonance group, lane el == 0 adds (fixed
+    // order).  TwoSum keeps these sums as exact as FP64 ones without the FP64
+    // pipe, which is narrow on this GPU.
     auto fold = [&]() {
-        double* wa = wacc + warp * wlen;
+        float2* wa = wacc + warp * wlen;
         if constexpr (GR) {
 #pragma unroll
             for (int j = 0; j < KPW; ++j)
@@ -339,14 +366,14 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
                     acc[j][q] = 0.f;
 #pragma unroll
                     for (int o = 1; o < EV; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (el == 0 && j < kcount) wa[(h + j * H) * kNV + q] += (double)v;
+                    if (el == 0 && j < kcount) two_sum_add(wa[(h + j * H) * kNV + q], v);
                 }
         }
         const float t0 = warp_sum(sc0), t1 = warp_sum(sc1);
         sc0 = sc1 = 0.f;
         if (lane == 0) {
-            wa[K * kNV + 0] += (double)t0;
-            wa[K * kNV + 1] += (double)t1;
+            two_sum_add(wa[K * kNV + 0], t0);
+            two_sum_add(wa[K * kNV + 1], t1);
         }
     };
 
@@ -357,31 +384,21 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
         for (int i = tid; i < K * kNV + kNScal; i += NT) {
             double v = 0.0;
             if (i < wlen)
-                for (int w = 0; w < W; ++w) v += wacc[w * wlen + i];
+                for (int w = 0; w < W; ++w) v += (double)wacc[w * wlen + i].x + (double)wacc[w * wlen + i].y;
             rec[i] = v;
         }
         __syncthreads();
-        for (int i = tid; i < W * wlen; i += NT) wacc[i] = 0.0;
+        for (int i = tid; i < W * wlen; i += NT) wacc[i] = make_float2(0.f, 0.f);
         __syncthreads();
     };
 
-    int cur_set = -1;
-    bool set_written[2] = {false, false};
     int win = 0;
     int st = 0;         // stage of iteration i (i mod NST), kept without 64-bit division
     uint32_t ph = 0;    // barrier phase parity of iteration i ((i / NST) & 1)
-    for (long long i = 0, t = blockIdx.x; t < T; ++i, t += G) {
-        const int smp = t < a.ntiles[0] ? 0 : 1;
+    // one tile of sample set SMP (0 data, 1 MC): global tile index t, iteration i of this block
+    auto tile = [&](auto smp_c, long long t, long long i) {
+        constexpr int smp = decltype(smp_c)::value;
         const long long lt = smp ? t - a.ntiles[0] : t;
-        if (smp != cur_set) {  // every warp reaches this tile index: a block barrier is safe
-            if (cur_set >= 0) {
-                fold();
-                write_set(cur_set);
-                set_written[cur_set] = true;
-            }
-            cur_set = smp;
-            win = 0;
-        }
         bool ok = false;
         if (!s_abort) {
             ok = __all_sync(0xffffffffu, mbar_wait(&mbar[st], ph, a.timeout_cycles));
@@ -397,53 +414,113 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
             // ---- sweep 1: BW, couplings, coherent sums over this lane's resonances ----
             // packed FP32 pairs: A_s += Re(F) c + Im(F) (i c), two paired FMAs per
             // complex product (and the same for Adot with cdot)
-            float2 A2[S], D2[S];
-#pragma unroll
-            for (int s = 0; s < S; ++s) A2[s] = D2[s] = make_float2(0.f, 0.f);
+            float Ar[S], Ai[S], Dr[S], Di[S];
             float2 Bk[GR ? KPW : 1];
-            auto visit = [&](int k, const float2* Fk, float& br, float& bi) {
-                const KConst c = kc[k];
-                breit_wigner(c, m2s[c.ch * E + e], br, bi);
-                const float cr = c.gre * br - c.gim * bi, ci = c.gre * bi + c.gim * br;
-                float dr = 0.f, di = 0.f;
-                if constexpr (HV) {
-                    const float tr = c.are + (br * c.bre - bi * c.bim);
-                    const float ti = c.aim + (br * c.bim + bi * c.bre);
-                    dr = br * tr - bi * ti;
-                    di = br * ti + bi * tr;
-                }
-                float2 fv[S];
-                load_row<S, E>(Fk, fv);
-                const float2 c2 = make_float2(cr, ci), ic2 = make_float2(-ci, cr);
-                const float2 d2 = make_float2(dr, di), id2 = make_float2(-di, dr);
+            if constexpr (S % 2 == 0) {
+                // packed pairs over two projections: (Ar_s, Ar_s+1) += (ReF) c_r - (ImF) c_i, ...
+                constexpr int Q = S / 2;
+                float2 ARp[Q], AIp[Q], DRp[Q], DIp[Q];
 #pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    const float2 fxx = make_float2(fv[s].x, fv[s].x), fyy = make_float2(fv[s].y, fv[s].y);
-                    A2[s] = __ffma2_rn(fyy, ic2, __ffma2_rn(fxx, c2, A2[s]));
-                    if constexpr (HV) D2[s] = __ffma2_rn(fyy, id2, __ffma2_rn(fxx, d2, D2[s]));
-                }
-            };
-            if constexpr (GR) {
+                for (int q = 0; q < Q; ++q) ARp[q] = AIp[q] = DRp[q] = DIp[q] = make_float2(0.f, 0.f);
+                auto visit = [&](int k, const float2* Fk, float m2v, float& br, float& bi) {
+                    const KConst c = kc[k];
+                    breit_wigner(c, m2v, br, bi);
+                    const float cr = c.gre * br - c.gim * bi, ci = c.gre * bi + c.gim * br;
+                    float dr = 0.f, di = 0.f;
+                    if constexpr (HV) {
+                        const float tr = c.are + (br * c.bre - bi * c.bim);
+                        const float ti = c.aim + (br * c.bim + bi * c.bre);
+                        dr = br * tr - bi * ti;
+                        di = br * ti + bi * tr;
+                    }
+                    float2 fv[S];
+                    load_row<S, E>(Fk, fv);  // fv[2q] = Re pair, fv[2q+1] = Im pair
+                    const float2 crr = make_float2(cr, cr), cii = make_float2(ci, ci), ncc = make_float2(-ci, -ci);
+                    const float2 drr = make_float2(dr, dr), dii = make_float2(di, di), ndd = make_float2(-di, -di);
 #pragma unroll
-                for (int j = 0; j < KPW; ++j) {
-                    if (j >= kcount) break;
-                    visit(h + j * H, Frow + j * H * S * E, Bk[j].x, Bk[j].y);
+                    for (int q = 0; q < Q; ++q) {
+                        const float2 R = fv[2 * q], Im = fv[2 * q + 1];
+                        ARp[q] = __ffma2_rn(Im, ncc, __ffma2_rn(R, crr, ARp[q]));
+                        AIp[q] = __ffma2_rn(Im, crr, __ffma2_rn(R, cii, AIp[q]));
+                        if constexpr (HV) {
+                            DRp[q] = __ffma2_rn(Im, ndd, __ffma2_rn(R, drr, DRp[q]));
+                            DIp[q] = __ffma2_rn(Im, drr, __ffma2_rn(R, dii, DIp[q]));
+                        }
+                    }
+                };
+                if constexpr (GR) {
+#pragma unroll
+                    for (int j = 0; j < KPW; ++j) {
+                        if (j >= kcount) break;
+                        visit(h + j * H, Frow + j * H * S * E, m2s[((chbits >> (2 * j)) & 3u) * E + e], Bk[j].x,
+                              Bk[j].y);
+                    }
+                } else {
+#pragma unroll 2
+                    for (int j = 0; j < kcount; ++j) {
+                        float br, bi;
+                        visit(h + j * H, Frow + j * H * S * E, m2s[kc[h + j * H].ch * E + e], br, bi);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    Ar[2 * q] = ARp[q].x;
+                    Ar[2 * q + 1] = ARp[q].y;
+                    Ai[2 * q] = AIp[q].x;
+                    Ai[2 * q + 1] = AIp[q].y;
+                    Dr[2 * q] = DRp[q].x;
+                    Dr[2 * q + 1] = DRp[q].y;
+                    Di[2 * q] = DIp[q].x;
+                    Di[2 * q + 1] = DIp[q].y;
                 }
             } else {
-                // the NLL-only pass is compiled once per W: the trip count is runtime
-#pragma unroll 2
-                for (int j = 0; j < kcount; ++j) {
-                    float br, bi;
-                    visit(h + j * H, Frow + j * H * S * E, br, bi);
-                }
-            }
-            float Ar[S], Ai[S], Dr[S], Di[S];
+                float2 A2[S], D2[S];
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                Ar[s] = A2[s].x;
-                Ai[s] = A2[s].y;
-                Dr[s] = D2[s].x;
-                Di[s] = D2[s].y;
+                for (int s = 0; s < S; ++s) A2[s] = D2[s] = make_float2(0.f, 0.f);
+                auto visit = [&](int k, const float2* Fk, float m2v, float& br, float& bi) {
+                    const KConst c = kc[k];
+                    breit_wigner(c, m2v, br, bi);
+                    const float cr = c.gre * br - c.gim * bi, ci = c.gre * bi + c.gim * br;
+                    float dr = 0.f, di = 0.f;
+                    if constexpr (HV) {
+                        const float tr = c.are + (br * c.bre - bi * c.bim);
+                        const float ti = c.aim + (br * c.bim + bi * c.bre);
+                        dr = br * tr - bi * ti;
+                        di = br * ti + bi * tr;
+                    }
+                    float2 fv[S];
+                    load_row<S, E>(Fk, fv);
+                    const float2 c2 = make_float2(cr, ci), ic2 = make_float2(-ci, cr);
+                    const float2 d2 = make_float2(dr, di), id2 = make_float2(-di, dr);
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+                        const float2 fxx = make_float2(fv[s].x, fv[s].x), fyy = make_float2(fv[s].y, fv[s].y);
+                        A2[s] = __ffma2_rn(fyy, ic2, __ffma2_rn(fxx, c2, A2[s]));
+                        if constexpr (HV) D2[s] = __ffma2_rn(fyy, id2, __ffma2_rn(fxx, d2, D2[s]));
+                    }
+                };
+                if constexpr (GR) {
+#pragma unroll
+                    for (int j = 0; j < KPW; ++j) {
+                        if (j >= kcount) break;
+                        visit(h + j * H, Frow + j * H * S * E, m2s[((chbits >> (2 * j)) & 3u) * E + e], Bk[j].x,
+                              Bk[j].y);
+                    }
+                } else {
+                    // the NLL-only pass is compiled once per W: the trip count is runtime
+#pragma unroll 2
+                    for (int j = 0; j < kcount; ++j) {
+                        float br, bi;
+                        visit(h + j * H, Frow + j * H * S * E, m2s[kc[h + j * H].ch * E + e], br, bi);
+                    }
+                }
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    Ar[s] = A2[s].x;
+                    Ai[s] = A2[s].y;
+                    Dr[s] = D2[s].x;
+                    Di[s] = D2[s].y;
+                }
             }
             // ---- the H lanes of the event combine their partial sums ----
 #pragma unroll
@@ -466,7 +543,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
             }
             Id *= 2.f;
             float wa = 0.f, wb = 0.f;  // (a, b) = (w/I, w Idot/I^2) for data, (1, 0) for MC
-            if (smp == 0) {
+            if constexpr (smp == 0) {
                 const float w = m2s[3 * E + e];
                 const bool good = I > 0.f && I < INFINITY;
                 if (valid && good) {
@@ -496,17 +573,38 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
             }
 
             if constexpr (GR) {
-                // ---- sweep 2 over the same resonances: Dh = sum_s conj(a A_s) F,
-                //      Dt = sum_s conj(a Adot_s - b A_s) F, then the five sums ----
+                // ---- sweep 2 (packed pairs over two projections): with a = (a Ar, a Ai) and
+                //      F = (ReF, ImF) pairs, Re Dh = sum (ReF a_r + ImF a_i), Im Dh = sum (ImF a_r - ReF a_i);
+                //      the same for Dt with (a Adot - b A) ----
+                constexpr int Q2 = S % 2 == 0 ? S / 2 : 1;
+                float2 aR[Q2], aI[Q2], naI[Q2], dR[Q2], dI[Q2], ndI[Q2];
+                if constexpr (S % 2 == 0) {
 #pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    const float ar = wa * Ar[s], ai = wa * Ai[s];
-                    if constexpr (HV) {
-                        Dr[s] = fmaf(wa, Dr[s], -wb * Ar[s]);
-                        Di[s] = fmaf(wa, Di[s], -wb * Ai[s]);
+                    for (int q = 0; q < Q2; ++q) {
+                        aR[q] = make_float2(wa * Ar[2 * q], wa * Ar[2 * q + 1]);
+                        aI[q] = make_float2(wa * Ai[2 * q], wa * Ai[2 * q + 1]);
+                        naI[q] = make_float2(-aI[q].x, -aI[q].y);
+                        if constexpr (HV) {
+                            dR[q] = make_float2(fmaf(wa, Dr[2 * q], -wb * Ar[2 * q]), fmaf(wa, Dr[2 * q + 1], -wb * Ar[2 * q + 1]));
+                            dI[q] = make_float2(fmaf(wa, Di[2 * q], -wb * Ai[2 * q]), fmaf(wa, Di[2 * q + 1], -wb * Ai[2 * q + 1]));
+                            ndI[q] = make_float2(-dI[q].x, -dI[q].y);
+                        }
                     }
-                    Ar[s] = ar;
-                    Ai[s] = ai;
+                }
+                float2 al[S], be[S], dl[S], de[S];
+                if constexpr (S % 2 != 0) {
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+                        const float ar = wa * Ar[s], ai = wa * Ai[s];
+                        al[s] = make_float2(ar, ai);
+                        be[s] = make_float2(-ai, ar);
+                        if constexpr (HV) {
+                            const float dr = fmaf(wa, Dr[s], -wb * Ar[s]);
+                            const float di = fmaf(wa, Di[s], -wb * Ai[s]);
+                            dl[s] = make_float2(dr, di);
+                            de[s] = make_float2(-di, dr);
+                        }
+                    }
                 }
 #pragma unroll
                 for (int j = 0; j < KPW; ++j) {
@@ -514,17 +612,31 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
                     const float br = Bk[j].x, bi = Bk[j].y;
                     float2 fv[S];
                     load_row<S, E>(Frow + j * H * S * E, fv);
-                    float hr = 0.f, hi = 0.f, tr = 0.f, ti = 0.f;
+                    float2 X = make_float2(0.f, 0.f), Y = X, XD = X, YD = X;
+                    if constexpr (S % 2 == 0) {
 #pragma unroll
-                    for (int s = 0; s < S; ++s) {
-                        const float2 f = fv[s];
-                        hr = fmaf(Ar[s], f.x, fmaf(Ai[s], f.y, hr));
-                        hi = fmaf(Ar[s], f.y, fmaf(-Ai[s], f.x, hi));
-                        if constexpr (HV) {
-                            tr = fmaf(Dr[s], f.x, fmaf(Di[s], f.y, tr));
-                            ti = fmaf(Dr[s], f.y, fmaf(-Di[s], f.x, ti));
+                        for (int q = 0; q < Q2; ++q) {
+                            const float2 R = fv[2 * q], Im = fv[2 * q + 1];
+                            X = __ffma2_rn(Im, aI[q], __ffma2_rn(R, aR[q], X));
+                            Y = __ffma2_rn(R, naI[q], __ffma2_rn(Im, aR[q], Y));
+                            if constexpr (HV) {
+                                XD = __ffma2_rn(Im, dI[q], __ffma2_rn(R, dR[q], XD));
+                                YD = __ffma2_rn(R, ndI[q], __ffma2_rn(Im, dR[q], YD));
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int s = 0; s < S; ++s) {
+                            X = __ffma2_rn(fv[s], al[s], X);
+                            Y = __ffma2_rn(fv[s], be[s], Y);
+                            if constexpr (HV) {
+                                XD = __ffma2_rn(fv[s], dl[s], XD);
+                                YD = __ffma2_rn(fv[s], de[s], YD);
+                            }
                         }
                     }
+                    const float hr = X.x + X.y, hi = Y.x + Y.y;
+                    const float tr = XD.x + XD.y, ti = YD.x + YD.y;
                     const float b2r = fmaf(br, br, -bi * bi), b2i = 2.f * br * bi;
                     acc[j][0] = fmaf(hr, br, fmaf(-hi, bi, acc[j][0]));
                     acc[j][1] = fmaf(hr, bi, fmaf(hi, br, acc[j][1]));
@@ -567,7 +679,15 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
             st = 0;
             ph ^= 1u;
         }
-    }
+    };
+    // the block's tiles are t = blockIdx.x + i G, i = 0, 1, ...: data tiles first, then MC tiles
+    long long t = blockIdx.x, i = 0;
+    for (const long long t_end = min((long long)a.ntiles[0], T); t < t_end; t += G, ++i)
+        tile(std::integral_constant<int, 0>{}, t, i);
+    fold();
+    write_set(0);
+    win = 0;
+    for (; t < T; t += G, ++i) tile(std::integral_constant<int, 1>{}, t, i);
     __syncthreads();
 
     if (s_abort) {
@@ -584,17 +704,8 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
         return;
     }
 
-    if (cur_set >= 0) {
-        fold();
-        write_set(cur_set);
-        set_written[cur_set] = true;
-    }
-    for (int s = 0; s < 2; ++s) {
-        if (!set_written[s]) {
-            double* rec = a.block_rec + (size_t)blockIdx.x * a.rec_len + (size_t)s * (K * kNV + kNScal);
-            for (int i = tid; i < K * kNV + kNScal; i += NT) rec[i] = 0.0;
-        }
-    }
+    fold();
+    write_set(1);
 
     // ---- two-level last-block-done reduction (fixed order) ----
     __threadfence();  // every thread's record writes are visible device-wide ...

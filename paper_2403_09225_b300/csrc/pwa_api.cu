@@ -58,7 +58,7 @@ __global__ void layout_kernel(const float2* __restrict__ F, const float* __restr
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total_F + total_x;
          i += (long long)gridDim.x * blockDim.x) {
         if (i < total_F) {
-            // i enumerates (tile, k, s, p); the destination follows f_slot
+            // i enumerates (tile, k, s, p); the destination follows f_re
             const long long t = i / per_tile_F;
             const long long r = i % per_tile_F;
             const int k = (int)(r / ((long long)S * E));
@@ -68,7 +68,10 @@ __global__ void layout_kernel(const float2* __restrict__ F, const float* __restr
             const long long e = t * E + el;
             float2 val = make_float2(0.f, 0.f);
             if (e < n) val = F[(e * K + k) * S + s];
-            reinterpret_cast<float2*>(tiles + (size_t)t * tile_bytes)[pwa::f_slot(k, s, p, S, E)] = val;
+            float* Ft = reinterpret_cast<float*>(tiles + (size_t)t * tile_bytes);
+            const int o = pwa::f_re(k, s, p, S, E);
+            Ft[o] = val.x;
+            Ft[o + pwa::f_im_off(S)] = val.y;
         } else {
             const long long j = i - total_F;
             const long long t = j / extra;
@@ -112,7 +115,9 @@ __global__ void intensity_kernel(pwa::PassArgs a, int smp, int S, float* __restr
                 const float cr = c.gre * br - c.gim * bi, ci = c.gre * bi + c.gim * br;
                 int p = el + c.shift;
                 p = p >= E ? p - E : p;
-                const float2 f = Fs[pwa::f_slot(k, s, p, S, E)];
+                const int o = pwa::f_re(k, s, p, S, E);
+                const float2 f = make_float2(reinterpret_cast<const float*>(Fs)[o],
+                                             reinterpret_cast<const float*>(Fs)[o + pwa::f_im_off(S)]);
                 Ar = fmaf(cr, f.x, fmaf(-ci, f.y, Ar));
                 Ai = fmaf(cr, f.y, fmaf(ci, f.x, Ai));
             }
@@ -163,7 +168,7 @@ KernelFn pick_kernel(int mode, int S, int W, int kpw)
 
 size_t smem_bytes(const Tiling& t, int K, int S)
 {
-    // stages | KConst[K] | per-warp FP64 sums [W][10 K + 2] | stage counters[4] | issued[4] | mbarriers[NST]
+    // stages | KConst[K] | per-warp (hi, lo) FP32 sums [W][10 K + 2] | stage counters[4] | issued[4] | mbarriers[NST]
     (void)S;
     return (size_t)t.NST * t.stage_bytes + (size_t)K * sizeof(pwa::KConst) +
            (size_t)t.W * (K * pwa::kNV + 2) * 8 + 16 + 32 + (size_t)t.NST * 8;
