@@ -414,7 +414,10 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
             // ---- sweep 1: BW, couplings, coherent sums over this lane's resonances ----
             // packed FP32 pairs: A_s += Re(F) c + Im(F) (i c), two paired FMAs per
             // complex product (and the same for Adot with cdot)
-            float Ar[S], Ai[S], Dr[S], Di[S];
+            // PA, PD: the lane's partial sums of A_s and Adot_s as S packed pairs.  Even S:
+            // PA[2q] = (Re A_2q, Re A_2q+1), PA[2q+1] = (Im A_2q, Im A_2q+1); odd S:
+            // PA[s] = (Re A_s, Im A_s).  Either way I = sum of the squares of all entries.
+            float2 PA[S], PD[S];
             float2 Bk[GR ? KPW : 1];
             if constexpr (S % 2 == 0) {
                 // packed pairs over two projections: (Ar_s, Ar_s+1) += (ReF) c_r - (ImF) c_i, ...
@@ -464,14 +467,10 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
                 }
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
-                    Ar[2 * q] = ARp[q].x;
-                    Ar[2 * q + 1] = ARp[q].y;
-                    Ai[2 * q] = AIp[q].x;
-                    Ai[2 * q + 1] = AIp[q].y;
-                    Dr[2 * q] = DRp[q].x;
-                    Dr[2 * q + 1] = DRp[q].y;
-                    Di[2 * q] = DIp[q].x;
-                    Di[2 * q + 1] = DIp[q].y;
+                    PA[2 * q] = ARp[q];
+                    PA[2 * q + 1] = AIp[q];
+                    PD[2 * q] = DRp[q];
+                    PD[2 * q + 1] = DIp[q];
                 }
             } else {
                 float2 A2[S], D2[S];
@@ -516,32 +515,31 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
                 }
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
-                    Ar[s] = A2[s].x;
-                    Ai[s] = A2[s].y;
-                    Dr[s] = D2[s].x;
-                    Di[s] = D2[s].y;
+                    PA[s] = A2[s];
+                    PD[s] = D2[s];
                 }
             }
             // ---- the H lanes of the event combine their partial sums ----
 #pragma unroll
             for (int off = EV; off < 32; off <<= 1) {
 #pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    Ar[s] += __shfl_xor_sync(0xffffffffu, Ar[s], off);
-                    Ai[s] += __shfl_xor_sync(0xffffffffu, Ai[s], off);
-                    if constexpr (HV) {
-                        Dr[s] += __shfl_xor_sync(0xffffffffu, Dr[s], off);
-                        Di[s] += __shfl_xor_sync(0xffffffffu, Di[s], off);
-                    }
+                for (int i = 0; i < S; ++i) {
+                    PA[i] = __fadd2_rn(PA[i], make_float2(__shfl_xor_sync(0xffffffffu, PA[i].x, off),
+                                                          __shfl_xor_sync(0xffffffffu, PA[i].y, off)));
+                    if constexpr (HV)
+                        PD[i] = __fadd2_rn(PD[i], make_float2(__shfl_xor_sync(0xffffffffu, PD[i].x, off),
+                                                              __shfl_xor_sync(0xffffffffu, PD[i].y, off)));
                 }
             }
-            float I = 0.f, Id = 0.f;
+            // I = sum_s |A_s|^2, Idot = 2 Re sum_s conj(A_s) Adot_s
+            float2 I2 = make_float2(0.f, 0.f), Id2 = I2;
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                I = fmaf(Ar[s], Ar[s], fmaf(Ai[s], Ai[s], I));
-                if constexpr (HV) Id = fmaf(Ar[s], Dr[s], fmaf(Ai[s], Di[s], Id));
+            for (int i = 0; i < S; ++i) {
+                I2 = __ffma2_rn(PA[i], PA[i], I2);
+                if constexpr (HV) Id2 = __ffma2_rn(PA[i], PD[i], Id2);
             }
-            Id *= 2.f;
+            const float I = I2.x + I2.y;
+            const float Id = 2.f * (Id2.x + Id2.y);
             float wa = 0.f, wb = 0.f;  // (a, b) = (w/I, w Idot/I^2) for data, (1, 0) for MC
             if constexpr (smp == 0) {
                 const float w = m2s[3 * E + e];
@@ -578,31 +576,33 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
                 //      the same for Dt with (a Adot - b A) ----
                 constexpr int Q2 = S % 2 == 0 ? S / 2 : 1;
                 float2 aR[Q2], aI[Q2], naI[Q2], dR[Q2], dI[Q2], ndI[Q2];
+                float2 al[S], be[S], dl[S], de[S];
+                const float2 waa = make_float2(wa, wa), nwaa = make_float2(-wa, -wa);
+                const float2 wbb = make_float2(wb, wb), nwbb = make_float2(-wb, -wb);
                 if constexpr (S % 2 == 0) {
 #pragma unroll
                     for (int q = 0; q < Q2; ++q) {
-                        aR[q] = make_float2(wa * Ar[2 * q], wa * Ar[2 * q + 1]);
-                        aI[q] = make_float2(wa * Ai[2 * q], wa * Ai[2 * q + 1]);
-                        naI[q] = make_float2(-aI[q].x, -aI[q].y);
-                        if constexpr (HV) {
-                            dR[q] = make_float2(fmaf(wa, Dr[2 * q], -wb * Ar[2 * q]), fmaf(wa, Dr[2 * q + 1], -wb * Ar[2 * q + 1]));
-                            dI[q] = make_float2(fmaf(wa, Di[2 * q], -wb * Ai[2 * q]), fmaf(wa, Di[2 * q + 1], -wb * Ai[2 * q + 1]));
-                            ndI[q] = make_float2(-dI[q].x, -dI[q].y);
+                        aR[q] = __fmul2_rn(waa, PA[2 * q]);
+                        aI[q] = __fmul2_rn(waa, PA[2 * q + 1]);
+                        naI[q] = __fmul2_rn(nwaa, PA[2 * q + 1]);
+                        if constexpr (HV && smp == 0) {
+                            dR[q] = __ffma2_rn(waa, PD[2 * q], __fmul2_rn(nwbb, PA[2 * q]));
+                            dI[q] = __ffma2_rn(waa, PD[2 * q + 1], __fmul2_rn(nwbb, PA[2 * q + 1]));
+                            ndI[q] = __ffma2_rn(nwaa, PD[2 * q + 1], __fmul2_rn(wbb, PA[2 * q + 1]));
+                        } else if constexpr (HV) {  // MC events: b = 0
+                            dR[q] = __fmul2_rn(waa, PD[2 * q]);
+                            dI[q] = __fmul2_rn(waa, PD[2 * q + 1]);
+                            ndI[q] = __fmul2_rn(nwaa, PD[2 * q + 1]);
                         }
                     }
-                }
-                float2 al[S], be[S], dl[S], de[S];
-                if constexpr (S % 2 != 0) {
+                } else {
 #pragma unroll
                     for (int s = 0; s < S; ++s) {
-                        const float ar = wa * Ar[s], ai = wa * Ai[s];
-                        al[s] = make_float2(ar, ai);
-                        be[s] = make_float2(-ai, ar);
+                        al[s] = __fmul2_rn(waa, PA[s]);
+                        be[s] = make_float2(-al[s].y, al[s].x);
                         if constexpr (HV) {
-                            const float dr = fmaf(wa, Dr[s], -wb * Ar[s]);
-                            const float di = fmaf(wa, Di[s], -wb * Ai[s]);
-                            dl[s] = make_float2(dr, di);
-                            de[s] = make_float2(-di, dr);
+                            dl[s] = __ffma2_rn(waa, PD[s], __fmul2_rn(nwbb, PA[s]));
+                            de[s] = make_float2(-dl[s].y, dl[s].x);
                         }
                     }
                 }
