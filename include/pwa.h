@@ -104,8 +104,11 @@ typedef enum {
     PWA_FIT_MAXITER = 2,     /* outer iteration limit reached                      */
     PWA_FIT_TIME_LIMIT = 3,  /* time_limit_s reached (early stopping)              */
     PWA_FIT_LINESEARCH = 4,  /* no step satisfied the Wolfe conditions             */
-    PWA_FIT_PRECISION = 5    /* converged: predicted decrease below the NLL's
+    PWA_FIT_PRECISION = 5,   /* converged: predicted decrease below the NLL's
                                 resolution, no further step can be resolved        */
+    PWA_FIT_ERROR = 6        /* stopped on an error (e.g. a non-finite NLL at its
+                                start point); only pwa_newton_cg_fit_batch reports
+                                it per fit, pwa_newton_cg_fit returns the error    */
 } pwa_fit_status;
 
 typedef struct {
@@ -178,6 +181,27 @@ pwa_status pwa_eval_device(pwa_handle* h, const double* d_theta, const double* d
 pwa_status pwa_eval_device_noalloc(pwa_handle* h, const double* d_theta, const double* d_v,
                                    double* d_out, int want_grad, int want_hv);
 
+/* Batched fused pass: B parameter vectors over the same events in one launch
+ * (multi-start and toy fits evaluate many parameter points of one model; the
+ * paper runs its 300 random starts one after another, Sec. 4).  Each vector's
+ * result is the same function value, gradient and H v as pwa_eval at that
+ * vector (the event sums are split over a different block grid, so the FP32
+ * partial sums round differently: agreement to the pass's own accuracy, not
+ * bit for bit).  theta: host [B][P] row-major; v: host [B][P] or NULL; nll:
+ * host [B]; grad, hv: host [B][P] or NULL (hv needs v).  B >= 1.  Grows the
+ * handle's batch scratch when B exceeds what earlier calls used.
+ * Errors: PWA_EINVAL, PWA_ENOMEM, PWA_ECUDA, PWA_ENONFINITE, PWA_ETIMEOUT. */
+pwa_status pwa_eval_batch(pwa_handle* h, int B, const double* theta, const double* v,
+                          double* nll, double* grad, double* hv);
+
+/* Asynchronous batched pass on device buffers, enqueued on the handle's
+ * stream: d_theta [B][P], d_v [B][P] (NULL when hv is not wanted), d_out
+ * [B][1 + 2P] (row b receives (NLL, grad[P], hv[P]) of vector b, with the
+ * same want_grad / want_hv rules as pwa_eval_device).  May allocate batch
+ * scratch (and then synchronises the stream) when B or the grid grows. */
+pwa_status pwa_eval_batch_device(pwa_handle* h, int B, const double* d_theta, const double* d_v,
+                                 double* d_out, int want_grad, int want_hv);
+
 /* Wait for the handle's stream and report device-side errors of earlier
  * asynchronous calls. */
 pwa_status pwa_sync(pwa_handle* h);
@@ -194,6 +218,23 @@ pwa_status pwa_event_intensity(pwa_handle* h, int sample, const double* theta,
  * which), PWA_ENOCONV when it stopped otherwise, or an error status. */
 pwa_status pwa_newton_cg_fit(pwa_handle* h, const double* theta0, const pwa_fit_opts* opts,
                              double* theta_out, pwa_fit_result* result);
+
+/* B Newton-CG fits of the same model (multi-start or repeated fits), run in
+ * lockstep so that each round of likelihood evaluations -- one per unfinished
+ * fit, f and g for the line search or H v for the inner CG -- is one batched
+ * launch (pwa_eval_batch_device); the paper's multi-start runs its starts one
+ * after another (Sec. 4).  Each fit follows the same iteration as
+ * pwa_newton_cg_fit, with the inner CG's FP64 vector arithmetic on the host
+ * instead of on the device (so the two may differ in the last bits and, on a
+ * flat or multimodal surface, in where they stop).  theta0, theta_out: host
+ * [B][P] (may alias); results: host [B] or NULL; opts apply to every fit (the
+ * time limit to each fit's wall time since the call began).  Returns PWA_OK
+ * when every fit converged or hit its time limit, PWA_ENOCONV when some fit
+ * stopped otherwise (its result says why, PWA_FIT_ERROR for a fit whose start
+ * point has a non-finite NLL), or an error status that stopped all fits. */
+pwa_status pwa_newton_cg_fit_batch(pwa_handle* h, int B, const double* theta0,
+                                   const pwa_fit_opts* opts, double* theta_out,
+                                   pwa_fit_result* results);
 
 /* Default options: xtol 1e-8, gtol 0, maxiter 0 (= 200 P), cg_maxiter 0
  * (= 20 P), no time limit. */

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpwa.so")
 PWA_OK, PWA_EINVAL, PWA_ENOMEM, PWA_ECUDA, PWA_ENONFINITE, PWA_ENOCONV, PWA_ETIMEOUT = range(7)
 STATUS_NAMES = {0: "PWA_OK", 1: "PWA_EINVAL", 2: "PWA_ENOMEM", 3: "PWA_ECUDA", 4: "PWA_ENONFINITE",
                 5: "PWA_ENOCONV", 6: "PWA_ETIMEOUT"}
-FIT_STATUS_NAMES = ("xtol", "gtol", "maxiter", "time_limit", "linesearch_failed", "precision_limit")
+FIT_STATUS_NAMES = ("xtol", "gtol", "maxiter", "time_limit", "linesearch_failed", "precision_limit", "error")
 
 
 class pwa_events(ctypes.Structure):
@@ -53,7 +53,8 @@ class PwaError(RuntimeError):
 
 #: every symbol include/pwa.h declares
 EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "pwa_grad", "pwa_hvp",
-           "pwa_eval", "pwa_eval_device", "pwa_eval_device_noalloc", "pwa_sync", "pwa_event_intensity", "pwa_newton_cg_fit",
+           "pwa_eval", "pwa_eval_device", "pwa_eval_device_noalloc", "pwa_eval_batch", "pwa_eval_batch_device",
+           "pwa_sync", "pwa_event_intensity", "pwa_newton_cg_fit", "pwa_newton_cg_fit_batch",
            "pwa_fit_opts_default", "pwa_set_stream", "pwa_set_tiling", "pwa_get_tiling",
            "pwa_selftest_bounded_wait", "pwa_last_error", "pwa_destroy")
 
@@ -76,9 +77,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pwa_eval": (st, [H, dp, dp, dp, dp, dp]),
         "pwa_eval_device": (st, [H, vp, vp, vp, i, i]),
         "pwa_eval_device_noalloc": (st, [H, vp, vp, vp, i, i]),
+        "pwa_eval_batch": (st, [H, i, dp, dp, dp, dp, dp]),
+        "pwa_eval_batch_device": (st, [H, i, vp, vp, vp, i, i]),
         "pwa_sync": (st, [H]),
         "pwa_event_intensity": (st, [H, i, dp, vp, i]),
         "pwa_newton_cg_fit": (st, [H, dp, ctypes.POINTER(pwa_fit_opts), dp, ctypes.POINTER(pwa_fit_result)]),
+        "pwa_newton_cg_fit_batch": (st, [H, i, dp, ctypes.POINTER(pwa_fit_opts), dp, ctypes.POINTER(pwa_fit_result)]),
         "pwa_fit_opts_default": (None, [ctypes.POINTER(pwa_fit_opts)]),
         "pwa_set_stream": (st, [H, vp]),
         "pwa_set_tiling": (st, [H, i, i, i]),
@@ -222,6 +226,27 @@ class Likelihood:
         self._check(lib().pwa_eval(self._h, _dptr(th), _dptr(vv), ctypes.byref(f), _dptr(g), _dptr(hv)))
         return f.value, g, hv
 
+    def eval_batch(self, thetas, vs=None):
+        """(NLL [B], grad [B, P], H v [B, P] or None) for B parameter vectors
+        (rows of thetas) in one batched pass."""
+        th = _f64(thetas).reshape(-1, self.P)
+        B = th.shape[0]
+        f = np.empty(B)
+        g = np.empty((B, self.P))
+        if vs is None:
+            self._check(lib().pwa_eval_batch(self._h, B, _dptr(th), None, _dptr(f), _dptr(g), None))
+            return f, g, None
+        vv = _f64(vs).reshape(B, self.P)
+        hv = np.empty((B, self.P))
+        self._check(lib().pwa_eval_batch(self._h, B, _dptr(th), _dptr(vv), _dptr(f), _dptr(g), _dptr(hv)))
+        return f, g, hv
+
+    def eval_batch_device(self, B: int, d_theta: int, d_v: int, d_out: int, want_grad: bool = True,
+                          want_hv: bool = True):
+        """Asynchronous batched pass on device pointers (theta [B][P], v [B][P], out [B][1 + 2P])."""
+        self._check(lib().pwa_eval_batch_device(self._h, int(B), ctypes.c_void_p(d_theta), ctypes.c_void_p(d_v),
+                                                ctypes.c_void_p(d_out), int(want_grad), int(want_hv)))
+
     def eval_device(self, d_theta: int, d_v: int, d_out: int, want_grad: bool = True, want_hv: bool = True):
         """Asynchronous fused pass on device pointers (theta [P], v [P], out [1 + 2P])."""
         self._check(lib().pwa_eval_device(self._h, ctypes.c_void_p(d_theta), ctypes.c_void_p(d_v),
@@ -268,6 +293,22 @@ class Likelihood:
         return out, {"nll": res.nll, "grad_max": res.grad_max, "iters": res.iters, "n_hvp": res.n_hvp,
                      "n_fev": res.n_fev, "status": FIT_STATUS_NAMES[res.status], "elapsed_s": res.elapsed_s,
                      "converged": st == PWA_OK}
+
+    def fit_batch(self, thetas0, xtol: float = 1e-8, gtol: float = 0.0, maxiter: int = 0, cg_maxiter: int = 0,
+                  time_limit_s: float = 0.0):
+        """B fits (rows of thetas0) in lockstep with batched passes; returns
+        (theta [B, P], list of per-fit info dicts, converged-or-time-limit for all)."""
+        th = _f64(thetas0).reshape(-1, self.P)
+        B = th.shape[0]
+        out = np.empty((B, self.P))
+        opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s)
+        res = (pwa_fit_result * B)()
+        st = lib().pwa_newton_cg_fit_batch(self._h, B, _dptr(th), ctypes.byref(opts), _dptr(out), res)
+        if st not in (PWA_OK, PWA_ENOCONV):
+            self._check(st)
+        infos = [{"nll": r.nll, "grad_max": r.grad_max, "iters": r.iters, "n_hvp": r.n_hvp, "n_fev": r.n_fev,
+                  "status": FIT_STATUS_NAMES[r.status], "elapsed_s": r.elapsed_s} for r in res]
+        return out, infos, st == PWA_OK
 
     # -- tiling --
     def set_tiling(self, warps: int, stages: int = 2, blocks_per_sm: int = 0):

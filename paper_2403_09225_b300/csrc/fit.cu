@@ -16,8 +16,11 @@
 //    (the "approximate Wolfe" idea of Hager & Zhang, 2005);
 //  * a failed line search whose predicted decrease |g.p| is below
 //    1e-7 (1 + |f|) ends the fit as converged at the precision limit.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <coroutine>
+#include <exception>
 #include <cstring>
 #include <vector>
 
@@ -228,17 +231,6 @@ struct DeviceCG {
     }
 };
 
-struct Evaluator {
-    pwa_handle* h;
-    int n_fev = 0, n_hvp = 0;
-
-    pwa_status fg(const std::vector<double>& x, double& f, std::vector<double>& g)
-    {
-        ++n_fev;
-        return pwa_eval(h, x.data(), nullptr, &f, g.data(), nullptr);
-    }
-};
-
 double dot(const std::vector<double>& a, const std::vector<double>& b)
 {
     double s = 0.0;
@@ -247,7 +239,7 @@ double dot(const std::vector<double>& a, const std::vector<double>& b)
 }
 
 struct LinePoint {
-    double a, f, df;
+    double a = 0.0, f = 0.0, df = 0.0;
     std::vector<double> x, g;
 };
 
@@ -263,6 +255,331 @@ bool cubic_min(double a, double fa, double dfa, double b, double fb, double dfb,
     out = b - (b - a) * (dfb + d2 - d1) / den;
     return std::isfinite(out);
 }
+
+// ---------------------------------------------------------------------------
+// The Newton-CG iteration as a coroutine.  It suspends whenever it needs the
+// likelihood -- f and g at a point (FG), H v at a point (HV), or a whole inner
+// CG solve (CG) -- and an executor serves the request and resumes it: one fit
+// at a time with the device-side CG (pwa_newton_cg_fit), or many fits whose
+// FG / HV requests share one batched launch (pwa_newton_cg_fit_batch).  The
+// arithmetic of the iteration is written once, here.
+// ---------------------------------------------------------------------------
+
+enum class Req { None, FG, HV, CG };
+
+struct FitState {
+    int P = 0;
+    pwa_fit_opts o{};
+    int maxiter = 0, cg_maxiter = 0;
+    bool device_cg = false;  // CG requests (device graph) instead of HV requests
+    std::chrono::steady_clock::time_point t_start;
+    std::vector<double> x, g, p;
+    double f = 0.0;
+    // the request posted at the last suspension, and its outcome
+    Req req = Req::None;
+    const double* rx = nullptr;  // FG, HV: the point
+    const double* rv = nullptr;  // HV: the direction
+    double* rf = nullptr;        // FG: f
+    double* rg = nullptr;        // FG: g
+    double* rhv = nullptr;       // HV: H v
+    double cg_eps = 0.0;         // CG: solve H p = -g at (x, g) to |r| < cg_eps into p
+    pwa_status req_status = PWA_OK;
+    // outcome of the fit
+    pwa_status error = PWA_OK;  // an evaluation failed (the fit stopped there)
+    int status = PWA_FIT_MAXITER, iters = 0, n_fev = 0, n_hvp = 0;
+    double elapsed = 0.0;
+
+    double since_start() const
+    {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    }
+};
+
+struct FitTask {
+    struct promise_type {
+        FitTask get_return_object() { return FitTask{std::coroutine_handle<promise_type>::from_promise(*this)}; }
+        std::suspend_always initial_suspend() noexcept { return {}; }
+        std::suspend_always final_suspend() noexcept { return {}; }
+        void return_void() {}
+        // a host exception (e.g. bad_alloc) ends the coroutine; the executor reports it
+        void unhandled_exception() { failed = true; }
+        bool failed = false;
+    };
+    std::coroutine_handle<promise_type> h;
+    bool failed() const { return h.promise().failed; }
+    explicit FitTask(std::coroutine_handle<promise_type> hh) : h(hh) {}
+    FitTask(FitTask&& o) noexcept : h(o.h) { o.h = nullptr; }
+    FitTask(const FitTask&) = delete;
+    ~FitTask()
+    {
+        if (h) h.destroy();
+    }
+};
+
+// suspension point: the request is already stored in the FitState
+struct Suspend {
+    bool await_ready() const noexcept { return false; }
+    void await_suspend(std::coroutine_handle<>) const noexcept {}
+    void await_resume() const noexcept {}
+};
+
+FitTask newton_cg(FitState& s)
+{
+    const int n = s.P;
+    const double c1 = 1e-4, c2 = 0.9;
+    s.req = Req::FG;
+    s.rx = s.x.data();
+    s.rf = &s.f;
+    s.rg = s.g.data();
+    co_await Suspend{};
+    if (s.req_status != PWA_OK) {
+        s.error = s.req_status;
+        co_return;
+    }
+    s.p.assign(n, 0.0);
+    std::vector<double> z, r, d, Hd;
+    int k = 0;
+    while (k < s.maxiter) {
+        double gmax = 0.0;
+        for (double v : s.g) gmax = std::max(gmax, std::fabs(v));
+        if (s.o.gtol > 0 && gmax <= s.o.gtol) {
+            s.status = PWA_FIT_GTOL;
+            break;
+        }
+        // ---- inner CG on H p = -g (N&W Algorithm 7.1) ----
+        const double gnorm = std::sqrt(dot(s.g, s.g));
+        const double eps = std::min(0.5, std::sqrt(gnorm)) * gnorm;
+        if (s.device_cg) {
+            s.req = Req::CG;
+            s.cg_eps = eps;
+            co_await Suspend{};
+            if (s.req_status != PWA_OK) {
+                s.error = s.req_status;
+                co_return;
+            }
+        } else {
+            z.assign(n, 0.0);
+            r = s.g;
+            d.resize(n);
+            Hd.resize(n);
+            for (int i = 0; i < n; ++i) d[i] = -r[i];
+            double rr = dot(r, r);
+            for (int j = 0;; ++j) {
+                s.req = Req::HV;
+                s.rx = s.x.data();
+                s.rv = d.data();
+                s.rhv = Hd.data();
+                co_await Suspend{};
+                if (s.req_status != PWA_OK) {
+                    s.error = s.req_status;
+                    co_return;
+                }
+                ++s.n_hvp;
+                const double curv = dot(d, Hd);
+                if (!(curv > 0.0)) {  // negative curvature: steepest descent first, else the iterate
+                    if (j == 0)
+                        for (int i = 0; i < n; ++i) s.p[i] = -s.g[i];
+                    else
+                        s.p = z;
+                    break;
+                }
+                const double alpha = rr / curv;
+                double rr_new = 0.0;
+                for (int i = 0; i < n; ++i) {
+                    z[i] += alpha * d[i];
+                    r[i] += alpha * Hd[i];
+                    rr_new += r[i] * r[i];
+                }
+                if (std::sqrt(rr_new) < eps || j + 1 >= s.cg_maxiter) {
+                    s.p = z;
+                    break;
+                }
+                const double beta = rr_new / rr;
+                for (int i = 0; i < n; ++i) d[i] = -r[i] + beta * d[i];
+                rr = rr_new;
+            }
+        }
+        ++k;
+        double pmean = 0.0;
+        for (double v : s.p) pmean += std::fabs(v);
+        pmean /= std::max(n, 1);
+        if (pmean <= s.o.xtol) {
+            s.status = PWA_FIT_XTOL;
+            break;
+        }
+        double df0 = dot(s.g, s.p);
+        if (!(df0 < 0)) {
+            for (int i = 0; i < n; ++i) s.p[i] = -s.g[i];
+            df0 = dot(s.g, s.p);
+        }
+        // ---- strong-Wolfe line search (N&W Algorithms 3.5 / 3.6) ----
+        // bracketing from a = 1 (doubling), then zoom with safeguarded cubic
+        // interpolation; one trial point per suspension
+        const double f0 = s.f;
+        const double eps_f = 1e-7 * std::fabs(f0);
+        auto armijo_fails = [&](const LinePoint& lp) { return !(lp.f <= f0 + c1 * lp.a * df0 + eps_f); };
+        LinePoint prev, cur, lo, hi, found;
+        prev.a = 0.0;
+        prev.f = f0;
+        prev.df = df0;
+        prev.x = s.x;
+        prev.g = s.g;
+        bool ok = false, zooming = false;
+        int bracket_it = 0, zoom_it = 0;
+        double a = 1.0;
+        while (true) {
+            if (zooming) {
+                if (zoom_it >= 30) break;
+                const double left = std::min(lo.a, hi.a), right = std::max(lo.a, hi.a), width = right - left;
+                if (!std::isfinite(hi.f) || !cubic_min(lo.a, lo.f, lo.df, hi.a, hi.f, hi.df, a) ||
+                    a < left + 0.1 * width || a > right - 0.1 * width)
+                    a = 0.5 * (lo.a + hi.a);
+            } else if (bracket_it >= 30) {
+                break;
+            }
+            // trial point x + a p
+            cur.a = a;
+            cur.x.resize(n);
+            cur.g.resize(n);
+            for (int i = 0; i < n; ++i) cur.x[i] = s.x[i] + a * s.p[i];
+            s.req = Req::FG;
+            s.rx = cur.x.data();
+            s.rf = &cur.f;
+            s.rg = cur.g.data();
+            co_await Suspend{};
+            if (s.req_status == PWA_ENONFINITE) {  // the trial point left the region where I > 0
+                cur.f = INFINITY;
+                cur.df = 0.0;
+            } else if (s.req_status != PWA_OK) {
+                s.error = s.req_status;
+                co_return;
+            } else {
+                cur.df = dot(cur.g, s.p);
+            }
+            if (!zooming) {
+                const int it = bracket_it++;
+                if (!std::isfinite(cur.f)) {
+                    a = 0.5 * (prev.a + a);
+                    continue;
+                }
+                if (armijo_fails(cur) || (it > 0 && cur.f >= prev.f + eps_f)) {
+                    zooming = true;
+                    lo = prev;
+                    hi = cur;
+                    continue;
+                }
+                if (std::fabs(cur.df) <= -c2 * df0) {
+                    found = cur;
+                    ok = true;
+                    break;
+                }
+                if (cur.df >= 0) {
+                    zooming = true;
+                    lo = cur;
+                    hi = prev;
+                    continue;
+                }
+                prev = cur;
+                a = std::min(2.0 * a, 1e3);
+            } else {
+                ++zoom_it;
+                if (armijo_fails(cur) || cur.f >= lo.f + eps_f) {
+                    hi = cur;
+                } else {
+                    if (std::fabs(cur.df) <= -c2 * df0) {
+                        found = cur;
+                        ok = true;
+                        break;
+                    }
+                    if (cur.df * (hi.a - lo.a) >= 0) hi = lo;
+                    lo = cur;
+                }
+                if (std::fabs(hi.a - lo.a) < 1e-14 * std::max(1.0, std::fabs(lo.a))) break;
+            }
+        }
+        if (!ok) {
+            s.status = std::fabs(df0) <= 1e-7 * (1.0 + std::fabs(f0)) ? PWA_FIT_PRECISION : PWA_FIT_LINESEARCH;
+            break;
+        }
+        double smean = 0.0;
+        for (int i = 0; i < n; ++i) smean += std::fabs(found.x[i] - s.x[i]);
+        smean /= std::max(n, 1);
+        s.x = found.x;
+        s.f = found.f;
+        s.g = found.g;
+        if (smean <= s.o.xtol) {
+            s.status = PWA_FIT_XTOL;
+            break;
+        }
+        if (s.o.time_limit_s > 0 && s.since_start() > s.o.time_limit_s) {
+            s.status = PWA_FIT_TIME_LIMIT;
+            break;
+        }
+    }
+    s.iters = k;
+}
+
+void init_state(FitState& s, const pwa_handle* h, const double* theta0, const pwa_fit_opts* opts_in)
+{
+    const int n = h->P;
+    s.P = n;
+    pwa_fit_opts_default(&s.o);
+    if (opts_in) s.o = *opts_in;
+    s.maxiter = s.o.maxiter > 0 ? s.o.maxiter : 200 * n;
+    s.cg_maxiter = s.o.cg_maxiter > 0 ? s.o.cg_maxiter : 20 * n;
+    s.x.assign(theta0, theta0 + n);
+    s.g.assign(n, 0.0);
+    s.t_start = std::chrono::steady_clock::now();
+}
+
+void fill_result(const FitState& s, pwa_fit_result* r)
+{
+    if (!r) return;
+    double gmax = 0.0;
+    for (double v : s.g) gmax = std::max(gmax, std::fabs(v));
+    r->nll = s.f;
+    r->grad_max = gmax;
+    r->iters = s.iters;
+    r->n_hvp = s.n_hvp;
+    r->n_fev = s.n_fev;
+    r->status = s.error != PWA_OK ? PWA_FIT_ERROR : s.status;
+    r->elapsed_s = s.elapsed;
+}
+
+bool fit_converged(const FitState& s)
+{
+    return s.error == PWA_OK && (s.status == PWA_FIT_XTOL || s.status == PWA_FIT_GTOL ||
+                                 s.status == PWA_FIT_PRECISION || s.status == PWA_FIT_TIME_LIMIT);
+}
+
+// Run the fits' work on a private non-blocking stream (the CG graph is
+// captured there); the caller's stream is restored on exit.
+struct FitStream {
+    pwa_handle* h;
+    cudaStream_t user = nullptr, own = nullptr;
+    pwa_status open(pwa_handle* hh)
+    {
+        h = hh;
+        user = h->stream;
+        if (cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            own = nullptr;
+            return pwa::set_error(h, PWA_ECUDA, "cannot create the fit stream");
+        }
+        if (user) cudaStreamSynchronize(user);
+        else cudaDeviceSynchronize();
+        h->stream = own;
+        return PWA_OK;
+    }
+    ~FitStream()
+    {
+        if (!own) return;
+        cudaStreamSynchronize(own);
+        h->stream = user;
+        cudaStreamDestroy(own);
+        cudaGetLastError();
+    }
+};
 
 }  // namespace
 
@@ -281,178 +598,139 @@ extern "C" pwa_status pwa_newton_cg_fit(pwa_handle* h, const double* theta0, con
 {
     if (!h) return PWA_EINVAL;
     if (!theta0 || !theta_out) return pwa::set_error(h, PWA_EINVAL, "theta0 and theta_out must not be NULL");
-    const auto t_start = std::chrono::steady_clock::now();
-    auto elapsed = [&]() {
-        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-    };
-    pwa_fit_opts o;
-    pwa_fit_opts_default(&o);
-    if (opts_in) o = *opts_in;
-    const int n = h->P;
-    const int maxiter = o.maxiter > 0 ? o.maxiter : 200 * n;
-    const int cg_maxiter = o.cg_maxiter > 0 ? o.cg_maxiter : 20 * n;
-    const double c1 = 1e-4, c2 = 0.9;
-
-    // the CG graph is captured on a private non-default stream
-    cudaStream_t user_stream = h->stream, fit_stream = nullptr;
-    if (cudaStreamCreateWithFlags(&fit_stream, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        return pwa::set_error(h, PWA_ECUDA, "cannot create the fit stream");
-    }
-    if (user_stream) cudaStreamSynchronize(user_stream);
-    else cudaDeviceSynchronize();
-    h->stream = fit_stream;
-    struct Restore {
-        pwa_handle* h;
-        cudaStream_t user, own;
-        ~Restore()
-        {
-            cudaStreamSynchronize(own);
-            h->stream = user;
-            cudaStreamDestroy(own);
-            cudaGetLastError();
-        }
-    } restore{h, user_stream, fit_stream};
+    FitState s;
+    init_state(s, h, theta0, opts_in);
+    s.device_cg = true;
+    FitStream fs;
+    pwa_status st = fs.open(h);
+    if (st != PWA_OK) return st;
     DeviceCG cg;
-    pwa_status st = cg.init(h);
+    st = cg.init(h);
     if (st != PWA_OK) return st;
 
-    Evaluator ev{h};
-    std::vector<double> x(theta0, theta0 + n), g(n), p(n);
-    double f = 0.0;
-    st = ev.fg(x, f, g);
+    // one fit: every request is served at once
+    FitTask task = newton_cg(s);
+    for (task.h.resume(); !task.h.done(); task.h.resume()) {
+        switch (s.req) {
+            case Req::FG:
+                ++s.n_fev;
+                s.req_status = pwa_eval(h, s.rx, nullptr, s.rf, s.rg, nullptr);
+                if (s.req_status == PWA_ENONFINITE) h->err.clear();
+                break;
+            case Req::CG:
+                s.req_status = cg.solve(s.x, s.g, s.cg_eps, s.cg_maxiter, s.p, s.n_hvp);
+                break;
+            default:
+                s.req_status = pwa::set_error(h, PWA_EINVAL, "internal: unexpected fit request");
+                break;
+        }
+    }
+    s.elapsed = s.since_start();
+    if (task.failed()) return pwa::set_error(h, PWA_ENOMEM, "host exception in the fit");
+    std::memcpy(theta_out, s.x.data(), sizeof(double) * s.P);
+    fill_result(s, result);
+    if (s.error != PWA_OK) {
+        if (s.error == PWA_ENONFINITE)
+            return pwa::set_error(h, PWA_ENONFINITE, "non-finite NLL at the start point");
+        return s.error;
+    }
+    return fit_converged(s) ? PWA_OK : PWA_ENOCONV;
+}
+
+extern "C" pwa_status pwa_newton_cg_fit_batch(pwa_handle* h, int B, const double* theta0,
+                                              const pwa_fit_opts* opts_in, double* theta_out,
+                                              pwa_fit_result* results)
+{
+    if (!h) return PWA_EINVAL;
+    h->err.clear();
+    if (B < 1) return pwa::set_error(h, PWA_EINVAL, "B must be at least 1");
+    if (!theta0 || !theta_out) return pwa::set_error(h, PWA_EINVAL, "theta0 and theta_out must not be NULL");
+    const int P = h->P;
+    for (size_t i = 0; i < (size_t)B * P; ++i)
+        if (!std::isfinite(theta0[i])) return pwa::set_error(h, PWA_EINVAL, "theta0 must be finite");
+    FitStream fs;
+    pwa_status st = fs.open(h);
+    if (st != PWA_OK) return st;
+    st = pwa::batch_io(h, B);
     if (st != PWA_OK) return st;
 
-    int status = PWA_FIT_MAXITER;
-    int k = 0;
-    while (k < maxiter) {
-        double gmax = 0.0;
-        for (double v : g) gmax = std::max(gmax, std::fabs(v));
-        if (o.gtol > 0 && gmax <= o.gtol) {
-            status = PWA_FIT_GTOL;
-            break;
+    std::vector<FitState> fits(B);
+    std::vector<FitTask> tasks;
+    tasks.reserve(B);
+    for (int b = 0; b < B; ++b) {
+        init_state(fits[b], h, theta0 + (size_t)b * P, opts_in);
+        tasks.push_back(newton_cg(fits[b]));
+        tasks[b].h.resume();  // runs to its first request
+    }
+    // lockstep rounds: every unfinished fit has one FG or HV request; all of
+    // them go into one batched launch (HVP mode when any asks for H v, with
+    // v = 0 for the FG requests), then every fit is resumed with its result
+    std::vector<int> live;
+    std::vector<double> zero(P, 0.0);
+    while (true) {
+        live.clear();
+        for (int b = 0; b < B; ++b)
+            if (!tasks[b].h.done()) live.push_back(b);
+        if (live.empty()) break;
+        const int nb = (int)live.size();
+        bool any_hv = false;
+        for (int b : live) any_hv |= fits[b].req == Req::HV;
+        pwa::BatchState& bs = h->batch;
+        const size_t BP = (size_t)nb * P;
+        double* pin = bs.h_io;
+        for (int i = 0; i < nb; ++i) {
+            const FitState& s = fits[live[i]];
+            std::memcpy(pin + (size_t)i * P, s.rx, sizeof(double) * P);
+            if (any_hv)
+                std::memcpy(pin + BP + (size_t)i * P, s.req == Req::HV ? s.rv : zero.data(), sizeof(double) * P);
         }
-        // ---- inner CG on H p = -g (N&W Algorithm 7.1), on the device ----
-        const double gnorm = std::sqrt(dot(g, g));
-        const double eps = std::min(0.5, std::sqrt(gnorm)) * gnorm;
-        st = cg.solve(x, g, eps, cg_maxiter, p, ev.n_hvp);
-        if (st != PWA_OK) break;
-        ++k;
-        double pmean = 0.0;
-        for (double v : p) pmean += std::fabs(v);
-        pmean /= std::max(n, 1);
-        if (pmean <= o.xtol) {
-            status = PWA_FIT_XTOL;
-            break;
+        double* d_th = bs.d_io;
+        double* d_v = bs.d_io + BP;
+        double* d_out = bs.d_io + 2 * BP;
+        const size_t ow = (size_t)nb * (1 + 2 * (size_t)P);
+        double* res = pin + 2 * BP;
+        int* errw = reinterpret_cast<int*>(pin + 2 * BP + ow);  // [nb] per-vector words, then the shared one
+        cudaError_t e = cudaMemcpyAsync(d_th, pin, sizeof(double) * (any_hv ? 2 * BP : BP),
+                                        cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) return pwa::cuda_error(h, e, "batch upload");
+        st = pwa::launch_batch(h, nb, d_th, any_hv ? d_v : nullptr, d_out,
+                               any_hv ? pwa::MODE_HVP : pwa::MODE_GRAD, true);
+        if (st != PWA_OK) return st;
+        e = cudaMemcpyAsync(res, d_out, sizeof(double) * ow, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(errw, bs.d_err_vec, sizeof(int) * nb, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(errw + nb, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return pwa::cuda_error(h, e, "batch download");
+        if (errw[nb]) {
+            // the shared error word: a timeout ends everything; non-finite
+            // intensities are attributed to their vectors by the per-vector words
+            st = pwa::check_device_errors(h);
+            if (st != PWA_OK && st != PWA_ENONFINITE) return st;
+            h->err.clear();
         }
-        double df0 = dot(g, p);
-        if (!(df0 < 0)) {
-            for (int i = 0; i < n; ++i) p[i] = -g[i];
-            df0 = dot(g, p);
-        }
-        // ---- strong-Wolfe line search (N&W Algorithms 3.5 / 3.6) ----
-        const double eps_f = 1e-7 * std::fabs(f);
-        auto phi = [&](double a, LinePoint& lp) -> pwa_status {
-            lp.a = a;
-            lp.x.resize(n);
-            lp.g.resize(n);
-            for (int i = 0; i < n; ++i) lp.x[i] = x[i] + a * p[i];
-            pwa_status s = ev.fg(lp.x, lp.f, lp.g);
-            if (s == PWA_ENONFINITE) {  // the trial point left the region where I > 0
-                h->err.clear();
-                lp.f = INFINITY;
-                lp.df = 0.0;
-                return PWA_OK;
+        for (int i = 0; i < nb; ++i) {
+            FitState& s = fits[live[i]];
+            const double* r = res + (size_t)i * (1 + 2 * P);
+            s.req_status = errw[i] ? PWA_ENONFINITE : PWA_OK;
+            if (s.req == Req::FG) {
+                ++s.n_fev;
+                *s.rf = r[0];
+                std::memcpy(s.rg, r + 1, sizeof(double) * P);
+            } else {
+                std::memcpy(s.rhv, r + 1 + P, sizeof(double) * P);
             }
-            lp.df = dot(lp.g, p);
-            return s;
-        };
-        auto armijo_fails = [&](const LinePoint& lp) { return !(lp.f <= f + c1 * lp.a * df0 + eps_f); };
-        LinePoint prev{0.0, f, df0, x, g}, cur, found;
-        bool ok = false;
-        auto zoom = [&](LinePoint lo, LinePoint hi) -> pwa_status {
-            for (int it = 0; it < 30; ++it) {
-                double a;
-                const double left = std::min(lo.a, hi.a), right = std::max(lo.a, hi.a), width = right - left;
-                if (!std::isfinite(hi.f) || !cubic_min(lo.a, lo.f, lo.df, hi.a, hi.f, hi.df, a) ||
-                    a < left + 0.1 * width || a > right - 0.1 * width)
-                    a = 0.5 * (lo.a + hi.a);
-                LinePoint lp;
-                pwa_status s = phi(a, lp);
-                if (s != PWA_OK) return s;
-                if (armijo_fails(lp) || lp.f >= lo.f + eps_f) {
-                    hi = lp;
-                } else {
-                    if (std::fabs(lp.df) <= -c2 * df0) {
-                        found = lp;
-                        ok = true;
-                        return PWA_OK;
-                    }
-                    if (lp.df * (hi.a - lo.a) >= 0) hi = lo;
-                    lo = lp;
-                }
-                if (std::fabs(hi.a - lo.a) < 1e-14 * std::max(1.0, std::fabs(lo.a))) break;
-            }
-            return PWA_OK;
-        };
-        double a = 1.0;
-        for (int it = 0; it < 30 && !ok; ++it) {
-            st = phi(a, cur);
-            if (st != PWA_OK) return st;
-            if (!std::isfinite(cur.f)) {
-                a = 0.5 * (prev.a + a);
-                continue;
-            }
-            if (armijo_fails(cur) || (it > 0 && cur.f >= prev.f + eps_f)) {
-                st = zoom(prev, cur);
-                if (st != PWA_OK) return st;
-                break;
-            }
-            if (std::fabs(cur.df) <= -c2 * df0) {
-                found = cur;
-                ok = true;
-                break;
-            }
-            if (cur.df >= 0) {
-                st = zoom(cur, prev);
-                if (st != PWA_OK) return st;
-                break;
-            }
-            prev = cur;
-            a = std::min(2.0 * a, 1e3);
-        }
-        if (!ok) {
-            status = std::fabs(df0) <= 1e-7 * (1.0 + std::fabs(f)) ? PWA_FIT_PRECISION : PWA_FIT_LINESEARCH;
-            break;
-        }
-        double smean = 0.0;
-        for (int i = 0; i < n; ++i) smean += std::fabs(found.x[i] - x[i]);
-        smean /= std::max(n, 1);
-        x = found.x;
-        f = found.f;
-        g = found.g;
-        if (smean <= o.xtol) {
-            status = PWA_FIT_XTOL;
-            break;
-        }
-        if (o.time_limit_s > 0 && elapsed() > o.time_limit_s) {
-            status = PWA_FIT_TIME_LIMIT;
-            break;
+            tasks[live[i]].h.resume();
+            if (tasks[live[i]].h.done()) s.elapsed = s.since_start();
         }
     }
-    std::memcpy(theta_out, x.data(), sizeof(double) * n);
-    if (result) {
-        double gmax = 0.0;
-        for (double v : g) gmax = std::max(gmax, std::fabs(v));
-        result->nll = f;
-        result->grad_max = gmax;
-        result->iters = k;
-        result->n_hvp = ev.n_hvp;
-        result->n_fev = ev.n_fev;
-        result->status = status;
-        result->elapsed_s = elapsed();
+    for (int b = 0; b < B; ++b)
+        if (tasks[b].failed()) return pwa::set_error(h, PWA_ENOMEM, "host exception in a fit");
+    bool all_ok = true;
+    for (int b = 0; b < B; ++b) {
+        std::memcpy(theta_out + (size_t)b * P, fits[b].x.data(), sizeof(double) * P);
+        if (results) fill_result(fits[b], results + b);
+        all_ok &= fit_converged(fits[b]);
     }
-    const bool converged = status == PWA_FIT_XTOL || status == PWA_FIT_GTOL || status == PWA_FIT_PRECISION ||
-                           status == PWA_FIT_TIME_LIMIT;
-    return converged ? PWA_OK : PWA_ENOCONV;
+    return all_ok ? PWA_OK : PWA_ENOCONV;
 }

@@ -118,6 +118,8 @@ extern "C" pwa_status pwa_eval_device_noalloc(pwa_handle* h, const double* d_the
     a.v = want_hv ? d_v : nullptr;
     a.Nd = h->Nd;
     a.Nmc = h->Nmc;
+    a.B = 1;
+    a.Gb = t.grid;
     a.block_rec = reinterpret_cast<double*>(base);
     a.group_rec = reinterpret_cast<double*>(base + block_bytes);
     a.group_count = counts;

@@ -89,19 +89,23 @@ struct PassArgs {
     uint32_t stage_bytes;
     int P;
     const ResParam* res;
-    const double* theta;
-    const double* v;
+    const double* theta;  // [B][P]
+    const double* v;      // [B][P] (HVP) or null
     double Nd, Nmc;
-    double* block_rec;
-    double* group_rec;
-    unsigned* group_count;
-    unsigned* top_count;
-    int group_size, ngroups, rec_len;
-    double* out;
+    // B parameter vectors are evaluated in one launch: block i works for vector
+    // i % B and is block i / B of the Gb blocks that share its events
+    int B = 1, Gb = 0;
+    double* block_rec;      // [B][Gb][rec_len]
+    double* group_rec;      // [B][ngroups][rec_len]
+    unsigned* group_count;  // [B][ngroups]
+    unsigned* top_count;    // [B]
+    int group_size, ngroups, rec_len;  // ngroups = groups per vector
+    double* out;                       // [B][1 + 2P]
     unsigned long long* bad;
     int* err;
     long long timeout_cycles;
     const int* skip = nullptr;  // when set and non-zero at launch, the pass does nothing
+    int* err_vec = nullptr;     // when set: per-vector error words [B] (besides err)
 };
 
 // ---------------------------------------------------------------------------
@@ -188,24 +192,26 @@ struct ResValues {
     double vr, vp, vm, vg;     // direction components (0 for fixed parameters)
 };
 
-__device__ __forceinline__ ResValues res_values(const PassArgs& a, int k, bool with_v)
+__device__ __forceinline__ ResValues res_values(const PassArgs& a, const double* theta, const double* v, int k,
+                                                bool with_v)
 {
     const ResParam r = a.res[k];
     double p[4], d[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        p[j] = r.idx[j] >= 0 ? a.theta[r.idx[j]] : r.fixed[j];
-        d[j] = (with_v && r.idx[j] >= 0) ? a.v[r.idx[j]] : 0.0;
+        p[j] = r.idx[j] >= 0 ? theta[r.idx[j]] : r.fixed[j];
+        d[j] = (with_v && r.idx[j] >= 0) ? v[r.idx[j]] : 0.0;
     }
     return ResValues{p[0], p[1], p[2], p[3], d[0], d[1], d[2], d[3]};
 }
 
-__device__ __forceinline__ KConst make_kconst(const PassArgs& a, int k, bool with_v, int ev)
+__device__ __forceinline__ KConst make_kconst(const PassArgs& a, const double* theta, const double* v, int k,
+                                              bool with_v, int ev)
 {
     // FP64 only where FP32 would lose the narrow peaks (M^2 as an FP32 pair,
     // M Gamma) and for the phase's range reduction; the FP32 constants are
     // otherwise computed in FP32 (the FP64 pipe is narrow on this GPU)
-    const ResValues rv = res_values(a, k, with_v);
+    const ResValues rv = res_values(a, theta, v, k, with_v);
     const double phr = rv.phi - 6.283185307179586 * rint(rv.phi * 0.15915494309189535);
     float s, c;
     sincosf((float)phr, &s, &c);
@@ -304,7 +310,13 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
 
     if (a.skip && *a.skip) return;  // a device-side loop has already finished (uniform for the grid)
     const long long T = (long long)a.ntiles[0] + a.ntiles[1];
-    const long long G = gridDim.x;
+    // parameter vector bt of the batch; this block is block gb of the G that share the events
+    const int bt = (int)(blockIdx.x % (unsigned)a.B), gb = (int)(blockIdx.x / (unsigned)a.B);
+    const long long G = a.Gb;
+    const double* theta = a.theta + (size_t)bt * a.P;
+    const double* vdir = HV ? a.v + (size_t)bt * a.P : nullptr;
+    double* out = a.out + (size_t)bt * (1 + 2 * a.P);
+    const int rec_block = bt * a.Gb + gb;  // index of this block's partial-sum record
 
     if (tid == 0) {
         s_abort = 0;
@@ -315,7 +327,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
         }
         fence_mbar_init();
         for (int i = 0; i < NST; ++i) {
-            const long long t = blockIdx.x + i * G;
+            const long long t = gb + i * G;
             if (t < T) {
                 const int smp = t < a.ntiles[0] ? 0 : 1;
                 const long long lt = smp ? t - a.ntiles[0] : t;
@@ -325,7 +337,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
             }
         }
     }
-    for (int k = tid; k < K; k += NT) kc[k] = make_kconst(a, k, HV, EV);
+    for (int k = tid; k < K; k += NT) kc[k] = make_kconst(a, theta, vdir, k, HV, EV);
     for (int i = tid; i < W * wlen; i += NT) wacc[i] = make_float2(0.f, 0.f);
     __syncthreads();
 
@@ -380,7 +392,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
     // the block's FP64 partials of one sample set: sum the warps in order
     auto write_set = [&](int set) {
         __syncthreads();
-        double* rec = a.block_rec + (size_t)blockIdx.x * a.rec_len + (size_t)set * (K * kNV + kNScal);
+        double* rec = a.block_rec + (size_t)rec_block * a.rec_len + (size_t)set * (K * kNV + kNScal);
         for (int i = tid; i < K * kNV + kNScal; i += NT) {
             double v = 0.0;
             if (i < wlen)
@@ -553,6 +565,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
                     if (valid && !good) {
                         atomicMin(a.bad, (unsigned long long)(e_base + e));
                         atomicOr(a.err, ERR_NONFINITE);
+                        if (a.err_vec) atomicOr(a.err_vec + bt, ERR_NONFINITE);
                     }
                     if (valid && good) sc0 += w * logf(I);
                 }
@@ -562,6 +575,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
                     if (valid && !(I < INFINITY)) {
                         atomicMin(a.bad, (unsigned long long)(a.nev[0] + e_base + e));
                         atomicOr(a.err, ERR_NONFINITE);
+                        if (a.err_vec) atomicOr(a.err_vec + bt, ERR_NONFINITE);
                     }
                     if (valid) {
                         sc0 += I;
@@ -680,8 +694,8 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
             ph ^= 1u;
         }
     };
-    // the block's tiles are t = blockIdx.x + i G, i = 0, 1, ...: data tiles first, then MC tiles
-    long long t = blockIdx.x, i = 0;
+    // the block's tiles are t = gb + i G, i = 0, 1, ...: data tiles first, then MC tiles
+    long long t = gb, i = 0;
     for (const long long t_end = min((long long)a.ntiles[0], T); t < t_end; t += G, ++i)
         tile(std::integral_constant<int, 0>{}, t, i);
     fold();
@@ -710,28 +724,29 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
     // ---- two-level last-block-done reduction (fixed order) ----
     __threadfence();  // every thread's record writes are visible device-wide ...
     __syncthreads();  // ... before thread 0 announces the block as done
-    const int g = blockIdx.x / a.group_size;
+    const int g = gb / a.group_size;                 // group of this block among the vector's blocks
+    const int gi = bt * a.ngroups + g;               // its counter and record
     if (tid == 0) {
-        const int members = min(a.group_size, (int)gridDim.x - g * a.group_size);
-        const unsigned prev = atomicAdd(&a.group_count[g], 1u);
+        const int members = min(a.group_size, a.Gb - g * a.group_size);
+        const unsigned prev = atomicAdd(&a.group_count[gi], 1u);
         s_flag = prev == (unsigned)(members - 1);
     }
     __syncthreads();
     if (!s_flag) return;
     __threadfence();
     {
-        const int b0 = g * a.group_size, b1 = min((int)gridDim.x, b0 + a.group_size);
+        const int b0 = bt * a.Gb + g * a.group_size, b1 = bt * a.Gb + min(a.Gb, (g + 1) * a.group_size);
         for (int i = tid; i < a.rec_len; i += NT) {
             double s = 0.0;
             for (int b = b0; b < b1; ++b) s += __ldcg(a.block_rec + (size_t)b * a.rec_len + i);
-            a.group_rec[(size_t)g * a.rec_len + i] = s;
+            a.group_rec[(size_t)gi * a.rec_len + i] = s;
         }
     }
     __threadfence();
     __syncthreads();
     if (tid == 0) {
-        a.group_count[g] = 0;
-        const unsigned prev = atomicAdd(a.top_count, 1u);
+        a.group_count[gi] = 0;
+        const unsigned prev = atomicAdd(&a.top_count[bt], 1u);
         s_flag = prev == (unsigned)(a.ngroups - 1);
     }
     __syncthreads();
@@ -741,20 +756,21 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
     double* tot = reinterpret_cast<double*>(stages);
     for (int i = tid; i < a.rec_len; i += NT) {
         double s = 0.0;
-        for (int gg = 0; gg < a.ngroups; ++gg) s += __ldcg(a.group_rec + (size_t)gg * a.rec_len + i);
+        for (int gg = 0; gg < a.ngroups; ++gg)
+            s += __ldcg(a.group_rec + (size_t)(bt * a.ngroups + gg) * a.rec_len + i);
         tot[i] = s;
     }
     __syncthreads();
-    if (tid == 0) *a.top_count = 0;
+    if (tid == 0) a.top_count[bt] = 0;
 
     // ---- combine (a-8, Eqs. 4, 6, 7) in FP64 ----
     const int L = K * kNV + kNScal;
     const double SlnI = tot[K * kNV + 0];
     const double Gm = tot[L + K * kNV + 0], Gdot = tot[L + K * kNV + 1];
-    if (tid == 0) a.out[0] = -SlnI + a.Nd * log(Gm / a.Nmc);
+    if (tid == 0) out[0] = -SlnI + a.Nd * log(Gm / a.Nmc);
     if constexpr (GR) {
         for (int k = tid; k < K; k += NT) {
-            const ResValues rv = res_values(a, k, HV);
+            const ResValues rv = res_values(a, theta, vdir, k, HV);
             const ResParam rp = a.res[k];
             double sn, cs;
             sincos(rv.phi, &sn, &cs);
@@ -796,7 +812,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
                 if (idx < 0) continue;
                 const double gD = 2.0 * (mul(kap1[j], Q1d).x + mul(kap2[j], Q2d).x);
                 const double gM = 2.0 * (mul(kap1[j], Q1m).x + mul(kap2[j], Q2m).x);
-                a.out[1 + idx] = -gD + a.Nd * gM / Gm;
+                out[1 + idx] = -gD + a.Nd * gM / Gm;
                 if constexpr (HV) {
                     const double2 Q3d = make_double2(td[4], td[5]), P1d = make_double2(td[6], td[7]),
                                   P2d = make_double2(td[8], td[9]);
@@ -806,7 +822,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
                                              mul(lam2[j], Q2d).x + mul(lam3[j], Q3d).x);
                     const double hM = 2.0 * (mul(kap1[j], P1m).x + mul(kap2[j], P2m).x + mul(lam1[j], Q1m).x +
                                              mul(lam2[j], Q2m).x + mul(lam3[j], Q3m).x);
-                    a.out[1 + a.P + idx] = -hD + a.Nd * (hM / Gm - gM * Gdot / (Gm * Gm));
+                    out[1 + a.P + idx] = -hD + a.Nd * (hM / Gm - gM * Gdot / (Gm * Gm));
                 }
             }
         }

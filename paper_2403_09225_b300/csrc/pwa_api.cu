@@ -95,7 +95,7 @@ __global__ void intensity_kernel(pwa::PassArgs a, int smp, int S, float* __restr
     pwa::KConst* kc = reinterpret_cast<pwa::KConst*>(smem_i);
     const int K = a.K, E = a.E;
     const int ev = 32 / a.W;
-    for (int k = threadIdx.x; k < K; k += blockDim.x) kc[k] = pwa::make_kconst(a, k, false, ev);
+    for (int k = threadIdx.x; k < K; k += blockDim.x) kc[k] = pwa::make_kconst(a, a.theta, nullptr, k, false, ev);
     __syncthreads();
     const long long n = a.nev[smp];
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -326,6 +326,8 @@ pwa::PassArgs make_args(pwa_handle* h, const double* d_theta, const double* d_v,
     a.v = d_v;
     a.Nd = h->Nd;
     a.Nmc = h->Nmc;
+    a.B = 1;
+    a.Gb = t.grid;
     a.block_rec = h->d_block_rec;
     a.group_rec = h->d_group_rec;
     a.group_count = h->d_counts;
@@ -511,6 +513,110 @@ pwa_status launch_pass(pwa_handle* h, const double* d_theta, const double* d_v, 
     return PWA_OK;
 }
 
+// ---- batched evaluation: B parameter vectors share one launch ----
+//
+// Block i of the launch works for vector i % B and is block i / B of the Gb
+// blocks that split the events for that vector, so neighbouring blocks stream
+// the same tiles (the second and later reads hit L2).  Each vector has its own
+// block records, groups and counters; its totals and results are those of a
+// single-vector pass over a grid of Gb blocks.
+
+namespace {
+
+void batch_geometry(const pwa_handle* h, int B, int& Gb, int& ngroups)
+{
+    const long long T = (long long)h->ntiles[0] + h->ntiles[1];
+    const long long want = ((long long)h->tiling.grid + B - 1) / B;
+    Gb = (int)std::max(1LL, std::min(want, T));
+    ngroups = (Gb + h->group_size - 1) / h->group_size;
+}
+
+}  // namespace
+
+pwa_status batch_io(pwa_handle* h, int B)
+{
+    BatchState& bs = h->batch;
+    if (B <= bs.cap_B) return PWA_OK;
+    if (bs.d_io) cudaFree(bs.d_io);
+    if (bs.h_io) cudaFreeHost(bs.h_io);
+    bs.d_io = nullptr;
+    bs.h_io = nullptr;
+    bs.cap_B = 0;
+    const size_t words = (size_t)B * (4 * (size_t)h->P + 1);
+    PWA_TRY(alloc(h, reinterpret_cast<void**>(&bs.d_io), sizeof(double) * words, "batch vectors"));
+    // pinned staging: the same layout, then B + 1 error words (B + 2 doubles of room)
+    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&bs.h_io), sizeof(double) * (words + B + 2));
+    if (e != cudaSuccess) {
+        bs.h_io = nullptr;
+        return cuda_error(h, e, "cudaMallocHost(batch staging)");
+    }
+    bs.cap_B = B;
+    return PWA_OK;
+}
+
+pwa_status launch_batch(pwa_handle* h, int B, const double* d_theta, const double* d_v, double* d_out, int mode,
+                        bool err_vec)
+{
+    if (h->broken) return set_error(h, PWA_ETIMEOUT, "handle is unusable after a device-side timeout");
+    if (B < 1) return set_error(h, PWA_EINVAL, "the batch needs at least one parameter vector");
+    KernelFn fn = pick_kernel(mode, h->S, h->tiling.W, h->tiling.KPW);
+    if (!fn) return set_error(h, PWA_EINVAL, "no kernel for this shape");
+    int Gb = 0, ngroups = 0;
+    batch_geometry(h, B, Gb, ngroups);
+    if ((long long)B * Gb > 0x7fffffffLL) return set_error(h, PWA_EINVAL, "batch too large for one launch");
+    BatchState& bs = h->batch;
+    const size_t blocks = (size_t)B * Gb, groups = (size_t)B * ngroups;
+    if (blocks > bs.cap_blocks || groups > bs.cap_groups || (size_t)B > bs.cap_top) {
+        // grow the scratch (block records, group records, counters); the
+        // counters start at zero and every completed pass leaves them at zero
+        PWA_CUDA(h, cudaStreamSynchronize(h->stream));
+        if (bs.d_block_rec) cudaFree(bs.d_block_rec);
+        if (bs.d_group_rec) cudaFree(bs.d_group_rec);
+        if (bs.d_counts) cudaFree(bs.d_counts);
+        bs.d_block_rec = bs.d_group_rec = nullptr;
+        bs.d_counts = nullptr;
+        bs.cap_blocks = bs.cap_groups = bs.cap_top = 0;
+        const size_t cb = std::max(blocks, (size_t)h->tiling.grid), cg = std::max(groups, (size_t)h->ngroups);
+        const size_t ct = std::max<size_t>(B, 64);
+        PWA_TRY(alloc(h, reinterpret_cast<void**>(&bs.d_block_rec), sizeof(double) * cb * h->rec_len,
+                      "batch block partials"));
+        PWA_TRY(alloc(h, reinterpret_cast<void**>(&bs.d_group_rec), sizeof(double) * cg * h->rec_len,
+                      "batch group partials"));
+        PWA_TRY(alloc(h, reinterpret_cast<void**>(&bs.d_counts), sizeof(unsigned) * (cg + 2 * ct), "batch counters"));
+        PWA_CUDA(h, cudaMemsetAsync(bs.d_counts, 0, sizeof(unsigned) * (cg + 2 * ct), h->stream));
+        bs.d_err_vec = reinterpret_cast<int*>(bs.d_counts + cg + ct);
+        bs.cap_blocks = cb;
+        bs.cap_groups = cg;
+        bs.cap_top = ct;
+    }
+    PassArgs a = make_args(h, d_theta, d_v, d_out);
+    a.B = B;
+    a.Gb = Gb;
+    a.block_rec = bs.d_block_rec;
+    a.group_rec = bs.d_group_rec;
+    a.group_count = bs.d_counts;
+    a.top_count = bs.d_counts + bs.cap_groups;
+    a.ngroups = ngroups;
+    if (err_vec) {
+        PWA_CUDA(h, cudaMemsetAsync(bs.d_err_vec, 0, sizeof(int) * B, h->stream));
+        a.err_vec = bs.d_err_vec;
+    }
+    fn<<<(unsigned)blocks, 32 * h->tiling.W, h->tiling.smem, h->stream>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(h, e, "batched pass kernel launch");
+    return PWA_OK;
+}
+
+void free_batch(pwa_handle* h)
+{
+    BatchState& bs = h->batch;
+    void* ptrs[] = {bs.d_block_rec, bs.d_group_rec, bs.d_counts, bs.d_io};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (bs.h_io) cudaFreeHost(bs.h_io);
+    bs = BatchState();
+}
+
 pwa_status check_device_errors(pwa_handle* h)
 {
     int err = 0;
@@ -638,6 +744,61 @@ pwa_status pwa_eval_device(pwa_handle* h, const double* d_theta, const double* d
     return pwa::launch_pass(h, d_theta, want_hv ? d_v : nullptr, d_out, mode);
 }
 
+pwa_status pwa_eval_batch_device(pwa_handle* h, int B, const double* d_theta, const double* d_v, double* d_out,
+                                 int want_grad, int want_hv)
+{
+    if (!h) return PWA_EINVAL;
+    h->err.clear();
+    if (B < 1) return pwa::set_error(h, PWA_EINVAL, "B must be at least 1");
+    if (!d_theta || !d_out || (want_hv && !d_v))
+        return pwa::set_error(h, PWA_EINVAL, "d_theta, d_out (and d_v for hv) must not be NULL");
+    const int mode = want_hv ? pwa::MODE_HVP : (want_grad ? pwa::MODE_GRAD : pwa::MODE_NLL);
+    return pwa::launch_batch(h, B, d_theta, want_hv ? d_v : nullptr, d_out, mode);
+}
+
+pwa_status pwa_eval_batch(pwa_handle* h, int B, const double* theta, const double* v, double* nll, double* grad,
+                          double* hv)
+{
+    if (!h) return PWA_EINVAL;
+    h->err.clear();
+    if (B < 1) return pwa::set_error(h, PWA_EINVAL, "B must be at least 1");
+    if (!theta || !nll) return pwa::set_error(h, PWA_EINVAL, "theta and nll must not be NULL");
+    if (hv && !v) return pwa::set_error(h, PWA_EINVAL, "v is required for hv");
+    const int P = h->P;
+    const size_t BP = (size_t)B * P;
+    for (size_t i = 0; i < BP; ++i)
+        if (!std::isfinite(theta[i]) || (hv && !std::isfinite(v[i])))
+            return pwa::set_error(h, PWA_EINVAL, "theta and v must be finite");
+    PWA_TRY(pwa::batch_io(h, B));
+    pwa::BatchState& bs = h->batch;
+    // staging: theta [B][P] then v [B][P]; results [B][1 + 2P]; then the error word
+    double* pin = bs.h_io;
+    std::memcpy(pin, theta, sizeof(double) * BP);
+    if (hv) std::memcpy(pin + BP, v, sizeof(double) * BP);
+    double* d_th = bs.d_io;
+    double* d_v = bs.d_io + BP;
+    double* d_out = bs.d_io + 2 * BP;
+    PWA_CUDA(h, cudaMemcpyAsync(d_th, pin, sizeof(double) * (hv ? 2 * BP : BP), cudaMemcpyHostToDevice, h->stream));
+    const int mode = hv ? pwa::MODE_HVP : (grad ? pwa::MODE_GRAD : pwa::MODE_NLL);
+    PWA_TRY(pwa::launch_batch(h, B, d_th, hv ? d_v : nullptr, d_out, mode));
+    const size_t ow = (size_t)B * (1 + 2 * (size_t)P);
+    double* res = pin + 2 * BP;
+    double* st = pin + 2 * BP + ow;
+    PWA_CUDA(h, cudaMemcpyAsync(res, d_out, sizeof(double) * ow, cudaMemcpyDeviceToHost, h->stream));
+    PWA_CUDA(h, cudaMemcpyAsync(st, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    PWA_CUDA(h, cudaStreamSynchronize(h->stream));
+    int err_word = 0;
+    std::memcpy(&err_word, st, sizeof(int));
+    if (err_word) PWA_TRY(pwa::check_device_errors(h));
+    for (int b = 0; b < B; ++b) {
+        const double* r = res + (size_t)b * (1 + 2 * P);
+        nll[b] = r[0];
+        if (grad) std::memcpy(grad + (size_t)b * P, r + 1, sizeof(double) * P);
+        if (hv) std::memcpy(hv + (size_t)b * P, r + 1 + P, sizeof(double) * P);
+    }
+    return PWA_OK;
+}
+
 pwa_status pwa_sync(pwa_handle* h)
 {
     if (!h) return PWA_EINVAL;
@@ -754,6 +915,7 @@ void pwa_destroy(pwa_handle* h)
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_pin) cudaFreeHost(h->h_pin);
+    pwa::free_batch(h);
     cudaGetLastError();
     delete h;
 }

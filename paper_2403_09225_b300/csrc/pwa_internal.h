@@ -35,6 +35,25 @@ __host__ __device__ inline int tile_shift(int k, int ev)
 
 }  // namespace pwa
 
+namespace pwa {
+// Scratch of batched evaluations (several parameter vectors in one launch),
+// grown on demand: per vector Gb block records, ngroups group records and
+// ngroups + 1 counters; device and pinned host buffers for the vectors and
+// their results.
+struct BatchState {
+    int cap_B = 0;           // vectors the I/O buffers hold
+    size_t cap_blocks = 0;   // block records the scratch holds
+    size_t cap_groups = 0;   // group records (and group counters) it holds
+    size_t cap_top = 0;      // per-vector top counters it holds
+    double* d_block_rec = nullptr;
+    double* d_group_rec = nullptr;
+    unsigned* d_counts = nullptr;  // [cap_groups] group counters, [cap_top] top counters, [cap_top] error words
+    int* d_err_vec = nullptr;      // per-vector error words (inside d_counts)
+    double* d_io = nullptr;        // theta [cap_B][P] | v [cap_B][P] | out [cap_B][1 + 2P]
+    double* h_io = nullptr;        // pinned, same layout, then 2 words for the error status
+};
+}  // namespace pwa
+
 struct pwa_handle {
     int K = 0, S = 0, P = 0;
     cudaStream_t stream = nullptr;
@@ -63,6 +82,7 @@ struct pwa_handle {
     unsigned long long* d_bad = nullptr;
     int* d_err = nullptr;
     double* h_pin = nullptr;        // pinned staging: theta[P], v[P], out[1 + 2P], status
+    pwa::BatchState batch;
     long long timeout_cycles = 0;
     bool broken = false;
     std::string err;
@@ -87,6 +107,14 @@ PWA_DECLARE_PICK(hvp)
 // skip: optional device flag; the pass does nothing when it is non-zero at launch.
 pwa_status launch_pass(pwa_handle* h, const double* d_theta, const double* d_v, double* d_out, int mode,
                        const int* skip = nullptr);
+// Enqueue one fused pass for B parameter vectors (theta, v: device [B][P]; out:
+// device [B][1 + 2P]); grows the batch scratch when needed.
+// err_vec: clear and fill the per-vector error words h->batch.d_err_vec [B].
+pwa_status launch_batch(pwa_handle* h, int B, const double* d_theta, const double* d_v, double* d_out, int mode,
+                        bool err_vec = false);
+// Device I/O buffers of the batch state for B vectors (grown when needed).
+pwa_status batch_io(pwa_handle* h, int B);
+void free_batch(pwa_handle* h);
 // Read back and clear the device error flags; turns them into a status + message.
 pwa_status check_device_errors(pwa_handle* h);
 pwa_status set_error(pwa_handle* h, pwa_status st, const std::string& msg);
