@@ -189,14 +189,17 @@ def cpu_baseline_leg():
                       "%.1f s" % (nd, nm, cfg.K, cfg.S, reps, dt)}
 
 
-def _fit_runs(L, wl, starts, time_limit: float):
-    from paper_2403_09225_b300 import workload as W
+def _fit_runs(L, wl, starts, time_limit: float, batched: bool = False):
+    """Fits from `starts`: one after another (plain multi-start), or all in
+    lockstep with batched passes (pwa_newton_cg_fit_batch).  GPU seconds are
+    the wall time of the fits (the device is busy or waiting on the host
+    between passes; nothing else runs)."""
     ref, ref_info = L.fit(wl.theta_true, xtol=1e-8, time_limit_s=time_limit)
-    results = []
     t0 = time.perf_counter()
-    for s in starts:
-        _, info = L.fit(s, xtol=1e-8, time_limit_s=time_limit)
-        results.append(info)
+    if batched:
+        _, results, _ = L.fit_batch(np.array(starts), xtol=1e-8, time_limit_s=time_limit)
+    else:
+        results = [L.fit(s, xtol=1e-8, time_limit_s=time_limit)[1] for s in starts]
     total = time.perf_counter() - t0
     best = min([ref_info["nll"]] + [r["nll"] for r in results])
     ok = sum(1 for r in results if r["nll"] <= best + 0.01)
@@ -212,7 +215,8 @@ def fit_metric(L, wl, n_starts: int, time_limit: float):
     seen over all fits of that workload (including one from theta_true).
     The paper-scale fits are bounded by an early-stopping time limit; the
     tiny configuration (K = 3, 2e4 + 1e5 events) shows the rate on a model
-    whose fits finish."""
+    whose fits finish, for plain multi-start (one fit after another) and for
+    the batched form (all starts in lockstep, one launch per round)."""
     from paper_2403_09225_b300 import binding
     from paper_2403_09225_b300 import workload as W
     out = {"xtol": 1e-8, "paper": _fit_runs(L, wl, W.random_starts(wl, n_starts), time_limit)}
@@ -221,7 +225,9 @@ def fit_metric(L, wl, n_starts: int, time_limit: float):
     tiny = W.make_workload(cfg, intensity=gpu_intensity_fn(table, cfg.K, cfg.S))
     Lt = binding.make_likelihood(tiny)
     try:
-        out["tiny"] = _fit_runs(Lt, tiny, W.random_starts(tiny, 32), time_limit)
+        starts = W.random_starts(tiny, 32)
+        out["tiny"] = _fit_runs(Lt, tiny, starts, time_limit)
+        out["tiny_batched"] = _fit_runs(Lt, tiny, starts, time_limit, batched=True)
     finally:
         Lt.close()
     return out

@@ -236,6 +236,19 @@ pwa_status pwa_newton_cg_fit_batch(pwa_handle* h, int B, const double* theta0,
                                    const pwa_fit_opts* opts, double* theta_out,
                                    pwa_fit_result* results);
 
+/* Lockstep fits over several handles (toy fits: different event samples,
+ * sizes, K and S), B[i] fits on handles[i].  Every round issues one batched
+ * pass per handle, each on a private stream of that handle, so the handles'
+ * kernels run concurrently; each fit's arithmetic is that of
+ * pwa_newton_cg_fit_batch on its own handle (results are identical to calling
+ * it per handle).  theta0[i], theta_out[i]: host [B[i]][P_i]; results[i]: host
+ * [B[i]] (results may be NULL).  A handle may appear only once.  Returns as
+ * pwa_newton_cg_fit_batch; an error on one handle (its pwa_last_error says
+ * which) stops all fits. */
+pwa_status pwa_newton_cg_fit_multi(int n_handles, pwa_handle* const* handles, const int* B,
+                                   const double* const* theta0, const pwa_fit_opts* opts,
+                                   double* const* theta_out, pwa_fit_result* const* results);
+
 /* Default options: xtol 1e-8, gtol 0, maxiter 0 (= 200 P), cg_maxiter 0
  * (= 20 P), no time limit. */
 void pwa_fit_opts_default(pwa_fit_opts* opts);
@@ -255,6 +268,18 @@ pwa_status pwa_set_tiling(pwa_handle* h, int warps, int stages, int blocks_per_s
 /* Current tiling and geometry: fills (warps, stages, blocks_per_sm,
  * events_per_tile, grid_blocks, smem_bytes_per_block). */
 pwa_status pwa_get_tiling(const pwa_handle* h, int out6[6]);
+
+/* Choose the tiling by measurement (no counterpart in the paper): times a
+ * batched HVP pass of B copies of theta (host [P]) under every tiling the
+ * model admits (warps 1, 2, 4, 8 with at most 8 resonances per warp; 2 or 3
+ * stages; the most blocks per SM that fit, and half as many), keeps the
+ * fastest and writes (warps, stages, blocks_per_sm) to out3 (may be NULL).
+ * Re-tiles the events for each candidate (as pwa_set_tiling does) and
+ * synchronises the handle's stream.  Timing noise can make two calls choose
+ * different tilings, and another tiling splits the FP32 event sums
+ * differently (results then agree to the pass's accuracy, not bit for bit).
+ * Errors: PWA_EINVAL, PWA_ECUDA, PWA_ENONFINITE (theta has a non-finite NLL). */
+pwa_status pwa_autotune(pwa_handle* h, const double* theta, int B, int out3[3]);
 
 /* Diagnostic of the device-side failure detection (no counterpart in the
  * paper).  Launches one block that waits on an mbarrier which nothing ever

@@ -55,6 +55,7 @@ class PwaError(RuntimeError):
 EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "pwa_grad", "pwa_hvp",
            "pwa_eval", "pwa_eval_device", "pwa_eval_device_noalloc", "pwa_eval_batch", "pwa_eval_batch_device",
            "pwa_sync", "pwa_event_intensity", "pwa_newton_cg_fit", "pwa_newton_cg_fit_batch",
+           "pwa_newton_cg_fit_multi", "pwa_autotune",
            "pwa_fit_opts_default", "pwa_set_stream", "pwa_set_tiling", "pwa_get_tiling",
            "pwa_selftest_bounded_wait", "pwa_last_error", "pwa_destroy")
 
@@ -83,6 +84,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pwa_event_intensity": (st, [H, i, dp, vp, i]),
         "pwa_newton_cg_fit": (st, [H, dp, ctypes.POINTER(pwa_fit_opts), dp, ctypes.POINTER(pwa_fit_result)]),
         "pwa_newton_cg_fit_batch": (st, [H, i, dp, ctypes.POINTER(pwa_fit_opts), dp, ctypes.POINTER(pwa_fit_result)]),
+        "pwa_newton_cg_fit_multi": (st, [i, ctypes.POINTER(ctypes.c_void_p), ip, ctypes.POINTER(dp),
+                                         ctypes.POINTER(pwa_fit_opts), ctypes.POINTER(dp),
+                                         ctypes.POINTER(ctypes.POINTER(pwa_fit_result))]),
+        "pwa_autotune": (st, [H, dp, i, ip]),
         "pwa_fit_opts_default": (None, [ctypes.POINTER(pwa_fit_opts)]),
         "pwa_set_stream": (st, [H, vp]),
         "pwa_set_tiling": (st, [H, i, i, i]),
@@ -314,11 +319,43 @@ class Likelihood:
     def set_tiling(self, warps: int, stages: int = 2, blocks_per_sm: int = 0):
         self._check(lib().pwa_set_tiling(self._h, warps, stages, blocks_per_sm))
 
+    def autotune(self, theta, batch: int = 1) -> dict:
+        """Pick the fastest tiling for batched HVP passes of `batch` vectors at theta."""
+        th = _f64(theta, self.P)
+        out = (ctypes.c_int * 3)()
+        self._check(lib().pwa_autotune(self._h, _dptr(th), int(batch), out))
+        return self.get_tiling()
+
     def get_tiling(self) -> dict:
         out = (ctypes.c_int * 6)()
         self._check(lib().pwa_get_tiling(self._h, out))
         keys = ("warps", "stages", "blocks_per_sm", "events_per_tile", "grid_blocks", "smem_bytes")
         return dict(zip(keys, list(out)))
+
+
+def fit_multi(likelihoods, thetas0, xtol: float = 1e-8, gtol: float = 0.0, maxiter: int = 0,
+              cg_maxiter: int = 0, time_limit_s: float = 0.0):
+    """Lockstep fits over several likelihoods (one group of starts per
+    likelihood; their batched passes run concurrently).  thetas0[i]: [B_i, P_i].
+    Returns ([theta [B_i, P_i]], [[info per fit]], all converged-or-time-limit)."""
+    n = len(likelihoods)
+    ths = [_f64(t).reshape(-1, L.P) for L, t in zip(likelihoods, thetas0)]
+    outs = [np.empty_like(t) for t in ths]
+    Bs = (ctypes.c_int * n)(*[t.shape[0] for t in ths])
+    res = [(pwa_fit_result * t.shape[0])() for t in ths]
+    hs = (ctypes.c_void_p * n)(*[L._h.value for L in likelihoods])
+    dpp = ctypes.POINTER(ctypes.c_double)
+    th_p = (dpp * n)(*[_dptr(t) for t in ths])
+    out_p = (dpp * n)(*[_dptr(o) for o in outs])
+    res_p = (ctypes.POINTER(pwa_fit_result) * n)(*[ctypes.cast(r, ctypes.POINTER(pwa_fit_result)) for r in res])
+    opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s)
+    st = lib().pwa_newton_cg_fit_multi(n, hs, Bs, th_p, ctypes.byref(opts), out_p, res_p)
+    if st not in (PWA_OK, PWA_ENOCONV):
+        msgs = "; ".join(filter(None, (lib().pwa_last_error(L._h).decode() for L in likelihoods)))
+        raise PwaError(st, msgs)
+    infos = [[{"nll": r.nll, "grad_max": r.grad_max, "iters": r.iters, "n_hvp": r.n_hvp, "n_fev": r.n_fev,
+               "status": FIT_STATUS_NAMES[r.status], "elapsed_s": r.elapsed_s} for r in rr] for rr in res]
+    return outs, infos, st == PWA_OK
 
 
 def make_likelihood(workload, stream: int = 0, device_inputs: bool = False) -> Likelihood:

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <coroutine>
 #include <exception>
+#include <memory>
 #include <cstring>
 #include <vector>
 
@@ -581,6 +582,154 @@ struct FitStream {
     }
 };
 
+// ---------------------------------------------------------------------------
+// lockstep executor: groups of fits, one group per handle (model and events);
+// every round issues one batched pass per group, each on its group's private
+// stream so that the groups' kernels run concurrently, then resumes every fit
+// ---------------------------------------------------------------------------
+
+struct FitGroup {
+    pwa_handle* h = nullptr;
+    int B = 0;
+    FitStream fs;
+    std::vector<FitState> fits;
+    std::vector<FitTask> tasks;
+    std::vector<int> live;
+    std::vector<double> zero;
+    bool any_hv = false;
+    int* errw = nullptr;
+    double* res = nullptr;
+};
+
+pwa_status open_group(FitGroup& g, pwa_handle* h, int B, const double* theta0, const pwa_fit_opts* opts)
+{
+    g.h = h;
+    g.B = B;
+    h->err.clear();
+    if (B < 1) return pwa::set_error(h, PWA_EINVAL, "B must be at least 1");
+    if (!theta0) return pwa::set_error(h, PWA_EINVAL, "theta0 must not be NULL");
+    const int P = h->P;
+    for (size_t i = 0; i < (size_t)B * P; ++i)
+        if (!std::isfinite(theta0[i])) return pwa::set_error(h, PWA_EINVAL, "theta0 must be finite");
+    pwa_status st = g.fs.open(h);
+    if (st != PWA_OK) return st;
+    st = pwa::batch_io(h, B);
+    if (st != PWA_OK) return st;
+    g.zero.assign(P, 0.0);
+    g.fits.resize(B);
+    g.tasks.reserve(B);
+    for (int b = 0; b < B; ++b) {
+        init_state(g.fits[b], h, theta0 + (size_t)b * P, opts);
+        g.tasks.push_back(newton_cg(g.fits[b]));
+        g.tasks[b].h.resume();  // runs to its first request
+    }
+    return PWA_OK;
+}
+
+// Enqueue the group's round: its unfinished fits' requests as one batched pass
+// (HVP mode when any asks for H v, with v = 0 for the f, g requests).
+pwa_status issue_round(FitGroup& g)
+{
+    g.live.clear();
+    for (int b = 0; b < g.B; ++b)
+        if (!g.tasks[b].h.done()) g.live.push_back(b);
+    if (g.live.empty()) return PWA_OK;
+    pwa_handle* h = g.h;
+    const int P = h->P, nb = (int)g.live.size();
+    g.any_hv = false;
+    for (int b : g.live) g.any_hv |= g.fits[b].req == Req::HV;
+    pwa::BatchState& bs = h->batch;
+    const size_t BP = (size_t)nb * P;
+    double* pin = bs.h_io;
+    for (int i = 0; i < nb; ++i) {
+        const FitState& s = g.fits[g.live[i]];
+        std::memcpy(pin + (size_t)i * P, s.rx, sizeof(double) * P);
+        if (g.any_hv)
+            std::memcpy(pin + BP + (size_t)i * P, s.req == Req::HV ? s.rv : g.zero.data(), sizeof(double) * P);
+    }
+    double* d_th = bs.d_io;
+    double* d_v = bs.d_io + BP;
+    double* d_out = bs.d_io + 2 * BP;
+    const size_t ow = (size_t)nb * (1 + 2 * (size_t)P);
+    g.res = pin + 2 * BP;
+    g.errw = reinterpret_cast<int*>(pin + 2 * BP + ow);  // [nb] per-vector words, then the shared one
+    cudaError_t e = cudaMemcpyAsync(d_th, pin, sizeof(double) * (g.any_hv ? 2 * BP : BP), cudaMemcpyHostToDevice,
+                                    h->stream);
+    if (e != cudaSuccess) return pwa::cuda_error(h, e, "batch upload");
+    pwa_status st = pwa::launch_batch(h, nb, d_th, g.any_hv ? d_v : nullptr, d_out,
+                                      g.any_hv ? pwa::MODE_HVP : pwa::MODE_GRAD, true);
+    if (st != PWA_OK) return st;
+    e = cudaMemcpyAsync(g.res, d_out, sizeof(double) * ow, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g.errw, bs.d_err_vec, sizeof(int) * nb, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g.errw + nb, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return pwa::cuda_error(h, e, "batch download");
+    return PWA_OK;
+}
+
+// Wait for the group's round and resume its fits with their results.
+pwa_status finish_round(FitGroup& g)
+{
+    if (g.live.empty()) return PWA_OK;
+    pwa_handle* h = g.h;
+    const int P = h->P, nb = (int)g.live.size();
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return pwa::cuda_error(h, e, "batch round");
+    if (g.errw[nb]) {
+        // the shared error word: a timeout ends everything; non-finite
+        // intensities are attributed to their vectors by the per-vector words
+        pwa_status st = pwa::check_device_errors(h);
+        if (st != PWA_OK && st != PWA_ENONFINITE) return st;
+        h->err.clear();
+    }
+    for (int i = 0; i < nb; ++i) {
+        FitState& s = g.fits[g.live[i]];
+        const double* r = g.res + (size_t)i * (1 + 2 * P);
+        s.req_status = g.errw[i] ? PWA_ENONFINITE : PWA_OK;
+        if (s.req == Req::FG) {
+            ++s.n_fev;
+            *s.rf = r[0];
+            std::memcpy(s.rg, r + 1, sizeof(double) * P);
+        } else {
+            std::memcpy(s.rhv, r + 1 + P, sizeof(double) * P);
+        }
+        g.tasks[g.live[i]].h.resume();
+        if (g.tasks[g.live[i]].h.done()) s.elapsed = s.since_start();
+    }
+    return PWA_OK;
+}
+
+pwa_status run_lockstep(std::vector<std::unique_ptr<FitGroup>>& groups)
+{
+    while (true) {
+        bool any = false;
+        for (auto& g : groups) {
+            pwa_status st = issue_round(*g);
+            if (st != PWA_OK) return st;
+            any |= !g->live.empty();
+        }
+        if (!any) return PWA_OK;
+        for (auto& g : groups) {
+            pwa_status st = finish_round(*g);
+            if (st != PWA_OK) return st;
+        }
+    }
+}
+
+// Results of a group; true when every fit converged or hit its time limit.
+pwa_status close_group(FitGroup& g, double* theta_out, pwa_fit_result* results, bool& all_ok)
+{
+    const int P = g.h->P;
+    for (int b = 0; b < g.B; ++b)
+        if (g.tasks[b].failed()) return pwa::set_error(g.h, PWA_ENOMEM, "host exception in a fit");
+    for (int b = 0; b < g.B; ++b) {
+        std::memcpy(theta_out + (size_t)b * P, g.fits[b].x.data(), sizeof(double) * P);
+        if (results) fill_result(g.fits[b], results + b);
+        all_ok &= fit_converged(g.fits[b]);
+    }
+    return PWA_OK;
+}
+
 }  // namespace
 
 extern "C" void pwa_fit_opts_default(pwa_fit_opts* o)
@@ -642,95 +791,34 @@ extern "C" pwa_status pwa_newton_cg_fit_batch(pwa_handle* h, int B, const double
                                               pwa_fit_result* results)
 {
     if (!h) return PWA_EINVAL;
-    h->err.clear();
-    if (B < 1) return pwa::set_error(h, PWA_EINVAL, "B must be at least 1");
-    if (!theta0 || !theta_out) return pwa::set_error(h, PWA_EINVAL, "theta0 and theta_out must not be NULL");
-    const int P = h->P;
-    for (size_t i = 0; i < (size_t)B * P; ++i)
-        if (!std::isfinite(theta0[i])) return pwa::set_error(h, PWA_EINVAL, "theta0 must be finite");
-    FitStream fs;
-    pwa_status st = fs.open(h);
-    if (st != PWA_OK) return st;
-    st = pwa::batch_io(h, B);
-    if (st != PWA_OK) return st;
+    if (!theta_out) return pwa::set_error(h, PWA_EINVAL, "theta_out must not be NULL");
+    return pwa_newton_cg_fit_multi(1, &h, &B, &theta0, opts_in, &theta_out, &results);
+}
 
-    std::vector<FitState> fits(B);
-    std::vector<FitTask> tasks;
-    tasks.reserve(B);
-    for (int b = 0; b < B; ++b) {
-        init_state(fits[b], h, theta0 + (size_t)b * P, opts_in);
-        tasks.push_back(newton_cg(fits[b]));
-        tasks[b].h.resume();  // runs to its first request
+extern "C" pwa_status pwa_newton_cg_fit_multi(int n_handles, pwa_handle* const* handles, const int* B,
+                                              const double* const* theta0, const pwa_fit_opts* opts,
+                                              double* const* theta_out, pwa_fit_result* const* results)
+{
+    if (n_handles < 1 || !handles || !B || !theta0 || !theta_out) return PWA_EINVAL;
+    for (int i = 0; i < n_handles; ++i) {
+        if (!handles[i]) return PWA_EINVAL;
+        if (!theta_out[i]) return pwa::set_error(handles[i], PWA_EINVAL, "theta_out must not be NULL");
+        for (int j = 0; j < i; ++j)
+            if (handles[j] == handles[i])
+                return pwa::set_error(handles[i], PWA_EINVAL, "a handle appears twice; put its fits in one group");
     }
-    // lockstep rounds: every unfinished fit has one FG or HV request; all of
-    // them go into one batched launch (HVP mode when any asks for H v, with
-    // v = 0 for the FG requests), then every fit is resumed with its result
-    std::vector<int> live;
-    std::vector<double> zero(P, 0.0);
-    while (true) {
-        live.clear();
-        for (int b = 0; b < B; ++b)
-            if (!tasks[b].h.done()) live.push_back(b);
-        if (live.empty()) break;
-        const int nb = (int)live.size();
-        bool any_hv = false;
-        for (int b : live) any_hv |= fits[b].req == Req::HV;
-        pwa::BatchState& bs = h->batch;
-        const size_t BP = (size_t)nb * P;
-        double* pin = bs.h_io;
-        for (int i = 0; i < nb; ++i) {
-            const FitState& s = fits[live[i]];
-            std::memcpy(pin + (size_t)i * P, s.rx, sizeof(double) * P);
-            if (any_hv)
-                std::memcpy(pin + BP + (size_t)i * P, s.req == Req::HV ? s.rv : zero.data(), sizeof(double) * P);
-        }
-        double* d_th = bs.d_io;
-        double* d_v = bs.d_io + BP;
-        double* d_out = bs.d_io + 2 * BP;
-        const size_t ow = (size_t)nb * (1 + 2 * (size_t)P);
-        double* res = pin + 2 * BP;
-        int* errw = reinterpret_cast<int*>(pin + 2 * BP + ow);  // [nb] per-vector words, then the shared one
-        cudaError_t e = cudaMemcpyAsync(d_th, pin, sizeof(double) * (any_hv ? 2 * BP : BP),
-                                        cudaMemcpyHostToDevice, h->stream);
-        if (e != cudaSuccess) return pwa::cuda_error(h, e, "batch upload");
-        st = pwa::launch_batch(h, nb, d_th, any_hv ? d_v : nullptr, d_out,
-                               any_hv ? pwa::MODE_HVP : pwa::MODE_GRAD, true);
+    std::vector<std::unique_ptr<FitGroup>> groups;
+    for (int i = 0; i < n_handles; ++i) {
+        groups.push_back(std::make_unique<FitGroup>());
+        pwa_status st = open_group(*groups.back(), handles[i], B[i], theta0[i], opts);
         if (st != PWA_OK) return st;
-        e = cudaMemcpyAsync(res, d_out, sizeof(double) * ow, cudaMemcpyDeviceToHost, h->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(errw, bs.d_err_vec, sizeof(int) * nb, cudaMemcpyDeviceToHost, h->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(errw + nb, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        if (e != cudaSuccess) return pwa::cuda_error(h, e, "batch download");
-        if (errw[nb]) {
-            // the shared error word: a timeout ends everything; non-finite
-            // intensities are attributed to their vectors by the per-vector words
-            st = pwa::check_device_errors(h);
-            if (st != PWA_OK && st != PWA_ENONFINITE) return st;
-            h->err.clear();
-        }
-        for (int i = 0; i < nb; ++i) {
-            FitState& s = fits[live[i]];
-            const double* r = res + (size_t)i * (1 + 2 * P);
-            s.req_status = errw[i] ? PWA_ENONFINITE : PWA_OK;
-            if (s.req == Req::FG) {
-                ++s.n_fev;
-                *s.rf = r[0];
-                std::memcpy(s.rg, r + 1, sizeof(double) * P);
-            } else {
-                std::memcpy(s.rhv, r + 1 + P, sizeof(double) * P);
-            }
-            tasks[live[i]].h.resume();
-            if (tasks[live[i]].h.done()) s.elapsed = s.since_start();
-        }
     }
-    for (int b = 0; b < B; ++b)
-        if (tasks[b].failed()) return pwa::set_error(h, PWA_ENOMEM, "host exception in a fit");
+    pwa_status st = run_lockstep(groups);
+    if (st != PWA_OK) return st;
     bool all_ok = true;
-    for (int b = 0; b < B; ++b) {
-        std::memcpy(theta_out + (size_t)b * P, fits[b].x.data(), sizeof(double) * P);
-        if (results) fill_result(fits[b], results + b);
-        all_ok &= fit_converged(fits[b]);
+    for (int i = 0; i < n_handles; ++i) {
+        st = close_group(*groups[i], theta_out[i], results ? results[i] : nullptr, all_ok);
+        if (st != PWA_OK) return st;
     }
     return all_ok ? PWA_OK : PWA_ENOCONV;
 }

@@ -861,6 +861,89 @@ pwa_status pwa_set_tiling(pwa_handle* h, int warps, int stages, int blocks_per_s
     return st;
 }
 
+pwa_status pwa_autotune(pwa_handle* h, const double* theta, int B, int out3[3])
+{
+    if (!h) return PWA_EINVAL;
+    h->err.clear();
+    if (!theta || B < 1) return pwa::set_error(h, PWA_EINVAL, "theta must not be NULL and B >= 1");
+    const int P = h->P;
+    for (int i = 0; i < P; ++i)
+        if (!std::isfinite(theta[i])) return pwa::set_error(h, PWA_EINVAL, "theta must be finite");
+    // B copies of theta and a fixed direction as the timed batch
+    PWA_TRY(pwa::batch_io(h, B));
+    pwa::BatchState& bs = h->batch;
+    const size_t BP = (size_t)B * P;
+    for (int b = 0; b < B; ++b) {
+        std::memcpy(bs.h_io + (size_t)b * P, theta, sizeof(double) * P);
+        for (int i = 0; i < P; ++i) bs.h_io[BP + (size_t)b * P + i] = 1.0 / std::sqrt((double)P);
+    }
+    PWA_CUDA(h, cudaMemcpyAsync(bs.d_io, bs.h_io, sizeof(double) * 2 * BP, cudaMemcpyHostToDevice, h->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PWA_CUDA(h, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return pwa::cuda_error(h, cudaGetLastError(), "cudaEventCreate");
+    }
+    struct Events {
+        cudaEvent_t a, b;
+        ~Events()
+        {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } ev{e0, e1};
+    const Tiling start = h->tiling;
+    Tiling best = start;
+    float best_ms = INFINITY;
+    const int Ws[] = {1, 2, 4, 8};
+    for (int W : Ws) {
+        if ((h->K + W - 1) / W > 8) continue;
+        for (int NST = 2; NST <= 3; ++NST) {
+            for (int half = 0; half < 2; ++half) {
+                // all blocks per SM the tiling allows, then half as many
+                if (pwa_set_tiling(h, W, NST, 0) != PWA_OK) {
+                    h->err.clear();
+                    continue;
+                }
+                if (half) {
+                    const int bps = std::max(1, h->tiling.blocks_per_sm / 2);
+                    if (bps == h->tiling.blocks_per_sm || pwa_set_tiling(h, W, NST, bps) != PWA_OK) {
+                        h->err.clear();
+                        continue;
+                    }
+                }
+                double* d_th = bs.d_io;
+                double* d_v = bs.d_io + BP;
+                double* d_out = bs.d_io + 2 * BP;
+                pwa_status st = PWA_OK;
+                for (int r = 0; r < 2 && st == PWA_OK; ++r)
+                    st = pwa::launch_batch(h, B, d_th, d_v, d_out, pwa::MODE_HVP);
+                PWA_CUDA(h, cudaEventRecord(e0, h->stream));
+                constexpr int kReps = 5;
+                for (int r = 0; r < kReps && st == PWA_OK; ++r)
+                    st = pwa::launch_batch(h, B, d_th, d_v, d_out, pwa::MODE_HVP);
+                PWA_CUDA(h, cudaEventRecord(e1, h->stream));
+                PWA_CUDA(h, cudaEventSynchronize(e1));
+                if (st != PWA_OK) return st;
+                PWA_TRY(pwa::check_device_errors(h));
+                float ms = 0.f;
+                PWA_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = h->tiling;
+                }
+            }
+        }
+    }
+    PWA_TRY(pwa_set_tiling(h, best.W, best.NST, best.blocks_per_sm));
+    if (out3) {
+        out3[0] = h->tiling.W;
+        out3[1] = h->tiling.NST;
+        out3[2] = h->tiling.blocks_per_sm;
+    }
+    return PWA_OK;
+}
+
 pwa_status pwa_get_tiling(const pwa_handle* h, int out6[6])
 {
     if (!h || !out6) return PWA_EINVAL;

@@ -127,3 +127,36 @@ def test_batched_fit_reports_a_bad_start_per_fit():
     assert infos[0]["status"] in ("xtol", "gtol", "precision_limit"), infos[0]
     th_single, info_single = L.fit(good, xtol=1e-8)
     assert abs(infos[0]["nll"] - info_single["nll"]) <= 1e-6 * abs(info_single["nll"])
+
+
+def test_fits_over_several_handles_equal_each_handles_own_batch():
+    """Toy fits of different models and sample sizes (K, S, N differ) in
+    lockstep over several handles: the same results, bit for bit, as each
+    handle's own batched fits (the groups only share the rounds)."""
+    from paper_2403_09225_b300 import binding
+    wls = [small_workload("tiny", 3000 + 7, 15000 + 3)[0], small_workload("tiny_k4", 2001, 8001)[0],
+           small_workload("paper", 800 + 5, 3000 + 11)[0]]
+    Ls = [make_L(wl) for wl in wls]
+    starts = []
+    for i, wl in enumerate(wls):
+        rng = np.random.default_rng(20 + i)
+        starts.append(wl.theta_true * (1 + 0.02 * rng.standard_normal((3, wl.theta_true.size))))
+    outs, infos, _ = binding.fit_multi(Ls, starts, xtol=1e-8, maxiter=20)
+    for L, st, o, inf in zip(Ls, starts, outs, infos):
+        o2, inf2, _ = L.fit_batch(st, xtol=1e-8, maxiter=20)
+        assert np.array_equal(o, o2)
+        assert [r["nll"] for r in inf] == [r["nll"] for r in inf2]
+        assert [r["status"] for r in inf] == [r["status"] for r in inf2]
+
+
+def test_autotune_keeps_results_within_tolerance():
+    wl, model = small_workload("paper", 1500 + 3, 6000 + 29)
+    L = make_L(wl)
+    th = wl.theta_true
+    v = np.random.default_rng(2).standard_normal(model.P)
+    til = L.autotune(th, batch=4)
+    assert til["warps"] in (1, 2, 4, 8) and til["stages"] in (2, 3) and til["blocks_per_sm"] >= 1
+    f, g, hv = L.eval(th, v)
+    fo, go, hvo = oracle.nll_grad_hvp(model, th, v, wl.data, wl.mc)
+    assert abs(f - fo) <= TOL_NLL * nll_scale(model, th, wl, fo)
+    assert relmax(g, go) <= TOL_GRAD and relmax(hv, hvo) <= TOL_HVP
