@@ -233,6 +233,58 @@ def fit_metric(L, wl, n_starts: int, time_limit: float):
     return out
 
 
+def batching_metric(n_toys: int, n_starts: int, time_limit: float, seed: int = 7):
+    """Toy fits of uneven size and model, plain against batched.  Each toy
+    draws data events log-uniform in [1e4, 1e5] (MC = 5 x data), K uniform in
+    5..30 and S uniform in 2..4 (the batching configuration's distributions,
+    with data sizes capped at 1e5 to keep a run to minutes), accept-rejects its
+    data from I at its own generating point, and is fitted from n_starts
+    random starts.  Plain: every fit of every toy one after another.  Batched:
+    all fits of all toys in lockstep (pwa_newton_cg_fit_multi; one batched
+    pass per toy per round, the toys' passes on concurrent streams).  A fit
+    reaches the global minimum when its NLL is within 0.01 of the best NLL of
+    its toy (over both arms and a fit from the generating point)."""
+    from paper_2403_09225_b300 import binding
+    from paper_2403_09225_b300 import workload as W
+    rng = np.random.default_rng(seed)
+    toys, Ls = [], []
+    for i in range(n_toys):
+        nd = int(round(10 ** rng.uniform(4, 5)))
+        cfg = W.Config("toy%d" % i, int(rng.integers(5, 31)), int(rng.integers(2, 5)), nd, 5 * nd, 4, False,
+                       100 + i)
+        table = W.make_table(cfg)
+        wl = W.make_workload(cfg, intensity=gpu_intensity_fn(table, cfg.K, cfg.S))
+        toys.append(wl)
+        Ls.append(binding.make_likelihood(wl))
+    try:
+        starts = [W.random_starts(wl, n_starts) for wl in toys]
+        best = [L.fit(wl.theta_true, xtol=1e-8, time_limit_s=time_limit)[1]["nll"] for L, wl in zip(Ls, toys)]
+        t0 = time.perf_counter()
+        plain = [[L.fit(s, xtol=1e-8, time_limit_s=time_limit)[1] for s in st] for L, st in zip(Ls, starts)]
+        t_plain = time.perf_counter() - t0
+        # in lockstep every fit advances once per round, so a fit's wall-clock
+        # limit is scaled by the number of fits sharing the rounds: both arms
+        # then grant a fit the same GPU time at most
+        t0 = time.perf_counter()
+        _, batched, _ = binding.fit_multi(Ls, starts, xtol=1e-8, time_limit_s=time_limit * n_toys * n_starts)
+        t_batched = time.perf_counter() - t0
+        for i in range(n_toys):
+            best[i] = min([best[i]] + [r["nll"] for r in plain[i]] + [r["nll"] for r in batched[i]])
+
+        def arm(results, seconds):
+            ok = sum(1 for i in range(n_toys) for r in results[i] if r["nll"] <= best[i] + 0.01)
+            return {"fits": n_toys * n_starts, "reached_global_min": ok, "gpu_seconds": seconds,
+                    "fits_to_global_min_per_s": ok / seconds if seconds > 0 else 0.0,
+                    "passes": int(sum(r["n_fev"] + r["n_hvp"] for rr in results for r in rr)),
+                    "statuses": sorted({r["status"] for rr in results for r in rr})}
+        return {"toys": n_toys, "starts_per_toy": n_starts, "time_limit_s_per_fit": time_limit,
+                "K": [wl.K for wl in toys], "S": [wl.S for wl in toys], "n_data": [wl.data.n for wl in toys],
+                "plain": arm(plain, t_plain), "batched": arm(batched, t_batched)}
+    finally:
+        for L in Ls:
+            L.close()
+
+
 def measured_traffic(tiling: dict):
     """DRAM bytes per launch of the fused HVP pass from the committed ncu
     summary, when it was taken with the tiling in use (else None)."""
@@ -275,6 +327,8 @@ def main():
     ap.add_argument("--fit-time-limit", type=float, default=10.0, help="seconds per fit (early stopping)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tiling", default="", help="warps,lanes_per_event,stages[,blocks_per_sm] (default: library's)")
+    ap.add_argument("--batching", default="", metavar="TOYS,STARTS",
+                    help="also run the uneven-size toy-fit comparison (plain vs batched), e.g. 12,4")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="event counts relative to the workload (profiling captures only; default 1)")
     args = ap.parse_args()
@@ -348,6 +402,11 @@ def main():
     if args.fits > 0 and rank == 0:
         fit = fit_metric(L, wl, args.fits, time_limit=args.fit_time_limit)
 
+    batching = None
+    if args.batching and rank == 0:
+        n_toys, n_starts = (int(x) for x in args.batching.split(","))
+        batching = batching_metric(n_toys, n_starts, time_limit=args.fit_time_limit)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_leg()
@@ -377,6 +436,8 @@ def main():
             res["cpu_baseline"] = cpu
         if fit is not None:
             res["fit"] = fit
+        if batching is not None:
+            res["batching"] = batching
         print(json.dumps(res))
     L.close()
     if dist:
