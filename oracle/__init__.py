@@ -15,6 +15,7 @@ Functions and the passages they follow:
   nll_grad_hvp     -ln L, its gradient and H v              Eqs. 4, 6, 7
   sample_sums      per-shard F_m, G_m and derivatives       Eq. 5
   hessian          full Hessian of -ln L                    Eq. 7
+  integral_matrix  Phi_kk' = sum_e sum_s conj(U_ks) U_k's   Eq. 1 (couplings factored out)
 """
 from __future__ import annotations
 
@@ -58,6 +59,8 @@ def _load():
         lib.or_sample_hessian.restype = L
         lib.or_nll.argtypes = [I, I, ip, dp, dp, L, fp, fp, fp, L, fp, fp, dp, dp, dp]
         lib.or_nll.restype = L
+        lib.or_integral_matrix.argtypes = [I, I, ip, dp, L, fp, fp, dp]
+        lib.or_integral_matrix.restype = L
         lib.or_hessian.argtypes = [I, I, ip, dp, L, fp, fp, fp, L, fp, fp, dp]
         lib.or_hessian.restype = L
         _lib = lib
@@ -144,6 +147,27 @@ def intensity(model: Model, theta, m2, F) -> np.ndarray:
     par = model.full(theta)
     lib.or_intensity(model.K, model.S, _i(model.channels), _d(par), n, _f(m2), _f(Fv), _d(out))
     return out
+
+
+def integral_matrix(model: Model, theta, m2, F) -> np.ndarray:
+    """Phi [K, K] complex at theta's masses and widths: sum over the events of
+    sum_s conj(U_ks) U_k's with U = BW F, so that sum_e I(e) = g^H Phi g for
+    the couplings g_k = rho_k e^{i phi_k} (Eq. 1 with the couplings factored out)."""
+    lib = _load()
+    m2, Fv, _ = _events(m2, F)
+    out = np.empty(2 * model.K * model.K)
+    rc = lib.or_integral_matrix(model.K, model.S, _i(model.channels), _d(model.full(theta)), m2.shape[1],
+                                _f(m2), _f(Fv), _d(out))
+    if rc != -1:
+        raise MemoryError("or_integral_matrix")
+    return (out[0::2] + 1j * out[1::2]).reshape(model.K, model.K)
+
+
+def couplings(model: Model, theta) -> np.ndarray:
+    """g_k = rho_k e^{i phi_k} of every resonance (fixed ones included)."""
+    par = model.full(theta)
+    K = model.K
+    return par[:K] * np.exp(1j * par[K:2 * K])
 
 
 def intensity_full(K, S, channels, par_full, m2, F) -> np.ndarray:

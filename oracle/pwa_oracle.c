@@ -336,3 +336,41 @@ long or_hessian(int K, int S, const int* ch, const double* par,
     if (bm >= 0) return nd + bm;
     return -1;
 }
+
+/*
+ * Integral matrix of the fixed-mass coupling problem (Eq. 1 written as a sum
+ * over coupling pairs: with U_{k,s}(e) = BW_k(e) F_{k,s}(e) and c_k = g_k BW_k,
+ * sum_e I(e) = sum_{k,k'} conj(g_k) g_{k'} Phi_{k k'}):
+ *   Phi_{k k'} = sum_e sum_s conj(U_{k,s}(e)) U_{k',s}(e),
+ * at the masses and widths of par (its couplings are not used).
+ * out[(k*K + k')*2 + {0,1}] = real/imag of Phi_{k k'}.
+ */
+long or_integral_matrix(int K, int S, const int* ch, const double* par,
+                        long n, const float* m2, const float* F, double* out)
+{
+    cd* phi = (cd*)calloc((size_t)K * K, sizeof(cd));
+    cd* U = (cd*)malloc((size_t)K * S * sizeof(cd));
+    if (!phi || !U) {
+        free(phi);
+        free(U);
+        return -2;
+    }
+    coupling cp;
+    for (long e = 0; e < n; ++e) {
+        for (int k = 0; k < K; ++k) {
+            /* rho = 1, phi = 0: the coupling is BW_k itself */
+            coupling_at(1.0, 0.0, par[2 * K + k], par[3 * K + k], (double)m2[(size_t)ch[k] * n + e], &cp);
+            for (int s = 0; s < S; ++s) U[k * S + s] = cp.c * F_at(F, e, k, s, K, S);
+        }
+        for (int k = 0; k < K; ++k)
+            for (int kp = 0; kp < K; ++kp)
+                for (int s = 0; s < S; ++s) phi[k * K + kp] += conj(U[k * S + s]) * U[kp * S + s];
+    }
+    for (int i = 0; i < K * K; ++i) {
+        out[2 * i] = creal(phi[i]);
+        out[2 * i + 1] = cimag(phi[i]);
+    }
+    free(phi);
+    free(U);
+    return -1;
+}

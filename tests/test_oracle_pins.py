@@ -184,3 +184,23 @@ def test_bad_events_are_reported(tiny_small):
     with pytest.raises(oracle.OracleError) as e:
         oracle.nll(model, wl.theta_true, wl.data, mc)
     assert e.value.index == wl.data.n + 5
+
+
+def test_integral_matrix_reproduces_the_mc_sum(paper_small):
+    """Eq. 1 with the couplings factored out: sum_mc I(e) = g^H Phi g for any
+    couplings at fixed masses and widths; Phi is Hermitian positive
+    semi-definite.  Pins the oracle's integral matrix against its own
+    intensity (an independent loop over events)."""
+    wl, model = paper_small
+    rng = np.random.default_rng(31)
+    for th in (wl.theta_true, W.random_starts(wl, 1)[0]):
+        phi = oracle.integral_matrix(model, th, wl.mc.m2, wl.mc.F)
+        assert np.allclose(phi, phi.conj().T, rtol=0, atol=1e-10 * np.abs(phi).max())
+        assert np.linalg.eigvalsh(phi).min() >= -1e-9 * np.abs(phi).max()
+        # other couplings at the same masses and widths
+        th2 = th.copy()
+        nc = int(np.sum([not r.fix_coupling for r in wl.table]))
+        th2[:2 * nc] += 0.3 * rng.standard_normal(2 * nc)
+        g = oracle.couplings(model, th2)
+        total = float(np.sum(oracle.intensity(model, th2, wl.mc.m2, wl.mc.F)))
+        assert abs(np.real(g.conj() @ phi @ g) - total) <= 1e-11 * total
