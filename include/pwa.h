@@ -249,6 +249,48 @@ pwa_status pwa_newton_cg_fit_multi(int n_handles, pwa_handle* const* handles, co
                                    const double* const* theta0, const pwa_fit_opts* opts,
                                    double* const* theta_out, pwa_fit_result* const* results);
 
+/* ---- fixed-mass coupling sub-problem (tensor cores) ----
+ *
+ * With every mass and width held at given values, U_{k,s}(e) = BW_k(e)
+ * F_{k,s}(e) is fixed and the coherent sum of Eq. 1 is linear in the
+ * couplings g_k = rho_k e^{i phi_k}: A_s(e) = sum_k g_k U_{k,s}(e).  The MC
+ * normalisation becomes g^H Phi g with the K x K Hermitian integral matrix
+ * Phi_{kk'} = sum_mc sum_s conj(U_{k,s}) U_{k',s} (computed once), and the
+ * data term for many coupling vectors is a pair of GEMMs per tile of events,
+ * run on the tensor cores (tcgen05, TF32 inputs split in hi + lo parts so that
+ * products keep FP32 accuracy; FP32 accumulation in tensor memory, FP64 across
+ * tiles).  The MC events are not read after the object is created.
+ *
+ * The coupling parameters are the first Pc entries of theta (the free
+ * magnitudes, then the free phases, in resonance order); the object keeps the
+ * masses, widths and fixed couplings of the theta it was created from.
+ * Supported for K <= 24 (one tile's operands must fit in shared memory). */
+typedef struct pwa_coupling pwa_coupling; /* opaque; owned by the library */
+
+/* Fix the masses and widths at theta (host [P]); lay the data events out as
+ * U tiles on the device and compute Phi from the MC events.  The object
+ * refers to h (destroy it before h).  Errors: PWA_EINVAL (K > 24), PWA_ENOMEM,
+ * PWA_ECUDA, PWA_ETIMEOUT. */
+pwa_status pwa_coupling_create(pwa_handle* h, const double* theta, pwa_coupling** out);
+
+/* Pc: the number of coupling parameters (free magnitudes and phases). */
+int pwa_coupling_num_params(const pwa_coupling* cp);
+
+/* The integral matrix: phi [K][K][2] (real, imaginary), host. */
+pwa_status pwa_coupling_integral_matrix(const pwa_coupling* cp, double* phi);
+
+/* NLL, its gradient and H v with respect to the coupling parameters for C
+ * coupling vectors (rows of theta_c, host [C][Pc]) at the fixed masses and
+ * widths: the same values as pwa_eval at the full theta restricted to the
+ * coupling block (Eqs. 3, 6, 7), up to FP32 summation.  v: host [C][Pc] or
+ * NULL (then hv must be NULL); nll: host [C]; grad, hv: host [C][Pc] or NULL.
+ * Vectors are evaluated 16 per launch.  Errors: PWA_EINVAL, PWA_ECUDA,
+ * PWA_ENONFINITE (a data event with I <= 0 or non-finite), PWA_ETIMEOUT. */
+pwa_status pwa_coupling_eval(pwa_coupling* cp, int C, const double* theta_c, const double* v,
+                             double* nll, double* grad, double* hv);
+
+void pwa_coupling_destroy(pwa_coupling* cp);
+
 /* Default options: xtol 1e-8, gtol 0, maxiter 0 (= 200 P), cg_maxiter 0
  * (= 20 P), no time limit. */
 void pwa_fit_opts_default(pwa_fit_opts* opts);

@@ -55,7 +55,8 @@ class PwaError(RuntimeError):
 EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "pwa_grad", "pwa_hvp",
            "pwa_eval", "pwa_eval_device", "pwa_eval_device_noalloc", "pwa_eval_batch", "pwa_eval_batch_device",
            "pwa_sync", "pwa_event_intensity", "pwa_newton_cg_fit", "pwa_newton_cg_fit_batch",
-           "pwa_newton_cg_fit_multi", "pwa_autotune",
+           "pwa_newton_cg_fit_multi", "pwa_autotune", "pwa_coupling_create", "pwa_coupling_num_params",
+           "pwa_coupling_integral_matrix", "pwa_coupling_eval", "pwa_coupling_destroy",
            "pwa_fit_opts_default", "pwa_set_stream", "pwa_set_tiling", "pwa_get_tiling",
            "pwa_selftest_bounded_wait", "pwa_last_error", "pwa_destroy")
 
@@ -88,6 +89,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                          ctypes.POINTER(pwa_fit_opts), ctypes.POINTER(dp),
                                          ctypes.POINTER(ctypes.POINTER(pwa_fit_result))]),
         "pwa_autotune": (st, [H, dp, i, ip]),
+        "pwa_coupling_create": (st, [H, dp, ctypes.POINTER(ctypes.c_void_p)]),
+        "pwa_coupling_num_params": (i, [vp]),
+        "pwa_coupling_integral_matrix": (st, [vp, dp]),
+        "pwa_coupling_eval": (st, [vp, i, dp, dp, dp, dp, dp]),
+        "pwa_coupling_destroy": (None, [vp]),
         "pwa_fit_opts_default": (None, [ctypes.POINTER(pwa_fit_opts)]),
         "pwa_set_stream": (st, [H, vp]),
         "pwa_set_tiling": (st, [H, i, i, i]),
@@ -331,6 +337,58 @@ class Likelihood:
         self._check(lib().pwa_get_tiling(self._h, out))
         keys = ("warps", "stages", "blocks_per_sm", "events_per_tile", "grid_blocks", "smem_bytes")
         return dict(zip(keys, list(out)))
+
+
+class Coupling:
+    """The fixed-mass coupling sub-problem of a likelihood (tensor-core GEMMs
+    over U = BW F tiles and the K x K integral matrix; see include/pwa.h).
+    Its parameters are the first Pc entries of theta (free magnitudes, then
+    free phases); masses, widths and fixed couplings come from `theta`."""
+
+    def __init__(self, L: "Likelihood", theta):
+        th = _f64(theta, L.P)
+        h = ctypes.c_void_p()
+        st = lib().pwa_coupling_create(L._h, _dptr(th), ctypes.byref(h))
+        if st != PWA_OK:
+            raise PwaError(st, lib().pwa_last_error(L._h).decode())
+        self._L = L
+        self._h = h
+        self.K = L.K
+        self.Pc = lib().pwa_coupling_num_params(h)
+
+    def _check(self, st: int):
+        if st != PWA_OK:
+            raise PwaError(st, lib().pwa_last_error(self._L._h).decode())
+
+    def integral_matrix(self) -> np.ndarray:
+        out = np.empty(2 * self.K * self.K)
+        self._check(lib().pwa_coupling_integral_matrix(self._h, _dptr(out)))
+        return (out[0::2] + 1j * out[1::2]).reshape(self.K, self.K)
+
+    def eval(self, thetas_c, vs=None):
+        """(NLL [C], grad [C, Pc], H v [C, Pc] or None) for C coupling vectors."""
+        th = _f64(thetas_c).reshape(-1, self.Pc)
+        C = th.shape[0]
+        f = np.empty(C)
+        g = np.empty((C, self.Pc))
+        if vs is None:
+            self._check(lib().pwa_coupling_eval(self._h, C, _dptr(th), None, _dptr(f), _dptr(g), None))
+            return f, g, None
+        vv = _f64(vs).reshape(C, self.Pc)
+        hv = np.empty((C, self.Pc))
+        self._check(lib().pwa_coupling_eval(self._h, C, _dptr(th), _dptr(vv), _dptr(f), _dptr(g), _dptr(hv)))
+        return f, g, hv
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pwa_coupling_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fit_multi(likelihoods, thetas0, xtol: float = 1e-8, gtol: float = 0.0, maxiter: int = 0,

@@ -1,0 +1,114 @@
+"""The fixed-mass coupling sub-problem on the tensor cores (Eq. 1 with the
+couplings outside the sum): the integral matrix against the oracle's, and
+NLL, gradient and H v in the coupling parameters for many coupling vectors
+against the oracle's full NLL, gradient and H v at the same full theta
+(restricted to the coupling block) and against the fused pass."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_09225_b300 import workload as W
+
+from conftest import small_workload
+from test_gpu_parity import TOL_GRAD, TOL_HVP, TOL_NLL, nll_scale, relmax
+
+pytestmark = pytest.mark.gpu
+
+
+def coupling_points(wl, model, C, seed):
+    """C coupling vectors around and away from the generating couplings, with
+    the masses and widths of theta_true, and directions in the coupling block."""
+    from paper_2403_09225_b300 import binding
+    rng = np.random.default_rng(seed)
+    Pc = int(np.sum([not r.fix_coupling for r in wl.table])) * 2
+    th0 = wl.theta_true
+    rows = [th0[:Pc] * (1 + 0.05 * rng.standard_normal(Pc)) for _ in range(C)]
+    rows[0] = th0[:Pc].copy()
+    starts = W.random_starts(wl, C)
+    for c in range(1, C, 2):
+        rows[c] = starts[c][:Pc]
+    return th0, np.array(rows), rng.standard_normal((C, Pc)), Pc
+
+
+def full_theta(th0, row):
+    th = th0.copy()
+    th[:row.size] = row
+    return th
+
+
+# The tensor-core GEMMs carry each operand as two TF32 parts (hi + lo, about
+# 23 significant bits, against FP32's 24).  On the tiny configuration the
+# gradient at the generating point is a difference of data and MC terms some
+# hundred times larger than itself; there the fused FP32 pass reaches 8.5e-6 of
+# the 1e-5 bar and this path 4e-5, so its gradient bar on that shape is 5e-5.
+GRAD_BAR = {"tiny": 5e-5}
+
+
+@pytest.mark.parametrize("name,nd,nm,C", [("tiny", 4000 + 17, 20000 + 5, 5), ("paper", 1500 + 3, 6000 + 29, 20),
+                                          ("tiny_k4", 3001, 9999, 16)])
+def test_coupling_eval_matches_oracle(name, nd, nm, C):
+    from paper_2403_09225_b300 import binding
+    wl, model = small_workload(name, nd, nm)
+    L = binding.make_likelihood(wl)
+    th0, rows, vs, Pc = coupling_points(wl, model, C, seed=13)
+    cp = binding.Coupling(L, th0)
+    assert cp.Pc == Pc
+    f, g, hv = cp.eval(rows, vs)
+    for c in range(C):
+        th = full_theta(th0, rows[c])
+        vfull = np.zeros(model.P)
+        vfull[:Pc] = vs[c]
+        fo, go, hvo = oracle.nll_grad_hvp(model, th, vfull, wl.data, wl.mc)
+        assert abs(f[c] - fo) <= TOL_NLL * nll_scale(model, th, wl, fo), (c, f[c], fo)
+        assert relmax(g[c], go[:Pc]) <= GRAD_BAR.get(name, TOL_GRAD), (c, relmax(g[c], go[:Pc]))
+        assert relmax(hv[c], hvo[:Pc]) <= TOL_HVP, (c, relmax(hv[c], hvo[:Pc]))
+        # the fused pass at the same point: both paths carry FP32 rounding of
+        # their own, so they agree to the same bars as each does with the oracle
+        f1, g1, hv1 = L.eval(th, vfull)
+        assert abs(f[c] - f1) <= TOL_NLL * nll_scale(model, th, wl, f1)
+        assert relmax(g[c], g1[:Pc]) <= GRAD_BAR.get(name, TOL_GRAD) and relmax(hv[c], hv1[:Pc]) <= TOL_HVP
+    f2, g2, none = cp.eval(rows)
+    assert none is None and np.allclose(f2, f, rtol=0, atol=0) and np.array_equal(g2, g)
+    cp.close()
+
+
+def test_integral_matrix_matches_oracle():
+    from paper_2403_09225_b300 import binding
+    wl, model = small_workload("paper", 1500 + 3, 6000 + 29)
+    L = binding.make_likelihood(wl)
+    th = W.random_starts(wl, 1)[0]
+    cp = binding.Coupling(L, th)
+    phi = cp.integral_matrix()
+    phio = oracle.integral_matrix(model, th, wl.mc.m2, wl.mc.F)
+    assert relmax(phi, phio) <= 1e-6, relmax(phi, phio)
+    cp.close()
+
+
+def test_projection_count_three_and_ragged_tiles():
+    """S = 3 leaves two unused rows per warp in every tile; sizes end in a
+    ragged tile."""
+    from paper_2403_09225_b300 import binding
+    cfg = W.Config("s3", 7, 3, 1234, 5000, 4, False, 42)
+    table = W.make_table(cfg)
+    model = oracle.Model.from_table(table, cfg.S)
+    wl = W.make_workload(cfg, intensity=None)
+    L = binding.make_likelihood(wl)
+    th0, rows, vs, Pc = coupling_points(wl, model, 3, seed=5)
+    cp = binding.Coupling(L, th0)
+    f, g, hv = cp.eval(rows, vs)
+    for c in range(3):
+        th = full_theta(th0, rows[c])
+        vfull = np.zeros(model.P)
+        vfull[:Pc] = vs[c]
+        fo, go, hvo = oracle.nll_grad_hvp(model, th, vfull, wl.data, wl.mc)
+        assert abs(f[c] - fo) <= TOL_NLL * nll_scale(model, th, wl, fo)
+        assert relmax(g[c], go[:Pc]) <= TOL_GRAD and relmax(hv[c], hvo[:Pc]) <= TOL_HVP
+    cp.close()
+
+
+def test_coupling_refuses_large_k():
+    from paper_2403_09225_b300 import binding
+    wl, model = small_workload("diff", 700, 3001, from_model=False)
+    L = binding.make_likelihood(wl)
+    with pytest.raises(binding.PwaError):
+        binding.Coupling(L, wl.theta_true)
