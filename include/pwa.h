@@ -289,6 +289,15 @@ pwa_status pwa_coupling_integral_matrix(const pwa_coupling* cp, double* phi);
 pwa_status pwa_coupling_eval(pwa_coupling* cp, int C, const double* theta_c, const double* v,
                              double* nll, double* grad, double* hv);
 
+/* Newton-CG fits in the coupling parameters alone (masses and widths fixed),
+ * C of them in lockstep: every round of likelihood requests is one call of the
+ * tensor-core evaluation above.  The iteration is that of pwa_newton_cg_fit
+ * (host-side CG as in pwa_newton_cg_fit_batch).  theta_c0, theta_c_out: host
+ * [C][Pc] (may alias); results: host [C] or NULL.  Returns as
+ * pwa_newton_cg_fit_batch. */
+pwa_status pwa_coupling_fit(pwa_coupling* cp, int C, const double* theta_c0, const pwa_fit_opts* opts,
+                            double* theta_c_out, pwa_fit_result* results);
+
 void pwa_coupling_destroy(pwa_coupling* cp);
 
 /* Default options: xtol 1e-8, gtol 0, maxiter 0 (= 200 P), cg_maxiter 0

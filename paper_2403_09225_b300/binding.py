@@ -56,7 +56,7 @@ EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "
            "pwa_eval", "pwa_eval_device", "pwa_eval_device_noalloc", "pwa_eval_batch", "pwa_eval_batch_device",
            "pwa_sync", "pwa_event_intensity", "pwa_newton_cg_fit", "pwa_newton_cg_fit_batch",
            "pwa_newton_cg_fit_multi", "pwa_autotune", "pwa_coupling_create", "pwa_coupling_num_params",
-           "pwa_coupling_integral_matrix", "pwa_coupling_eval", "pwa_coupling_destroy",
+           "pwa_coupling_integral_matrix", "pwa_coupling_eval", "pwa_coupling_fit", "pwa_coupling_destroy",
            "pwa_fit_opts_default", "pwa_set_stream", "pwa_set_tiling", "pwa_get_tiling",
            "pwa_selftest_bounded_wait", "pwa_last_error", "pwa_destroy")
 
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pwa_coupling_num_params": (i, [vp]),
         "pwa_coupling_integral_matrix": (st, [vp, dp]),
         "pwa_coupling_eval": (st, [vp, i, dp, dp, dp, dp, dp]),
+        "pwa_coupling_fit": (st, [vp, i, dp, ctypes.POINTER(pwa_fit_opts), dp, ctypes.POINTER(pwa_fit_result)]),
         "pwa_coupling_destroy": (None, [vp]),
         "pwa_fit_opts_default": (None, [ctypes.POINTER(pwa_fit_opts)]),
         "pwa_set_stream": (st, [H, vp]),
@@ -378,6 +379,21 @@ class Coupling:
         hv = np.empty((C, self.Pc))
         self._check(lib().pwa_coupling_eval(self._h, C, _dptr(th), _dptr(vv), _dptr(f), _dptr(g), _dptr(hv)))
         return f, g, hv
+
+    def fit(self, thetas_c0, xtol: float = 1e-8, gtol: float = 0.0, maxiter: int = 0, cg_maxiter: int = 0,
+            time_limit_s: float = 0.0):
+        """C coupling-only fits in lockstep; returns (theta_c [C, Pc], infos, all converged)."""
+        th = _f64(thetas_c0).reshape(-1, self.Pc)
+        C = th.shape[0]
+        out = np.empty((C, self.Pc))
+        opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s)
+        res = (pwa_fit_result * C)()
+        st = lib().pwa_coupling_fit(self._h, C, _dptr(th), ctypes.byref(opts), _dptr(out), res)
+        if st not in (PWA_OK, PWA_ENOCONV):
+            self._check(st)
+        infos = [{"nll": r.nll, "grad_max": r.grad_max, "iters": r.iters, "n_hvp": r.n_hvp, "n_fev": r.n_fev,
+                  "status": FIT_STATUS_NAMES[r.status], "elapsed_s": r.elapsed_s} for r in res]
+        return out, infos, st == PWA_OK
 
     def close(self):
         if getattr(self, "_h", None):

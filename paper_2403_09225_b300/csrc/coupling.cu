@@ -870,34 +870,23 @@ pwa_status pwa_coupling_eval(pwa_coupling* cp, int C, const double* theta_c, con
     h->err.clear();
     if (C < 1 || !theta_c || !nll) return pwa::set_error(h, PWA_EINVAL, "C >= 1, theta_c and nll are required");
     if (hv && !v_c) return pwa::set_error(h, PWA_EINVAL, "v is required for hv");
-    if (h->broken) return pwa::set_error(h, PWA_ETIMEOUT, "handle is unusable after a device-side timeout");
     const int Pc = cp->Pc;
     for (size_t i = 0; i < (size_t)C * Pc; ++i)
         if (!std::isfinite(theta_c[i]) || (v_c && !std::isfinite(v_c[i])))
             return pwa::set_error(h, PWA_EINVAL, "theta_c and v must be finite");
-    for (int c0 = 0; c0 < C; c0 += kCV) {
-        const int nv = std::min(kCV, C - c0);
-        pwa_status st = cp_launch(cp, nv, theta_c + (size_t)c0 * Pc, v_c ? v_c + (size_t)c0 * Pc : nullptr);
-        if (st != PWA_OK) return st;
-        const size_t ow = (size_t)nv * (1 + 2 * Pc);
-        double* res = cp->h_pin;
-        int* errw = reinterpret_cast<int*>(cp->h_pin + (size_t)kCV * (1 + 2 * Pc));
-        cudaError_t e = cudaMemcpyAsync(res, cp->d_out, sizeof(double) * ow, cudaMemcpyDeviceToHost, h->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(errw, cp->d_err, sizeof(int) * (1 + kCV), cudaMemcpyDeviceToHost, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        if (e != cudaSuccess) return pwa::cuda_error(h, e, "coupling results");
-        if (errw[0] & pwa::ERR_TIMEOUT) {
-            h->broken = true;
-            return pwa::set_error(h, PWA_ETIMEOUT, "a coupling tile or MMA did not complete within the wait limit");
-        }
-        if (errw[0]) return pwa::set_error(h, PWA_ENONFINITE, "non-finite or non-positive data intensity");
-        for (int c = 0; c < nv; ++c) {
-            const double* r = res + (size_t)c * (1 + 2 * Pc);
-            nll[c0 + c] = r[0];
-            if (grad) std::memcpy(grad + (size_t)(c0 + c) * Pc, r + 1, sizeof(double) * Pc);
-            if (hv) std::memcpy(hv + (size_t)(c0 + c) * Pc, r + 1 + Pc, sizeof(double) * Pc);
-        }
+    std::vector<double> res((size_t)C * (1 + 2 * Pc));
+    std::vector<int> errw(C);
+    pwa_status st = pwa::coupling_eval_rows(cp, C, theta_c, v_c, res.data(), errw.data());
+    if (st != PWA_OK) return st;
+    for (int c = 0; c < C; ++c)
+        if (errw[c])
+            return pwa::set_error(h, PWA_ENONFINITE, "coupling vector " + std::to_string(c) +
+                                                         ": non-finite or non-positive data intensity");
+    for (int c = 0; c < C; ++c) {
+        const double* r = res.data() + (size_t)c * (1 + 2 * Pc);
+        nll[c] = r[0];
+        if (grad) std::memcpy(grad + (size_t)c * Pc, r + 1, sizeof(double) * Pc);
+        if (hv) std::memcpy(hv + (size_t)c * Pc, r + 1 + Pc, sizeof(double) * Pc);
     }
     return PWA_OK;
 }
@@ -915,3 +904,34 @@ void pwa_coupling_destroy(pwa_coupling* cp)
 }
 
 }  // extern "C"
+
+namespace pwa {
+
+pwa_handle* coupling_handle(const pwa_coupling* cp) { return cp->h; }
+
+pwa_status coupling_eval_rows(pwa_coupling* cp, int nb, const double* theta, const double* v, double* out, int* errw)
+{
+    pwa_handle* h = cp->h;
+    if (h->broken) return set_error(h, PWA_ETIMEOUT, "handle is unusable after a device-side timeout");
+    const int Pc = cp->Pc;
+    for (int c0 = 0; c0 < nb; c0 += kCV) {
+        const int nv = std::min(kCV, nb - c0);
+        pwa_status st = cp_launch(cp, nv, theta + (size_t)c0 * Pc, v ? v + (size_t)c0 * Pc : nullptr);
+        if (st != PWA_OK) return st;
+        const size_t ow = (size_t)nv * (1 + 2 * Pc);
+        int* ew = reinterpret_cast<int*>(cp->h_pin + (size_t)kCV * (1 + 2 * Pc));
+        cudaError_t e = cudaMemcpyAsync(cp->h_pin, cp->d_out, sizeof(double) * ow, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ew, cp->d_err, sizeof(int) * (1 + kCV), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_error(h, e, "coupling results");
+        if (ew[0] & ERR_TIMEOUT) {
+            h->broken = true;
+            return set_error(h, PWA_ETIMEOUT, "a coupling tile or MMA did not complete within the wait limit");
+        }
+        std::memcpy(out + (size_t)c0 * (1 + 2 * Pc), cp->h_pin, sizeof(double) * ow);
+        for (int c = 0; c < nv; ++c) errw[c0 + c] = ew[1 + c];
+    }
+    return PWA_OK;
+}
+
+}  // namespace pwa

@@ -520,9 +520,8 @@ FitTask newton_cg(FitState& s)
     s.iters = k;
 }
 
-void init_state(FitState& s, const pwa_handle* h, const double* theta0, const pwa_fit_opts* opts_in)
+void init_state(FitState& s, int n, const double* theta0, const pwa_fit_opts* opts_in)
 {
-    const int n = h->P;
     s.P = n;
     pwa_fit_opts_default(&s.o);
     if (opts_in) s.o = *opts_in;
@@ -583,109 +582,184 @@ struct FitStream {
 };
 
 // ---------------------------------------------------------------------------
-// lockstep executor: groups of fits, one group per handle (model and events);
-// every round issues one batched pass per group, each on its group's private
-// stream so that the groups' kernels run concurrently, then resumes every fit
+// lockstep executor: groups of fits, one group per evaluator (a handle's
+// batched pass, or a coupling object); every round issues each group's
+// requests (one batched evaluation per group, the groups on their own streams
+// so that their kernels run concurrently), then resumes every fit
 // ---------------------------------------------------------------------------
 
+// One batched evaluation per round: rows theta [nb][P] (and v [nb][P] when any
+// request wants H v; zero rows for the others) -> rows (f, g[P], Hv[P]) and a
+// per-row non-finite flag.
+struct RoundEvaluator {
+    virtual ~RoundEvaluator() = default;
+    virtual int P() const = 0;
+    virtual pwa_handle* handle() const = 0;
+    // staging for nb rows: theta, v (pinned where the evaluator copies from)
+    virtual pwa_status reserve(int nb, double** theta, double** v) = 0;
+    virtual pwa_status issue(int nb, bool any_hv) = 0;                      // asynchronous
+    virtual pwa_status finish(int nb, const double** out, const int** err) = 0;  // waits
+};
+
+// a likelihood handle: pwa_eval_batch_device's pass on the handle's batch buffers
+struct HandleRounds final : RoundEvaluator {
+    pwa_handle* h;
+    explicit HandleRounds(pwa_handle* hh) : h(hh) {}
+    int P() const override { return h->P; }
+    pwa_handle* handle() const override { return h; }
+    pwa_status reserve(int nb, double** theta, double** v) override
+    {
+        pwa_status st = pwa::batch_io(h, nb);
+        if (st != PWA_OK) return st;
+        *theta = h->batch.h_io;
+        *v = h->batch.h_io + (size_t)nb * h->P;
+        return PWA_OK;
+    }
+    pwa_status issue(int nb, bool any_hv) override
+    {
+        pwa::BatchState& bs = h->batch;
+        const size_t BP = (size_t)nb * h->P;
+        const size_t ow = (size_t)nb * (1 + 2 * (size_t)h->P);
+        double* pin = bs.h_io;
+        double* d_th = bs.d_io;
+        cudaError_t e = cudaMemcpyAsync(d_th, pin, sizeof(double) * (any_hv ? 2 * BP : BP), cudaMemcpyHostToDevice,
+                                        h->stream);
+        if (e != cudaSuccess) return pwa::cuda_error(h, e, "batch upload");
+        pwa_status st = pwa::launch_batch(h, nb, d_th, any_hv ? bs.d_io + BP : nullptr, bs.d_io + 2 * BP,
+                                          any_hv ? pwa::MODE_HVP : pwa::MODE_GRAD, true);
+        if (st != PWA_OK) return st;
+        int* errw = reinterpret_cast<int*>(pin + 2 * BP + ow);  // [nb] per-vector words, then the shared one
+        e = cudaMemcpyAsync(pin + 2 * BP, bs.d_io + 2 * BP, sizeof(double) * ow, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(errw, bs.d_err_vec, sizeof(int) * nb, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(errw + nb, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+        if (e != cudaSuccess) return pwa::cuda_error(h, e, "batch download");
+        return PWA_OK;
+    }
+    pwa_status finish(int nb, const double** out, const int** err) override
+    {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return pwa::cuda_error(h, e, "batch round");
+        const size_t BP = (size_t)nb * h->P;
+        const size_t ow = (size_t)nb * (1 + 2 * (size_t)h->P);
+        double* pin = h->batch.h_io;
+        const int* errw = reinterpret_cast<const int*>(pin + 2 * BP + ow);
+        if (errw[nb]) {
+            // the shared error word: a timeout ends everything; non-finite
+            // intensities are attributed to their vectors by the per-vector words
+            pwa_status st = pwa::check_device_errors(h);
+            if (st != PWA_OK && st != PWA_ENONFINITE) return st;
+            h->err.clear();
+        }
+        *out = pin + 2 * BP;
+        *err = errw;
+        return PWA_OK;
+    }
+};
+
+// a coupling object: its tensor-core evaluation (synchronous, 16 rows per launch)
+struct CouplingRounds final : RoundEvaluator {
+    pwa_coupling* cp;
+    pwa_handle* h;
+    int Pc;
+    std::vector<double> th, vv, res;
+    std::vector<int> errw;
+    CouplingRounds(pwa_coupling* c, pwa_handle* hh, int pc) : cp(c), h(hh), Pc(pc) {}
+    int P() const override { return Pc; }
+    pwa_handle* handle() const override { return h; }
+    pwa_status reserve(int nb, double** theta, double** v) override
+    {
+        th.resize((size_t)nb * Pc);
+        vv.resize((size_t)nb * Pc);
+        *theta = th.data();
+        *v = vv.data();
+        return PWA_OK;
+    }
+    pwa_status issue(int nb, bool any_hv) override
+    {
+        res.resize((size_t)nb * (1 + 2 * Pc));
+        errw.resize(nb);
+        return pwa::coupling_eval_rows(cp, nb, th.data(), any_hv ? vv.data() : nullptr, res.data(), errw.data());
+    }
+    pwa_status finish(int nb, const double** out, const int** err) override
+    {
+        (void)nb;
+        *out = res.data();
+        *err = errw.data();
+        return PWA_OK;
+    }
+};
+
 struct FitGroup {
-    pwa_handle* h = nullptr;
-    int B = 0;
+    std::unique_ptr<RoundEvaluator> ev;
+    int B = 0, P = 0;
     FitStream fs;
     std::vector<FitState> fits;
     std::vector<FitTask> tasks;
     std::vector<int> live;
     std::vector<double> zero;
-    bool any_hv = false;
-    int* errw = nullptr;
-    double* res = nullptr;
 };
 
-pwa_status open_group(FitGroup& g, pwa_handle* h, int B, const double* theta0, const pwa_fit_opts* opts)
+pwa_status open_group(FitGroup& g, std::unique_ptr<RoundEvaluator> ev, int B, const double* theta0,
+                      const pwa_fit_opts* opts)
 {
-    g.h = h;
+    pwa_handle* h = ev->handle();
+    g.ev = std::move(ev);
     g.B = B;
+    g.P = g.ev->P();
     h->err.clear();
     if (B < 1) return pwa::set_error(h, PWA_EINVAL, "B must be at least 1");
     if (!theta0) return pwa::set_error(h, PWA_EINVAL, "theta0 must not be NULL");
-    const int P = h->P;
+    const int P = g.P;
     for (size_t i = 0; i < (size_t)B * P; ++i)
         if (!std::isfinite(theta0[i])) return pwa::set_error(h, PWA_EINVAL, "theta0 must be finite");
     pwa_status st = g.fs.open(h);
-    if (st != PWA_OK) return st;
-    st = pwa::batch_io(h, B);
     if (st != PWA_OK) return st;
     g.zero.assign(P, 0.0);
     g.fits.resize(B);
     g.tasks.reserve(B);
     for (int b = 0; b < B; ++b) {
-        init_state(g.fits[b], h, theta0 + (size_t)b * P, opts);
+        init_state(g.fits[b], P, theta0 + (size_t)b * P, opts);
         g.tasks.push_back(newton_cg(g.fits[b]));
         g.tasks[b].h.resume();  // runs to its first request
     }
     return PWA_OK;
 }
 
-// Enqueue the group's round: its unfinished fits' requests as one batched pass
-// (HVP mode when any asks for H v, with v = 0 for the f, g requests).
+// Enqueue the group's round: its unfinished fits' requests as one batched
+// evaluation (H v for all when any asks for it, with v = 0 for the f, g requests).
 pwa_status issue_round(FitGroup& g)
 {
     g.live.clear();
     for (int b = 0; b < g.B; ++b)
         if (!g.tasks[b].h.done()) g.live.push_back(b);
     if (g.live.empty()) return PWA_OK;
-    pwa_handle* h = g.h;
-    const int P = h->P, nb = (int)g.live.size();
-    g.any_hv = false;
-    for (int b : g.live) g.any_hv |= g.fits[b].req == Req::HV;
-    pwa::BatchState& bs = h->batch;
-    const size_t BP = (size_t)nb * P;
-    double* pin = bs.h_io;
+    const int P = g.P, nb = (int)g.live.size();
+    bool any_hv = false;
+    for (int b : g.live) any_hv |= g.fits[b].req == Req::HV;
+    double *th = nullptr, *v = nullptr;
+    pwa_status st = g.ev->reserve(nb, &th, &v);
+    if (st != PWA_OK) return st;
     for (int i = 0; i < nb; ++i) {
         const FitState& s = g.fits[g.live[i]];
-        std::memcpy(pin + (size_t)i * P, s.rx, sizeof(double) * P);
-        if (g.any_hv)
-            std::memcpy(pin + BP + (size_t)i * P, s.req == Req::HV ? s.rv : g.zero.data(), sizeof(double) * P);
+        std::memcpy(th + (size_t)i * P, s.rx, sizeof(double) * P);
+        if (any_hv) std::memcpy(v + (size_t)i * P, s.req == Req::HV ? s.rv : g.zero.data(), sizeof(double) * P);
     }
-    double* d_th = bs.d_io;
-    double* d_v = bs.d_io + BP;
-    double* d_out = bs.d_io + 2 * BP;
-    const size_t ow = (size_t)nb * (1 + 2 * (size_t)P);
-    g.res = pin + 2 * BP;
-    g.errw = reinterpret_cast<int*>(pin + 2 * BP + ow);  // [nb] per-vector words, then the shared one
-    cudaError_t e = cudaMemcpyAsync(d_th, pin, sizeof(double) * (g.any_hv ? 2 * BP : BP), cudaMemcpyHostToDevice,
-                                    h->stream);
-    if (e != cudaSuccess) return pwa::cuda_error(h, e, "batch upload");
-    pwa_status st = pwa::launch_batch(h, nb, d_th, g.any_hv ? d_v : nullptr, d_out,
-                                      g.any_hv ? pwa::MODE_HVP : pwa::MODE_GRAD, true);
-    if (st != PWA_OK) return st;
-    e = cudaMemcpyAsync(g.res, d_out, sizeof(double) * ow, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(g.errw, bs.d_err_vec, sizeof(int) * nb, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(g.errw + nb, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
-    if (e != cudaSuccess) return pwa::cuda_error(h, e, "batch download");
-    return PWA_OK;
+    return g.ev->issue(nb, any_hv);
 }
 
 // Wait for the group's round and resume its fits with their results.
 pwa_status finish_round(FitGroup& g)
 {
     if (g.live.empty()) return PWA_OK;
-    pwa_handle* h = g.h;
-    const int P = h->P, nb = (int)g.live.size();
-    cudaError_t e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return pwa::cuda_error(h, e, "batch round");
-    if (g.errw[nb]) {
-        // the shared error word: a timeout ends everything; non-finite
-        // intensities are attributed to their vectors by the per-vector words
-        pwa_status st = pwa::check_device_errors(h);
-        if (st != PWA_OK && st != PWA_ENONFINITE) return st;
-        h->err.clear();
-    }
+    const int P = g.P, nb = (int)g.live.size();
+    const double* res = nullptr;
+    const int* errw = nullptr;
+    pwa_status st = g.ev->finish(nb, &res, &errw);
+    if (st != PWA_OK) return st;
     for (int i = 0; i < nb; ++i) {
         FitState& s = g.fits[g.live[i]];
-        const double* r = g.res + (size_t)i * (1 + 2 * P);
-        s.req_status = g.errw[i] ? PWA_ENONFINITE : PWA_OK;
+        const double* r = res + (size_t)i * (1 + 2 * P);
+        s.req_status = errw[i] ? PWA_ENONFINITE : PWA_OK;
         if (s.req == Req::FG) {
             ++s.n_fev;
             *s.rf = r[0];
@@ -716,12 +790,12 @@ pwa_status run_lockstep(std::vector<std::unique_ptr<FitGroup>>& groups)
     }
 }
 
-// Results of a group; true when every fit converged or hit its time limit.
+// Results of a group; all_ok stays true when every fit converged or hit its time limit.
 pwa_status close_group(FitGroup& g, double* theta_out, pwa_fit_result* results, bool& all_ok)
 {
-    const int P = g.h->P;
+    const int P = g.P;
     for (int b = 0; b < g.B; ++b)
-        if (g.tasks[b].failed()) return pwa::set_error(g.h, PWA_ENOMEM, "host exception in a fit");
+        if (g.tasks[b].failed()) return pwa::set_error(g.ev->handle(), PWA_ENOMEM, "host exception in a fit");
     for (int b = 0; b < g.B; ++b) {
         std::memcpy(theta_out + (size_t)b * P, g.fits[b].x.data(), sizeof(double) * P);
         if (results) fill_result(g.fits[b], results + b);
@@ -748,7 +822,7 @@ extern "C" pwa_status pwa_newton_cg_fit(pwa_handle* h, const double* theta0, con
     if (!h) return PWA_EINVAL;
     if (!theta0 || !theta_out) return pwa::set_error(h, PWA_EINVAL, "theta0 and theta_out must not be NULL");
     FitState s;
-    init_state(s, h, theta0, opts_in);
+    init_state(s, h->P, theta0, opts_in);
     s.device_cg = true;
     FitStream fs;
     pwa_status st = fs.open(h);
@@ -810,7 +884,7 @@ extern "C" pwa_status pwa_newton_cg_fit_multi(int n_handles, pwa_handle* const* 
     std::vector<std::unique_ptr<FitGroup>> groups;
     for (int i = 0; i < n_handles; ++i) {
         groups.push_back(std::make_unique<FitGroup>());
-        pwa_status st = open_group(*groups.back(), handles[i], B[i], theta0[i], opts);
+        pwa_status st = open_group(*groups.back(), std::make_unique<HandleRounds>(handles[i]), B[i], theta0[i], opts);
         if (st != PWA_OK) return st;
     }
     pwa_status st = run_lockstep(groups);
@@ -820,5 +894,24 @@ extern "C" pwa_status pwa_newton_cg_fit_multi(int n_handles, pwa_handle* const* 
         st = close_group(*groups[i], theta_out[i], results ? results[i] : nullptr, all_ok);
         if (st != PWA_OK) return st;
     }
+    return all_ok ? PWA_OK : PWA_ENOCONV;
+}
+
+extern "C" pwa_status pwa_coupling_fit(pwa_coupling* cp, int C, const double* theta_c0, const pwa_fit_opts* opts,
+                                       double* theta_c_out, pwa_fit_result* results)
+{
+    if (!cp) return PWA_EINVAL;
+    pwa_handle* h = pwa::coupling_handle(cp);
+    if (!theta_c_out) return pwa::set_error(h, PWA_EINVAL, "theta_c_out must not be NULL");
+    std::vector<std::unique_ptr<FitGroup>> groups;
+    groups.push_back(std::make_unique<FitGroup>());
+    pwa_status st = open_group(*groups.back(), std::make_unique<CouplingRounds>(cp, h, pwa_coupling_num_params(cp)), C,
+                               theta_c0, opts);
+    if (st != PWA_OK) return st;
+    st = run_lockstep(groups);
+    if (st != PWA_OK) return st;
+    bool all_ok = true;
+    st = close_group(*groups[0], theta_c_out, results, all_ok);
+    if (st != PWA_OK) return st;
     return all_ok ? PWA_OK : PWA_ENOCONV;
 }

@@ -115,6 +115,11 @@ pwa_status launch_batch(pwa_handle* h, int B, const double* d_theta, const doubl
 // Device I/O buffers of the batch state for B vectors (grown when needed).
 pwa_status batch_io(pwa_handle* h, int B);
 void free_batch(pwa_handle* h);
+// Coupling sub-problem rows for the lockstep fits: theta, v [nb][Pc] (v may be
+// null) -> out [nb][1 + 2Pc] (f, g, Hv) and per-row non-finite flags; synchronous.
+pwa_status coupling_eval_rows(pwa_coupling* cp, int nb, const double* theta, const double* v, double* out,
+                              int* errw);
+pwa_handle* coupling_handle(const pwa_coupling* cp);
 // Read back and clear the device error flags; turns them into a status + message.
 pwa_status check_device_errors(pwa_handle* h);
 pwa_status set_error(pwa_handle* h, pwa_status st, const std::string& msg);

@@ -112,3 +112,42 @@ def test_coupling_refuses_large_k():
     L = binding.make_likelihood(wl)
     with pytest.raises(binding.PwaError):
         binding.Coupling(L, wl.theta_true)
+
+
+@pytest.mark.parametrize("name,nd,nm", [("tiny_k4", 3001, 9999), ("paper", 1500 + 3, 6000 + 29)])
+def test_coupling_fit_reaches_the_oracle_coupling_minimum(name, nd, nm):
+    """Coupling-only fits (masses and widths fixed at theta_true) from starts
+    scattered around the generating couplings all converge to the minimum the
+    oracle's textbook Newton-CG finds over the same coupling parameters, within
+    1e-3 of the oracle's errors of those parameters."""
+    from oracle import newton_cg as ncg
+    from paper_2403_09225_b300 import binding
+    wl, model = small_workload(name, nd, nm)
+    th0 = wl.theta_true
+    Pc = int(np.sum([not r.fix_coupling for r in wl.table])) * 2
+    full = lambda xc: full_theta(th0, xc)
+
+    def fg(xc):
+        f, g = oracle.nll_grad(model, full(xc), wl.data, wl.mc)
+        return f, g[:Pc]
+
+    def hp(xc, v):
+        vf = np.zeros(model.P)
+        vf[:Pc] = v
+        return oracle.nll_grad_hvp(model, full(xc), vf, wl.data, wl.mc)[2][:Pc]
+
+    rng = np.random.default_rng(17)
+    starts = th0[:Pc] * (1 + 0.02 * rng.standard_normal((4, Pc)))
+    ref = ncg.newton_cg(fg, hp, starts[0], xtol=1e-10, maxiter=200)
+    assert ref.status in ncg.CONVERGED, ref.status_name
+    H = oracle.hessian(model, full(ref.x), wl.data, wl.mc)[:Pc, :Pc]
+    sig = oracle.parameter_errors(H)
+    L = binding.make_likelihood(wl)
+    cp = binding.Coupling(L, th0)
+    xs, infos, ok = cp.fit(starts, xtol=1e-10)
+    assert ok, infos
+    for b in range(len(starts)):
+        d = oracle.canonical(model, full(xs[b]))[:Pc] - oracle.canonical(model, full(ref.x))[:Pc]
+        assert np.max(np.abs(d / sig)) <= 1e-3, (b, np.max(np.abs(d / sig)), infos[b])
+        assert abs(infos[b]["nll"] - ref.fun) <= 1e-6 * abs(ref.fun)
+    cp.close()
