@@ -49,6 +49,16 @@ def peaks():
         return 6400.0, "fallback"
 
 
+def tf32_peak():
+    """Dense TF32 tensor peak: the measured bf16 figure times the nominal
+    tf32 / bf16 ratio (1.1 / 2.25 PFLOP/s), or the fallback bf16 figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]) * (1.1 / 2.25), "measured bf16 x nominal tf32/bf16"
+    except Exception:
+        return 1800.0 * (1.1 / 2.25), "fallback bf16 x nominal tf32/bf16"
+
+
 def bytes_per_pass(nd, nm, K, S):
     """Algorithmic HBM bytes of one pass: F (8 S bytes per event-amplitude),
     three m^2 values per event, one weight per data event."""
@@ -285,6 +295,49 @@ def batching_metric(n_toys: int, n_starts: int, time_limit: float, seed: int = 7
             L.close()
 
 
+def coupling_metric(L, wl, reps: int = 20):
+    """The fixed-mass coupling sub-problem at the paper scale: NLL, gradient
+    and H v in the coupling parameters for 16 coupling vectors per call
+    (tcgen05 TF32-split GEMMs over U = BW F tiles of the data events plus the
+    K x K integral matrix for the MC term), against one fused pass per vector.
+    Times are host-synchronous calls (upload, launches, download)."""
+    from paper_2403_09225_b300 import binding
+    th0 = wl.theta_true
+    t0 = time.perf_counter()
+    cp = binding.Coupling(L, th0)
+    create_s = time.perf_counter() - t0
+    try:
+        rng = np.random.default_rng(3)
+        C = 16
+        rows = th0[:cp.Pc] * (1 + 0.05 * rng.standard_normal((C, cp.Pc)))
+        vs = rng.standard_normal((C, cp.Pc))
+        cp.eval(rows, vs)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            cp.eval(rows, vs)
+        ms = (time.perf_counter() - t0) / reps * 1e3
+        v = np.linspace(-1.0, 1.0, L.P)
+        L.eval(th0, v)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            L.eval(th0, v)
+        fused_ms = (time.perf_counter() - t0) / reps * 1e3
+        rows_per_call = wl.data.n * wl.S
+        # useful flops per (event, projection) row: two real GEMMs of 2K x 4C
+        flops = 2 * 2.0 * (2 * wl.K) * (4 * C) * rows_per_call
+        tpk, tkind = tf32_peak()
+        achieved = flops / (ms * 1e-3) / 1e12
+        return {"vectors_per_call": C, "ms_per_call": ms, "us_per_vector": ms * 1e3 / C,
+                "fused_pass_us_per_vector": fused_ms * 1e3, "speedup_per_vector": fused_ms * C / ms,
+                "create_s": create_s, "K": wl.K, "S": wl.S, "data_events": wl.data.n,
+                "roofline": {"bound": "tensor", "achieved": achieved, "unit": "TFLOP/s",
+                             "peak": tpk, "frac": achieved / tpk, "peak_kind": tkind,
+                             "flops_per_call": flops, "note": "useful flops of the two GEMMs; the TF32 "
+                             "three-term split issues 3x as many"}}
+    finally:
+        cp.close()
+
+
 def measured_traffic(tiling: dict):
     """DRAM bytes per launch of the fused HVP pass from the committed ncu
     summary, when it was taken with the tiling in use (else None)."""
@@ -327,6 +380,7 @@ def main():
     ap.add_argument("--fit-time-limit", type=float, default=10.0, help="seconds per fit (early stopping)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tiling", default="", help="warps,lanes_per_event,stages[,blocks_per_sm] (default: library's)")
+    ap.add_argument("--no-coupling", action="store_true", help="skip the fixed-mass coupling sub-problem leg")
     ap.add_argument("--batching", default="", metavar="TOYS,STARTS",
                     help="also run the uneven-size toy-fit comparison (plain vs batched), e.g. 12,4")
     ap.add_argument("--scale", type=float, default=1.0,
@@ -402,6 +456,10 @@ def main():
     if args.fits > 0 and rank == 0:
         fit = fit_metric(L, wl, args.fits, time_limit=args.fit_time_limit)
 
+    coupling = None
+    if rank == 0 and not args.no_coupling:
+        coupling = coupling_metric(L, wl)
+
     batching = None
     if args.batching and rank == 0:
         n_toys, n_starts = (int(x) for x in args.batching.split(","))
@@ -438,6 +496,8 @@ def main():
             res["fit"] = fit
         if batching is not None:
             res["batching"] = batching
+        if coupling is not None:
+            res["coupling"] = coupling
         print(json.dumps(res))
     L.close()
     if dist:
