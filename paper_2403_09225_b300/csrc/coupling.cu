@@ -12,15 +12,26 @@
 //    their directional derivatives) and, after the per-event weights
 //    a = w/I, b = w Idot/I^2, Q = W^T U (GEMM2, the adjoint sums of Eqs. 6-7
 //    contracted over the events).
-// Both GEMMs run on tcgen05 in kind::tf32 with the three-term split
-// (x = hi + lo, both rounded to TF32; a b ~ ahi bhi + ahi blo + alo bhi),
-// which keeps FP32-level accuracy; accumulators live in
-// tensor memory, the per-event epilogue in registers, cross-tile sums in
-// FP64.  Operands use the canonical K-major layout without swizzle: 8-row x
-// 16-byte core matrices, LBO = stride between cores along K, SBO = stride
-// between 8-row groups.  Operands written column-wise by the epilogue use a
-// 144-byte core stride along K (16 bytes of padding per core) so that the 32
-// threads of a warp hit 32 different banks.
+// Both GEMMs run on tcgen05 (kind::f16, BF16 operands, FP32 accumulation) with
+// every FP32 operand split into three BF16 parts, x = x0 + x1 + x2 (each the
+// nearest BF16 of what the previous parts leave), which represents it
+// exactly; a b is taken as the six products with i + j <= 2 (the others are
+// below FP32 resolution).  The x0 y0 products and the five correction products
+// go to separate accumulators in tensor memory (the tensor cores' FP32
+// accumulation of terms of very different size loses the small ones), and
+// GEMM2's are flushed every tile into compensated FP32 sums (TwoSum).  U is stored split, twice: once as GEMM1's A operand and once
+// transposed as GEMM2's B operand, so that a tile needs no conversion work.
+// Operands use the canonical K-major layout without swizzle: 8-row x 16-byte
+// core matrices (8 BF16 along K), LBO = stride between cores along K, SBO =
+// stride between 8-row groups.  The W operand, written column-wise by the
+// epilogue, uses a 144-byte core stride so that a warp's stores spread over
+// 32 banks.
+//
+// Pipeline of one CTA (8 warps, one per SM): GEMM1 of tile i + 1 runs while
+// the threads work on tile i (two GEMM1 accumulators); GEMM2 of tile i runs
+// while the next GEMM1 is waited for; U tiles and their transposed copies are
+// double-buffered and fetched by TMA bulk copies two tiles ahead.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,29 +45,38 @@
 namespace {
 
 constexpr int kCT = 256;        // threads per CTA: threads r and r + 128 share row r of a tile
-                                // (each takes half of the row's K-cores and of the vectors)
 constexpr int kRows = 128;      // (event, projection) rows per tile
 constexpr int kCV = 16;         // coupling vectors per launch
+constexpr int kCH = kCV / 2;    // vectors per thread
 constexpr int kN1 = 4 * kCV;    // GEMM1 columns: Re A, Im A, Re Adot, Im Adot of every vector
-constexpr uint32_t kLboT = 144; // core stride along K of the column-written operands
-constexpr uint32_t kSboT = 32 * kLboT;  // 8-row-group stride of those (32 cores of 4 rows)
-constexpr int kMaxK2p = 48;     // 2K rounded up to 8; bounded by shared memory (K <= 24)
-constexpr int kTmemCols = 256;  // D1 at column 0 (kN1 columns); GEMM2: hi x hi at column 64, the
-                                // correction terms at column 64 + K2p (K2p columns each)
+constexpr int kParts = 3;       // BF16 parts per FP32 operand
+constexpr uint32_t kLboW = 144; // core stride along K of the W operand (16 bytes of padding per core)
+constexpr uint32_t kSboW = (kRows / 8) * kLboW;  // its 8-row-group stride
+constexpr int kMaxK2p = 48;     // 2K rounded up to 16; bounded by shared memory (K <= 24)
+constexpr int kTmemCols = 512;  // GEMM1 x0 y0 (x 2 tiles) at 0 and 64, its corrections at 128 and 192;
+                                // GEMM2 x0 y0 in four accumulators (K steps ks mod 4) at 256 + 48 j,
+                                // its corrections at 448
+constexpr int kNBars = 8;       // tmaA[2], tmaB[2], mma1[2], mma2, spare
 
 struct CpArgs {
-    const float* U;       // [ntiles] tile records: kRows x K2p U values in the K-major core
-                          // layout, then Et data weights (0 past the last event), padded to 16 bytes
-    long long n;          // data events
+    const unsigned char* U;  // [ntiles] tile records (layout below)
+    long long n;             // data events
     int ntiles, K, S, K2p, EW, Et;
-    uint32_t tile_bytes;
-    int nst;              // U tiles in flight (2, or 1 when two do not fit in shared memory)
-    const float* gc;      // [kCV][K][4]: Re g, Im g, Re gdot, Im gdot
-    int nv;               // vectors in use (the others are zero and skipped)
-    double* rec;          // [grid][kN1 * K2p + kCV] FP64 partial sums per CTA (zeroed by the host)
-    int* err;             // [1 + kCV]: shared word, per-vector words
-    long long timeout;    // SM cycles per wait
+    uint32_t rec_bytes;      // bytes of one tile record
+    uint32_t a_bytes;        // split U (GEMM1 operand) + weights: the first TMA copy
+    uint32_t b_bytes;        // split transposed U (GEMM2 operand): the second TMA copy
+    const float* gc;         // [kCV][K][4]: Re g, Im g, Re gdot, Im gdot
+    int nv;                  // vectors in use (the others are zero and skipped)
+    double* rec;             // [grid][kN1 * K2p + kCV] FP64 partial sums per CTA
+    int* err;                // [1 + kCV]: shared word, per-vector words
+    long long timeout;       // SM cycles per wait
 };
+
+// Tile record: U parts [3][128 x K2p] (GEMM1 A: K-major, SBO = K2p / 8 * 128),
+// then the Et weights (padded to 16 bytes), then transposed U parts
+// [3][K2p x 128] (GEMM2 B: K-major, SBO = 128 / 8 * 128 = 2048).
+__host__ __device__ inline uint32_t part_bytes(int K2p) { return (uint32_t)kRows * K2p * 2; }
+__host__ __device__ inline uint32_t w_bytes(int Et) { return (uint32_t)((Et + 3) / 4) * 16; }
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
@@ -67,10 +87,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
            ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
 {
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
             d_tmem),
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
@@ -94,20 +114,27 @@ __device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&r)[8])
 }
 __device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// x rounded to the nearest TF32 value (10 mantissa bits; the low 13 bits cleared).
-// Both parts of a split x = hi + lo are rounded this way, so the tensor cores
-// read them exactly and the dropped remainder has no systematic sign.
-__device__ __forceinline__ float tf32_rn(float x)
+// x = x0 + x1 + x2 in BF16, each part the nearest BF16 of the remainder
+__host__ __device__ inline void split3(float x, __nv_bfloat16& b0, __nv_bfloat16& b1, __nv_bfloat16& b2)
 {
-    // adding half a unit of the 10th mantissa bit carries into the exponent
-    // when needed, which is round-half-away-from-zero on the magnitude
-    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+    b0 = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(b0);
+    b1 = __float2bfloat16_rn(r1);
+    b2 = __float2bfloat16_rn(r1 - __bfloat162float(b1));
 }
 
-// byte offset of element (row, col) in a K-major operand with 16-byte cores
-__device__ __forceinline__ uint32_t kmaj(int row, int col, uint32_t lbo, uint32_t sbo)
+// byte offset of element (row, col) of a K-major 16-bit operand
+__host__ __device__ inline uint32_t kmaj16(int row, int col, uint32_t lbo, uint32_t sbo)
 {
-    return (uint32_t)(row >> 3) * sbo + (uint32_t)(col >> 2) * lbo + (uint32_t)(row & 7) * 16 + (uint32_t)(col & 3) * 4;
+    return (uint32_t)(row >> 3) * sbo + (uint32_t)(col >> 3) * lbo + (uint32_t)(row & 7) * 16 + (uint32_t)(col & 7) * 2;
+}
+
+__device__ __forceinline__ void two_sum(float2& p, float x)
+{
+    const float sum = __fadd_rn(p.x, x);
+    const float bp = __fsub_rn(sum, p.x);
+    const float err = __fadd_rn(__fsub_rn(p.x, __fsub_rn(sum, bp)), __fsub_rn(x, bp));
+    p = make_float2(sum, __fadd_rn(p.y, err));
 }
 
 __global__ void __launch_bounds__(kCT, 1) coupling_kernel(const CpArgs a)
@@ -116,30 +143,28 @@ __global__ void __launch_bounds__(kCT, 1) coupling_kernel(const CpArgs a)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row = tid & (kRows - 1), half = tid >> 7, wq = warp & 3;  // wq: TMEM lane quarter
     const int K = a.K, S = a.S, K2p = a.K2p;
-    const uint32_t TB = a.tile_bytes;
-    const uint32_t sbo_u = (uint32_t)(K2p / 4) * 128;       // U and B1: 8-row-group stride
-    const uint32_t B1B = (uint32_t)kN1 * K2p * 4;
-    const uint32_t UTB = (uint32_t)(K2p / 8) * kSboT;
-    const uint32_t WTB = (uint32_t)(kN1 / 8) * kSboT;
-    const int NST = a.nst;
-    unsigned char* uraw[2] = {sm, sm + (NST - 1) * TB};
-    unsigned char* ulo = sm + NST * TB;
-    unsigned char* b1hi = ulo + TB;
-    unsigned char* b1lo = b1hi + B1B;
-    unsigned char* uthi = b1lo + B1B;
-    unsigned char* utlo = uthi + UTB;
-    unsigned char* wthi = utlo + UTB;
-    unsigned char* wtlo = wthi + WTB;
-    // per-CTA sums of the GEMM2 results as (hi, lo) FP32 pairs (TwoSum): rows n, stride K2p + 1 pairs
-    float2* acc = reinterpret_cast<float2*>(wtlo + WTB);
-    const int acc_stride = K2p + 1;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(acc + (size_t)kN1 * acc_stride);  // tma[2], mma1, mma2
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4);
+    const uint32_t PB = part_bytes(K2p);
+    const uint32_t sbo_a = (uint32_t)(K2p / 8) * 128;  // U parts and B1 parts: 8-row-group stride
+    const uint32_t sbo_t = (uint32_t)(kRows / 8) * 128; // transposed U parts
+    const uint32_t B1P = (uint32_t)kN1 * K2p * 2;       // one part of B1
+    const uint32_t WTP = (uint32_t)(kN1 / 8) * kSboW;   // one part of W
+    // shared memory: A stages [2] | B stages [2] | B1 parts | W parts | barriers
+    unsigned char* sA[2] = {sm, sm + a.a_bytes};
+    unsigned char* sB[2] = {sm + 2 * a.a_bytes, sm + 2 * a.a_bytes + a.b_bytes};
+    unsigned char* b1 = sm + 2 * a.a_bytes + 2 * a.b_bytes;
+    unsigned char* wt = b1 + kParts * B1P;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wt + kParts * WTP);
+    uint64_t *tmaA = bars, *tmaB = bars + 2, *mma1 = bars + 4, *mma2 = bars + 6;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + kNBars);
     __shared__ int s_abort;
-    __shared__ double s_red[kCT / 32][kCV / 2];
+    __shared__ double s_red[kCT / 32][kCH];
 
     const int G = gridDim.x;
-    // ---- GEMM1 B operand from the coupling vectors: row n, column kk of (2K | padding)
+    const int T = a.ntiles;
+    const int nmine = blockIdx.x < T ? (T - 1 - (int)blockIdx.x) / G + 1 : 0;  // tiles of this CTA
+    auto tile_of = [&](int i) { return (long long)blockIdx.x + (long long)i * G; };
+
+    // ---- GEMM1 B operand from the coupling vectors: row n, column kk of (2K | padding), 3 parts
     for (int i = tid; i < kN1 * K2p; i += kCT) {
         const int n = i / K2p, kk = i % K2p;
         const int blk = n / kCV, c = n % kCV;
@@ -151,22 +176,26 @@ __global__ void __launch_bounds__(kCT, 1) coupling_kernel(const CpArgs a)
             // Re part: Ur gr - Ui gi;  Im part: Ur gi + Ui gr
             v = (blk & 1) == 0 ? (kk < K ? gr : -gi) : (kk < K ? gi : gr);
         }
-        const float hi = tf32_rn(v);
-        const uint32_t off = kmaj(n, kk, 128, sbo_u);
-        *reinterpret_cast<float*>(b1hi + off) = hi;
-        *reinterpret_cast<float*>(b1lo + off) = tf32_rn(v - hi);
+        __nv_bfloat16 p0, p1, p2;
+        split3(v, p0, p1, p2);
+        const uint32_t off = kmaj16(n, kk, 128, sbo_a);
+        *reinterpret_cast<__nv_bfloat16*>(b1 + off) = p0;
+        *reinterpret_cast<__nv_bfloat16*>(b1 + B1P + off) = p1;
+        *reinterpret_cast<__nv_bfloat16*>(b1 + 2 * B1P + off) = p2;
     }
-    for (int i = tid; i < kN1 * acc_stride; i += kCT) acc[i] = make_float2(0.f, 0.f);
+    auto issue_A = [&](int i, int st) {
+        pwa::tma_load_tile(sA[st], a.U + (size_t)tile_of(i) * a.rec_bytes, a.a_bytes, &tmaA[st]);
+    };
+    auto issue_B = [&](int i, int st) {
+        pwa::tma_load_tile(sB[st], a.U + (size_t)tile_of(i) * a.rec_bytes + a.a_bytes, a.b_bytes, &tmaB[st]);
+    };
     if (tid == 0) {
         s_abort = 0;
-        for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(&bars[i])));
+        for (int i = 0; i < kNBars; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(&bars[i])));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int i = 0; i < NST; ++i) {
-            const long long t = blockIdx.x + (long long)i * G;
-            if (t < a.ntiles) {
-                pwa::tma_load_tile(uraw[i], reinterpret_cast<const unsigned char*>(a.U) + (size_t)t * TB, TB,
-                                   &bars[i]);
-            }
+        for (int i = 0; i < 2 && i < nmine; ++i) {
+            issue_A(i, i);
+            issue_B(i, i);
         }
     }
     if (warp == 0) {
@@ -180,20 +209,13 @@ __global__ void __launch_bounds__(kCT, 1) coupling_kernel(const CpArgs a)
     tc_fence_after();
     const uint32_t tm = *tslot;
     const uint32_t tm_lane = (uint32_t)(32 * wq) << 16;
-    // instruction descriptors: D f32, A/B tf32, both K-major, N >> 3, M >> 4
-    const uint32_t idesc1 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN1 >> 3) << 17) | ((128u >> 4) << 24);
-    const uint32_t idesc2 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(K2p >> 3) << 17) |
+    const uint32_t tD2 = tm + 256, tD2c = tm + 256 + 4 * kMaxK2p;
+    // instruction descriptors: D f32, A/B bf16, both K-major, N >> 3, M >> 4
+    const uint32_t idesc1 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN1 >> 3) << 17) | ((128u >> 4) << 24);
+    const uint32_t idesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(K2p >> 3) << 17) |
                             ((uint32_t)(kN1 >> 4) << 24);
 
-    // this thread's row: lane quarter wq, slot j of the quarter's EW events, projection s
-    const int j = lane / S, s = lane % S;
-    const bool row_used = j < a.EW;
-    constexpr int kCH = kCV / 2;  // vectors of this thread: c = kCH half + cc
-    float2 slnI[kCH];             // per-thread sums of w ln I as (hi, lo) pairs (TwoSum)
-#pragma unroll
-    for (int c = 0; c < kCH; ++c) slnI[c] = make_float2(0.f, 0.f);
-
-    int mma1_waits = 0, mma2_commits = 0, mma2_waits = 0;
+    // bounded waits: every thread waits on its own; decisions are combined by barriers
     auto wait_bar = [&](uint64_t* bar, uint32_t parity) -> bool {
         const long long t0 = clock64();
         while (true) {
@@ -207,120 +229,131 @@ __global__ void __launch_bounds__(kCT, 1) coupling_kernel(const CpArgs a)
             if (clock64() - t0 > a.timeout) return false;
         }
     };
-    auto wait_mma2 = [&]() -> bool {
-        if (mma2_waits == mma2_commits) return true;
-        const bool ok = wait_bar(&bars[3], (uint32_t)(mma2_waits & 1));
-        ++mma2_waits;
-        return ok;
-    };
-    // Add one tile's GEMM2 results (rows n = 16 warp + lane for lane < 16; both
-    // accumulators) into the CTA's (hi, lo) sums.  Each tile is flushed: the
-    // tensor cores' FP32 accumulation then spans 16 steps at most.
-    auto two_sum = [](float2& p, float x) {
-        const float sum = __fadd_rn(p.x, x);
-        const float bp = __fsub_rn(sum, p.x);
-        const float err = __fadd_rn(__fsub_rn(p.x, __fsub_rn(sum, bp)), __fsub_rn(x, bp));
-        p = make_float2(sum, __fadd_rn(p.y, err));
-    };
-    // The two warps of a lane quarter split the 8-column chunks.
-    const int nchunk = K2p / 8, chunk0 = half ? (nchunk + 1) / 2 : 0, chunk1 = half ? nchunk : (nchunk + 1) / 2;
-    auto flush_d2 = [&]() {
-        tc_fence_after();
-        float2* arow = acc + (size_t)(16 * wq + (lane & 15)) * acc_stride;
-        for (int ch = chunk0; ch < chunk1; ch += 2) {
-            // up to 16 columns of both accumulators in flight, one wait
-            uint32_t vh[2][8], vl[2][8];
-            const bool two = ch + 1 < chunk1;
-            tmem_ld8(tm + tm_lane + 64 + 8 * ch, vh[0]);
-            tmem_ld8(tm + tm_lane + 64 + K2p + 8 * ch, vl[0]);
-            if (two) {
-                tmem_ld8(tm + tm_lane + 64 + 8 * ch + 8, vh[1]);
-                tmem_ld8(tm + tm_lane + 64 + K2p + 8 * ch + 8, vl[1]);
+    // GEMM1 of tile i: D1[i % 2] = U(i) B1 (six products per 16-wide K step)
+    auto gemm1 = [&](int i) {
+        const int st = i & 1;
+        const uint32_t ab = sa(sA[st]), bb = sa(b1);
+        const uint32_t d = tm + 64 * st, dc = tm + 128 + 64 * st;
+        for (int ks = 0; ks < K2p / 16; ++ks) {
+            uint64_t ad[kParts], bd[kParts];
+            for (int p = 0; p < kParts; ++p) {
+                ad[p] = sdesc(ab + p * PB + ks * 256, 128, sbo_a);
+                bd[p] = sdesc(bb + p * B1P + ks * 256, 128, sbo_a);
             }
-            tmem_wait();
-            if (lane < 16)
-                for (int hh = 0; hh < (two ? 2 : 1); ++hh)
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        two_sum(arow[8 * ch + 8 * hh + q], __uint_as_float(vh[hh][q]));
-                        two_sum(arow[8 * ch + 8 * hh + q], __uint_as_float(vl[hh][q]));
-                    }
+            mma_bf16(d, ad[0], bd[0], idesc1, ks > 0);
+            mma_bf16(dc, ad[0], bd[1], idesc1, ks > 0);
+            mma_bf16(dc, ad[1], bd[0], idesc1, 1);
+            mma_bf16(dc, ad[0], bd[2], idesc1, 1);
+            mma_bf16(dc, ad[1], bd[1], idesc1, 1);
+            mma_bf16(dc, ad[2], bd[0], idesc1, 1);
         }
+        mma_commit(&mma1[st]);
+    };
+    // GEMM2 of tile i: D2 = W UT(i) (x0 y0 products), D2c = the five corrections
+    auto gemm2 = [&](int i) {
+        const uint32_t ab = sa(wt), bb = sa(sB[i & 1]);
+        for (int ks = 0; ks < kRows / 16; ++ks) {
+            uint64_t ad[kParts], bd[kParts];
+            for (int p = 0; p < kParts; ++p) {
+                ad[p] = sdesc(ab + p * WTP + ks * 2 * kLboW, kLboW, kSboW);
+                bd[p] = sdesc(bb + p * PB + ks * 256, 128, sbo_t);
+            }
+            mma_bf16(tD2 + kMaxK2p * (ks & 3), ad[0], bd[0], idesc2, ks >= 4);
+            mma_bf16(tD2c, ad[0], bd[1], idesc2, ks > 0);
+            mma_bf16(tD2c, ad[1], bd[0], idesc2, 1);
+            mma_bf16(tD2c, ad[0], bd[2], idesc2, 1);
+            mma_bf16(tD2c, ad[1], bd[1], idesc2, 1);
+            mma_bf16(tD2c, ad[2], bd[0], idesc2, 1);
+        }
+        mma_commit(mma2);
     };
 
-    long long i = 0;
-    for (long long t = blockIdx.x; t < a.ntiles; t += G, ++i) {
-        const int st = NST == 2 ? (int)(i & 1) : 0;
-        bool ok = wait_bar(&bars[st], (uint32_t)((NST == 2 ? i >> 1 : i) & 1));
-        ok = wait_mma2() && ok;  // the previous GEMM2 has read UT and Wt
-        if (!ok) s_abort = 1;
-        __syncthreads();
-        if (s_abort) break;
-        if (i > 0) flush_d2();   // the previous tile's GEMM2 results
-        // ---- split this thread's half of its U row: hi in place, lo beside it, both
-        //      transposed for GEMM2; the event weight is read before the stage is refilled
-        unsigned char* ub = uraw[st];
-        const float wgt_tile = reinterpret_cast<const float*>(ub + (size_t)kRows * K2p * 4)[wq * a.EW + min(j, a.EW - 1)];
-        const int nq = K2p / 4, q0 = half ? nq / 2 : 0, q1 = half ? nq : nq / 2;
-        for (int q = q0; q < q1; ++q) {
-            const uint32_t off = kmaj(row, 4 * q, 128, sbo_u);
-            const float4 x = *reinterpret_cast<const float4*>(ub + off);
-            const float4 h = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
-            const float4 l = make_float4(tf32_rn(x.x - h.x), tf32_rn(x.y - h.y), tf32_rn(x.z - h.z), tf32_rn(x.w - h.w));
-            *reinterpret_cast<float4*>(ub + off) = h;
-            *reinterpret_cast<float4*>(ulo + off) = l;
-            const float hv[4] = {h.x, h.y, h.z, h.w}, lv[4] = {l.x, l.y, l.z, l.w};
+    // this thread's row: lane quarter wq, slot j of the quarter's EW events, projection s
+    const int j = lane / S, s = lane % S;
+    const bool row_used = j < a.EW;
+    float2 slnI[kCH];  // per-thread sums of w ln I as (hi, lo) pairs
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const uint32_t o2 = kmaj(4 * q + e, row, kLboT, kSboT);
-                *reinterpret_cast<float*>(uthi + o2) = hv[e];
-                *reinterpret_cast<float*>(utlo + o2) = lv[e];
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc_fence_before();
-        __syncthreads();
+    for (int c = 0; c < kCH; ++c) slnI[c] = make_float2(0.f, 0.f);
+    // the GEMM2 results of the CTA, rows n = 16 wq + lane (lane < 16), this warp's
+    // half of the 8-column chunks, as (hi, lo) pairs
+    const int nch = K2p / 16;  // chunks per half (1..3)
+    float2 acc[3][8];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) acc[q][e] = make_float2(0.f, 0.f);
+    auto flush_d2 = [&]() {
         tc_fence_after();
-        // ---- GEMM1: D1[r][n] = sum_kk U[r][kk] B1[n][kk]  (three-term TF32 split)
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (q < nch) {
+                const int col = 8 * (nch * half + q);
+                uint32_t v[5][8];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) tmem_ld8(tD2 + kMaxK2p * m + tm_lane + col, v[m]);
+                tmem_ld8(tD2c + tm_lane + col, v[4]);
+                tmem_wait();
+#pragma unroll
+                for (int m = 0; m < 5; ++m)
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) two_sum(acc[q][e], __uint_as_float(v[m][e]));
+            }
+    };
+
+    int mma2_pending = 0;  // GEMM2 commits not yet waited for (0 or 1)
+    int mma2_phase = 0;
+    bool fail = false;
+    if (tid == 0 && nmine > 0) {
+        fail = !wait_bar(&tmaA[0], 0);
+        if (!fail) gemm1(0);
+    }
+    if (__syncthreads_or(fail)) s_abort = 1;
+    int i = 0;
+    for (; i < nmine && !s_abort; ++i) {
+        const int st = i & 1;
+        const uint32_t ph = (uint32_t)((i >> 1) & 1);
+        // (a) GEMM1(i) done; the weights of tile i are read before its stage is refilled
+        bool ok = wait_bar(&mma1[st], ph);
+        tc_fence_after();
+        const float wgt_tile = reinterpret_cast<const float*>(sA[st] + kParts * PB)[wq * a.EW + min(j, a.EW - 1)];
+        if (__syncthreads_or(!ok)) {
+            s_abort = 1;
+            break;
+        }
         if (tid == 0) {
-            for (int ks = 0; ks < K2p / 8; ++ks) {
-                const uint64_t ah = sdesc(sa(ub) + ks * 256, 128, sbo_u), al = sdesc(sa(ulo) + ks * 256, 128, sbo_u);
-                const uint64_t bh = sdesc(sa(b1hi) + ks * 256, 128, sbo_u), bl = sdesc(sa(b1lo) + ks * 256, 128, sbo_u);
-                mma_tf32(tm, ah, bh, idesc1, ks > 0);
-                mma_tf32(tm, ah, bl, idesc1, 1);
-                mma_tf32(tm, al, bh, idesc1, 1);
-            }
-            mma_commit(&bars[2]);
-        }
-        ok = wait_bar(&bars[2], (uint32_t)(mma1_waits & 1));
-        ++mma1_waits;
-        if (!ok) s_abort = 1;
-        tc_fence_after();
-        // the stage is free: thread 0 refills it with the tile two steps ahead
-        if (tid == 0 && ok) {
-            const long long tn = t + (long long)NST * G;
-            if (tn < a.ntiles) {
+            // (b) stage A(i) is free: fetch tile i + 2; (c) GEMM1(i + 1) into the other accumulator
+            if (i + 2 < nmine) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                pwa::tma_load_tile(ub, reinterpret_cast<const unsigned char*>(a.U) + (size_t)tn * TB, TB, &bars[st]);
+                issue_A(i + 2, st);
+            }
+            if (i + 1 < nmine) {
+                if (wait_bar(&tmaA[st ^ 1], (uint32_t)(((i + 1) >> 1) & 1)))
+                    gemm1(i + 1);
+                else
+                    s_abort = 1;
             }
         }
-        // ---- epilogue: this row's coherent sums for this thread's vectors
-        //      (columns Re A, Im A, Re Adot, Im Adot of c = kCH half + cc)
+        // (d) epilogue: this row's coherent sums for this thread's vectors
         float d1[4][kCH];
         {
-            uint32_t v[4][8];
+            uint32_t v[4][8], vc[4][8];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) tmem_ld8(tm + tm_lane + q * kCV + kCH * half, v[q]);
+            for (int q = 0; q < 4; ++q) {
+                tmem_ld8(tm + 64 * st + tm_lane + q * kCV + kCH * half, v[q]);
+                tmem_ld8(tm + 128 + 64 * st + tm_lane + q * kCV + kCH * half, vc[q]);
+            }
             tmem_wait();
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
-                for (int cc = 0; cc < kCH; ++cc) d1[q][cc] = __uint_as_float(v[q][cc]);
+                for (int cc = 0; cc < kCH; ++cc) d1[q][cc] = __uint_as_float(v[q][cc]) + __uint_as_float(vc[q][cc]);
         }
+        const long long t = tile_of(i);
         const long long ev = t * a.Et + (long long)wq * a.EW + j;
         const bool valid = row_used && ev < a.n;
         const float wgt = valid ? wgt_tile : 0.f;
         const int base = S * j;  // first lane of this row's event
+        float wv[4][kCH];
 #pragma unroll
         for (int cc = 0; cc < kCH; ++cc) {
             const int c = kCH * half + cc;
@@ -343,52 +376,82 @@ __global__ void __launch_bounds__(kCT, 1) coupling_kernel(const CpArgs a)
                     atomicOr(a.err + 1 + c, pwa::ERR_NONFINITE);
                 }
             }
-            const float wv[4] = {wa * Ar, wa * Ai, fmaf(wa, Dr, -wb * Ar), fmaf(wa, Di, -wb * Ai)};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float hi = tf32_rn(wv[q]);
-                const uint32_t off = kmaj(q * kCV + c, row, kLboT, kSboT);
-                *reinterpret_cast<float*>(wthi + off) = hi;
-                *reinterpret_cast<float*>(wtlo + off) = tf32_rn(wv[q] - hi);
+            wv[0][cc] = wa * Ar;
+            wv[1][cc] = wa * Ai;
+            wv[2][cc] = fmaf(wa, Dr, -wb * Ar);
+            wv[3][cc] = fmaf(wa, Di, -wb * Ai);
+        }
+        // (e) GEMM2(i - 1) done: flush its results, refill its transposed-U buffer
+        if (mma2_pending) {
+            ok = wait_bar(mma2, (uint32_t)(mma2_phase & 1));
+            ++mma2_phase;
+            mma2_pending = 0;
+            if (__syncthreads_or(!ok)) {
+                s_abort = 1;
+                break;
+            }
+            flush_d2();
+            if (tid == 0 && i + 1 < nmine) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue_B(i + 1, st ^ 1);
             }
         }
+        // (f) the W rows of this tile (three parts)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int cc = 0; cc < kCH; ++cc) {
+                __nv_bfloat16 p0, p1, p2;
+                split3(wv[q][cc], p0, p1, p2);
+                const uint32_t off = kmaj16(q * kCV + kCH * half + cc, row, kLboW, kSboW);
+                *reinterpret_cast<__nv_bfloat16*>(wt + off) = p0;
+                *reinterpret_cast<__nv_bfloat16*>(wt + WTP + off) = p1;
+                *reinterpret_cast<__nv_bfloat16*>(wt + 2 * WTP + off) = p2;
+            }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
         if (s_abort) break;
-        // ---- GEMM2: D2[n][kk] += sum_r Wt[n][r] UT[kk][r]
+        // (g) GEMM2(i) once its transposed U has arrived
+        bool late = false;
         if (tid == 0) {
-            for (int ks = 0; ks < kRows / 8; ++ks) {
-                const uint64_t ah = sdesc(sa(wthi) + ks * 2 * kLboT, kLboT, kSboT),
-                               al = sdesc(sa(wtlo) + ks * 2 * kLboT, kLboT, kSboT);
-                const uint64_t bh = sdesc(sa(uthi) + ks * 2 * kLboT, kLboT, kSboT),
-                               bl = sdesc(sa(utlo) + ks * 2 * kLboT, kLboT, kSboT);
-                mma_tf32(tm + 64, ah, bh, idesc2, ks > 0);
-                mma_tf32(tm + 64 + K2p, ah, bl, idesc2, ks > 0);
-                mma_tf32(tm + 64 + K2p, al, bh, idesc2, 1);
-            }
-            mma_commit(&bars[3]);
+            if (wait_bar(&tmaB[st], ph))
+                gemm2(i);
+            else
+                late = true;
         }
-        ++mma2_commits;
+        if (__syncthreads_or(late)) {
+            s_abort = 1;
+            break;
+        }
+        mma2_pending = 1;
     }
-    // ---- finish: the last GEMM2, its flush, the CTA's sums of w ln I
+    // ---- finish: the last GEMM2, its flush, the CTA's sums
+    if (!s_abort && mma2_pending) {
+        const bool ok = wait_bar(mma2, (uint32_t)(mma2_phase & 1));
+        ++mma2_phase;
+        mma2_pending = 0;
+        if (__syncthreads_or(!ok))
+            s_abort = 1;
+        else
+            flush_d2();
+    }
     __syncthreads();
-    if (!s_abort) {
-        // every thread waits; the flush (warp-collective TMEM loads) is decided together
-        if (__syncthreads_or(!wait_mma2())) s_abort = 1;
-        if (!s_abort && mma2_commits > 0) flush_d2();
-    }
     if (s_abort) {
         if (tid == 0) atomicOr(a.err, pwa::ERR_TIMEOUT);
     } else {
-        __syncthreads();
         double* rq = a.rec + (size_t)blockIdx.x * (kN1 * K2p + kCV);
-        for (int q = tid; q < kN1 * K2p; q += kCT) {
-            const float2 p = acc[(size_t)(q / K2p) * acc_stride + q % K2p];
-            rq[q] = (double)p.x + (double)p.y;
+        if (lane < 16) {
+            const int n = 16 * wq + lane;
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                if (q < nch)
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        rq[(size_t)n * K2p + 8 * (nch * half + q) + e] = (double)acc[q][e].x + (double)acc[q][e].y;
         }
-        double* rec = rq + (size_t)kN1 * K2p;
+        double* rs = rq + (size_t)kN1 * K2p;
 #pragma unroll
         for (int cc = 0; cc < kCH; ++cc) {
             double v = (double)slnI[cc].x + (double)slnI[cc].y;
@@ -398,14 +461,17 @@ __global__ void __launch_bounds__(kCT, 1) coupling_kernel(const CpArgs a)
         __syncthreads();
         if (tid < kCV) {
             const int h = tid / kCH, cc = tid % kCH;  // vector tid: warps 4 h .. 4 h + 3
-            rec[tid] = ((s_red[4 * h][cc] + s_red[4 * h + 1][cc]) + s_red[4 * h + 2][cc]) + s_red[4 * h + 3][cc];
+            rs[tid] = ((s_red[4 * h][cc] + s_red[4 * h + 1][cc]) + s_red[4 * h + 2][cc]) + s_red[4 * h + 3][cc];
         }
     }
-    // drain: a timed-out CTA waits (bounded) for its own copies and MMAs before freeing TMEM
+    // drain: a timed-out CTA waits (bounded) for its own MMAs and copies before freeing TMEM
     if (s_abort && tid == 0) {
-        (void)wait_mma2();
-        (void)wait_bar(&bars[2], (uint32_t)(mma1_waits & 1));
-        for (int q = 0; q < NST; ++q) (void)wait_bar(&bars[q], (uint32_t)(((i + q) / NST) & 1));
+        if (mma2_pending) (void)wait_bar(mma2, (uint32_t)(mma2_phase & 1));
+        for (int q = 0; q < 2; ++q) {
+            (void)wait_bar(&mma1[q], (uint32_t)(((i + q) >> 1) & 1));
+            (void)wait_bar(&tmaA[q], (uint32_t)(((i + q) >> 1) & 1));
+            (void)wait_bar(&tmaB[q], (uint32_t)(((i + q) >> 1) & 1));
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -429,13 +495,16 @@ __device__ __forceinline__ float2 bw_f32(const CpRes& r, float m2)
     return make_float2(d * q, r.mg * q);
 }
 
-// U tiles: row (warp w, slot j, projection s) of tile t is event t Et + w EW + j
+// Tile records: row r = (lane quarter w, slot j, projection s) of tile t is
+// event t Et + w EW + j; U (split in three BF16 parts) as GEMM1's operand and,
+// transposed, as GEMM2's, and the event weights.
 __global__ void coupling_u_kernel(const float2* __restrict__ F, const float* __restrict__ m2,
                                   const float* __restrict__ w, long long n, int K, int S, int K2p, int EW, int Et,
-                                  int ntiles, long long tile_floats, const CpRes* __restrict__ res,
-                                  float* __restrict__ U)
+                                  int ntiles, uint32_t rec_bytes, uint32_t a_bytes, const CpRes* __restrict__ res,
+                                  unsigned char* __restrict__ U)
 {
-    const uint32_t sbo = (uint32_t)(K2p / 4) * 128;
+    const uint32_t PB = part_bytes(K2p);
+    const uint32_t sbo_a = (uint32_t)(K2p / 8) * 128, sbo_t = (uint32_t)(kRows / 8) * 128;
     const long long per_tile = (long long)kRows * K2p;
     const long long total = (long long)ntiles * per_tile;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -453,19 +522,24 @@ __global__ void coupling_u_kernel(const float2* __restrict__ F, const float* __r
             const float2 f = F[((size_t)e * K + k) * S + s];
             v = kk < K ? b.x * f.x - b.y * f.y : b.x * f.y + b.y * f.x;
         }
-        const uint32_t off = (uint32_t)(r >> 3) * sbo + (uint32_t)(kk >> 2) * 128 + (uint32_t)(r & 7) * 16 +
-                             (uint32_t)(kk & 3) * 4;
-        U[t * tile_floats + off / 4] = v;
+        __nv_bfloat16 p[3];
+        split3(v, p[0], p[1], p[2]);
+        unsigned char* rec = U + (size_t)t * rec_bytes;
+        const uint32_t oa = kmaj16(r, kk, 128, sbo_a), ot = kmaj16(kk, r, 128, sbo_t);
+        for (int q = 0; q < 3; ++q) {
+            *reinterpret_cast<__nv_bfloat16*>(rec + q * PB + oa) = p[q];
+            *reinterpret_cast<__nv_bfloat16*>(rec + a_bytes + q * PB + ot) = p[q];
+        }
     }
-    // the weights after the U block of each record (zero past the last event and in the padding)
-    const int wpad = (int)(tile_floats - per_tile);
-    const long long nw = (long long)ntiles * wpad;
+    // the weights after the U parts (zero past the last event and in the padding)
+    const int nw_tile = (int)(w_bytes(Et) / 4);
+    const long long nw = (long long)ntiles * nw_tile;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nw;
          i += (long long)gridDim.x * blockDim.x) {
-        const long long t = i / wpad;
-        const int el = (int)(i % wpad);
+        const long long t = i / nw_tile;
+        const int el = (int)(i % nw_tile);
         const long long e = t * Et + el;
-        U[t * tile_floats + per_tile + el] = (el < Et && e < n) ? (w ? w[e] : 1.f) : 0.f;
+        reinterpret_cast<float*>(U + (size_t)t * rec_bytes + 3 * PB)[el] = (el < Et && e < n) ? (w ? w[e] : 1.f) : 0.f;
     }
 }
 
@@ -638,8 +712,7 @@ __global__ void coupling_combine_kernel(const double* __restrict__ rec, int nrec
 struct pwa_coupling {
     pwa_handle* h = nullptr;
     int K = 0, S = 0, Pc = 0, K2p = 0, EW = 0, Et = 0, ntiles = 0, grid = 0;
-    uint32_t tile_bytes = 0;
-    int nst = 2;
+    uint32_t rec_bytes = 0, a_bytes = 0, b_bytes = 0;  // tile record and its two TMA copies
     size_t smem = 0;
     std::vector<double> par;   // rho, phi, M, Gamma per resonance (the fixed values)
     std::vector<int> ridx;     // theta index of rho_k, phi_k (-1 when fixed)
@@ -706,7 +779,7 @@ pwa_status cp_launch(pwa_coupling* cp, int nv, const double* theta_c, const doub
     if (e == cudaSuccess) e = cudaMemsetAsync(cp->d_err, 0, sizeof(int) * (1 + kCV), s);
     if (e != cudaSuccess) return cp_cuda(cp, e, "coupling upload");
     CpArgs a;
-    a.U = cp->d_U;
+    a.U = reinterpret_cast<const unsigned char*>(cp->d_U);
     a.n = h->n[0];
     a.ntiles = cp->ntiles;
     a.K = K;
@@ -714,8 +787,9 @@ pwa_status cp_launch(pwa_coupling* cp, int nv, const double* theta_c, const doub
     a.K2p = cp->K2p;
     a.EW = cp->EW;
     a.Et = cp->Et;
-    a.tile_bytes = cp->tile_bytes;
-    a.nst = cp->nst;
+    a.rec_bytes = cp->rec_bytes;
+    a.a_bytes = cp->a_bytes;
+    a.b_bytes = cp->b_bytes;
     a.gc = cp->d_gc;
     a.nv = nv;
     a.rec = cp->d_rec;
@@ -745,7 +819,7 @@ pwa_status pwa_coupling_create(pwa_handle* h, const double* theta, pwa_coupling*
     const int K = h->K, S = h->S, P = h->P;
     for (int i = 0; i < P; ++i)
         if (!std::isfinite(theta[i])) return pwa::set_error(h, PWA_EINVAL, "theta must be finite");
-    const int K2p = (2 * K + 7) / 8 * 8;
+    const int K2p = (2 * K + 15) / 16 * 16;
     if (K2p > kMaxK2p)
         return pwa::set_error(h, PWA_EINVAL, "the coupling sub-problem supports K <= " + std::to_string(kMaxK2p / 2) +
                                                  " (shared memory of one tile)");
@@ -757,8 +831,9 @@ pwa_status pwa_coupling_create(pwa_handle* h, const double* theta, pwa_coupling*
     cp->K2p = K2p;
     cp->EW = 32 / S;
     cp->Et = 4 * cp->EW;
-    const int Etp = (cp->Et + 3) / 4 * 4;  // weights padded to 16 bytes
-    cp->tile_bytes = (uint32_t)(kRows * K2p + Etp) * 4;
+    cp->b_bytes = kParts * part_bytes(K2p);
+    cp->a_bytes = cp->b_bytes + w_bytes(cp->Et);
+    cp->rec_bytes = cp->a_bytes + cp->b_bytes;
     cp->ntiles = (int)((h->n[0] + cp->Et - 1) / cp->Et);
     // parameter values: theta where free, the table where fixed
     cp->par.assign(4 * K, 0.0);
@@ -788,12 +863,9 @@ pwa_status pwa_coupling_create(pwa_handle* h, const double* theta, pwa_coupling*
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    auto smem_for = [&](int nst) {
-        return (size_t)(nst + 1) * cp->tile_bytes + 2 * (size_t)kN1 * K2p * 4 + 2 * (size_t)(K2p / 8) * kSboT +
-               2 * (size_t)(kN1 / 8) * kSboT + (size_t)kN1 * (K2p + 1) * 8 + 64;
-    };
-    cp->nst = smem_for(2) + 2048 <= (size_t)optin ? 2 : 1;
-    cp->smem = smem_for(cp->nst);
+    // A stages x 2 | B stages x 2 | B1 parts | W parts | barriers and the TMEM address
+    cp->smem = 2 * (size_t)cp->a_bytes + 2 * (size_t)cp->b_bytes + kParts * (size_t)kN1 * K2p * 2 +
+               kParts * (size_t)(kN1 / 8) * kSboW + kNBars * 8 + 16;
     pwa_status st = PWA_OK;
     cudaError_t e = cudaSuccess;
     CpRes* d_rs = nullptr;
@@ -808,8 +880,7 @@ pwa_status pwa_coupling_create(pwa_handle* h, const double* theta, pwa_coupling*
         e = cudaFuncSetAttribute(coupling_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cp->smem);
         if (e != cudaSuccess) break;
         cp->grid = std::max(1, std::min(sms, cp->ntiles));
-        const size_t ufloats = (size_t)cp->ntiles * (cp->tile_bytes / 4);
-        if ((e = cudaMalloc(&cp->d_U, ufloats * sizeof(float))) != cudaSuccess) break;
+        if ((e = cudaMalloc(&cp->d_U, (size_t)cp->ntiles * cp->rec_bytes)) != cudaSuccess) break;
         if ((e = cudaMalloc(&cp->d_phi, sizeof(double) * 2 * K * K)) != cudaSuccess) break;
         if ((e = cudaMalloc(&cp->d_gc, sizeof(float) * kCV * K * 4)) != cudaSuccess) break;
         if ((e = cudaMalloc(&cp->d_vec, sizeof(CpVec) * kCV * K)) != cudaSuccess) break;
@@ -821,11 +892,11 @@ pwa_status pwa_coupling_create(pwa_handle* h, const double* theta, pwa_coupling*
         if ((e = cudaMalloc(&d_part, sizeof(double) * 2 * K * K * (size_t)std::max(phi_blocks, 1))) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(d_rs, rs.data(), sizeof(CpRes) * K, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
             break;
-        const long long uthreads = (long long)ufloats;
+        const long long uthreads = (long long)cp->ntiles * kRows * K2p;
         const int ublocks = (int)std::min<long long>((uthreads + 255) / 256, 65535LL * 8);
         coupling_u_kernel<<<std::max(ublocks, 1), 256, 0, h->stream>>>(
             reinterpret_cast<const float2*>(h->d_F[0]), h->d_m2[0], h->d_w, h->n[0], K, S, K2p, cp->EW, cp->Et,
-            cp->ntiles, (long long)(cp->tile_bytes / 4), d_rs, cp->d_U);
+            cp->ntiles, cp->rec_bytes, cp->a_bytes, d_rs, reinterpret_cast<unsigned char*>(cp->d_U));
         if ((e = cudaGetLastError()) != cudaSuccess) break;
         if (K * K > 8 * kPhiThreads) {
             st = pwa::set_error(h, PWA_EINVAL, "K too large for the integral-matrix kernel");
