@@ -44,7 +44,8 @@
 
 namespace {
 
-constexpr int kCT = 256;        // threads per CTA: threads r and r + 128 share row r of a tile
+constexpr int kCT = 256;        // epilogue threads per CTA: threads r and r + 128 share row r of a
+                                // tile; one more warp issues the copies and the MMAs
 constexpr int kRows = 128;      // (event, projection) rows per tile
 constexpr int kCV = 16;         // coupling vectors per launch
 constexpr int kCH = kCV / 2;    // vectors per thread
@@ -56,7 +57,7 @@ constexpr int kMaxK2p = 48;     // 2K rounded up to 16; bounded by shared memory
 constexpr int kTmemCols = 512;  // GEMM1 x0 y0 (x 2 tiles) at 0 and 64, its corrections at 128 and 192;
                                 // GEMM2 x0 y0 in four accumulators (K steps ks mod 4) at 256 + 48 j,
                                 // its corrections at 448
-constexpr int kNBars = 8;       // tmaA[2], tmaB[2], mma1[2], mma2, spare
+constexpr int kNBars = 8;       // tmaA[2], tmaB[2], g1[2], g2, wready
 
 struct CpArgs {
     const unsigned char* U;  // [ntiles] tile records (layout below)
@@ -123,6 +124,20 @@ __host__ __device__ inline void split3(float x, __nv_bfloat16& b0, __nv_bfloat16
     b2 = __float2bfloat16_rn(r1 - __bfloat162float(b1));
 }
 
+// The same split by truncation (each part the leading 8 significant bits of
+// what is left; also exact, since 8 + 8 + 8 bits hold an FP32 significand),
+// returned as raw BF16 bit patterns: a few integer operations per value.
+__device__ __forceinline__ void split3_bits(float x, unsigned short& b0, unsigned short& b1, unsigned short& b2)
+{
+    const uint32_t u0 = __float_as_uint(x);
+    const float r1 = x - __uint_as_float(u0 & 0xFFFF0000u);
+    const uint32_t u1 = __float_as_uint(r1);
+    const float r2 = r1 - __uint_as_float(u1 & 0xFFFF0000u);
+    b0 = (unsigned short)(u0 >> 16);
+    b1 = (unsigned short)(u1 >> 16);
+    b2 = (unsigned short)(__float_as_uint(r2) >> 16);
+}
+
 // byte offset of element (row, col) of a K-major 16-bit operand
 __host__ __device__ inline uint32_t kmaj16(int row, int col, uint32_t lbo, uint32_t sbo)
 {
@@ -137,11 +152,12 @@ __device__ __forceinline__ void two_sum(float2& p, float x)
     p = make_float2(sum, __fadd_rn(p.y, err));
 }
 
-__global__ void __launch_bounds__(kCT, 1) coupling_kernel(const CpArgs a)
+__global__ void __launch_bounds__(kCT + 32, 1) coupling_kernel(const CpArgs a)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int row = tid & (kRows - 1), half = tid >> 7, wq = warp & 3;  // wq: TMEM lane quarter
+    const bool producer = warp == kCT / 32;  // warp 8: TMA copies and MMA issue; warps 0-7: epilogue
+    const int row = tid & (kRows - 1), half = (tid >> 7) & 1, wq = warp & 3;  // wq: TMEM lane quarter
     const int K = a.K, S = a.S, K2p = a.K2p;
     const uint32_t PB = part_bytes(K2p);
     const uint32_t sbo_a = (uint32_t)(K2p / 8) * 128;  // U parts and B1 parts: 8-row-group stride
@@ -154,9 +170,11 @@ __global__ void __launch_bounds__(kCT, 1) coupling_kernel(const CpArgs a)
     unsigned char* b1 = sm + 2 * a.a_bytes + 2 * a.b_bytes;
     unsigned char* wt = b1 + kParts * B1P;
     uint64_t* bars = reinterpret_cast<uint64_t*>(wt + kParts * WTP);
-    uint64_t *tmaA = bars, *tmaB = bars + 2, *mma1 = bars + 4, *mma2 = bars + 6;
+    // tmaA[2], tmaB[2]: tile halves arrived; g1[2]: GEMM1 of a tile done; g2: GEMM2 done;
+    // wready: the 8 epilogue warps have written W and are done with the tile's D1 and weights
+    uint64_t *tmaA = bars, *tmaB = bars + 2, *g1 = bars + 4, *g2 = bars + 6, *wready = bars + 7;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + kNBars);
-    __shared__ int s_abort;
+    __shared__ volatile int s_abort;
     __shared__ double s_red[kCT / 32][kCH];
 
     const int G = gridDim.x;
@@ -165,7 +183,7 @@ __global__ void __launch_bounds__(kCT, 1) coupling_kernel(const CpArgs a)
     auto tile_of = [&](int i) { return (long long)blockIdx.x + (long long)i * G; };
 
     // ---- GEMM1 B operand from the coupling vectors: row n, column kk of (2K | padding), 3 parts
-    for (int i = tid; i < kN1 * K2p; i += kCT) {
+    for (int i = tid; i < kN1 * K2p; i += kCT + 32) {
         const int n = i / K2p, kk = i % K2p;
         const int blk = n / kCV, c = n % kCV;
         float v = 0.f;
@@ -191,14 +209,13 @@ __global__ void __launch_bounds__(kCT, 1) coupling_kernel(const CpArgs a)
     };
     if (tid == 0) {
         s_abort = 0;
-        for (int i = 0; i < kNBars; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(&bars[i])));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int i = 0; i < 2 && i < nmine; ++i) {
-            issue_A(i, i);
-            issue_B(i, i);
+        for (int i = 0; i < kNBars; ++i) {
+            const uint32_t count = (bars + i == wready) ? kCT / 32 : 1;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(&bars[i])), "r"(count));
         }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (producer) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(tslot)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -215,7 +232,8 @@ __global__ void __launch_bounds__(kCT, 1) coupling_kernel(const CpArgs a)
     const uint32_t idesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(K2p >> 3) << 17) |
                             ((uint32_t)(kN1 >> 4) << 24);
 
-    // bounded waits: every thread waits on its own; decisions are combined by barriers
+    // bounded wait on a barrier phase; gives up at once when another thread has
+    // already given up (the whole CTA then winds down)
     auto wait_bar = [&](uint64_t* bar, uint32_t parity) -> bool {
         const long long t0 = clock64();
         while (true) {
@@ -226,257 +244,243 @@ __global__ void __launch_bounds__(kCT, 1) coupling_kernel(const CpArgs a)
                 : "r"(sa(bar)), "r"(parity)
                 : "memory");
             if (done) return true;
-            if (clock64() - t0 > a.timeout) return false;
-        }
-    };
-    // GEMM1 of tile i: D1[i % 2] = U(i) B1 (six products per 16-wide K step)
-    auto gemm1 = [&](int i) {
-        const int st = i & 1;
-        const uint32_t ab = sa(sA[st]), bb = sa(b1);
-        const uint32_t d = tm + 64 * st, dc = tm + 128 + 64 * st;
-        for (int ks = 0; ks < K2p / 16; ++ks) {
-            uint64_t ad[kParts], bd[kParts];
-            for (int p = 0; p < kParts; ++p) {
-                ad[p] = sdesc(ab + p * PB + ks * 256, 128, sbo_a);
-                bd[p] = sdesc(bb + p * B1P + ks * 256, 128, sbo_a);
+            if (s_abort || clock64() - t0 > a.timeout) {
+                s_abort = 1;
+                return false;
             }
-            mma_bf16(d, ad[0], bd[0], idesc1, ks > 0);
-            mma_bf16(dc, ad[0], bd[1], idesc1, ks > 0);
-            mma_bf16(dc, ad[1], bd[0], idesc1, 1);
-            mma_bf16(dc, ad[0], bd[2], idesc1, 1);
-            mma_bf16(dc, ad[1], bd[1], idesc1, 1);
-            mma_bf16(dc, ad[2], bd[0], idesc1, 1);
         }
-        mma_commit(&mma1[st]);
-    };
-    // GEMM2 of tile i: D2 = W UT(i) (x0 y0 products), D2c = the five corrections
-    auto gemm2 = [&](int i) {
-        const uint32_t ab = sa(wt), bb = sa(sB[i & 1]);
-        for (int ks = 0; ks < kRows / 16; ++ks) {
-            uint64_t ad[kParts], bd[kParts];
-            for (int p = 0; p < kParts; ++p) {
-                ad[p] = sdesc(ab + p * WTP + ks * 2 * kLboW, kLboW, kSboW);
-                bd[p] = sdesc(bb + p * PB + ks * 256, 128, sbo_t);
-            }
-            mma_bf16(tD2 + kMaxK2p * (ks & 3), ad[0], bd[0], idesc2, ks >= 4);
-            mma_bf16(tD2c, ad[0], bd[1], idesc2, ks > 0);
-            mma_bf16(tD2c, ad[1], bd[0], idesc2, 1);
-            mma_bf16(tD2c, ad[0], bd[2], idesc2, 1);
-            mma_bf16(tD2c, ad[1], bd[1], idesc2, 1);
-            mma_bf16(tD2c, ad[2], bd[0], idesc2, 1);
-        }
-        mma_commit(mma2);
     };
 
-    // this thread's row: lane quarter wq, slot j of the quarter's EW events, projection s
-    const int j = lane / S, s = lane % S;
-    const bool row_used = j < a.EW;
-    float2 slnI[kCH];  // per-thread sums of w ln I as (hi, lo) pairs
+    if (producer) {
+        // ======== producer: one lane issues everything ========
+        if (lane == 0) {
+            for (int i = 0; i < 2 && i < nmine; ++i) {
+                issue_A(i, i);
+                issue_B(i, i);
+            }
+            for (int i = 0; i <= nmine && !s_abort; ++i) {
+                if (i < nmine) {
+                    // GEMM1(i) into accumulator pair i % 2 (read by the epilogue of tile i - 2, done)
+                    const int st = i & 1;
+                    if (!wait_bar(&tmaA[st], (uint32_t)((i >> 1) & 1))) break;
+                    tc_fence_after();
+                    const uint32_t ab = sa(sA[st]), bb = sa(b1);
+                    const uint32_t d = tm + 64 * st, dc = tm + 128 + 64 * st;
+                    for (int ks = 0; ks < K2p / 16; ++ks) {
+                        uint64_t ad[kParts], bd[kParts];
+                        for (int q = 0; q < kParts; ++q) {
+                            ad[q] = sdesc(ab + q * PB + ks * 256, 128, sbo_a);
+                            bd[q] = sdesc(bb + q * B1P + ks * 256, 128, sbo_a);
+                        }
+                        mma_bf16(d, ad[0], bd[0], idesc1, ks > 0);
+                        mma_bf16(dc, ad[0], bd[1], idesc1, ks > 0);
+                        mma_bf16(dc, ad[1], bd[0], idesc1, 1);
+                        mma_bf16(dc, ad[0], bd[2], idesc1, 1);
+                        mma_bf16(dc, ad[1], bd[1], idesc1, 1);
+                        mma_bf16(dc, ad[2], bd[0], idesc1, 1);
+                    }
+                    mma_commit(&g1[st]);
+                }
+                if (i >= 1) {
+                    const int p = i - 1, sp = p & 1;
+                    // W(p) written, D2 of tile p - 1 flushed, tile p's D1 and weights read
+                    if (!wait_bar(wready, (uint32_t)(p & 1))) break;
+                    tc_fence_after();
+                    if (p + 2 < nmine) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        issue_A(p + 2, sp);
+                    }
+                    if (!wait_bar(&tmaB[sp], (uint32_t)((p >> 1) & 1))) break;
+                    const uint32_t ab = sa(wt), bb = sa(sB[sp]);
+                    for (int ks = 0; ks < kRows / 16; ++ks) {
+                        uint64_t ad[kParts], bd[kParts];
+                        for (int q = 0; q < kParts; ++q) {
+                            ad[q] = sdesc(ab + q * WTP + ks * 2 * kLboW, kLboW, kSboW);
+                            bd[q] = sdesc(bb + q * PB + ks * 256, 128, sbo_t);
+                        }
+                        mma_bf16(tD2 + kMaxK2p * (ks & 3), ad[0], bd[0], idesc2, ks >= 4);
+                        mma_bf16(tD2c, ad[0], bd[1], idesc2, ks > 0);
+                        mma_bf16(tD2c, ad[1], bd[0], idesc2, 1);
+                        mma_bf16(tD2c, ad[0], bd[2], idesc2, 1);
+                        mma_bf16(tD2c, ad[1], bd[1], idesc2, 1);
+                        mma_bf16(tD2c, ad[2], bd[0], idesc2, 1);
+                    }
+                    mma_commit(g2);
+                    // its transposed-U stage is refilled once GEMM2(p) has read it
+                    if (p + 2 < nmine) {
+                        if (!wait_bar(g2, (uint32_t)(p & 1))) break;
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        issue_B(p + 2, sp);
+                    }
+                }
+            }
+        }
+    } else {
+        // ======== epilogue warps ========
+        const int j = lane / S, s = lane % S;  // slot j of the quarter's EW events, projection s
+        const bool row_used = j < a.EW;
+        float2 slnI[kCH];  // per-thread sums of w ln I as (hi, lo) pairs
 #pragma unroll
-    for (int c = 0; c < kCH; ++c) slnI[c] = make_float2(0.f, 0.f);
-    // the GEMM2 results of the CTA, rows n = 16 wq + lane (lane < 16), this warp's
-    // half of the 8-column chunks, as (hi, lo) pairs
-    const int nch = K2p / 16;  // chunks per half (1..3)
-    float2 acc[3][8];
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-#pragma unroll
-        for (int e = 0; e < 8; ++e) acc[q][e] = make_float2(0.f, 0.f);
-    auto flush_d2 = [&]() {
-        tc_fence_after();
+        for (int c = 0; c < kCH; ++c) slnI[c] = make_float2(0.f, 0.f);
+        // the GEMM2 results of the CTA, rows n = 16 wq + lane (lane < 16), this warp's
+        // half of the 8-column chunks, as (hi, lo) pairs
+        const int nch = K2p / 16;  // chunks per half (1..3)
+        float2 acc[3][8];
 #pragma unroll
         for (int q = 0; q < 3; ++q)
-            if (q < nch) {
-                const int col = 8 * (nch * half + q);
-                uint32_t v[5][8];
 #pragma unroll
-                for (int m = 0; m < 4; ++m) tmem_ld8(tD2 + kMaxK2p * m + tm_lane + col, v[m]);
-                tmem_ld8(tD2c + tm_lane + col, v[4]);
+            for (int e = 0; e < 8; ++e) acc[q][e] = make_float2(0.f, 0.f);
+        auto flush_d2 = [&]() {
+            tc_fence_after();
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                if (q < nch) {
+                    const int col = 8 * (nch * half + q);
+                    uint32_t v[5][8];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) tmem_ld8(tD2 + kMaxK2p * m + tm_lane + col, v[m]);
+                    tmem_ld8(tD2c + tm_lane + col, v[4]);
+                    tmem_wait();
+                    // the tile's five partials in FP32 (rounded to nearest: no systematic
+                    // error), then one compensated addition into the running sums
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const float x = ((__uint_as_float(v[0][e]) + __uint_as_float(v[1][e])) +
+                                         (__uint_as_float(v[2][e]) + __uint_as_float(v[3][e]))) +
+                                        __uint_as_float(v[4][e]);
+                        two_sum(acc[q][e], x);
+                    }
+                }
+        };
+        // a warp-uniform wait: lane 0 waits, the warp follows its verdict
+        auto warp_wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+            int ok = 1;
+            if (lane == 0) ok = wait_bar(bar, parity) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            tc_fence_after();
+            return ok != 0;
+        };
+        for (int i = 0; i < nmine; ++i) {
+            const int st = i & 1;
+            const uint32_t ph = (uint32_t)((i >> 1) & 1);
+            if (!warp_wait(&g1[st], ph) || !warp_wait(&tmaA[st], ph)) break;
+            const float wgt_tile =
+                reinterpret_cast<const float*>(sA[st] + kParts * PB)[wq * a.EW + min(j, a.EW - 1)];
+            // this row's coherent sums for this thread's vectors (main + correction accumulators)
+            float d1[4][kCH];
+            {
+                uint32_t v[4][8], vc[4][8];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    tmem_ld8(tm + 64 * st + tm_lane + q * kCV + kCH * half, v[q]);
+                    tmem_ld8(tm + 128 + 64 * st + tm_lane + q * kCV + kCH * half, vc[q]);
+                }
                 tmem_wait();
 #pragma unroll
-                for (int m = 0; m < 5; ++m)
+                for (int q = 0; q < 4; ++q)
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) two_sum(acc[q][e], __uint_as_float(v[m][e]));
+                    for (int cc = 0; cc < kCH; ++cc)
+                        d1[q][cc] = __uint_as_float(v[q][cc]) + __uint_as_float(vc[q][cc]);
             }
-    };
-
-    int mma2_pending = 0;  // GEMM2 commits not yet waited for (0 or 1)
-    int mma2_phase = 0;
-    bool fail = false;
-    if (tid == 0 && nmine > 0) {
-        fail = !wait_bar(&tmaA[0], 0);
-        if (!fail) gemm1(0);
-    }
-    if (__syncthreads_or(fail)) s_abort = 1;
-    int i = 0;
-    for (; i < nmine && !s_abort; ++i) {
-        const int st = i & 1;
-        const uint32_t ph = (uint32_t)((i >> 1) & 1);
-        // (a) GEMM1(i) done; the weights of tile i are read before its stage is refilled
-        bool ok = wait_bar(&mma1[st], ph);
-        tc_fence_after();
-        const float wgt_tile = reinterpret_cast<const float*>(sA[st] + kParts * PB)[wq * a.EW + min(j, a.EW - 1)];
-        if (__syncthreads_or(!ok)) {
-            s_abort = 1;
-            break;
-        }
-        if (tid == 0) {
-            // (b) stage A(i) is free: fetch tile i + 2; (c) GEMM1(i + 1) into the other accumulator
-            if (i + 2 < nmine) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue_A(i + 2, st);
-            }
-            if (i + 1 < nmine) {
-                if (wait_bar(&tmaA[st ^ 1], (uint32_t)(((i + 1) >> 1) & 1)))
-                    gemm1(i + 1);
-                else
-                    s_abort = 1;
-            }
-        }
-        // (d) epilogue: this row's coherent sums for this thread's vectors
-        float d1[4][kCH];
-        {
-            uint32_t v[4][8], vc[4][8];
+            const long long t = tile_of(i);
+            const long long ev = t * a.Et + (long long)wq * a.EW + j;
+            const bool valid = row_used && ev < a.n;
+            const float wgt = valid ? wgt_tile : 0.f;
+            const int base = S * j;  // first lane of this row's event
+            float wv[4][kCH];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                tmem_ld8(tm + 64 * st + tm_lane + q * kCV + kCH * half, v[q]);
-                tmem_ld8(tm + 128 + 64 * st + tm_lane + q * kCV + kCH * half, vc[q]);
+            for (int cc = 0; cc < kCH; ++cc) {
+                const int c = kCH * half + cc;
+                const float Ar = d1[0][cc], Ai = d1[1][cc], Dr = d1[2][cc], Di = d1[3][cc];
+                const float ip = fmaf(Ar, Ar, Ai * Ai), dp = 2.f * fmaf(Ar, Dr, Ai * Di);
+                float I = 0.f, Id = 0.f;
+                for (int q = 0; q < S; ++q) {
+                    I += __shfl_sync(0xffffffffu, ip, base + q);
+                    Id += __shfl_sync(0xffffffffu, dp, base + q);
+                }
+                float wa = 0.f, wb = 0.f;
+                if (valid && c < a.nv) {
+                    if (I > 0.f && I < INFINITY) {
+                        const float rI = __frcp_rn(I);
+                        wa = wgt * rI;
+                        wb = wa * Id * rI;
+                        if (s == 0) two_sum(slnI[cc], wgt * logf(I));
+                    } else if (s == 0) {
+                        atomicOr(a.err, pwa::ERR_NONFINITE);
+                        atomicOr(a.err + 1 + c, pwa::ERR_NONFINITE);
+                    }
+                }
+                wv[0][cc] = wa * Ar;
+                wv[1][cc] = wa * Ai;
+                wv[2][cc] = fmaf(wa, Dr, -wb * Ar);
+                wv[3][cc] = fmaf(wa, Di, -wb * Ai);
             }
-            tmem_wait();
+            // GEMM2(i - 1) done: take its results; then W of this tile may be written
+            if (i >= 1) {
+                if (!warp_wait(g2, (uint32_t)((i - 1) & 1))) break;
+                flush_d2();
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
-                for (int cc = 0; cc < kCH; ++cc) d1[q][cc] = __uint_as_float(v[q][cc]) + __uint_as_float(vc[q][cc]);
-        }
-        const long long t = tile_of(i);
-        const long long ev = t * a.Et + (long long)wq * a.EW + j;
-        const bool valid = row_used && ev < a.n;
-        const float wgt = valid ? wgt_tile : 0.f;
-        const int base = S * j;  // first lane of this row's event
-        float wv[4][kCH];
-#pragma unroll
-        for (int cc = 0; cc < kCH; ++cc) {
-            const int c = kCH * half + cc;
-            const float Ar = d1[0][cc], Ai = d1[1][cc], Dr = d1[2][cc], Di = d1[3][cc];
-            const float ip = fmaf(Ar, Ar, Ai * Ai), dp = 2.f * fmaf(Ar, Dr, Ai * Di);
-            float I = 0.f, Id = 0.f;
-            for (int q = 0; q < S; ++q) {
-                I += __shfl_sync(0xffffffffu, ip, base + q);
-                Id += __shfl_sync(0xffffffffu, dp, base + q);
-            }
-            float wa = 0.f, wb = 0.f;
-            if (valid && c < a.nv) {
-                if (I > 0.f && I < INFINITY) {
-                    const float rI = __frcp_rn(I);
-                    wa = wgt * rI;
-                    wb = wa * Id * rI;
-                    if (s == 0) two_sum(slnI[cc], wgt * logf(I));
-                } else if (s == 0) {
-                    atomicOr(a.err, pwa::ERR_NONFINITE);
-                    atomicOr(a.err + 1 + c, pwa::ERR_NONFINITE);
+                for (int cc = 0; cc < kCH; ++cc) {
+                    unsigned short p0, p1, p2;
+                    split3_bits(wv[q][cc], p0, p1, p2);
+                    const uint32_t off = kmaj16(q * kCV + kCH * half + cc, row, kLboW, kSboW);
+                    *reinterpret_cast<unsigned short*>(wt + off) = p0;
+                    *reinterpret_cast<unsigned short*>(wt + WTP + off) = p1;
+                    *reinterpret_cast<unsigned short*>(wt + 2 * WTP + off) = p2;
                 }
-            }
-            wv[0][cc] = wa * Ar;
-            wv[1][cc] = wa * Ai;
-            wv[2][cc] = fmaf(wa, Dr, -wb * Ar);
-            wv[3][cc] = fmaf(wa, Di, -wb * Ai);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(wready)) : "memory");
         }
-        // (e) GEMM2(i - 1) done: flush its results, refill its transposed-U buffer
-        if (mma2_pending) {
-            ok = wait_bar(mma2, (uint32_t)(mma2_phase & 1));
-            ++mma2_phase;
-            mma2_pending = 0;
-            if (__syncthreads_or(!ok)) {
-                s_abort = 1;
-                break;
-            }
-            flush_d2();
-            if (tid == 0 && i + 1 < nmine) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue_B(i + 1, st ^ 1);
-            }
-        }
-        // (f) the W rows of this tile (three parts)
+        // the last GEMM2
+        if (nmine > 0 && !s_abort && warp_wait(g2, (uint32_t)((nmine - 1) & 1))) flush_d2();
+        if (!s_abort) {
+            double* rq = a.rec + (size_t)blockIdx.x * (kN1 * K2p + kCV);
+            if (lane < 16) {
+                const int n = 16 * wq + lane;
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+                for (int q = 0; q < 3; ++q)
+                    if (q < nch)
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            rq[(size_t)n * K2p + 8 * (nch * half + q) + e] =
+                                (double)acc[q][e].x + (double)acc[q][e].y;
+            }
 #pragma unroll
             for (int cc = 0; cc < kCH; ++cc) {
-                __nv_bfloat16 p0, p1, p2;
-                split3(wv[q][cc], p0, p1, p2);
-                const uint32_t off = kmaj16(q * kCV + kCH * half + cc, row, kLboW, kSboW);
-                *reinterpret_cast<__nv_bfloat16*>(wt + off) = p0;
-                *reinterpret_cast<__nv_bfloat16*>(wt + WTP + off) = p1;
-                *reinterpret_cast<__nv_bfloat16*>(wt + 2 * WTP + off) = p2;
+                double v = (double)slnI[cc].x + (double)slnI[cc].y;
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) s_red[warp][cc] = v;
             }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (s_abort) break;
-        // (g) GEMM2(i) once its transposed U has arrived
-        bool late = false;
-        if (tid == 0) {
-            if (wait_bar(&tmaB[st], ph))
-                gemm2(i);
-            else
-                late = true;
         }
-        if (__syncthreads_or(late)) {
-            s_abort = 1;
-            break;
-        }
-        mma2_pending = 1;
-    }
-    // ---- finish: the last GEMM2, its flush, the CTA's sums
-    if (!s_abort && mma2_pending) {
-        const bool ok = wait_bar(mma2, (uint32_t)(mma2_phase & 1));
-        ++mma2_phase;
-        mma2_pending = 0;
-        if (__syncthreads_or(!ok))
-            s_abort = 1;
-        else
-            flush_d2();
     }
     __syncthreads();
     if (s_abort) {
         if (tid == 0) atomicOr(a.err, pwa::ERR_TIMEOUT);
-    } else {
-        double* rq = a.rec + (size_t)blockIdx.x * (kN1 * K2p + kCV);
-        if (lane < 16) {
-            const int n = 16 * wq + lane;
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-                if (q < nch)
-#pragma unroll
-                    for (int e = 0; e < 8; ++e)
-                        rq[(size_t)n * K2p + 8 * (nch * half + q) + e] = (double)acc[q][e].x + (double)acc[q][e].y;
-        }
-        double* rs = rq + (size_t)kN1 * K2p;
-#pragma unroll
-        for (int cc = 0; cc < kCH; ++cc) {
-            double v = (double)slnI[cc].x + (double)slnI[cc].y;
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) s_red[warp][cc] = v;
-        }
-        __syncthreads();
-        if (tid < kCV) {
-            const int h = tid / kCH, cc = tid % kCH;  // vector tid: warps 4 h .. 4 h + 3
-            rs[tid] = ((s_red[4 * h][cc] + s_red[4 * h + 1][cc]) + s_red[4 * h + 2][cc]) + s_red[4 * h + 3][cc];
-        }
+    } else if (tid < kCV) {
+        double* rs = a.rec + (size_t)blockIdx.x * (kN1 * K2p + kCV) + (size_t)kN1 * K2p;
+        const int h = tid / kCH, cc = tid % kCH;  // vector tid: warps 4 h .. 4 h + 3
+        rs[tid] = ((s_red[4 * h][cc] + s_red[4 * h + 1][cc]) + s_red[4 * h + 2][cc]) + s_red[4 * h + 3][cc];
     }
-    // drain: a timed-out CTA waits (bounded) for its own MMAs and copies before freeing TMEM
-    if (s_abort && tid == 0) {
-        if (mma2_pending) (void)wait_bar(mma2, (uint32_t)(mma2_phase & 1));
+    // a CTA that gave up waits (bounded, each barrier once) for the work it started before freeing TMEM
+    if (s_abort && producer && lane == 0) {
+        s_abort = 0;  // let the drain waits run their course
         for (int q = 0; q < 2; ++q) {
-            (void)wait_bar(&mma1[q], (uint32_t)(((i + q) >> 1) & 1));
-            (void)wait_bar(&tmaA[q], (uint32_t)(((i + q) >> 1) & 1));
-            (void)wait_bar(&tmaB[q], (uint32_t)(((i + q) >> 1) & 1));
+            (void)wait_bar(&g1[q], 0);
+            (void)wait_bar(&tmaA[q], 0);
+            (void)wait_bar(&tmaB[q], 0);
         }
+        (void)wait_bar(g2, 0);
+        s_abort = 1;
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kTmemCols));
+    if (producer) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kTmemCols));
 }
 
 // ---------------------------------------------------------------------------
@@ -795,7 +799,7 @@ pwa_status cp_launch(pwa_coupling* cp, int nv, const double* theta_c, const doub
     a.rec = cp->d_rec;
     a.err = cp->d_err;
     a.timeout = h->timeout_cycles;
-    coupling_kernel<<<cp->grid, kCT, cp->smem, s>>>(a);
+    coupling_kernel<<<cp->grid, kCT + 32, cp->smem, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cp_cuda(cp, e, "coupling kernel launch");
     coupling_combine_kernel<<<nv, std::max(32, (K + 31) / 32 * 32), sizeof(double) * (8 * K + 4), s>>>(
