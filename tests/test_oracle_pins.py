@@ -204,3 +204,109 @@ def test_integral_matrix_reproduces_the_mc_sum(paper_small):
         g = oracle.couplings(model, th2)
         total = float(np.sum(oracle.intensity(model, th2, wl.mc.m2, wl.mc.F)))
         assert abs(np.real(g.conj() @ phi @ g) - total) <= 1e-11 * total
+
+
+def test_mlp_oracle_gradients_match_finite_differences():
+    """The proposal network's oracle (plain FP64, no rounding): backward pass
+    against central differences of its own loss, for squared-error and
+    periodic (1 - cos) outputs."""
+    from oracle import mlp
+    rng = np.random.default_rng(3)
+    sizes = [12, 8, 8, 5]
+    params = mlp.init_params(sizes, seed=1)
+    x = rng.standard_normal((7, 12))
+    t = rng.standard_normal((7, 5))
+    weight = np.array([1.0, 0.5, 2.0, 1.0, 1.0])
+    periodic = [0, 0, 1, 0, 1]
+    loss, grads = mlp.loss_and_grads(params, x, t, weight, periodic)
+    h = 1e-6
+
+    def perturbed(l, which, idx, s):
+        ps = [(w.copy(), bb.copy()) for w, bb in params]
+        ps[l][which][idx] += s
+        return mlp.loss_and_grads(ps, x, t, weight, periodic)[0]
+
+    for l, (W, b) in enumerate(params):
+        for idx in [(0, 0), (W.shape[0] - 1, W.shape[1] - 1), (1, 2)]:
+            fd = (perturbed(l, 0, idx, h) - perturbed(l, 0, idx, -h)) / (2 * h)
+            assert abs(fd - grads[l][0][idx]) <= 1e-6 * max(1.0, abs(fd)), (l, idx, fd, grads[l][0][idx])
+        k = (b.size - 1,)
+        fd = (perturbed(l, 1, k, h) - perturbed(l, 1, k, -h)) / (2 * h)
+        assert abs(fd - grads[l][1][k]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_mlp_oracle_reduces_to_least_squares():
+    """One affine layer with squared error: the loss is the least-squares
+    objective, whose gradient vanishes at numpy's lstsq solution."""
+    from oracle import mlp
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((40, 6))
+    t = rng.standard_normal((40, 3))
+    X1 = np.hstack([x, np.ones((40, 1))])
+    sol = np.linalg.lstsq(X1, t, rcond=None)[0]
+    params = [(sol[:6].T.copy(), sol[6].copy())]
+    loss, grads = mlp.loss_and_grads(params, x, t, np.ones(3), [0, 0, 0])
+    assert np.max(np.abs(grads[0][0])) < 1e-12 and np.max(np.abs(grads[0][1])) < 1e-12
+    assert abs(loss - 0.5 * np.sum((X1 @ sol - t) ** 2) / 40) < 1e-12
+
+
+def test_bf16_rounding_is_nearest_even():
+    from oracle import mlp
+    # 1 + 2^-8 lies halfway between 1 and 1 + 2^-7: ties go to the even 1
+    assert mlp.bf16(np.array([1.0 + 2 ** -8]))[0] == 1.0
+    assert mlp.bf16(np.array([1.0 + 3 * 2 ** -8]))[0] == 1.0 + 2 ** -6
+    x = np.random.default_rng(0).standard_normal(1000)
+    assert np.max(np.abs(mlp.bf16(x) - x) / np.abs(x)) <= 2 ** -8
+
+
+def test_splitmix64_known_answers():
+    """splitmix64 started at 0: its first three outputs as published with the
+    reference implementation (Vigna, splitmix64.c)."""
+    from oracle import generate as og
+    out = og.splitmix64(0, np.arange(3))
+    assert [int(v) for v in out] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_accept_reject_oracle_against_a_plain_loop_and_its_distribution():
+    from oracle import generate as og
+    rng = np.random.default_rng(5)
+    n = 3000
+    I = rng.random(n).astype(np.float32) * 4
+    idx, C = og.accept_reject(I, 0.0, seed=77, start=1234, n_target=400)
+    assert C == float(np.float32(I).max())
+    # brute force: walk the pool from `start`, keep while fewer than n_target
+    want = []
+    for i in range(n):
+        j = (1234 + i) % n
+        u = int(og.splitmix64(77, np.array([j]))[0] >> np.uint64(11)) * 2.0 ** -53
+        if u * C < float(I[j]) and len(want) < 400:
+            want.append(j)
+    assert idx.tolist() == want
+    # I = C everywhere keeps every event in order; I = 0 keeps none
+    full, _ = og.accept_reject(np.full(50, 2.0, np.float32), 2.0, seed=1, start=45, n_target=50)
+    assert full.tolist() == list(range(45, 50)) + list(range(45))
+    none, _ = og.accept_reject(np.zeros(50, np.float32), 1.0, seed=1, start=0, n_target=50)
+    assert none.size == 0
+    # kept fraction per intensity band follows I / C (binomial, 5 sigma)
+    I = np.repeat(np.array([0.1, 0.5, 0.9], np.float32), 20000)
+    idx, _ = og.accept_reject(I, 1.0, seed=9, start=0, n_target=10 ** 9)
+    for b, p in enumerate([0.1, 0.5, 0.9]):
+        k = np.sum((idx >= 20000 * b) & (idx < 20000 * (b + 1)))
+        assert abs(k - 20000 * p) < 5 * np.sqrt(20000 * p * (1 - p))
+
+
+def test_dalitz_histogram_oracle_against_a_plain_loop():
+    from oracle import generate as og
+    rng = np.random.default_rng(8)
+    m2 = rng.uniform(0.0, 9.0, size=(3, 500)).astype(np.float32)
+    idx = rng.choice(500, size=300, replace=False)
+    bounds = (0.5, 8.0, 0.25, 7.5)
+    h = og.dalitz_histogram(m2, idx, 8, bounds, log_scale=False)
+    want = np.zeros(64)
+    for e in idx:
+        bx = min(max(int(math.floor((float(m2[0, e]) - 0.5) * 8 / 7.5)), 0), 7)
+        by = min(max(int(math.floor((float(m2[2, e]) - 0.25) * 8 / 7.25)), 0), 7)
+        want[bx * 8 + by] += 1
+    assert np.array_equal(h, want) and h.sum() == 300
+    hl = og.dalitz_histogram(m2, idx, 8, bounds, log_scale=True)
+    assert np.allclose(hl, np.log(1 + want * 64 / 300), rtol=0, atol=1e-15)
