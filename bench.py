@@ -49,14 +49,13 @@ def peaks():
         return 6400.0, "fallback"
 
 
-def tf32_peak():
-    """Dense TF32 tensor peak: the measured bf16 figure times the nominal
-    tf32 / bf16 ratio (1.1 / 2.25 PFLOP/s), or the fallback bf16 figure."""
+def bf16_peak():
+    """Dense BF16 tensor peak: the measured burst figure, or the fallback."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["bf16_tflops"]) * (1.1 / 2.25), "measured bf16 x nominal tf32/bf16"
+            return float(json.load(f)["bf16_tflops"]), "measured"
     except Exception:
-        return 1800.0 * (1.1 / 2.25), "fallback bf16 x nominal tf32/bf16"
+        return 1800.0, "fallback"
 
 
 def bytes_per_pass(nd, nm, K, S):
@@ -298,8 +297,9 @@ def batching_metric(n_toys: int, n_starts: int, time_limit: float, seed: int = 7
 def coupling_metric(L, wl, reps: int = 20):
     """The fixed-mass coupling sub-problem at the paper scale: NLL, gradient
     and H v in the coupling parameters for 16 coupling vectors per call
-    (tcgen05 TF32-split GEMMs over U = BW F tiles of the data events plus the
-    K x K integral matrix for the MC term), against one fused pass per vector.
+    (tcgen05 GEMMs on three-part BF16 splits of U = BW F tiles of the data
+    events plus the K x K integral matrix for the MC term), against one fused
+    pass per vector.
     Times are host-synchronous calls (upload, launches, download)."""
     from paper_2403_09225_b300 import binding
     th0 = wl.theta_true
@@ -325,17 +325,78 @@ def coupling_metric(L, wl, reps: int = 20):
         rows_per_call = wl.data.n * wl.S
         # useful flops per (event, projection) row: two real GEMMs of 2K x 4C
         flops = 2 * 2.0 * (2 * wl.K) * (4 * C) * rows_per_call
-        tpk, tkind = tf32_peak()
+        tpk, tkind = bf16_peak()
         achieved = flops / (ms * 1e-3) / 1e12
         return {"vectors_per_call": C, "ms_per_call": ms, "us_per_vector": ms * 1e3 / C,
                 "fused_pass_us_per_vector": fused_ms * 1e3, "speedup_per_vector": fused_ms * C / ms,
                 "create_s": create_s, "K": wl.K, "S": wl.S, "data_events": wl.data.n,
                 "roofline": {"bound": "tensor", "achieved": achieved, "unit": "TFLOP/s",
                              "peak": tpk, "frac": achieved / tpk, "peak_kind": tkind,
-                             "flops_per_call": flops, "note": "useful flops of the two GEMMs; the TF32 "
-                             "three-term split issues 3x as many"}}
+                             "flops_per_call": flops, "note": "useful flops of the two GEMMs; the BF16 "
+                             "three-part split issues 6 products (split terms i + j <= 2) per useful one"}}
     finally:
         cp.close()
+
+
+def learned_metric(n_train: int, n_eval: int, n_random: int, time_limit: float, pool: int = 10_000_000,
+                   n_events: int = 100_000, n_mc: int = 500_000, epochs: int = 40):
+    """The learned starting-point proposal on the paper-scale model (K = 20,
+    S = 4, 78 parameters): n_train pseudo-experiments (theta from the prior,
+    up to n_events events accept-rejected from a pool of phase-space events,
+    labels from capped Newton-CG fits started at theta), the 4096 -> 3 x 512
+    -> 78 network trained with the library's BF16 kernels, then n_eval
+    held-out experiments fitted from the network's start and from n_random
+    prior starts (one batched call) with the same options."""
+    import torch
+    from paper_2403_09225_b300 import proposal, workload as W
+    cfg = W.CONFIGS["paper"]
+    table = W.make_table(cfg)
+    t0 = time.perf_counter()
+    gen = proposal.Generator(table, cfg.S, pool_size=pool, n_mc=n_mc, seed=7)
+    gen_setup_s = time.perf_counter() - t0
+    try:
+        t0 = time.perf_counter()
+        ex = proposal.make_experiments(gen, n_train, n_events, seed=100)
+        make_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        net, codec, hist = proposal.train(ex, table, epochs=epochs, batch=128, lr=1e-3)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        # one training step's tensor-core throughput (forward + backward products: 6 B fan_in fan_out)
+        sizes = [(net.n_in, net.hidden)] + [(net.hidden, net.hidden)] * (net.layers - 1) + \
+                [(net.hidden, 128 * ((net.n_out + 127) // 128))]
+        flops = 6.0 * 128 * sum(a * b for a, b in sizes)
+        T = torch.from_numpy(codec.encode(ex.theta_fit[:128])).cuda()
+        stream = torch.cuda.current_stream()
+        for _ in range(5):
+            net.gradients(ex.X[:128], T)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 50
+        e0.record(stream)
+        for _ in range(reps):
+            net.gradients(ex.X[:128], T)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms = e0.elapsed_time(e1) / reps
+        peak, kind = bf16_peak()
+        t0 = time.perf_counter()
+        recs, summ = proposal.evaluate(gen, net, codec, n_eval, n_events, n_random, seed=999,
+                                       fit_opts=dict(time_limit_s=time_limit))
+        eval_s = time.perf_counter() - t0
+        net.close()
+        return {"model": "paper-scale table: K=20, S=4, P=78", "train_experiments": n_train,
+                "eval_experiments": n_eval, "events_per_experiment": n_events, "pool_events": pool,
+                "mc_events": n_mc, "kept_events_min_mean": [int(ex.n_events.min()), float(ex.n_events.mean())],
+                "label_fit_s": ex.fit_s, "generate_s": ex.gen_s, "setup_s": gen_setup_s, "make_s": make_s,
+                "epochs": epochs, "train_s": train_s, "loss_first_last": [hist[0], hist[-1]],
+                "fit_time_limit_s": time_limit, "eval_s": eval_s, **summ,
+                "gradient_step": {"batch": 128, "ms": step_ms, "flops": flops,
+                                  "roofline": {"bound": "tensor", "achieved": flops / (step_ms * 1e-3) / 1e12,
+                                               "unit": "TFLOP/s", "peak": peak,
+                                               "frac": flops / (step_ms * 1e-3) / 1e12 / peak,
+                                               "peak_kind": kind}}}
+    finally:
+        gen.close()
 
 
 def measured_traffic(tiling: dict):
@@ -383,6 +444,8 @@ def main():
     ap.add_argument("--no-coupling", action="store_true", help="skip the fixed-mass coupling sub-problem leg")
     ap.add_argument("--batching", default="", metavar="TOYS,STARTS",
                     help="also run the uneven-size toy-fit comparison (plain vs batched), e.g. 12,4")
+    ap.add_argument("--learned", default="", metavar="TRAIN,EVAL,STARTS",
+                    help="also train and evaluate the learned starting-point proposal, e.g. 4096,16,16")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="event counts relative to the workload (profiling captures only; default 1)")
     args = ap.parse_args()
@@ -465,6 +528,11 @@ def main():
         n_toys, n_starts = (int(x) for x in args.batching.split(","))
         batching = batching_metric(n_toys, n_starts, time_limit=args.fit_time_limit)
 
+    learned = None
+    if args.learned and rank == 0:
+        n_train, n_eval, n_rand = (int(x) for x in args.learned.split(","))
+        learned = learned_metric(n_train, n_eval, n_rand, time_limit=args.fit_time_limit)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_leg()
@@ -498,6 +566,8 @@ def main():
             res["batching"] = batching
         if coupling is not None:
             res["coupling"] = coupling
+        if learned is not None:
+            res["learned"] = learned
         print(json.dumps(res))
     L.close()
     if dist:

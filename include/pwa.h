@@ -300,6 +300,94 @@ pwa_status pwa_coupling_fit(pwa_coupling* cp, int C, const double* theta_c0, con
 
 void pwa_coupling_destroy(pwa_coupling* cp);
 
+/* ---- pseudo-experiment generation (paper Sec. 3 draws its test samples
+ * from the PWA model itself) ----
+ *
+ * A pool of phase-space events (m2 [3][n], F [n][K][S] as in pwa_events) and
+ * their intensities I(e; theta) (pwa_event_intensity of a handle whose MC
+ * sample is the pool) define a pseudo-experiment by accept-reject: event j is
+ * kept when u_j C < I_j, with u_j = (z >> 11) 2^-53 and z output j + 1 of
+ * splitmix64 started at `seed` (Steele, Lea and Flood 2014), compared in
+ * double precision.  All three calls work on device arrays and synchronise
+ * cuda_stream (a cudaStream_t or NULL) before they return.  Errors go to
+ * pwa_last_generate_error(). */
+
+/* Pool indices of the first n_target kept events in the order
+ * start, start + 1, ..., n - 1, 0, ..., start - 1, written to d_idx
+ * [n_target]; *n_out = how many were kept (<= n_target).  C <= 0 takes
+ * C = max_j I_j; *C_used (may be NULL) receives the C applied.
+ * Errors: PWA_EINVAL (n < 1 or >= 2^31, start outside [0, n), n_target < 0,
+ * C not finite), PWA_ENONFINITE (an I_j negative or not finite), PWA_ECUDA. */
+pwa_status pwa_accept_reject(const float* d_I, long long n, double C, unsigned long long seed,
+                             long long start, int n_target, int* d_idx, int* n_out,
+                             double* C_used, void* cuda_stream);
+
+/* Binned Dalitz plot of the events d_idx [n] of a pool with m2 [3][ld]:
+ * x = m12^2, y = m23^2, nb x nb bins over [x0, x1) x [y0, y1),
+ * bx = floor((x - x0) nb / (x1 - x0)) clamped to 0 .. nb - 1 (double
+ * precision), likewise by; d_out [nb * nb] FP32 at bx * nb + by holds the
+ * count, or log(1 + count nb^2 / n) when log_scale is 1.
+ * Errors: PWA_EINVAL, PWA_ECUDA. */
+pwa_status pwa_dalitz_histogram(const float* d_m2, long long ld, const int* d_idx, int n, int nb,
+                                double x0, double x1, double y0, double y1, int log_scale,
+                                float* d_out, void* cuda_stream);
+
+/* Gather events d_idx [n] of a pool (m2 [3][ld], F [ld][KS] complex) into a
+ * sample: m2_out [3][n], F_out [n][KS] complex.  Errors: PWA_EINVAL, PWA_ECUDA. */
+pwa_status pwa_gather_events(const float* d_m2, long long ld, const float* d_F, int KS,
+                             const int* d_idx, int n, float* d_m2_out, float* d_F_out,
+                             void* cuda_stream);
+
+/* Message of the last failure of the three calls above in this thread. */
+const char* pwa_last_generate_error(void);
+
+/* ---- learned starting-point proposal (no counterpart in the paper) ----
+ *
+ * A multilayer perceptron that maps a binned Dalitz histogram of a data set
+ * to a starting theta for Newton-CG, trained on pseudo-experiments the method
+ * generates (sample theta, accept-reject events from I, fit).  in inputs ->
+ * `layers` hidden layers of `hidden` units with GELU (tanh form) -> out
+ * outputs.  BF16 weights and activations, FP32 accumulation: every matrix
+ * product is one tcgen05 tensor-core kernel of this library; Adam on FP32
+ * master weights.  Loss: weighted squared error per output, or 1 - cos of the
+ * difference for outputs flagged periodic (phases), averaged over the rows.
+ * Sizes: in % 64 == 0, hidden % 128 == 0, batches a multiple of 128 up to
+ * max_batch.  Initial weights uniform in +-sqrt(6 / (fan_in + fan_out)) from a
+ * splitmix64 stream seeded with `seed`; biases 0.  All array arguments of the
+ * forward and training calls are device pointers (FP32, row-major). */
+typedef struct pwa_mlp pwa_mlp; /* opaque; owned by the library */
+
+pwa_status pwa_mlp_create(int in, int hidden, int layers, int out, int max_batch,
+                          unsigned long long seed, const int* periodic /* host [out] or NULL */,
+                          const float* loss_weight /* host [out] or NULL (= 1) */,
+                          void* cuda_stream, pwa_mlp** out_m);
+
+/* y [B][out] = network(x [B][in]); synchronous on the network's stream. */
+pwa_status pwa_mlp_forward(pwa_mlp* m, int B, const float* d_x, float* d_y);
+
+/* Loss (host, mean over the B rows) and the gradients of every parameter for
+ * inputs x [B][in] and targets t [B][out]; the gradients stay in the object
+ * (pwa_mlp_params, which = 2 and 3). */
+pwa_status pwa_mlp_gradients(pwa_mlp* m, int B, const float* d_x, const float* d_t, double* loss);
+
+/* pwa_mlp_gradients followed by one Adam step (beta 0.9, 0.999, eps 1e-8). */
+pwa_status pwa_mlp_train_step(pwa_mlp* m, int B, const float* d_x, const float* d_t, float lr, double* loss);
+
+/* Copy parameters between the object and host memory.  layer 0 .. layers
+ * (the last is the output layer); which: 0 W [fan_out][fan_in], 1 bias
+ * [fan_out], 2 the last weight gradient, 3 the last bias gradient (2 and 3
+ * read only).  to_device = 1 writes the object (0 and 1 only). */
+pwa_status pwa_mlp_params(pwa_mlp* m, int layer, int which, float* host, int to_device);
+
+/* The tensor-core product alone: C [M][N] = A [M][K] B [N][K]^T for host FP32
+ * arrays rounded to BF16 (M % 128, N % 64, K % 64 == 0); for tests. */
+pwa_status pwa_mlp_gemm_check(pwa_mlp* m, int M, int N, int K, const float* A, const float* B, float* C);
+
+/* Message of the last failure of m (or of the last pwa_mlp_create when m is NULL). */
+const char* pwa_mlp_last_error(const pwa_mlp* m);
+
+void pwa_mlp_destroy(pwa_mlp* m);
+
 /* Default options: xtol 1e-8, gtol 0, maxiter 0 (= 200 P), cg_maxiter 0
  * (= 20 P), no time limit. */
 void pwa_fit_opts_default(pwa_fit_opts* opts);

@@ -58,7 +58,10 @@ EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "
            "pwa_newton_cg_fit_multi", "pwa_autotune", "pwa_coupling_create", "pwa_coupling_num_params",
            "pwa_coupling_integral_matrix", "pwa_coupling_eval", "pwa_coupling_fit", "pwa_coupling_destroy",
            "pwa_fit_opts_default", "pwa_set_stream", "pwa_set_tiling", "pwa_get_tiling",
-           "pwa_selftest_bounded_wait", "pwa_last_error", "pwa_destroy")
+           "pwa_selftest_bounded_wait", "pwa_last_error", "pwa_destroy", "pwa_mlp_create", "pwa_mlp_forward",
+           "pwa_mlp_gradients", "pwa_mlp_train_step", "pwa_mlp_params", "pwa_mlp_gemm_check",
+           "pwa_mlp_last_error", "pwa_mlp_destroy", "pwa_accept_reject", "pwa_dalitz_histogram",
+           "pwa_gather_events", "pwa_last_generate_error")
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -67,6 +70,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib = ctypes.CDLL(path)
     H, vp, dp, ip, i = ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), \
         ctypes.POINTER(ctypes.c_int), ctypes.c_int
+    fp = ctypes.POINTER(ctypes.c_float)
     st = ctypes.c_int
     sig = {
         "pwa_create": (st, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(pwa_events),
@@ -102,6 +106,20 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pwa_selftest_bounded_wait": (st, [ctypes.c_double]),
         "pwa_last_error": (ctypes.c_char_p, [H]),
         "pwa_destroy": (None, [H]),
+        "pwa_mlp_create": (st, [i, i, i, i, i, ctypes.c_ulonglong, ip, fp, vp, ctypes.POINTER(ctypes.c_void_p)]),
+        "pwa_mlp_forward": (st, [vp, i, vp, vp]),
+        "pwa_mlp_gradients": (st, [vp, i, vp, vp, dp]),
+        "pwa_mlp_train_step": (st, [vp, i, vp, vp, ctypes.c_float, dp]),
+        "pwa_mlp_params": (st, [vp, i, i, fp, i]),
+        "pwa_mlp_gemm_check": (st, [vp, i, i, i, fp, fp, fp]),
+        "pwa_mlp_last_error": (ctypes.c_char_p, [vp]),
+        "pwa_mlp_destroy": (None, [vp]),
+        "pwa_accept_reject": (st, [vp, ctypes.c_longlong, ctypes.c_double, ctypes.c_ulonglong, ctypes.c_longlong, i,
+                                   vp, ip, dp, vp]),
+        "pwa_dalitz_histogram": (st, [vp, ctypes.c_longlong, vp, i, i, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, i, vp, vp]),
+        "pwa_gather_events": (st, [vp, ctypes.c_longlong, vp, i, vp, i, vp, vp, vp]),
+        "pwa_last_generate_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -430,6 +448,150 @@ def fit_multi(likelihoods, thetas0, xtol: float = 1e-8, gtol: float = 0.0, maxit
     infos = [[{"nll": r.nll, "grad_max": r.grad_max, "iters": r.iters, "n_hvp": r.n_hvp, "n_fev": r.n_fev,
                "status": FIT_STATUS_NAMES[r.status], "elapsed_s": r.elapsed_s} for r in rr] for rr in res]
     return outs, infos, st == PWA_OK
+
+
+def _gen_check(st: int):
+    if st != PWA_OK:
+        raise PwaError(st, lib().pwa_last_generate_error().decode())
+
+
+def _cuda_f32(t, what: str):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError("%s: expected a contiguous CUDA float32 tensor" % what)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def accept_reject(I, seed: int, start: int, n_target: int, C: float = 0.0, stream: int = 0):
+    """Counter-based accept-reject over a pool's intensities I (CUDA float32
+    [n]); returns (pool indices as a CUDA int32 tensor [n_kept], C used)."""
+    import torch
+    idx = torch.empty(max(1, n_target), dtype=torch.int32, device=I.device)
+    n_out = ctypes.c_int()
+    c_used = ctypes.c_double()
+    _gen_check(lib().pwa_accept_reject(_cuda_f32(I, "I"), int(I.numel()), float(C), ctypes.c_ulonglong(seed),
+                                       int(start), int(n_target), ctypes.c_void_p(idx.data_ptr()),
+                                       ctypes.byref(n_out), ctypes.byref(c_used), ctypes.c_void_p(stream)))
+    return idx[:n_out.value], c_used.value
+
+
+def dalitz_histogram(m2, idx, nb: int, bounds, log_scale: bool = True, out=None, stream: int = 0):
+    """nb x nb histogram of (m12^2, m23^2) over the pool events idx (CUDA int32);
+    m2: CUDA float32 [3, ld]; returns CUDA float32 [nb * nb] (or fills out)."""
+    import torch
+    if out is None:
+        out = torch.empty(nb * nb, dtype=torch.float32, device=m2.device)
+    x0, x1, y0, y1 = bounds
+    _gen_check(lib().pwa_dalitz_histogram(_cuda_f32(m2, "m2"), int(m2.shape[1]), ctypes.c_void_p(idx.data_ptr()),
+                                          int(idx.numel()), int(nb), x0, x1, y0, y1, int(bool(log_scale)),
+                                          _cuda_f32(out, "out"), ctypes.c_void_p(stream)))
+    return out
+
+
+def gather_events(m2, F, idx, stream: int = 0):
+    """Sample arrays (m2 [3, n], F [n, K, S] complex as float32 [..., 2]) of the
+    pool events idx; m2: CUDA float32 [3, ld], F: CUDA float32 [ld, K, S, 2]."""
+    import torch
+    n = int(idx.numel())
+    KS = int(F.shape[1] * F.shape[2])
+    m2o = torch.empty((3, max(n, 1)), dtype=torch.float32, device=m2.device)
+    Fo = torch.empty((max(n, 1),) + tuple(F.shape[1:]), dtype=torch.float32, device=m2.device)
+    _gen_check(lib().pwa_gather_events(_cuda_f32(m2, "m2"), int(m2.shape[1]), _cuda_f32(F, "F"), KS,
+                                       ctypes.c_void_p(idx.data_ptr()), n, _cuda_f32(m2o, "m2_out"),
+                                       _cuda_f32(Fo, "F_out"), ctypes.c_void_p(stream)))
+    return m2o[:, :n], Fo[:n]
+
+
+class ProposalMLP:
+    """The learned starting-point proposal network (see include/pwa.h):
+    in -> `layers` x hidden (GELU) -> out, BF16 tensor-core products, Adam.
+    Inputs and targets are torch CUDA float32 tensors [B, in] / [B, out] with
+    B a multiple of 128; parameters move through host numpy arrays."""
+
+    def __init__(self, n_in: int, hidden: int, layers: int, n_out: int, max_batch: int, seed: int = 1,
+                 periodic=None, loss_weight=None, stream: int = 0):
+        per = None if periodic is None else (ctypes.c_int * n_out)(*[int(bool(x)) for x in periodic])
+        wg = None if loss_weight is None else (ctypes.c_float * n_out)(*[float(x) for x in loss_weight])
+        h = ctypes.c_void_p()
+        st = lib().pwa_mlp_create(n_in, hidden, layers, n_out, max_batch, ctypes.c_ulonglong(seed),
+                                  ctypes.cast(per, ctypes.POINTER(ctypes.c_int)) if per is not None else None,
+                                  ctypes.cast(wg, ctypes.POINTER(ctypes.c_float)) if wg is not None else None,
+                                  ctypes.c_void_p(stream), ctypes.byref(h))
+        if st != PWA_OK:
+            raise PwaError(st, lib().pwa_mlp_last_error(None).decode())
+        self._h = h
+        self.n_in, self.hidden, self.layers, self.n_out, self.max_batch = n_in, hidden, layers, n_out, max_batch
+
+    def _check(self, st: int):
+        if st != PWA_OK:
+            raise PwaError(st, lib().pwa_mlp_last_error(self._h).decode())
+
+    @staticmethod
+    def _dev(t, cols: int):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+                and t.dim() == 2 and t.shape[1] == cols):
+            raise ValueError("expected a contiguous CUDA float32 tensor [B, %d]" % cols)
+        return ctypes.c_void_p(t.data_ptr())
+
+    def forward(self, x):
+        import torch
+        y = torch.empty((x.shape[0], self.n_out), dtype=torch.float32, device=x.device)
+        self._check(lib().pwa_mlp_forward(self._h, int(x.shape[0]), self._dev(x, self.n_in), self._dev(y, self.n_out)))
+        return y
+
+    def gradients(self, x, t) -> float:
+        loss = ctypes.c_double()
+        self._check(lib().pwa_mlp_gradients(self._h, int(x.shape[0]), self._dev(x, self.n_in),
+                                            self._dev(t, self.n_out), ctypes.byref(loss)))
+        return loss.value
+
+    def train_step(self, x, t, lr: float) -> float:
+        loss = ctypes.c_double()
+        self._check(lib().pwa_mlp_train_step(self._h, int(x.shape[0]), self._dev(x, self.n_in),
+                                             self._dev(t, self.n_out), ctypes.c_float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def _shape(self, layer: int, which: int):
+        fi = self.n_in if layer == 0 else self.hidden
+        fo = self.n_out if layer == self.layers else self.hidden
+        return (fo, fi) if which in (0, 2) else (fo,)
+
+    def get(self, layer: int, which: int) -> np.ndarray:
+        """which: 0 W, 1 bias, 2 last weight gradient, 3 last bias gradient."""
+        a = np.empty(self._shape(layer, which), dtype=np.float32)
+        self._check(lib().pwa_mlp_params(self._h, layer, which, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 0))
+        return a
+
+    def set(self, layer: int, which: int, values):
+        a = np.ascontiguousarray(np.asarray(values, dtype=np.float32).reshape(self._shape(layer, which)))
+        self._check(lib().pwa_mlp_params(self._h, layer, which, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 1))
+
+    def params(self):
+        """[(W, b)] per layer as float64 arrays."""
+        return [(self.get(l, 0).astype(np.float64), self.get(l, 1).astype(np.float64))
+                for l in range(self.layers + 1)]
+
+    def gemm_check(self, A, B) -> np.ndarray:
+        """C = bf16(A) bf16(B)^T on the tensor cores (FP32 accumulation)."""
+        A = np.ascontiguousarray(A, dtype=np.float32)
+        B = np.ascontiguousarray(B, dtype=np.float32)
+        C = np.empty((A.shape[0], B.shape[0]), dtype=np.float32)
+        fpp = ctypes.POINTER(ctypes.c_float)
+        self._check(lib().pwa_mlp_gemm_check(self._h, A.shape[0], B.shape[0], A.shape[1], A.ctypes.data_as(fpp),
+                                             B.ctypes.data_as(fpp), C.ctypes.data_as(fpp)))
+        return C
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pwa_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def make_likelihood(workload, stream: int = 0, device_inputs: bool = False) -> Likelihood:

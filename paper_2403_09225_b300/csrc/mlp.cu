@@ -1,0 +1,676 @@
+// mlp.cu -- the learned starting-point proposal: a small MLP with BF16 weights
+// and FP32 accumulation, trained and run by this library's own kernels.
+//
+// Network: x (a log-scaled 64 x 64 Dalitz histogram, 4096 inputs) -> three
+// hidden layers of 512 with GELU -> P outputs (a starting theta, standardised).
+// Every matrix product runs on the tensor cores (tcgen05.mma kind::f16, BF16
+// operands, FP32 accumulation in tensor memory) in one kernel,
+// C[M x N] = A[M x K] B[N x K]^T with both operands K-major BF16 in global
+// memory (row-major, K contiguous).  The backward pass forms the transposed
+// operands it needs with explicit transpose kernels.  Loss: squared error on
+// the standardised outputs, 1 - cos(difference) on outputs flagged periodic
+// (phases); Adam on FP32 master weights, whose BF16 copies the products read.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pwa_internal.h"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// GEMM: 128 x 64 output tile per CTA, K in chunks of 64 staged in shared memory
+// ---------------------------------------------------------------------------
+
+constexpr int kGM = 128, kGN = 64, kGK = 64;  // tile; K chunk (four MMAs of K = 16)
+constexpr int kGThreads = 128;                // 4 warps: one per TMEM lane quarter
+
+__device__ __forceinline__ uint32_t sa(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// C = A B^T (+ C when accumulate): A [M][K], B [N][K] BF16 row-major with leading
+// dimensions lda, ldb (elements); C [M][N] FP32 with ldc.  M % 128 == 0,
+// N % 64 == 0, K % 64 == 0, leading dimensions multiples of 8.
+__global__ void __launch_bounds__(kGThreads, 1) gemm_bf16_kernel(const __nv_bfloat16* __restrict__ A, int lda,
+                                                                const __nv_bfloat16* __restrict__ B, int ldb,
+                                                                float* __restrict__ C, int ldc, int K,
+                                                                long long timeout, int* err)
+{
+    // A chunk: 128 rows x 64 K = 16 8-row groups x 8 cores (SBO 1024); B chunk: 64 rows (SBO 1024)
+    __shared__ __align__(1024) unsigned char sA[kGM * kGK * 2];
+    __shared__ __align__(1024) unsigned char sB[kGN * kGK * 2];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * kGM, n0 = blockIdx.x * kGN;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(&bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(sa(&tslot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tm = tslot;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kGN >> 3) << 17) | ((uint32_t)(kGM >> 4) << 24);
+    bool ok = true;
+    int phase = 0;
+    for (int k0 = 0; k0 < K && ok; k0 += kGK) {
+        // 16-byte pieces (8 K values of one row) straight into their core-matrix rows
+        for (int p = tid; p < kGM * (kGK / 8); p += kGThreads) {
+            const int r = p / (kGK / 8), c = p % (kGK / 8);
+            const uint4 v = *reinterpret_cast<const uint4*>(A + (size_t)(m0 + r) * lda + k0 + 8 * c);
+            *reinterpret_cast<uint4*>(sA + (r >> 3) * 1024 + c * 128 + (r & 7) * 16) = v;
+        }
+        for (int p = tid; p < kGN * (kGK / 8); p += kGThreads) {
+            const int r = p / (kGK / 8), c = p % (kGK / 8);
+            const uint4 v = *reinterpret_cast<const uint4*>(B + (size_t)(n0 + r) * ldb + k0 + 8 * c);
+            *reinterpret_cast<uint4*>(sB + (r >> 3) * 1024 + c * 128 + (r & 7) * 16) = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            for (int ks = 0; ks < kGK / 16; ++ks) {
+                const uint64_t ad = sdesc(sa(sA) + ks * 256, 128, 1024), bd = sdesc(sa(sB) + ks * 256, 128, 1024);
+                const uint32_t acc = (k0 > 0 || ks > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                        tm),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(&bar))
+                         : "memory");
+        }
+        // every thread waits for the chunk's MMAs (bounded) before the buffers are refilled
+        const long long t0 = clock64();
+        while (true) {
+            uint32_t done;
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(sa(&bar)), "r"((uint32_t)phase)
+                : "memory");
+            if (done) break;
+            if (clock64() - t0 > timeout) {
+                ok = false;
+                break;
+            }
+        }
+        phase ^= 1;
+        ok = __syncthreads_and(ok);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (ok && K > 0) {
+        // row m0 + 32 warp + lane of C from TMEM lane 32 warp + lane
+        const int m = m0 + 32 * warp + lane;
+        for (int c0 = 0; c0 < kGN; c0 += 16) {
+            uint32_t r[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(tm + ((uint32_t)(32 * warp) << 16) + c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float* crow = C + (size_t)m * ldc + n0 + c0;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) crow[q] = __uint_as_float(r[q]);
+        }
+    } else if (!ok && tid == 0) {
+        atomicOr(err, pwa::ERR_TIMEOUT);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tm));
+}
+
+// ---------------------------------------------------------------------------
+// elementwise parts
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float gelu(float z)  // tanh form
+{
+    const float u = 0.7978845608028654f * (z + 0.044715f * z * z * z);
+    return 0.5f * z * (1.f + tanhf(u));
+}
+
+__device__ __forceinline__ float gelu_grad(float z)
+{
+    const float u = 0.7978845608028654f * (z + 0.044715f * z * z * z);
+    const float t = tanhf(u);
+    const float du = 0.7978845608028654f * (1.f + 3.f * 0.044715f * z * z);
+    return 0.5f * (1.f + t) + 0.5f * z * (1.f - t * t) * du;
+}
+
+// z = acc + bias (pre-activation, kept for the backward pass); h = GELU(z) (or z
+// for the output layer) in BF16 for the next product.  [rows][cols], leading dims.
+__global__ void bias_act_kernel(const float* __restrict__ acc, int lda, const float* __restrict__ bias, int rows,
+                                int cols, int act, float* __restrict__ z, int ldz, __nv_bfloat16* __restrict__ h, int ldh)
+{
+    const long long n = (long long)rows * cols;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / cols), c = (int)(i % cols);
+        const float v = acc[(size_t)r * lda + c] + bias[c];
+        z[(size_t)r * ldz + c] = v;
+        if (h) h[(size_t)r * ldh + c] = __float2bfloat16_rn(act ? gelu(v) : v);
+    }
+}
+
+// Loss over the output rows and its gradient with respect to the outputs:
+// squared error, or 1 - cos(y - t) where periodic[c]; weights per output.
+// dy[r][c] = d loss / d y / rows; loss_part[r] = the row's loss.
+__global__ void loss_kernel(const float* __restrict__ y, int ldy, const float* __restrict__ t, int rows, int cols,
+                            const float* __restrict__ wgt, const int* __restrict__ periodic, float* __restrict__ dy,
+                            int lddy, float* __restrict__ loss_row)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    float l = 0.f;
+    for (int c = 0; c < cols; ++c) {
+        const float d = y[(size_t)r * ldy + c] - t[(size_t)r * cols + c];
+        float lc, g;
+        if (periodic[c]) {
+            lc = 1.f - cosf(d);
+            g = sinf(d);
+        } else {
+            lc = 0.5f * d * d;
+            g = d;
+        }
+        l += wgt[c] * lc;
+        dy[(size_t)r * lddy + c] = wgt[c] * g / rows;
+    }
+    loss_row[r] = l / rows;
+}
+
+// dz = dh * GELU'(z) (hidden layers) as BF16 for the next products
+__global__ void act_back_kernel(const float* __restrict__ dh, int lddh, const float* __restrict__ z, int ldz, int rows,
+                                int cols, __nv_bfloat16* __restrict__ dz, int lddz, float* __restrict__ dz32)
+{
+    const long long n = (long long)rows * cols;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / cols), c = (int)(i % cols);
+        const float v = dh[(size_t)r * lddh + c] * gelu_grad(z[(size_t)r * ldz + c]);
+        dz[(size_t)r * lddz + c] = __float2bfloat16_rn(v);
+        if (dz32) dz32[(size_t)r * cols + c] = v;
+    }
+}
+
+// out[c][r] = in[r][c] (BF16), zero in the padding of out
+__global__ void transpose_bf16_kernel(const __nv_bfloat16* __restrict__ in, int ldin, int rows, int cols,
+                                      __nv_bfloat16* __restrict__ out, int ldout, int out_rows, int out_cols)
+{
+    const long long n = (long long)out_rows * out_cols;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i / out_cols), r = (int)(i % out_cols);
+        out[(size_t)c * ldout + r] = (c < cols && r < rows) ? in[(size_t)r * ldin + c] : __float2bfloat16_rn(0.f);
+    }
+}
+
+// FP32 [rows][cols] -> BF16 with leading dimension ld (zero in the padding)
+__global__ void to_bf16_kernel(const float* __restrict__ in, int rows, int cols, __nv_bfloat16* __restrict__ out,
+                               int ld, int out_rows)
+{
+    const long long n = (long long)out_rows * ld;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / ld), c = (int)(i % ld);
+        out[i] = __float2bfloat16_rn((r < rows && c < cols) ? in[(size_t)r * cols + c] : 0.f);
+    }
+}
+
+// bias gradient: db[c] = sum_r dz[r][c] (fixed order)
+__global__ void bias_grad_kernel(const float* __restrict__ dz, int ld, int rows, int cols, float* __restrict__ db)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float s = 0.f;
+    for (int r = 0; r < rows; ++r) s += dz[(size_t)r * ld + c];
+    db[c] = s;
+}
+
+// Adam on FP32 masters; the BF16 copy (leading dimension ldb, rows x cols) follows
+__global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, int ldg, float* __restrict__ m1,
+                            float* __restrict__ m2, int rows, int cols, float lr, float b1, float b2, float eps,
+                            float c1, float c2, __nv_bfloat16* __restrict__ wb, int ldb)
+{
+    const long long n = (long long)rows * cols;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / cols), c = (int)(i % cols);
+        const float gi = g[(size_t)r * ldg + c];
+        const float a = b1 * m1[i] + (1.f - b1) * gi, b = b2 * m2[i] + (1.f - b2) * gi * gi;
+        m1[i] = a;
+        m2[i] = b;
+        const float v = w[i] - lr * (a / c1) / (sqrtf(b / c2) + eps);
+        w[i] = v;
+        if (wb) wb[(size_t)r * ldb + c] = __float2bfloat16_rn(v);
+    }
+}
+
+int blocks_for(long long n) { return (int)std::max(1LL, std::min((n + 255) / 256, 65535LL * 4)); }
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the network object
+// ---------------------------------------------------------------------------
+
+struct pwa_mlp {
+    int in = 0, hid = 0, out = 0, layers = 0;  // layers: hidden layers (3)
+    int outp = 0;                             // out padded to 128 (rows of the last W in dW products)
+    int maxB = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int* d_err = nullptr;
+    long long timeout = 0;
+    // per layer l = 0 .. layers (the last is the output layer): W [fan_out][fan_in] FP32 master,
+    // BF16 copy [fan_out_p][fan_in], bias, Adam moments, gradients
+    std::vector<int> fin, fout, foutp;
+    std::vector<float*> W, b, mW1, mW2, mb1, mb2, gW, gb;
+    std::vector<__nv_bfloat16*> Wb;
+    // activations for up to maxB rows: H_l (BF16 input of layer l) [maxB][fin], Z_l [maxB][fout_p]
+    std::vector<__nv_bfloat16*> H;
+    std::vector<float*> Z;
+    float* acc = nullptr;     // GEMM output scratch [maxB x max(fout_p, fin)] or [fout_p x fin]
+    float* dY = nullptr;      // [maxB][outp]
+    __nv_bfloat16* dZb = nullptr;   // BF16 dz [maxB][max fout_p]
+    float* dZ32 = nullptr;    // FP32 dz [maxB][max fout]
+    __nv_bfloat16* T1 = nullptr;    // transposes
+    __nv_bfloat16* T2 = nullptr;
+    float* loss_rows = nullptr;
+    int* d_periodic = nullptr;
+    float* d_wgt = nullptr;
+    int step = 0;
+};
+
+namespace {
+
+pwa_status mlp_fail(pwa_mlp* m, pwa_status st, const std::string& msg)
+{
+    m->err = msg;
+    return st;
+}
+
+pwa_status mlp_cuda(pwa_mlp* m, cudaError_t e, const char* what)
+{
+    cudaGetLastError();
+    return mlp_fail(m, PWA_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define MLP_CUDA(m, call)                                        \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return mlp_cuda((m), e_, #call);  \
+    } while (0)
+
+// C[M][N] = A[M][K] B[N][K]^T on the tensor cores
+pwa_status gemm(pwa_mlp* m, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, float* C, int ldc, int M,
+                int N, int K)
+{
+    if (M % kGM || N % kGN || K % kGK || lda % 8 || ldb % 8)
+        return mlp_fail(m, PWA_EINVAL, "internal: GEMM shape not tile-aligned");
+    dim3 grid(N / kGN, M / kGM);
+    gemm_bf16_kernel<<<grid, kGThreads, 0, m->stream>>>(A, lda, B, ldb, C, ldc, K, m->timeout, m->d_err);
+    MLP_CUDA(m, cudaGetLastError());
+    return PWA_OK;
+}
+
+#define MLP_TRY(call)                 \
+    do {                              \
+        pwa_status s_ = (call);       \
+        if (s_ != PWA_OK) return s_;  \
+    } while (0)
+
+// forward over B rows (B % 128 == 0) from X (FP32 [B][in]); outputs in Z[layers] (FP32)
+pwa_status forward(pwa_mlp* m, int B, const float* d_x)
+{
+    const int L = m->layers + 1;
+    to_bf16_kernel<<<blocks_for((long long)B * m->in), 256, 0, m->stream>>>(d_x, B, m->in, m->H[0], m->in, B);
+    MLP_CUDA(m, cudaGetLastError());
+    for (int l = 0; l < L; ++l) {
+        const bool last = l == L - 1;
+        MLP_TRY(gemm(m, m->H[l], m->fin[l], m->Wb[l], m->fin[l], m->acc, m->foutp[l], B, m->foutp[l], m->fin[l]));
+        bias_act_kernel<<<blocks_for((long long)B * m->fout[l]), 256, 0, m->stream>>>(
+            m->acc, m->foutp[l], m->b[l], B, m->fout[l], last ? 0 : 1, m->Z[l], m->foutp[l], last ? nullptr : m->H[l + 1],
+            m->fin[l + 1 < L ? l + 1 : l]);
+        MLP_CUDA(m, cudaGetLastError());
+    }
+    return PWA_OK;
+}
+
+// backward after forward: gradients into gW, gb; loss rows in loss_rows
+pwa_status backward(pwa_mlp* m, int B, const float* d_t)
+{
+    const int L = m->layers + 1;
+    loss_kernel<<<(B + 127) / 128, 128, 0, m->stream>>>(m->Z[L - 1], m->foutp[L - 1], d_t, B, m->out, m->d_wgt,
+                                                       m->d_periodic, m->dY, m->outp, m->loss_rows);
+    MLP_CUDA(m, cudaGetLastError());
+    // dZ of the output layer (no activation): BF16 copy of dY with the padding zero
+    to_bf16_kernel<<<blocks_for((long long)B * m->outp), 256, 0, m->stream>>>(m->dY, B, m->outp, m->dZb, m->outp, B);
+    MLP_CUDA(m, cudaGetLastError());
+    const float* dz32 = m->dY;
+    int dz_ld32 = m->outp;
+    for (int l = L - 1; l >= 0; --l) {
+        const int fo = m->fout[l], fop = m->foutp[l], fi = m->fin[l];
+        // bias gradient
+        bias_grad_kernel<<<(fo + 127) / 128, 128, 0, m->stream>>>(dz32, dz_ld32, B, fo, m->gb[l]);
+        MLP_CUDA(m, cudaGetLastError());
+        // dW [fop][fi] = dZ^T [fop][B] x H^T [fi][B]^T
+        transpose_bf16_kernel<<<blocks_for((long long)fop * B), 256, 0, m->stream>>>(m->dZb, fop, B, fop, m->T1, B, fop, B);
+        MLP_CUDA(m, cudaGetLastError());
+        transpose_bf16_kernel<<<blocks_for((long long)fi * B), 256, 0, m->stream>>>(m->H[l], fi, B, fi, m->T2, B, fi, B);
+        MLP_CUDA(m, cudaGetLastError());
+        MLP_TRY(gemm(m, m->T1, B, m->T2, B, m->gW[l], fi, fop, fi, B));
+        if (l == 0) break;
+        // dH_l [B][fi] = dZ [B][fop] x W [fop][fi]: second operand W^T [fi][fop]
+        transpose_bf16_kernel<<<blocks_for((long long)fi * fop), 256, 0, m->stream>>>(m->Wb[l], fi, fop, fi, m->T1, fop, fi,
+                                                                                     fop);
+        MLP_CUDA(m, cudaGetLastError());
+        MLP_TRY(gemm(m, m->dZb, fop, m->T1, fop, m->acc, fi, B, fi, fop));
+        act_back_kernel<<<blocks_for((long long)B * fi), 256, 0, m->stream>>>(m->acc, fi, m->Z[l - 1], m->foutp[l - 1], B,
+                                                                             fi, m->dZb, m->foutp[l - 1], m->dZ32);
+        MLP_CUDA(m, cudaGetLastError());
+        dz32 = m->dZ32;
+        dz_ld32 = fi;
+    }
+    return PWA_OK;
+}
+
+pwa_status alloc_f(pwa_mlp* m, float** p, size_t n)
+{
+    MLP_CUDA(m, cudaMalloc(p, std::max<size_t>(n, 1) * sizeof(float)));
+    MLP_CUDA(m, cudaMemsetAsync(*p, 0, std::max<size_t>(n, 1) * sizeof(float), m->stream));
+    return PWA_OK;
+}
+
+pwa_status alloc_b(pwa_mlp* m, __nv_bfloat16** p, size_t n)
+{
+    MLP_CUDA(m, cudaMalloc(p, std::max<size_t>(n, 1) * sizeof(__nv_bfloat16)));
+    MLP_CUDA(m, cudaMemsetAsync(*p, 0, std::max<size_t>(n, 1) * sizeof(__nv_bfloat16), m->stream));
+    return PWA_OK;
+}
+
+pwa_status create_impl(pwa_mlp* m, int in, int hid, int layers, int out, int maxB, unsigned long long seed,
+                       const int* periodic, const float* wgt)
+{
+    m->in = in;
+    m->hid = hid;
+    m->layers = layers;
+    m->out = out;
+    m->outp = round_up(out, kGM);
+    m->maxB = maxB;
+    int dev = 0, clock_khz = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev);
+    m->timeout = (long long)std::max(clock_khz, 1000000) * 2000LL;  // about 2 s of SM cycles
+    const int L = layers + 1;
+    for (int l = 0; l < L; ++l) {
+        m->fin.push_back(l == 0 ? in : hid);
+        m->fout.push_back(l == L - 1 ? out : hid);
+        m->foutp.push_back(l == L - 1 ? m->outp : hid);
+    }
+    MLP_CUDA(m, cudaMalloc(&m->d_err, sizeof(int)));
+    MLP_CUDA(m, cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream));
+    size_t max_f = 0;
+    for (int l = 0; l < L; ++l) {
+        const size_t nW = (size_t)m->fout[l] * m->fin[l];
+        float *W, *b, *a1, *a2, *c1, *c2, *gW, *gb;
+        __nv_bfloat16* Wb;
+        MLP_TRY(alloc_f(m, &W, nW));
+        MLP_TRY(alloc_f(m, &b, m->fout[l]));
+        MLP_TRY(alloc_f(m, &a1, nW));
+        MLP_TRY(alloc_f(m, &a2, nW));
+        MLP_TRY(alloc_f(m, &c1, m->fout[l]));
+        MLP_TRY(alloc_f(m, &c2, m->fout[l]));
+        MLP_TRY(alloc_f(m, &gW, (size_t)m->foutp[l] * m->fin[l]));
+        MLP_TRY(alloc_f(m, &gb, m->fout[l]));
+        MLP_TRY(alloc_b(m, &Wb, (size_t)m->foutp[l] * m->fin[l]));
+        m->W.push_back(W);
+        m->b.push_back(b);
+        m->mW1.push_back(a1);
+        m->mW2.push_back(a2);
+        m->mb1.push_back(c1);
+        m->mb2.push_back(c2);
+        m->gW.push_back(gW);
+        m->gb.push_back(gb);
+        m->Wb.push_back(Wb);
+        __nv_bfloat16* H;
+        float* Z;
+        MLP_TRY(alloc_b(m, &H, (size_t)maxB * m->fin[l]));
+        MLP_TRY(alloc_f(m, &Z, (size_t)maxB * m->foutp[l]));
+        m->H.push_back(H);
+        m->Z.push_back(Z);
+        max_f = std::max(max_f, (size_t)std::max(m->foutp[l], m->fin[l]));
+    }
+    MLP_TRY(alloc_f(m, &m->acc, (size_t)maxB * max_f));
+    MLP_TRY(alloc_f(m, &m->dY, (size_t)maxB * m->outp));
+    MLP_TRY(alloc_b(m, &m->dZb, (size_t)maxB * std::max(m->outp, hid)));
+    MLP_TRY(alloc_f(m, &m->dZ32, (size_t)maxB * hid));
+    MLP_TRY(alloc_b(m, &m->T1, std::max((size_t)max_f * maxB, (size_t)hid * std::max(hid, m->outp))));
+    MLP_TRY(alloc_b(m, &m->T2, (size_t)max_f * maxB));
+    MLP_TRY(alloc_f(m, &m->loss_rows, maxB));
+    MLP_CUDA(m, cudaMalloc(&m->d_periodic, sizeof(int) * out));
+    MLP_CUDA(m, cudaMalloc(&m->d_wgt, sizeof(float) * out));
+    std::vector<int> per(out, 0);
+    std::vector<float> wg(out, 1.f);
+    for (int c = 0; c < out; ++c) {
+        if (periodic) per[c] = periodic[c] != 0;
+        if (wgt) wg[c] = wgt[c];
+    }
+    MLP_CUDA(m, cudaMemcpyAsync(m->d_periodic, per.data(), sizeof(int) * out, cudaMemcpyHostToDevice, m->stream));
+    MLP_CUDA(m, cudaMemcpyAsync(m->d_wgt, wg.data(), sizeof(float) * out, cudaMemcpyHostToDevice, m->stream));
+    // initial weights: uniform in +-sqrt(6 / (fan_in + fan_out)) from a splitmix64 stream (host), biases 0
+    unsigned long long st = seed;
+    auto next = [&st]() {
+        st += 0x9E3779B97F4A7C15ull;
+        unsigned long long z = st;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    for (int l = 0; l < L; ++l) {
+        const size_t nW = (size_t)m->fout[l] * m->fin[l];
+        std::vector<float> w(nW);
+        const double lim = std::sqrt(6.0 / (m->fin[l] + m->fout[l]));
+        for (size_t i = 0; i < nW; ++i) w[i] = (float)(lim * (2.0 * ((next() >> 11) * (1.0 / 9007199254740992.0)) - 1.0));
+        MLP_CUDA(m, cudaMemcpy(m->W[l], w.data(), nW * sizeof(float), cudaMemcpyHostToDevice));
+        to_bf16_kernel<<<blocks_for((long long)m->foutp[l] * m->fin[l]), 256, 0, m->stream>>>(
+            m->W[l], m->fout[l], m->fin[l], m->Wb[l], m->fin[l], m->foutp[l]);
+        MLP_CUDA(m, cudaGetLastError());
+    }
+    MLP_CUDA(m, cudaStreamSynchronize(m->stream));
+    return PWA_OK;
+}
+
+pwa_status check_err(pwa_mlp* m)
+{
+    int e = 0;
+    MLP_CUDA(m, cudaMemcpyAsync(&e, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    MLP_CUDA(m, cudaStreamSynchronize(m->stream));
+    if (e) return mlp_fail(m, PWA_ETIMEOUT, "a tensor-core product did not complete within the wait limit");
+    return PWA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+thread_local std::string g_mlp_create_error;
+
+pwa_status pwa_mlp_create(int in, int hidden, int layers, int out, int max_batch, unsigned long long seed,
+                          const int* periodic, const float* loss_weight, void* cuda_stream, pwa_mlp** out_m)
+{
+    if (!out_m) return PWA_EINVAL;
+    *out_m = nullptr;
+    g_mlp_create_error.clear();
+    if (in <= 0 || hidden <= 0 || layers < 1 || out <= 0 || max_batch <= 0 || in % kGK || hidden % kGM ||
+        max_batch % kGM) {
+        g_mlp_create_error = "sizes: in % 64 == 0, hidden % 128 == 0, max_batch % 128 == 0, layers >= 1";
+        return PWA_EINVAL;
+    }
+    auto* m = new (std::nothrow) pwa_mlp();
+    if (!m) return PWA_ENOMEM;
+    m->stream = static_cast<cudaStream_t>(cuda_stream);
+    pwa_status st = create_impl(m, in, hidden, layers, out, max_batch, seed, periodic, loss_weight);
+    if (st != PWA_OK) {
+        g_mlp_create_error = m->err;
+        pwa_mlp_destroy(m);
+        return st;
+    }
+    *out_m = m;
+    return PWA_OK;
+}
+
+pwa_status pwa_mlp_forward(pwa_mlp* m, int B, const float* d_x, float* d_y)
+{
+    if (!m || !d_x || !d_y) return PWA_EINVAL;
+    m->err.clear();
+    if (B <= 0 || B > m->maxB || B % kGM) return mlp_fail(m, PWA_EINVAL, "B must be a multiple of 128 up to max_batch");
+    MLP_TRY(forward(m, B, d_x));
+    const int L = m->layers + 1;
+    MLP_CUDA(m, cudaMemcpy2DAsync(d_y, sizeof(float) * m->out, m->Z[L - 1], sizeof(float) * m->foutp[L - 1],
+                                  sizeof(float) * m->out, B, cudaMemcpyDeviceToDevice, m->stream));
+    return check_err(m);
+}
+
+pwa_status pwa_mlp_gradients(pwa_mlp* m, int B, const float* d_x, const float* d_t, double* loss)
+{
+    if (!m || !d_x || !d_t) return PWA_EINVAL;
+    m->err.clear();
+    if (B <= 0 || B > m->maxB || B % kGM) return mlp_fail(m, PWA_EINVAL, "B must be a multiple of 128 up to max_batch");
+    MLP_TRY(forward(m, B, d_x));
+    MLP_TRY(backward(m, B, d_t));
+    if (loss) {
+        std::vector<float> lr(B);
+        MLP_CUDA(m, cudaMemcpyAsync(lr.data(), m->loss_rows, sizeof(float) * B, cudaMemcpyDeviceToHost, m->stream));
+        MLP_TRY(check_err(m));
+        double s = 0.0;
+        for (float v : lr) s += v;
+        *loss = s;
+    }
+    return check_err(m);
+}
+
+pwa_status pwa_mlp_train_step(pwa_mlp* m, int B, const float* d_x, const float* d_t, float lr, double* loss)
+{
+    MLP_TRY(pwa_mlp_gradients(m, B, d_x, d_t, loss));
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    m->step += 1;
+    const float c1 = 1.f - std::pow(b1, (float)m->step), c2 = 1.f - std::pow(b2, (float)m->step);
+    for (int l = 0; l <= m->layers; ++l) {
+        adam_kernel<<<blocks_for((long long)m->fout[l] * m->fin[l]), 256, 0, m->stream>>>(
+            m->W[l], m->gW[l], m->fin[l], m->mW1[l], m->mW2[l], m->fout[l], m->fin[l], lr, b1, b2, eps, c1, c2, m->Wb[l],
+            m->fin[l]);
+        MLP_CUDA(m, cudaGetLastError());
+        adam_kernel<<<blocks_for(m->fout[l]), 256, 0, m->stream>>>(m->b[l], m->gb[l], 0, m->mb1[l], m->mb2[l], 1,
+                                                                   m->fout[l], lr, b1, b2, eps, c1, c2, nullptr, 0);
+        MLP_CUDA(m, cudaGetLastError());
+    }
+    return PWA_OK;
+}
+
+pwa_status pwa_mlp_params(pwa_mlp* m, int layer, int which, float* host, int to_device)
+{
+    // which: 0 W [fout][fin], 1 b [fout], 2 dW [fout][fin] (last gradients), 3 db [fout]
+    if (!m || !host || layer < 0 || layer > m->layers || which < 0 || which > 3) return PWA_EINVAL;
+    const int fo = m->fout[layer], fi = m->fin[layer];
+    if (which == 2) {
+        if (to_device) return PWA_EINVAL;
+        MLP_CUDA(m, cudaMemcpy2DAsync(host, sizeof(float) * fi, m->gW[layer], sizeof(float) * fi, sizeof(float) * fi, fo,
+                                      cudaMemcpyDeviceToHost, m->stream));
+        MLP_CUDA(m, cudaStreamSynchronize(m->stream));
+        return PWA_OK;
+    }
+    float* d = which == 0 ? m->W[layer] : which == 1 ? m->b[layer] : m->gb[layer];
+    const size_t n = which == 0 ? (size_t)fo * fi : (size_t)fo;
+    if (to_device) {
+        if (which == 3) return PWA_EINVAL;
+        MLP_CUDA(m, cudaMemcpyAsync(d, host, n * sizeof(float), cudaMemcpyHostToDevice, m->stream));
+        if (which == 0) {
+            to_bf16_kernel<<<blocks_for((long long)m->foutp[layer] * fi), 256, 0, m->stream>>>(
+                m->W[layer], fo, fi, m->Wb[layer], fi, m->foutp[layer]);
+            MLP_CUDA(m, cudaGetLastError());
+        }
+    } else {
+        MLP_CUDA(m, cudaMemcpyAsync(host, d, n * sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+    }
+    MLP_CUDA(m, cudaStreamSynchronize(m->stream));
+    return PWA_OK;
+}
+
+pwa_status pwa_mlp_gemm_check(pwa_mlp* m, int M, int N, int K, const float* hA, const float* hB, float* hC)
+{
+    // the tensor-core product alone, on BF16-rounded copies of host FP32 A [M][K], B [N][K]
+    if (!m || !hA || !hB || !hC) return PWA_EINVAL;
+    if (M % kGM || N % kGN || K % kGK) return mlp_fail(m, PWA_EINVAL, "M % 128, N % 64, K % 64 must be 0");
+    float *dA = nullptr, *dB = nullptr, *dC = nullptr;
+    __nv_bfloat16 *bA = nullptr, *bB = nullptr;
+    pwa_status st = PWA_OK;
+    cudaError_t e = cudaMalloc(&dA, sizeof(float) * (size_t)M * K);
+    if (e == cudaSuccess) e = cudaMalloc(&dB, sizeof(float) * (size_t)N * K);
+    if (e == cudaSuccess) e = cudaMalloc(&dC, sizeof(float) * (size_t)M * N);
+    if (e == cudaSuccess) e = cudaMalloc(&bA, sizeof(__nv_bfloat16) * (size_t)M * K);
+    if (e == cudaSuccess) e = cudaMalloc(&bB, sizeof(__nv_bfloat16) * (size_t)N * K);
+    if (e == cudaSuccess) e = cudaMemcpy(dA, hA, sizeof(float) * (size_t)M * K, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dB, hB, sizeof(float) * (size_t)N * K, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        to_bf16_kernel<<<blocks_for((long long)M * K), 256, 0, m->stream>>>(dA, M, K, bA, K, M);
+        to_bf16_kernel<<<blocks_for((long long)N * K), 256, 0, m->stream>>>(dB, N, K, bB, K, N);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) st = gemm(m, bA, K, bB, K, dC, N, M, N, K);
+    if (e == cudaSuccess && st == PWA_OK) st = check_err(m);
+    if (e == cudaSuccess && st == PWA_OK) e = cudaMemcpy(hC, dC, sizeof(float) * (size_t)M * N, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess && st == PWA_OK) st = mlp_cuda(m, e, "gemm check");
+    void* ps[] = {dA, dB, dC, bA, bB};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    return st;
+}
+
+const char* pwa_mlp_last_error(const pwa_mlp* m) { return m ? m->err.c_str() : g_mlp_create_error.c_str(); }
+
+void pwa_mlp_destroy(pwa_mlp* m)
+{
+    if (!m) return;
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    else cudaDeviceSynchronize();
+    auto fr = [](void* p) {
+        if (p) cudaFree(p);
+    };
+    for (size_t l = 0; l < m->W.size(); ++l) {
+        fr(m->W[l]);
+        fr(m->b[l]);
+        fr(m->mW1[l]);
+        fr(m->mW2[l]);
+        fr(m->mb1[l]);
+        fr(m->mb2[l]);
+        fr(m->gW[l]);
+        fr(m->gb[l]);
+        fr(m->Wb[l]);
+    }
+    for (auto* p : m->H) fr(p);
+    for (auto* p : m->Z) fr(p);
+    void* ps[] = {m->acc, m->dY, m->dZb, m->dZ32, m->T1, m->T2, m->loss_rows, m->d_periodic, m->d_wgt, m->d_err};
+    for (void* p : ps) fr(p);
+    cudaGetLastError();
+    delete m;
+}
+
+}  // extern "C"
