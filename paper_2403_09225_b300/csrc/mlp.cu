@@ -39,23 +39,60 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
            ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
-// C = A B^T (+ C when accumulate): A [M][K], B [N][K] BF16 row-major with leading
-// dimensions lda, ldb (elements); C [M][N] FP32 with ldc.  M % 128 == 0,
-// N % 64 == 0, K % 64 == 0, leading dimensions multiples of 8.
+// C = A B^T: A [M][K], B [N][K] BF16 row-major with leading dimensions lda, ldb
+// (elements); C [M][N] FP32 with ldc.  M % 128 == 0, N % 64 == 0, K % 64 == 0,
+// leading dimensions multiples of 8.  Split K: CTA z of gridDim.z takes the
+// K chunks [z n / Z, (z + 1) n / Z) of the n = K / 64 and writes its partial
+// product to C + z split_stride (a workspace the caller reduces in fixed order).
+constexpr int kGStageBytes = (kGM + kGN) * kGK * 2;  // one K chunk of A and B: 24 KB
+constexpr int kGSmem = 2 * kGStageBytes + 1024;         // two stages + alignment slack
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long timeout)
+{
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    if (done) return true;
+    const long long t0 = clock64();
+    while (true) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > timeout) return false;
+    }
+}
+
 __global__ void __launch_bounds__(kGThreads, 1) gemm_bf16_kernel(const __nv_bfloat16* __restrict__ A, int lda,
                                                                 const __nv_bfloat16* __restrict__ B, int ldb,
-                                                                float* __restrict__ C, int ldc, int K,
+                                                                float* __restrict__ C, int ldc,
+                                                                long long split_stride, int K,
                                                                 long long timeout, int* err)
 {
-    // A chunk: 128 rows x 64 K = 16 8-row groups x 8 cores (SBO 1024); B chunk: 64 rows (SBO 1024)
-    __shared__ __align__(1024) unsigned char sA[kGM * kGK * 2];
-    __shared__ __align__(1024) unsigned char sB[kGN * kGK * 2];
-    __shared__ __align__(8) uint64_t bar;
+    // per stage: A chunk 128 rows x 64 K (16 8-row groups of 8 core matrices, SBO 1024),
+    // then B chunk 64 rows (SBO 1024); element (r, k) of a chunk at (r >> 3) 1024 + (k >> 3) 128 + (r & 7) 16
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * kGM, n0 = blockIdx.x * kGN;
+    const int nchunk = K / kGK, z = blockIdx.z, Z = gridDim.z;
+    const int cbeg = (int)((long long)z * nchunk / Z), cend = (int)((long long)(z + 1) * nchunk / Z);
+    C += (long long)z * split_stride;
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(&bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(&bar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(&bar[1])));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -67,56 +104,72 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_bf16_kernel(const __nv_bflo
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tm = tslot;
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kGN >> 3) << 17) | ((uint32_t)(kGM >> 4) << 24);
-    bool ok = true;
-    int phase = 0;
-    for (int k0 = 0; k0 < K && ok; k0 += kGK) {
-        // 16-byte pieces (8 K values of one row) straight into their core-matrix rows
-        for (int p = tid; p < kGM * (kGK / 8); p += kGThreads) {
-            const int r = p / (kGK / 8), c = p % (kGK / 8);
-            const uint4 v = *reinterpret_cast<const uint4*>(A + (size_t)(m0 + r) * lda + k0 + 8 * c);
-            *reinterpret_cast<uint4*>(sA + (r >> 3) * 1024 + c * 128 + (r & 7) * 16) = v;
+    const uint32_t s0 = sa(smem);
+
+    // 16-byte pieces of chunk c into stage st: A 8 per thread, B 4 per thread, all in flight together
+    auto load_chunk = [&](int c, int st) {
+        const int k0 = c * kGK;
+        const uint32_t dA = s0 + st * kGStageBytes, dB = dA + kGM * kGK * 2;
+#pragma unroll
+        for (int i = 0; i < kGM * (kGK / 8) / kGThreads; ++i) {
+            const int p = tid + i * kGThreads, r = p >> 3, q = p & 7;
+            cp_async16(dA + (r >> 3) * 1024 + q * 128 + (r & 7) * 16, A + (size_t)(m0 + r) * lda + k0 + 8 * q);
         }
-        for (int p = tid; p < kGN * (kGK / 8); p += kGThreads) {
-            const int r = p / (kGK / 8), c = p % (kGK / 8);
-            const uint4 v = *reinterpret_cast<const uint4*>(B + (size_t)(n0 + r) * ldb + k0 + 8 * c);
-            *reinterpret_cast<uint4*>(sB + (r >> 3) * 1024 + c * 128 + (r & 7) * 16) = v;
+#pragma unroll
+        for (int i = 0; i < kGN * (kGK / 8) / kGThreads; ++i) {
+            const int p = tid + i * kGThreads, r = p >> 3, q = p & 7;
+            cp_async16(dB + (r >> 3) * 1024 + q * 128 + (r & 7) * 16, B + (size_t)(n0 + r) * ldb + k0 + 8 * q);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+
+    bool ok = true;
+    uint32_t ph = 0u;  // bit b: parity of the next phase of bar[b] to wait for
+    if (cbeg < cend) load_chunk(cbeg, 0);
+    for (int c = cbeg; c < cend; ++c) {
+        const int i = c - cbeg, st = i & 1;
+        if (c + 1 < cend) {
+            // stage st ^ 1 was read by the MMAs of chunk c - 1: wait for them before refilling it
+            if (i >= 1) {
+                ok = mbar_wait_bounded(sa(&bar[st ^ 1]), (ph >> (st ^ 1)) & 1u, timeout);
+                ph ^= 1u << (st ^ 1);
+            }
+            ok = __syncthreads_and(ok);
+            if (!ok) break;
+            load_chunk(c + 1, st ^ 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (tid == 0) {
+            const uint32_t dA = s0 + st * kGStageBytes, dB = dA + kGM * kGK * 2;
+#pragma unroll
             for (int ks = 0; ks < kGK / 16; ++ks) {
-                const uint64_t ad = sdesc(sa(sA) + ks * 256, 128, 1024), bd = sdesc(sa(sB) + ks * 256, 128, 1024);
-                const uint32_t acc = (k0 > 0 || ks > 0) ? 1u : 0u;
+                const uint64_t ad = sdesc(dA + ks * 256, 128, 1024), bd = sdesc(dB + ks * 256, 128, 1024);
+                const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
                         tm),
                     "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(&bar))
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             sa(&bar[st]))
                          : "memory");
         }
-        // every thread waits for the chunk's MMAs (bounded) before the buffers are refilled
-        const long long t0 = clock64();
-        while (true) {
-            uint32_t done;
-            asm volatile(
-                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                : "=r"(done)
-                : "r"(sa(&bar)), "r"((uint32_t)phase)
-                : "memory");
-            if (done) break;
-            if (clock64() - t0 > timeout) {
-                ok = false;
-                break;
-            }
-        }
-        phase ^= 1;
-        ok = __syncthreads_and(ok);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
-    if (ok && K > 0) {
+    // the last chunk's MMAs (and with them every earlier one) before the accumulator is read
+    if (ok && cend > cbeg) {
+        const int st = (cend - 1 - cbeg) & 1;
+        ok = mbar_wait_bounded(sa(&bar[st]), (ph >> st) & 1u, timeout);
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    ok = __syncthreads_and(ok);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok && cend > cbeg) {
         // row m0 + 32 warp + lane of C from TMEM lane 32 warp + lane
         const int m = m0 + 32 * warp + lane;
         for (int c0 = 0; c0 < kGN; c0 += 16) {
@@ -127,9 +180,11 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_bf16_kernel(const __nv_bflo
                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
                 : "r"(tm + ((uint32_t)(32 * warp) << 16) + c0));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            float* crow = C + (size_t)m * ldc + n0 + c0;
+            float4* crow = reinterpret_cast<float4*>(C + (size_t)m * ldc + n0 + c0);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) crow[q] = __uint_as_float(r[q]);
+            for (int q = 0; q < 4; ++q)
+                crow[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                      __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
         }
     } else if (!ok && tid == 0) {
         atomicOr(err, pwa::ERR_TIMEOUT);
@@ -138,6 +193,19 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_bf16_kernel(const __nv_bflo
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tm));
+}
+
+// C [M][N] (ldc) = sum over z = 0 .. Z - 1 of W [z][M][N] (ldw, stride), in that order
+__global__ void split_reduce_kernel(const float* __restrict__ W, int ldw, long long stride, int Z, int M, int N,
+                                    float* __restrict__ C, int ldc)
+{
+    const long long n = (long long)M * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / N), c = (int)(i % N);
+        float s = 0.f;
+        for (int z = 0; z < Z; ++z) s += W[z * stride + (long long)r * ldw + c];
+        C[(size_t)r * ldc + c] = s;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -294,6 +362,8 @@ struct pwa_mlp {
     __nv_bfloat16* T1 = nullptr;    // transposes
     __nv_bfloat16* T2 = nullptr;
     float* loss_rows = nullptr;
+    float* ws = nullptr;      // split-K partial products
+    size_t ws_floats = 0;
     int* d_periodic = nullptr;
     float* d_wgt = nullptr;
     int step = 0;
@@ -319,14 +389,34 @@ pwa_status mlp_cuda(pwa_mlp* m, cudaError_t e, const char* what)
         if (e_ != cudaSuccess) return mlp_cuda((m), e_, #call);  \
     } while (0)
 
-// C[M][N] = A[M][K] B[N][K]^T on the tensor cores
+// K splits for an M x N x K product: enough CTAs for two waves over the SMs,
+// at least two K chunks per split
+int k_splits(int M, int N, int K)
+{
+    const int tiles = (M / kGM) * (N / kGN), chunks = K / kGK;
+    int z = std::max(1, (2 * 148 + tiles - 1) / tiles);
+    return std::max(1, std::min(z, chunks / 2));
+}
+
+// C[M][N] = A[M][K] B[N][K]^T on the tensor cores (split K through the workspace when it pays)
 pwa_status gemm(pwa_mlp* m, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, float* C, int ldc, int M,
                 int N, int K)
 {
     if (M % kGM || N % kGN || K % kGK || lda % 8 || ldb % 8)
         return mlp_fail(m, PWA_EINVAL, "internal: GEMM shape not tile-aligned");
-    dim3 grid(N / kGN, M / kGM);
-    gemm_bf16_kernel<<<grid, kGThreads, 0, m->stream>>>(A, lda, B, ldb, C, ldc, K, m->timeout, m->d_err);
+    const int Z = k_splits(M, N, K);
+    if (Z > 1 && (size_t)Z * M * N > m->ws_floats) return mlp_fail(m, PWA_EINVAL, "internal: split-K workspace too small");
+    dim3 grid(N / kGN, M / kGM, Z);
+    if (Z == 1) {
+        gemm_bf16_kernel<<<grid, kGThreads, kGSmem, m->stream>>>(A, lda, B, ldb, C, ldc, 0, K, m->timeout, m->d_err);
+        MLP_CUDA(m, cudaGetLastError());
+        return PWA_OK;
+    }
+    const long long stride = (long long)M * N;
+    gemm_bf16_kernel<<<grid, kGThreads, kGSmem, m->stream>>>(A, lda, B, ldb, m->ws, N, stride, K, m->timeout,
+                                                             m->d_err);
+    MLP_CUDA(m, cudaGetLastError());
+    split_reduce_kernel<<<blocks_for(stride), 256, 0, m->stream>>>(m->ws, N, stride, Z, M, N, C, ldc);
     MLP_CUDA(m, cudaGetLastError());
     return PWA_OK;
 }
@@ -425,6 +515,7 @@ pwa_status create_impl(pwa_mlp* m, int in, int hid, int layers, int out, int max
         m->fout.push_back(l == L - 1 ? out : hid);
         m->foutp.push_back(l == L - 1 ? m->outp : hid);
     }
+    MLP_CUDA(m, cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem));
     MLP_CUDA(m, cudaMalloc(&m->d_err, sizeof(int)));
     MLP_CUDA(m, cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream));
     size_t max_f = 0;
@@ -465,6 +556,17 @@ pwa_status create_impl(pwa_mlp* m, int in, int hid, int layers, int out, int max
     MLP_TRY(alloc_b(m, &m->T1, std::max((size_t)max_f * maxB, (size_t)hid * std::max(hid, m->outp))));
     MLP_TRY(alloc_b(m, &m->T2, (size_t)max_f * maxB));
     MLP_TRY(alloc_f(m, &m->loss_rows, maxB));
+    // split-K workspace: the largest Z M N over the network's products at batches up to maxB
+    for (int B = kGM; B <= maxB; B += kGM)
+        for (int l = 0; l < L; ++l) {
+            const int fi = m->fin[l], fop = m->foutp[l];
+            const int shapes[3][3] = {{B, fop, fi}, {fop, fi, B}, {B, fi, fop}};
+            for (const auto& sh : shapes) {
+                const int Z = k_splits(sh[0], sh[1], sh[2]);
+                if (Z > 1) m->ws_floats = std::max(m->ws_floats, (size_t)Z * sh[0] * sh[1]);
+            }
+        }
+    if (m->ws_floats) MLP_TRY(alloc_f(m, &m->ws, m->ws_floats));
     MLP_CUDA(m, cudaMalloc(&m->d_periodic, sizeof(int) * out));
     MLP_CUDA(m, cudaMalloc(&m->d_wgt, sizeof(float) * out));
     std::vector<int> per(out, 0);
@@ -634,11 +736,28 @@ pwa_status pwa_mlp_gemm_check(pwa_mlp* m, int M, int N, int K, const float* hA, 
         to_bf16_kernel<<<blocks_for((long long)N * K), 256, 0, m->stream>>>(dB, N, K, bB, K, N);
         e = cudaGetLastError();
     }
+    // a product larger than the network's own may need a larger split-K workspace for the call
+    float* ws_saved = m->ws;
+    const size_t ws_saved_n = m->ws_floats;
+    float* ws_tmp = nullptr;
+    const int Z = k_splits(M, N, K);
+    if (e == cudaSuccess && Z > 1 && (size_t)Z * M * N > m->ws_floats) {
+        e = cudaMalloc(&ws_tmp, sizeof(float) * (size_t)Z * M * N);
+        if (e == cudaSuccess) {
+            m->ws = ws_tmp;
+            m->ws_floats = (size_t)Z * M * N;
+        }
+    }
     if (e == cudaSuccess) st = gemm(m, bA, K, bB, K, dC, N, M, N, K);
     if (e == cudaSuccess && st == PWA_OK) st = check_err(m);
     if (e == cudaSuccess && st == PWA_OK) e = cudaMemcpy(hC, dC, sizeof(float) * (size_t)M * N, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess && st == PWA_OK) st = mlp_cuda(m, e, "gemm check");
-    void* ps[] = {dA, dB, dC, bA, bB};
+    if (ws_tmp) {
+        cudaStreamSynchronize(m->stream);
+        m->ws = ws_saved;
+        m->ws_floats = ws_saved_n;
+    }
+    void* ps[] = {dA, dB, dC, bA, bB, ws_tmp};
     for (void* p : ps)
         if (p) cudaFree(p);
     return st;
@@ -667,7 +786,7 @@ void pwa_mlp_destroy(pwa_mlp* m)
     }
     for (auto* p : m->H) fr(p);
     for (auto* p : m->Z) fr(p);
-    void* ps[] = {m->acc, m->dY, m->dZb, m->dZ32, m->T1, m->T2, m->loss_rows, m->d_periodic, m->d_wgt, m->d_err};
+    void* ps[] = {m->acc, m->dY, m->dZb, m->dZ32, m->T1, m->T2, m->loss_rows, m->ws, m->d_periodic, m->d_wgt, m->d_err};
     for (void* p : ps) fr(p);
     cudaGetLastError();
     delete m;
