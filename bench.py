@@ -399,6 +399,68 @@ def learned_metric(n_train: int, n_eval: int, n_random: int, time_limit: float, 
         gen.close()
 
 
+def variant_shapes(table):
+    """The benchmark's variant model: every third resonance (k = 1, 4, ...)
+    with a mass-dependent width, resonance 6 (a pi pi resonance) Flatte with a
+    K K second channel, the rest constant width."""
+    from types import SimpleNamespace
+    from paper_2403_09225_b300 import binding, workload as W
+    out = []
+    for k, r in enumerate(table):
+        a, b, _ = W.CHANNEL_PAIRS[r.channel]
+        ma, mb = W.DAUGHTER_MASSES[a], W.DAUGHTER_MASSES[b]
+        if k == 6:
+            out.append(SimpleNamespace(kind=binding.SHAPE_FLATTE, ma=ma, mb=mb, mc=0.4937, md=0.4937, radius=3.0,
+                                       width2=0.25))
+        elif k % 3 == 1:
+            out.append(SimpleNamespace(kind=binding.SHAPE_MASS_DEPENDENT, ma=ma, mb=mb, mc=0.0, md=0.0, radius=3.0,
+                                       width2=0.0))
+        else:
+            out.append(SimpleNamespace(kind=binding.SHAPE_CONSTANT, ma=0.0, mb=0.0, mc=0.0, md=0.0, radius=3.0,
+                                       width2=0.0))
+    return out
+
+
+def variant_metric(wl, reps: int = 10):
+    """The physics variants at the paper scale (same events): one fused
+    NLL + gradient + H v pass of the variant kernel per call, with one coupling
+    per resonance and with one per (resonance, projection).  Host-synchronous
+    calls, timed with CUDA events on the calling stream over `reps` calls."""
+    import torch
+    from paper_2403_09225_b300 import binding
+    shapes = variant_shapes(wl.table)
+    nd, nm, K, S = wl.data.n, wl.mc.n, wl.K, wl.S
+    stream = torch.cuda.current_stream()
+    peak, kind = peaks()
+    out = {"model": "paper-scale table, every third resonance with a mass-dependent width, one Flatte",
+           "events": nd + nm}
+    for pp in (False, True):
+        Lv = binding.Variant(wl.data, wl.mc, wl.table, K, S, shapes=shapes, per_projection=pp,
+                             stream=stream.cuda_stream)
+        try:
+            th = binding.Variant.initial_theta(wl.table, shapes, S, pp)
+            v = np.linspace(-1.0, 1.0, Lv.P)
+            for _ in range(3):
+                Lv.eval(th, v)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                Lv.eval(th, v)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            bpp = bytes_per_pass(nd, nm, K, S)
+            achieved = bpp / (ms * 1e-3) / 1e9
+            out["per_projection" if pp else "per_resonance"] = {
+                "P": Lv.P, "ms_per_pass": ms, "event_amps_per_s": (nd + nm) * K / (ms * 1e-3),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "peak_kind": kind, "algorithmic_bytes_per_launch": bpp}}
+        finally:
+            Lv.close()
+    return out
+
+
 def measured_traffic(tiling: dict):
     """DRAM bytes per launch of the fused HVP pass from the committed ncu
     summary, when it was taken with the tiling in use (else None)."""
@@ -442,6 +504,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tiling", default="", help="warps,lanes_per_event,stages[,blocks_per_sm] (default: library's)")
     ap.add_argument("--no-coupling", action="store_true", help="skip the fixed-mass coupling sub-problem leg")
+    ap.add_argument("--no-variants", action="store_true", help="skip the physics-variant leg")
     ap.add_argument("--batching", default="", metavar="TOYS,STARTS",
                     help="also run the uneven-size toy-fit comparison (plain vs batched), e.g. 12,4")
     ap.add_argument("--learned", default="", metavar="TRAIN,EVAL,STARTS",
@@ -528,6 +591,10 @@ def main():
         n_toys, n_starts = (int(x) for x in args.batching.split(","))
         batching = batching_metric(n_toys, n_starts, time_limit=args.fit_time_limit)
 
+    variants = None
+    if rank == 0 and not args.no_variants:
+        variants = variant_metric(wl)
+
     learned = None
     if args.learned and rank == 0:
         n_train, n_eval, n_rand = (int(x) for x in args.learned.split(","))
@@ -566,6 +633,8 @@ def main():
             res["batching"] = batching
         if coupling is not None:
             res["coupling"] = coupling
+        if variants is not None:
+            res["variants"] = variants
         if learned is not None:
             res["learned"] = learned
         print(json.dumps(res))

@@ -300,6 +300,65 @@ pwa_status pwa_coupling_fit(pwa_coupling* cp, int C, const double* theta_c0, con
 
 void pwa_coupling_destroy(pwa_coupling* cp);
 
+/* ---- physics variants (paper Sec. 2.2, Eq. 1 with other line shapes and
+ * couplings; Eqs. 3, 6, 7 for the likelihood, gradient and H v) ----
+ *
+ * BW_k = 1 / D_k with m^2 the channel invariant of resonance k:
+ *   PWA_SHAPE_CONSTANT        D = M^2 - m^2 - i M Gamma (the main path's form)
+ *   PWA_SHAPE_MASS_DEPENDENT  D = M^2 - m^2 - i M Gamma(m),
+ *       Gamma(m) = Gamma0 (q(m)/q(M)) (M/m) (F_L(q(m))/F_L(q(M)))^2, q the
+ *       breakup momentum of the daughters (ma, mb), F_L the von Hippel-Quigg
+ *       barrier factor (unnormalised, z = (q radius)^2) of the resonance's
+ *       spin L = pwa_resonance.spin (0..4); M must stay above ma + mb
+ *   PWA_SHAPE_FLATTE          D = M^2 - m^2 - i (gamma1 rho1(m) + gamma2 rho2(m)),
+ *       rho_i = 2 q_i / m for the channel masses (ma, mb) and (mc, md),
+ *       q_i = i sqrt(-q_i^2) below a channel's threshold
+ * The table's width is Gamma, Gamma0 or gamma1; width2 gives gamma2.
+ * per_projection = 1 gives every (resonance, projection) its own coupling
+ * g_ks = mag e^{i phase} (A_s = sum_k g_ks BW_k F_ks; each projection's
+ * overall phase is then unobservable, so fix the couplings of one resonance).
+ * theta order: free magnitudes (resonance-major, then projection), free
+ * phases (same order), free masses, free widths (Gamma, Gamma0 or gamma1),
+ * free gamma2 of the Flatte resonances; fix_coupling fixes all couplings of
+ * a resonance, fix_width both width parameters. */
+enum { PWA_SHAPE_CONSTANT = 0, PWA_SHAPE_MASS_DEPENDENT = 1, PWA_SHAPE_FLATTE = 2 };
+
+typedef struct {
+    int kind;           /* PWA_SHAPE_*                                        */
+    double ma, mb;      /* daughter masses (Flatte: channel 1), GeV           */
+    double mc, md;      /* Flatte channel 2 masses, GeV                       */
+    double radius;      /* barrier radius, GeV^-1 (mass-dependent width)      */
+    double width2;      /* Flatte gamma2 (start or fixed value)               */
+} pwa_lineshape;
+
+typedef struct pwa_variant pwa_variant; /* opaque; owned by the library */
+
+/* Build a variant likelihood: events as for pwa_create (copied to the device),
+ * shapes [K] (NULL: all constant width), K <= 32, S <= 4.
+ * Errors: PWA_EINVAL, PWA_ENOMEM, PWA_ECUDA (message: pwa_variant_last_error(NULL)). */
+pwa_status pwa_variant_create(pwa_variant** out, const pwa_events* data, const pwa_events* mc,
+                              const pwa_resonance* table, const pwa_lineshape* shapes, int K, int S,
+                              int per_projection, void* cuda_stream);
+
+int pwa_variant_num_params(const pwa_variant* v);
+
+/* NLL, and the gradient [P] and H v [P] when the pointers are non-NULL (hv
+ * needs v), in one pass over the events (host arrays; synchronous).
+ * Errors: PWA_EINVAL (bad theta, a mass below its pair threshold),
+ * PWA_ENONFINITE, PWA_ECUDA. */
+pwa_status pwa_variant_eval(pwa_variant* v, const double* theta, const double* dir, double* nll,
+                            double* grad, double* hv);
+
+/* B Newton-CG fits (rows of theta0 [B][P]) in lockstep on the variant
+ * likelihood; results as pwa_newton_cg_fit_batch. */
+pwa_status pwa_variant_fit(pwa_variant* v, int B, const double* theta0, const pwa_fit_opts* opts,
+                           double* theta_out, pwa_fit_result* results);
+
+/* Message of the last failure of v (of the last pwa_variant_create when v is NULL). */
+const char* pwa_variant_last_error(const pwa_variant* v);
+
+void pwa_variant_destroy(pwa_variant* v);
+
 /* ---- pseudo-experiment generation (paper Sec. 3 draws its test samples
  * from the PWA model itself) ----
  *

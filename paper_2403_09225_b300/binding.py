@@ -39,6 +39,11 @@ class pwa_fit_opts(ctypes.Structure):
                 ("cg_maxiter", ctypes.c_int), ("time_limit_s", ctypes.c_double)]
 
 
+class pwa_lineshape(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("ma", ctypes.c_double), ("mb", ctypes.c_double), ("mc", ctypes.c_double),
+                ("md", ctypes.c_double), ("radius", ctypes.c_double), ("width2", ctypes.c_double)]
+
+
 class pwa_fit_result(ctypes.Structure):
     _fields_ = [("nll", ctypes.c_double), ("grad_max", ctypes.c_double), ("iters", ctypes.c_int),
                 ("n_hvp", ctypes.c_int), ("n_fev", ctypes.c_int), ("status", ctypes.c_int),
@@ -61,7 +66,8 @@ EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "
            "pwa_selftest_bounded_wait", "pwa_last_error", "pwa_destroy", "pwa_mlp_create", "pwa_mlp_forward",
            "pwa_mlp_gradients", "pwa_mlp_train_step", "pwa_mlp_params", "pwa_mlp_gemm_check",
            "pwa_mlp_last_error", "pwa_mlp_destroy", "pwa_accept_reject", "pwa_dalitz_histogram",
-           "pwa_gather_events", "pwa_last_generate_error")
+           "pwa_gather_events", "pwa_last_generate_error", "pwa_variant_create", "pwa_variant_num_params",
+           "pwa_variant_eval", "pwa_variant_fit", "pwa_variant_last_error", "pwa_variant_destroy")
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -120,6 +126,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                       ctypes.c_double, ctypes.c_double, i, vp, vp]),
         "pwa_gather_events": (st, [vp, ctypes.c_longlong, vp, i, vp, i, vp, vp, vp]),
         "pwa_last_generate_error": (ctypes.c_char_p, []),
+        "pwa_variant_create": (st, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(pwa_events),
+                                    ctypes.POINTER(pwa_events), ctypes.POINTER(pwa_resonance),
+                                    ctypes.POINTER(pwa_lineshape), i, i, i, vp]),
+        "pwa_variant_num_params": (i, [vp]),
+        "pwa_variant_eval": (st, [vp, dp, dp, dp, dp, dp]),
+        "pwa_variant_fit": (st, [vp, i, dp, ctypes.POINTER(pwa_fit_opts), dp, ctypes.POINTER(pwa_fit_result)]),
+        "pwa_variant_last_error": (ctypes.c_char_p, [vp]),
+        "pwa_variant_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -448,6 +462,100 @@ def fit_multi(likelihoods, thetas0, xtol: float = 1e-8, gtol: float = 0.0, maxit
     infos = [[{"nll": r.nll, "grad_max": r.grad_max, "iters": r.iters, "n_hvp": r.n_hvp, "n_fev": r.n_fev,
                "status": FIT_STATUS_NAMES[r.status], "elapsed_s": r.elapsed_s} for r in rr] for rr in res]
     return outs, infos, st == PWA_OK
+
+
+SHAPE_CONSTANT, SHAPE_MASS_DEPENDENT, SHAPE_FLATTE = 0, 1, 2
+
+
+class Variant:
+    """A physics-variant likelihood (see include/pwa.h): line shapes per
+    resonance (objects with kind, ma, mb, mc, md, radius, width2 attributes,
+    or None for constant widths) and one coupling per resonance or per
+    (resonance, projection)."""
+
+    def __init__(self, data, mc, table, K: int, S: int, shapes=None, per_projection: bool = False,
+                 stream: int = 0):
+        keep: list = []
+        de = _events(data.m2, data.F, getattr(data, "w", None), keep)
+        me = _events(mc.m2, mc.F, None, keep)
+        tab = resonance_table(table)
+        shp = None
+        if shapes is not None:
+            shp = (pwa_lineshape * K)()
+            for k, sh in enumerate(shapes):
+                shp[k] = pwa_lineshape(int(sh.kind), float(sh.ma), float(sh.mb), float(sh.mc), float(sh.md),
+                                       float(sh.radius), float(sh.width2))
+        h = ctypes.c_void_p()
+        st = lib().pwa_variant_create(ctypes.byref(h), ctypes.byref(de), ctypes.byref(me), tab, shp, int(K), int(S),
+                                      int(bool(per_projection)), ctypes.c_void_p(stream))
+        if st != PWA_OK:
+            raise PwaError(st, lib().pwa_variant_last_error(None).decode())
+        self._h = h
+        self.K, self.S = int(K), int(S)
+        self.P = lib().pwa_variant_num_params(h)
+
+    @staticmethod
+    def initial_theta(table, shapes, S: int, per_projection: bool = False) -> np.ndarray:
+        """theta in the variant's order from the table's values (width2 of
+        the Flatte shapes for gamma2), as pwa_variant_create lays it out."""
+        ns = S if per_projection else 1
+        K = len(table)
+        kind = [0 if shapes is None else int(shapes[k].kind) for k in range(K)]
+        th = [r.mag for r in table if not r.fix_coupling for _ in range(ns)]
+        th += [r.phase for r in table if not r.fix_coupling for _ in range(ns)]
+        th += [r.mass for r in table if not r.fix_mass]
+        th += [r.width for r in table if not r.fix_width]
+        th += [shapes[k].width2 for k, r in enumerate(table) if not r.fix_width and kind[k] == SHAPE_FLATTE]
+        return np.array(th, dtype=np.float64)
+
+    def _check(self, st: int):
+        if st != PWA_OK:
+            raise PwaError(st, lib().pwa_variant_last_error(self._h).decode())
+
+    def nll(self, theta) -> float:
+        th = _f64(theta, self.P)
+        f = ctypes.c_double()
+        self._check(lib().pwa_variant_eval(self._h, _dptr(th), None, ctypes.byref(f), None, None))
+        return f.value
+
+    def eval(self, theta, v=None):
+        """(NLL, grad, H v or None) from one pass."""
+        th = _f64(theta, self.P)
+        f = ctypes.c_double()
+        g = np.empty(self.P)
+        if v is None:
+            self._check(lib().pwa_variant_eval(self._h, _dptr(th), None, ctypes.byref(f), _dptr(g), None))
+            return f.value, g, None
+        vv = _f64(v, self.P)
+        hv = np.empty(self.P)
+        self._check(lib().pwa_variant_eval(self._h, _dptr(th), _dptr(vv), ctypes.byref(f), _dptr(g), _dptr(hv)))
+        return f.value, g, hv
+
+    def fit(self, thetas0, xtol: float = 1e-8, gtol: float = 0.0, maxiter: int = 0, cg_maxiter: int = 0,
+            time_limit_s: float = 0.0):
+        """B fits (rows of thetas0) in lockstep; returns (theta [B, P], infos, all converged)."""
+        th = _f64(thetas0).reshape(-1, self.P)
+        B = th.shape[0]
+        out = np.empty((B, self.P))
+        opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s)
+        res = (pwa_fit_result * B)()
+        st = lib().pwa_variant_fit(self._h, B, _dptr(th), ctypes.byref(opts), _dptr(out), res)
+        if st not in (PWA_OK, PWA_ENOCONV):
+            self._check(st)
+        infos = [{"nll": r.nll, "grad_max": r.grad_max, "iters": r.iters, "n_hvp": r.n_hvp, "n_fev": r.n_fev,
+                  "status": FIT_STATUS_NAMES[r.status], "elapsed_s": r.elapsed_s} for r in res]
+        return out, infos, st == PWA_OK
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pwa_variant_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _gen_check(st: int):

@@ -23,6 +23,7 @@
 #include <exception>
 #include <memory>
 #include <cstring>
+#include <limits>
 #include <vector>
 
 #include "pwa_internal.h"
@@ -689,6 +690,54 @@ struct CouplingRounds final : RoundEvaluator {
     }
 };
 
+// a physics-variant likelihood: one synchronous evaluation per row
+struct VariantRounds final : RoundEvaluator {
+    pwa_variant* v;
+    pwa_handle* h;
+    int Pv;
+    std::vector<double> th, vv, res;
+    std::vector<int> errw;
+    VariantRounds(pwa_variant* vr, int p) : v(vr), h(pwa::variant_base(vr)), Pv(p) {}
+    int P() const override { return Pv; }
+    pwa_handle* handle() const override { return h; }
+    pwa_status reserve(int nb, double** theta, double** dir) override
+    {
+        th.resize((size_t)nb * Pv);
+        vv.resize((size_t)nb * Pv);
+        *theta = th.data();
+        *dir = vv.data();
+        return PWA_OK;
+    }
+    pwa_status issue(int nb, bool any_hv) override
+    {
+        const size_t ow = 1 + 2 * (size_t)Pv;
+        res.assign((size_t)nb * ow, 0.0);
+        errw.assign(nb, 0);
+        for (int b = 0; b < nb; ++b) {
+            double* r = res.data() + b * ow;
+            pwa_status st = pwa::variant_eval(v, th.data() + (size_t)b * Pv, any_hv ? vv.data() + (size_t)b * Pv : nullptr,
+                                              r, r + 1, any_hv ? r + 1 + Pv : nullptr);
+            if (st == PWA_ENONFINITE || st == PWA_EINVAL) {
+                // a point outside the model's domain (non-finite intensity, a mass below its threshold):
+                // the fit sees an error for this row and backs off
+                errw[b] = 1;
+                h->err.clear();
+                r[0] = std::numeric_limits<double>::infinity();
+            } else if (st != PWA_OK) {
+                return st;
+            }
+        }
+        return PWA_OK;
+    }
+    pwa_status finish(int nb, const double** out, const int** err) override
+    {
+        (void)nb;
+        *out = res.data();
+        *err = errw.data();
+        return PWA_OK;
+    }
+};
+
 struct FitGroup {
     std::unique_ptr<RoundEvaluator> ev;
     int B = 0, P = 0;
@@ -894,6 +943,25 @@ extern "C" pwa_status pwa_newton_cg_fit_multi(int n_handles, pwa_handle* const* 
         st = close_group(*groups[i], theta_out[i], results ? results[i] : nullptr, all_ok);
         if (st != PWA_OK) return st;
     }
+    return all_ok ? PWA_OK : PWA_ENOCONV;
+}
+
+extern "C" pwa_status pwa_variant_fit(pwa_variant* v, int B, const double* theta0, const pwa_fit_opts* opts,
+                                      double* theta_out, pwa_fit_result* results)
+{
+    if (!v) return PWA_EINVAL;
+    pwa_handle* h = pwa::variant_base(v);
+    if (!theta_out) return pwa::set_error(h, PWA_EINVAL, "theta_out must not be NULL");
+    std::vector<std::unique_ptr<FitGroup>> groups;
+    groups.push_back(std::make_unique<FitGroup>());
+    pwa_status st = open_group(*groups.back(), std::make_unique<VariantRounds>(v, pwa_variant_num_params(v)), B,
+                               theta0, opts);
+    if (st != PWA_OK) return st;
+    st = run_lockstep(groups);
+    if (st != PWA_OK) return st;
+    bool all_ok = true;
+    st = close_group(*groups[0], theta_out, results, all_ok);
+    if (st != PWA_OK) return st;
     return all_ok ? PWA_OK : PWA_ENOCONV;
 }
 

@@ -120,6 +120,12 @@ void free_batch(pwa_handle* h);
 pwa_status coupling_eval_rows(pwa_coupling* cp, int nb, const double* theta, const double* v, double* out,
                               int* errw);
 pwa_handle* coupling_handle(const pwa_coupling* cp);
+// Physics-variant likelihood: one synchronous evaluation at host theta (dir may
+// be null; grad and hv may be null) and the embedded handle that carries the
+// stream and the error text.
+pwa_status variant_eval(pwa_variant* v, const double* theta, const double* dir, double* nll, double* grad,
+                        double* hv);
+pwa_handle* variant_base(pwa_variant* v);
 // Read back and clear the device error flags; turns them into a status + message.
 pwa_status check_device_errors(pwa_handle* h);
 pwa_status set_error(pwa_handle* h, pwa_status st, const std::string& msg);

@@ -1,0 +1,802 @@
+// variant.cu -- physics variants of the likelihood: line shapes beyond the
+// constant-width Breit-Wigner (a mass-dependent width, the Flatte form) and one
+// coupling per (resonance, projection), with the NLL, its gradient and the exact
+// H v (paper Eqs. 1, 3, 6, 7) from one pass over the events.
+//
+// Kernel layout: a warp walks tiles of 32 events one event at a time; lane k
+// owns resonance k: it evaluates BW_k and its derivatives in the resonance's
+// shape parameters for the event, forms its terms of the coherent sums
+// A_s = sum_k g_ks BW_k F_ks (and of the directional sums Adot_s), which a
+// butterfly over the warp adds up, and accumulates the gradient and H v
+// contributions of its own parameters in registers (FP32 over a tile, FP64
+// across tiles).  Every warp writes one FP64 record; a second kernel sums the
+// records in fixed order and the host combines them (Eqs. 3, 6, 7).
+//
+// Line shapes, D = BW^-1 with m^2 the resonance's channel invariant:
+//   constant width   D = M^2 - m^2 - i M Gamma
+//   mass-dependent   D = M^2 - m^2 - i Gamma0 h(M) rho(m),
+//                    rho(m) = q(m) F_L(q(m))^2 / m, h(M) = M^2 / (q(M) F_L(q(M))^2)
+//                    (i.e. M Gamma(m) with Gamma(m) = Gamma0 (q/q0)(M/m)(F_L(q)/F_L(q0))^2)
+//   Flatte           D = M^2 - m^2 - i (gamma1 rho1(m) + gamma2 rho2(m)), rho_i = 2 q_i / m,
+//                    q_i = i sqrt(-q_i^2) below the channel's threshold.
+// All three are D = (M^2 - m^2) - i (A0 + A1 rho_a + A2 rho_b) with event
+// factors rho_a, rho_b and parameter-only coefficients, and so are their first
+// and second derivatives in (M, w1, w2); the host evaluates those coefficients
+// in FP64 for each theta (h, h', h'' by second-order forward differentiation).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pwa_internal.h"
+
+namespace {
+
+constexpr int kVarWarps = 4;  // warps per block
+constexpr int kVarE = 32;     // events per tile
+
+// A complex linear form of the event factors, X = al - i (e0 + e1 rho_a + e2 rho_b).
+struct Lin {
+    float al, e0, e1, e2;
+};
+
+// Per-resonance constants of one evaluation (FP32, host-computed from theta and v).
+struct VarRes {
+    int ch, kind, L, pad;
+    float M2hi, M2lo;        // M^2 = hi + lo
+    float A0, A1, A2;        // D = (M^2 - m^2) - i (A0 + A1 rho_a + A2 rho_b)
+    float a_pp, a_pm, r2;    // rho_a: (m_a + m_b)^2, (m_a - m_b)^2, barrier radius^2 (kind 1)
+    float b_pp, b_pm;        // rho_b (Flatte channel 2)
+    Lin dD[3];               // dD / d(M, w1, w2)
+    Lin Dv;                  // sum_j dD_j v_j
+    Lin ddv[3];              // sum_i d2D / d theta_j d theta_i v_i
+    float2 g[4], eph[4], gd[4], gd_r[4], gd_p[4];  // per projection: g, e^{i phi}, gdot, d gdot/d rho, d gdot/d phi
+};
+
+struct VarArgs {
+    const float* m2[2];     // [3][n]
+    const float2* F[2];     // [n][K][S]
+    const float* w;         // data weights or null
+    long long n[2];
+    int K;
+    int blocks0;            // blocks of the data sample (the rest take the MC sample)
+    const VarRes* res;
+    double* rec;            // [warps][rec_len] per sample, data warps first
+    int rec_len;
+    int* err;
+};
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 ctimes_i(float2 a) { return make_float2(-a.y, a.x); }
+// Re(a b)
+__device__ __forceinline__ float re_mul(float2 a, float2 b) { return a.x * b.x - a.y * b.y; }
+
+// al - i (e0 + e1 ra + e2 rb) for complex ra, rb
+__device__ __forceinline__ float2 lin_form(Lin c, float2 ra, float2 rb)
+{
+    const float wr = c.e0 + c.e1 * ra.x + c.e2 * rb.x, wi = c.e1 * ra.y + c.e2 * rb.y;
+    return make_float2(c.al + wi, -wr);
+}
+
+__device__ __forceinline__ float barrier_sq(int L, float z)
+{
+    switch (L) {
+    case 0: return 1.f;
+    case 1: return 2.f * z / (1.f + z);
+    case 2: return 13.f * z * z / ((z - 3.f) * (z - 3.f) + 9.f * z);
+    case 3: return 277.f * z * z * z / (z * (z - 15.f) * (z - 15.f) + 9.f * (2.f * z - 5.f) * (2.f * z - 5.f));
+    default: {
+        const float a = z * z - 45.f * z + 105.f, b = 2.f * z - 21.f;
+        return 12746.f * z * z * z * z / (a * a + 25.f * z * b * b);
+    }
+    }
+}
+
+// 2 q / m for masses with (m_a + m_b)^2 = pp, (m_a - m_b)^2 = pm, continued below threshold
+__device__ __forceinline__ float2 rho_flatte(float m2, float pp, float pm)
+{
+    const float q2 = (m2 - pp) * (m2 - pm) / (4.f * m2);
+    const float r = 2.f * sqrtf(fabsf(q2)) * rsqrtf(m2);
+    return q2 >= 0.f ? make_float2(r, 0.f) : make_float2(0.f, r);
+}
+
+template <int S, bool PKS, bool HV>
+__global__ void __launch_bounds__(32 * kVarWarps) variant_kernel(const VarArgs a)
+{
+    constexpr int NC = PKS ? S : 1;     // distinct couplings per resonance
+    constexpr int NP = 2 * NC + 3;      // parameter slots per lane: mags, phases, M, w1, w2
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sample = blockIdx.x < a.blocks0 ? 0 : 1;
+    const int blk = sample ? blockIdx.x - a.blocks0 : blockIdx.x;
+    const int nblk = sample ? gridDim.x - a.blocks0 : a.blocks0;
+    const int wg = blk * kVarWarps + warp, nw = nblk * kVarWarps;
+    const long long n = a.n[sample];
+    const long long ntiles = (n + kVarE - 1) / kVarE;
+    const bool active = lane < a.K;
+    const float* m2p = a.m2[sample];
+    const float2* Fp = a.F[sample];
+    const float* wp = sample == 0 ? a.w : nullptr;
+
+    // this lane's resonance
+    VarRes r{};
+    if (active) r = a.res[lane];
+    const float* m2c = m2p + (long long)r.ch * n;
+
+    double G[NP], H[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) G[j] = H[j] = 0.0;
+    double s0 = 0.0, s1 = 0.0;  // lane 0: sum w ln I (data) or sum I, sum Idot (MC)
+    int bad = 0;
+
+    for (long long t = wg; t < ntiles; t += nw) {
+        float tg[NP], th[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) tg[j] = th[j] = 0.f;
+        float t0 = 0.f, t1 = 0.f;
+        const long long e0 = t * kVarE;
+        const int ne = (int)min((long long)kVarE, n - e0);
+        for (int i = 0; i < ne; ++i) {
+            const long long e = e0 + i;
+            float2 F[S];
+            float m2v = 1.f;
+            if (active) {
+#pragma unroll
+                for (int s = 0; s < S; ++s) F[s] = Fp[(e * a.K + lane) * S + s];
+                m2v = m2c[e];
+            } else {
+#pragma unroll
+                for (int s = 0; s < S; ++s) F[s] = make_float2(0.f, 0.f);
+            }
+            // event factors of the line shape
+            float2 ra = make_float2(0.f, 0.f), rb = make_float2(0.f, 0.f);
+            if (r.kind == 1) {
+                const float q2 = (m2v - r.a_pp) * (m2v - r.a_pm) / (4.f * m2v);
+                const float q = sqrtf(fmaxf(q2, 0.f));
+                ra.x = q * barrier_sq(r.L, q2 * r.r2) * rsqrtf(m2v);
+            } else if (r.kind == 2) {
+                ra = rho_flatte(m2v, r.a_pp, r.a_pm);
+                rb = rho_flatte(m2v, r.b_pp, r.b_pm);
+            }
+            // D and BW = 1 / D
+            const float wr = r.A0 + r.A1 * ra.x + r.A2 * rb.x, wi = r.A1 * ra.y + r.A2 * rb.y;
+            const float2 D = make_float2(((r.M2hi - m2v) + r.M2lo) + wi, -wr);
+            const float inv = active ? 1.f / (D.x * D.x + D.y * D.y) : 0.f;
+            const float2 BW = make_float2(D.x * inv, -D.y * inv);
+            const float2 BW2 = cmul(BW, BW);
+            float2 BWv = make_float2(0.f, 0.f), Dv = make_float2(0.f, 0.f);
+            if (HV) {
+                Dv = lin_form(r.Dv, ra, rb);
+                BWv = cscale(cmul(BW2, Dv), -1.f);
+            }
+            // coherent sums and their directional derivatives, summed over the warp
+            float2 A[S], Ad[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const int c = PKS ? s : 0;
+                const float2 cks = cmul(r.g[c], BW);
+                A[s] = cmul(cks, F[s]);
+                if (HV) Ad[s] = cmul(cadd(cmul(r.gd[c], BW), cmul(r.g[c], BWv)), F[s]);
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    A[s].x += __shfl_xor_sync(0xffffffffu, A[s].x, o);
+                    A[s].y += __shfl_xor_sync(0xffffffffu, A[s].y, o);
+                    if (HV) {
+                        Ad[s].x += __shfl_xor_sync(0xffffffffu, Ad[s].x, o);
+                        Ad[s].y += __shfl_xor_sync(0xffffffffu, Ad[s].y, o);
+                    }
+                }
+            }
+            float I = 0.f, Id = 0.f;
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                I += A[s].x * A[s].x + A[s].y * A[s].y;
+                if (HV) Id += 2.f * (A[s].x * Ad[s].x + A[s].y * Ad[s].y);
+            }
+            float wa = 1.f, wb = 0.f;
+            if (sample == 0) {
+                const float we = wp ? wp[e] : 1.f;
+                if (!(I > 0.f) || !isfinite(I)) {
+                    bad = 1;
+                    continue;
+                }
+                wa = we / I;
+                wb = HV ? we * Id / (I * I) : 0.f;
+                if (lane == 0) t0 += we * logf(I);
+            } else {
+                if (!isfinite(I)) {
+                    bad = 1;
+                    continue;
+                }
+                if (lane == 0) {
+                    t0 += I;
+                    t1 += Id;
+                }
+            }
+            // D_s = conj(A_s) F_ks, Dd_s = conj(Adot_s) F_ks; E = sum_s D_s g_s and friends
+            float2 Dk[S], Ddk[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                Dk[s] = cmul(cconj(A[s]), F[s]);
+                if (HV) Ddk[s] = cmul(cconj(Ad[s]), F[s]);
+            }
+            // couplings
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                float2 Dc = Dk[c], Ddc = HV ? Ddk[c] : make_float2(0.f, 0.f);
+                if (!PKS) {
+#pragma unroll
+                    for (int s = 1; s < S; ++s) {
+                        Dc = cadd(Dc, Dk[s]);
+                        if (HV) Ddc = cadd(Ddc, Ddk[s]);
+                    }
+                }
+                const float2 dmag = cmul(r.eph[c], BW), dph = cmul(ctimes_i(r.g[c]), BW);
+                const float gm = 2.f * re_mul(Dc, dmag), gp = 2.f * re_mul(Dc, dph);
+                tg[c] += wa * gm;
+                tg[NC + c] += wa * gp;
+                if (HV) {
+                    const float hm = 2.f * (re_mul(Ddc, dmag) +
+                                            re_mul(Dc, cadd(cmul(r.gd_r[c], BW), cmul(r.eph[c], BWv))));
+                    const float hp = 2.f * (re_mul(Ddc, dph) +
+                                            re_mul(Dc, cadd(cmul(r.gd_p[c], BW), cmul(ctimes_i(r.g[c]), BWv))));
+                    th[c] += wa * hm - wb * gm;
+                    th[NC + c] += wa * hp - wb * gp;
+                }
+            }
+            // shape parameters M, w1, w2
+            float2 E = make_float2(0.f, 0.f), Ed = E;
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const int c = PKS ? s : 0;
+                E = cadd(E, cmul(Dk[s], r.g[c]));
+                if (HV) Ed = cadd(Ed, cadd(cmul(Ddk[s], r.g[c]), cmul(Dk[s], r.gd[c])));
+            }
+            const float2 BW3 = cmul(BW2, BW);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float2 dD = lin_form(r.dD[j], ra, rb);
+                const float2 dBW = cscale(cmul(BW2, dD), -1.f);
+                const float gj = 2.f * re_mul(E, dBW);
+                tg[2 * NC + j] += wa * gj;
+                if (HV) {
+                    const float2 dBWv = cadd(cscale(cmul(BW3, cmul(dD, Dv)), 2.f),
+                                             cscale(cmul(BW2, lin_form(r.ddv[j], ra, rb)), -1.f));
+                    const float hj = 2.f * (re_mul(Ed, dBW) + re_mul(E, dBWv));
+                    th[2 * NC + j] += wa * hj - wb * gj;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            G[j] += (double)tg[j];
+            H[j] += (double)th[j];
+        }
+        s0 += (double)t0;
+        s1 += (double)t1;
+    }
+    double* rec = a.rec + ((long long)(sample ? a.blocks0 * kVarWarps : 0) + wg) * a.rec_len;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        rec[lane * 2 * NP + j] = G[j];
+        rec[lane * 2 * NP + NP + j] = H[j];
+    }
+    if (lane == 0) {
+        rec[32 * 2 * NP] = s0;
+        rec[32 * 2 * NP + 1] = s1;
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, 1);
+}
+
+// out[sample][j] = sum over the sample's warps of rec[warp][j], in warp order
+__global__ void variant_reduce_kernel(const double* __restrict__ rec, int rec_len, int warps0, int warps1,
+                                      double* __restrict__ out)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= 2 * rec_len) return;
+    const int sample = j / rec_len, slot = j % rec_len;
+    const int w0 = sample ? warps0 : 0, nw = sample ? warps1 : warps0;
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += rec[(long long)(w0 + w) * rec_len + slot];
+    out[j] = s;
+}
+
+using VarKernel = void (*)(const VarArgs);
+
+template <int S>
+VarKernel pick_s(bool pks, bool hv)
+{
+    if (pks) return hv ? variant_kernel<S, true, true> : variant_kernel<S, true, false>;
+    return hv ? variant_kernel<S, false, true> : variant_kernel<S, false, false>;
+}
+
+VarKernel pick(int S, bool pks, bool hv)
+{
+    switch (S) {
+    case 1: return pick_s<1>(pks, hv);
+    case 2: return pick_s<2>(pks, hv);
+    case 3: return pick_s<3>(pks, hv);
+    case 4: return pick_s<4>(pks, hv);
+    }
+    return nullptr;
+}
+
+// value, first and second derivative of a function of one variable
+struct Jet {
+    double v, d, dd;
+};
+Jet operator+(Jet a, Jet b) { return {a.v + b.v, a.d + b.d, a.dd + b.dd}; }
+Jet operator-(Jet a, Jet b) { return {a.v - b.v, a.d - b.d, a.dd - b.dd}; }
+Jet operator*(Jet a, Jet b) { return {a.v * b.v, a.d * b.v + a.v * b.d, a.dd * b.v + 2 * a.d * b.d + a.v * b.dd}; }
+Jet operator*(double s, Jet a) { return {s * a.v, s * a.d, s * a.dd}; }
+Jet operator+(Jet a, double s) { return {a.v + s, a.d, a.dd}; }
+Jet recip(Jet a)
+{
+    const double r = 1.0 / a.v;
+    return {r, -a.d * r * r, (2 * a.d * a.d * r - a.dd) * r * r};
+}
+Jet operator/(Jet a, Jet b) { return a * recip(b); }
+Jet jsqrt(Jet a)
+{
+    const double r = std::sqrt(a.v);
+    return {r, a.d / (2 * r), a.dd / (2 * r) - a.d * a.d / (4 * r * a.v)};
+}
+
+Jet barrier_sq_jet(int L, Jet z)
+{
+    switch (L) {
+    case 0: return {1.0, 0.0, 0.0};
+    case 1: return (2.0 * z) / (z + 1.0);
+    case 2: {
+        const Jet a = z + (-3.0);
+        return (13.0 * (z * z)) / (a * a + 9.0 * z);
+    }
+    case 3: {
+        const Jet a = z + (-15.0), b = 2.0 * z + (-5.0);
+        return (277.0 * (z * z * z)) / (z * a * a + 9.0 * (b * b));
+    }
+    default: {
+        const Jet a = z * z - 45.0 * z + 105.0, b = 2.0 * z + (-21.0);
+        return (12746.0 * (z * z * z * z)) / (a * a + 25.0 * (z * b * b));
+    }
+    }
+}
+
+}  // namespace
+
+struct pwa_variant {
+    pwa_handle base;  // stream, error text, K, S, P for the shared fit machinery
+    int per_projection = 0;
+    // plain arrays: the header's structs are unnamed typedefs, which the CUDA
+    // front end does not place in standard containers in C++20 mode
+    pwa_resonance* table = nullptr;  // [K]
+    pwa_lineshape* shapes = nullptr; // [K]
+    // theta layout: (what, k, s) with what 0 mag, 1 phase, 2 mass, 3 w1, 4 w2
+    std::vector<int> lay_what, lay_k, lay_s;
+    float* d_m2[2] = {nullptr, nullptr};
+    float2* d_F[2] = {nullptr, nullptr};
+    float* d_w = nullptr;
+    VarRes* d_res = nullptr;
+    double* d_rec = nullptr;
+    double* d_sums = nullptr;
+    int* d_err = nullptr;
+    double* h_sums = nullptr;  // pinned: 2 rec_len sums + the error word
+    int rec_len = 0, blocks0 = 0, blocks1 = 0;
+    VarRes* h_res = nullptr;   // pinned
+};
+
+namespace {
+
+pwa_status vfail(pwa_variant* v, pwa_status st, const std::string& msg) { return pwa::set_error(&v->base, st, msg); }
+
+#define VAR_TRY(call)                 \
+    do {                              \
+        pwa_status s_ = (call);       \
+        if (s_ != PWA_OK) return s_;  \
+    } while (0)
+
+#define VAR_CUDA(v, call)                                                   \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) return pwa::cuda_error(&(v)->base, e_, #call); \
+    } while (0)
+
+int NC_of(const pwa_variant* v) { return v->per_projection ? v->base.S : 1; }
+
+// host: per-resonance constants for theta (and direction v, may be null)
+pwa_status fill_res(pwa_variant* vv, const double* theta, const double* dir)
+{
+    const int K = vv->base.K, S = vv->base.S, NC = NC_of(vv);
+    std::vector<double> mag((size_t)K * NC), ph((size_t)K * NC), M(K), w1(K), w2(K);
+    std::vector<double> vmag((size_t)K * NC, 0.0), vph((size_t)K * NC, 0.0), vM(K, 0.0), vw1(K, 0.0), vw2(K, 0.0);
+    for (int k = 0; k < K; ++k) {
+        for (int c = 0; c < NC; ++c) {
+            mag[k * NC + c] = vv->table[k].mag;
+            ph[k * NC + c] = vv->table[k].phase;
+        }
+        M[k] = vv->table[k].mass;
+        w1[k] = vv->table[k].width;
+        w2[k] = vv->shapes[k].width2;
+    }
+    for (size_t i = 0; i < vv->lay_what.size(); ++i) {
+        const int k = vv->lay_k[i], c = vv->lay_s[i];
+        const double x = theta[i], d = dir ? dir[i] : 0.0;
+        switch (vv->lay_what[i]) {
+        case 0: mag[k * NC + c] = x; vmag[k * NC + c] = d; break;
+        case 1: ph[k * NC + c] = x; vph[k * NC + c] = d; break;
+        case 2: M[k] = x; vM[k] = d; break;
+        case 3: w1[k] = x; vw1[k] = d; break;
+        default: w2[k] = x; vw2[k] = d; break;
+        }
+    }
+    for (int k = 0; k < K; ++k) {
+        VarRes& r = vv->h_res[k];
+        std::memset(&r, 0, sizeof(r));
+        const pwa_lineshape& sh = vv->shapes[k];
+        r.ch = vv->table[k].channel;
+        r.kind = sh.kind;
+        r.L = vv->table[k].spin;
+        const double Mk = M[k];
+        if (!(Mk > 0.0)) return vfail(vv, PWA_EINVAL, "masses must be positive");
+        const double M2 = Mk * Mk;
+        r.M2hi = (float)M2;
+        r.M2lo = (float)(M2 - (double)r.M2hi);
+        // dD[j] = {al, e0, e1, e2}; second derivatives d2[j][i] likewise
+        double dD[3][4] = {{0}}, d2[3][3][4] = {{{0}}};
+        dD[0][0] = 2 * Mk;
+        d2[0][0][0] = 2.0;
+        if (sh.kind == PWA_SHAPE_CONSTANT) {
+            r.A0 = (float)(Mk * w1[k]);
+            dD[0][1] = w1[k];  // d(M Gamma)/dM
+            dD[1][1] = Mk;     // d(M Gamma)/dGamma
+            d2[0][1][1] = d2[1][0][1] = 1.0;
+        } else if (sh.kind == PWA_SHAPE_MASS_DEPENDENT) {
+            const double pp = (sh.ma + sh.mb) * (sh.ma + sh.mb), pm = (sh.ma - sh.mb) * (sh.ma - sh.mb);
+            r.a_pp = (float)pp;
+            r.a_pm = (float)pm;
+            r.r2 = (float)(sh.radius * sh.radius);
+            // h(M) = M^2 / (q(M) F_L(q(M))^2) with its first two derivatives
+            const Jet Mj{Mk, 1.0, 0.0};
+            const Jet M2j = Mj * Mj;
+            const Jet q2 = ((M2j + (-pp)) * (M2j + (-pm))) / (4.0 * M2j);
+            if (!(q2.v > 0.0)) return vfail(vv, PWA_EINVAL, "a mass-dependent width needs M above the pair threshold");
+            const Jet h = M2j / (jsqrt(q2) * barrier_sq_jet(r.L, (sh.radius * sh.radius) * q2));
+            r.A1 = (float)(w1[k] * h.v);
+            dD[0][2] = w1[k] * h.d;
+            dD[1][2] = h.v;
+            d2[0][0][2] = w1[k] * h.dd;
+            d2[0][1][2] = d2[1][0][2] = h.d;
+        } else {
+            r.a_pp = (float)((sh.ma + sh.mb) * (sh.ma + sh.mb));
+            r.a_pm = (float)((sh.ma - sh.mb) * (sh.ma - sh.mb));
+            r.b_pp = (float)((sh.mc + sh.md) * (sh.mc + sh.md));
+            r.b_pm = (float)((sh.mc - sh.md) * (sh.mc - sh.md));
+            r.A1 = (float)w1[k];
+            r.A2 = (float)w2[k];
+            dD[1][2] = 1.0;
+            dD[2][3] = 1.0;
+        }
+        const double vs[3] = {vM[k], vw1[k], vw2[k]};
+        auto lin = [](const double c[4]) { return Lin{(float)c[0], (float)c[1], (float)c[2], (float)c[3]}; };
+        double dv[4] = {0, 0, 0, 0};
+        for (int j = 0; j < 3; ++j) {
+            double ddvj[4] = {0, 0, 0, 0};
+            for (int q = 0; q < 4; ++q) {
+                dv[q] += dD[j][q] * vs[j];
+                for (int i = 0; i < 3; ++i) ddvj[q] += d2[j][i][q] * vs[i];
+            }
+            r.dD[j] = lin(dD[j]);
+            r.ddv[j] = lin(ddvj);
+        }
+        r.Dv = lin(dv);
+        for (int s = 0; s < S && s < 4; ++s) {
+            const int c = vv->per_projection ? s : 0;
+            const double rho = mag[k * NC + c], phi = ph[k * NC + c], vr = vmag[k * NC + c], vp = vph[k * NC + c];
+            const double er = std::cos(phi), ei = std::sin(phi);
+            const double gr_ = rho * er, gi_ = rho * ei;                        // g = rho e^{i phi}
+            const double gdr = vr * er - vp * gi_, gdi = vr * ei + vp * gr_;    // gdot = vr e + vp i g
+            const double grr = -vp * ei, gri = vp * er;                         // d gdot / d rho = vp i e
+            const double gpr = -vr * ei - vp * gr_, gpi = vr * er - vp * gi_;   // d gdot / d phi = vr i e - vp g
+            r.g[s] = make_float2((float)gr_, (float)gi_);
+            r.eph[s] = make_float2((float)er, (float)ei);
+            r.gd[s] = make_float2((float)gdr, (float)gdi);
+            r.gd_r[s] = make_float2((float)grr, (float)gri);
+            r.gd_p[s] = make_float2((float)gpr, (float)gpi);
+        }
+    }
+    return PWA_OK;
+}
+
+pwa_status copy_sample(pwa_variant* v, int s, const pwa_events* ev, bool is_data)
+{
+    const int K = v->base.K, S = v->base.S;
+    const long long n = ev->n;
+    const size_t nF = (size_t)n * K * S;
+    VAR_CUDA(v, cudaMalloc(&v->d_m2[s], sizeof(float) * 3 * (size_t)n));
+    VAR_CUDA(v, cudaMalloc(&v->d_F[s], sizeof(float2) * nF));
+    const cudaMemcpyKind kind = ev->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    VAR_CUDA(v, cudaMemcpyAsync(v->d_m2[s], ev->m2, sizeof(float) * 3 * (size_t)n, kind, v->base.stream));
+    VAR_CUDA(v, cudaMemcpyAsync(v->d_F[s], ev->F, sizeof(float2) * nF, kind, v->base.stream));
+    if (is_data && ev->w) {
+        VAR_CUDA(v, cudaMalloc(&v->d_w, sizeof(float) * (size_t)n));
+        VAR_CUDA(v, cudaMemcpyAsync(v->d_w, ev->w, sizeof(float) * (size_t)n, kind, v->base.stream));
+    }
+    return PWA_OK;
+}
+
+// host checks of a sample given in host memory (device inputs are taken as given: the kernel flags a
+// non-finite or non-positive intensity at evaluation time)
+pwa_status check_sample(pwa_variant* v, const pwa_events* ev, bool is_data, double& weight_sum)
+{
+    if (!ev || ev->n < 1 || !ev->m2 || !ev->F) return vfail(v, PWA_EINVAL, "every sample needs n >= 1, m2 and F");
+    weight_sum = (double)ev->n;
+    if (!is_data && ev->w) return vfail(v, PWA_EINVAL, "the MC sample takes no weights");
+    if (ev->on_device) return PWA_OK;
+    const long long n = ev->n;
+    const size_t nF = (size_t)n * v->base.K * v->base.S * 2;
+    for (size_t i = 0; i < 3 * (size_t)n; ++i)
+        if (!std::isfinite(ev->m2[i]) || !(ev->m2[i] > 0.f)) return vfail(v, PWA_EINVAL, "m2 must be finite and > 0");
+    for (size_t i = 0; i < nF; ++i)
+        if (!std::isfinite(ev->F[i])) return vfail(v, PWA_EINVAL, "F must be finite");
+    if (is_data && ev->w) {
+        weight_sum = 0.0;
+        for (long long i = 0; i < n; ++i) {
+            if (!std::isfinite(ev->w[i]) || ev->w[i] < 0.f) return vfail(v, PWA_EINVAL, "weights must be finite, >= 0");
+            weight_sum += ev->w[i];
+        }
+    }
+    return PWA_OK;
+}
+
+pwa_status create_impl(pwa_variant* v, const pwa_events* data, const pwa_events* mc, const pwa_resonance* table,
+                       const pwa_lineshape* shapes, int K, int S, int per_projection)
+{
+    if (!data || !mc || !table) return vfail(v, PWA_EINVAL, "data, mc and table must not be NULL");
+    if (K < 1 || K > 32 || S < 1 || S > 4) return vfail(v, PWA_EINVAL, "need 1 <= K <= 32 and 1 <= S <= 4");
+    v->base.K = K;
+    v->base.S = S;
+    v->per_projection = per_projection ? 1 : 0;
+    v->table = new (std::nothrow) pwa_resonance[K];
+    v->shapes = new (std::nothrow) pwa_lineshape[K];
+    if (!v->table || !v->shapes) return vfail(v, PWA_ENOMEM, "host allocation failed");
+    for (int k = 0; k < K; ++k) v->table[k] = table[k];
+    for (int k = 0; k < K; ++k) {
+        pwa_lineshape sh{};
+        sh.kind = PWA_SHAPE_CONSTANT;
+        if (shapes) sh = shapes[k];
+        const pwa_resonance& r = table[k];
+        if (r.channel < 0 || r.channel > 2) return vfail(v, PWA_EINVAL, "channels are 0..2");
+        if (sh.kind < 0 || sh.kind > 2) return vfail(v, PWA_EINVAL, "unknown line shape");
+        if (sh.kind == PWA_SHAPE_MASS_DEPENDENT && (r.spin < 0 || r.spin > 4 || !(sh.radius > 0.0) ||
+                                                     !(sh.ma >= 0.0) || !(sh.mb >= 0.0)))
+            return vfail(v, PWA_EINVAL, "a mass-dependent width needs spin 0..4, radius > 0, daughter masses >= 0");
+        if (sh.kind == PWA_SHAPE_FLATTE && !(sh.ma >= 0.0 && sh.mb >= 0.0 && sh.mc >= 0.0 && sh.md >= 0.0))
+            return vfail(v, PWA_EINVAL, "Flatte channel masses must be >= 0");
+        if (!std::isfinite(r.mass) || !(r.mass > 0.0) || !std::isfinite(r.width) || !std::isfinite(r.mag) ||
+            !std::isfinite(r.phase) || !std::isfinite(sh.width2))
+            return vfail(v, PWA_EINVAL, "table values must be finite, masses positive");
+        v->shapes[k] = sh;
+    }
+    // theta layout
+    const int NC = NC_of(v);
+    for (int what = 0; what < 2; ++what)
+        for (int k = 0; k < K; ++k)
+            if (!table[k].fix_coupling)
+                for (int c = 0; c < NC; ++c) {
+                    v->lay_what.push_back(what);
+                    v->lay_k.push_back(k);
+                    v->lay_s.push_back(c);
+                }
+    for (int k = 0; k < K; ++k)
+        if (!table[k].fix_mass) {
+            v->lay_what.push_back(2);
+            v->lay_k.push_back(k);
+            v->lay_s.push_back(0);
+        }
+    for (int k = 0; k < K; ++k)
+        if (!table[k].fix_width) {
+            v->lay_what.push_back(3);
+            v->lay_k.push_back(k);
+            v->lay_s.push_back(0);
+        }
+    for (int k = 0; k < K; ++k)
+        if (!table[k].fix_width && v->shapes[k].kind == PWA_SHAPE_FLATTE) {
+            v->lay_what.push_back(4);
+            v->lay_k.push_back(k);
+            v->lay_s.push_back(0);
+        }
+    v->base.P = (int)v->lay_what.size();
+    double wsum = 0.0, dummy = 0.0;
+    pwa_status st = check_sample(v, data, true, wsum);
+    if (st != PWA_OK) return st;
+    st = check_sample(v, mc, false, dummy);
+    if (st != PWA_OK) return st;
+    v->base.n[0] = data->n;
+    v->base.n[1] = mc->n;
+    v->base.Nd = wsum;
+    v->base.Nmc = (double)mc->n;
+    if (data->on_device && data->w) {
+        // the weight sum of device weights
+        std::vector<float> hw((size_t)data->n);
+        VAR_CUDA(v, cudaMemcpy(hw.data(), data->w, sizeof(float) * (size_t)data->n, cudaMemcpyDeviceToHost));
+        v->base.Nd = 0.0;
+        for (float x : hw) v->base.Nd += x;
+    }
+    st = copy_sample(v, 0, data, true);
+    if (st != PWA_OK) return st;
+    st = copy_sample(v, 1, mc, false);
+    if (st != PWA_OK) return st;
+    // grid: about three blocks per SM, split between the samples by their tile counts
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long t0 = (data->n + kVarE - 1) / kVarE, t1 = (mc->n + kVarE - 1) / kVarE;
+    const long long total = std::max(2LL, std::min((long long)3 * sms, (t0 + t1 + kVarWarps - 1) / kVarWarps));
+    long long b0 = std::max(1LL, std::llround((double)total * t0 / (double)(t0 + t1)));
+    b0 = std::min(b0, std::max(1LL, (t0 + kVarWarps - 1) / kVarWarps));
+    long long b1 = std::max(1LL, std::min(total - b0, (t1 + kVarWarps - 1) / kVarWarps));
+    v->blocks0 = (int)b0;
+    v->blocks1 = (int)b1;
+    const int NP = 2 * NC + 3;
+    v->rec_len = 32 * 2 * NP + 2;
+    VAR_CUDA(v, cudaMalloc(&v->d_rec, sizeof(double) * (size_t)(b0 + b1) * kVarWarps * v->rec_len));
+    VAR_CUDA(v, cudaMalloc(&v->d_sums, sizeof(double) * 2 * (size_t)v->rec_len));
+    VAR_CUDA(v, cudaMalloc(&v->d_res, sizeof(VarRes) * K));
+    VAR_CUDA(v, cudaMalloc(&v->d_err, sizeof(int)));
+    VAR_CUDA(v, cudaMemsetAsync(v->d_err, 0, sizeof(int), v->base.stream));
+    VAR_CUDA(v, cudaMallocHost(&v->h_sums, sizeof(double) * (2 * (size_t)v->rec_len + 1)));
+    VAR_CUDA(v, cudaMallocHost(&v->h_res, sizeof(VarRes) * K));
+    VAR_CUDA(v, cudaStreamSynchronize(v->base.stream));
+    return PWA_OK;
+}
+
+}  // namespace
+
+namespace pwa {
+
+// One evaluation (NLL, and the gradient and H v when asked) at host theta, v.
+pwa_status variant_eval(pwa_variant* v, const double* theta, const double* dir, double* nll, double* grad, double* hv)
+{
+    const int K = v->base.K, S = v->base.S, P = v->base.P, NC = NC_of(v), NP = 2 * NC + 3;
+    VAR_TRY(fill_res(v, theta, hv ? dir : nullptr));
+    cudaStream_t st = v->base.stream;
+    VAR_CUDA(v, cudaMemcpyAsync(v->d_res, v->h_res, sizeof(VarRes) * K, cudaMemcpyHostToDevice, st));
+    VarArgs a{};
+    a.m2[0] = v->d_m2[0];
+    a.m2[1] = v->d_m2[1];
+    a.F[0] = v->d_F[0];
+    a.F[1] = v->d_F[1];
+    a.w = v->d_w;
+    a.n[0] = v->base.n[0];
+    a.n[1] = v->base.n[1];
+    a.K = K;
+    a.blocks0 = v->blocks0;
+    a.res = v->d_res;
+    a.rec = v->d_rec;
+    a.rec_len = v->rec_len;
+    a.err = v->d_err;
+    VarKernel fn = pick(S, v->per_projection != 0, hv != nullptr);
+    if (!fn) return vfail(v, PWA_EINVAL, "no variant kernel for this S");
+    fn<<<v->blocks0 + v->blocks1, 32 * kVarWarps, 0, st>>>(a);
+    VAR_CUDA(v, cudaGetLastError());
+    variant_reduce_kernel<<<(2 * v->rec_len + 255) / 256, 256, 0, st>>>(v->d_rec, v->rec_len, v->blocks0 * kVarWarps,
+                                                                        v->blocks1 * kVarWarps, v->d_sums);
+    VAR_CUDA(v, cudaGetLastError());
+    VAR_CUDA(v, cudaMemcpyAsync(v->h_sums, v->d_sums, sizeof(double) * 2 * v->rec_len, cudaMemcpyDeviceToHost, st));
+    VAR_CUDA(v, cudaMemcpyAsync(v->h_sums + 2 * v->rec_len, v->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VAR_CUDA(v, cudaMemsetAsync(v->d_err, 0, sizeof(int), st));
+    VAR_CUDA(v, cudaStreamSynchronize(st));
+    int errw = 0;
+    std::memcpy(&errw, v->h_sums + 2 * v->rec_len, sizeof(int));
+    if (errw) return vfail(v, PWA_ENONFINITE, "an event's intensity is not finite, or not positive for a data event");
+    // Eqs. 3, 6, 7 from the sums
+    const double* sd = v->h_sums;                 // data: lanes' [G NP][H NP], then sum w ln I
+    const double* sm = v->h_sums + v->rec_len;    // MC: lanes' [G NP][H NP], then sum I, sum Idot
+    const double SL = sd[32 * 2 * NP], G = sm[32 * 2 * NP], Gd = sm[32 * 2 * NP + 1];
+    if (!(G > 0.0) || !std::isfinite(SL)) return vfail(v, PWA_ENONFINITE, "the MC normalisation is not positive");
+    const double Nd = v->base.Nd;
+    *nll = -SL + Nd * std::log(G / v->base.Nmc);
+    if (grad || hv) {
+        for (int i = 0; i < P; ++i) {
+            const int what = v->lay_what[i], k = v->lay_k[i], c = v->lay_s[i];
+            const int slot = what == 0 ? c : what == 1 ? NC + c : 2 * NC + (what - 2);
+            const double gD = sd[k * 2 * NP + slot], hD = sd[k * 2 * NP + NP + slot];
+            const double gM = sm[k * 2 * NP + slot], hM = sm[k * 2 * NP + NP + slot];
+            if (grad) grad[i] = -gD + Nd * gM / G;
+            if (hv) hv[i] = -hD + Nd * (hM / G - gM * Gd / (G * G));
+        }
+    }
+    (void)S;
+    return PWA_OK;
+}
+
+}  // namespace pwa
+
+extern "C" {
+
+thread_local std::string g_variant_create_error;
+
+pwa_status pwa_variant_create(pwa_variant** out, const pwa_events* data, const pwa_events* mc,
+                              const pwa_resonance* table, const pwa_lineshape* shapes, int K, int S, int per_projection,
+                              void* cuda_stream)
+{
+    g_variant_create_error.clear();
+    if (!out) return PWA_EINVAL;
+    *out = nullptr;
+    auto* v = new (std::nothrow) pwa_variant();
+    if (!v) return PWA_ENOMEM;
+    v->base.stream = static_cast<cudaStream_t>(cuda_stream);
+    pwa_status st;
+    try {
+        st = create_impl(v, data, mc, table, shapes, K, S, per_projection);
+    } catch (...) {
+        st = vfail(v, PWA_ENOMEM, "host exception during create");
+    }
+    if (st != PWA_OK) {
+        g_variant_create_error = v->base.err;
+        pwa_variant_destroy(v);
+        return st;
+    }
+    *out = v;
+    return PWA_OK;
+}
+
+int pwa_variant_num_params(const pwa_variant* v) { return v ? v->base.P : -1; }
+
+pwa_status pwa_variant_eval(pwa_variant* v, const double* theta, const double* dir, double* nll, double* grad,
+                            double* hv)
+{
+    if (!v) return PWA_EINVAL;
+    v->base.err.clear();
+    if (!theta || !nll) return vfail(v, PWA_EINVAL, "theta and nll must not be NULL");
+    if (hv && !dir) return vfail(v, PWA_EINVAL, "v is required for hv");
+    for (int i = 0; i < v->base.P; ++i)
+        if (!std::isfinite(theta[i]) || (hv && !std::isfinite(dir[i])))
+            return vfail(v, PWA_EINVAL, "theta and v must be finite");
+    std::vector<double> g_tmp;
+    if (hv && !grad) {
+        g_tmp.resize(v->base.P);
+        grad = g_tmp.data();
+    }
+    return pwa::variant_eval(v, theta, dir, nll, grad, hv);
+}
+
+const char* pwa_variant_last_error(const pwa_variant* v)
+{
+    return v ? v->base.err.c_str() : g_variant_create_error.c_str();
+}
+
+void pwa_variant_destroy(pwa_variant* v)
+{
+    if (!v) return;
+    if (v->base.stream) cudaStreamSynchronize(v->base.stream);
+    else cudaDeviceSynchronize();
+    for (int s = 0; s < 2; ++s) {
+        if (v->d_m2[s]) cudaFree(v->d_m2[s]);
+        if (v->d_F[s]) cudaFree(v->d_F[s]);
+    }
+    void* ps[] = {v->d_w, v->d_res, v->d_rec, v->d_sums, v->d_err};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    if (v->h_sums) cudaFreeHost(v->h_sums);
+    if (v->h_res) cudaFreeHost(v->h_res);
+    delete[] v->table;
+    delete[] v->shapes;
+    cudaGetLastError();
+    delete v;
+}
+
+}  // extern "C"
+
+namespace pwa {
+pwa_handle* variant_base(pwa_variant* v) { return v ? &v->base : nullptr; }
+}  // namespace pwa
