@@ -107,153 +107,170 @@ __device__ __forceinline__ float2 rho_flatte(float m2, float pp, float pm)
     return q2 >= 0.f ? make_float2(r, 0.f) : make_float2(0.f, r);
 }
 
+// Shared memory of a block: the K resonances' constants, then per warp a
+// [2 NP][33] FP32 transpose tile and [32][2 NP] FP64 accumulators.
+template <int NP>
+__host__ __device__ constexpr size_t var_smem_bytes()
+{
+    return ((32 * sizeof(VarRes) + 15) / 16) * 16 + kVarWarps * (2 * NP * 33 * sizeof(float)) +
+           kVarWarps * (32 * 2 * NP * sizeof(double));
+}
+
+// event factors of resonance r's line shape at pair mass^2 m2v
+__device__ __forceinline__ void shape_factors(const VarRes& r, float m2v, float2& ra, float2& rb)
+{
+    ra = make_float2(0.f, 0.f);
+    rb = make_float2(0.f, 0.f);
+    if (r.kind == 1) {
+        const float q2 = (m2v - r.a_pp) * (m2v - r.a_pm) / (4.f * m2v);
+        const float q = sqrtf(fmaxf(q2, 0.f));
+        ra.x = q * barrier_sq(r.L, q2 * r.r2) * rsqrtf(m2v);
+    } else if (r.kind == 2) {
+        ra = rho_flatte(m2v, r.a_pp, r.a_pm);
+        rb = rho_flatte(m2v, r.b_pp, r.b_pm);
+    }
+}
+
+// BW = 1 / D for D = (M^2 - m^2) - i (A0 + A1 ra + A2 rb)
+__device__ __forceinline__ float2 breit_wigner_v(const VarRes& r, float m2v, float2 ra, float2 rb)
+{
+    const float wr = r.A0 + r.A1 * ra.x + r.A2 * rb.x, wi = r.A1 * ra.y + r.A2 * rb.y;
+    const float2 D = make_float2(((r.M2hi - m2v) + r.M2lo) + wi, -wr);
+    const float inv = 1.f / (D.x * D.x + D.y * D.y);
+    return make_float2(D.x * inv, -D.y * inv);
+}
+
+// One thread per event: a warp takes tiles of 32 events.  Pass 1 over the
+// resonances forms A_s and Adot_s in registers; pass 2 recomputes each
+// resonance's terms and writes its 2 NP weighted parameter contributions to the
+// warp's transpose tile, whose columns (one per contribution, summed over the
+// 32 events by one lane each) go into the warp's FP64 accumulators.
 template <int S, bool PKS, bool HV>
 __global__ void __launch_bounds__(32 * kVarWarps) variant_kernel(const VarArgs a)
 {
     constexpr int NC = PKS ? S : 1;     // distinct couplings per resonance
-    constexpr int NP = 2 * NC + 3;      // parameter slots per lane: mags, phases, M, w1, w2
+    constexpr int NP = 2 * NC + 3;      // parameter slots per resonance: mags, phases, M, w1, w2
+    constexpr int NV = 2 * NP;          // gradient and H v contribution per slot
+    extern __shared__ __align__(16) unsigned char var_smem[];
+    VarRes* sres = reinterpret_cast<VarRes*>(var_smem);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* tile = reinterpret_cast<float*>(var_smem + ((32 * sizeof(VarRes) + 15) / 16) * 16) + warp * (NV * 33);
+    double* acc = reinterpret_cast<double*>(var_smem + ((32 * sizeof(VarRes) + 15) / 16) * 16 +
+                                            kVarWarps * (NV * 33 * sizeof(float))) + warp * (32 * NV);
+    const int K = a.K;
+    for (int i = threadIdx.x; i < K; i += blockDim.x) sres[i] = a.res[i];
+    for (int i = lane; i < 32 * NV; i += 32) acc[i] = 0.0;
+    __syncthreads();
+
     const int sample = blockIdx.x < a.blocks0 ? 0 : 1;
     const int blk = sample ? blockIdx.x - a.blocks0 : blockIdx.x;
     const int nblk = sample ? gridDim.x - a.blocks0 : a.blocks0;
     const int wg = blk * kVarWarps + warp, nw = nblk * kVarWarps;
     const long long n = a.n[sample];
     const long long ntiles = (n + kVarE - 1) / kVarE;
-    const bool active = lane < a.K;
     const float* m2p = a.m2[sample];
     const float2* Fp = a.F[sample];
     const float* wp = sample == 0 ? a.w : nullptr;
-
-    // this lane's resonance
-    VarRes r{};
-    if (active) r = a.res[lane];
-    const float* m2c = m2p + (long long)r.ch * n;
-
-    double G[NP], H[NP];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) G[j] = H[j] = 0.0;
-    double s0 = 0.0, s1 = 0.0;  // lane 0: sum w ln I (data) or sum I, sum Idot (MC)
+    double s0 = 0.0, s1 = 0.0;  // per thread: sum w ln I (data) or sum I, sum Idot (MC)
     int bad = 0;
 
     for (long long t = wg; t < ntiles; t += nw) {
-        float tg[NP], th[NP];
+        const long long e = t * kVarE + lane;
+        const bool live = e < n;
+        const long long ec = live ? e : n - 1;  // a dead lane repeats a valid event and contributes nothing
+        const float m2e0 = m2p[ec], m2e1 = m2p[n + ec], m2e2 = m2p[2 * n + ec];
+        const float2* Fe = Fp + ec * (long long)K * S;
+        // pass 1: coherent sums
+        float2 A[S], Ad[S];
 #pragma unroll
-        for (int j = 0; j < NP; ++j) tg[j] = th[j] = 0.f;
-        float t0 = 0.f, t1 = 0.f;
-        const long long e0 = t * kVarE;
-        const int ne = (int)min((long long)kVarE, n - e0);
-        for (int i = 0; i < ne; ++i) {
-            const long long e = e0 + i;
-            float2 F[S];
-            float m2v = 1.f;
-            if (active) {
-#pragma unroll
-                for (int s = 0; s < S; ++s) F[s] = Fp[(e * a.K + lane) * S + s];
-                m2v = m2c[e];
-            } else {
-#pragma unroll
-                for (int s = 0; s < S; ++s) F[s] = make_float2(0.f, 0.f);
-            }
-            // event factors of the line shape
-            float2 ra = make_float2(0.f, 0.f), rb = make_float2(0.f, 0.f);
-            if (r.kind == 1) {
-                const float q2 = (m2v - r.a_pp) * (m2v - r.a_pm) / (4.f * m2v);
-                const float q = sqrtf(fmaxf(q2, 0.f));
-                ra.x = q * barrier_sq(r.L, q2 * r.r2) * rsqrtf(m2v);
-            } else if (r.kind == 2) {
-                ra = rho_flatte(m2v, r.a_pp, r.a_pm);
-                rb = rho_flatte(m2v, r.b_pp, r.b_pm);
-            }
-            // D and BW = 1 / D
-            const float wr = r.A0 + r.A1 * ra.x + r.A2 * rb.x, wi = r.A1 * ra.y + r.A2 * rb.y;
-            const float2 D = make_float2(((r.M2hi - m2v) + r.M2lo) + wi, -wr);
-            const float inv = active ? 1.f / (D.x * D.x + D.y * D.y) : 0.f;
-            const float2 BW = make_float2(D.x * inv, -D.y * inv);
-            const float2 BW2 = cmul(BW, BW);
-            float2 BWv = make_float2(0.f, 0.f), Dv = make_float2(0.f, 0.f);
-            if (HV) {
-                Dv = lin_form(r.Dv, ra, rb);
-                BWv = cscale(cmul(BW2, Dv), -1.f);
-            }
-            // coherent sums and their directional derivatives, summed over the warp
-            float2 A[S], Ad[S];
+        for (int s = 0; s < S; ++s) A[s] = Ad[s] = make_float2(0.f, 0.f);
+        for (int k = 0; k < K; ++k) {
+            const VarRes& r = sres[k];
+            const float m2v = r.ch == 0 ? m2e0 : (r.ch == 1 ? m2e1 : m2e2);
+            float2 ra, rb;
+            shape_factors(r, m2v, ra, rb);
+            const float2 BW = breit_wigner_v(r, m2v, ra, rb);
+            float2 BWv = make_float2(0.f, 0.f);
+            if (HV) BWv = cscale(cmul(cmul(BW, BW), lin_form(r.Dv, ra, rb)), -1.f);
 #pragma unroll
             for (int s = 0; s < S; ++s) {
                 const int c = PKS ? s : 0;
-                const float2 cks = cmul(r.g[c], BW);
-                A[s] = cmul(cks, F[s]);
-                if (HV) Ad[s] = cmul(cadd(cmul(r.gd[c], BW), cmul(r.g[c], BWv)), F[s]);
+                const float2 F = Fe[k * S + s];
+                A[s] = cadd(A[s], cmul(cmul(r.g[c], BW), F));
+                if (HV) Ad[s] = cadd(Ad[s], cmul(cadd(cmul(r.gd[c], BW), cmul(r.g[c], BWv)), F));
             }
+        }
+        float I = 0.f, Id = 0.f;
 #pragma unroll
-            for (int o = 16; o; o >>= 1) {
-#pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    A[s].x += __shfl_xor_sync(0xffffffffu, A[s].x, o);
-                    A[s].y += __shfl_xor_sync(0xffffffffu, A[s].y, o);
-                    if (HV) {
-                        Ad[s].x += __shfl_xor_sync(0xffffffffu, Ad[s].x, o);
-                        Ad[s].y += __shfl_xor_sync(0xffffffffu, Ad[s].y, o);
-                    }
-                }
-            }
-            float I = 0.f, Id = 0.f;
-#pragma unroll
-            for (int s = 0; s < S; ++s) {
-                I += A[s].x * A[s].x + A[s].y * A[s].y;
-                if (HV) Id += 2.f * (A[s].x * Ad[s].x + A[s].y * Ad[s].y);
-            }
-            float wa = 1.f, wb = 0.f;
+        for (int s = 0; s < S; ++s) {
+            I += A[s].x * A[s].x + A[s].y * A[s].y;
+            if (HV) Id += 2.f * (A[s].x * Ad[s].x + A[s].y * Ad[s].y);
+        }
+        float wa = 0.f, wb = 0.f;
+        if (live) {
             if (sample == 0) {
                 const float we = wp ? wp[e] : 1.f;
                 if (!(I > 0.f) || !isfinite(I)) {
                     bad = 1;
-                    continue;
+                } else {
+                    wa = we / I;
+                    wb = HV ? we * Id / (I * I) : 0.f;
+                    s0 += (double)(we * logf(I));
                 }
-                wa = we / I;
-                wb = HV ? we * Id / (I * I) : 0.f;
-                if (lane == 0) t0 += we * logf(I);
+            } else if (!isfinite(I)) {
+                bad = 1;
             } else {
-                if (!isfinite(I)) {
-                    bad = 1;
-                    continue;
-                }
-                if (lane == 0) {
-                    t0 += I;
-                    t1 += Id;
-                }
+                wa = 1.f;
+                s0 += (double)I;
+                s1 += (double)Id;
             }
-            // D_s = conj(A_s) F_ks, Dd_s = conj(Adot_s) F_ks; E = sum_s D_s g_s and friends
+        }
+        // pass 2: parameter contributions, transposed through shared memory
+        for (int k = 0; k < K; ++k) {
+            const VarRes& r = sres[k];
+            const float m2v = r.ch == 0 ? m2e0 : (r.ch == 1 ? m2e1 : m2e2);
+            float2 ra, rb;
+            shape_factors(r, m2v, ra, rb);
+            const float2 BW = breit_wigner_v(r, m2v, ra, rb);
+            const float2 BW2 = cmul(BW, BW);
+            float2 Dv = make_float2(0.f, 0.f), BWv = Dv;
+            if (HV) {
+                Dv = lin_form(r.Dv, ra, rb);
+                BWv = cscale(cmul(BW2, Dv), -1.f);
+            }
             float2 Dk[S], Ddk[S];
 #pragma unroll
             for (int s = 0; s < S; ++s) {
-                Dk[s] = cmul(cconj(A[s]), F[s]);
-                if (HV) Ddk[s] = cmul(cconj(Ad[s]), F[s]);
+                const float2 F = Fe[k * S + s];
+                Dk[s] = cmul(cconj(A[s]), F);
+                Ddk[s] = HV ? cmul(cconj(Ad[s]), F) : make_float2(0.f, 0.f);
             }
-            // couplings
+            float val[NV];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                float2 Dc = Dk[c], Ddc = HV ? Ddk[c] : make_float2(0.f, 0.f);
+                float2 Dc = Dk[c], Ddc = Ddk[c];
                 if (!PKS) {
 #pragma unroll
                     for (int s = 1; s < S; ++s) {
                         Dc = cadd(Dc, Dk[s]);
-                        if (HV) Ddc = cadd(Ddc, Ddk[s]);
+                        Ddc = cadd(Ddc, Ddk[s]);
                     }
                 }
                 const float2 dmag = cmul(r.eph[c], BW), dph = cmul(ctimes_i(r.g[c]), BW);
                 const float gm = 2.f * re_mul(Dc, dmag), gp = 2.f * re_mul(Dc, dph);
-                tg[c] += wa * gm;
-                tg[NC + c] += wa * gp;
+                val[c] = wa * gm;
+                val[NC + c] = wa * gp;
                 if (HV) {
                     const float hm = 2.f * (re_mul(Ddc, dmag) +
                                             re_mul(Dc, cadd(cmul(r.gd_r[c], BW), cmul(r.eph[c], BWv))));
                     const float hp = 2.f * (re_mul(Ddc, dph) +
                                             re_mul(Dc, cadd(cmul(r.gd_p[c], BW), cmul(ctimes_i(r.g[c]), BWv))));
-                    th[c] += wa * hm - wb * gm;
-                    th[NC + c] += wa * hp - wb * gp;
+                    val[NP + c] = wa * hm - wb * gm;
+                    val[NP + NC + c] = wa * hp - wb * gp;
+                } else {
+                    val[NP + c] = val[NP + NC + c] = 0.f;
                 }
             }
-            // shape parameters M, w1, w2
             float2 E = make_float2(0.f, 0.f), Ed = E;
 #pragma unroll
             for (int s = 0; s < S; ++s) {
@@ -267,32 +284,41 @@ __global__ void __launch_bounds__(32 * kVarWarps) variant_kernel(const VarArgs a
                 const float2 dD = lin_form(r.dD[j], ra, rb);
                 const float2 dBW = cscale(cmul(BW2, dD), -1.f);
                 const float gj = 2.f * re_mul(E, dBW);
-                tg[2 * NC + j] += wa * gj;
+                val[2 * NC + j] = wa * gj;
                 if (HV) {
                     const float2 dBWv = cadd(cscale(cmul(BW3, cmul(dD, Dv)), 2.f),
                                              cscale(cmul(BW2, lin_form(r.ddv[j], ra, rb)), -1.f));
                     const float hj = 2.f * (re_mul(Ed, dBW) + re_mul(E, dBWv));
-                    th[2 * NC + j] += wa * hj - wb * gj;
+                    val[NP + 2 * NC + j] = wa * hj - wb * gj;
+                } else {
+                    val[NP + 2 * NC + j] = 0.f;
                 }
             }
-        }
+            // transpose: contribution j of event `lane` at tile[j][lane] (row stride 33: no bank conflicts)
 #pragma unroll
-        for (int j = 0; j < NP; ++j) {
-            G[j] += (double)tg[j];
-            H[j] += (double)th[j];
+            for (int j = 0; j < NV; ++j) tile[j * 33 + lane] = val[j];
+            __syncwarp();
+            if (lane < NV) {
+                float sum = 0.f;
+#pragma unroll 8
+                for (int q = 0; q < 32; ++q) sum += tile[lane * 33 + q];
+                acc[k * NV + lane] += (double)sum;
+            }
+            __syncwarp();
         }
-        s0 += (double)t0;
-        s1 += (double)t1;
     }
+    // scalars: sum over the warp's threads (FP64)
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    __syncwarp();
     double* rec = a.rec + ((long long)(sample ? a.blocks0 * kVarWarps : 0) + wg) * a.rec_len;
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-        rec[lane * 2 * NP + j] = G[j];
-        rec[lane * 2 * NP + NP + j] = H[j];
-    }
+    for (int i = lane; i < 32 * NV; i += 32) rec[i] = acc[i];
     if (lane == 0) {
-        rec[32 * 2 * NP] = s0;
-        rec[32 * 2 * NP + 1] = s1;
+        rec[32 * NV] = s0;
+        rec[32 * NV + 1] = s1;
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, 1);
 }
@@ -317,6 +343,16 @@ VarKernel pick_s(bool pks, bool hv)
 {
     if (pks) return hv ? variant_kernel<S, true, true> : variant_kernel<S, true, false>;
     return hv ? variant_kernel<S, false, true> : variant_kernel<S, false, false>;
+}
+
+size_t var_smem_for(int S, bool pks)
+{
+    switch (pks ? S : 1) {
+    case 1: return var_smem_bytes<5>();
+    case 2: return var_smem_bytes<7>();
+    case 3: return var_smem_bytes<9>();
+    default: return var_smem_bytes<11>();
+    }
 }
 
 VarKernel pick(int S, bool pks, bool hv)
@@ -635,12 +671,21 @@ pwa_status create_impl(pwa_variant* v, const pwa_events* data, const pwa_events*
     if (st != PWA_OK) return st;
     st = copy_sample(v, 1, mc, false);
     if (st != PWA_OK) return st;
-    // grid: about three blocks per SM, split between the samples by their tile counts
-    int dev = 0, sms = 148;
+    // grid: as many blocks as fit on the SMs (shared memory and registers of the
+    // H v instance), split between the samples by their tile counts
+    int dev = 0, sms = 148, per_sm = 2;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    {
+        VarKernel fh = pick(S, v->per_projection != 0, true);
+        const size_t smem = var_smem_for(S, v->per_projection != 0);
+        VAR_CUDA(v, cudaFuncSetAttribute(fh, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        VAR_CUDA(v, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fh, 32 * kVarWarps, smem));
+        per_sm = std::max(per_sm, 1);
+    }
     const long long t0 = (data->n + kVarE - 1) / kVarE, t1 = (mc->n + kVarE - 1) / kVarE;
-    const long long total = std::max(2LL, std::min((long long)3 * sms, (t0 + t1 + kVarWarps - 1) / kVarWarps));
+    const long long total =
+        std::max(2LL, std::min((long long)per_sm * sms, (t0 + kVarWarps - 1) / kVarWarps + (t1 + kVarWarps - 1) / kVarWarps));
     long long b0 = std::max(1LL, std::llround((double)total * t0 / (double)(t0 + t1)));
     b0 = std::min(b0, std::max(1LL, (t0 + kVarWarps - 1) / kVarWarps));
     long long b1 = std::max(1LL, std::min(total - b0, (t1 + kVarWarps - 1) / kVarWarps));
@@ -686,7 +731,9 @@ pwa_status variant_eval(pwa_variant* v, const double* theta, const double* dir, 
     a.err = v->d_err;
     VarKernel fn = pick(S, v->per_projection != 0, hv != nullptr);
     if (!fn) return vfail(v, PWA_EINVAL, "no variant kernel for this S");
-    fn<<<v->blocks0 + v->blocks1, 32 * kVarWarps, 0, st>>>(a);
+    const size_t smem = var_smem_for(S, v->per_projection != 0);
+    VAR_CUDA(v, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    fn<<<v->blocks0 + v->blocks1, 32 * kVarWarps, smem, st>>>(a);
     VAR_CUDA(v, cudaGetLastError());
     variant_reduce_kernel<<<(2 * v->rec_len + 255) / 256, 256, 0, st>>>(v->d_rec, v->rec_len, v->blocks0 * kVarWarps,
                                                                         v->blocks1 * kVarWarps, v->d_sums);
