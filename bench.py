@@ -339,7 +339,7 @@ def coupling_metric(L, wl, reps: int = 20):
 
 
 def learned_metric(n_train: int, n_eval: int, n_random: int, time_limit: float, pool: int = 10_000_000,
-                   n_events: int = 100_000, n_mc: int = 500_000, epochs: int = 40):
+                   n_events: int = 100_000, n_mc: int = 500_000, epochs: int = 60):
     """The learned starting-point proposal on the paper-scale model (K = 20,
     S = 4, 78 parameters): n_train pseudo-experiments (theta from the prior,
     up to n_events events accept-rejected from a pool of phase-space events,

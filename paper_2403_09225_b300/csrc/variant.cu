@@ -59,7 +59,7 @@ struct VarRes {
 
 struct VarArgs {
     const float* m2[2];     // [3][n]
-    const float2* F[2];     // [n][K][S]
+    const float2* F[2];     // tiles: [ceil(n / 32)][K S][32 events], zero past the last event
     const float* w;         // data weights or null
     long long n[2];
     int K;
@@ -140,17 +140,89 @@ __device__ __forceinline__ float2 breit_wigner_v(const VarRes& r, float m2v, flo
     return make_float2(D.x * inv, -D.y * inv);
 }
 
-// One thread per event: a warp takes tiles of 32 events.  Pass 1 over the
-// resonances forms A_s and Adot_s in registers; pass 2 recomputes each
-// resonance's terms and writes its 2 NP weighted parameter contributions to the
-// warp's transpose tile, whose columns (one per contribution, summed over the
-// 32 events by one lane each) go into the warp's FP64 accumulators.
+// Per-resonance terms of one event (pass 2): the 2 NP weighted contributions
+// (gradient, then H v) of resonance r's parameters, added to val.
+template <int S, bool PKS, bool HV>
+__device__ __forceinline__ void add_contributions(const VarRes& r, float m2v, const float2* __restrict__ Fk,
+                                                  const float2 (&A)[S], const float2 (&Ad)[S], float wa, float wb,
+                                                  float (&val)[2 * (2 * (PKS ? S : 1) + 3)])
+{
+    constexpr int NC = PKS ? S : 1;
+    constexpr int NP = 2 * NC + 3;
+    float2 ra, rb;
+    shape_factors(r, m2v, ra, rb);
+    const float2 BW = breit_wigner_v(r, m2v, ra, rb);
+    const float2 BW2 = cmul(BW, BW);
+    float2 Dv = make_float2(0.f, 0.f), BWv = Dv;
+    if (HV) {
+        Dv = lin_form(r.Dv, ra, rb);
+        BWv = cscale(cmul(BW2, Dv), -1.f);
+    }
+    float2 Dk[S], Ddk[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const float2 F = Fk[s * kVarE];
+        Dk[s] = cmul(cconj(A[s]), F);
+        Ddk[s] = HV ? cmul(cconj(Ad[s]), F) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        float2 Dc = Dk[c], Ddc = Ddk[c];
+        if (!PKS) {
+#pragma unroll
+            for (int s = 1; s < S; ++s) {
+                Dc = cadd(Dc, Dk[s]);
+                Ddc = cadd(Ddc, Ddk[s]);
+            }
+        }
+        const float2 dmag = cmul(r.eph[c], BW), dph = cmul(ctimes_i(r.g[c]), BW);
+        const float gm = 2.f * re_mul(Dc, dmag), gp = 2.f * re_mul(Dc, dph);
+        val[c] += wa * gm;
+        val[NC + c] += wa * gp;
+        if (HV) {
+            const float hm = 2.f * (re_mul(Ddc, dmag) + re_mul(Dc, cadd(cmul(r.gd_r[c], BW), cmul(r.eph[c], BWv))));
+            const float hp = 2.f * (re_mul(Ddc, dph) +
+                                    re_mul(Dc, cadd(cmul(r.gd_p[c], BW), cmul(ctimes_i(r.g[c]), BWv))));
+            val[NP + c] += wa * hm - wb * gm;
+            val[NP + NC + c] += wa * hp - wb * gp;
+        }
+    }
+    float2 E = make_float2(0.f, 0.f), Ed = E;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int c = PKS ? s : 0;
+        E = cadd(E, cmul(Dk[s], r.g[c]));
+        if (HV) Ed = cadd(Ed, cadd(cmul(Ddk[s], r.g[c]), cmul(Dk[s], r.gd[c])));
+    }
+    const float2 BW3 = cmul(BW2, BW);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float2 dD = lin_form(r.dD[j], ra, rb);
+        const float2 dBW = cscale(cmul(BW2, dD), -1.f);
+        const float gj = 2.f * re_mul(E, dBW);
+        val[2 * NC + j] += wa * gj;
+        if (HV) {
+            const float2 dBWv = cadd(cscale(cmul(BW3, cmul(dD, Dv)), 2.f),
+                                     cscale(cmul(BW2, lin_form(r.ddv[j], ra, rb)), -1.f));
+            const float hj = 2.f * (re_mul(Ed, dBW) + re_mul(E, dBWv));
+            val[NP + 2 * NC + j] += wa * hj - wb * gj;
+        }
+    }
+}
+
+// Two events per thread: a warp takes pairs of 32-event tiles (thread `lane`
+// has event lane of each).  Pass 1 over the resonances forms A_s and Adot_s of
+// both events in registers; pass 2 recomputes each resonance's terms and adds
+// both events' 2 NP weighted parameter contributions, which go through the
+// warp's transpose tile: one lane per contribution sums the 32 threads' values
+// into the warp's FP64 accumulators.
 template <int S, bool PKS, bool HV>
 __global__ void __launch_bounds__(32 * kVarWarps) variant_kernel(const VarArgs a)
 {
     constexpr int NC = PKS ? S : 1;     // distinct couplings per resonance
     constexpr int NP = 2 * NC + 3;      // parameter slots per resonance: mags, phases, M, w1, w2
     constexpr int NV = 2 * NP;          // gradient and H v contribution per slot
+    constexpr int EV = 2;               // events per thread
     extern __shared__ __align__(16) unsigned char var_smem[];
     VarRes* sres = reinterpret_cast<VarRes*>(var_smem);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -168,133 +240,104 @@ __global__ void __launch_bounds__(32 * kVarWarps) variant_kernel(const VarArgs a
     const int wg = blk * kVarWarps + warp, nw = nblk * kVarWarps;
     const long long n = a.n[sample];
     const long long ntiles = (n + kVarE - 1) / kVarE;
+    const long long npairs = (ntiles + EV - 1) / EV;
     const float* m2p = a.m2[sample];
     const float2* Fp = a.F[sample];
     const float* wp = sample == 0 ? a.w : nullptr;
     double s0 = 0.0, s1 = 0.0;  // per thread: sum w ln I (data) or sum I, sum Idot (MC)
+    float f0 = 0.f, f1 = 0.f;   // FP32 partial of the last (up to) 8 tile pairs
+    int nf = 0;
     int bad = 0;
 
-    for (long long t = wg; t < ntiles; t += nw) {
-        const long long e = t * kVarE + lane;
-        const bool live = e < n;
-        const long long ec = live ? e : n - 1;  // a dead lane repeats a valid event and contributes nothing
-        const float m2e0 = m2p[ec], m2e1 = m2p[n + ec], m2e2 = m2p[2 * n + ec];
-        const float2* Fe = Fp + ec * (long long)K * S;
-        // pass 1: coherent sums
-        float2 A[S], Ad[S];
+    for (long long tp = wg; tp < npairs; tp += nw) {
+        if (++nf == 8) {
+            s0 += (double)f0;
+            s1 += (double)f1;
+            f0 = f1 = 0.f;
+            nf = 0;
+        }
+        bool live[EV];
+        float m2e[EV][3];
+        const float2* Fe[EV];
 #pragma unroll
-        for (int s = 0; s < S; ++s) A[s] = Ad[s] = make_float2(0.f, 0.f);
+        for (int u = 0; u < EV; ++u) {
+            // a tile past the last one, or an event past the last one, repeats valid memory and contributes nothing
+            const long long t = min(tp * EV + u, ntiles - 1);
+            const long long e = (tp * EV + u) * kVarE + lane;
+            live[u] = e < n;
+            const long long ec = live[u] ? e : n - 1;
+            m2e[u][0] = m2p[ec];
+            m2e[u][1] = m2p[n + ec];
+            m2e[u][2] = m2p[2 * n + ec];
+            Fe[u] = Fp + t * (long long)K * S * kVarE + lane;  // entry (k, s) at Fe[(k S + s) 32]
+        }
+        // pass 1: coherent sums
+        float2 A[EV][S], Ad[EV][S];
+#pragma unroll
+        for (int u = 0; u < EV; ++u)
+#pragma unroll
+            for (int s = 0; s < S; ++s) A[u][s] = Ad[u][s] = make_float2(0.f, 0.f);
         for (int k = 0; k < K; ++k) {
             const VarRes& r = sres[k];
-            const float m2v = r.ch == 0 ? m2e0 : (r.ch == 1 ? m2e1 : m2e2);
-            float2 ra, rb;
-            shape_factors(r, m2v, ra, rb);
-            const float2 BW = breit_wigner_v(r, m2v, ra, rb);
-            float2 BWv = make_float2(0.f, 0.f);
-            if (HV) BWv = cscale(cmul(cmul(BW, BW), lin_form(r.Dv, ra, rb)), -1.f);
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                const int c = PKS ? s : 0;
-                const float2 F = Fe[k * S + s];
-                A[s] = cadd(A[s], cmul(cmul(r.g[c], BW), F));
-                if (HV) Ad[s] = cadd(Ad[s], cmul(cadd(cmul(r.gd[c], BW), cmul(r.g[c], BWv)), F));
+            for (int u = 0; u < EV; ++u) {
+                const float m2v = r.ch == 0 ? m2e[u][0] : (r.ch == 1 ? m2e[u][1] : m2e[u][2]);
+                float2 ra, rb;
+                shape_factors(r, m2v, ra, rb);
+                const float2 BW = breit_wigner_v(r, m2v, ra, rb);
+                float2 BWv = make_float2(0.f, 0.f);
+                if (HV) BWv = cscale(cmul(cmul(BW, BW), lin_form(r.Dv, ra, rb)), -1.f);
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    const int c = PKS ? s : 0;
+                    const float2 F = Fe[u][(k * S + s) * kVarE];
+                    A[u][s] = cadd(A[u][s], cmul(cmul(r.g[c], BW), F));
+                    if (HV) Ad[u][s] = cadd(Ad[u][s], cmul(cadd(cmul(r.gd[c], BW), cmul(r.g[c], BWv)), F));
+                }
             }
         }
-        float I = 0.f, Id = 0.f;
+        float wa[EV], wb[EV];
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-            I += A[s].x * A[s].x + A[s].y * A[s].y;
-            if (HV) Id += 2.f * (A[s].x * Ad[s].x + A[s].y * Ad[s].y);
-        }
-        float wa = 0.f, wb = 0.f;
-        if (live) {
-            if (sample == 0) {
-                const float we = wp ? wp[e] : 1.f;
-                if (!(I > 0.f) || !isfinite(I)) {
+        for (int u = 0; u < EV; ++u) {
+            float I = 0.f, Id = 0.f;
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                I += A[u][s].x * A[u][s].x + A[u][s].y * A[u][s].y;
+                if (HV) Id += 2.f * (A[u][s].x * Ad[u][s].x + A[u][s].y * Ad[u][s].y);
+            }
+            wa[u] = wb[u] = 0.f;
+            if (live[u]) {
+                const long long e = (tp * EV + u) * kVarE + lane;
+                if (sample == 0) {
+                    const float we = wp ? wp[e] : 1.f;
+                    if (!(I > 0.f) || !isfinite(I)) {
+                        bad = 1;
+                    } else {
+                        wa[u] = we / I;
+                        wb[u] = HV ? we * Id / (I * I) : 0.f;
+                        f0 += we * logf(I);
+                    }
+                } else if (!isfinite(I)) {
                     bad = 1;
                 } else {
-                    wa = we / I;
-                    wb = HV ? we * Id / (I * I) : 0.f;
-                    s0 += (double)(we * logf(I));
+                    wa[u] = 1.f;
+                    f0 += I;
+                    f1 += Id;
                 }
-            } else if (!isfinite(I)) {
-                bad = 1;
-            } else {
-                wa = 1.f;
-                s0 += (double)I;
-                s1 += (double)Id;
             }
         }
         // pass 2: parameter contributions, transposed through shared memory
         for (int k = 0; k < K; ++k) {
             const VarRes& r = sres[k];
-            const float m2v = r.ch == 0 ? m2e0 : (r.ch == 1 ? m2e1 : m2e2);
-            float2 ra, rb;
-            shape_factors(r, m2v, ra, rb);
-            const float2 BW = breit_wigner_v(r, m2v, ra, rb);
-            const float2 BW2 = cmul(BW, BW);
-            float2 Dv = make_float2(0.f, 0.f), BWv = Dv;
-            if (HV) {
-                Dv = lin_form(r.Dv, ra, rb);
-                BWv = cscale(cmul(BW2, Dv), -1.f);
-            }
-            float2 Dk[S], Ddk[S];
-#pragma unroll
-            for (int s = 0; s < S; ++s) {
-                const float2 F = Fe[k * S + s];
-                Dk[s] = cmul(cconj(A[s]), F);
-                Ddk[s] = HV ? cmul(cconj(Ad[s]), F) : make_float2(0.f, 0.f);
-            }
             float val[NV];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                float2 Dc = Dk[c], Ddc = Ddk[c];
-                if (!PKS) {
+            for (int j = 0; j < NV; ++j) val[j] = 0.f;
 #pragma unroll
-                    for (int s = 1; s < S; ++s) {
-                        Dc = cadd(Dc, Dk[s]);
-                        Ddc = cadd(Ddc, Ddk[s]);
-                    }
-                }
-                const float2 dmag = cmul(r.eph[c], BW), dph = cmul(ctimes_i(r.g[c]), BW);
-                const float gm = 2.f * re_mul(Dc, dmag), gp = 2.f * re_mul(Dc, dph);
-                val[c] = wa * gm;
-                val[NC + c] = wa * gp;
-                if (HV) {
-                    const float hm = 2.f * (re_mul(Ddc, dmag) +
-                                            re_mul(Dc, cadd(cmul(r.gd_r[c], BW), cmul(r.eph[c], BWv))));
-                    const float hp = 2.f * (re_mul(Ddc, dph) +
-                                            re_mul(Dc, cadd(cmul(r.gd_p[c], BW), cmul(ctimes_i(r.g[c]), BWv))));
-                    val[NP + c] = wa * hm - wb * gm;
-                    val[NP + NC + c] = wa * hp - wb * gp;
-                } else {
-                    val[NP + c] = val[NP + NC + c] = 0.f;
-                }
+            for (int u = 0; u < EV; ++u) {
+                const float m2v = r.ch == 0 ? m2e[u][0] : (r.ch == 1 ? m2e[u][1] : m2e[u][2]);
+                add_contributions<S, PKS, HV>(r, m2v, Fe[u] + k * S * kVarE, A[u], Ad[u], wa[u], wb[u], val);
             }
-            float2 E = make_float2(0.f, 0.f), Ed = E;
-#pragma unroll
-            for (int s = 0; s < S; ++s) {
-                const int c = PKS ? s : 0;
-                E = cadd(E, cmul(Dk[s], r.g[c]));
-                if (HV) Ed = cadd(Ed, cadd(cmul(Ddk[s], r.g[c]), cmul(Dk[s], r.gd[c])));
-            }
-            const float2 BW3 = cmul(BW2, BW);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const float2 dD = lin_form(r.dD[j], ra, rb);
-                const float2 dBW = cscale(cmul(BW2, dD), -1.f);
-                const float gj = 2.f * re_mul(E, dBW);
-                val[2 * NC + j] = wa * gj;
-                if (HV) {
-                    const float2 dBWv = cadd(cscale(cmul(BW3, cmul(dD, Dv)), 2.f),
-                                             cscale(cmul(BW2, lin_form(r.ddv[j], ra, rb)), -1.f));
-                    const float hj = 2.f * (re_mul(Ed, dBW) + re_mul(E, dBWv));
-                    val[NP + 2 * NC + j] = wa * hj - wb * gj;
-                } else {
-                    val[NP + 2 * NC + j] = 0.f;
-                }
-            }
-            // transpose: contribution j of event `lane` at tile[j][lane] (row stride 33: no bank conflicts)
+            // contribution j of this thread's events at tile[j][lane] (row stride 33: no bank conflicts)
 #pragma unroll
             for (int j = 0; j < NV; ++j) tile[j * 33 + lane] = val[j];
             __syncwarp();
@@ -308,6 +351,8 @@ __global__ void __launch_bounds__(32 * kVarWarps) variant_kernel(const VarArgs a
         }
     }
     // scalars: sum over the warp's threads (FP64)
+    s0 += (double)f0;
+    s1 += (double)f1;
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
         s0 += __shfl_xor_sync(0xffffffffu, s0, o);
@@ -321,6 +366,20 @@ __global__ void __launch_bounds__(32 * kVarWarps) variant_kernel(const VarArgs a
         rec[32 * NV + 1] = s1;
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, 1);
+}
+
+// F [n][KS] -> tiles [ceil(n / 32)][KS][32], zero past the last event
+__global__ void variant_tile_kernel(const float2* __restrict__ F, long long n, int KS, float2* __restrict__ out)
+{
+    const long long total = (n + kVarE - 1) / kVarE * kVarE * KS;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int l = (int)(i % kVarE);
+        const long long rest = i / kVarE;
+        const int q = (int)(rest % KS);
+        const long long t = rest / KS;
+        const long long e = t * kVarE + l;
+        out[i] = e < n ? F[e * KS + q] : make_float2(0.f, 0.f);
+    }
 }
 
 // out[sample][j] = sum over the sample's warps of rec[warp][j], in warp order
@@ -557,11 +616,28 @@ pwa_status copy_sample(pwa_variant* v, int s, const pwa_events* ev, bool is_data
     const int K = v->base.K, S = v->base.S;
     const long long n = ev->n;
     const size_t nF = (size_t)n * K * S;
+    const size_t nT = (size_t)((n + kVarE - 1) / kVarE) * kVarE * K * S;
     VAR_CUDA(v, cudaMalloc(&v->d_m2[s], sizeof(float) * 3 * (size_t)n));
-    VAR_CUDA(v, cudaMalloc(&v->d_F[s], sizeof(float2) * nF));
+    VAR_CUDA(v, cudaMalloc(&v->d_F[s], sizeof(float2) * nT));
     const cudaMemcpyKind kind = ev->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     VAR_CUDA(v, cudaMemcpyAsync(v->d_m2[s], ev->m2, sizeof(float) * 3 * (size_t)n, kind, v->base.stream));
-    VAR_CUDA(v, cudaMemcpyAsync(v->d_F[s], ev->F, sizeof(float2) * nF, kind, v->base.stream));
+    // F in the caller's [n][K][S] layout, then into event tiles (SoA within a tile)
+    const float2* src = reinterpret_cast<const float2*>(ev->F);
+    float2* raw = nullptr;
+    if (!ev->on_device) {
+        VAR_CUDA(v, cudaMalloc(&raw, sizeof(float2) * nF));
+        cudaError_t e = cudaMemcpyAsync(raw, ev->F, sizeof(float2) * nF, cudaMemcpyHostToDevice, v->base.stream);
+        if (e != cudaSuccess) {
+            cudaFree(raw);
+            return pwa::cuda_error(&v->base, e, "copy of F");
+        }
+        src = raw;
+    }
+    variant_tile_kernel<<<1184, 256, 0, v->base.stream>>>(src, n, K * S, v->d_F[s]);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(v->base.stream);
+    if (raw) cudaFree(raw);
+    if (e != cudaSuccess) return pwa::cuda_error(&v->base, e, "tiling of F");
     if (is_data && ev->w) {
         VAR_CUDA(v, cudaMalloc(&v->d_w, sizeof(float) * (size_t)n));
         VAR_CUDA(v, cudaMemcpyAsync(v->d_w, ev->w, sizeof(float) * (size_t)n, kind, v->base.stream));
@@ -683,7 +759,8 @@ pwa_status create_impl(pwa_variant* v, const pwa_events* data, const pwa_events*
         VAR_CUDA(v, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fh, 32 * kVarWarps, smem));
         per_sm = std::max(per_sm, 1);
     }
-    const long long t0 = (data->n + kVarE - 1) / kVarE, t1 = (mc->n + kVarE - 1) / kVarE;
+    // work units: pairs of 32-event tiles (one per warp step)
+    const long long t0 = (data->n + 2 * kVarE - 1) / (2 * kVarE), t1 = (mc->n + 2 * kVarE - 1) / (2 * kVarE);
     const long long total =
         std::max(2LL, std::min((long long)per_sm * sms, (t0 + kVarWarps - 1) / kVarWarps + (t1 + kVarWarps - 1) / kVarWarps));
     long long b0 = std::max(1LL, std::llround((double)total * t0 / (double)(t0 + t1)));

@@ -248,10 +248,11 @@ def make_experiments(gen: Generator, count: int, n_events: int, seed: int, group
 
 
 def train(ex: Experiments, table, hidden: int = 512, layers: int = 3, batch: int = 128, epochs: int = 20,
-          lr: float = 1e-3, seed: int = 1, log=None):
+          lr: float = 1e-3, lr_final: float = 1e-5, seed: int = 1, log=None):
     """Train a ProposalMLP on the experiments (rows in the stored order,
     mini-batches of `batch` consecutive rows visited in a seeded random order
-    each epoch).  Returns (net, codec, loss per epoch)."""
+    each epoch; the learning rate falls from lr to lr_final on a cosine).
+    Returns (net, codec, mean loss per epoch)."""
     torch = _torch()
     codec = Codec(table, ex.theta_fit)
     N = (ex.X.shape[0] // batch) * batch
@@ -261,12 +262,16 @@ def train(ex: Experiments, table, hidden: int = 512, layers: int = 3, batch: int
                               periodic=codec.periodic, loss_weight=weight)
     rng = np.random.default_rng(seed)
     nbatch = N // batch
+    steps = max(1, epochs * nbatch)
     hist = []
+    step = 0
     for ep in range(epochs):
         tot = 0.0
         for b in rng.permutation(nbatch):
             a = int(b) * batch
-            tot += net.train_step(ex.X[a:a + batch], T[a:a + batch], lr)
+            rate = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * step / steps))
+            tot += net.train_step(ex.X[a:a + batch], T[a:a + batch], rate)
+            step += 1
         hist.append(tot / nbatch)
         if log:
             log("epoch %d loss %.4f" % (ep, hist[-1]))
@@ -290,55 +295,78 @@ def propose(net, codec: Codec, X) -> np.ndarray:
     return codec.decode(np.concatenate(out))
 
 
+def perturbed_starts(codec: Codec, start: np.ndarray, count: int, rng, scale: float = 0.3) -> np.ndarray:
+    """The start itself and count - 1 draws around it: Gaussian steps of
+    `scale` in the network's standardised target space (radians for phases)."""
+    t = codec.encode(start[None])[0].astype(np.float64)
+    rows = [t] + [t + scale * rng.standard_normal(t.size) for _ in range(count - 1)]
+    return codec.decode(np.stack(rows))
+
+
 def evaluate(gen: Generator, net, codec: Codec, count: int, n_events: int, n_random: int, seed: int,
-             fit_opts: Optional[dict] = None, tol: float = 0.01):
-    """Held-out pseudo-experiments: fit from the network's start and, in one
-    batched call, from n_random prior starts.  The global minimum of an
-    experiment is the lowest NLL any of its fits reached; a fit reaches it when
-    its NLL is within `tol`.  Returns per-experiment records and a summary with
-    the GPU-seconds per global-minimum hit of each method."""
+             fit_opts: Optional[dict] = None, tol: float = 0.01, n_learned: int = 4):
+    """Held-out pseudo-experiments, three ways with the same fit options:
+    one fit from the network's start; one batched call from the network's
+    start and n_learned - 1 draws around it; one batched call from n_random
+    prior starts.  The global minimum of an experiment is the lowest NLL any
+    of its fits reached; a fit reaches it when its NLL is within `tol`.
+    Returns per-experiment records and the summary of summarize()."""
     opts = dict(xtol=1e-8, maxiter=0)
     opts.update(fit_opts or {})
-    ex = make_experiments(gen, count, n_events, seed, label_fit=False, keep_idx=True)
-    ex, idxs = ex
+    ex, idxs = make_experiments(gen, count, n_events, seed, label_fit=False, keep_idx=True)
     starts = propose(net, codec, ex.X)
     rng = W.rng_stream(seed + 1, W.STREAM_STARTS)
+    prng = np.random.default_rng(seed + 2)
     recs = []
     for i in range(count):
         L = gen.likelihood(idxs[i])
         rnd = np.stack([W.sample_start(rng, gen.table) for _ in range(n_random)])
         t0 = time.perf_counter()
-        th_m, info_m = L.fit(starts[i], **opts)
+        _, info_m = L.fit(starts[i], **opts)
         t_m = time.perf_counter() - t0
+        lb = perturbed_starts(codec, starts[i], n_learned, prng)
         t0 = time.perf_counter()
-        th_r, info_r, _ = L.fit_batch(rnd, **opts)
+        _, info_b, _ = L.fit_batch(lb, **opts)
+        t_b = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        _, info_r, _ = L.fit_batch(rnd, **opts)
         t_r = time.perf_counter() - t0
         f_true = L.nll(ex.theta_true[i])
         L.close()
         nll_r = np.array([d["nll"] for d in info_r])
-        best = min(info_m["nll"], float(np.min(nll_r)))
-        recs.append(dict(n_events=int(ex.n_events[i]), nll_mlp=info_m["nll"], nll_random=nll_r.tolist(),
-                         nll_true=f_true, best=best, t_mlp=t_m, t_random=t_r,
-                         mlp_hit=bool(info_m["nll"] <= best + tol), random_hits=int(np.sum(nll_r <= best + tol))))
-    return recs, summarize(recs, n_random)
+        nll_b = np.array([d["nll"] for d in info_b])
+        best = min(info_m["nll"], float(np.min(nll_b)), float(np.min(nll_r)))
+        recs.append(dict(n_events=int(ex.n_events[i]), nll_mlp=info_m["nll"], nll_learned_batch=nll_b.tolist(),
+                         nll_random=nll_r.tolist(), nll_true=f_true, best=best, t_mlp=t_m, t_learned_batch=t_b,
+                         t_random=t_r, mlp_hit=bool(info_m["nll"] <= best + tol),
+                         learned_batch_hit=bool(np.min(nll_b) <= best + tol),
+                         random_hits=int(np.sum(nll_r <= best + tol))))
+    return recs, summarize(recs, n_random, n_learned)
 
 
-def summarize(recs: Sequence[dict], n_random: int) -> dict:
+def summarize(recs: Sequence[dict], n_random: int, n_learned: int = 1) -> dict:
     """Expected GPU-seconds until an experiment's global minimum is found.
     Random multi-start runs batches of n_random prior starts until one hits:
     with p the pooled hit rate of a start and T the mean time of a batched
     call, E = T / (1 - (1 - p)^n_random).  Learned: the time of the fit from
-    the network's start, plus E when that fit misses (random multi-start
-    remains the fallback)."""
+    the network's start (or of the batched call from it and the draws around
+    it), plus E when that misses (random multi-start remains the fallback)."""
     t_rand = float(np.mean([r["t_random"] for r in recs]))
     hits = sum(r["random_hits"] for r in recs)
     p = hits / max(1, n_random * len(recs))
     q = 1.0 - (1.0 - p) ** n_random
     e_rand = t_rand / q if q > 0 else float("inf")
     learned = [r["t_mlp"] + (0.0 if r["mlp_hit"] else e_rand) for r in recs]
-    return dict(experiments=len(recs), random_starts=n_random,
-                mlp_hit_rate=float(np.mean([r["mlp_hit"] for r in recs])), random_hit_rate=p,
-                random_s_to_min=e_rand, learned_s_to_min=float(np.mean(learned)),
-                mean_t_mlp_fit=float(np.mean([r["t_mlp"] for r in recs])), mean_t_random_batch=t_rand,
-                mean_dnll_mlp=float(np.mean([r["nll_mlp"] - r["best"] for r in recs])),
-                mean_dnll_random=float(np.mean([np.mean(np.asarray(r["nll_random"]) - r["best"]) for r in recs])))
+    out = dict(experiments=len(recs), random_starts=n_random,
+               mlp_hit_rate=float(np.mean([r["mlp_hit"] for r in recs])), random_hit_rate=p,
+               random_s_to_min=e_rand, learned_s_to_min=float(np.mean(learned)),
+               mean_t_mlp_fit=float(np.mean([r["t_mlp"] for r in recs])), mean_t_random_batch=t_rand,
+               mean_dnll_mlp=float(np.mean([r["nll_mlp"] - r["best"] for r in recs])),
+               mean_dnll_random=float(np.mean([np.mean(np.asarray(r["nll_random"]) - r["best"]) for r in recs])))
+    if recs and "t_learned_batch" in recs[0]:
+        lb = [r["t_learned_batch"] + (0.0 if r["learned_batch_hit"] else e_rand) for r in recs]
+        out.update(learned_starts=n_learned,
+                   learned_batch_hit_rate=float(np.mean([r["learned_batch_hit"] for r in recs])),
+                   learned_batch_s_to_min=float(np.mean(lb)),
+                   mean_t_learned_batch=float(np.mean([r["t_learned_batch"] for r in recs])))
+    return out

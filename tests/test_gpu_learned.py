@@ -10,7 +10,11 @@ NLL of those 9 fits, and a fit reaches it within 0.01.  The test requires
 the network's start to reach the minimum more often than a random start, and
 the expected GPU-seconds to the minimum (network start, with random
 multi-start as the fallback when it misses) to be lower than random
-multi-start's own."""
+multi-start's own, alone and in the batched form (the network's start and
+three draws around it fitted in one lockstep call).  The batched form is at
+least as likely to reach the minimum as the single start whose draws it
+adds (its first row is that start; the lockstep path may end one such fit
+elsewhere, so one experiment of slack)."""
 import numpy as np
 import pytest
 
@@ -57,5 +61,8 @@ def test_learned_proposal_beats_random_starts():
     print(s)
     assert s["mlp_hit_rate"] > s["random_hit_rate"] + 0.1, s
     assert s["learned_s_to_min"] < s["random_s_to_min"], s
+    # the batched form (the network's start and three draws around it in one call)
+    assert s["learned_batch_hit_rate"] >= s["mlp_hit_rate"] - 1.0 / 24, s
+    assert s["learned_batch_s_to_min"] < s["random_s_to_min"], s
     net.close()
     gen.close()
