@@ -38,6 +38,12 @@ namespace {
 
 constexpr int kVarWarps = 4;  // warps per block
 constexpr int kVarE = 32;     // events per tile
+// Events per thread (a warp step takes kVarEV tiles).  Two were measured slower
+// than one on the paper-scale model (3.68 against 3.51 ms per pass with one
+// coupling per resonance, 5.82 against 4.54 with one per projection): the
+// registers they need cost more occupancy than the shared per-resonance work
+// saves.
+constexpr int kVarEV = 1;
 
 // A complex linear form of the event factors, X = al - i (e0 + e1 rho_a + e2 rho_b).
 struct Lin {
@@ -210,19 +216,19 @@ __device__ __forceinline__ void add_contributions(const VarRes& r, float m2v, co
     }
 }
 
-// Two events per thread: a warp takes pairs of 32-event tiles (thread `lane`
-// has event lane of each).  Pass 1 over the resonances forms A_s and Adot_s of
-// both events in registers; pass 2 recomputes each resonance's terms and adds
-// both events' 2 NP weighted parameter contributions, which go through the
-// warp's transpose tile: one lane per contribution sums the 32 threads' values
-// into the warp's FP64 accumulators.
+// kVarEV events per thread: a warp takes groups of kVarEV 32-event tiles
+// (thread `lane` has event lane of each).  Pass 1 over the resonances forms
+// A_s and Adot_s of its events in registers; pass 2 recomputes each
+// resonance's terms and adds the events' 2 NP weighted parameter
+// contributions, which go through the warp's transpose tile: one lane per
+// contribution sums the 32 threads' values into the warp's FP64 accumulators.
 template <int S, bool PKS, bool HV>
 __global__ void __launch_bounds__(32 * kVarWarps) variant_kernel(const VarArgs a)
 {
     constexpr int NC = PKS ? S : 1;     // distinct couplings per resonance
     constexpr int NP = 2 * NC + 3;      // parameter slots per resonance: mags, phases, M, w1, w2
     constexpr int NV = 2 * NP;          // gradient and H v contribution per slot
-    constexpr int EV = 2;               // events per thread
+    constexpr int EV = kVarEV;          // events per thread
     extern __shared__ __align__(16) unsigned char var_smem[];
     VarRes* sres = reinterpret_cast<VarRes*>(var_smem);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -240,17 +246,17 @@ __global__ void __launch_bounds__(32 * kVarWarps) variant_kernel(const VarArgs a
     const int wg = blk * kVarWarps + warp, nw = nblk * kVarWarps;
     const long long n = a.n[sample];
     const long long ntiles = (n + kVarE - 1) / kVarE;
-    const long long npairs = (ntiles + EV - 1) / EV;
+    const long long ngroups = (ntiles + EV - 1) / EV;
     const float* m2p = a.m2[sample];
     const float2* Fp = a.F[sample];
     const float* wp = sample == 0 ? a.w : nullptr;
     double s0 = 0.0, s1 = 0.0;  // per thread: sum w ln I (data) or sum I, sum Idot (MC)
-    float f0 = 0.f, f1 = 0.f;   // FP32 partial of the last (up to) 8 tile pairs
+    float f0 = 0.f, f1 = 0.f;   // FP32 partial of the last (up to) 16 / EV tile groups
     int nf = 0;
     int bad = 0;
 
-    for (long long tp = wg; tp < npairs; tp += nw) {
-        if (++nf == 8) {
+    for (long long tg = wg; tg < ngroups; tg += nw) {
+        if (++nf == 16 / EV) {
             s0 += (double)f0;
             s1 += (double)f1;
             f0 = f1 = 0.f;
@@ -262,8 +268,8 @@ __global__ void __launch_bounds__(32 * kVarWarps) variant_kernel(const VarArgs a
 #pragma unroll
         for (int u = 0; u < EV; ++u) {
             // a tile past the last one, or an event past the last one, repeats valid memory and contributes nothing
-            const long long t = min(tp * EV + u, ntiles - 1);
-            const long long e = (tp * EV + u) * kVarE + lane;
+            const long long t = min(tg * EV + u, ntiles - 1);
+            const long long e = (tg * EV + u) * kVarE + lane;
             live[u] = e < n;
             const long long ec = live[u] ? e : n - 1;
             m2e[u][0] = m2p[ec];
@@ -307,7 +313,7 @@ __global__ void __launch_bounds__(32 * kVarWarps) variant_kernel(const VarArgs a
             }
             wa[u] = wb[u] = 0.f;
             if (live[u]) {
-                const long long e = (tp * EV + u) * kVarE + lane;
+                const long long e = (tg * EV + u) * kVarE + lane;
                 if (sample == 0) {
                     const float we = wp ? wp[e] : 1.f;
                     if (!(I > 0.f) || !isfinite(I)) {
@@ -759,8 +765,9 @@ pwa_status create_impl(pwa_variant* v, const pwa_events* data, const pwa_events*
         VAR_CUDA(v, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fh, 32 * kVarWarps, smem));
         per_sm = std::max(per_sm, 1);
     }
-    // work units: pairs of 32-event tiles (one per warp step)
-    const long long t0 = (data->n + 2 * kVarE - 1) / (2 * kVarE), t1 = (mc->n + 2 * kVarE - 1) / (2 * kVarE);
+    // work units: groups of kVarEV 32-event tiles (one per warp step)
+    const long long ge = (long long)kVarEV * kVarE;
+    const long long t0 = (data->n + ge - 1) / ge, t1 = (mc->n + ge - 1) / ge;
     const long long total =
         std::max(2LL, std::min((long long)per_sm * sms, (t0 + kVarWarps - 1) / kVarWarps + (t1 + kVarWarps - 1) / kVarWarps));
     long long b0 = std::max(1LL, std::llround((double)total * t0 / (double)(t0 + t1)));
