@@ -41,6 +41,7 @@
 #include <vector>
 
 #include "pwa_internal.h"
+#include "tcgen05.cuh"
 
 namespace {
 
@@ -79,41 +80,14 @@ struct CpArgs {
 __host__ __device__ inline uint32_t part_bytes(int K2p) { return (uint32_t)kRows * K2p * 2; }
 __host__ __device__ inline uint32_t w_bytes(int Et) { return (uint32_t)((Et + 3) / 4) * 16; }
 
-__device__ __forceinline__ uint32_t sa(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
-
-// shared-memory matrix descriptor: start, LBO, SBO (bytes), no swizzle
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
-{
-    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 8 consecutive 32-bit columns of this thread's TMEM lane; the values are
-// valid after tmem_wait() (several loads may be in flight before one wait)
-__device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&r)[8])
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(addr));
-}
-__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+using pwa::tc::mma_bf16;
+using pwa::tc::mma_commit;
+using pwa::tc::sa;
+using pwa::tc::sdesc;
+using pwa::tc::tmem_ld8;
+using pwa::tc::tmem_wait;
+__device__ __forceinline__ void tc_fence_before() { pwa::tc::fence_before(); }
+__device__ __forceinline__ void tc_fence_after() { pwa::tc::fence_after(); }
 
 // x = x0 + x1 + x2 in BF16, each part the nearest BF16 of the remainder
 __host__ __device__ inline void split3(float x, __nv_bfloat16& b0, __nv_bfloat16& b1, __nv_bfloat16& b2)

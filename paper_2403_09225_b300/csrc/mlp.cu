@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "pwa_internal.h"
+#include "tcgen05.cuh"
 
 namespace {
 
@@ -31,13 +32,10 @@ namespace {
 constexpr int kGM = 128, kGN = 64, kGK = 64;  // tile; K chunk (four MMAs of K = 16)
 constexpr int kGThreads = 128;                // 4 warps: one per TMEM lane quarter
 
-__device__ __forceinline__ uint32_t sa(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
-
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
-{
-    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
-}
+using pwa::tc::mma_bf16;
+using pwa::tc::mma_commit;
+using pwa::tc::sa;
+using pwa::tc::sdesc;
 
 // C = A B^T: A [M][K], B [N][K] BF16 row-major with leading dimensions lda, ldb
 // (elements); C [M][N] FP32 with ldc.  M % 128 == 0, N % 64 == 0, K % 64 == 0,
@@ -150,15 +148,9 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_bf16_kernel(const __nv_bflo
 #pragma unroll
             for (int ks = 0; ks < kGK / 16; ++ks) {
                 const uint64_t ad = sdesc(dA + ks * 256, 128, 1024), bd = sdesc(dB + ks * 256, 128, 1024);
-                const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                        tm),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                mma_bf16(tm, ad, bd, idesc, (i > 0 || ks > 0) ? 1u : 0u);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             sa(&bar[st]))
-                         : "memory");
+            mma_commit(&bar[st]);
         }
     }
     // the last chunk's MMAs (and with them every earlier one) before the accumulator is read
