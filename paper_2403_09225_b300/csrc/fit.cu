@@ -602,10 +602,31 @@ struct RoundEvaluator {
     virtual pwa_status finish(int nb, const double** out, const int** err) = 0;  // waits
 };
 
-// a likelihood handle: pwa_eval_batch_device's pass on the handle's batch buffers
+// a likelihood handle: pwa_eval_batch_device's pass on the handle's batch buffers.
+// A round is a fixed sequence (upload theta and v from the pinned staging, the
+// batched pass, download of the results and error words); the third time a
+// (rows, mode) shape comes up it is captured into a CUDA graph and replayed
+// from then on.  A graph is dropped when the handle's buffers, tiling or
+// stream are no longer those it was captured with (the batch scratch grows
+// in the eager rounds that precede a capture).
 struct HandleRounds final : RoundEvaluator {
+    struct Captured {
+        cudaGraphExec_t exec = nullptr;
+        int uses = 0;
+        // what the graph's nodes point at
+        const void *d_io = nullptr, *h_io = nullptr, *rec = nullptr, *grec = nullptr, *cnt = nullptr;
+        cudaStream_t stream = nullptr;
+        int grid = 0, W = 0, kpw = 0;
+    };
     pwa_handle* h;
+    std::vector<Captured> cache;  // index 2 nb + any_hv
     explicit HandleRounds(pwa_handle* hh) : h(hh) {}
+    ~HandleRounds() override
+    {
+        for (auto& c : cache)
+            if (c.exec) cudaGraphExecDestroy(c.exec);
+        cudaGetLastError();
+    }
     int P() const override { return h->P; }
     pwa_handle* handle() const override { return h; }
     pwa_status reserve(int nb, double** theta, double** v) override
@@ -616,7 +637,8 @@ struct HandleRounds final : RoundEvaluator {
         *v = h->batch.h_io + (size_t)nb * h->P;
         return PWA_OK;
     }
-    pwa_status issue(int nb, bool any_hv) override
+    // the round's operations, enqueued on the handle's stream
+    pwa_status enqueue(int nb, bool any_hv)
     {
         pwa::BatchState& bs = h->batch;
         const size_t BP = (size_t)nb * h->P;
@@ -634,6 +656,66 @@ struct HandleRounds final : RoundEvaluator {
         if (e == cudaSuccess) e = cudaMemcpyAsync(errw, bs.d_err_vec, sizeof(int) * nb, cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(errw + nb, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
         if (e != cudaSuccess) return pwa::cuda_error(h, e, "batch download");
+        return PWA_OK;
+    }
+    bool same_state(const Captured& c) const
+    {
+        const pwa::BatchState& bs = h->batch;
+        return c.d_io == bs.d_io && c.h_io == bs.h_io && c.rec == bs.d_block_rec && c.grec == bs.d_group_rec &&
+               c.cnt == bs.d_counts && c.stream == h->stream && c.grid == h->tiling.grid && c.W == h->tiling.W &&
+               c.kpw == h->tiling.KPW;
+    }
+    pwa_status issue(int nb, bool any_hv) override
+    {
+        const size_t key = 2 * (size_t)nb + (any_hv ? 1 : 0);
+        if (cache.size() <= key) cache.resize(key + 1);
+        Captured& c = cache[key];
+        if (c.exec && !same_state(c)) {
+            cudaGraphExecDestroy(c.exec);
+            c = Captured();
+        }
+        if (c.exec) {
+            cudaError_t e = cudaGraphLaunch(c.exec, h->stream);
+            if (e != cudaSuccess) return pwa::cuda_error(h, e, "round graph launch");
+            return PWA_OK;
+        }
+        if (++c.uses < 3 || h->stream == nullptr) return enqueue(nb, any_hv);
+        // capture this round (the scratch for nb rows exists: earlier rounds of the shape grew it)
+        const pwa::BatchState& bs = h->batch;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return enqueue(nb, any_hv);
+        }
+        pwa_status st = enqueue(nb, any_hv);
+        e = cudaStreamEndCapture(h->stream, &g);
+        if (st != PWA_OK || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            h->err.clear();
+            c.uses = -1000000;  // this shape stays eager
+            return enqueue(nb, any_hv);
+        }
+        e = cudaGraphInstantiate(&c.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c.exec = nullptr;
+            c.uses = -1000000;
+            return enqueue(nb, any_hv);
+        }
+        c.d_io = bs.d_io;
+        c.h_io = bs.h_io;
+        c.rec = bs.d_block_rec;
+        c.grec = bs.d_group_rec;
+        c.cnt = bs.d_counts;
+        c.stream = h->stream;
+        c.grid = h->tiling.grid;
+        c.W = h->tiling.W;
+        c.kpw = h->tiling.KPW;
+        e = cudaGraphLaunch(c.exec, h->stream);
+        if (e != cudaSuccess) return pwa::cuda_error(h, e, "round graph launch");
         return PWA_OK;
     }
     pwa_status finish(int nb, const double** out, const int** err) override
