@@ -599,6 +599,8 @@ struct CpVec {  // per vector and resonance: rho, phi, Re g, Im g, Re gdot, Im g
     double v[8];
 };
 
+constexpr int kCombRows = 8;  // thread rows of the combine kernel (CTA records split between them)
+
 __global__ void coupling_combine_kernel(const double* __restrict__ rec, int nrec, int K, int K2p,
                                         const double* __restrict__ phi, const CpVec* __restrict__ vec,
                                         const pwa::ResParam* __restrict__ res, int Pc, double Nd, double Nmc,
@@ -606,26 +608,45 @@ __global__ void coupling_combine_kernel(const double* __restrict__ rec, int nrec
 {
     const int c = blockIdx.x;
     if (c >= nvec) return;
-    extern __shared__ double sh[];  // [K][8] partials, then 4 scalars
+    // blockDim (32, kCombRows): thread (k, y) adds the CTA records y, y + kCombRows, ...;
+    // the rows are then added in row order (fixed order, independent of the launch)
+    extern __shared__ double sh[];  // [K][8] partials, then 4 scalars, then [kCombRows][32][8] row sums, [kCombRows * 32] ln-terms
     const int reclen = kN1 * K2p + kCV;
     double* part = sh;
     double* scal = sh + 8 * K;
-    const int k = threadIdx.x;
+    double* rows = scal + 4;
+    double* lns = rows + kCombRows * 32 * 8;
+    const int k = threadIdx.x, y = threadIdx.y;
+    {
+        double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (k < K)
+            for (int b = y; b < nrec; b += kCombRows) {
+                const double* r = rec + (size_t)b * reclen;
+                q[0] += r[(size_t)c * K2p + k];
+                q[1] += r[(size_t)c * K2p + K + k];
+                q[2] += r[(size_t)(kCV + c) * K2p + k];
+                q[3] += r[(size_t)(kCV + c) * K2p + K + k];
+                q[4] += r[(size_t)(2 * kCV + c) * K2p + k];
+                q[5] += r[(size_t)(2 * kCV + c) * K2p + K + k];
+                q[6] += r[(size_t)(3 * kCV + c) * K2p + k];
+                q[7] += r[(size_t)(3 * kCV + c) * K2p + K + k];
+            }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) rows[(y * 32 + k) * 8 + i] = q[i];
+        // the data's sum w ln I of this vector, one record per thread
+        const int t = y * 32 + k;
+        double l = 0.0;
+        for (int b = t; b < nrec; b += 32 * kCombRows) l += rec[(size_t)b * reclen + (size_t)kN1 * K2p + c];
+        lns[t] = l;
+    }
+    __syncthreads();
+    if (y > 0) return;
     double2 Q1d = make_double2(0, 0), P1d = make_double2(0, 0), Pg = make_double2(0, 0), Pd = make_double2(0, 0);
     if (k < K) {
-        // data sums over the CTAs in fixed order
         double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int b = 0; b < nrec; ++b) {
-            const double* r = rec + (size_t)b * reclen;
-            q[0] += r[(size_t)c * K2p + k];
-            q[1] += r[(size_t)c * K2p + K + k];
-            q[2] += r[(size_t)(kCV + c) * K2p + k];
-            q[3] += r[(size_t)(kCV + c) * K2p + K + k];
-            q[4] += r[(size_t)(2 * kCV + c) * K2p + k];
-            q[5] += r[(size_t)(2 * kCV + c) * K2p + K + k];
-            q[6] += r[(size_t)(3 * kCV + c) * K2p + k];
-            q[7] += r[(size_t)(3 * kCV + c) * K2p + K + k];
-        }
+        for (int yy = 0; yy < kCombRows; ++yy)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) q[i] += rows[(yy * 32 + k) * 8 + i];
         // sum_r (a Ar + i ... ) U: Q1 = sum a conj(A) U, P1 = sum (a conj(Adot) - b conj(A)) U
         Q1d = make_double2(q[0] + q[3], q[1] - q[2]);
         P1d = make_double2(q[4] + q[7], q[5] - q[6]);
@@ -643,19 +664,19 @@ __global__ void coupling_combine_kernel(const double* __restrict__ rec, int nrec
         part[8 * k + 0] = gr * Pg.x + gi * Pg.y;        // Re conj(g_k) (Phi g)_k
         part[8 * k + 1] = 2.0 * (gr * Pd.x + gi * Pd.y);  // 2 Re conj(g_k) (Phi gdot)_k
     }
-    __syncthreads();
+    __syncwarp();
     if (threadIdx.x == 0) {
         double Gm = 0.0, Gd = 0.0, sln = 0.0;
         for (int kk = 0; kk < K; ++kk) {
             Gm += part[8 * kk + 0];
             Gd += part[8 * kk + 1];
         }
-        for (int b = 0; b < nrec; ++b) sln += rec[(size_t)b * reclen + (size_t)kN1 * K2p + c];
+        for (int t = 0; t < 32 * kCombRows; ++t) sln += lns[t];
         scal[0] = Gm;
         scal[1] = Gd;
         out[(size_t)c * (1 + 2 * Pc)] = -sln + Nd * log(Gm / Nmc);
     }
-    __syncthreads();
+    __syncwarp();
     if (k >= K) return;
     const double Gm = scal[0], Gd = scal[1];
     const CpVec v = vec[(size_t)c * K + k];
@@ -776,7 +797,8 @@ pwa_status cp_launch(pwa_coupling* cp, int nv, const double* theta_c, const doub
     coupling_kernel<<<cp->grid, kCT + 32, cp->smem, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cp_cuda(cp, e, "coupling kernel launch");
-    coupling_combine_kernel<<<nv, std::max(32, (K + 31) / 32 * 32), sizeof(double) * (8 * K + 4), s>>>(
+    coupling_combine_kernel<<<nv, dim3(32, kCombRows),
+                              sizeof(double) * (8 * K + 4 + kCombRows * 32 * 8 + kCombRows * 32), s>>>(
         cp->d_rec, cp->grid, K, cp->K2p, cp->d_phi, cp->d_vec, h->d_res, Pc, h->Nd, h->Nmc, nv, cp->d_out);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cp_cuda(cp, e, "coupling combine launch");

@@ -388,17 +388,28 @@ __global__ void variant_tile_kernel(const float2* __restrict__ F, long long n, i
     }
 }
 
-// out[sample][j] = sum over the sample's warps of rec[warp][j], in warp order
-__global__ void variant_reduce_kernel(const double* __restrict__ rec, int rec_len, int warps0, int warps1,
-                                      double* __restrict__ out)
+// out[sample][j] = sum over the sample's warps of rec[warp][j], in a fixed order:
+// block x takes 32 consecutive slots (threadIdx.x, coalesced reads), and
+// thread row y sums the warps y, y + 32, ...; the 32 row sums are then added
+// in row order.
+__global__ void __launch_bounds__(1024) variant_reduce_kernel(const double* __restrict__ rec, int rec_len, int warps0,
+                                                              int warps1, double* __restrict__ out)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= 2 * rec_len) return;
-    const int sample = j / rec_len, slot = j % rec_len;
+    __shared__ double part[32][33];
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    const bool ok = j < 2 * rec_len;
+    const int sample = ok ? j / rec_len : 0, slot = ok ? j % rec_len : 0;
     const int w0 = sample ? warps0 : 0, nw = sample ? warps1 : warps0;
     double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += rec[(long long)(w0 + w) * rec_len + slot];
-    out[j] = s;
+    if (ok)
+        for (int w = threadIdx.y; w < nw; w += 32) s += rec[(long long)(w0 + w) * rec_len + slot];
+    part[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && ok) {
+        double t = 0.0;
+        for (int y = 0; y < 32; ++y) t += part[y][threadIdx.x];
+        out[j] = t;
+    }
 }
 
 using VarKernel = void (*)(const VarArgs);
@@ -819,8 +830,8 @@ pwa_status variant_eval(pwa_variant* v, const double* theta, const double* dir, 
     VAR_CUDA(v, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     fn<<<v->blocks0 + v->blocks1, 32 * kVarWarps, smem, st>>>(a);
     VAR_CUDA(v, cudaGetLastError());
-    variant_reduce_kernel<<<(2 * v->rec_len + 255) / 256, 256, 0, st>>>(v->d_rec, v->rec_len, v->blocks0 * kVarWarps,
-                                                                        v->blocks1 * kVarWarps, v->d_sums);
+    variant_reduce_kernel<<<(2 * v->rec_len + 31) / 32, dim3(32, 32), 0, st>>>(
+        v->d_rec, v->rec_len, v->blocks0 * kVarWarps, v->blocks1 * kVarWarps, v->d_sums);
     VAR_CUDA(v, cudaGetLastError());
     VAR_CUDA(v, cudaMemcpyAsync(v->h_sums, v->d_sums, sizeof(double) * 2 * v->rec_len, cudaMemcpyDeviceToHost, st));
     VAR_CUDA(v, cudaMemcpyAsync(v->h_sums + 2 * v->rec_len, v->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
