@@ -60,7 +60,8 @@ struct VarRes {
     Lin dD[3];               // dD / d(M, w1, w2)
     Lin Dv;                  // sum_j dD_j v_j
     Lin ddv[3];              // sum_i d2D / d theta_j d theta_i v_i
-    float2 g[4], eph[4], gd[4], gd_r[4], gd_p[4];  // per projection: g, e^{i phi}, gdot, d gdot/d rho, d gdot/d phi
+    float2 g[4], eph[4], gd[4];      // per projection: g = rho e^{i phi}, e^{i phi}, gdot = v_rho e + v_phi i g
+    float rho[4], vrho[4], vphi[4];  // per projection: rho and the direction's components
 };
 
 struct VarArgs {
@@ -80,7 +81,6 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
-__device__ __forceinline__ float2 ctimes_i(float2 a) { return make_float2(-a.y, a.x); }
 // Re(a b)
 __device__ __forceinline__ float re_mul(float2 a, float2 b) { return a.x * b.x - a.y * b.y; }
 
@@ -171,6 +171,11 @@ __device__ __forceinline__ void add_contributions(const VarRes& r, float m2v, co
         Dk[s] = cmul(cconj(A[s]), F);
         Ddk[s] = HV ? cmul(cconj(Ad[s]), F) : make_float2(0.f, 0.f);
     }
+    // couplings: with dmag = dc/d rho = e^{i phi} BW, dc/d phi = i rho dmag, and
+    // z1 = Ddot dmag, z2 = D dmag, z3 = D e^{i phi} BWv:
+    //   g_rho = 2 Re z2,                      g_phi = -2 rho Im z2,
+    //   h_rho = 2 (Re z1 - v_phi Im z2 + Re z3),
+    //   h_phi = -2 (rho Im z1 + v_rho Im z2 + v_phi rho Re z2 + rho Im z3)
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         float2 Dc = Dk[c], Ddc = Ddk[c];
@@ -181,14 +186,16 @@ __device__ __forceinline__ void add_contributions(const VarRes& r, float m2v, co
                 Ddc = cadd(Ddc, Ddk[s]);
             }
         }
-        const float2 dmag = cmul(r.eph[c], BW), dph = cmul(ctimes_i(r.g[c]), BW);
-        const float gm = 2.f * re_mul(Dc, dmag), gp = 2.f * re_mul(Dc, dph);
+        const float2 dmag = cmul(r.eph[c], BW);
+        const float2 z2 = cmul(Dc, dmag);
+        const float rho = r.rho[c];
+        const float gm = 2.f * z2.x, gp = -2.f * rho * z2.y;
         val[c] += wa * gm;
         val[NC + c] += wa * gp;
         if (HV) {
-            const float hm = 2.f * (re_mul(Ddc, dmag) + re_mul(Dc, cadd(cmul(r.gd_r[c], BW), cmul(r.eph[c], BWv))));
-            const float hp = 2.f * (re_mul(Ddc, dph) +
-                                    re_mul(Dc, cadd(cmul(r.gd_p[c], BW), cmul(ctimes_i(r.g[c]), BWv))));
+            const float2 z1 = cmul(Ddc, dmag), z3 = cmul(Dc, cmul(r.eph[c], BWv));
+            const float hm = 2.f * (z1.x - r.vphi[c] * z2.y + z3.x);
+            const float hp = -2.f * (rho * (z1.y + z3.y) + r.vrho[c] * z2.y + r.vphi[c] * rho * z2.x);
             val[NP + c] += wa * hm - wb * gm;
             val[NP + NC + c] += wa * hp - wb * gp;
         }
@@ -203,6 +210,9 @@ __device__ __forceinline__ void add_contributions(const VarRes& r, float m2v, co
     const float2 BW3 = cmul(BW2, BW);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
+        // the second width parameter exists for Flatte shapes only (the branch is the
+        // same for the whole warp: its threads all work on resonance r)
+        if (j == 2 && r.kind != 2) break;
         const float2 dD = lin_form(r.dD[j], ra, rb);
         const float2 dBW = cscale(cmul(BW2, dD), -1.f);
         const float gj = 2.f * re_mul(E, dBW);
@@ -616,13 +626,12 @@ pwa_status fill_res(pwa_variant* vv, const double* theta, const double* dir)
             const double er = std::cos(phi), ei = std::sin(phi);
             const double gr_ = rho * er, gi_ = rho * ei;                        // g = rho e^{i phi}
             const double gdr = vr * er - vp * gi_, gdi = vr * ei + vp * gr_;    // gdot = vr e + vp i g
-            const double grr = -vp * ei, gri = vp * er;                         // d gdot / d rho = vp i e
-            const double gpr = -vr * ei - vp * gr_, gpi = vr * er - vp * gi_;   // d gdot / d phi = vr i e - vp g
             r.g[s] = make_float2((float)gr_, (float)gi_);
             r.eph[s] = make_float2((float)er, (float)ei);
             r.gd[s] = make_float2((float)gdr, (float)gdi);
-            r.gd_r[s] = make_float2((float)grr, (float)gri);
-            r.gd_p[s] = make_float2((float)gpr, (float)gpi);
+            r.rho[s] = (float)rho;
+            r.vrho[s] = (float)vr;
+            r.vphi[s] = (float)vp;
         }
     }
     return PWA_OK;
