@@ -207,20 +207,22 @@ __device__ __forceinline__ void add_contributions(const VarRes& r, float m2v, co
         E = cadd(E, cmul(Dk[s], r.g[c]));
         if (HV) Ed = cadd(Ed, cadd(cmul(Ddk[s], r.g[c]), cmul(Dk[s], r.gd[c])));
     }
-    const float2 BW3 = cmul(BW2, BW);
+    // shape parameters: dBW_j = -BW^2 dD_j and d(BWv)/d theta_j = 2 BW^3 Dv dD_j - BW^2 ddv_j, so with
+    // W = E BW^2, X = Edot BW^2 (Edot = sum_s Ddot_s g_s + D_s gdot_s) and Y = 2 W BW Dv:
+    //   g_j = -2 Re(W dD_j),   h_j = 2 Re((Y - X) dD_j - W ddv_j)
+    const float2 Wm = cmul(E, BW2);
+    float2 YX = make_float2(0.f, 0.f);
+    if (HV) YX = cadd(cscale(cmul(cmul(Wm, BW), Dv), 2.f), cscale(cmul(Ed, BW2), -1.f));
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         // the second width parameter exists for Flatte shapes only (the branch is the
         // same for the whole warp: its threads all work on resonance r)
         if (j == 2 && r.kind != 2) break;
         const float2 dD = lin_form(r.dD[j], ra, rb);
-        const float2 dBW = cscale(cmul(BW2, dD), -1.f);
-        const float gj = 2.f * re_mul(E, dBW);
+        const float gj = -2.f * re_mul(Wm, dD);
         val[2 * NC + j] += wa * gj;
         if (HV) {
-            const float2 dBWv = cadd(cscale(cmul(BW3, cmul(dD, Dv)), 2.f),
-                                     cscale(cmul(BW2, lin_form(r.ddv[j], ra, rb)), -1.f));
-            const float hj = 2.f * (re_mul(Ed, dBW) + re_mul(E, dBWv));
+            const float hj = 2.f * (re_mul(YX, dD) - re_mul(Wm, lin_form(r.ddv[j], ra, rb)));
             val[NP + 2 * NC + j] += wa * hj - wb * gj;
         }
     }
