@@ -330,3 +330,22 @@ def nll_grad_hvp(model: VariantModel, theta, v, data, mc):
 
 def intensity(model: VariantModel, theta, m2, F) -> np.ndarray:
     return np.real(intensity_hd(model, _params(model, theta), m2, F).a)
+
+
+def integral_matrices(model: VariantModel, theta, m2, F) -> np.ndarray:
+    """Phi [S][K][K] complex: Phi_s,kk' = sum over the sample of
+    conj(U_ks) U_k's with U_ks = BW_k F_ks at the line-shape parameters of
+    theta (Eq. 1 written as sum_s g_s^H Phi_s g_s over the events)."""
+    pars = _params(model, theta)
+    _, _, mass, w1, w2 = pars
+    K, S = model.K, model.S
+    U = np.empty((F.shape[0], K, S), dtype=np.complex128)
+    for k in range(K):
+        bw = breit_wigner(model, k, np.asarray(m2[model.channels[k]], dtype=np.float64), mass[k], w1[k], w2[k]).a
+        U[:, k, :] = bw[:, None] * np.asarray(F[:, k, :], dtype=np.complex128)
+    return np.einsum("eks,ejs->skj", np.conj(U), U)
+
+
+def coupling_count(model: VariantModel) -> int:
+    """Number of coupling parameters (magnitudes and phases) at the head of theta."""
+    return sum(1 for name, _, _ in model.layout() if name in ("mag", "phase"))

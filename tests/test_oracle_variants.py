@@ -142,3 +142,26 @@ def test_each_projection_has_its_own_phase_invariance():
     assert abs(V.nll(vm, th + 0.7 * d, data, mc) - f0) <= 1e-12 * abs(f0)
     _, g, _ = V.nll_grad_hvp(vm, th, np.zeros(vm.P), data, mc)
     assert abs(g @ d) <= 1e-9 * np.max(np.abs(g))
+
+
+@pytest.mark.parametrize("per_projection", [False, True])
+def test_integral_matrices_give_the_mc_sum(per_projection):
+    """sum_e I(e) = sum_s g_s^H Phi_s g_s for any couplings (the MC term of
+    Eq. 3 from the integral matrices), and each Phi_s is Hermitian."""
+    cfg, table, data, mc = tiny_samples()
+    vm = variant_model(table, cfg.S, per_projection)
+    rng = np.random.default_rng(9)
+    th = vm.theta0() * (1 + 0.05 * rng.standard_normal(vm.P))
+    phi = V.integral_matrices(vm, th, mc.m2, mc.F)
+    for s in range(cfg.S):
+        assert np.allclose(phi[s], np.conj(phi[s].T), rtol=0, atol=1e-9 * np.abs(phi[s]).max())
+    pars = V._params(vm, th)
+    mag, phase = pars[0], pars[1]
+    G = 0.0
+    for s in range(cfg.S):
+        j = s if per_projection else 0
+        g = np.array([mag[k][j].a * np.exp(1j * phase[k][j].a) for k in range(vm.K)])
+        G += float(np.real(np.conj(g) @ phi[s] @ g))
+    I = V.intensity(vm, th, mc.m2, mc.F)
+    assert abs(G - I.sum()) <= 1e-10 * I.sum()
+    assert V.coupling_count(vm) == (4 * cfg.S if per_projection else 4)
