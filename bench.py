@@ -452,10 +452,31 @@ def variant_metric(wl, reps: int = 10):
             ms = e0.elapsed_time(e1) / reps
             bpp = bytes_per_pass(nd, nm, K, S)
             achieved = bpp / (ms * 1e-3) / 1e9
-            out["per_projection" if pp else "per_resonance"] = {
-                "P": Lv.P, "ms_per_pass": ms, "event_amps_per_s": (nd + nm) * K / (ms * 1e-3),
-                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "peak_kind": kind, "algorithmic_bytes_per_launch": bpp}}
+            rec = {"P": Lv.P, "ms_per_pass": ms, "event_amps_per_s": (nd + nm) * K / (ms * 1e-3),
+                   "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                "frac": achieved / peak, "peak_kind": kind, "algorithmic_bytes_per_launch": bpp}}
+            if pp:
+                # couplings only at fixed line shapes: the MC integral matrices once, then
+                # one pass over the data events per call
+                t0 = time.perf_counter()
+                Lv.set_shapes(th)
+                torch.cuda.synchronize()
+                setup_s = time.perf_counter() - t0
+                Pc = Lv.Pc
+                vc = v[:Pc]
+                for _ in range(3):
+                    Lv.coupling_eval(th[:Pc], vc)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(reps):
+                    Lv.coupling_eval(th[:Pc], vc)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                cms = e0.elapsed_time(e1) / reps
+                rec["couplings_only"] = {"Pc": Pc, "set_shapes_s": setup_s, "ms_per_call": cms,
+                                         "speedup_vs_full_pass": ms / cms,
+                                         "data_bytes_per_call": nd * (8 * K * S + 16)}
+            out["per_projection" if pp else "per_resonance"] = rec
         finally:
             Lv.close()
     return out

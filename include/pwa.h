@@ -354,6 +354,28 @@ pwa_status pwa_variant_eval(pwa_variant* v, const double* theta, const double* d
 pwa_status pwa_variant_fit(pwa_variant* v, int B, const double* theta0, const pwa_fit_opts* opts,
                            double* theta_out, pwa_fit_result* results);
 
+/* Coupling-only evaluation at fixed line shapes (the K S x K S integral
+ * matrix of per-projection couplings, block-diagonal in s): computes, at the
+ * masses and widths of theta (host [P]), Phi_s,kk' = sum_mc conj(U_ks) U_k's
+ * with U_ks = BW_k F_ks, so that sum_mc I = sum_s g_s^H Phi_s g_s and the MC
+ * events are not read again by the coupling-only calls below.  phi_out
+ * (host [S][K][K] complex as (re, im) pairs, or NULL) receives the matrices.
+ * Errors: PWA_EINVAL, PWA_ENONFINITE, PWA_ECUDA. */
+pwa_status pwa_variant_set_shapes(pwa_variant* v, const double* theta, double* phi_out);
+
+/* Number of coupling parameters: the free magnitudes and phases at the head of theta. */
+int pwa_variant_coupling_num_params(const pwa_variant* v);
+
+/* NLL, gradient and H v in the coupling parameters theta_c [Pc] (line shapes
+ * as given to pwa_variant_set_shapes, which must come first): one pass over
+ * the data events plus the integral matrices.  Errors as pwa_variant_eval. */
+pwa_status pwa_variant_coupling_eval(pwa_variant* v, const double* theta_c, const double* dir_c,
+                                     double* nll, double* grad, double* hv);
+
+/* B coupling-only Newton-CG fits in lockstep (rows of theta_c0 [B][Pc]). */
+pwa_status pwa_variant_coupling_fit(pwa_variant* v, int B, const double* theta_c0, const pwa_fit_opts* opts,
+                                    double* theta_c_out, pwa_fit_result* results);
+
 /* Message of the last failure of v (of the last pwa_variant_create when v is NULL). */
 const char* pwa_variant_last_error(const pwa_variant* v);
 

@@ -67,7 +67,8 @@ EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "
            "pwa_mlp_gradients", "pwa_mlp_train_step", "pwa_mlp_params", "pwa_mlp_gemm_check",
            "pwa_mlp_last_error", "pwa_mlp_destroy", "pwa_accept_reject", "pwa_dalitz_histogram",
            "pwa_gather_events", "pwa_last_generate_error", "pwa_variant_create", "pwa_variant_num_params",
-           "pwa_variant_eval", "pwa_variant_fit", "pwa_variant_last_error", "pwa_variant_destroy")
+           "pwa_variant_eval", "pwa_variant_fit", "pwa_variant_set_shapes", "pwa_variant_coupling_num_params",
+           "pwa_variant_coupling_eval", "pwa_variant_coupling_fit", "pwa_variant_last_error", "pwa_variant_destroy")
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -132,6 +133,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pwa_variant_num_params": (i, [vp]),
         "pwa_variant_eval": (st, [vp, dp, dp, dp, dp, dp]),
         "pwa_variant_fit": (st, [vp, i, dp, ctypes.POINTER(pwa_fit_opts), dp, ctypes.POINTER(pwa_fit_result)]),
+        "pwa_variant_set_shapes": (st, [vp, dp, dp]),
+        "pwa_variant_coupling_num_params": (i, [vp]),
+        "pwa_variant_coupling_eval": (st, [vp, dp, dp, dp, dp, dp]),
+        "pwa_variant_coupling_fit": (st, [vp, i, dp, ctypes.POINTER(pwa_fit_opts), dp, ctypes.POINTER(pwa_fit_result)]),
         "pwa_variant_last_error": (ctypes.c_char_p, [vp]),
         "pwa_variant_destroy": (None, [vp]),
     }
@@ -540,6 +545,47 @@ class Variant:
         opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s)
         res = (pwa_fit_result * B)()
         st = lib().pwa_variant_fit(self._h, B, _dptr(th), ctypes.byref(opts), _dptr(out), res)
+        if st not in (PWA_OK, PWA_ENOCONV):
+            self._check(st)
+        infos = [{"nll": r.nll, "grad_max": r.grad_max, "iters": r.iters, "n_hvp": r.n_hvp, "n_fev": r.n_fev,
+                  "status": FIT_STATUS_NAMES[r.status], "elapsed_s": r.elapsed_s} for r in res]
+        return out, infos, st == PWA_OK
+
+    # -- couplings only, at fixed line shapes (integral matrices of the MC events) --
+    def set_shapes(self, theta) -> np.ndarray:
+        """Fix the line shapes at theta's masses and widths; returns the MC
+        integral matrices Phi [S, K, K] (complex)."""
+        th = _f64(theta, self.P)
+        out = np.empty(2 * self.S * self.K * self.K)
+        self._check(lib().pwa_variant_set_shapes(self._h, _dptr(th), _dptr(out)))
+        self.Pc = lib().pwa_variant_coupling_num_params(self._h)
+        return (out[0::2] + 1j * out[1::2]).reshape(self.S, self.K, self.K)
+
+    def coupling_eval(self, theta_c, v=None):
+        """(NLL, grad [Pc], H v [Pc] or None) in the coupling parameters."""
+        Pc = lib().pwa_variant_coupling_num_params(self._h)
+        th = _f64(theta_c, Pc)
+        f = ctypes.c_double()
+        g = np.empty(Pc)
+        if v is None:
+            self._check(lib().pwa_variant_coupling_eval(self._h, _dptr(th), None, ctypes.byref(f), _dptr(g), None))
+            return f.value, g, None
+        vv = _f64(v, Pc)
+        hv = np.empty(Pc)
+        self._check(lib().pwa_variant_coupling_eval(self._h, _dptr(th), _dptr(vv), ctypes.byref(f), _dptr(g),
+                                                    _dptr(hv)))
+        return f.value, g, hv
+
+    def coupling_fit(self, thetas_c0, xtol: float = 1e-8, gtol: float = 0.0, maxiter: int = 0, cg_maxiter: int = 0,
+                     time_limit_s: float = 0.0):
+        """B coupling-only fits in lockstep; returns (theta_c [B, Pc], infos, all converged)."""
+        Pc = lib().pwa_variant_coupling_num_params(self._h)
+        th = _f64(thetas_c0).reshape(-1, Pc)
+        B = th.shape[0]
+        out = np.empty((B, Pc))
+        opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s)
+        res = (pwa_fit_result * B)()
+        st = lib().pwa_variant_coupling_fit(self._h, B, _dptr(th), ctypes.byref(opts), _dptr(out), res)
         if st not in (PWA_OK, PWA_ENOCONV):
             self._check(st)
         infos = [{"nll": r.nll, "grad_max": r.grad_max, "iters": r.iters, "n_hvp": r.n_hvp, "n_fev": r.n_fev,

@@ -779,7 +779,11 @@ struct VariantRounds final : RoundEvaluator {
     int Pv;
     std::vector<double> th, vv, res;
     std::vector<int> errw;
-    VariantRounds(pwa_variant* vr, int p) : v(vr), h(pwa::variant_base(vr)), Pv(p) {}
+    bool couplings_only;
+    VariantRounds(pwa_variant* vr, int p, bool conly = false)
+        : v(vr), h(pwa::variant_base(vr)), Pv(p), couplings_only(conly)
+    {
+    }
     int P() const override { return Pv; }
     pwa_handle* handle() const override { return h; }
     pwa_status reserve(int nb, double** theta, double** dir) override
@@ -797,8 +801,11 @@ struct VariantRounds final : RoundEvaluator {
         errw.assign(nb, 0);
         for (int b = 0; b < nb; ++b) {
             double* r = res.data() + b * ow;
-            pwa_status st = pwa::variant_eval(v, th.data() + (size_t)b * Pv, any_hv ? vv.data() + (size_t)b * Pv : nullptr,
-                                              r, r + 1, any_hv ? r + 1 + Pv : nullptr);
+            const double* tb = th.data() + (size_t)b * Pv;
+            const double* vb = any_hv ? vv.data() + (size_t)b * Pv : nullptr;
+            pwa_status st = couplings_only
+                                ? pwa::variant_coupling_eval(v, tb, vb, r, r + 1, any_hv ? r + 1 + Pv : nullptr)
+                                : pwa::variant_eval(v, tb, vb, r, r + 1, any_hv ? r + 1 + Pv : nullptr);
             if (st == PWA_ENONFINITE || st == PWA_EINVAL) {
                 // a point outside the model's domain (non-finite intensity, a mass below its threshold):
                 // the fit sees an error for this row and backs off
@@ -1043,6 +1050,26 @@ extern "C" pwa_status pwa_variant_fit(pwa_variant* v, int B, const double* theta
     if (st != PWA_OK) return st;
     bool all_ok = true;
     st = close_group(*groups[0], theta_out, results, all_ok);
+    if (st != PWA_OK) return st;
+    return all_ok ? PWA_OK : PWA_ENOCONV;
+}
+
+extern "C" pwa_status pwa_variant_coupling_fit(pwa_variant* v, int B, const double* theta_c0,
+                                               const pwa_fit_opts* opts, double* theta_c_out, pwa_fit_result* results)
+{
+    if (!v) return PWA_EINVAL;
+    pwa_handle* h = pwa::variant_base(v);
+    if (!theta_c_out) return pwa::set_error(h, PWA_EINVAL, "theta_c_out must not be NULL");
+    std::vector<std::unique_ptr<FitGroup>> groups;
+    groups.push_back(std::make_unique<FitGroup>());
+    pwa_status st = open_group(*groups.back(),
+                               std::make_unique<VariantRounds>(v, pwa_variant_coupling_num_params(v), true), B,
+                               theta_c0, opts);
+    if (st != PWA_OK) return st;
+    st = run_lockstep(groups);
+    if (st != PWA_OK) return st;
+    bool all_ok = true;
+    st = close_group(*groups[0], theta_c_out, results, all_ok);
     if (st != PWA_OK) return st;
     return all_ok ? PWA_OK : PWA_ENOCONV;
 }

@@ -126,6 +126,9 @@ pwa_handle* coupling_handle(const pwa_coupling* cp);
 pwa_status variant_eval(pwa_variant* v, const double* theta, const double* dir, double* nll, double* grad,
                         double* hv);
 pwa_handle* variant_base(pwa_variant* v);
+// The same with the couplings only, at the line shapes of the last pwa_variant_set_shapes.
+pwa_status variant_coupling_eval(pwa_variant* v, const double* theta_c, const double* dir_c, double* nll,
+                                 double* grad, double* hv);
 // Read back and clear the device error flags; turns them into a status + message.
 pwa_status check_device_errors(pwa_handle* h);
 pwa_status set_error(pwa_handle* h, pwa_status st, const std::string& msg);

@@ -386,6 +386,86 @@ __global__ void __launch_bounds__(32 * kVarWarps) variant_kernel(const VarArgs a
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, 1);
 }
 
+// Integral matrices of the MC sample at fixed line shapes:
+// Phi_s,kk' = sum_mc conj(U_ks) U_k's, U_ks = BW_k F_ks.  A block takes 32-event
+// tiles in turn: its threads write U of the tile to shared memory ([K S] rows of
+// 32 events, row stride 33 against bank conflicts), then thread i accumulates
+// the entries q = i, i + blockDim, ... of the S K K matrix over the tile's
+// events in FP32 and adds the tile's sum to its FP64 totals.  Each block writes
+// one FP64 record [S K K][2].
+constexpr int kPhiThreads = 256;
+constexpr int kPhiMaxPerThread = 16;  // S K K <= 4 * 32 * 32 = 16 kPhiThreads
+
+__global__ void __launch_bounds__(kPhiThreads) variant_phi_kernel(const float* __restrict__ m2, const float2* __restrict__ Ft,
+                                                                 long long n, int K, int S,
+                                                                 const VarRes* __restrict__ res,
+                                                                 double* __restrict__ rec)
+{
+    extern __shared__ __align__(16) unsigned char phi_smem[];
+    VarRes* sres = reinterpret_cast<VarRes*>(phi_smem);
+    float2* U = reinterpret_cast<float2*>(phi_smem + ((32 * sizeof(VarRes) + 15) / 16) * 16);  // [K S][33]
+    const int tid = threadIdx.x;
+    for (int i = tid; i < K; i += blockDim.x) sres[i] = res[i];
+    __syncthreads();
+    const int KS = K * S, NQ = S * K * K;
+    double accr[kPhiMaxPerThread], acci[kPhiMaxPerThread];
+#pragma unroll
+    for (int j = 0; j < kPhiMaxPerThread; ++j) accr[j] = acci[j] = 0.0;
+    const long long ntiles = (n + kVarE - 1) / kVarE;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        // U of the tile's events (zero past the last event: F is zero there)
+        for (int i = tid; i < K * kVarE; i += blockDim.x) {
+            const int k = i / kVarE, l = i % kVarE;
+            const long long e = min(t * kVarE + l, n - 1);
+            const VarRes& r = sres[k];
+            const float m2v = m2[(long long)r.ch * n + e];
+            float2 ra, rb;
+            shape_factors(r, m2v, ra, rb);
+            const float2 BW = breit_wigner_v(r, m2v, ra, rb);
+            for (int s = 0; s < S; ++s) U[(k * S + s) * 33 + l] = cmul(BW, Ft[(t * KS + k * S + s) * kVarE + l]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kPhiMaxPerThread; ++j) {
+            const int q = tid + j * kPhiThreads;
+            if (q < NQ) {
+                const int s = q / (K * K), kk = q % (K * K), k = kk / K, kp = kk % K;
+                const float2* Ua = U + (k * S + s) * 33;
+                const float2* Ub = U + (kp * S + s) * 33;
+                float sr = 0.f, si = 0.f;
+#pragma unroll 8
+                for (int l = 0; l < kVarE; ++l) {
+                    const float2 a = Ua[l], b = Ub[l];  // conj(a) b
+                    sr += a.x * b.x + a.y * b.y;
+                    si += a.x * b.y - a.y * b.x;
+                }
+                accr[j] += (double)sr;
+                acci[j] += (double)si;
+            }
+        }
+        __syncthreads();
+    }
+    double* out = rec + (size_t)blockIdx.x * 2 * NQ;
+#pragma unroll
+    for (int j = 0; j < kPhiMaxPerThread; ++j) {
+        const int q = tid + j * kPhiThreads;
+        if (q < NQ) {
+            out[2 * q] = accr[j];
+            out[2 * q + 1] = acci[j];
+        }
+    }
+}
+
+// out[j] = sum over the blocks' records of rec[b][j], in block order
+__global__ void variant_phi_reduce_kernel(const double* __restrict__ rec, int nblocks, int len, double* __restrict__ out)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= len) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += rec[(size_t)b * len + j];
+    out[j] = s;
+}
+
 // F [n][KS] -> tiles [ceil(n / 32)][KS][32], zero past the last event
 __global__ void variant_tile_kernel(const float2* __restrict__ F, long long n, int KS, float2* __restrict__ out)
 {
@@ -516,6 +596,12 @@ struct pwa_variant {
     double* h_sums = nullptr;  // pinned: 2 rec_len sums + the error word
     int rec_len = 0, blocks0 = 0, blocks1 = 0;
     VarRes* h_res = nullptr;   // pinned
+    // coupling-only evaluation at fixed line shapes: the shape parameters and
+    // the MC integral matrices Phi [S][K][K] (complex FP64, host)
+    int Pc = 0;                       // coupling parameters at the head of theta
+    std::vector<double> shape_theta;  // theta[Pc ..] of the last pwa_variant_set_shapes
+    std::vector<double> phi;          // [S][K][K][2]
+    bool have_phi = false;
 };
 
 namespace {
@@ -755,6 +841,7 @@ pwa_status create_impl(pwa_variant* v, const pwa_events* data, const pwa_events*
             v->lay_s.push_back(0);
         }
     v->base.P = (int)v->lay_what.size();
+    for (int w : v->lay_what) v->Pc += (w <= 1) ? 1 : 0;
     double wsum = 0.0, dummy = 0.0;
     pwa_status st = check_sample(v, data, true, wsum);
     if (st != PWA_OK) return st;
@@ -814,10 +901,12 @@ pwa_status create_impl(pwa_variant* v, const pwa_events* data, const pwa_events*
 
 namespace pwa {
 
-// One evaluation (NLL, and the gradient and H v when asked) at host theta, v.
-pwa_status variant_eval(pwa_variant* v, const double* theta, const double* dir, double* nll, double* grad, double* hv)
+// One pass of the variant kernel at host theta (and direction dir when hv):
+// the data sample, and the MC sample unless data_only; leaves the summed
+// records in v->h_sums (data, then MC).
+static pwa_status run_pass(pwa_variant* v, const double* theta, const double* dir, bool hv, bool data_only)
 {
-    const int K = v->base.K, S = v->base.S, P = v->base.P, NC = NC_of(v), NP = 2 * NC + 3;
+    const int K = v->base.K, S = v->base.S;
     VAR_TRY(fill_res(v, theta, hv ? dir : nullptr));
     cudaStream_t st = v->base.stream;
     VAR_CUDA(v, cudaMemcpyAsync(v->d_res, v->h_res, sizeof(VarRes) * K, cudaMemcpyHostToDevice, st));
@@ -830,19 +919,22 @@ pwa_status variant_eval(pwa_variant* v, const double* theta, const double* dir, 
     a.n[0] = v->base.n[0];
     a.n[1] = v->base.n[1];
     a.K = K;
-    a.blocks0 = v->blocks0;
+    // data only: the whole grid takes the data sample (the records hold that many warps)
+    const int blocks0 = data_only ? v->blocks0 + v->blocks1 : v->blocks0;
+    const int blocks1 = data_only ? 0 : v->blocks1;
+    a.blocks0 = blocks0;
     a.res = v->d_res;
     a.rec = v->d_rec;
     a.rec_len = v->rec_len;
     a.err = v->d_err;
-    VarKernel fn = pick(S, v->per_projection != 0, hv != nullptr);
+    VarKernel fn = pick(S, v->per_projection != 0, hv);
     if (!fn) return vfail(v, PWA_EINVAL, "no variant kernel for this S");
     const size_t smem = var_smem_for(S, v->per_projection != 0);
     VAR_CUDA(v, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    fn<<<v->blocks0 + v->blocks1, 32 * kVarWarps, smem, st>>>(a);
+    fn<<<blocks0 + blocks1, 32 * kVarWarps, smem, st>>>(a);
     VAR_CUDA(v, cudaGetLastError());
     variant_reduce_kernel<<<(2 * v->rec_len + 31) / 32, dim3(32, 32), 0, st>>>(
-        v->d_rec, v->rec_len, v->blocks0 * kVarWarps, v->blocks1 * kVarWarps, v->d_sums);
+        v->d_rec, v->rec_len, blocks0 * kVarWarps, blocks1 * kVarWarps, v->d_sums);
     VAR_CUDA(v, cudaGetLastError());
     VAR_CUDA(v, cudaMemcpyAsync(v->h_sums, v->d_sums, sizeof(double) * 2 * v->rec_len, cudaMemcpyDeviceToHost, st));
     VAR_CUDA(v, cudaMemcpyAsync(v->h_sums + 2 * v->rec_len, v->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -851,9 +943,17 @@ pwa_status variant_eval(pwa_variant* v, const double* theta, const double* dir, 
     int errw = 0;
     std::memcpy(&errw, v->h_sums + 2 * v->rec_len, sizeof(int));
     if (errw) return vfail(v, PWA_ENONFINITE, "an event's intensity is not finite, or not positive for a data event");
+    return PWA_OK;
+}
+
+// One evaluation (NLL, and the gradient and H v when asked) at host theta, v.
+pwa_status variant_eval(pwa_variant* v, const double* theta, const double* dir, double* nll, double* grad, double* hv)
+{
+    const int P = v->base.P, NC = NC_of(v), NP = 2 * NC + 3;
+    VAR_TRY(run_pass(v, theta, dir, hv != nullptr, false));
     // Eqs. 3, 6, 7 from the sums
-    const double* sd = v->h_sums;                 // data: lanes' [G NP][H NP], then sum w ln I
-    const double* sm = v->h_sums + v->rec_len;    // MC: lanes' [G NP][H NP], then sum I, sum Idot
+    const double* sd = v->h_sums;                 // data: per resonance [G NP][H NP], then sum w ln I
+    const double* sm = v->h_sums + v->rec_len;    // MC: per resonance [G NP][H NP], then sum I, sum Idot
     const double SL = sd[32 * 2 * NP], G = sm[32 * 2 * NP], Gd = sm[32 * 2 * NP + 1];
     if (!(G > 0.0) || !std::isfinite(SL)) return vfail(v, PWA_ENONFINITE, "the MC normalisation is not positive");
     const double Nd = v->base.Nd;
@@ -868,7 +968,154 @@ pwa_status variant_eval(pwa_variant* v, const double* theta, const double* dir, 
             if (hv) hv[i] = -hD + Nd * (hM / G - gM * Gd / (G * G));
         }
     }
-    (void)S;
+    return PWA_OK;
+}
+
+// The MC integral matrices at the line shapes of theta (kept in v with theta's shape part).
+pwa_status variant_set_shapes(pwa_variant* v, const double* theta)
+{
+    const int K = v->base.K, S = v->base.S, NQ = S * K * K;
+    VAR_TRY(fill_res(v, theta, nullptr));
+    cudaStream_t st = v->base.stream;
+    VAR_CUDA(v, cudaMemcpyAsync(v->d_res, v->h_res, sizeof(VarRes) * K, cudaMemcpyHostToDevice, st));
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long ntiles = (v->base.n[1] + kVarE - 1) / kVarE;
+    const int nb = (int)std::max(1LL, std::min((long long)2 * sms, ntiles));
+    const size_t smem = ((32 * sizeof(VarRes) + 15) / 16) * 16 + sizeof(float2) * (size_t)K * S * 33;
+    double* d_rec = nullptr;
+    double* d_out = nullptr;
+    VAR_CUDA(v, cudaMallocAsync(&d_rec, sizeof(double) * 2 * (size_t)NQ * nb, st));
+    cudaError_t e = cudaMallocAsync(&d_out, sizeof(double) * 2 * (size_t)NQ, st);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(variant_phi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        variant_phi_kernel<<<nb, kPhiThreads, smem, st>>>(v->d_m2[1], v->d_F[1], v->base.n[1], K, S, v->d_res, d_rec);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        variant_phi_reduce_kernel<<<(2 * NQ + 255) / 256, 256, 0, st>>>(d_rec, nb, 2 * NQ, d_out);
+        e = cudaGetLastError();
+    }
+    v->phi.assign(2 * (size_t)NQ, 0.0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(v->phi.data(), d_out, sizeof(double) * 2 * NQ, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(d_rec, st);
+    if (d_out) cudaFreeAsync(d_out, st);
+    if (e != cudaSuccess) return pwa::cuda_error(&v->base, e, "integral matrices");
+    VAR_CUDA(v, cudaStreamSynchronize(st));
+    for (double x : v->phi)
+        if (!std::isfinite(x)) return vfail(v, PWA_ENONFINITE, "an integral matrix entry is not finite");
+    v->shape_theta.assign(theta + v->Pc, theta + v->base.P);
+    v->have_phi = true;
+    return PWA_OK;
+}
+
+// Coupling-only evaluation at the fixed line shapes: the data by the variant
+// kernel, the MC term from the integral matrices, sum_mc I = sum_s g_s^H Phi_s g_s.
+pwa_status variant_coupling_eval(pwa_variant* v, const double* theta_c, const double* dir_c, double* nll, double* grad,
+                                 double* hv)
+{
+    if (!v->have_phi) return vfail(v, PWA_EINVAL, "call pwa_variant_set_shapes first");
+    const int K = v->base.K, S = v->base.S, P = v->base.P, Pc = v->Pc, NC = NC_of(v), NP = 2 * NC + 3;
+    std::vector<double> th(P), dv(P, 0.0);
+    std::copy(theta_c, theta_c + Pc, th.begin());
+    std::copy(v->shape_theta.begin(), v->shape_theta.end(), th.begin() + Pc);
+    if (hv) std::copy(dir_c, dir_c + Pc, dv.begin());
+    VAR_TRY(run_pass(v, th.data(), dv.data(), hv != nullptr, true));
+    const double* sd = v->h_sums;
+    const double SL = sd[32 * 2 * NP];
+    if (!std::isfinite(SL)) return vfail(v, PWA_ENONFINITE, "a data term is not finite");
+    // couplings g_ks and directions gdot_ks for every (k, s) (fixed ones from the table)
+    const size_t KS = (size_t)K * S;
+    std::vector<double> gr(KS), gi(KS), er(KS), ei(KS), dr(KS, 0.0), di(KS, 0.0), vrh(KS, 0.0), vph(KS, 0.0);
+    std::vector<double> mag((size_t)K * NC), ph((size_t)K * NC), vm((size_t)K * NC, 0.0), vp((size_t)K * NC, 0.0);
+    for (int k = 0; k < K; ++k)
+        for (int c = 0; c < NC; ++c) {
+            mag[k * NC + c] = v->table[k].mag;
+            ph[k * NC + c] = v->table[k].phase;
+        }
+    for (int i = 0; i < Pc; ++i) {
+        const int k = v->lay_k[i], c = v->lay_s[i];
+        if (v->lay_what[i] == 0) {
+            mag[k * NC + c] = theta_c[i];
+            if (hv) vm[k * NC + c] = dir_c[i];
+        } else {
+            ph[k * NC + c] = theta_c[i];
+            if (hv) vp[k * NC + c] = dir_c[i];
+        }
+    }
+    for (int k = 0; k < K; ++k)
+        for (int s2 = 0; s2 < S; ++s2) {
+            const int c = v->per_projection ? s2 : 0;
+            const size_t q = (size_t)k * S + s2;
+            const double rho = mag[k * NC + c];
+            er[q] = std::cos(ph[k * NC + c]);
+            ei[q] = std::sin(ph[k * NC + c]);
+            gr[q] = rho * er[q];
+            gi[q] = rho * ei[q];
+            vrh[q] = vm[k * NC + c];
+            vph[q] = vp[k * NC + c];
+            dr[q] = vrh[q] * er[q] - vph[q] * gi[q];  // gdot = v_rho e + v_phi i g
+            di[q] = vrh[q] * ei[q] + vph[q] * gr[q];
+        }
+    // (Phi_s g_s)_k and (Phi_s gdot_s)_k; G = sum_s g_s^H Phi_s g_s, Gdot = 2 Re sum_s gdot_s^H Phi_s g_s
+    std::vector<double> pgr(KS), pgi(KS), pdr(KS), pdi(KS);
+    double G = 0.0, Gd = 0.0;
+    for (int s2 = 0; s2 < S; ++s2)
+        for (int k = 0; k < K; ++k) {
+            double ar = 0, ai = 0, br = 0, bi = 0;
+            for (int kp = 0; kp < K; ++kp) {
+                const size_t o = 2 * (((size_t)s2 * K + k) * K + kp);
+                const double fr = v->phi[o], fi = v->phi[o + 1];
+                const size_t q = (size_t)kp * S + s2;
+                ar += fr * gr[q] - fi * gi[q];
+                ai += fr * gi[q] + fi * gr[q];
+                br += fr * dr[q] - fi * di[q];
+                bi += fr * di[q] + fi * dr[q];
+            }
+            const size_t q = (size_t)k * S + s2;
+            pgr[q] = ar;
+            pgi[q] = ai;
+            pdr[q] = br;
+            pdi[q] = bi;
+            G += gr[q] * ar + gi[q] * ai;          // Re conj(g) (Phi g)
+            Gd += 2.0 * (dr[q] * ar + di[q] * ai);  // 2 Re conj(gdot) (Phi g)
+        }
+    if (!(G > 0.0)) return vfail(v, PWA_ENONFINITE, "the MC normalisation is not positive");
+    const double Nd = v->base.Nd;
+    *nll = -SL + Nd * std::log(G / v->base.Nmc);
+    if (grad || hv) {
+        for (int i = 0; i < Pc; ++i) {
+            const int what = v->lay_what[i], k = v->lay_k[i], c = v->lay_s[i];
+            const int slot = what == 0 ? c : NC + c;
+            const double gD = sd[k * 2 * NP + slot], hD = sd[k * 2 * NP + NP + slot];
+            double gM = 0.0, hM = 0.0;
+            for (int s2 = 0; s2 < S; ++s2) {
+                if (v->per_projection && s2 != c) continue;
+                const size_t q = (size_t)k * S + s2;
+                // dg and d gdot of this parameter (rho: e and v_phi i e; phi: i g and v_rho i e - v_phi g)
+                double ar, ai, br, bi;
+                if (what == 0) {
+                    ar = er[q];
+                    ai = ei[q];
+                    br = -vph[q] * ei[q];
+                    bi = vph[q] * er[q];
+                } else {
+                    ar = -gi[q];
+                    ai = gr[q];
+                    br = -vrh[q] * ei[q] - vph[q] * gr[q];
+                    bi = vrh[q] * er[q] - vph[q] * gi[q];
+                }
+                gM += 2.0 * (ar * pgr[q] + ai * pgi[q]);  // 2 Re conj(dg) (Phi g)
+                hM += 2.0 * (br * pgr[q] + bi * pgi[q]) + 2.0 * (ar * pdr[q] + ai * pdi[q]);
+            }
+            if (grad) grad[i] = -gD + Nd * gM / G;
+            if (hv) hv[i] = -hD + Nd * (hM / G - gM * Gd / (G * G));
+        }
+    }
     return PWA_OK;
 }
 
@@ -921,6 +1168,39 @@ pwa_status pwa_variant_eval(pwa_variant* v, const double* theta, const double* d
         grad = g_tmp.data();
     }
     return pwa::variant_eval(v, theta, dir, nll, grad, hv);
+}
+
+pwa_status pwa_variant_set_shapes(pwa_variant* v, const double* theta, double* phi_out)
+{
+    if (!v) return PWA_EINVAL;
+    v->base.err.clear();
+    if (!theta) return vfail(v, PWA_EINVAL, "theta must not be NULL");
+    for (int i = 0; i < v->base.P; ++i)
+        if (!std::isfinite(theta[i])) return vfail(v, PWA_EINVAL, "theta must be finite");
+    v->have_phi = false;
+    pwa_status st = pwa::variant_set_shapes(v, theta);
+    if (st == PWA_OK && phi_out) std::memcpy(phi_out, v->phi.data(), sizeof(double) * v->phi.size());
+    return st;
+}
+
+int pwa_variant_coupling_num_params(const pwa_variant* v) { return v ? v->Pc : -1; }
+
+pwa_status pwa_variant_coupling_eval(pwa_variant* v, const double* theta_c, const double* dir_c, double* nll,
+                                     double* grad, double* hv)
+{
+    if (!v) return PWA_EINVAL;
+    v->base.err.clear();
+    if (!theta_c || !nll) return vfail(v, PWA_EINVAL, "theta_c and nll must not be NULL");
+    if (hv && !dir_c) return vfail(v, PWA_EINVAL, "v is required for hv");
+    for (int i = 0; i < v->Pc; ++i)
+        if (!std::isfinite(theta_c[i]) || (hv && !std::isfinite(dir_c[i])))
+            return vfail(v, PWA_EINVAL, "theta_c and v must be finite");
+    std::vector<double> g_tmp;
+    if (hv && !grad) {
+        g_tmp.resize(v->Pc);
+        grad = g_tmp.data();
+    }
+    return pwa::variant_coupling_eval(v, theta_c, dir_c, nll, grad, hv);
 }
 
 const char* pwa_variant_last_error(const pwa_variant* v)

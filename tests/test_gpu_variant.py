@@ -160,3 +160,73 @@ def test_variant_fit_matches_oracle_fit():
     assert np.max(np.abs(pull)) <= 1e-3, (pull, infos)
     assert abs(infos[0]["nll"] - ref.fun) <= 1e-6 * max(abs(ref.fun), 1.0)
     Lv.close()
+
+
+@pytest.mark.parametrize("name,per_projection", [("tiny", True), ("k7s3", True), ("paper", False), ("paper", True)])
+def test_coupling_only_matches_oracle(name, per_projection):
+    """Fixed line shapes: the integral matrices Phi_s against the oracle's, and
+    the coupling-only NLL, gradient and H v (data pass + Phi) against the
+    oracle's full evaluation restricted to the couplings."""
+    cfg, table, vm, wl = variant_case(name, per_projection)
+    Lv = make_variant(cfg, table, vm, wl)
+    rng = np.random.default_rng(11)
+    th = vm.theta0() * (1 + 0.02 * rng.standard_normal(vm.P))
+    phi = Lv.set_shapes(th)
+    phio = V.integral_matrices(vm, th, wl.mc.m2, wl.mc.F)
+    assert np.max(np.abs(phi - phio)) <= 1e-6 * np.max(np.abs(phio))
+    Pc = V.coupling_count(vm)
+    assert Lv.Pc == Pc
+    v = np.zeros(vm.P)
+    v[:Pc] = rng.standard_normal(Pc)
+    f, g, hv = Lv.coupling_eval(th[:Pc], v[:Pc])
+    fo, go, hvo = V.nll_grad_hvp(vm, th, v, wl.data, wl.mc)
+    I = V.intensity(vm, th, wl.data.m2, wl.data.F)
+    scale = max(abs(fo), float(np.sum(np.abs(np.log(I)))))
+    assert abs(f - fo) <= 1e-6 * scale, (f, fo)
+    eg = np.max(np.abs(g - go[:Pc])) / np.max(np.abs(go[:Pc]))
+    eh = np.max(np.abs(hv - hvo[:Pc])) / np.max(np.abs(hvo[:Pc]))
+    print("%s per_projection=%s Pc=%d: coupling-only grad %.2e, H v %.2e" % (name, per_projection, Pc, eg, eh))
+    assert eg <= 1e-5 and eh <= 1e-4, (eg, eh)
+    Lv.close()
+
+
+def test_coupling_only_needs_the_shapes_first():
+    from paper_2403_09225_b300 import binding
+    cfg, table, vm, wl = variant_case("tiny", True)
+    Lv = make_variant(cfg, table, vm, wl)
+    with pytest.raises(binding.PwaError):
+        Lv.coupling_eval(vm.theta0()[:V.coupling_count(vm)])
+    Lv.close()
+
+
+def test_coupling_only_fit_matches_oracle_fit():
+    """Coupling-only Newton-CG (lockstep, on the data pass + Phi) against the
+    oracle's Newton-CG on the couplings with the line shapes held fixed."""
+    cfg, table, vm, wl = variant_case("tiny", True)
+    Pc = V.coupling_count(vm)
+    rng = np.random.default_rng(6)
+    th_all = vm.theta0()
+    shape = th_all[Pc:]
+    c0 = th_all[:Pc] * (1 + 0.05 * rng.standard_normal(Pc))
+
+    def full(c):
+        return np.concatenate([c, shape])
+
+    def fg(c):
+        f, g, _ = V.nll_grad_hvp(vm, full(c), np.zeros(vm.P), wl.data, wl.mc)
+        return f, g[:Pc]
+
+    def hp(c, vc):
+        return V.nll_grad_hvp(vm, full(c), np.concatenate([vc, np.zeros(vm.P - Pc)]), wl.data, wl.mc)[2][:Pc]
+
+    ref = ncg.newton_cg(fg, hp, c0, xtol=1e-10, maxiter=200)
+    assert ref.status in ncg.CONVERGED, ref.status_name
+    Lv = make_variant(cfg, table, vm, wl)
+    Lv.set_shapes(th_all)
+    out, infos, ok = Lv.coupling_fit(c0[None], xtol=1e-10)
+    assert ok, infos
+    H = np.stack([hp(ref.x, e) for e in np.eye(Pc)])
+    sig = np.sqrt(np.diag(np.linalg.inv(0.5 * (H + H.T))))
+    pull = (_canonical(vm, full(out[0]))[:Pc] - _canonical(vm, full(ref.x))[:Pc]) / sig
+    assert np.max(np.abs(pull)) <= 1e-3, (pull, infos)
+    Lv.close()
