@@ -35,6 +35,13 @@
  *   usual choice (resonance 0's coupling fixed to 1, everything else free)
  *   P = 4K - 2 and theta = (rho_1..rho_{K-1}, phi_1..phi_{K-1}, M_0..M_{K-1},
  *   Gamma_0..Gamma_{K-1}).
+ *
+ * Besides the likelihood handle: pwa_coupling (the fixed-mass coupling
+ * sub-problem on the tensor cores), pwa_variant (other line shapes and one
+ * coupling per projection), the pseudo-experiment generator calls and
+ * pwa_mlp (the learned starting-point proposal's network).  Each section
+ * below states its own arguments and errors; the conventions above hold for
+ * all of them.
  */
 #ifndef LIBPWA_PWA_H
 #define LIBPWA_PWA_H
