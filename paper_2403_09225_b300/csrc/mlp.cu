@@ -356,6 +356,12 @@ struct pwa_mlp {
     float* loss_rows = nullptr;
     float* ws = nullptr;      // split-K partial products
     size_t ws_floats = 0;
+    float* T = nullptr;       // targets of the current batch [maxB][out] (copied in, read by the loss)
+    cudaStream_t own_stream = nullptr;  // created when the caller passes none (graphs need a real stream)
+    // the gradient pass of a batch size (layers' products, loss, backward) as a CUDA
+    // graph, captured on the third call with that size; index B / 128
+    std::vector<cudaGraphExec_t> graph;
+    std::vector<int> graph_uses;
     int* d_periodic = nullptr;
     float* d_wgt = nullptr;
     int step = 0;
@@ -420,11 +426,18 @@ pwa_status gemm(pwa_mlp* m, const __nv_bfloat16* A, int lda, const __nv_bfloat16
     } while (0)
 
 // forward over B rows (B % 128 == 0) from X (FP32 [B][in]); outputs in Z[layers] (FP32)
-pwa_status forward(pwa_mlp* m, int B, const float* d_x)
+// the network's input in BF16 (H[0]) from the caller's FP32 rows
+pwa_status forward_input(pwa_mlp* m, int B, const float* d_x)
 {
-    const int L = m->layers + 1;
     to_bf16_kernel<<<blocks_for((long long)B * m->in), 256, 0, m->stream>>>(d_x, B, m->in, m->H[0], m->in, B);
     MLP_CUDA(m, cudaGetLastError());
+    return PWA_OK;
+}
+
+// the layers from H[0]; outputs in Z[layers] (FP32)
+pwa_status forward_layers(pwa_mlp* m, int B)
+{
+    const int L = m->layers + 1;
     for (int l = 0; l < L; ++l) {
         const bool last = l == L - 1;
         MLP_TRY(gemm(m, m->H[l], m->fin[l], m->Wb[l], m->fin[l], m->acc, m->foutp[l], B, m->foutp[l], m->fin[l]));
@@ -436,10 +449,18 @@ pwa_status forward(pwa_mlp* m, int B, const float* d_x)
     return PWA_OK;
 }
 
-// backward after forward: gradients into gW, gb; loss rows in loss_rows
-pwa_status backward(pwa_mlp* m, int B, const float* d_t)
+// forward over B rows (B % 128 == 0) from X (FP32 [B][in]); outputs in Z[layers] (FP32)
+pwa_status forward(pwa_mlp* m, int B, const float* d_x)
+{
+    MLP_TRY(forward_input(m, B, d_x));
+    return forward_layers(m, B);
+}
+
+// backward after forward, with the targets in m->T: gradients into gW, gb; loss rows in loss_rows
+pwa_status backward(pwa_mlp* m, int B)
 {
     const int L = m->layers + 1;
+    const float* d_t = m->T;
     loss_kernel<<<(B + 127) / 128, 128, 0, m->stream>>>(m->Z[L - 1], m->foutp[L - 1], d_t, B, m->out, m->d_wgt,
                                                        m->d_periodic, m->dY, m->outp, m->loss_rows);
     MLP_CUDA(m, cudaGetLastError());
@@ -548,6 +569,9 @@ pwa_status create_impl(pwa_mlp* m, int in, int hid, int layers, int out, int max
     MLP_TRY(alloc_b(m, &m->T1, std::max((size_t)max_f * maxB, (size_t)hid * std::max(hid, m->outp))));
     MLP_TRY(alloc_b(m, &m->T2, (size_t)max_f * maxB));
     MLP_TRY(alloc_f(m, &m->loss_rows, maxB));
+    MLP_TRY(alloc_f(m, &m->T, (size_t)maxB * out));
+    m->graph.assign(maxB / kGM + 1, nullptr);
+    m->graph_uses.assign(maxB / kGM + 1, 0);
     // split-K workspace: the largest Z M N over the network's products at batches up to maxB
     for (int B = kGM; B <= maxB; B += kGM)
         for (int l = 0; l < L; ++l) {
@@ -592,6 +616,44 @@ pwa_status create_impl(pwa_mlp* m, int in, int hid, int layers, int out, int max
     return PWA_OK;
 }
 
+// forward layers + loss + backward from H[0] and T: eager for the first two calls
+// with a batch size, then captured into a CUDA graph and replayed
+pwa_status gradient_pass(pwa_mlp* m, int B)
+{
+    const int gi = B / kGM;
+    if (m->graph[gi]) {
+        MLP_CUDA(m, cudaGraphLaunch(m->graph[gi], m->stream));
+        return PWA_OK;
+    }
+    if (++m->graph_uses[gi] < 3) {
+        MLP_TRY(forward_layers(m, B));
+        return backward(m, B);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        m->graph_uses[gi] = -1000000;  // this size stays eager
+        MLP_TRY(forward_layers(m, B));
+        return backward(m, B);
+    }
+    pwa_status st = forward_layers(m, B);
+    if (st == PWA_OK) st = backward(m, B);
+    e = cudaStreamEndCapture(m->stream, &g);
+    if (st != PWA_OK || e != cudaSuccess || !g || cudaGraphInstantiate(&m->graph[gi], g, 0) != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        m->graph[gi] = nullptr;
+        m->graph_uses[gi] = -1000000;
+        m->err.clear();
+        MLP_TRY(forward_layers(m, B));
+        return backward(m, B);
+    }
+    cudaGraphDestroy(g);
+    MLP_CUDA(m, cudaGraphLaunch(m->graph[gi], m->stream));
+    return PWA_OK;
+}
+
 pwa_status check_err(pwa_mlp* m)
 {
     int e = 0;
@@ -621,6 +683,17 @@ pwa_status pwa_mlp_create(int in, int hidden, int layers, int out, int max_batch
     auto* m = new (std::nothrow) pwa_mlp();
     if (!m) return PWA_ENOMEM;
     m->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (!m->stream) {
+        // a stream of our own (ordered with the legacy default stream) so that the
+        // gradient pass can be captured into a graph
+        if (cudaStreamCreate(&m->own_stream) != cudaSuccess) {
+            cudaGetLastError();
+            g_mlp_create_error = "cannot create the network's stream";
+            delete m;
+            return PWA_ECUDA;
+        }
+        m->stream = m->own_stream;
+    }
     pwa_status st = create_impl(m, in, hidden, layers, out, max_batch, seed, periodic, loss_weight);
     if (st != PWA_OK) {
         g_mlp_create_error = m->err;
@@ -648,8 +721,9 @@ pwa_status pwa_mlp_gradients(pwa_mlp* m, int B, const float* d_x, const float* d
     if (!m || !d_x || !d_t) return PWA_EINVAL;
     m->err.clear();
     if (B <= 0 || B > m->maxB || B % kGM) return mlp_fail(m, PWA_EINVAL, "B must be a multiple of 128 up to max_batch");
-    MLP_TRY(forward(m, B, d_x));
-    MLP_TRY(backward(m, B, d_t));
+    MLP_TRY(forward_input(m, B, d_x));
+    MLP_CUDA(m, cudaMemcpyAsync(m->T, d_t, sizeof(float) * (size_t)B * m->out, cudaMemcpyDeviceToDevice, m->stream));
+    MLP_TRY(gradient_pass(m, B));
     if (loss) {
         std::vector<float> lr(B);
         MLP_CUDA(m, cudaMemcpyAsync(lr.data(), m->loss_rows, sizeof(float) * B, cudaMemcpyDeviceToHost, m->stream));
@@ -778,8 +852,12 @@ void pwa_mlp_destroy(pwa_mlp* m)
     }
     for (auto* p : m->H) fr(p);
     for (auto* p : m->Z) fr(p);
-    void* ps[] = {m->acc, m->dY, m->dZb, m->dZ32, m->T1, m->T2, m->loss_rows, m->ws, m->d_periodic, m->d_wgt, m->d_err};
+    void* ps[] = {m->acc, m->dY, m->dZb, m->dZ32, m->T1, m->T2, m->loss_rows, m->ws, m->T, m->d_periodic, m->d_wgt,
+                  m->d_err};
     for (void* p : ps) fr(p);
+    for (auto g : m->graph)
+        if (g) cudaGraphExecDestroy(g);
+    if (m->own_stream) cudaStreamDestroy(m->own_stream);
     cudaGetLastError();
     delete m;
 }

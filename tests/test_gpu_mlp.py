@@ -149,3 +149,24 @@ def test_training_fits_a_smooth_map():
         last = net.train_step(xd, td, 1e-3)
     assert last < first / 10, (first, last)
     net.close()
+
+
+def test_graph_replayed_gradients_equal_the_eager_ones():
+    """The gradient pass of a batch size runs eagerly twice, is captured into a
+    CUDA graph on the third call and replayed from then on: the same kernels in
+    the same order, so the results are bit-identical; a new input reaches the
+    replayed graph (it is copied into the network's buffers first)."""
+    import torch
+    net, x, t, xd, td, periodic, weight = _setup(256, 256, 2, 12, 256, seed=21)
+    ref_loss = net.gradients(xd, td)
+    ref = [net.get(l, 2).copy() for l in range(3)]
+    for _ in range(4):
+        assert net.gradients(xd, td) == ref_loss
+        for l in range(3):
+            assert np.array_equal(net.get(l, 2), ref[l])
+    x2 = torch.flip(xd, dims=[0]).contiguous()
+    l2 = net.gradients(x2, td)
+    params = net.params()
+    lo, _ = omlp.loss_and_grads(params, x2.cpu().numpy(), t, weight, periodic, quantize=True)
+    assert abs(l2 - lo) <= 1e-3 * abs(lo) and l2 != ref_loss
+    net.close()
