@@ -339,7 +339,7 @@ def coupling_metric(L, wl, reps: int = 20):
 
 
 def learned_metric(n_train: int, n_eval: int, n_random: int, time_limit: float, pool: int = 10_000_000,
-                   n_events: int = 100_000, n_mc: int = 500_000, epochs: int = 60):
+                   n_events: int = 100_000, n_mc: int = 500_000, epochs: int = 60, polish: bool = False):
     """The learned starting-point proposal on the paper-scale model (K = 20,
     S = 4, 78 parameters): n_train pseudo-experiments (theta from the prior,
     up to n_events events accept-rejected from a pool of phase-space events,
@@ -381,7 +381,7 @@ def learned_metric(n_train: int, n_eval: int, n_random: int, time_limit: float, 
         peak, kind = bf16_peak()
         t0 = time.perf_counter()
         recs, summ = proposal.evaluate(gen, net, codec, n_eval, n_events, n_random, seed=999,
-                                       fit_opts=dict(time_limit_s=time_limit))
+                                       fit_opts=dict(time_limit_s=time_limit), polish=polish)
         eval_s = time.perf_counter() - t0
         net.close()
         return {"model": "paper-scale table: K=20, S=4, P=78", "train_experiments": n_train,
@@ -530,6 +530,8 @@ def main():
                     help="also run the uneven-size toy-fit comparison (plain vs batched), e.g. 12,4")
     ap.add_argument("--learned", default="", metavar="TRAIN,EVAL,STARTS",
                     help="also train and evaluate the learned starting-point proposal, e.g. 4096,16,16")
+    ap.add_argument("--learned-polish", action="store_true",
+                    help="in the learned leg, also fit each learned start's couplings first (coupling object)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="event counts relative to the workload (profiling captures only; default 1)")
     args = ap.parse_args()
@@ -619,7 +621,7 @@ def main():
     learned = None
     if args.learned and rank == 0:
         n_train, n_eval, n_rand = (int(x) for x in args.learned.split(","))
-        learned = learned_metric(n_train, n_eval, n_rand, time_limit=args.fit_time_limit)
+        learned = learned_metric(n_train, n_eval, n_rand, time_limit=args.fit_time_limit, polish=args.learned_polish)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

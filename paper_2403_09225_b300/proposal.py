@@ -303,12 +303,38 @@ def perturbed_starts(codec: Codec, start: np.ndarray, count: int, rng, scale: fl
     return codec.decode(np.stack(rows))
 
 
+def polish_couplings(L, starts: np.ndarray, opts: Optional[dict] = None) -> np.ndarray:
+    """Each start with its couplings replaced by the coupling-only Newton-CG
+    fit at its own masses and widths (the tensor-core coupling object of
+    binding.Coupling: the data events as U = BW F tiles, the MC events as the
+    integral matrix)."""
+    out = np.array(starts, dtype=np.float64, copy=True)
+    o = dict(xtol=1e-6, maxiter=50)
+    o.update(opts or {})
+    for i in range(out.shape[0]):
+        try:
+            cp = binding.Coupling(L, out[i])
+        except binding.PwaError:
+            continue  # a start the coupling object refuses keeps its couplings
+        try:
+            c, _, _ = cp.fit(out[i, :cp.Pc][None], **o)
+            if np.all(np.isfinite(c[0])):
+                out[i, :cp.Pc] = c[0]
+        except binding.PwaError:
+            pass
+        finally:
+            cp.close()
+    return out
+
+
 def evaluate(gen: Generator, net, codec: Codec, count: int, n_events: int, n_random: int, seed: int,
-             fit_opts: Optional[dict] = None, tol: float = 0.01, n_learned: int = 4):
+             fit_opts: Optional[dict] = None, tol: float = 0.01, n_learned: int = 4, polish: bool = False):
     """Held-out pseudo-experiments, three ways with the same fit options:
     one fit from the network's start; one batched call from the network's
     start and n_learned - 1 draws around it; one batched call from n_random
-    prior starts.  The global minimum of an experiment is the lowest NLL any
+    prior starts.  With polish, also the first two with their starts'
+    couplings fitted first at the starts' masses and widths
+    (polish_couplings; its time counts).  The global minimum of an experiment is the lowest NLL any
     of its fits reached; a fit reaches it when its NLL is within `tol`.
     Returns per-experiment records and the summary of summarize()."""
     opts = dict(xtol=1e-8, maxiter=0)
@@ -331,16 +357,36 @@ def evaluate(gen: Generator, net, codec: Codec, count: int, n_events: int, n_ran
         t0 = time.perf_counter()
         _, info_r, _ = L.fit_batch(rnd, **opts)
         t_r = time.perf_counter() - t0
+        extra = {}
+        if polish:
+            # the same starts with their couplings fitted at their masses and widths first
+            t0 = time.perf_counter()
+            ps = polish_couplings(L, starts[i][None])[0]
+            _, info_p = L.fit(ps, **opts)
+            t_p = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            pb = polish_couplings(L, lb)
+            _, info_pb, _ = L.fit_batch(pb, **opts)
+            t_pb = time.perf_counter() - t0
+            extra = dict(nll_polish=info_p["nll"], t_polish=t_p,
+                         nll_polish_batch=[d["nll"] for d in info_pb], t_polish_batch=t_pb)
         f_true = L.nll(ex.theta_true[i])
         L.close()
         nll_r = np.array([d["nll"] for d in info_r])
         nll_b = np.array([d["nll"] for d in info_b])
-        best = min(info_m["nll"], float(np.min(nll_b)), float(np.min(nll_r)))
-        recs.append(dict(n_events=int(ex.n_events[i]), nll_mlp=info_m["nll"], nll_learned_batch=nll_b.tolist(),
-                         nll_random=nll_r.tolist(), nll_true=f_true, best=best, t_mlp=t_m, t_learned_batch=t_b,
-                         t_random=t_r, mlp_hit=bool(info_m["nll"] <= best + tol),
-                         learned_batch_hit=bool(np.min(nll_b) <= best + tol),
-                         random_hits=int(np.sum(nll_r <= best + tol))))
+        cands = [info_m["nll"], float(np.min(nll_b)), float(np.min(nll_r))]
+        if polish:
+            cands += [extra["nll_polish"], float(np.min(extra["nll_polish_batch"]))]
+        best = min(cands)
+        rec = dict(n_events=int(ex.n_events[i]), nll_mlp=info_m["nll"], nll_learned_batch=nll_b.tolist(),
+                   nll_random=nll_r.tolist(), nll_true=f_true, best=best, t_mlp=t_m, t_learned_batch=t_b,
+                   t_random=t_r, mlp_hit=bool(info_m["nll"] <= best + tol),
+                   learned_batch_hit=bool(np.min(nll_b) <= best + tol),
+                   random_hits=int(np.sum(nll_r <= best + tol)))
+        if polish:
+            rec.update(extra, polish_hit=bool(extra["nll_polish"] <= best + tol),
+                       polish_batch_hit=bool(min(extra["nll_polish_batch"]) <= best + tol))
+        recs.append(rec)
     return recs, summarize(recs, n_random, n_learned)
 
 
@@ -369,4 +415,13 @@ def summarize(recs: Sequence[dict], n_random: int, n_learned: int = 1) -> dict:
                    learned_batch_hit_rate=float(np.mean([r["learned_batch_hit"] for r in recs])),
                    learned_batch_s_to_min=float(np.mean(lb)),
                    mean_t_learned_batch=float(np.mean([r["t_learned_batch"] for r in recs])))
+    if recs and "t_polish" in recs[0]:
+        lp = [r["t_polish"] + (0.0 if r["polish_hit"] else e_rand) for r in recs]
+        lpb = [r["t_polish_batch"] + (0.0 if r["polish_batch_hit"] else e_rand) for r in recs]
+        out.update(polish_hit_rate=float(np.mean([r["polish_hit"] for r in recs])),
+                   polish_s_to_min=float(np.mean(lp)),
+                   polish_batch_hit_rate=float(np.mean([r["polish_batch_hit"] for r in recs])),
+                   polish_batch_s_to_min=float(np.mean(lpb)),
+                   mean_t_polish=float(np.mean([r["t_polish"] for r in recs])),
+                   mean_t_polish_batch=float(np.mean([r["t_polish_batch"] for r in recs])))
     return out

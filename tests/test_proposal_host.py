@@ -80,3 +80,14 @@ def test_summary_time_to_minimum():
     assert math.isclose(s["learned_s_to_min"], (0.5 + 0.5 + e) / 2)
     assert math.isclose(s["learned_batch_s_to_min"], (0.8 + 0.8 + e) / 2)
     assert s["mlp_hit_rate"] == 0.5
+
+
+def test_summary_of_the_polished_forms():
+    recs = [dict(t_random=2.0, random_hits=1, t_mlp=0.5, mlp_hit=False, nll_mlp=1.0, best=0.0,
+                 nll_random=[0.0, 1.0], t_learned_batch=0.8, learned_batch_hit=True,
+                 t_polish=0.6, polish_hit=True, t_polish_batch=0.9, polish_batch_hit=False)]
+    s = proposal.summarize(recs, n_random=2, n_learned=4)
+    e = 2.0 / (1 - (1 - 0.5) ** 2)
+    assert math.isclose(s["polish_s_to_min"], 0.6)
+    assert math.isclose(s["polish_batch_s_to_min"], 0.9 + e)
+    assert s["polish_hit_rate"] == 1.0 and s["polish_batch_hit_rate"] == 0.0
