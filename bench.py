@@ -399,6 +399,41 @@ def learned_metric(n_train: int, n_eval: int, n_random: int, time_limit: float, 
         gen.close()
 
 
+def mlp_step_metric(batches=(128, 512, 1024), reps: int = 50):
+    """The learned proposal's network (4096 -> 3 x 512 GELU -> 78) alone: one
+    gradient step (forward, loss, backward on the tcgen05 products; replayed
+    as a CUDA graph after its first calls) per batch size, CUDA events over
+    `reps` host-synchronous calls, useful flops 6 B sum fan_in fan_out."""
+    import torch
+    from paper_2403_09225_b300 import binding
+    peak, kind = bf16_peak()
+    sizes = [(4096, 512), (512, 512), (512, 512), (512, 128)]
+    out = {"network": "4096 -> 3 x 512 GELU -> 78 (output padded to 128 in the products)"}
+    for B in batches:
+        net = binding.ProposalMLP(4096, 512, 3, 78, B, seed=1)
+        try:
+            g = torch.Generator(device="cuda").manual_seed(B)
+            x = torch.randn(B, 4096, device="cuda", generator=g)
+            t = torch.randn(B, 78, device="cuda", generator=g)
+            for _ in range(5):
+                net.gradients(x, t)
+            stream = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                net.gradients(x, t)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            flops = 6.0 * B * sum(a * b for a, b in sizes)
+            out["batch_%d" % B] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+                                   "frac": flops / (ms * 1e-3) / 1e12 / peak, "peak": peak, "peak_kind": kind}
+        finally:
+            net.close()
+    return out
+
+
 def variant_shapes(table):
     """The benchmark's variant model: every third resonance (k = 1, 4, ...)
     with a mass-dependent width, resonance 6 (a pi pi resonance) Flatte with a
@@ -526,6 +561,8 @@ def main():
     ap.add_argument("--tiling", default="", help="warps,lanes_per_event,stages[,blocks_per_sm] (default: library's)")
     ap.add_argument("--no-coupling", action="store_true", help="skip the fixed-mass coupling sub-problem leg")
     ap.add_argument("--no-variants", action="store_true", help="skip the physics-variant leg")
+    ap.add_argument("--mlp-timing", action="store_true",
+                    help="also time the learned proposal's network (gradient step at batches 128, 512, 1024)")
     ap.add_argument("--batching", default="", metavar="TOYS,STARTS",
                     help="also run the uneven-size toy-fit comparison (plain vs batched), e.g. 12,4")
     ap.add_argument("--learned", default="", metavar="TRAIN,EVAL,STARTS",
@@ -618,6 +655,10 @@ def main():
     if rank == 0 and not args.no_variants:
         variants = variant_metric(wl)
 
+    mlp_step = None
+    if args.mlp_timing and rank == 0:
+        mlp_step = mlp_step_metric()
+
     learned = None
     if args.learned and rank == 0:
         n_train, n_eval, n_rand = (int(x) for x in args.learned.split(","))
@@ -658,6 +699,8 @@ def main():
             res["coupling"] = coupling
         if variants is not None:
             res["variants"] = variants
+        if mlp_step is not None:
+            res["mlp_step"] = mlp_step
         if learned is not None:
             res["learned"] = learned
         print(json.dumps(res))
