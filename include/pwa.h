@@ -264,9 +264,11 @@ pwa_status pwa_newton_cg_fit_multi(int n_handles, pwa_handle* const* handles, co
  * normalisation becomes g^H Phi g with the K x K Hermitian integral matrix
  * Phi_{kk'} = sum_mc sum_s conj(U_{k,s}) U_{k',s} (computed once), and the
  * data term for many coupling vectors is a pair of GEMMs per tile of events,
- * run on the tensor cores (tcgen05, TF32 inputs split in hi + lo parts so that
- * products keep FP32 accuracy; FP32 accumulation in tensor memory, FP64 across
- * tiles).  The MC events are not read after the object is created.
+ * run on the tensor cores (tcgen05 kind::f16: every FP32 operand split into
+ * three BF16 parts, which represent it exactly, and the six part products
+ * with i + j <= 2 accumulated in FP32 in tensor memory, the leading products
+ * apart from the corrections; FP64 across tiles).  The MC events are not
+ * read after the object is created.
  *
  * The coupling parameters are the first Pc entries of theta (the free
  * magnitudes, then the free phases, in resonance order); the object keeps the
