@@ -95,6 +95,22 @@ typedef struct {
     int fix_coupling, fix_mass, fix_width;
 } pwa_resonance;
 
+/* One outer Newton iteration of a fit, as recorded when the caller asks for
+ * a trace (pwa_fit_opts.trace).  cg_exit: 1 negative curvature, 2 residual
+ * below the forcing tolerance, 3 inner iteration limit. */
+typedef struct pwa_fit_iter {
+    double nll;        /* NLL at the start of the iteration                     */
+    double grad_max;   /* max |grad| there                                      */
+    double cg_eps;     /* forcing tolerance min(0.5, sqrt|g|) |g| of the CG     */
+    double cg_res;     /* |r| of the inner CG when it stopped                   */
+    double step;       /* accepted line-search step length (0: none found)      */
+    double dir_deriv;  /* g . p along the Newton direction                      */
+    int cg_iters;      /* inner CG iterations (one H v each)                    */
+    int cg_exit;       /* why the inner CG stopped (see above)                  */
+    int n_fev;         /* line-search evaluations (one pass each)               */
+    int hessian;       /* 1 when H came from an explicit Hessian pass           */
+} pwa_fit_iter;
+
 /* Options of pwa_newton_cg_fit (paper Sec. 3: scipy's Newton-CG with xtol,
  * default 1e-8, and early stopping after 500 s). */
 typedef struct {
@@ -103,6 +119,10 @@ typedef struct {
     int maxiter;          /* outer iterations (0: 200 P)                            */
     int cg_maxiter;       /* inner CG iterations per outer step (0: 20 P)           */
     double time_limit_s;  /* wall-clock limit, 0: none (the paper uses 500 s)       */
+    int trace_cap;        /* records per fit that trace can hold (0: no trace)      */
+    pwa_fit_iter* trace;  /* host [fits][trace_cap] or NULL: per-iteration record;
+                             fits are numbered in the order of theta0 (over all
+                             handles in order for pwa_newton_cg_fit_multi)     */
 } pwa_fit_opts;
 
 typedef enum {
@@ -126,6 +146,7 @@ typedef struct {
     int n_fev;        /* NLL+gradient evaluations (one pass over F each)   */
     int status;       /* pwa_fit_status                                    */
     double elapsed_s; /* wall-clock seconds inside the call                */
+    int n_trace;      /* iterations recorded in opts->trace (<= trace_cap) */
 } pwa_fit_result;
 
 /* Build a likelihood handle.  Copies data and MC events to the device and

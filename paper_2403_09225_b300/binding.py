@@ -34,9 +34,17 @@ class pwa_resonance(ctypes.Structure):
                 ("fix_coupling", ctypes.c_int), ("fix_mass", ctypes.c_int), ("fix_width", ctypes.c_int)]
 
 
+class pwa_fit_iter(ctypes.Structure):
+    _fields_ = [("nll", ctypes.c_double), ("grad_max", ctypes.c_double), ("cg_eps", ctypes.c_double),
+                ("cg_res", ctypes.c_double), ("step", ctypes.c_double), ("dir_deriv", ctypes.c_double),
+                ("cg_iters", ctypes.c_int), ("cg_exit", ctypes.c_int), ("n_fev", ctypes.c_int),
+                ("hessian", ctypes.c_int)]
+
+
 class pwa_fit_opts(ctypes.Structure):
     _fields_ = [("xtol", ctypes.c_double), ("gtol", ctypes.c_double), ("maxiter", ctypes.c_int),
-                ("cg_maxiter", ctypes.c_int), ("time_limit_s", ctypes.c_double)]
+                ("cg_maxiter", ctypes.c_int), ("time_limit_s", ctypes.c_double), ("trace_cap", ctypes.c_int),
+                ("trace", ctypes.POINTER(pwa_fit_iter))]
 
 
 class pwa_lineshape(ctypes.Structure):
@@ -47,7 +55,27 @@ class pwa_lineshape(ctypes.Structure):
 class pwa_fit_result(ctypes.Structure):
     _fields_ = [("nll", ctypes.c_double), ("grad_max", ctypes.c_double), ("iters", ctypes.c_int),
                 ("n_hvp", ctypes.c_int), ("n_fev", ctypes.c_int), ("status", ctypes.c_int),
-                ("elapsed_s", ctypes.c_double)]
+                ("elapsed_s", ctypes.c_double), ("n_trace", ctypes.c_int)]
+
+
+_TRACE_KEYS = ("nll", "grad_max", "cg_eps", "cg_res", "step", "dir_deriv", "cg_iters", "cg_exit", "n_fev",
+               "hessian")
+
+
+def _attach_trace(opts: pwa_fit_opts, n_fits: int, cap: int):
+    """Give opts a per-fit trace buffer of cap records (kept alive by the return value)."""
+    if cap <= 0:
+        return None
+    buf = (pwa_fit_iter * (n_fits * cap))()
+    opts.trace_cap = cap
+    opts.trace = ctypes.cast(buf, ctypes.POINTER(pwa_fit_iter))
+    return buf
+
+
+def _read_trace(buf, cap: int, row: int, n: int):
+    if buf is None:
+        return None
+    return [{k: getattr(buf[row * cap + i], k) for k in _TRACE_KEYS} for i in range(n)]
 
 
 class PwaError(RuntimeError):
@@ -331,32 +359,42 @@ class Likelihood:
 
     # -- fitting --
     def fit(self, theta0, xtol: float = 1e-8, gtol: float = 0.0, maxiter: int = 0, cg_maxiter: int = 0,
-            time_limit_s: float = 0.0):
+            time_limit_s: float = 0.0, trace: int = 0):
+        """Newton-CG fit from theta0; with trace > 0 the info dict carries the
+        first `trace` outer iterations' records under "trace"."""
         th = _f64(theta0, self.P)
         out = np.empty(self.P)
         opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s)
+        tbuf = _attach_trace(opts, 1, trace)
         res = pwa_fit_result()
         st = lib().pwa_newton_cg_fit(self._h, _dptr(th), ctypes.byref(opts), _dptr(out), ctypes.byref(res))
         if st not in (PWA_OK, PWA_ENOCONV):
             self._check(st)
-        return out, {"nll": res.nll, "grad_max": res.grad_max, "iters": res.iters, "n_hvp": res.n_hvp,
-                     "n_fev": res.n_fev, "status": FIT_STATUS_NAMES[res.status], "elapsed_s": res.elapsed_s,
-                     "converged": st == PWA_OK}
+        info = {"nll": res.nll, "grad_max": res.grad_max, "iters": res.iters, "n_hvp": res.n_hvp,
+                "n_fev": res.n_fev, "status": FIT_STATUS_NAMES[res.status], "elapsed_s": res.elapsed_s,
+                "converged": st == PWA_OK}
+        if tbuf is not None:
+            info["trace"] = _read_trace(tbuf, trace, 0, res.n_trace)
+        return out, info
 
     def fit_batch(self, thetas0, xtol: float = 1e-8, gtol: float = 0.0, maxiter: int = 0, cg_maxiter: int = 0,
-                  time_limit_s: float = 0.0):
+                  time_limit_s: float = 0.0, trace: int = 0):
         """B fits (rows of thetas0) in lockstep with batched passes; returns
         (theta [B, P], list of per-fit info dicts, converged-or-time-limit for all)."""
         th = _f64(thetas0).reshape(-1, self.P)
         B = th.shape[0]
         out = np.empty((B, self.P))
         opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s)
+        tbuf = _attach_trace(opts, B, trace)
         res = (pwa_fit_result * B)()
         st = lib().pwa_newton_cg_fit_batch(self._h, B, _dptr(th), ctypes.byref(opts), _dptr(out), res)
         if st not in (PWA_OK, PWA_ENOCONV):
             self._check(st)
         infos = [{"nll": r.nll, "grad_max": r.grad_max, "iters": r.iters, "n_hvp": r.n_hvp, "n_fev": r.n_fev,
                   "status": FIT_STATUS_NAMES[r.status], "elapsed_s": r.elapsed_s} for r in res]
+        if tbuf is not None:
+            for b, (r, info) in enumerate(zip(res, infos)):
+                info["trace"] = _read_trace(tbuf, trace, b, r.n_trace)
         return out, infos, st == PWA_OK
 
     # -- tiling --

@@ -225,12 +225,17 @@ __global__ void __launch_bounds__(kCT + 32, 1) coupling_kernel(const CpArgs a)
         }
     };
 
+    // phases armed on each asynchronous barrier by the producer lane (TMA copies,
+    // MMA commits): a CTA that gives up drains exactly the last phase of each
+    int nA[2] = {0, 0}, nB[2] = {0, 0}, nG1[2] = {0, 0}, nG2 = 0;
     if (producer) {
         // ======== producer: one lane issues everything ========
         if (lane == 0) {
             for (int i = 0; i < 2 && i < nmine; ++i) {
                 issue_A(i, i);
                 issue_B(i, i);
+                ++nA[i];
+                ++nB[i];
             }
             for (int i = 0; i <= nmine && !s_abort; ++i) {
                 if (i < nmine) {
@@ -254,6 +259,7 @@ __global__ void __launch_bounds__(kCT + 32, 1) coupling_kernel(const CpArgs a)
                         mma_bf16(dc, ad[2], bd[0], idesc1, 1);
                     }
                     mma_commit(&g1[st]);
+                    ++nG1[st];
                 }
                 if (i >= 1) {
                     const int p = i - 1, sp = p & 1;
@@ -263,6 +269,7 @@ __global__ void __launch_bounds__(kCT + 32, 1) coupling_kernel(const CpArgs a)
                     if (p + 2 < nmine) {
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                         issue_A(p + 2, sp);
+                        ++nA[sp];
                     }
                     if (!wait_bar(&tmaB[sp], (uint32_t)((p >> 1) & 1))) break;
                     const uint32_t ab = sa(wt), bb = sa(sB[sp]);
@@ -280,11 +287,13 @@ __global__ void __launch_bounds__(kCT + 32, 1) coupling_kernel(const CpArgs a)
                         mma_bf16(tD2c, ad[2], bd[0], idesc2, 1);
                     }
                     mma_commit(g2);
+                    ++nG2;
                     // its transposed-U stage is refilled once GEMM2(p) has read it
                     if (p + 2 < nmine) {
                         if (!wait_bar(g2, (uint32_t)(p & 1))) break;
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                         issue_B(p + 2, sp);
+                        ++nB[sp];
                     }
                 }
             }
@@ -440,15 +449,22 @@ __global__ void __launch_bounds__(kCT + 32, 1) coupling_kernel(const CpArgs a)
         const int h = tid / kCH, cc = tid % kCH;  // vector tid: warps 4 h .. 4 h + 3
         rs[tid] = ((s_red[4 * h][cc] + s_red[4 * h + 1][cc]) + s_red[4 * h + 2][cc]) + s_red[4 * h + 3][cc];
     }
-    // a CTA that gave up waits (bounded, each barrier once) for the work it started before freeing TMEM
+    // A CTA that gave up waits (bounded) for the last phase it armed on each
+    // barrier -- every earlier phase of a barrier completed before the
+    // producer armed the next one -- so that no TMA copy or MMA still writes
+    // shared memory or TMEM when TMEM is freed and the CTA exits.  Barriers
+    // never armed are skipped.
     if (s_abort && producer && lane == 0) {
         s_abort = 0;  // let the drain waits run their course
         for (int q = 0; q < 2; ++q) {
-            (void)wait_bar(&g1[q], 0);
-            (void)wait_bar(&tmaA[q], 0);
-            (void)wait_bar(&tmaB[q], 0);
+            if (nG1[q] > 0) (void)wait_bar(&g1[q], (uint32_t)((nG1[q] - 1) & 1));
+            s_abort = 0;
+            if (nA[q] > 0) (void)wait_bar(&tmaA[q], (uint32_t)((nA[q] - 1) & 1));
+            s_abort = 0;
+            if (nB[q] > 0) (void)wait_bar(&tmaB[q], (uint32_t)((nB[q] - 1) & 1));
+            s_abort = 0;
         }
-        (void)wait_bar(g2, 0);
+        if (nG2 > 0) (void)wait_bar(g2, (uint32_t)((nG2 - 1) & 1));
         s_abort = 1;
     }
     tc_fence_before();

@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(kCgThreads) cg_step_kernel(DevCG c, int P, int
         if (threadIdx.x == 0) {
             c.flags[0] = 2;
             c.flags[1] = j + 1;
+            c.scal[0] = rr_new;
         }
         return;
     }
@@ -127,6 +128,7 @@ __global__ void __launch_bounds__(kCgThreads) cg_step_kernel(DevCG c, int P, int
         if (threadIdx.x == 0) {
             c.flags[0] = 3;
             c.flags[1] = j + 1;
+            c.scal[0] = rr_new;
         }
         return;
     }
@@ -191,7 +193,7 @@ struct DeviceCG {
 
     // p = approximate solution of H p = -g at x (inner loop of Algorithm 7.1)
     pwa_status solve(const std::vector<double>& x, const std::vector<double>& g, double eps, int maxiter,
-                     std::vector<double>& p, int& n_hvp)
+                     std::vector<double>& p, int& n_hvp, pwa_fit_iter* rec)
     {
         if (!exec) {
             pwa_status st = capture(maxiter);
@@ -218,9 +220,16 @@ struct DeviceCG {
         }
         n_hvp += flags[2];
         e = cudaMemcpyAsync(pin, c.z, sizeof(double) * P, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(pin + P, c.scal, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return pwa::cuda_error(h, e, "CG download");
         p.assign(pin, pin + P);
+        if (rec) {
+            rec->cg_iters = flags[2];
+            rec->cg_exit = flags[0];
+            rec->cg_res = std::sqrt(pin[P]);
+        }
         return pwa::check_device_errors(h);
     }
 
@@ -286,6 +295,9 @@ struct FitState {
     double* rhv = nullptr;       // HV: H v
     double cg_eps = 0.0;         // CG: solve H p = -g at (x, g) to |r| < cg_eps into p
     pwa_status req_status = PWA_OK;
+    // per-iteration records (opts.trace); cur_it is the one being filled
+    std::vector<pwa_fit_iter> trace;
+    pwa_fit_iter cur_it{};
     // outcome of the fit
     pwa_status error = PWA_OK;  // an evaluation failed (the fit stopped there)
     int status = PWA_FIT_MAXITER, iters = 0, n_fev = 0, n_hvp = 0;
@@ -325,6 +337,12 @@ struct Suspend {
     void await_resume() const noexcept {}
 };
 
+// the record of the current iteration goes to the trace when it ends
+void push_iter(FitState& s)
+{
+    if ((int)s.trace.size() < s.o.trace_cap) s.trace.push_back(s.cur_it);
+}
+
 FitTask newton_cg(FitState& s)
 {
     const int n = s.P;
@@ -351,6 +369,10 @@ FitTask newton_cg(FitState& s)
         // ---- inner CG on H p = -g (N&W Algorithm 7.1) ----
         const double gnorm = std::sqrt(dot(s.g, s.g));
         const double eps = std::min(0.5, std::sqrt(gnorm)) * gnorm;
+        s.cur_it = pwa_fit_iter();
+        s.cur_it.nll = s.f;
+        s.cur_it.grad_max = gmax;
+        s.cur_it.cg_eps = eps;
         if (s.device_cg) {
             s.req = Req::CG;
             s.cg_eps = eps;
@@ -377,12 +399,15 @@ FitTask newton_cg(FitState& s)
                     co_return;
                 }
                 ++s.n_hvp;
+                s.cur_it.cg_iters = j + 1;
                 const double curv = dot(d, Hd);
                 if (!(curv > 0.0)) {  // negative curvature: steepest descent first, else the iterate
                     if (j == 0)
                         for (int i = 0; i < n; ++i) s.p[i] = -s.g[i];
                     else
                         s.p = z;
+                    s.cur_it.cg_exit = 1;
+                    s.cur_it.cg_res = std::sqrt(rr);
                     break;
                 }
                 const double alpha = rr / curv;
@@ -394,6 +419,8 @@ FitTask newton_cg(FitState& s)
                 }
                 if (std::sqrt(rr_new) < eps || j + 1 >= s.cg_maxiter) {
                     s.p = z;
+                    s.cur_it.cg_exit = std::sqrt(rr_new) < eps ? 2 : 3;
+                    s.cur_it.cg_res = std::sqrt(rr_new);
                     break;
                 }
                 const double beta = rr_new / rr;
@@ -407,6 +434,7 @@ FitTask newton_cg(FitState& s)
         pmean /= std::max(n, 1);
         if (pmean <= s.o.xtol) {
             s.status = PWA_FIT_XTOL;
+            push_iter(s);
             break;
         }
         double df0 = dot(s.g, s.p);
@@ -414,6 +442,7 @@ FitTask newton_cg(FitState& s)
             for (int i = 0; i < n; ++i) s.p[i] = -s.g[i];
             df0 = dot(s.g, s.p);
         }
+        s.cur_it.dir_deriv = df0;
         // ---- strong-Wolfe line search (N&W Algorithms 3.5 / 3.6) ----
         // bracketing from a = 1 (doubling), then zoom with safeguarded cubic
         // interpolation; one trial point per suspension
@@ -499,10 +528,14 @@ FitTask newton_cg(FitState& s)
                 if (std::fabs(hi.a - lo.a) < 1e-14 * std::max(1.0, std::fabs(lo.a))) break;
             }
         }
+        s.cur_it.n_fev = bracket_it + zoom_it;
         if (!ok) {
             s.status = std::fabs(df0) <= 1e-7 * (1.0 + std::fabs(f0)) ? PWA_FIT_PRECISION : PWA_FIT_LINESEARCH;
+            push_iter(s);
             break;
         }
+        s.cur_it.step = found.a;
+        push_iter(s);
         double smean = 0.0;
         for (int i = 0; i < n; ++i) smean += std::fabs(found.x[i] - s.x[i]);
         smean /= std::max(n, 1);
@@ -545,6 +578,14 @@ void fill_result(const FitState& s, pwa_fit_result* r)
     r->n_fev = s.n_fev;
     r->status = s.error != PWA_OK ? PWA_FIT_ERROR : s.status;
     r->elapsed_s = s.elapsed;
+    r->n_trace = (int)s.trace.size();
+}
+
+// copy a fit's records into the caller's trace rows (fit b of a group)
+void copy_trace(const FitState& s, int b)
+{
+    if (!s.o.trace || s.o.trace_cap <= 0 || s.trace.empty()) return;
+    std::memcpy(s.o.trace + (size_t)b * s.o.trace_cap, s.trace.data(), sizeof(pwa_fit_iter) * s.trace.size());
 }
 
 bool fit_converged(const FitState& s)
@@ -929,7 +970,7 @@ pwa_status run_lockstep(std::vector<std::unique_ptr<FitGroup>>& groups)
 }
 
 // Results of a group; all_ok stays true when every fit converged or hit its time limit.
-pwa_status close_group(FitGroup& g, double* theta_out, pwa_fit_result* results, bool& all_ok)
+pwa_status close_group(FitGroup& g, double* theta_out, pwa_fit_result* results, bool& all_ok, int trace_row0 = 0)
 {
     const int P = g.P;
     for (int b = 0; b < g.B; ++b)
@@ -937,6 +978,7 @@ pwa_status close_group(FitGroup& g, double* theta_out, pwa_fit_result* results, 
     for (int b = 0; b < g.B; ++b) {
         std::memcpy(theta_out + (size_t)b * P, g.fits[b].x.data(), sizeof(double) * P);
         if (results) fill_result(g.fits[b], results + b);
+        copy_trace(g.fits[b], trace_row0 + b);
         all_ok &= fit_converged(g.fits[b]);
     }
     return PWA_OK;
@@ -952,6 +994,8 @@ extern "C" void pwa_fit_opts_default(pwa_fit_opts* o)
     o->maxiter = 0;
     o->cg_maxiter = 0;
     o->time_limit_s = 0.0;
+    o->trace_cap = 0;
+    o->trace = nullptr;
 }
 
 extern "C" pwa_status pwa_newton_cg_fit(pwa_handle* h, const double* theta0, const pwa_fit_opts* opts_in,
@@ -979,7 +1023,7 @@ extern "C" pwa_status pwa_newton_cg_fit(pwa_handle* h, const double* theta0, con
                 if (s.req_status == PWA_ENONFINITE) h->err.clear();
                 break;
             case Req::CG:
-                s.req_status = cg.solve(s.x, s.g, s.cg_eps, s.cg_maxiter, s.p, s.n_hvp);
+                s.req_status = cg.solve(s.x, s.g, s.cg_eps, s.cg_maxiter, s.p, s.n_hvp, &s.cur_it);
                 break;
             default:
                 s.req_status = pwa::set_error(h, PWA_EINVAL, "internal: unexpected fit request");
@@ -990,6 +1034,7 @@ extern "C" pwa_status pwa_newton_cg_fit(pwa_handle* h, const double* theta0, con
     if (task.failed()) return pwa::set_error(h, PWA_ENOMEM, "host exception in the fit");
     std::memcpy(theta_out, s.x.data(), sizeof(double) * s.P);
     fill_result(s, result);
+    copy_trace(s, 0);
     if (s.error != PWA_OK) {
         if (s.error == PWA_ENONFINITE)
             return pwa::set_error(h, PWA_ENONFINITE, "non-finite NLL at the start point");
@@ -1028,9 +1073,11 @@ extern "C" pwa_status pwa_newton_cg_fit_multi(int n_handles, pwa_handle* const* 
     pwa_status st = run_lockstep(groups);
     if (st != PWA_OK) return st;
     bool all_ok = true;
+    int row0 = 0;  // trace rows run over the fits of all handles in order
     for (int i = 0; i < n_handles; ++i) {
-        st = close_group(*groups[i], theta_out[i], results ? results[i] : nullptr, all_ok);
+        st = close_group(*groups[i], theta_out[i], results ? results[i] : nullptr, all_ok, row0);
         if (st != PWA_OK) return st;
+        row0 += B[i];
     }
     return all_ok ? PWA_OK : PWA_ENOCONV;
 }

@@ -64,22 +64,6 @@ extern "C" pwa_status pwa_eval_device_noalloc(pwa_handle* h, const double* d_the
         return pwa::set_error(h, PWA_EINVAL, "d_theta, d_out (and d_v for hv) must not be NULL");
     const pwa::Tiling& t = h->tiling;
     const int mode = want_hv ? pwa::MODE_HVP : (want_grad ? pwa::MODE_GRAD : pwa::MODE_NLL);
-    pwa::KernelFn fn = nullptr;
-    switch (h->S) {
-#define PWA_NOALLOC_PICK(s)                                                              \
-    case s:                                                                              \
-        fn = mode == pwa::MODE_HVP   ? pwa::pick_pass_hvp_s##s(t.W, t.KPW)               \
-             : mode == pwa::MODE_GRAD ? pwa::pick_pass_grad_s##s(t.W, t.KPW)             \
-                                      : pwa::pick_pass_nll_s##s(t.W, t.KPW);             \
-        break;
-        PWA_NOALLOC_PICK(1)
-        PWA_NOALLOC_PICK(2)
-        PWA_NOALLOC_PICK(3)
-        PWA_NOALLOC_PICK(4)
-#undef PWA_NOALLOC_PICK
-        default: break;
-    }
-    if (!fn) return pwa::set_error(h, PWA_EINVAL, "no kernel for this shape");
 
     // scratch layout: block partials | group partials | counters (ngroups + 1)
     const size_t rec = (size_t)h->rec_len;
@@ -99,40 +83,11 @@ extern "C" pwa_status pwa_eval_device_noalloc(pwa_handle* h, const double* d_the
     cudaError_t e = cudaMemsetAsync(counts, 0, count_bytes, h->stream);
     if (e != cudaSuccess) return pwa::cuda_error(h, e, "clearing the scratch counters");
 
-    pwa::PassArgs a;
-    for (int s = 0; s < 2; ++s) {
-        a.tiles[s] = h->d_tiles[s];
-        a.tile_bytes[s] = h->tile_bytes[s];
-        a.ntiles[s] = h->ntiles[s];
-        a.nev[s] = h->n[s];
-    }
-    a.K = h->K;
-    a.E = t.E;
-    a.H = t.H;
-    a.W = t.W;
-    a.NST = t.NST;
-    a.stage_bytes = t.stage_bytes;
-    a.P = h->P;
-    a.res = h->d_res;
-    a.theta = d_theta;
-    a.v = want_hv ? d_v : nullptr;
-    a.Nd = h->Nd;
-    a.Nmc = h->Nmc;
-    a.B = 1;
-    a.Gb = t.grid;
+    // the handle's pass arguments with the reduction scratch moved into the array
+    pwa::PassArgs a = pwa::pass_args(h, d_theta, want_hv ? d_v : nullptr, d_out);
     a.block_rec = reinterpret_cast<double*>(base);
     a.group_rec = reinterpret_cast<double*>(base + block_bytes);
     a.group_count = counts;
     a.top_count = counts + h->ngroups;
-    a.group_size = h->group_size;
-    a.ngroups = h->ngroups;
-    a.rec_len = h->rec_len;
-    a.out = d_out;
-    a.bad = h->d_bad;
-    a.err = h->d_err;
-    a.timeout_cycles = h->timeout_cycles;
-    fn<<<t.grid, 32 * t.W, t.smem, h->stream>>>(a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return pwa::cuda_error(h, e, "pass kernel launch");
-    return PWA_OK;
+    return pwa::launch_pass_args(h, a, mode);
 }

@@ -492,8 +492,12 @@ pwa_status cuda_error(pwa_handle* h, cudaError_t e, const char* what)
     return set_error(h, PWA_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-pwa_status launch_pass(pwa_handle* h, const double* d_theta, const double* d_v, double* d_out, int mode,
-                       const int* skip)
+PassArgs pass_args(pwa_handle* h, const double* d_theta, const double* d_v, double* d_out)
+{
+    return make_args(h, d_theta, d_v, d_out);
+}
+
+pwa_status launch_pass_args(pwa_handle* h, const PassArgs& a, int mode)
 {
     if (h->broken) return set_error(h, PWA_ETIMEOUT, "handle is unusable after a device-side timeout");
     KernelFn fn = pick_kernel(mode, h->S, h->tiling.W, h->tiling.KPW);
@@ -505,12 +509,18 @@ pwa_status launch_pass(pwa_handle* h, const double* d_theta, const double* d_v, 
         if (h->tile_bytes[s] > t.stage_bytes || (long long)h->ntiles[s] * t.E < h->n[s] ||
             h->tile_bytes[s] % 16 != 0)
             return set_error(h, PWA_EINVAL, "inconsistent tile geometry");
-    PassArgs a = make_args(h, d_theta, d_v, d_out);
-    a.skip = skip;
     fn<<<h->tiling.grid, 32 * h->tiling.W, h->tiling.smem, h->stream>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(h, e, "pass kernel launch");
     return PWA_OK;
+}
+
+pwa_status launch_pass(pwa_handle* h, const double* d_theta, const double* d_v, double* d_out, int mode,
+                       const int* skip)
+{
+    PassArgs a = make_args(h, d_theta, d_v, d_out);
+    a.skip = skip;
+    return launch_pass_args(h, a, mode);
 }
 
 // ---- batched evaluation: B parameter vectors share one launch ----

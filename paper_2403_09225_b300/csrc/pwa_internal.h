@@ -107,6 +107,11 @@ PWA_DECLARE_PICK(hvp)
 // skip: optional device flag; the pass does nothing when it is non-zero at launch.
 pwa_status launch_pass(pwa_handle* h, const double* d_theta, const double* d_v, double* d_out, int mode,
                        const int* skip = nullptr);
+// The arguments of one single-vector pass on the handle's own scratch, and the
+// launch of a pass with given arguments (after the tile-geometry checks every
+// launch runs); launch_pass is the two in a row.
+PassArgs pass_args(pwa_handle* h, const double* d_theta, const double* d_v, double* d_out);
+pwa_status launch_pass_args(pwa_handle* h, const PassArgs& a, int mode);
 // Enqueue one fused pass for B parameter vectors (theta, v: device [B][P]; out:
 // device [B][1 + 2P]); grows the batch scratch when needed.
 // err_vec: clear and fill the per-vector error words h->batch.d_err_vec [B].
