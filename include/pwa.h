@@ -119,6 +119,12 @@ typedef struct {
     int maxiter;          /* outer iterations (0: 200 P)                            */
     int cg_maxiter;       /* inner CG iterations per outer step (0: 20 P)           */
     double time_limit_s;  /* wall-clock limit, 0: none (the paper uses 500 s)       */
+    int matrix_free;      /* 1: every inner CG step is one fused H v pass (the
+                             paper's setup); 0: one Hessian pass (pwa_hessian)
+                             per outer iteration and the CG on its products --
+                             the same iteration, far fewer passes over F (the
+                             default; handles with K > 44 and the coupling and
+                             variant fits always run matrix-free)            */
     int trace_cap;        /* records per fit that trace can hold (0: no trace)      */
     pwa_fit_iter* trace;  /* host [fits][trace_cap] or NULL: per-iteration record;
                              fits are numbered in the order of theta0 (over all
@@ -147,6 +153,7 @@ typedef struct {
     int status;       /* pwa_fit_status                                    */
     double elapsed_s; /* wall-clock seconds inside the call                */
     int n_trace;      /* iterations recorded in opts->trace (<= trace_cap) */
+    int n_hess;       /* Hessian passes (one pass over F each)             */
 } pwa_fit_result;
 
 /* Build a likelihood handle.  Copies data and MC events to the device and
@@ -161,6 +168,19 @@ pwa_status pwa_create(pwa_handle** out, const pwa_events* data, const pwa_events
 /* Message of the last pwa_create failure in this thread ("" if none). */
 const char* pwa_last_create_error(void);
 
+/* Free the device copies of the caller's events in the ABI layout that
+ * pwa_create keeps beside the tiled layout the passes stream (no counterpart
+ * in the paper: a memory option).  Halves the handle's device memory (2 x F
+ * -> 1 x F plus the tiles' m^2 and w); afterwards the tiling is fixed
+ * (pwa_set_tiling and pwa_autotune return PWA_EINVAL) and pwa_coupling_create
+ * refuses the handle.  Every pass, the Hessian pass and the fits are
+ * unaffected.  Idempotent. */
+pwa_status pwa_release_event_copies(pwa_handle* h);
+
+/* Device bytes the handle holds: event copies (unless released), tiles,
+ * reduction and batch scratch, Hessian records. */
+pwa_status pwa_device_bytes(const pwa_handle* h, long long* out);
+
 /* Number of free parameters P (length of theta, grad, v, hv). */
 int pwa_num_params(const pwa_handle* h);
 
@@ -174,6 +194,17 @@ pwa_status pwa_grad(pwa_handle* h, const double* theta, double* nll_or_null, dou
 /* Hessian-vector product H v of NLL at theta (Eq. 7 contracted with v).
  * theta, v, hv: host [P]. */
 pwa_status pwa_hvp(pwa_handle* h, const double* theta, const double* v, double* hv);
+
+/* The full Hessian of NLL at theta (Eq. 7 written out without the
+ * contraction with a direction), with NLL and its gradient, from one pass
+ * over F.  Per event it accumulates weighted Gram matrices of the first
+ * derivatives of the coherent sums (B F and B^2 F for every resonance and
+ * projection) and of the adjoint terms B^p D_k, plus the resonance-diagonal
+ * second-derivative sums; the host combines them in FP64.  theta: host [P];
+ * nll, grad: host (either may be NULL); hess: host [P][P] row-major,
+ * symmetric.  Supported for K <= 44.  Errors: PWA_EINVAL (K > 44, non-finite
+ * theta), PWA_ENOMEM, PWA_ECUDA, PWA_ENONFINITE, PWA_ETIMEOUT. */
+pwa_status pwa_hessian(pwa_handle* h, const double* theta, double* nll, double* grad, double* hess);
 
 /* The fused pass: NLL, gradient and H v from one read of F.  Any of grad,
  * hv may be NULL (then the cheaper pass without them runs); v is required

@@ -15,6 +15,7 @@ Functions and the passages they follow:
   nll_grad_hvp     -ln L, its gradient and H v              Eqs. 4, 6, 7
   sample_sums      per-shard F_m, G_m and derivatives       Eq. 5
   hessian          full Hessian of -ln L                    Eq. 7
+  sharded_*        the same over event shards in workers    Eqs. 4-5 (shard sums add up)
   integral_matrix  Phi_kk' = sum_e sum_s conj(U_ks) U_k's   Eq. 1 (couplings factored out)
 """
 from __future__ import annotations
@@ -23,7 +24,7 @@ import ctypes
 import math
 import os
 import subprocess
-from concurrent.futures import ProcessPoolExecutor
+from concurrent.futures import ProcessPoolExecutor, as_completed
 from typing import Optional, Sequence
 
 import numpy as np
@@ -267,7 +268,17 @@ def sharded_nll_grad_hvp(model: Model, theta, v, data, mc, workers: int = 8, sha
         import multiprocessing as mp
         pool = ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
     try:
-        parts = list(pool.map(_shard_job, jobs))
+        # at most 2 x workers shards in flight (each submitted shard holds a
+        # pickled copy of its events); results are kept in shard order
+        parts = [None] * len(jobs)
+        pending = {}
+        nxt = 0
+        while nxt < len(jobs) or pending:
+            while nxt < len(jobs) and len(pending) < 2 * workers:
+                pending[pool.submit(_shard_job, jobs[nxt])] = nxt
+                nxt += 1
+            done = next(iter(as_completed(list(pending))))
+            parts[pending.pop(done)] = done.result()
     finally:
         if own:
             pool.shutdown()
@@ -275,6 +286,60 @@ def sharded_nll_grad_hvp(model: Model, theta, v, data, mc, workers: int = 8, sha
     sd = np.sum(parts[:nd_jobs], axis=0) if nd_jobs else np.zeros(2 + 8 * model.K + 1)
     sm = np.sum(parts[nd_jobs:], axis=0)
     return combine(model, sd, sm, mc.n)
+
+
+def sample_hessian(model: Model, theta, m2, F, w, is_data: bool) -> np.ndarray:
+    """Per-shard second-derivative sums (full 4K x 4K order): d2F_m for data
+    (sum w [d2I / I - dI dI^T / I^2]) and d2G_m for MC (sum d2I), Eq. 7."""
+    lib = _load()
+    m2, Fv, w = _events(m2, F, w)
+    K = model.K
+    out = np.empty((4 * K, 4 * K))
+    bad = lib.or_sample_hessian(K, model.S, _i(model.channels), _d(model.full(theta)), m2.shape[1], _f(m2), _f(w),
+                                _f(Fv), int(bool(is_data)), _d(out))
+    if bad >= 0:
+        raise OracleError(int(bad))
+    return out
+
+
+def _shard_hessian_job(args):
+    model, theta, m2, F, w, is_data = args
+    return sample_sums(model, theta, None, m2, F, w, is_data), sample_hessian(model, theta, m2, F, w, is_data)
+
+
+def sharded_hessian(model: Model, theta, data, mc, workers: int = 8, shard: int = 20_000,
+                    pool: Optional[ProcessPoolExecutor] = None):
+    """(NLL, grad, full Hessian) over event shards in spawned worker processes:
+    the shard sums add up (Eqs. 4-5) and Eq. 7 combines them,
+    H = -d2F + N_d [d2G / G - dG dG^T / G^2] (the combination or_hessian makes)."""
+    jobs = []
+    for s, is_data in ((data, True), (mc, False)):
+        for a in range(0, s.n, shard):
+            b = min(s.n, a + shard)
+            w = None if s.w is None else s.w[a:b]
+            jobs.append((model, np.asarray(theta), np.ascontiguousarray(s.m2[:, a:b]),
+                         np.ascontiguousarray(s.F[a:b]), w, is_data))
+    own = pool is None
+    if own:
+        import multiprocessing as mp
+        pool = ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+    try:
+        parts = list(pool.map(_shard_hessian_job, jobs))
+    finally:
+        if own:
+            pool.shutdown()
+    nd_jobs = sum(1 for j in jobs if j[5])
+    sd = np.sum([p[0] for p in parts[:nd_jobs]], axis=0)
+    sm = np.sum([p[0] for p in parts[nd_jobs:]], axis=0)
+    Hd = np.sum([p[1] for p in parts[:nd_jobs]], axis=0)
+    Hm = np.sum([p[1] for p in parts[nd_jobs:]], axis=0)
+    nll, grad, _ = combine(model, sd, sm, mc.n)
+    P4 = 4 * model.K
+    Nd, G = sd[1], sm[0]
+    dG = sm[2:2 + P4]
+    H = -Hd + Nd * (Hm / G - np.outer(dG, dG) / (G * G))
+    idx = model.free_index
+    return nll, grad, H[np.ix_(idx, idx)]
 
 
 def parameter_errors(H: np.ndarray) -> np.ndarray:

@@ -43,8 +43,8 @@ class pwa_fit_iter(ctypes.Structure):
 
 class pwa_fit_opts(ctypes.Structure):
     _fields_ = [("xtol", ctypes.c_double), ("gtol", ctypes.c_double), ("maxiter", ctypes.c_int),
-                ("cg_maxiter", ctypes.c_int), ("time_limit_s", ctypes.c_double), ("trace_cap", ctypes.c_int),
-                ("trace", ctypes.POINTER(pwa_fit_iter))]
+                ("cg_maxiter", ctypes.c_int), ("time_limit_s", ctypes.c_double), ("matrix_free", ctypes.c_int),
+                ("trace_cap", ctypes.c_int), ("trace", ctypes.POINTER(pwa_fit_iter))]
 
 
 class pwa_lineshape(ctypes.Structure):
@@ -55,7 +55,7 @@ class pwa_lineshape(ctypes.Structure):
 class pwa_fit_result(ctypes.Structure):
     _fields_ = [("nll", ctypes.c_double), ("grad_max", ctypes.c_double), ("iters", ctypes.c_int),
                 ("n_hvp", ctypes.c_int), ("n_fev", ctypes.c_int), ("status", ctypes.c_int),
-                ("elapsed_s", ctypes.c_double), ("n_trace", ctypes.c_int)]
+                ("elapsed_s", ctypes.c_double), ("n_trace", ctypes.c_int), ("n_hess", ctypes.c_int)]
 
 
 _TRACE_KEYS = ("nll", "grad_max", "cg_eps", "cg_res", "step", "dir_deriv", "cg_iters", "cg_exit", "n_fev",
@@ -85,7 +85,8 @@ class PwaError(RuntimeError):
 
 
 #: every symbol include/pwa.h declares
-EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "pwa_grad", "pwa_hvp",
+EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "pwa_grad", "pwa_hvp", "pwa_hessian", "pwa_release_event_copies",
+           "pwa_device_bytes",
            "pwa_eval", "pwa_eval_device", "pwa_eval_device_noalloc", "pwa_eval_batch", "pwa_eval_batch_device",
            "pwa_sync", "pwa_event_intensity", "pwa_newton_cg_fit", "pwa_newton_cg_fit_batch",
            "pwa_newton_cg_fit_multi", "pwa_autotune", "pwa_coupling_create", "pwa_coupling_num_params",
@@ -116,6 +117,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pwa_grad": (st, [H, dp, dp, dp]),
         "pwa_hvp": (st, [H, dp, dp, dp]),
         "pwa_eval": (st, [H, dp, dp, dp, dp, dp]),
+        "pwa_hessian": (st, [H, dp, dp, dp, dp]),
+        "pwa_release_event_copies": (st, [H]),
+        "pwa_device_bytes": (st, [H, ctypes.POINTER(ctypes.c_longlong)]),
         "pwa_eval_device": (st, [H, vp, vp, vp, i, i]),
         "pwa_eval_device_noalloc": (st, [H, vp, vp, vp, i, i]),
         "pwa_eval_batch": (st, [H, i, dp, dp, dp, dp, dp]),
@@ -290,6 +294,24 @@ class Likelihood:
         self._check(lib().pwa_hvp(self._h, _dptr(th), _dptr(vv), _dptr(hv)))
         return hv
 
+    def release_event_copies(self):
+        """Free the caller-layout event copies (the tiling becomes fixed)."""
+        self._check(lib().pwa_release_event_copies(self._h))
+
+    def device_bytes(self) -> int:
+        out = ctypes.c_longlong()
+        self._check(lib().pwa_device_bytes(self._h, ctypes.byref(out)))
+        return out.value
+
+    def hessian(self, theta):
+        """(NLL, gradient [P], Hessian [P, P]) at theta from one Hessian pass."""
+        th = _f64(theta, self.P)
+        f = ctypes.c_double()
+        g = np.empty(self.P)
+        H = np.empty((self.P, self.P))
+        self._check(lib().pwa_hessian(self._h, _dptr(th), ctypes.byref(f), _dptr(g), _dptr(H)))
+        return f.value, g, H
+
     def eval(self, theta, v=None):
         """(NLL, grad, H v) from one fused pass; H v is None when v is None."""
         th = _f64(theta, self.P)
@@ -359,39 +381,41 @@ class Likelihood:
 
     # -- fitting --
     def fit(self, theta0, xtol: float = 1e-8, gtol: float = 0.0, maxiter: int = 0, cg_maxiter: int = 0,
-            time_limit_s: float = 0.0, trace: int = 0):
+            time_limit_s: float = 0.0, trace: int = 0, matrix_free: bool = False):
         """Newton-CG fit from theta0; with trace > 0 the info dict carries the
-        first `trace` outer iterations' records under "trace"."""
+        first `trace` outer iterations' records under "trace".  matrix_free:
+        every CG step is one fused H v pass instead of a product with the
+        outer iteration's Hessian (pwa_hessian)."""
         th = _f64(theta0, self.P)
         out = np.empty(self.P)
-        opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s)
+        opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s, int(matrix_free))
         tbuf = _attach_trace(opts, 1, trace)
         res = pwa_fit_result()
         st = lib().pwa_newton_cg_fit(self._h, _dptr(th), ctypes.byref(opts), _dptr(out), ctypes.byref(res))
         if st not in (PWA_OK, PWA_ENOCONV):
             self._check(st)
         info = {"nll": res.nll, "grad_max": res.grad_max, "iters": res.iters, "n_hvp": res.n_hvp,
-                "n_fev": res.n_fev, "status": FIT_STATUS_NAMES[res.status], "elapsed_s": res.elapsed_s,
+                "n_fev": res.n_fev, "n_hess": res.n_hess, "status": FIT_STATUS_NAMES[res.status], "elapsed_s": res.elapsed_s,
                 "converged": st == PWA_OK}
         if tbuf is not None:
             info["trace"] = _read_trace(tbuf, trace, 0, res.n_trace)
         return out, info
 
     def fit_batch(self, thetas0, xtol: float = 1e-8, gtol: float = 0.0, maxiter: int = 0, cg_maxiter: int = 0,
-                  time_limit_s: float = 0.0, trace: int = 0):
+                  time_limit_s: float = 0.0, trace: int = 0, matrix_free: bool = False):
         """B fits (rows of thetas0) in lockstep with batched passes; returns
         (theta [B, P], list of per-fit info dicts, converged-or-time-limit for all)."""
         th = _f64(thetas0).reshape(-1, self.P)
         B = th.shape[0]
         out = np.empty((B, self.P))
-        opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s)
+        opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s, int(matrix_free))
         tbuf = _attach_trace(opts, B, trace)
         res = (pwa_fit_result * B)()
         st = lib().pwa_newton_cg_fit_batch(self._h, B, _dptr(th), ctypes.byref(opts), _dptr(out), res)
         if st not in (PWA_OK, PWA_ENOCONV):
             self._check(st)
         infos = [{"nll": r.nll, "grad_max": r.grad_max, "iters": r.iters, "n_hvp": r.n_hvp, "n_fev": r.n_fev,
-                  "status": FIT_STATUS_NAMES[r.status], "elapsed_s": r.elapsed_s} for r in res]
+                  "n_hess": r.n_hess, "status": FIT_STATUS_NAMES[r.status], "elapsed_s": r.elapsed_s} for r in res]
         if tbuf is not None:
             for b, (r, info) in enumerate(zip(res, infos)):
                 info["trace"] = _read_trace(tbuf, trace, b, r.n_trace)
@@ -467,7 +491,7 @@ class Coupling:
         if st not in (PWA_OK, PWA_ENOCONV):
             self._check(st)
         infos = [{"nll": r.nll, "grad_max": r.grad_max, "iters": r.iters, "n_hvp": r.n_hvp, "n_fev": r.n_fev,
-                  "status": FIT_STATUS_NAMES[r.status], "elapsed_s": r.elapsed_s} for r in res]
+                  "n_hess": r.n_hess, "status": FIT_STATUS_NAMES[r.status], "elapsed_s": r.elapsed_s} for r in res]
         return out, infos, st == PWA_OK
 
     def close(self):
@@ -483,7 +507,7 @@ class Coupling:
 
 
 def fit_multi(likelihoods, thetas0, xtol: float = 1e-8, gtol: float = 0.0, maxiter: int = 0,
-              cg_maxiter: int = 0, time_limit_s: float = 0.0):
+              cg_maxiter: int = 0, time_limit_s: float = 0.0, matrix_free: bool = False):
     """Lockstep fits over several likelihoods (one group of starts per
     likelihood; their batched passes run concurrently).  thetas0[i]: [B_i, P_i].
     Returns ([theta [B_i, P_i]], [[info per fit]], all converged-or-time-limit)."""
@@ -497,13 +521,13 @@ def fit_multi(likelihoods, thetas0, xtol: float = 1e-8, gtol: float = 0.0, maxit
     th_p = (dpp * n)(*[_dptr(t) for t in ths])
     out_p = (dpp * n)(*[_dptr(o) for o in outs])
     res_p = (ctypes.POINTER(pwa_fit_result) * n)(*[ctypes.cast(r, ctypes.POINTER(pwa_fit_result)) for r in res])
-    opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s)
+    opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s, int(matrix_free))
     st = lib().pwa_newton_cg_fit_multi(n, hs, Bs, th_p, ctypes.byref(opts), out_p, res_p)
     if st not in (PWA_OK, PWA_ENOCONV):
         msgs = "; ".join(filter(None, (lib().pwa_last_error(L._h).decode() for L in likelihoods)))
         raise PwaError(st, msgs)
     infos = [[{"nll": r.nll, "grad_max": r.grad_max, "iters": r.iters, "n_hvp": r.n_hvp, "n_fev": r.n_fev,
-               "status": FIT_STATUS_NAMES[r.status], "elapsed_s": r.elapsed_s} for r in rr] for rr in res]
+               "n_hess": r.n_hess, "status": FIT_STATUS_NAMES[r.status], "elapsed_s": r.elapsed_s} for r in rr] for rr in res]
     return outs, infos, st == PWA_OK
 
 
@@ -586,7 +610,7 @@ class Variant:
         if st not in (PWA_OK, PWA_ENOCONV):
             self._check(st)
         infos = [{"nll": r.nll, "grad_max": r.grad_max, "iters": r.iters, "n_hvp": r.n_hvp, "n_fev": r.n_fev,
-                  "status": FIT_STATUS_NAMES[r.status], "elapsed_s": r.elapsed_s} for r in res]
+                  "n_hess": r.n_hess, "status": FIT_STATUS_NAMES[r.status], "elapsed_s": r.elapsed_s} for r in res]
         return out, infos, st == PWA_OK
 
     # -- couplings only, at fixed line shapes (integral matrices of the MC events) --
@@ -627,7 +651,7 @@ class Variant:
         if st not in (PWA_OK, PWA_ENOCONV):
             self._check(st)
         infos = [{"nll": r.nll, "grad_max": r.grad_max, "iters": r.iters, "n_hvp": r.n_hvp, "n_fev": r.n_fev,
-                  "status": FIT_STATUS_NAMES[r.status], "elapsed_s": r.elapsed_s} for r in res]
+                  "n_hess": r.n_hess, "status": FIT_STATUS_NAMES[r.status], "elapsed_s": r.elapsed_s} for r in res]
         return out, infos, st == PWA_OK
 
     def close(self):

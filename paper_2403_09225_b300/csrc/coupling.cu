@@ -831,6 +831,9 @@ pwa_status pwa_coupling_create(pwa_handle* h, const double* theta, pwa_coupling*
     *out = nullptr;
     h->err.clear();
     if (!theta) return pwa::set_error(h, PWA_EINVAL, "theta must not be NULL");
+    if (h->released)
+        return pwa::set_error(h, PWA_EINVAL, "the events' caller-layout copies were released; the coupling "
+                                             "object is built from them");
     if (h->broken) return pwa::set_error(h, PWA_ETIMEOUT, "handle is unusable after a device-side timeout");
     const int K = h->K, S = h->S, P = h->P;
     for (int i = 0; i < P; ++i)

@@ -276,13 +276,15 @@ bool cubic_min(double a, double fa, double dfa, double b, double fb, double dfb,
 // arithmetic of the iteration is written once, here.
 // ---------------------------------------------------------------------------
 
-enum class Req { None, FG, HV, CG };
+enum class Req { None, FG, HV, CG, HESS };
 
 struct FitState {
     int P = 0;
     pwa_fit_opts o{};
     int maxiter = 0, cg_maxiter = 0;
     bool device_cg = false;  // CG requests (device graph) instead of HV requests
+    bool explicit_h = false; // one HESS request per outer iteration, the CG on its products
+    std::vector<double> H;   // [P][P] Hessian at x (explicit_h)
     std::chrono::steady_clock::time_point t_start;
     std::vector<double> x, g, p;
     double f = 0.0;
@@ -293,6 +295,7 @@ struct FitState {
     double* rf = nullptr;        // FG: f
     double* rg = nullptr;        // FG: g
     double* rhv = nullptr;       // HV: H v
+    double* rH = nullptr;        // HESS: the Hessian [P][P] at rx
     double cg_eps = 0.0;         // CG: solve H p = -g at (x, g) to |r| < cg_eps into p
     pwa_status req_status = PWA_OK;
     // per-iteration records (opts.trace); cur_it is the one being filled
@@ -300,7 +303,7 @@ struct FitState {
     pwa_fit_iter cur_it{};
     // outcome of the fit
     pwa_status error = PWA_OK;  // an evaluation failed (the fit stopped there)
-    int status = PWA_FIT_MAXITER, iters = 0, n_fev = 0, n_hvp = 0;
+    int status = PWA_FIT_MAXITER, iters = 0, n_fev = 0, n_hvp = 0, n_hess = 0;
     double elapsed = 0.0;
 
     double since_start() const
@@ -373,7 +376,20 @@ FitTask newton_cg(FitState& s)
         s.cur_it.nll = s.f;
         s.cur_it.grad_max = gmax;
         s.cur_it.cg_eps = eps;
-        if (s.device_cg) {
+        if (s.explicit_h) {
+            // one Hessian pass at x; every CG product below is a product with it
+            s.H.resize((size_t)n * n);
+            s.req = Req::HESS;
+            s.rx = s.x.data();
+            s.rH = s.H.data();
+            co_await Suspend{};
+            if (s.req_status != PWA_OK) {
+                s.error = s.req_status;
+                co_return;
+            }
+            s.cur_it.hessian = 1;
+        }
+        if (s.device_cg && !s.explicit_h) {
             s.req = Req::CG;
             s.cg_eps = eps;
             co_await Suspend{};
@@ -389,16 +405,25 @@ FitTask newton_cg(FitState& s)
             for (int i = 0; i < n; ++i) d[i] = -r[i];
             double rr = dot(r, r);
             for (int j = 0;; ++j) {
-                s.req = Req::HV;
-                s.rx = s.x.data();
-                s.rv = d.data();
-                s.rhv = Hd.data();
-                co_await Suspend{};
-                if (s.req_status != PWA_OK) {
-                    s.error = s.req_status;
-                    co_return;
+                if (s.explicit_h) {
+                    for (int i = 0; i < n; ++i) {
+                        const double* Hi = s.H.data() + (size_t)i * n;
+                        double acc = 0.0;
+                        for (int l = 0; l < n; ++l) acc += Hi[l] * d[l];
+                        Hd[i] = acc;
+                    }
+                } else {
+                    s.req = Req::HV;
+                    s.rx = s.x.data();
+                    s.rv = d.data();
+                    s.rhv = Hd.data();
+                    co_await Suspend{};
+                    if (s.req_status != PWA_OK) {
+                        s.error = s.req_status;
+                        co_return;
+                    }
+                    ++s.n_hvp;
                 }
-                ++s.n_hvp;
                 s.cur_it.cg_iters = j + 1;
                 const double curv = dot(d, Hd);
                 if (!(curv > 0.0)) {  // negative curvature: steepest descent first, else the iterate
@@ -560,6 +585,7 @@ void init_state(FitState& s, int n, const double* theta0, const pwa_fit_opts* op
     pwa_fit_opts_default(&s.o);
     if (opts_in) s.o = *opts_in;
     s.maxiter = s.o.maxiter > 0 ? s.o.maxiter : 200 * n;
+    s.explicit_h = !s.o.matrix_free;  // the executor turns it off where no Hessian pass exists
     s.cg_maxiter = s.o.cg_maxiter > 0 ? s.o.cg_maxiter : 20 * n;
     s.x.assign(theta0, theta0 + n);
     s.g.assign(n, 0.0);
@@ -579,6 +605,7 @@ void fill_result(const FitState& s, pwa_fit_result* r)
     r->status = s.error != PWA_OK ? PWA_FIT_ERROR : s.status;
     r->elapsed_s = s.elapsed;
     r->n_trace = (int)s.trace.size();
+    r->n_hess = s.n_hess;
 }
 
 // copy a fit's records into the caller's trace rows (fit b of a group)
@@ -641,6 +668,9 @@ struct RoundEvaluator {
     virtual pwa_status reserve(int nb, double** theta, double** v) = 0;
     virtual pwa_status issue(int nb, bool any_hv) = 0;                      // asynchronous
     virtual pwa_status finish(int nb, const double** out, const int** err) = 0;  // waits
+    // the full Hessian at one point (synchronous), where the evaluator has a Hessian pass
+    virtual bool has_hessian() const { return false; }
+    virtual pwa_status hessian(const double* theta, double* H) { (void)theta; (void)H; return PWA_EINVAL; }
 };
 
 // a likelihood handle: pwa_eval_batch_device's pass on the handle's batch buffers.
@@ -670,6 +700,13 @@ struct HandleRounds final : RoundEvaluator {
     }
     int P() const override { return h->P; }
     pwa_handle* handle() const override { return h; }
+    bool has_hessian() const override { return h->K <= pwa::kMaxKHessian; }
+    pwa_status hessian(const double* theta, double* H) override
+    {
+        pwa_status st = pwa::hessian_device(h, theta, nullptr, nullptr, H);
+        if (st == PWA_ENONFINITE) h->err.clear();
+        return st;
+    }
     pwa_status reserve(int nb, double** theta, double** v) override
     {
         pwa_status st = pwa::batch_io(h, nb);
@@ -898,6 +935,7 @@ pwa_status open_group(FitGroup& g, std::unique_ptr<RoundEvaluator> ev, int B, co
     g.tasks.reserve(B);
     for (int b = 0; b < B; ++b) {
         init_state(g.fits[b], P, theta0 + (size_t)b * P, opts);
+        g.fits[b].explicit_h &= g.ev->has_hessian();
         g.tasks.push_back(newton_cg(g.fits[b]));
         g.tasks[b].h.resume();  // runs to its first request
     }
@@ -908,6 +946,17 @@ pwa_status open_group(FitGroup& g, std::unique_ptr<RoundEvaluator> ev, int B, co
 // evaluation (H v for all when any asks for it, with v = 0 for the f, g requests).
 pwa_status issue_round(FitGroup& g)
 {
+    // Hessian requests first, one Hessian pass each (synchronous); each such
+    // fit then runs its CG on the host and posts its next request
+    for (int b = 0; b < g.B; ++b) {
+        FitState& s = g.fits[b];
+        while (!g.tasks[b].h.done() && s.req == Req::HESS) {
+            ++s.n_hess;
+            s.req_status = g.ev->hessian(s.rx, s.rH);
+            g.tasks[b].h.resume();
+            if (g.tasks[b].h.done()) s.elapsed = s.since_start();
+        }
+    }
     g.live.clear();
     for (int b = 0; b < g.B; ++b)
         if (!g.tasks[b].h.done()) g.live.push_back(b);
@@ -1006,6 +1055,7 @@ extern "C" pwa_status pwa_newton_cg_fit(pwa_handle* h, const double* theta0, con
     FitState s;
     init_state(s, h->P, theta0, opts_in);
     s.device_cg = true;
+    s.explicit_h &= h->K <= pwa::kMaxKHessian;
     FitStream fs;
     pwa_status st = fs.open(h);
     if (st != PWA_OK) return st;
@@ -1024,6 +1074,11 @@ extern "C" pwa_status pwa_newton_cg_fit(pwa_handle* h, const double* theta0, con
                 break;
             case Req::CG:
                 s.req_status = cg.solve(s.x, s.g, s.cg_eps, s.cg_maxiter, s.p, s.n_hvp, &s.cur_it);
+                break;
+            case Req::HESS:
+                ++s.n_hess;
+                s.req_status = pwa::hessian_device(h, s.rx, nullptr, nullptr, s.rH);
+                if (s.req_status == PWA_ENONFINITE) h->err.clear();
                 break;
             default:
                 s.req_status = pwa::set_error(h, PWA_EINVAL, "internal: unexpected fit request");

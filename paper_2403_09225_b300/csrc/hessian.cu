@@ -1,0 +1,682 @@
+// hessian.cu -- pwa_hessian: the full P x P Hessian of the NLL, with the NLL
+// and its gradient, from one pass over F.
+//
+// Eq. 7 of the paper contracts the Hessian of ln L with a direction; written
+// out without the contraction, every entry is a sum over events of products
+// of first derivatives plus a resonance-diagonal second-derivative term.  For
+// resonance k with parameters theta_k = (rho, phi, M, Gamma),
+//   dc_k/dtheta_kj = kappa1_j B_k + kappa2_j B_k^2,
+//   d2c_k/dtheta_kj dtheta_kj' = mu1 B_k + mu2 B_k^2 + mu3 B_k^3,
+// with theta-dependent complex coefficients (B_k = BW_k(e), c_k = g_k B_k).
+// With V_{(k,p),s}(e) = B_k^p F_{k,s}(e) (p = 1, 2) and D_k = sum_s conj(A_s) F_ks,
+//   sum_e a d2I/dtheta_i dtheta_j
+//       = 2 Re sum_{p,p'} conj(kappa_p,i) kappa_p',j C[(k_i,p), (k_j,p')]
+//         + delta_{k_i k_j} 2 Re (mu1 Q1 + mu2 Q2 + mu3 Q3)_k,
+//   C = sum_e a sum_s conj(V_s) V_s^T   (2K x 2K Hermitian Gram matrix),
+//   Qp_k = sum_e a B_k^p D_k,
+// and dI/dtheta_i = 2 Re (kappa1 Z1 + kappa2 Z2)_k with Zp_k = B_k^p D_k, so
+//   sum_data (w/I^2) dI/dtheta_i dI/dtheta_j = c_i^T Zg c_j,
+//   Zg = sum_data (w/I^2) z z^T  (z = Re, Im of Z: 4K reals per event).
+// The kernel therefore accumulates, per sample set, the real Gram matrix
+// X^T X of the rows (e, s) of X = sqrt(a) (Re V, Im V) (4K columns; its
+// entries give C), for data also Zg, and the sums Q1..Q3, sum w ln I and
+// G = sum_mc I.  The host combines them in FP64 with the coefficients into
+// H = -(sum_data (w/I) d2I - Zg) + N_d (sum_mc d2I / G - dG dG^T / G^2)
+// (Eqs. 4-7 with the data weight a = w/I, a = 1 for MC).
+//
+// Work split (one CTA of NT threads streams tiles of 32 events, the records
+// pwa_create lays out, by TMA bulk copies into two shared stages):
+//   phase 1: a warp per event, a lane per resonance: B, the coherent sums by a
+//            warp reduction, I, the weights; the lane writes its resonance's
+//            columns of X and z into shared memory and accumulates its Q sums;
+//   phase 2: every thread owns NB 4 x 4 blocks of the upper triangle of the
+//            4K x 4K Gram matrices and accumulates them over the tile's rows
+//            in FP32 registers.
+// FP32 sums are folded into per-CTA FP64 records every kFold tiles; a second
+// kernel adds the records in a fixed order (run-to-run bit-identical).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pwa_internal.h"
+
+namespace {
+
+using pwa::KConst;
+constexpr int kE = pwa::kTileE;  // events per tile
+constexpr int kFold = 16;        // tiles between FP32 -> FP64 folds
+constexpr int kMaxKHess = pwa::kMaxKHessian;  // K (K + 1) / 2 Gram blocks fit 2 per thread of 512
+
+struct HessArgs {
+    const unsigned char* tiles[2];  // data, MC tile records (the handle's layout)
+    uint32_t tile_bytes[2];
+    int ntiles[2];
+    long long nev[2];
+    int K;
+    int ev;                // events per warp of the tiling the records were laid out for
+    uint32_t stage_bytes;  // shared bytes per stage (16-byte multiple >= both tile records)
+    const pwa::ResParam* res;
+    const double* theta;   // device [P]
+    int nblk;              // 4 x 4 blocks in the upper triangle of the 4K x 4K Gram: K (K + 1) / 2
+    double* rec;           // [grid][rec_len] per-CTA FP64 sums (zeroed before the launch)
+    int rec_len;
+    unsigned long long* bad;
+    int* err;
+    long long timeout_cycles;
+};
+
+// Record layout of one CTA (FP64):
+//   [0, 16 nblk)           data Gram of X, block b's 16 entries row-major
+//   [16 nblk, 32 nblk)     data Gram of z
+//   [32 nblk, 48 nblk)     MC Gram of X
+//   then Q [2 sets][NW warps][K][6] (Re, Im of Q1, Q2, Q3), then the scalars
+//   [NW][2] (sum w ln I of the data, G = sum I of the MC) per warp
+__host__ __device__ inline int hess_rec_len(int K, int nblk, int NW) { return 48 * nblk + 12 * NW * K + 2 * NW; }
+
+// block index -> (bi, bj), bi <= bj, enumerating the upper triangle row by row
+__host__ __device__ inline void block_of(int b, int nb, int& bi, int& bj)
+{
+    int i = 0, rem = b;
+    while (rem >= nb - i) {
+        rem -= nb - i;
+        ++i;
+    }
+    bi = i;
+    bj = i + rem;
+}
+
+template <int S, int NT, int NB>
+__global__ void __launch_bounds__(NT, 1) hess_kernel(const HessArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int NW = NT / 32;
+    constexpr int EPW = kE / NW;  // events per warp in phase 1
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int K = a.K, C = 4 * K, XS = C + 4;  // X row stride in floats (16-byte rows)
+
+    // shared memory: stages[2] | KConst[K] | X [kE S][XS] | z [kE][XS] | mbarriers[2]
+    unsigned char* stages = smem;
+    KConst* kc = reinterpret_cast<KConst*>(smem + 2 * (size_t)a.stage_bytes);
+    float* X = reinterpret_cast<float*>(kc + K);
+    float* Zs = X + (size_t)kE * S * XS;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(Zs + (size_t)kE * XS);
+    __shared__ long long issued[2];
+    __shared__ int s_abort;
+
+    const int G = gridDim.x;
+    const long long T = (long long)a.ntiles[0] + a.ntiles[1];
+    auto tile_src = [&](long long t, int& smp, long long& lt) {
+        smp = t < a.ntiles[0] ? 0 : 1;
+        lt = smp ? t - a.ntiles[0] : t;
+    };
+    if (tid == 0) {
+        s_abort = 0;
+        for (int s = 0; s < 2; ++s) {
+            pwa::mbar_init(&mbar[s], 1);
+            issued[s] = -1;
+        }
+        pwa::fence_mbar_init();
+        for (int i = 0; i < 2; ++i) {
+            const long long t = blockIdx.x + (long long)i * G;
+            if (t < T) {
+                int smp;
+                long long lt;
+                tile_src(t, smp, lt);
+                pwa::tma_load_tile(stages + (size_t)i * a.stage_bytes, a.tiles[smp] + (size_t)lt * a.tile_bytes[smp],
+                                   a.tile_bytes[smp], &mbar[i]);
+                issued[i] = i;
+            }
+        }
+    }
+    {
+        pwa::PassArgs pa;
+        pa.res = a.res;
+        for (int k = tid; k < K; k += NT) kc[k] = pwa::make_kconst(pa, a.theta, nullptr, k, false, a.ev);
+    }
+    __syncthreads();
+
+    // this thread's Gram blocks
+    int bi[NB], bj[NB];
+#pragma unroll
+    for (int m = 0; m < NB; ++m) {
+        const int b = tid + m * NT;
+        if (b < a.nblk) block_of(b, K, bi[m], bj[m]);
+        else bi[m] = bj[m] = -1;
+    }
+    float R[NB][16], Zg[NB][16];
+#pragma unroll
+    for (int m = 0; m < NB; ++m)
+#pragma unroll
+        for (int u = 0; u < 16; ++u) R[m][u] = Zg[m][u] = 0.f;
+    // lane's resonances k = lane, lane + 32: Q sums (Re, Im of Q1, Q2, Q3)
+    float q[2][6];
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int u = 0; u < 6; ++u) q[j][u] = 0.f;
+    float sc = 0.f;
+
+    double* rec = a.rec + (size_t)blockIdx.x * a.rec_len;
+    const int offQ = 48 * a.nblk, offS = offQ + 12 * NW * K;
+    // add the FP32 sums of the current window to the FP64 record of sample set smp
+    auto fold = [&](int smp) {
+        const int offR = smp == 0 ? 0 : 32 * a.nblk;
+#pragma unroll
+        for (int m = 0; m < NB; ++m) {
+            if (bi[m] < 0) continue;
+            const int b = tid + m * NT;
+            double* rr = rec + offR + 16 * b;
+            double* rz = rec + 16 * a.nblk + 16 * b;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                rr[u] += (double)R[m][u];
+                R[m][u] = 0.f;
+                if (smp == 0) rz[u] += (double)Zg[m][u];
+                Zg[m][u] = 0.f;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int k = lane + 32 * j;
+            if (k < K) {
+                double* rq = rec + offQ + ((size_t)(smp * NW + warp) * K + k) * 6;
+#pragma unroll
+                for (int u = 0; u < 6; ++u) rq[u] += (double)q[j][u];
+            }
+#pragma unroll
+            for (int u = 0; u < 6; ++u) q[j][u] = 0.f;
+        }
+        const float s = pwa::warp_sum(sc);
+        sc = 0.f;
+        if (lane == 0) rec[offS + 2 * warp + smp] += (double)s;
+    };
+
+    int st = 0;
+    uint32_t ph = 0;
+    int win = 0;
+    int cur_smp = 0;
+    long long i = 0;
+    for (long long t = blockIdx.x; t < T; t += G, ++i) {
+        int smp;
+        long long lt;
+        tile_src(t, smp, lt);
+        if (smp != cur_smp) {  // the data tiles are done: their sums go to the data record
+            fold(0);
+            win = 0;
+            cur_smp = smp;
+        }
+        const bool ok = pwa::mbar_wait(&mbar[st], ph, a.timeout_cycles);
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) s_abort = 1;
+            break;
+        }
+        const float2* Fs = reinterpret_cast<const float2*>(stages + (size_t)st * a.stage_bytes);
+        const float* Ft = reinterpret_cast<const float*>(Fs);
+        const float* m2s = reinterpret_cast<const float*>(Fs + (size_t)K * S * kE);
+        const long long e_base = lt * kE;
+        const int nvalid = (int)min((long long)kE, a.nev[smp] - e_base);
+
+        // ---- phase 1: a warp per event, a lane per resonance ----
+        for (int ie = 0; ie < EPW; ++ie) {
+            const int e = warp * EPW + ie;
+            const bool valid = e < nvalid;
+            float br[2], bim[2], fr[2][S], fi[2][S];
+            float Ar[S], Ai[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) Ar[s] = Ai[s] = 0.f;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int k = lane + 32 * j;
+                br[j] = bim[j] = 0.f;
+#pragma unroll
+                for (int s = 0; s < S; ++s) fr[j][s] = fi[j][s] = 0.f;
+                if (k < K) {
+                    const KConst c = kc[k];
+                    pwa::breit_wigner(c, m2s[c.ch * kE + e], br[j], bim[j]);
+                    const float cr = c.gre * br[j] - c.gim * bim[j], ci = c.gre * bim[j] + c.gim * br[j];
+                    const int p = (e + c.shift) & (kE - 1);
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+                        const int o = pwa::f_re(k, s, p, S, kE);
+                        fr[j][s] = Ft[o];
+                        fi[j][s] = Ft[o + pwa::f_im_off(S)];
+                        Ar[s] += cr * fr[j][s] - ci * fi[j][s];
+                        Ai[s] += cr * fi[j][s] + ci * fr[j][s];
+                    }
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                Ar[s] = pwa::warp_sum(Ar[s]);
+                Ai[s] = pwa::warp_sum(Ai[s]);
+            }
+            float I = 0.f;
+#pragma unroll
+            for (int s = 0; s < S; ++s) I += Ar[s] * Ar[s] + Ai[s] * Ai[s];
+            float aw = 0.f, sqa = 0.f, zw = 0.f;
+            if (smp == 0) {
+                const float w = m2s[3 * kE + e];
+                const bool good = I > 0.f && I < INFINITY;
+                if (valid && good) {
+                    aw = w / I;
+                    sqa = sqrtf(aw);
+                    zw = sqrtf(w) / I;
+                    if (lane == 0) sc += w * logf(I);
+                } else if (valid && lane == 0) {
+                    atomicMin(a.bad, (unsigned long long)(e_base + e));
+                    atomicOr(a.err, pwa::ERR_NONFINITE);
+                }
+            } else {
+                const bool good = I < INFINITY;
+                if (valid && good) {
+                    aw = 1.f;
+                    sqa = 1.f;
+                    if (lane == 0) sc += I;
+                } else if (valid && lane == 0) {
+                    atomicMin(a.bad, (unsigned long long)(a.nev[0] + e_base + e));
+                    atomicOr(a.err, pwa::ERR_NONFINITE);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int k = lane + 32 * j;
+                if (k >= K) continue;
+                const float b1r = br[j], b1i = bim[j];
+                const float b2r = b1r * b1r - b1i * b1i, b2i = 2.f * b1r * b1i;
+                const float b3r = b2r * b1r - b2i * b1i, b3i = b2r * b1i + b2i * b1r;
+                float Dr = 0.f, Di = 0.f;  // D = sum_s conj(A_s) F_ks
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    Dr += Ar[s] * fr[j][s] + Ai[s] * fi[j][s];
+                    Di += Ar[s] * fi[j][s] - Ai[s] * fr[j][s];
+                    float* xr = X + (size_t)(e * S + s) * XS;
+                    // V1 = B F, V2 = B^2 F, weighted by sqrt(a)
+                    const float v1r = b1r * fr[j][s] - b1i * fi[j][s], v1i = b1r * fi[j][s] + b1i * fr[j][s];
+                    const float v2r = b2r * fr[j][s] - b2i * fi[j][s], v2i = b2r * fi[j][s] + b2i * fr[j][s];
+                    *reinterpret_cast<float2*>(xr + 2 * k) = make_float2(sqa * v1r, sqa * v1i);
+                    *reinterpret_cast<float2*>(xr + 2 * (K + k)) = make_float2(sqa * v2r, sqa * v2i);
+                }
+                const float z1r = b1r * Dr - b1i * Di, z1i = b1r * Di + b1i * Dr;
+                const float z2r = b2r * Dr - b2i * Di, z2i = b2r * Di + b2i * Dr;
+                const float z3r = b3r * Dr - b3i * Di, z3i = b3r * Di + b3i * Dr;
+                if (smp == 0) {
+                    float* zr = Zs + (size_t)e * XS;
+                    *reinterpret_cast<float2*>(zr + 2 * k) = make_float2(zw * z1r, zw * z1i);
+                    *reinterpret_cast<float2*>(zr + 2 * (K + k)) = make_float2(zw * z2r, zw * z2i);
+                }
+                q[j][0] = fmaf(aw, z1r, q[j][0]);
+                q[j][1] = fmaf(aw, z1i, q[j][1]);
+                q[j][2] = fmaf(aw, z2r, q[j][2]);
+                q[j][3] = fmaf(aw, z2i, q[j][3]);
+                q[j][4] = fmaf(aw, z3r, q[j][4]);
+                q[j][5] = fmaf(aw, z3i, q[j][5]);
+            }
+        }
+        __syncthreads();  // X and z complete; the stage has been read
+        if (tid == 0) {
+            const long long tn = t + 2LL * G;
+            if (tn < T) {
+                int s2;
+                long long lt2;
+                tile_src(tn, s2, lt2);
+                pwa::fence_proxy_async();
+                issued[st] = i + 2;
+                pwa::tma_load_tile(stages + (size_t)st * a.stage_bytes, a.tiles[s2] + (size_t)lt2 * a.tile_bytes[s2],
+                                   a.tile_bytes[s2], &mbar[st]);
+            }
+        }
+
+        // ---- phase 2: Gram blocks over the tile's rows ----
+#pragma unroll
+        for (int m = 0; m < NB; ++m) {
+            if (bi[m] < 0) continue;
+            const float* xi0 = X + 4 * bi[m];
+            const float* xj0 = X + 4 * bj[m];
+#pragma unroll 4
+            for (int r = 0; r < kE * S; ++r) {
+                const float4 xi = *reinterpret_cast<const float4*>(xi0 + (size_t)r * XS);
+                const float4 xj = *reinterpret_cast<const float4*>(xj0 + (size_t)r * XS);
+                const float u[4] = {xi.x, xi.y, xi.z, xi.w}, v[4] = {xj.x, xj.y, xj.z, xj.w};
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) R[m][4 * p + qq] = fmaf(u[p], v[qq], R[m][4 * p + qq]);
+            }
+            if (smp == 0) {
+                const float* zi0 = Zs + 4 * bi[m];
+                const float* zj0 = Zs + 4 * bj[m];
+#pragma unroll 4
+                for (int r = 0; r < kE; ++r) {
+                    const float4 xi = *reinterpret_cast<const float4*>(zi0 + (size_t)r * XS);
+                    const float4 xj = *reinterpret_cast<const float4*>(zj0 + (size_t)r * XS);
+                    const float u[4] = {xi.x, xi.y, xi.z, xi.w}, v[4] = {xj.x, xj.y, xj.z, xj.w};
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+#pragma unroll
+                        for (int qq = 0; qq < 4; ++qq) Zg[m][4 * p + qq] = fmaf(u[p], v[qq], Zg[m][4 * p + qq]);
+                }
+            }
+        }
+        if (++win == kFold) {
+            fold(smp);
+            win = 0;
+        }
+        if (++st == 2) {
+            st = 0;
+            ph ^= 1u;
+        }
+        __syncthreads();  // phase 2 is done with X and z before the next tile rewrites them
+    }
+    if (s_abort) {
+        // a tile never arrived: report it and wait (bounded) for the copies in flight
+        if (tid == 0) {
+            atomicOr(a.err, pwa::ERR_TIMEOUT);
+            for (int s = 0; s < 2; ++s)
+                if (issued[s] >= 0) (void)pwa::mbar_wait(&mbar[s], (uint32_t)((issued[s] / 2) & 1), a.timeout_cycles);
+        }
+        __syncthreads();
+        return;
+    }
+    fold(cur_smp);
+}
+
+// Fixed-order sum of the per-CTA records.
+__global__ void hess_reduce_kernel(const double* __restrict__ rec, int grid, int rec_len, double* __restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rec_len; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < grid; ++b) s += rec[(size_t)b * rec_len + i];
+        out[i] = s;
+    }
+}
+
+using KernelH = void (*)(const HessArgs);
+
+template <int S>
+KernelH pick_s(int NT)
+{
+    return NT == 256 ? hess_kernel<S, 256, 1> : hess_kernel<S, 512, 2>;
+}
+
+KernelH pick_hess(int S, int NT)
+{
+    switch (S) {
+        case 1: return pick_s<1>(NT);
+        case 2: return pick_s<2>(NT);
+        case 3: return pick_s<3>(NT);
+        case 4: return pick_s<4>(NT);
+        default: return nullptr;
+    }
+}
+
+using cplx = std::complex<double>;
+
+// Combine the summed records into NLL, gradient and Hessian in the free
+// parameters (FP64, host).
+void combine(const pwa_handle* h, const double* theta, const double* sum, int NW, double* nll, double* grad,
+             double* hess)
+{
+    const int K = h->K, P = h->P, nb = K * (K + 1) / 2, C = 4 * K;
+    // full symmetric 4K x 4K Gram matrices from the upper-triangle blocks
+    auto gram = [&](int off) {
+        std::vector<double> Gm((size_t)C * C);
+        for (int b = 0; b < nb; ++b) {
+            int bi, bj;
+            block_of(b, K, bi, bj);
+            for (int u = 0; u < 4; ++u)
+                for (int v = 0; v < 4; ++v) {
+                    const double x = sum[off + 16 * b + 4 * u + v];
+                    Gm[(size_t)(4 * bi + u) * C + 4 * bj + v] = x;
+                    Gm[(size_t)(4 * bj + v) * C + 4 * bi + u] = x;
+                }
+        }
+        return Gm;
+    };
+    const std::vector<double> RD = gram(0), ZD = gram(16 * nb), RM = gram(32 * nb);
+    // C[c][c'] = sum a sum_s conj(V_c) V_c', c = p K + k
+    auto cgram = [&](const std::vector<double>& R, int c, int cp) {
+        const double* r0 = R.data() + (size_t)(2 * c) * C;
+        const double* r1 = R.data() + (size_t)(2 * c + 1) * C;
+        return cplx(r0[2 * cp] + r1[2 * cp + 1], r0[2 * cp + 1] - r1[2 * cp]);
+    };
+    const int offQ = 48 * nb, offS = offQ + 12 * NW * K;
+    std::vector<cplx> Q[2][3];
+    for (int smp = 0; smp < 2; ++smp)
+        for (int pp = 0; pp < 3; ++pp) Q[smp][pp].assign(K, cplx(0, 0));
+    for (int smp = 0; smp < 2; ++smp)
+        for (int w = 0; w < NW; ++w)
+            for (int k = 0; k < K; ++k) {
+                const double* qq = sum + offQ + ((size_t)(smp * NW + w) * K + k) * 6;
+                for (int pp = 0; pp < 3; ++pp) Q[smp][pp][k] += cplx(qq[2 * pp], qq[2 * pp + 1]);
+            }
+    double SlnI = 0.0, Gm = 0.0;
+    for (int w = 0; w < NW; ++w) {
+        SlnI += sum[offS + 2 * w];
+        Gm += sum[offS + 2 * w + 1];
+    }
+    const double Nd = h->Nd;
+    *nll = -SlnI + Nd * std::log(Gm / h->Nmc);
+
+    // per free parameter: resonance, kind, kappa1, kappa2
+    struct ParInfo {
+        int k, j;
+        cplx k1, k2;
+    };
+    std::vector<ParInfo> par(P);
+    std::vector<double> rho(K), phi(K), M(K), Gw(K);
+    for (int k = 0; k < K; ++k) {
+        const pwa::ResParam& r = h->res[k];
+        double v[4];
+        for (int j = 0; j < 4; ++j) v[j] = r.idx[j] >= 0 ? theta[r.idx[j]] : r.fixed[j];
+        rho[k] = v[0];
+        phi[k] = v[1];
+        M[k] = v[2];
+        Gw[k] = v[3];
+        const cplx E1 = std::polar(1.0, v[1]), g = v[0] * E1;
+        const cplx a1(-2.0 * v[2], v[3]), a2(0.0, v[2]);
+        const cplx kap1[4] = {E1, cplx(0, 1) * g, 0.0, 0.0};
+        const cplx kap2[4] = {0.0, 0.0, g * a1, g * a2};
+        for (int j = 0; j < 4; ++j)
+            if (r.idx[j] >= 0) par[r.idx[j]] = ParInfo{k, j, kap1[j], kap2[j]};
+    }
+    // second-derivative coefficients mu1, mu2, mu3 of d2c_k / dtheta_j dtheta_j'
+    auto mu = [&](int k, int j, int jp, cplx& m1, cplx& m2, cplx& m3) {
+        const cplx E1 = std::polar(1.0, phi[k]), g = rho[k] * E1, I1(0, 1);
+        const cplx a1(-2.0 * M[k], Gw[k]), a2(0.0, M[k]);
+        if (j > jp) std::swap(j, jp);
+        m1 = m2 = m3 = 0.0;
+        if (j == 0 && jp == 1) m1 = I1 * E1;
+        else if (j == 0 && jp == 2) m2 = E1 * a1;
+        else if (j == 0 && jp == 3) m2 = E1 * a2;
+        else if (j == 1 && jp == 1) m1 = -g;
+        else if (j == 1 && jp == 2) m2 = I1 * g * a1;
+        else if (j == 1 && jp == 3) m2 = I1 * g * a2;
+        else if (j == 2 && jp == 2) {
+            m2 = -2.0 * g;
+            m3 = 2.0 * g * a1 * a1;
+        } else if (j == 2 && jp == 3) {
+            m2 = I1 * g;
+            m3 = 2.0 * g * a1 * a2;
+        } else if (j == 3 && jp == 3) {
+            m3 = 2.0 * g * a2 * a2;
+        }
+    };
+    // gradients of the data and MC sums: dI sums = 2 Re (kappa1 Q1 + kappa2 Q2)
+    std::vector<double> gD(P), gM(P);
+    for (int i = 0; i < P; ++i) {
+        const ParInfo& pi = par[i];
+        gD[i] = 2.0 * std::real(pi.k1 * Q[0][0][pi.k] + pi.k2 * Q[0][1][pi.k]);
+        gM[i] = 2.0 * std::real(pi.k1 * Q[1][0][pi.k] + pi.k2 * Q[1][1][pi.k]);
+        if (grad) grad[i] = -gD[i] + Nd * gM[i] / Gm;
+    }
+    if (!hess) return;
+    // z coefficients: dI/dtheta_i = c_i . z with c at columns 2 (p K + k) + (0, 1)
+    for (int i = 0; i < P; ++i)
+        for (int ip = i; ip < P; ++ip) {
+            const ParInfo &a = par[i], &b = par[ip];
+            const cplx ka[2] = {a.k1, a.k2}, kb[2] = {b.k1, b.k2};
+            double s2d = 0.0, s2m = 0.0, jg = 0.0;
+            for (int p = 0; p < 2; ++p)
+                for (int pp = 0; pp < 2; ++pp) {
+                    if (ka[p] == 0.0 || kb[pp] == 0.0) continue;
+                    const int c = p * K + a.k, cp = pp * K + b.k;
+                    s2d += 2.0 * std::real(std::conj(ka[p]) * kb[pp] * cgram(RD, c, cp));
+                    s2m += 2.0 * std::real(std::conj(ka[p]) * kb[pp] * cgram(RM, c, cp));
+                    // c_a^T Zg c_b with c = (2 Re kappa, -2 Im kappa) at the z columns of (p, k)
+                    const double ca[2] = {2.0 * ka[p].real(), -2.0 * ka[p].imag()};
+                    const double cb[2] = {2.0 * kb[pp].real(), -2.0 * kb[pp].imag()};
+                    for (int u = 0; u < 2; ++u)
+                        for (int v = 0; v < 2; ++v)
+                            jg += ca[u] * cb[v] * ZD[(size_t)(2 * c + u) * C + 2 * cp + v];
+                }
+            if (a.k == b.k) {
+                cplx m1, m2, m3;
+                mu(a.k, a.j, b.j, m1, m2, m3);
+                s2d += 2.0 * std::real(m1 * Q[0][0][a.k] + m2 * Q[0][1][a.k] + m3 * Q[0][2][a.k]);
+                s2m += 2.0 * std::real(m1 * Q[1][0][a.k] + m2 * Q[1][1][a.k] + m3 * Q[1][2][a.k]);
+            }
+            const double hval = -(s2d - jg) + Nd * (s2m / Gm - gM[i] * gM[ip] / (Gm * Gm));
+            hess[(size_t)i * P + ip] = hval;
+            hess[(size_t)ip * P + i] = hval;
+        }
+}
+
+}  // namespace
+
+namespace pwa {
+
+pwa_status hessian_device(pwa_handle* h, const double* theta, double* nll, double* grad, double* hess)
+{
+    const int K = h->K, S = h->S;
+    if (K > kMaxKHess)
+        return set_error(h, PWA_EINVAL, "the Hessian pass supports K <= " + std::to_string(kMaxKHess));
+    if (h->broken) return set_error(h, PWA_ETIMEOUT, "handle is unusable after a device-side timeout");
+    const int nblk = K * (K + 1) / 2;
+    const int NT = nblk <= 256 ? 256 : 512;
+    const int NW = NT / 32;
+    KernelH fn = pick_hess(S, NT);
+    if (!fn) return set_error(h, PWA_EINVAL, "no Hessian kernel for this S");
+    const Tiling& t = h->tiling;
+    const uint32_t stage = (uint32_t)((std::max(h->tile_bytes[0], h->tile_bytes[1]) + 127) / 128 * 128);
+    const int C = 4 * K, XS = C + 4;
+    const size_t smem = 2 * (size_t)stage + sizeof(KConst) * K + sizeof(float) * (size_t)(kE * S + kE) * XS + 16;
+    HessState& hs = h->hess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(h, e, "cudaGetDevice");
+    if (hs.fn != reinterpret_cast<const void*>(fn) || hs.smem != smem) {
+        int max_optin = 0;
+        e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return cuda_error(h, e, "cudaDeviceGetAttribute");
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(fn));
+        if (e != cudaSuccess) return cuda_error(h, e, "cudaFuncGetAttributes");
+        const int dyn_max = max_optin - (int)fa.sharedSizeBytes;
+        if ((int)smem > dyn_max)
+            return set_error(h, PWA_EINVAL, "the Hessian pass needs " + std::to_string(smem) +
+                                                " bytes of shared memory per block (max " + std::to_string(dyn_max) +
+                                                ")");
+        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 dyn_max);
+        if (e != cudaSuccess) return cuda_error(h, e, "cudaFuncSetAttribute");
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reinterpret_cast<const void*>(fn), NT, smem);
+        if (e != cudaSuccess) return cuda_error(h, e, "occupancy");
+        if (occ < 1) return set_error(h, PWA_EINVAL, "the Hessian pass does not fit on an SM");
+        const long long T = (long long)h->ntiles[0] + h->ntiles[1];
+        const int grid = (int)std::max(1LL, std::min((long long)h->num_sms * occ, T));
+        const int rec_len = hess_rec_len(K, nblk, NW);
+        const size_t need = sizeof(double) * ((size_t)grid * rec_len + rec_len);
+        if (need > hs.cap_bytes) {
+            if (hs.d_rec) cudaFree(hs.d_rec);
+            if (hs.h_sum) cudaFreeHost(hs.h_sum);
+            hs.d_rec = nullptr;
+            hs.h_sum = nullptr;
+            hs.cap_bytes = 0;
+            if (cudaMalloc(reinterpret_cast<void**>(&hs.d_rec), need) != cudaSuccess) {
+                cudaGetLastError();
+                return set_error(h, PWA_ENOMEM, "cudaMalloc failed for the Hessian records");
+            }
+            if (cudaMallocHost(reinterpret_cast<void**>(&hs.h_sum), sizeof(double) * rec_len) != cudaSuccess) {
+                cudaGetLastError();
+                return set_error(h, PWA_ENOMEM, "pinned allocation failed for the Hessian sums");
+            }
+            hs.cap_bytes = need;
+        }
+        hs.fn = reinterpret_cast<const void*>(fn);
+        hs.smem = smem;
+        hs.grid = grid;
+        hs.rec_len = rec_len;
+    }
+    HessArgs a;
+    for (int s = 0; s < 2; ++s) {
+        a.tiles[s] = h->d_tiles[s];
+        a.tile_bytes[s] = h->tile_bytes[s];
+        a.ntiles[s] = h->ntiles[s];
+        a.nev[s] = h->n[s];
+        if (h->tile_bytes[s] > stage || h->tile_bytes[s] % 16 != 0 || (long long)h->ntiles[s] * kE < h->n[s])
+            return set_error(h, PWA_EINVAL, "inconsistent tile geometry");
+    }
+    a.K = K;
+    a.ev = 32 / t.W;
+    a.stage_bytes = stage;
+    a.res = h->d_res;
+    a.theta = h->d_theta;
+    a.nblk = nblk;
+    a.rec = hs.d_rec;
+    a.rec_len = hs.rec_len;
+    a.bad = h->d_bad;
+    a.err = h->d_err;
+    a.timeout_cycles = h->timeout_cycles;
+    double* d_sum = hs.d_rec + (size_t)hs.grid * hs.rec_len;
+
+    std::memcpy(h->h_pin, theta, sizeof(double) * h->P);
+    e = cudaMemcpyAsync(h->d_theta, h->h_pin, sizeof(double) * h->P, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(hs.d_rec, 0, sizeof(double) * (size_t)hs.grid * hs.rec_len, h->stream);
+    if (e != cudaSuccess) return cuda_error(h, e, "Hessian inputs");
+    fn<<<hs.grid, NT, smem, h->stream>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(h, e, "Hessian kernel launch");
+    hess_reduce_kernel<<<(hs.rec_len + 255) / 256, 256, 0, h->stream>>>(hs.d_rec, hs.grid, hs.rec_len, d_sum);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hs.h_sum, d_sum, sizeof(double) * hs.rec_len, cudaMemcpyDeviceToHost, h->stream);
+    int errw = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_pin + h->P, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_error(h, e, "Hessian pass");
+    std::memcpy(&errw, h->h_pin + h->P, sizeof(int));
+    if (errw) {
+        pwa_status st = check_device_errors(h);
+        if (st != PWA_OK) return st;
+    }
+    double f = 0.0;
+    combine(h, theta, hs.h_sum, NW, &f, grad, hess);
+    if (nll) *nll = f;
+    return PWA_OK;
+}
+
+void free_hessian(pwa_handle* h)
+{
+    if (h->hess.d_rec) cudaFree(h->hess.d_rec);
+    if (h->hess.h_sum) cudaFreeHost(h->hess.h_sum);
+    h->hess = HessState();
+}
+
+}  // namespace pwa
+
+extern "C" pwa_status pwa_hessian(pwa_handle* h, const double* theta, double* nll, double* grad, double* hess)
+{
+    if (!h) return PWA_EINVAL;
+    h->err.clear();
+    if (!theta || !hess) return pwa::set_error(h, PWA_EINVAL, "theta and hess must not be NULL");
+    for (int i = 0; i < h->P; ++i)
+        if (!std::isfinite(theta[i])) return pwa::set_error(h, PWA_EINVAL, "theta must be finite");
+    return pwa::hessian_device(h, theta, nll, grad, hess);
+}

@@ -262,6 +262,8 @@ Tiling default_tiling(int K, int S)
 
 pwa_status build_tiles(pwa_handle* h)
 {
+    if (h->released)
+        return pwa::set_error(h, PWA_EINVAL, "the events' caller-layout copies were released: the tiling is fixed");
     Tiling& t = h->tiling;
     PWA_TRY(finish_tiling(h, t));  // sets t.E first: everything below depends on it
     const int ev = 32 / t.W;
@@ -686,6 +688,38 @@ pwa_status pwa_create(pwa_handle** out, const pwa_events* data, const pwa_events
 
 const char* pwa_last_create_error(void) { return g_create_error.c_str(); }
 
+pwa_status pwa_release_event_copies(pwa_handle* h)
+{
+    if (!h) return PWA_EINVAL;
+    h->err.clear();
+    if (h->released) return PWA_OK;
+    PWA_CUDA(h, h->stream ? cudaStreamSynchronize(h->stream) : cudaDeviceSynchronize());
+    float* ptrs[] = {h->d_F[0], h->d_F[1], h->d_m2[0], h->d_m2[1], h->d_w};
+    for (float* p : ptrs)
+        if (p) cudaFree(p);
+    h->d_F[0] = h->d_F[1] = h->d_m2[0] = h->d_m2[1] = h->d_w = nullptr;
+    h->released = true;
+    PWA_CUDA(h, cudaGetLastError());
+    return PWA_OK;
+}
+
+pwa_status pwa_device_bytes(const pwa_handle* h, long long* out)
+{
+    if (!h || !out) return PWA_EINVAL;
+    long long b = 0;
+    const long long n0 = h->n[0], n1 = h->n[1], KS = (long long)h->K * h->S;
+    if (!h->released) b += (n0 + n1) * (8 * KS + 12) + (h->d_w ? 4 * n0 : 0);
+    b += (long long)h->ntiles[0] * h->tile_bytes[0] + (long long)h->ntiles[1] * h->tile_bytes[1];
+    b += 8LL * ((long long)h->tiling.grid + h->ngroups) * h->rec_len + 4LL * (h->ngroups + 1);
+    b += 8LL * (4 * (long long)h->P + 3) + (long long)sizeof(pwa::ResParam) * h->K;
+    b += (long long)h->hess.cap_bytes;
+    const pwa::BatchState& bs = h->batch;
+    b += 8LL * (long long)(bs.cap_blocks + bs.cap_groups) * h->rec_len + 4LL * (long long)(bs.cap_groups + 2 * bs.cap_top);
+    b += 8LL * (long long)bs.cap_B * (2 * (long long)h->P + 1 + 2 * (long long)h->P);
+    *out = b;
+    return PWA_OK;
+}
+
 int pwa_num_params(const pwa_handle* h) { return h ? h->P : -1; }
 
 pwa_status pwa_eval(pwa_handle* h, const double* theta, const double* v, double* nll, double* grad, double* hv)
@@ -1009,6 +1043,7 @@ void pwa_destroy(pwa_handle* h)
         if (p) cudaFree(p);
     if (h->h_pin) cudaFreeHost(h->h_pin);
     pwa::free_batch(h);
+    pwa::free_hessian(h);
     cudaGetLastError();
     delete h;
 }

@@ -54,6 +54,20 @@ struct BatchState {
 };
 }  // namespace pwa
 
+namespace pwa {
+// Scratch of the Hessian pass: per-CTA FP64 records and their sum (device),
+// the summed record on the host (pinned); sized for the kernel instance and
+// grid it was set up for.
+struct HessState {
+    const void* fn = nullptr;  // kernel instance the geometry below belongs to
+    size_t smem = 0;
+    int grid = 0, rec_len = 0;
+    size_t cap_bytes = 0;
+    double* d_rec = nullptr;   // [grid][rec_len] records, then [rec_len] sums
+    double* h_sum = nullptr;   // [rec_len] pinned
+};
+}  // namespace pwa
+
 struct pwa_handle {
     int K = 0, S = 0, P = 0;
     cudaStream_t stream = nullptr;
@@ -83,8 +97,10 @@ struct pwa_handle {
     int* d_err = nullptr;
     double* h_pin = nullptr;        // pinned staging: theta[P], v[P], out[1 + 2P], status
     pwa::BatchState batch;
+    pwa::HessState hess;
     long long timeout_cycles = 0;
     bool broken = false;
+    bool released = false;  // d_F, d_m2, d_w freed (pwa_release_event_copies)
     std::string err;
 };
 
@@ -134,6 +150,12 @@ pwa_handle* variant_base(pwa_variant* v);
 // The same with the couplings only, at the line shapes of the last pwa_variant_set_shapes.
 pwa_status variant_coupling_eval(pwa_variant* v, const double* theta_c, const double* dir_c, double* nll,
                                  double* grad, double* hv);
+// Largest K the Hessian pass serves (its Gram blocks fit the threads of a CTA).
+constexpr int kMaxKHessian = 44;
+// The full Hessian of NLL at host theta (plus NLL and gradient; either may be
+// null) from one Hessian pass; synchronous.  hess: host [P][P].
+pwa_status hessian_device(pwa_handle* h, const double* theta, double* nll, double* grad, double* hess);
+void free_hessian(pwa_handle* h);
 // Read back and clear the device error flags; turns them into a status + message.
 pwa_status check_device_errors(pwa_handle* h);
 pwa_status set_error(pwa_handle* h, pwa_status st, const std::string& msg);

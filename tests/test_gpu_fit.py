@@ -1,7 +1,10 @@
 """Newton-CG fit parity (paper Sec. 3): the GPU fit and the oracle's FP64
-textbook Newton-CG, started from the same point on the full tiny
-configuration, reach the same minimum within 1e-3 of the oracle's parameter
-errors (after mapping (rho, phi) ~ (-rho, phi + pi) to one representative)."""
+textbook Newton-CG, started from the same point, reach the same minimum
+within 1e-3 of the oracle's parameter errors (after mapping (rho, phi) ~
+(-rho, phi + pi) to one representative).  Both inner-product modes of the
+GPU fit are checked: products with one Hessian pass per outer iteration
+(the default) and one fused H v pass per CG step (matrix-free, the paper's
+scipy setup)."""
 import numpy as np
 import pytest
 
@@ -14,20 +17,76 @@ from conftest import small_workload
 pytestmark = pytest.mark.gpu
 
 
-def test_fit_matches_oracle_fit_on_tiny():
+def _oracle_fit(model, wl, th0):
+    fg = lambda x: oracle.nll_grad(model, x, wl.data, wl.mc)
+    hp = lambda x, v: oracle.nll_grad_hvp(model, x, v, wl.data, wl.mc)[2]
+    ref = ncg.newton_cg(fg, hp, th0, xtol=1e-10, maxiter=200)
+    assert ref.status in ncg.CONVERGED, ref.status_name
+    sig = oracle.parameter_errors(oracle.hessian(model, ref.x, wl.data, wl.mc))
+    return ref, sig
+
+
+@pytest.mark.parametrize("matrix_free", [False, True])
+def test_fit_matches_oracle_fit_on_tiny(matrix_free):
     from paper_2403_09225_b300 import binding
     cfg = W.CONFIGS["tiny"]
     wl, model = small_workload("tiny", cfg.n_data, cfg.n_mc)
     rng = np.random.default_rng(4)
     th0 = wl.theta_true * (1 + 0.03 * rng.standard_normal(model.P))
-    fg = lambda x: oracle.nll_grad(model, x, wl.data, wl.mc)
-    hp = lambda x, v: oracle.nll_grad_hvp(model, x, v, wl.data, wl.mc)[2]
-    ref = ncg.newton_cg(fg, hp, th0, xtol=1e-10, maxiter=200)
-    assert ref.status in ncg.CONVERGED, ref.status_name
+    ref, sig = _oracle_fit(model, wl, th0)
     L = binding.make_likelihood(wl)
-    th, info = L.fit(th0, xtol=1e-10)
+    th, info = L.fit(th0, xtol=1e-10, matrix_free=matrix_free, trace=500)
     assert info["converged"], info
-    sig = oracle.parameter_errors(oracle.hessian(model, ref.x, wl.data, wl.mc))
+    assert (info["n_hess"] > 0) == (not matrix_free)
+    assert all(r["hessian"] == (0 if matrix_free else 1) for r in info["trace"])
     pull = (oracle.canonical(model, th) - oracle.canonical(model, ref.x)) / sig
     assert np.max(np.abs(pull)) <= 1e-3, (pull, info)
     assert abs(info["nll"] - ref.fun) <= 1e-6 * abs(ref.fun)
+
+
+def test_fit_matches_oracle_fit_at_paper_scale_model():
+    """The paper-scale model (K = 20, S = 4, P = 78) on a reduced sample
+    (2e4 data events accept-rejected from I at theta_true, 1e5 MC), started
+    near theta_true.  The oracle's minimum from the same start is stored in
+    tests/golden/fit_k20.npz by tests/golden/make_fit_k20.py (the oracle's
+    Newton-CG alone; about 5 CPU-minutes on 8 cores), with a hash of the
+    sample that this test regenerates."""
+    import os
+    import sys
+    from paper_2403_09225_b300 import binding
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    sys.path.insert(0, here)
+    import make_fit_k20 as mk
+    g = np.load(os.path.join(here, "fit_k20.npz"))
+    wl, model = small_workload("paper", int(g["n_data"]), int(g["n_mc"]))
+    assert mk.sample_hash(wl) == str(g["sample_sha256"]), "the generator's events changed: rerun make_fit_k20.py"
+    th0 = mk.start(wl, model.P)
+    assert np.array_equal(th0, g["theta0"])
+    ref_x, sig = g["theta_min"], g["sigma"]
+    L = binding.make_likelihood(wl)
+    for matrix_free in (False, True):
+        th, info = L.fit(th0, xtol=1e-10, matrix_free=matrix_free)
+        assert info["converged"], info
+        pull = (oracle.canonical(model, th) - oracle.canonical(model, ref_x)) / sig
+        assert np.max(np.abs(pull)) <= 1e-3, (matrix_free, np.max(np.abs(pull)), info)
+    L.close()
+
+
+def test_lockstep_fits_with_hessian_passes():
+    """Lockstep fits (pwa_newton_cg_fit_batch) in both modes reach the same
+    minima as single fits from the same starts."""
+    from paper_2403_09225_b300 import binding
+    cfg = W.CONFIGS["tiny"]
+    wl, model = small_workload("tiny", cfg.n_data, cfg.n_mc)
+    rng = np.random.default_rng(6)
+    starts = wl.theta_true * (1 + 0.03 * rng.standard_normal((4, model.P)))
+    L = binding.make_likelihood(wl)
+    sig = oracle.parameter_errors(oracle.hessian(model, wl.theta_true, wl.data, wl.mc))
+    for matrix_free in (False, True):
+        ths, infos, ok = L.fit_batch(starts, xtol=1e-10, matrix_free=matrix_free)
+        assert ok, infos
+        for th, s, info in zip(ths, starts, infos):
+            assert (info["n_hess"] > 0) == (not matrix_free)
+            th1, _ = L.fit(s, xtol=1e-10, matrix_free=matrix_free)
+            pull = (oracle.canonical(model, th) - oracle.canonical(model, th1)) / sig
+            assert np.max(np.abs(pull)) <= 1e-3, (matrix_free, pull)

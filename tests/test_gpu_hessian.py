@@ -1,0 +1,91 @@
+"""The Hessian pass (pwa_hessian) against the FP64 oracle's full Hessian.
+
+Eq. 7 written out without the contraction with a direction: the oracle forms
+every entry per event from the analytic first and second derivatives of the
+couplings (oracle.hessian, itself pinned by its agreement with the oracle's
+H v and by symmetry).  Bars: Hessian 1e-4 relative in max-norm (the HVP's
+bar), gradient 1e-5 relative in max-norm, NLL 1e-6 of the summand scale
+(the small-sample reading of the NLL bar, as in test_gpu_parity).  Sizes span
+several tiles and end in ragged tiles; points are theta_true, an offset from
+it and random starts of the prior.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_09225_b300 import workload as W
+
+from conftest import small_workload
+from test_gpu_parity import TOL_GRAD, TOL_HVP, TOL_NLL, nll_scale, points, relmax
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(L, model, wl, th):
+    f, g, H = L.hessian(th)
+    fo, go = oracle.nll_grad(model, th, wl.data, wl.mc)
+    Ho = oracle.hessian(model, th, wl.data, wl.mc)
+    assert abs(f - fo) <= TOL_NLL * nll_scale(model, th, wl, fo), (f, fo)
+    assert relmax(g, go) <= TOL_GRAD, relmax(g, go)
+    assert relmax(H, Ho) <= TOL_HVP, relmax(H, Ho)
+    assert np.array_equal(H, H.T)
+    # H v from the Hessian and from the fused pass agree
+    v = np.linspace(-1.0, 1.0, model.P)
+    hv = L.hvp(th, v)
+    assert relmax(H @ v, hv) <= 2 * TOL_HVP, relmax(H @ v, hv)
+    return relmax(H, Ho)
+
+
+@pytest.mark.parametrize("name,nd,nm", [("tiny", 4000 + 17, 20000 + 5), ("tiny_k4", 3001, 9999),
+                                        ("paper", 1500 + 3, 6000 + 29)])
+def test_hessian_matches_oracle(name, nd, nm):
+    from paper_2403_09225_b300 import binding
+    wl, model = small_workload(name, nd, nm)
+    L = binding.make_likelihood(wl)
+    for th in points(wl, n_random=1):
+        _check(L, model, wl, th)
+    L.close()
+
+
+def test_hessian_k40_fixed_parameters_and_tilings():
+    """K = 40 (the differentiation model: 512-thread instance, two Gram
+    blocks per thread), odd S with fixed parameters, and a re-tiled handle
+    (the tile rotation depends on the tiling)."""
+    from paper_2403_09225_b300 import binding
+    wl, model = small_workload("diff", 700, 3001, from_model=False)
+    L = binding.make_likelihood(wl)
+    _check(L, model, wl, W.random_starts(wl, 1)[0])
+    L.close()
+    cfg = W.Config("k7s3", 7, 3, 0, 0, 2, False, 11)
+    base = W.make_workload(cfg, intensity=None, n_data=1234, n_mc=5077)
+    table = [W.Resonance(**{**r.__dict__}) for r in base.table]
+    table[2].fix_mass = True
+    table[4].fix_width = True
+    table[5].fix_coupling = True
+    wl = W.Workload(cfg, table, W.free_parameter_vector(table), base.data, base.mc, {})
+    model = oracle.Model.from_table(table, cfg.S)
+    L = binding.make_likelihood(wl)
+    assert L.P == model.P == 4 * 7 - 2 - 1 - 1 - 2
+    th = wl.theta_true * 1.02
+    _check(L, model, wl, th)
+    for tiling in ((1, 2), (2, 3), (8, 2)):
+        L.set_tiling(*tiling)
+        _check(L, model, wl, th)
+    L.close()
+
+
+def test_hessian_is_reproducible_and_refuses_large_k():
+    from paper_2403_09225_b300 import binding
+    wl, model = small_workload("paper", 1500 + 3, 6000 + 29)
+    L = binding.make_likelihood(wl)
+    th = W.random_starts(wl, 1)[0]
+    a, b = L.hessian(th), L.hessian(th)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    L.close()
+    cfg = W.Config("k48", 48, 1, 0, 0, 2, False, 7)
+    wl = W.make_workload(cfg, intensity=None, n_data=500, n_mc=2000)
+    L = binding.make_likelihood(wl)
+    with pytest.raises(binding.PwaError) as e:
+        L.hessian(wl.theta_true)
+    assert e.value.status == binding.PWA_EINVAL
+    L.close()

@@ -310,3 +310,21 @@ def test_dalitz_histogram_oracle_against_a_plain_loop():
     assert np.array_equal(h, want) and h.sum() == 300
     hl = og.dalitz_histogram(m2, idx, 8, bounds, log_scale=True)
     assert np.allclose(hl, np.log(1 + want * 64 / 300), rtol=0, atol=1e-15)
+
+
+def test_sharded_hessian_matches_the_single_pass_hessian(paper_small):
+    """Shard sums of the second derivatives combined by Eq. 7 on the host
+    (oracle.sharded_hessian) equal the C combination of the whole-sample sums
+    (oracle.hessian): shard additivity (Eqs. 4-5) for the Hessian, and the two
+    combinations of Eq. 7 agree."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    wl, model = paper_small
+    th = W.random_starts(wl, 1)[0]
+    with ProcessPoolExecutor(max_workers=2, mp_context=mp.get_context("spawn")) as pool:
+        f, g, H = oracle.sharded_hessian(model, th, wl.data, wl.mc, pool=pool, shard=1000)
+    fo, go = oracle.nll_grad(model, th, wl.data, wl.mc)
+    Ho = oracle.hessian(model, th, wl.data, wl.mc)
+    assert abs(f - fo) <= 1e-12 * abs(fo)
+    assert rel(g, go) <= 1e-12
+    assert rel(H, Ho) <= 1e-12
