@@ -58,6 +58,10 @@ def bf16_peak():
         return 1800.0, "fallback"
 
 
+def units_per_pass(nd, nm, K):
+    return (nd + nm) * K
+
+
 def bytes_per_pass(nd, nm, K, S):
     """Algorithmic HBM bytes of one pass: F (8 S bytes per event-amplitude),
     three m^2 values per event, one weight per data event."""
@@ -171,7 +175,8 @@ def run_reference(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": "paper-scale K=20 S=4 (bounded CPU sample)",
                                         "n_data": nd, "n_mc": nm, "K": cfg.K, "S": cfg.S},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -193,50 +198,76 @@ def cpu_baseline_leg():
         oracle.nll_grad_hvp(model, th, v, wl.data, wl.mc)
         reps += 1
         dt = time.perf_counter() - t0
-    return {"value": reps * (nd + nm) * cfg.K / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": reps * (nd + nm) * cfg.K / dt, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+            "kind": "oracle",
             "sample": "%d data + %d MC events (1/60 of the workload), K=%d, S=%d, %d fused evaluations, "
                       "%.1f s" % (nd, nm, cfg.K, cfg.S, reps, dt)}
 
 
-def _fit_runs(L, wl, starts, time_limit: float, batched: bool = False):
+def _fit_runs(L, wl, starts, time_limit: float, batched: bool = False, method: int = 0,
+              matrix_free: bool = False, best_extra=()):
     """Fits from `starts`: one after another (plain multi-start), or all in
     lockstep with batched passes (pwa_newton_cg_fit_batch).  GPU seconds are
     the wall time of the fits (the device is busy or waiting on the host
     between passes; nothing else runs)."""
-    ref, ref_info = L.fit(wl.theta_true, xtol=1e-8, time_limit_s=time_limit)
+    kw = dict(xtol=1e-8, time_limit_s=time_limit, method=method, matrix_free=matrix_free)
     t0 = time.perf_counter()
     if batched:
-        _, results, _ = L.fit_batch(np.array(starts), xtol=1e-8, time_limit_s=time_limit)
+        _, results, _ = L.fit_batch(np.array(starts), **kw)
     else:
-        results = [L.fit(s, xtol=1e-8, time_limit_s=time_limit)[1] for s in starts]
+        results = [L.fit(s, **kw)[1] for s in starts]
     total = time.perf_counter() - t0
-    best = min([ref_info["nll"]] + [r["nll"] for r in results])
-    ok = sum(1 for r in results if r["nll"] <= best + 0.01)
-    return {"starts": len(starts), "reached_global_min": ok, "gpu_seconds": total,
-            "fits_to_global_min_per_s": ok / total if total > 0 else 0.0, "best_nll": best,
-            "passes": int(sum(r["n_fev"] + r["n_hvp"] for r in results)),
-            "statuses": sorted({r["status"] for r in results}), "time_limit_s": time_limit}
+    return {"starts": len(starts), "gpu_seconds": total, "nll": [r["nll"] for r in results],
+            "iters": [r["iters"] for r in results], "statuses": sorted({r["status"] for r in results}),
+            "passes": int(sum(r["n_fev"] + r["n_hvp"] + r["n_hess"] for r in results)),
+            "hessian_passes": int(sum(r["n_hess"] for r in results)), "time_limit_s": time_limit,
+            "method": "trust-region" if method == 1 else "line-search",
+            "hessian": "matrix-free H v passes" if matrix_free else "one Hessian pass per outer iteration"}
+
+
+def _score(arms: dict, best: float, tol: float = 0.01):
+    """Hits (NLL within tol of the best seen) and hits per GPU-second per arm."""
+    for a in arms.values():
+        ok = sum(1 for f in a["nll"] if f <= best + tol)
+        a["reached_global_min"] = ok
+        a["fits_to_global_min_per_s"] = ok / a["gpu_seconds"] if a["gpu_seconds"] > 0 else 0.0
+        a["dnll_median"] = float(np.median(np.asarray(a["nll"]) - best))
 
 
 def fit_metric(L, wl, n_starts: int, time_limit: float):
-    """Newton-CG fits (xtol 1e-8) from random starts of the prior.  A fit
-    reaches the global minimum when its NLL is within 0.01 of the best NLL
-    seen over all fits of that workload (including one from theta_true).
-    The paper-scale fits are bounded by an early-stopping time limit; the
-    tiny configuration (K = 3, 2e4 + 1e5 events) shows the rate on a model
-    whose fits finish, for plain multi-start (one fit after another) and for
-    the batched form (all starts in lockstep, one launch per round)."""
+    """Newton-CG fits (xtol 1e-8) from random starts of the prior, every
+    outer iteration driven by one Hessian pass.  A fit reaches the global
+    minimum when its NLL is within 0.01 of the best NLL seen over all fits of
+    that workload (including fits from theta_true).  Paper scale: the paper's
+    line-search Newton-CG one start after another, and half of the starts with
+    the trust-region Newton-CG.  The tiny configuration (K = 3, 2e4 + 1e5
+    events) shows the rate on a model whose random starts often find the
+    minimum, also in lockstep (one batched f, g launch per round)."""
     from paper_2403_09225_b300 import binding
     from paper_2403_09225_b300 import workload as W
-    out = {"xtol": 1e-8, "paper": _fit_runs(L, wl, W.random_starts(wl, n_starts), time_limit)}
+    starts = W.random_starts(wl, n_starts)
+    refs = [L.fit(wl.theta_true, xtol=1e-8, time_limit_s=time_limit, method=m)[1]["nll"] for m in (0, 1)]
+    paper = {"line_search": _fit_runs(L, wl, starts, time_limit),
+             "trust_region": _fit_runs(L, wl, starts[:max(1, n_starts // 2)], time_limit, method=1)}
+    best = min(refs + [f for a in paper.values() for f in a["nll"]])
+    _score(paper, best)
+    paper["best_nll"] = best
+    paper["nll_from_theta_true"] = refs
+    out = {"xtol": 1e-8, "paper": paper}
     cfg = W.CONFIGS["tiny"]
     table = W.make_table(cfg)
-    tiny = W.make_workload(cfg, intensity=gpu_intensity_fn(table, cfg.K, cfg.S))
-    Lt = binding.make_likelihood(tiny)
+    tiny_wl = W.make_workload(cfg, intensity=gpu_intensity_fn(table, cfg.K, cfg.S))
+    Lt = binding.make_likelihood(tiny_wl)
     try:
-        starts = W.random_starts(tiny, 32)
-        out["tiny"] = _fit_runs(Lt, tiny, starts, time_limit)
-        out["tiny_batched"] = _fit_runs(Lt, tiny, starts, time_limit, batched=True)
+        ts = W.random_starts(tiny_wl, 32)
+        tref = Lt.fit(tiny_wl.theta_true, xtol=1e-8, time_limit_s=time_limit)[1]["nll"]
+        tiny = {"line_search": _fit_runs(Lt, tiny_wl, ts, time_limit),
+                "line_search_lockstep": _fit_runs(Lt, tiny_wl, ts, time_limit * 32, batched=True),
+                "trust_region": _fit_runs(Lt, tiny_wl, ts, time_limit, method=1)}
+        tbest = min([tref] + [f for a in tiny.values() for f in a["nll"]])
+        _score(tiny, tbest)
+        tiny["best_nll"] = tbest
+        out["tiny"] = tiny
     finally:
         Lt.close()
     return out
@@ -284,7 +315,7 @@ def batching_metric(n_toys: int, n_starts: int, time_limit: float, seed: int = 7
             ok = sum(1 for i in range(n_toys) for r in results[i] if r["nll"] <= best[i] + 0.01)
             return {"fits": n_toys * n_starts, "reached_global_min": ok, "gpu_seconds": seconds,
                     "fits_to_global_min_per_s": ok / seconds if seconds > 0 else 0.0,
-                    "passes": int(sum(r["n_fev"] + r["n_hvp"] for rr in results for r in rr)),
+                    "passes": int(sum(r["n_fev"] + r["n_hvp"] + r["n_hess"] for rr in results for r in rr)),
                     "statuses": sorted({r["status"] for rr in results for r in rr})}
         return {"toys": n_toys, "starts_per_toy": n_starts, "time_limit_s_per_fit": time_limit,
                 "K": [wl.K for wl in toys], "S": [wl.S for wl in toys], "n_data": [wl.data.n for wl in toys],
@@ -517,6 +548,59 @@ def variant_metric(wl, reps: int = 10):
     return out
 
 
+def diff_metric(reps: int = 20):
+    """The differentiation configuration at full size: K = 40, S = 4, 2e6
+    data + 1e7 MC phase-space events (15.4 GB of F), its caller-layout copy
+    released after tiling (tiles only on the device).  The fused NLL +
+    gradient + H v pass over device-resident parameters, CUDA events over
+    `reps` back-to-back passes; the Hessian pass once (host-synchronous)."""
+    import torch
+    from paper_2403_09225_b300 import binding, workload as W
+    cfg = W.CONFIGS["diff"]
+    t0 = time.perf_counter()
+    wl = W.make_workload(cfg, intensity=None)
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    L = binding.make_likelihood(wl, stream=stream.cuda_stream)
+    try:
+        before = L.device_bytes()
+        L.release_event_copies()
+        after = L.device_bytes()
+        P = L.P
+        th = W.random_starts(wl, 1)[0]
+        d_th = torch.tensor(th, dtype=torch.float64, device="cuda")
+        d_v = torch.tensor(np.linspace(-1.0, 1.0, P), dtype=torch.float64, device="cuda")
+        d_out = torch.empty(1 + 2 * P, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            L.eval_device(d_th.data_ptr(), d_v.data_ptr(), d_out.data_ptr(), True, True)
+        L.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            L.eval_device(d_th.data_ptr(), d_v.data_ptr(), d_out.data_ptr(), True, True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        L.sync()
+        ms = e0.elapsed_time(e1) / reps
+        nd, nm = wl.data.n, wl.mc.n
+        bpp = bytes_per_pass(nd, nm, cfg.K, cfg.S)
+        peak, kind = peaks()
+        achieved = bpp / (ms * 1e-3) / 1e9
+        L.hessian(th)
+        t0 = time.perf_counter()
+        L.hessian(th)
+        hess_ms = (time.perf_counter() - t0) * 1e3
+        return {"workload": "differentiation: K=40, S=4, 2e6 data + 1e7 MC (phase space), P=%d" % P,
+                "generate_s": gen_s, "ms_per_pass": ms, "event_amps_per_s": (nd + nm) * cfg.K / (ms * 1e-3),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "peak_kind": kind, "algorithmic_bytes_per_launch": bpp},
+                "device_bytes_with_copies": before, "device_bytes_after_release": after,
+                "f_bytes": (nd + nm) * cfg.K * cfg.S * 8, "hessian_call_ms": hess_ms}
+    finally:
+        L.close()
+
+
 def measured_traffic(tiling: dict):
     """DRAM bytes per launch of the fused HVP pass from the committed ncu
     summary, when it was taken with the tiling in use (else None)."""
@@ -555,18 +639,20 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fits", type=int, default=2, help="random-start fits for the fit metric (0: skip)")
-    ap.add_argument("--fit-time-limit", type=float, default=10.0, help="seconds per fit (early stopping)")
+    ap.add_argument("--fits", type=int, default=16, help="random-start fits for the fit metric (0: skip)")
+    ap.add_argument("--fit-time-limit", type=float, default=60.0, help="seconds per fit (early stopping)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tiling", default="", help="warps,lanes_per_event,stages[,blocks_per_sm] (default: library's)")
     ap.add_argument("--no-coupling", action="store_true", help="skip the fixed-mass coupling sub-problem leg")
     ap.add_argument("--no-variants", action="store_true", help="skip the physics-variant leg")
+    ap.add_argument("--no-diff", action="store_true", help="skip the full-size differentiation configuration leg")
     ap.add_argument("--mlp-timing", action="store_true",
                     help="also time the learned proposal's network (gradient step at batches 128, 512, 1024)")
-    ap.add_argument("--batching", default="", metavar="TOYS,STARTS",
-                    help="also run the uneven-size toy-fit comparison (plain vs batched), e.g. 12,4")
-    ap.add_argument("--learned", default="", metavar="TRAIN,EVAL,STARTS",
-                    help="also train and evaluate the learned starting-point proposal, e.g. 4096,16,16")
+    ap.add_argument("--batching", default="12,4", metavar="TOYS,STARTS",
+                    help="uneven-size toy-fit comparison (plain vs batched); 0 to skip")
+    ap.add_argument("--learned", default="4096,24,16", metavar="TRAIN,EVAL,STARTS",
+                    help="train and evaluate the learned starting-point proposal; 0 to skip")
+    ap.add_argument("--learned-time-limit", type=float, default=20.0, help="seconds per fit call in the learned leg")
     ap.add_argument("--learned-polish", action="store_true",
                     help="in the learned leg, also fit each learned start's couplings first (coupling object)")
     ap.add_argument("--scale", type=float, default=1.0,
@@ -629,6 +715,28 @@ def main():
     peak, peak_kind = peaks()
     achieved = bpp / (ms * 1e-3) / 1e9
 
+    # ---- the conjugate-gradient product: H v passes reusing the full pass's sums at th ----
+    L.eval_device(d_th.data_ptr(), d_v.data_ptr(), d_out.data_ptr(), True, True)  # full pass keeps the sums
+    for _ in range(3):
+        L.hvp_reuse_device(d_th.data_ptr(), d_v.data_ptr(), d_out.data_ptr())
+    torch.cuda.synchronize()
+    L.sync()
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for _ in range(args.steps):
+        L.hvp_reuse_device(d_th.data_ptr(), d_v.data_ptr(), d_out.data_ptr())
+    r1.record(stream)
+    torch.cuda.synchronize()
+    L.sync()
+    reuse_ms = r0.elapsed_time(r1) / args.steps
+    reuse = {"ms_per_pass": reuse_ms, "event_amps_per_s": units_per_pass(nd, nm, K) / (reuse_ms * 1e-3),
+             "roofline": {"bound": "hbm", "achieved": bytes_per_pass(nd, nm, K, S) / (reuse_ms * 1e-3) / 1e9,
+                          "peak": peaks()[0], "unit": "GB/s",
+                          "frac": bytes_per_pass(nd, nm, K, S) / (reuse_ms * 1e-3) / 1e9 / peaks()[0],
+                          "peak_kind": peaks()[1], "algorithmic_bytes_per_launch": bytes_per_pass(nd, nm, K, S)},
+             "note": "H v at the theta of the last full pass: Q sums, G and the gradient reused, P1, P2 and "
+                     "Gdot formed (one inner CG iteration of a matrix-free Newton-CG solve)"}
+
     # ---- end to end through the C ABI with host vectors (pinned staging inside) ----
     e2e_steps = max(1, args.steps)
     torch.cuda.synchronize()
@@ -640,29 +748,40 @@ def main():
 
     fit = None
     if args.fits > 0 and rank == 0:
+        t0 = time.perf_counter()
         fit = fit_metric(L, wl, args.fits, time_limit=args.fit_time_limit)
+        fit["leg_s"] = time.perf_counter() - t0
 
     coupling = None
     if rank == 0 and not args.no_coupling:
         coupling = coupling_metric(L, wl)
 
     batching = None
-    if args.batching and rank == 0:
+    if args.batching not in ("", "0") and rank == 0:
         n_toys, n_starts = (int(x) for x in args.batching.split(","))
+        t0 = time.perf_counter()
         batching = batching_metric(n_toys, n_starts, time_limit=args.fit_time_limit)
+        batching["leg_s"] = time.perf_counter() - t0
 
     variants = None
     if rank == 0 and not args.no_variants:
         variants = variant_metric(wl)
+
+    diff = None
+    if rank == 0 and not args.no_diff:
+        diff = diff_metric()
 
     mlp_step = None
     if args.mlp_timing and rank == 0:
         mlp_step = mlp_step_metric()
 
     learned = None
-    if args.learned and rank == 0:
+    if args.learned not in ("", "0") and rank == 0:
         n_train, n_eval, n_rand = (int(x) for x in args.learned.split(","))
-        learned = learned_metric(n_train, n_eval, n_rand, time_limit=args.fit_time_limit, polish=args.learned_polish)
+        t0 = time.perf_counter()
+        learned = learned_metric(n_train, n_eval, n_rand, time_limit=args.learned_time_limit,
+                                 polish=args.learned_polish)
+        learned["leg_s"] = time.perf_counter() - t0
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -689,6 +808,7 @@ def main():
             "gpu_launches": args.steps,
             "clocks": clk.summary(),
         }
+        res["hvp_reuse"] = reuse
         if cpu is not None:
             res["cpu_baseline"] = cpu
         if fit is not None:
@@ -699,6 +819,8 @@ def main():
             res["coupling"] = coupling
         if variants is not None:
             res["variants"] = variants
+        if diff is not None:
+            res["diff"] = diff
         if mlp_step is not None:
             res["mlp_step"] = mlp_step
         if learned is not None:

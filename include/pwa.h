@@ -97,7 +97,8 @@ typedef struct {
 
 /* One outer Newton iteration of a fit, as recorded when the caller asks for
  * a trace (pwa_fit_opts.trace).  cg_exit: 1 negative curvature, 2 residual
- * below the forcing tolerance, 3 inner iteration limit. */
+ * below the forcing tolerance, 3 inner iteration limit, 4 trust-region
+ * boundary (method 1). */
 typedef struct pwa_fit_iter {
     double nll;        /* NLL at the start of the iteration                     */
     double grad_max;   /* max |grad| there                                      */
@@ -125,6 +126,12 @@ typedef struct {
                              the same iteration, far fewer passes over F (the
                              default; handles with K > 44 and the coupling and
                              variant fits always run matrix-free)            */
+    int method;           /* 0: line-search Newton-CG (Nocedal & Wright Alg. 7.1,
+                             scipy's Newton-CG, the paper's method; default);
+                             1: trust-region Newton-CG (Alg. 7.2, CG-Steihaug,
+                             scipy's trust-ncg): the CG stops on the region's
+                             boundary instead of on negative curvature, one
+                             f, g evaluation per outer iteration            */
     int trace_cap;        /* records per fit that trace can hold (0: no trace)      */
     pwa_fit_iter* trace;  /* host [fits][trace_cap] or NULL: per-iteration record;
                              fits are numbered in the order of theta0 (over all
@@ -221,6 +228,24 @@ pwa_status pwa_eval(pwa_handle* h, const double* theta, const double* v,
 pwa_status pwa_eval_device(pwa_handle* h, const double* d_theta, const double* d_v,
                            double* d_out, int want_grad, int want_hv);
 
+/* H v at theta from a cheaper pass that reuses what the last full H v pass
+ * (pwa_eval or pwa_hvp with hv, pwa_eval_device with want_hv, or the
+ * Newton-CG inner loop) computed at the SAME theta: in Eq. 7 only the sums
+ * of the direction derivatives (P1 = sum a Ddot_t B, P2 = sum a Ddot_t B^2
+ * with Ddot_t = a Ddot - b D) and Gdot depend on v; the Q sums, G, sum w ln I
+ * and the gradient do not.  So the pass accumulates 4 reals per resonance
+ * instead of 10 and, on MC events, skips the coherent sum A and the adjoint D
+ * (only Adot and Ddot are formed); Gdot = (dG/dtheta) . v from the kept
+ * sums.  This is the product a conjugate-gradient solve repeats at one
+ * theta.  Returns the same H v as the full pass to the pass's own accuracy.
+ * If the last full pass was at another theta (checked on the device, exact
+ * comparison), the call fails: PWA_EINVAL (host call), or the device error
+ * reported by pwa_sync (device call; d_out is then NaN).  theta, v, hv: host
+ * [P]; d_theta, d_v: device [P]; d_out: device [1 + 2P] (NLL, gradient,
+ * H v as pwa_eval_device writes them). */
+pwa_status pwa_hvp_reuse(pwa_handle* h, const double* theta, const double* v, double* hv);
+pwa_status pwa_hvp_reuse_device(pwa_handle* h, const double* d_theta, const double* d_v, double* d_out);
+
 /* pwa_eval_device without any device allocation (the paper has no
  * counterpart: this is a deployment variant).  For callers that may not call
  * cudaMalloc while they evaluate -- e.g. code under an external memory manager
@@ -233,7 +258,10 @@ pwa_status pwa_eval_device(pwa_handle* h, const double* d_theta, const double* d
  * GPU loading the library holds until exit; a handle needing more
  * (grid blocks + groups) x (20 K + 6) x 8 bytes + counters is refused with
  * PWA_EINVAL.  The array's device address is looked up on the first call on
- * each device: make that first call before any stream capture.  All calls
+ * each device and kept for the life of the process: make that first call
+ * before any stream capture, and do not use this entry point after a
+ * cudaDeviceReset in the same process (the kept address belongs to the
+ * destroyed context).  All calls
  * share the array and the counters are cleared at each call, so calls whose
  * kernels overlap on the GPU (e.g. on different streams) race and must not be
  * issued concurrently. */

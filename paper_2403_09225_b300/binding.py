@@ -44,7 +44,7 @@ class pwa_fit_iter(ctypes.Structure):
 class pwa_fit_opts(ctypes.Structure):
     _fields_ = [("xtol", ctypes.c_double), ("gtol", ctypes.c_double), ("maxiter", ctypes.c_int),
                 ("cg_maxiter", ctypes.c_int), ("time_limit_s", ctypes.c_double), ("matrix_free", ctypes.c_int),
-                ("trace_cap", ctypes.c_int), ("trace", ctypes.POINTER(pwa_fit_iter))]
+                ("method", ctypes.c_int), ("trace_cap", ctypes.c_int), ("trace", ctypes.POINTER(pwa_fit_iter))]
 
 
 class pwa_lineshape(ctypes.Structure):
@@ -85,7 +85,7 @@ class PwaError(RuntimeError):
 
 
 #: every symbol include/pwa.h declares
-EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "pwa_grad", "pwa_hvp", "pwa_hessian", "pwa_release_event_copies",
+EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "pwa_grad", "pwa_hvp", "pwa_hessian", "pwa_hvp_reuse", "pwa_hvp_reuse_device", "pwa_release_event_copies",
            "pwa_device_bytes",
            "pwa_eval", "pwa_eval_device", "pwa_eval_device_noalloc", "pwa_eval_batch", "pwa_eval_batch_device",
            "pwa_sync", "pwa_event_intensity", "pwa_newton_cg_fit", "pwa_newton_cg_fit_batch",
@@ -118,6 +118,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pwa_hvp": (st, [H, dp, dp, dp]),
         "pwa_eval": (st, [H, dp, dp, dp, dp, dp]),
         "pwa_hessian": (st, [H, dp, dp, dp, dp]),
+        "pwa_hvp_reuse": (st, [H, dp, dp, dp]),
+        "pwa_hvp_reuse_device": (st, [H, vp, vp, vp]),
         "pwa_release_event_copies": (st, [H]),
         "pwa_device_bytes": (st, [H, ctypes.POINTER(ctypes.c_longlong)]),
         "pwa_eval_device": (st, [H, vp, vp, vp, i, i]),
@@ -303,6 +305,17 @@ class Likelihood:
         self._check(lib().pwa_device_bytes(self._h, ctypes.byref(out)))
         return out.value
 
+    def hvp_reuse(self, theta, v) -> np.ndarray:
+        """H v reusing the sums of the last full H v pass at the same theta."""
+        th = _f64(theta, self.P)
+        vv = _f64(v, self.P)
+        hv = np.empty(self.P)
+        self._check(lib().pwa_hvp_reuse(self._h, _dptr(th), _dptr(vv), _dptr(hv)))
+        return hv
+
+    def hvp_reuse_device(self, d_theta: int, d_v: int, d_out: int):
+        self._check(lib().pwa_hvp_reuse_device(self._h, d_theta, d_v, d_out))
+
     def hessian(self, theta):
         """(NLL, gradient [P], Hessian [P, P]) at theta from one Hessian pass."""
         th = _f64(theta, self.P)
@@ -381,14 +394,15 @@ class Likelihood:
 
     # -- fitting --
     def fit(self, theta0, xtol: float = 1e-8, gtol: float = 0.0, maxiter: int = 0, cg_maxiter: int = 0,
-            time_limit_s: float = 0.0, trace: int = 0, matrix_free: bool = False):
+            time_limit_s: float = 0.0, trace: int = 0, matrix_free: bool = False, method: int = 0):
         """Newton-CG fit from theta0; with trace > 0 the info dict carries the
         first `trace` outer iterations' records under "trace".  matrix_free:
         every CG step is one fused H v pass instead of a product with the
-        outer iteration's Hessian (pwa_hessian)."""
+        outer iteration's Hessian (pwa_hessian).  method: 0 line search
+        (the paper's), 1 trust region."""
         th = _f64(theta0, self.P)
         out = np.empty(self.P)
-        opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s, int(matrix_free))
+        opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s, int(matrix_free), int(method))
         tbuf = _attach_trace(opts, 1, trace)
         res = pwa_fit_result()
         st = lib().pwa_newton_cg_fit(self._h, _dptr(th), ctypes.byref(opts), _dptr(out), ctypes.byref(res))
@@ -402,13 +416,13 @@ class Likelihood:
         return out, info
 
     def fit_batch(self, thetas0, xtol: float = 1e-8, gtol: float = 0.0, maxiter: int = 0, cg_maxiter: int = 0,
-                  time_limit_s: float = 0.0, trace: int = 0, matrix_free: bool = False):
+                  time_limit_s: float = 0.0, trace: int = 0, matrix_free: bool = False, method: int = 0):
         """B fits (rows of thetas0) in lockstep with batched passes; returns
         (theta [B, P], list of per-fit info dicts, converged-or-time-limit for all)."""
         th = _f64(thetas0).reshape(-1, self.P)
         B = th.shape[0]
         out = np.empty((B, self.P))
-        opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s, int(matrix_free))
+        opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s, int(matrix_free), int(method))
         tbuf = _attach_trace(opts, B, trace)
         res = (pwa_fit_result * B)()
         st = lib().pwa_newton_cg_fit_batch(self._h, B, _dptr(th), ctypes.byref(opts), _dptr(out), res)
@@ -507,7 +521,7 @@ class Coupling:
 
 
 def fit_multi(likelihoods, thetas0, xtol: float = 1e-8, gtol: float = 0.0, maxiter: int = 0,
-              cg_maxiter: int = 0, time_limit_s: float = 0.0, matrix_free: bool = False):
+              cg_maxiter: int = 0, time_limit_s: float = 0.0, matrix_free: bool = False, method: int = 0):
     """Lockstep fits over several likelihoods (one group of starts per
     likelihood; their batched passes run concurrently).  thetas0[i]: [B_i, P_i].
     Returns ([theta [B_i, P_i]], [[info per fit]], all converged-or-time-limit)."""
@@ -521,7 +535,7 @@ def fit_multi(likelihoods, thetas0, xtol: float = 1e-8, gtol: float = 0.0, maxit
     th_p = (dpp * n)(*[_dptr(t) for t in ths])
     out_p = (dpp * n)(*[_dptr(o) for o in outs])
     res_p = (ctypes.POINTER(pwa_fit_result) * n)(*[ctypes.cast(r, ctypes.POINTER(pwa_fit_result)) for r in res])
-    opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s, int(matrix_free))
+    opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s, int(matrix_free), int(method))
     st = lib().pwa_newton_cg_fit_multi(n, hs, Bs, th_p, ctypes.byref(opts), out_p, res_p)
     if st not in (PWA_OK, PWA_ENOCONV):
         msgs = "; ".join(filter(None, (lib().pwa_last_error(L._h).decode() for L in likelihoods)))

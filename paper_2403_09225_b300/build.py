@@ -27,7 +27,7 @@ HEADERS = ["pass_kernel.cuh", "pwa_internal.h", "tcgen05.cuh"]
 SHAPES_S = (1, 2, 3, 4)
 SHAPES_W = (1, 2, 4, 8)
 SHAPES_KPW = (1, 2, 3, 4, 5, 6, 7, 8)
-MODES = {"nll": "MODE_NLL", "grad": "MODE_GRAD", "hvp": "MODE_HVP"}
+MODES = {"nll": "MODE_NLL", "grad": "MODE_GRAD", "hvp": "MODE_HVP", "hvpr": "MODE_HVP_REUSE"}
 
 
 def _instance_units() -> dict:

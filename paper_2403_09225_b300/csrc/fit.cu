@@ -169,14 +169,15 @@ struct DeviceCG {
         return PWA_OK;
     }
 
-    // capture kCgBatch iterations (HVP pass at x along d, then the update) once
+    // capture kCgBatch iterations (H v pass at x along d, reusing the sums of
+    // the solve's first, full pass at x; then the update) once
     pwa_status capture(int maxiter)
     {
         cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return pwa::cuda_error(h, e, "cudaStreamBeginCapture");
         pwa_status st = PWA_OK;
         for (int b = 0; b < kCgBatch && st == PWA_OK; ++b) {
-            st = pwa::launch_pass(h, c.x, c.d, c.out, pwa::MODE_HVP, c.flags);
+            st = pwa::launch_pass(h, c.x, c.d, c.out, pwa::MODE_HVP_REUSE, c.flags);
             if (st == PWA_OK) {
                 cg_step_kernel<<<1, kCgThreads, 0, h->stream>>>(c, P, maxiter);
                 e = cudaGetLastError();
@@ -207,6 +208,12 @@ struct DeviceCG {
         cg_init_kernel<<<1, kCgThreads, 0, h->stream>>>(c, P, eps);
         e = cudaGetLastError();
         if (e != cudaSuccess) return pwa::cuda_error(h, e, "cg_init launch");
+        // the first iteration's product with the full pass, which keeps the sums at x for the others
+        pwa_status st0 = pwa::launch_pass(h, c.x, c.d, c.out, pwa::MODE_HVP, c.flags);
+        if (st0 != PWA_OK) return st0;
+        cg_step_kernel<<<1, kCgThreads, 0, h->stream>>>(c, P, maxiter);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return pwa::cuda_error(h, e, "cg_step launch");
         int flags[3] = {0, 0, 0};
         for (int done_batches = 0;; ++done_batches) {
             e = cudaGraphLaunch(exec, h->stream);
@@ -579,6 +586,202 @@ FitTask newton_cg(FitState& s)
     s.iters = k;
 }
 
+// ---------------------------------------------------------------------------
+// Trust-region Newton-CG (Nocedal & Wright Algorithm 7.2, CG-Steihaug, inside
+// the trust-region iteration of their Algorithm 4.1): the inner CG stops at
+// the trust-region boundary instead of giving up on negative curvature, and
+// no line search is needed -- one f, g evaluation per outer iteration.  The
+// acceptance ratio rho = actual / predicted reduction is taken from f where
+// the predicted reduction is above the NLL's FP32 resolution; below it a step
+// is taken when the NLL does not rise beyond that resolution and the
+// gradient along the step meets the line search's curvature test, and a
+// rejected step whose predicted decrease g.p is below the resolution ends the
+// fit at the precision limit -- the same concern that gives the line search
+// its approximate Wolfe test.
+// ---------------------------------------------------------------------------
+
+// tau >= 0 with |z + tau d| = delta
+double to_boundary(const std::vector<double>& z, const std::vector<double>& d, double delta)
+{
+    const double dd = dot(d, d), zd = dot(z, d), zz = dot(z, z);
+    const double disc = std::max(0.0, zd * zd - dd * (zz - delta * delta));
+    return dd > 0 ? (-zd + std::sqrt(disc)) / dd : 0.0;
+}
+
+FitTask newton_cg_tr(FitState& s)
+{
+    const int n = s.P;
+    const double eta = 0.15, delta_max = 1e3;
+    s.req = Req::FG;
+    s.rx = s.x.data();
+    s.rf = &s.f;
+    s.rg = s.g.data();
+    co_await Suspend{};
+    if (s.req_status != PWA_OK) {
+        s.error = s.req_status;
+        co_return;
+    }
+    std::vector<double> z(n), r(n), d(n), Hd(n), Hz(n), xn(n), gn(n), p(n);
+    double delta = 1.0;
+    int k = 0;
+    while (k < s.maxiter) {
+        double gmax = 0.0;
+        for (double v : s.g) gmax = std::max(gmax, std::fabs(v));
+        if (s.o.gtol > 0 && gmax <= s.o.gtol) {
+            s.status = PWA_FIT_GTOL;
+            break;
+        }
+        const double gnorm = std::sqrt(dot(s.g, s.g));
+        const double eps = std::min(0.5, std::sqrt(gnorm)) * gnorm;
+        s.cur_it = pwa_fit_iter();
+        s.cur_it.nll = s.f;
+        s.cur_it.grad_max = gmax;
+        s.cur_it.cg_eps = eps;
+        if (s.explicit_h) {
+            s.H.resize((size_t)n * n);
+            s.req = Req::HESS;
+            s.rx = s.x.data();
+            s.rH = s.H.data();
+            co_await Suspend{};
+            if (s.req_status != PWA_OK) {
+                s.error = s.req_status;
+                co_return;
+            }
+            s.cur_it.hessian = 1;
+        }
+        // ---- CG-Steihaug on the model m(p) = g.p + p.H.p / 2 within |p| <= delta ----
+        std::fill(z.begin(), z.end(), 0.0);
+        std::fill(Hz.begin(), Hz.end(), 0.0);  // H z, kept for the model value
+        r = s.g;
+        for (int i = 0; i < n; ++i) d[i] = -r[i];
+        double rr = dot(r, r);
+        for (int j = 0;; ++j) {
+            if (s.explicit_h) {
+                for (int i = 0; i < n; ++i) {
+                    const double* Hi = s.H.data() + (size_t)i * n;
+                    double acc = 0.0;
+                    for (int l = 0; l < n; ++l) acc += Hi[l] * d[l];
+                    Hd[i] = acc;
+                }
+            } else {
+                s.req = Req::HV;
+                s.rx = s.x.data();
+                s.rv = d.data();
+                s.rhv = Hd.data();
+                co_await Suspend{};
+                if (s.req_status != PWA_OK) {
+                    s.error = s.req_status;
+                    co_return;
+                }
+                ++s.n_hvp;
+            }
+            s.cur_it.cg_iters = j + 1;
+            const double curv = dot(d, Hd);
+            if (!(curv > 0.0)) {  // negative curvature: follow d to the boundary
+                const double tau = to_boundary(z, d, delta);
+                for (int i = 0; i < n; ++i) {
+                    z[i] += tau * d[i];
+                    Hz[i] += tau * Hd[i];
+                }
+                s.cur_it.cg_exit = 1;
+                s.cur_it.cg_res = std::sqrt(rr);
+                break;
+            }
+            const double alpha = rr / curv;
+            double zz = 0.0;
+            for (int i = 0; i < n; ++i) zz += (z[i] + alpha * d[i]) * (z[i] + alpha * d[i]);
+            if (std::sqrt(zz) >= delta) {  // the step leaves the region: stop on its boundary
+                const double tau = to_boundary(z, d, delta);
+                for (int i = 0; i < n; ++i) {
+                    z[i] += tau * d[i];
+                    Hz[i] += tau * Hd[i];
+                }
+                s.cur_it.cg_exit = 4;
+                s.cur_it.cg_res = std::sqrt(rr);
+                break;
+            }
+            double rr_new = 0.0;
+            for (int i = 0; i < n; ++i) {
+                z[i] += alpha * d[i];
+                Hz[i] += alpha * Hd[i];
+                r[i] += alpha * Hd[i];
+                rr_new += r[i] * r[i];
+            }
+            if (std::sqrt(rr_new) < eps || j + 1 >= s.cg_maxiter) {
+                s.cur_it.cg_exit = std::sqrt(rr_new) < eps ? 2 : 3;
+                s.cur_it.cg_res = std::sqrt(rr_new);
+                break;
+            }
+            const double beta = rr_new / rr;
+            for (int i = 0; i < n; ++i) d[i] = -r[i] + beta * d[i];
+            rr = rr_new;
+        }
+        p = z;
+        ++k;
+        const double pred = -(dot(s.g, p) + 0.5 * dot(p, Hz));  // predicted reduction
+        const double pnorm = std::sqrt(dot(p, p));
+        s.cur_it.dir_deriv = dot(s.g, p);
+        // ---- trial point ----
+        for (int i = 0; i < n; ++i) xn[i] = s.x[i] + p[i];
+        double fn = 0.0;
+        s.req = Req::FG;
+        s.rx = xn.data();
+        s.rf = &fn;
+        s.rg = gn.data();
+        co_await Suspend{};
+        bool finite = true;
+        if (s.req_status == PWA_ENONFINITE) {
+            finite = false;
+        } else if (s.req_status != PWA_OK) {
+            s.error = s.req_status;
+            co_return;
+        }
+        s.cur_it.n_fev = 1;
+        const double resolution = 1e-7 * (1.0 + std::fabs(s.f));
+        double rho;
+        bool noise = false;  // the model's reduction is below what the NLL resolves
+        if (!finite || !std::isfinite(fn)) rho = -1.0;
+        else if (pred > 10.0 * resolution) rho = (s.f - fn) / pred;
+        else {
+            // judge by the gradient along p: the curvature test of the line search
+            noise = true;
+            const bool fok = fn <= s.f + resolution;
+            const bool curv = std::fabs(dot(gn, p)) <= 0.9 * std::fabs(dot(s.g, p));
+            rho = (fok && curv) ? 1.0 : -1.0;
+        }
+        if (rho < 0.25) delta = 0.25 * pnorm;
+        else if (rho > 0.75 && s.cur_it.cg_exit != 2 && s.cur_it.cg_exit != 3) delta = std::min(2.0 * delta, delta_max);
+        if (rho > eta) {
+            double smean = 0.0;
+            for (int i = 0; i < n; ++i) smean += std::fabs(p[i]);
+            smean /= std::max(n, 1);
+            s.x = xn;
+            s.f = fn;
+            s.g = gn;
+            s.cur_it.step = 1.0;
+            push_iter(s);
+            if (smean <= s.o.xtol) {
+                s.status = PWA_FIT_XTOL;
+                break;
+            }
+        } else {
+            push_iter(s);
+            if (delta < 1e-12 * (1.0 + std::sqrt(dot(s.x, s.x))) ||
+                (noise && std::fabs(dot(s.g, p)) <= resolution)) {
+                s.status = PWA_FIT_PRECISION;  // no step the NLL can resolve
+                break;
+            }
+        }
+        if (s.o.time_limit_s > 0 && s.since_start() > s.o.time_limit_s) {
+            s.status = PWA_FIT_TIME_LIMIT;
+            break;
+        }
+    }
+    s.iters = k;
+}
+
+FitTask run_fit(FitState& s) { return s.o.method == 1 ? newton_cg_tr(s) : newton_cg(s); }
+
 void init_state(FitState& s, int n, const double* theta0, const pwa_fit_opts* opts_in)
 {
     s.P = n;
@@ -936,7 +1139,7 @@ pwa_status open_group(FitGroup& g, std::unique_ptr<RoundEvaluator> ev, int B, co
     for (int b = 0; b < B; ++b) {
         init_state(g.fits[b], P, theta0 + (size_t)b * P, opts);
         g.fits[b].explicit_h &= g.ev->has_hessian();
-        g.tasks.push_back(newton_cg(g.fits[b]));
+        g.tasks.push_back(run_fit(g.fits[b]));
         g.tasks[b].h.resume();  // runs to its first request
     }
     return PWA_OK;
@@ -1043,6 +1246,8 @@ extern "C" void pwa_fit_opts_default(pwa_fit_opts* o)
     o->maxiter = 0;
     o->cg_maxiter = 0;
     o->time_limit_s = 0.0;
+    o->matrix_free = 0;
+    o->method = 0;
     o->trace_cap = 0;
     o->trace = nullptr;
 }
@@ -1064,7 +1269,7 @@ extern "C" pwa_status pwa_newton_cg_fit(pwa_handle* h, const double* theta0, con
     if (st != PWA_OK) return st;
 
     // one fit: every request is served at once
-    FitTask task = newton_cg(s);
+    FitTask task = run_fit(s);
     for (task.h.resume(); !task.h.done(); task.h.resume()) {
         switch (s.req) {
             case Req::FG:
@@ -1080,6 +1285,12 @@ extern "C" pwa_status pwa_newton_cg_fit(pwa_handle* h, const double* theta0, con
                 s.req_status = pwa::hessian_device(h, s.rx, nullptr, nullptr, s.rH);
                 if (s.req_status == PWA_ENONFINITE) h->err.clear();
                 break;
+            case Req::HV: {  // matrix-free trust-region CG: one fused pass per product
+                double f_unused = 0.0;
+                s.req_status = pwa_eval(h, s.rx, s.rv, &f_unused, nullptr, s.rhv);
+                if (s.req_status == PWA_ENONFINITE) h->err.clear();
+                break;
+            }
             default:
                 s.req_status = pwa::set_error(h, PWA_EINVAL, "internal: unexpected fit request");
                 break;

@@ -74,11 +74,14 @@ struct HessArgs {
 //   [0, 16 nblk)           data Gram of X, block b's 16 entries row-major
 //   [16 nblk, 32 nblk)     data Gram of z
 //   [32 nblk, 48 nblk)     MC Gram of X
-//   then Q [2 sets][NW warps][K][6] (Re, Im of Q1, Q2, Q3), then the scalars
-//   [NW][2] (sum w ln I of the data, G = sum I of the MC) per warp
-__host__ __device__ inline int hess_rec_len(int K, int nblk, int NW) { return 48 * nblk + 12 * NW * K + 2 * NW; }
+//   then Q [2 sets][K][6] (Re, Im of Q1, Q2, Q3), then the scalars [NW][2]
+//   (sum w ln I of the data, G = sum I of the MC) per warp
+__host__ __device__ inline int hess_rec_len(int K, int nblk, int NW) { return 48 * nblk + 12 * K + 2 * NW; }
 
-// block index -> (bi, bj), bi <= bj, enumerating the upper triangle row by row
+// block index -> (bi, bj), bi <= bj, enumerating the upper triangle row by
+// row.  Block (bi, bj) covers the Gram entries of columns bi + u K and
+// bj + v K (u, v = 0..3): the four columns of a block are K apart, so that
+// the threads of a warp (consecutive bj) read consecutive columns.
 __host__ __device__ inline void block_of(int b, int nb, int& bi, int& bj)
 {
     int i = 0, rem = b;
@@ -90,21 +93,32 @@ __host__ __device__ inline void block_of(int b, int nb, int& bi, int& bj)
     bj = i + rem;
 }
 
+constexpr int kKW = 3;  // resonances per warp in phase 1 (K <= 3 x warps)
+
+// Shared-memory row strides (floats): X and z are stored column-major, a
+// column's rows contiguous, so that phase 1 (a lane per event) writes 32
+// consecutive floats and phase 2 reads 16-byte groups of rows; the strides
+// are 4 (mod 8) floats... times an odd number of 16-byte groups, so the
+// columns a warp reads start in different bank groups.
+__host__ __device__ inline int x_stride(int S) { return 32 * S + 4; }
+constexpr int kZStride = 36;
+
 template <int S, int NT, int NB>
 __global__ void __launch_bounds__(NT, 1) hess_kernel(const HessArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int NW = NT / 32;
-    constexpr int EPW = kE / NW;  // events per warp in phase 1
+    constexpr int RS = 32 * S + 4;  // x_stride(S)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int K = a.K, C = 4 * K, XS = C + 4;  // X row stride in floats (16-byte rows)
+    const int K = a.K, C = 4 * K;
 
-    // shared memory: stages[2] | KConst[K] | X [kE S][XS] | z [kE][XS] | mbarriers[2]
+    // shared memory: stages[2] | KConst[K] | X [C][RS] | z [C][36] | partial A [NW][2S][32] | mbarriers[2]
     unsigned char* stages = smem;
     KConst* kc = reinterpret_cast<KConst*>(smem + 2 * (size_t)a.stage_bytes);
     float* X = reinterpret_cast<float*>(kc + K);
-    float* Zs = X + (size_t)kE * S * XS;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(Zs + (size_t)kE * XS);
+    float* Zs = X + (size_t)C * RS;
+    float* PA = Zs + (size_t)C * kZStride;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(PA + NW * 2 * S * 32);
     __shared__ long long issued[2];
     __shared__ int s_abort;
 
@@ -153,16 +167,16 @@ __global__ void __launch_bounds__(NT, 1) hess_kernel(const HessArgs a)
     for (int m = 0; m < NB; ++m)
 #pragma unroll
         for (int u = 0; u < 16; ++u) R[m][u] = Zg[m][u] = 0.f;
-    // lane's resonances k = lane, lane + 32: Q sums (Re, Im of Q1, Q2, Q3)
-    float q[2][6];
+    // the warp's resonances k = warp + j NW; this lane's event's share of their Q sums
+    float q[kKW][6];
 #pragma unroll
-    for (int j = 0; j < 2; ++j)
+    for (int j = 0; j < kKW; ++j)
 #pragma unroll
         for (int u = 0; u < 6; ++u) q[j][u] = 0.f;
     float sc = 0.f;
 
     double* rec = a.rec + (size_t)blockIdx.x * a.rec_len;
-    const int offQ = 48 * a.nblk, offS = offQ + 12 * NW * K;
+    const int offQ = 48 * a.nblk, offS = offQ + 12 * K;
     // add the FP32 sums of the current window to the FP64 record of sample set smp
     auto fold = [&](int smp) {
         const int offR = smp == 0 ? 0 : 32 * a.nblk;
@@ -181,19 +195,18 @@ __global__ void __launch_bounds__(NT, 1) hess_kernel(const HessArgs a)
             }
         }
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int k = lane + 32 * j;
-            if (k < K) {
-                double* rq = rec + offQ + ((size_t)(smp * NW + warp) * K + k) * 6;
+        for (int j = 0; j < kKW; ++j) {
+            const int k = warp + j * NW;
 #pragma unroll
-                for (int u = 0; u < 6; ++u) rq[u] += (double)q[j][u];
+            for (int u = 0; u < 6; ++u) {
+                const float v = pwa::warp_sum(q[j][u]);
+                q[j][u] = 0.f;
+                if (lane == 0 && k < K) rec[offQ + ((size_t)smp * K + k) * 6 + u] += (double)v;
             }
-#pragma unroll
-            for (int u = 0; u < 6; ++u) q[j][u] = 0.f;
         }
-        const float s = pwa::warp_sum(sc);
+        const float v = pwa::warp_sum(sc);
         sc = 0.f;
-        if (lane == 0) rec[offS + 2 * warp + smp] += (double)s;
+        if (lane == 0) rec[offS + 2 * warp + smp] += (double)v;
     };
 
     int st = 0;
@@ -215,107 +228,135 @@ __global__ void __launch_bounds__(NT, 1) hess_kernel(const HessArgs a)
             if (tid == 0) s_abort = 1;
             break;
         }
-        const float2* Fs = reinterpret_cast<const float2*>(stages + (size_t)st * a.stage_bytes);
-        const float* Ft = reinterpret_cast<const float*>(Fs);
-        const float* m2s = reinterpret_cast<const float*>(Fs + (size_t)K * S * kE);
+        const float* Ft = reinterpret_cast<const float*>(stages + (size_t)st * a.stage_bytes);
+        const float* m2s = Ft + (size_t)2 * K * S * kE;
         const long long e_base = lt * kE;
-        const int nvalid = (int)min((long long)kE, a.nev[smp] - e_base);
+        const int e = lane;  // this lane's event in the tile
+        const bool valid = e < (int)min((long long)kE, a.nev[smp] - e_base);
 
-        // ---- phase 1: a warp per event, a lane per resonance ----
-        for (int ie = 0; ie < EPW; ++ie) {
-            const int e = warp * EPW + ie;
-            const bool valid = e < nvalid;
-            float br[2], bim[2], fr[2][S], fi[2][S];
-            float Ar[S], Ai[S];
+        // ---- phase 1a: the warp's resonances for this lane's event: B, F, partial A ----
+        float br[kKW], bim[kKW], fr[kKW][S], fi[kKW][S];
+        float Ar[S], Ai[S];
 #pragma unroll
-            for (int s = 0; s < S; ++s) Ar[s] = Ai[s] = 0.f;
+        for (int s = 0; s < S; ++s) Ar[s] = Ai[s] = 0.f;
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int k = lane + 32 * j;
-                br[j] = bim[j] = 0.f;
+        for (int j = 0; j < kKW; ++j) {
+            const int k = warp + j * NW;
+            br[j] = bim[j] = 0.f;
 #pragma unroll
-                for (int s = 0; s < S; ++s) fr[j][s] = fi[j][s] = 0.f;
-                if (k < K) {
-                    const KConst c = kc[k];
-                    pwa::breit_wigner(c, m2s[c.ch * kE + e], br[j], bim[j]);
-                    const float cr = c.gre * br[j] - c.gim * bim[j], ci = c.gre * bim[j] + c.gim * br[j];
-                    const int p = (e + c.shift) & (kE - 1);
+            for (int s = 0; s < S; ++s) fr[j][s] = fi[j][s] = 0.f;
+            if (k < K) {
+                const KConst c = kc[k];
+                pwa::breit_wigner(c, m2s[c.ch * kE + e], br[j], bim[j]);
+                const float cr = c.gre * br[j] - c.gim * bim[j], ci = c.gre * bim[j] + c.gim * br[j];
+                const int p = (e + c.shift) & (kE - 1);
+                if constexpr (S % 2 == 0) {
+#pragma unroll
+                    for (int qq = 0; qq < S / 2; ++qq) {
+                        // (Re F_2q, Re F_2q+1, Im F_2q, Im F_2q+1) of (k, p): one 16-byte load
+                        const float4 f4 = *reinterpret_cast<const float4*>(Ft + 4 * ((k * (S / 2) + qq) * kE + p));
+                        fr[j][2 * qq] = f4.x;
+                        fr[j][2 * qq + 1] = f4.y;
+                        fi[j][2 * qq] = f4.z;
+                        fi[j][2 * qq + 1] = f4.w;
+                    }
+                } else {
 #pragma unroll
                     for (int s = 0; s < S; ++s) {
-                        const int o = pwa::f_re(k, s, p, S, kE);
-                        fr[j][s] = Ft[o];
-                        fi[j][s] = Ft[o + pwa::f_im_off(S)];
-                        Ar[s] += cr * fr[j][s] - ci * fi[j][s];
-                        Ai[s] += cr * fi[j][s] + ci * fr[j][s];
+                        const float2 f2 = *reinterpret_cast<const float2*>(Ft + 2 * ((k * S + s) * kE + p));
+                        fr[j][s] = f2.x;
+                        fi[j][s] = f2.y;
                     }
                 }
-            }
-#pragma unroll
-            for (int s = 0; s < S; ++s) {
-                Ar[s] = pwa::warp_sum(Ar[s]);
-                Ai[s] = pwa::warp_sum(Ai[s]);
-            }
-            float I = 0.f;
-#pragma unroll
-            for (int s = 0; s < S; ++s) I += Ar[s] * Ar[s] + Ai[s] * Ai[s];
-            float aw = 0.f, sqa = 0.f, zw = 0.f;
-            if (smp == 0) {
-                const float w = m2s[3 * kE + e];
-                const bool good = I > 0.f && I < INFINITY;
-                if (valid && good) {
-                    aw = w / I;
-                    sqa = sqrtf(aw);
-                    zw = sqrtf(w) / I;
-                    if (lane == 0) sc += w * logf(I);
-                } else if (valid && lane == 0) {
-                    atomicMin(a.bad, (unsigned long long)(e_base + e));
-                    atomicOr(a.err, pwa::ERR_NONFINITE);
-                }
-            } else {
-                const bool good = I < INFINITY;
-                if (valid && good) {
-                    aw = 1.f;
-                    sqa = 1.f;
-                    if (lane == 0) sc += I;
-                } else if (valid && lane == 0) {
-                    atomicMin(a.bad, (unsigned long long)(a.nev[0] + e_base + e));
-                    atomicOr(a.err, pwa::ERR_NONFINITE);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int k = lane + 32 * j;
-                if (k >= K) continue;
-                const float b1r = br[j], b1i = bim[j];
-                const float b2r = b1r * b1r - b1i * b1i, b2i = 2.f * b1r * b1i;
-                const float b3r = b2r * b1r - b2i * b1i, b3i = b2r * b1i + b2i * b1r;
-                float Dr = 0.f, Di = 0.f;  // D = sum_s conj(A_s) F_ks
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
-                    Dr += Ar[s] * fr[j][s] + Ai[s] * fi[j][s];
-                    Di += Ar[s] * fi[j][s] - Ai[s] * fr[j][s];
-                    float* xr = X + (size_t)(e * S + s) * XS;
-                    // V1 = B F, V2 = B^2 F, weighted by sqrt(a)
-                    const float v1r = b1r * fr[j][s] - b1i * fi[j][s], v1i = b1r * fi[j][s] + b1i * fr[j][s];
-                    const float v2r = b2r * fr[j][s] - b2i * fi[j][s], v2i = b2r * fi[j][s] + b2i * fr[j][s];
-                    *reinterpret_cast<float2*>(xr + 2 * k) = make_float2(sqa * v1r, sqa * v1i);
-                    *reinterpret_cast<float2*>(xr + 2 * (K + k)) = make_float2(sqa * v2r, sqa * v2i);
+                    Ar[s] += cr * fr[j][s] - ci * fi[j][s];
+                    Ai[s] += cr * fi[j][s] + ci * fr[j][s];
                 }
-                const float z1r = b1r * Dr - b1i * Di, z1i = b1r * Di + b1i * Dr;
-                const float z2r = b2r * Dr - b2i * Di, z2i = b2r * Di + b2i * Dr;
-                const float z3r = b3r * Dr - b3i * Di, z3i = b3r * Di + b3i * Dr;
-                if (smp == 0) {
-                    float* zr = Zs + (size_t)e * XS;
-                    *reinterpret_cast<float2*>(zr + 2 * k) = make_float2(zw * z1r, zw * z1i);
-                    *reinterpret_cast<float2*>(zr + 2 * (K + k)) = make_float2(zw * z2r, zw * z2i);
-                }
-                q[j][0] = fmaf(aw, z1r, q[j][0]);
-                q[j][1] = fmaf(aw, z1i, q[j][1]);
-                q[j][2] = fmaf(aw, z2r, q[j][2]);
-                q[j][3] = fmaf(aw, z2i, q[j][3]);
-                q[j][4] = fmaf(aw, z3r, q[j][4]);
-                q[j][5] = fmaf(aw, z3i, q[j][5]);
             }
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            PA[(warp * 2 * S + 2 * s) * 32 + e] = Ar[s];
+            PA[(warp * 2 * S + 2 * s + 1) * 32 + e] = Ai[s];
+        }
+        __syncthreads();
+        // ---- phase 1b: the coherent sums of the lane's event (every warp adds the partials) ----
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            float xr = 0.f, xi = 0.f;
+            for (int w = 0; w < NW; ++w) {
+                xr += PA[(w * 2 * S + 2 * s) * 32 + e];
+                xi += PA[(w * 2 * S + 2 * s + 1) * 32 + e];
+            }
+            Ar[s] = xr;
+            Ai[s] = xi;
+        }
+        float I = 0.f;
+#pragma unroll
+        for (int s = 0; s < S; ++s) I += Ar[s] * Ar[s] + Ai[s] * Ai[s];
+        float aw = 0.f, sqa = 0.f, zw = 0.f;
+        if (smp == 0) {
+            const float w = m2s[3 * kE + e];
+            const bool good = I > 0.f && I < INFINITY;
+            if (valid && good) {
+                aw = w / I;
+                sqa = sqrtf(aw);
+                zw = sqrtf(w) / I;
+                if (warp == 0) sc += w * logf(I);
+            } else if (valid && warp == 0) {
+                atomicMin(a.bad, (unsigned long long)(e_base + e));
+                atomicOr(a.err, pwa::ERR_NONFINITE);
+            }
+        } else {
+            const bool good = I < INFINITY;
+            if (valid && good) {
+                aw = 1.f;
+                sqa = 1.f;
+                if (warp == 0) sc += I;
+            } else if (valid && warp == 0) {
+                atomicMin(a.bad, (unsigned long long)(a.nev[0] + e_base + e));
+                atomicOr(a.err, pwa::ERR_NONFINITE);
+            }
+        }
+        // ---- phase 1c: the warp's columns of X and z for this event, its Q sums ----
+#pragma unroll
+        for (int j = 0; j < kKW; ++j) {
+            const int k = warp + j * NW;
+            if (k >= K) continue;
+            const float b1r = br[j], b1i = bim[j];
+            const float b2r = b1r * b1r - b1i * b1i, b2i = 2.f * b1r * b1i;
+            const float b3r = b2r * b1r - b2i * b1i, b3i = b2r * b1i + b2i * b1r;
+            float* x1r = X + (size_t)(2 * k) * RS;            // column 2 k: Re (B F); 2 k + 1: Im
+            float* x2r = X + (size_t)(2 * (K + k)) * RS;      // column 2 (K + k): Re (B^2 F); + 1: Im
+            float Dr = 0.f, Di = 0.f;  // D = sum_s conj(A_s) F_ks
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                Dr += Ar[s] * fr[j][s] + Ai[s] * fi[j][s];
+                Di += Ar[s] * fi[j][s] - Ai[s] * fr[j][s];
+                const float v1r = b1r * fr[j][s] - b1i * fi[j][s], v1i = b1r * fi[j][s] + b1i * fr[j][s];
+                const float v2r = b2r * fr[j][s] - b2i * fi[j][s], v2i = b2r * fi[j][s] + b2i * fr[j][s];
+                const int r = s * 32 + e;
+                x1r[r] = sqa * v1r;
+                x1r[RS + r] = sqa * v1i;
+                x2r[r] = sqa * v2r;
+                x2r[RS + r] = sqa * v2i;
+            }
+            const float z1r = b1r * Dr - b1i * Di, z1i = b1r * Di + b1i * Dr;
+            const float z2r = b2r * Dr - b2i * Di, z2i = b2r * Di + b2i * Dr;
+            const float z3r = b3r * Dr - b3i * Di, z3i = b3r * Di + b3i * Dr;
+            if (smp == 0) {
+                Zs[(size_t)(2 * k) * kZStride + e] = zw * z1r;
+                Zs[(size_t)(2 * k + 1) * kZStride + e] = zw * z1i;
+                Zs[(size_t)(2 * (K + k)) * kZStride + e] = zw * z2r;
+                Zs[(size_t)(2 * (K + k) + 1) * kZStride + e] = zw * z2i;
+            }
+            q[j][0] = fmaf(aw, z1r, q[j][0]);
+            q[j][1] = fmaf(aw, z1i, q[j][1]);
+            q[j][2] = fmaf(aw, z2r, q[j][2]);
+            q[j][3] = fmaf(aw, z2i, q[j][3]);
+            q[j][4] = fmaf(aw, z3r, q[j][4]);
+            q[j][5] = fmaf(aw, z3i, q[j][5]);
         }
         __syncthreads();  // X and z complete; the stage has been read
         if (tid == 0) {
@@ -331,34 +372,56 @@ __global__ void __launch_bounds__(NT, 1) hess_kernel(const HessArgs a)
             }
         }
 
-        // ---- phase 2: Gram blocks over the tile's rows ----
+        // ---- phase 2: Gram blocks over the tile's rows, 4 rows per 16-byte load ----
 #pragma unroll
         for (int m = 0; m < NB; ++m) {
             if (bi[m] < 0) continue;
-            const float* xi0 = X + 4 * bi[m];
-            const float* xj0 = X + 4 * bj[m];
-#pragma unroll 4
-            for (int r = 0; r < kE * S; ++r) {
-                const float4 xi = *reinterpret_cast<const float4*>(xi0 + (size_t)r * XS);
-                const float4 xj = *reinterpret_cast<const float4*>(xj0 + (size_t)r * XS);
-                const float u[4] = {xi.x, xi.y, xi.z, xi.w}, v[4] = {xj.x, xj.y, xj.z, xj.w};
+            const float* xi0 = X + (size_t)bi[m] * RS;
+            const float* xj0 = X + (size_t)bj[m] * RS;
+            const size_t cs = (size_t)K * RS;  // stride between a block's columns
+#pragma unroll 2
+            for (int r = 0; r < 32 * S; r += 4) {
+                float4 xi[4], xj[4];
 #pragma unroll
-                for (int p = 0; p < 4; ++p)
+                for (int u = 0; u < 4; ++u) {
+                    xi[u] = *reinterpret_cast<const float4*>(xi0 + u * cs + r);
+                    xj[u] = *reinterpret_cast<const float4*>(xj0 + u * cs + r);
+                }
 #pragma unroll
-                    for (int qq = 0; qq < 4; ++qq) R[m][4 * p + qq] = fmaf(u[p], v[qq], R[m][4 * p + qq]);
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        float acc = R[m][4 * u + v];
+                        acc = fmaf(xi[u].x, xj[v].x, acc);
+                        acc = fmaf(xi[u].y, xj[v].y, acc);
+                        acc = fmaf(xi[u].z, xj[v].z, acc);
+                        acc = fmaf(xi[u].w, xj[v].w, acc);
+                        R[m][4 * u + v] = acc;
+                    }
             }
             if (smp == 0) {
-                const float* zi0 = Zs + 4 * bi[m];
-                const float* zj0 = Zs + 4 * bj[m];
-#pragma unroll 4
-                for (int r = 0; r < kE; ++r) {
-                    const float4 xi = *reinterpret_cast<const float4*>(zi0 + (size_t)r * XS);
-                    const float4 xj = *reinterpret_cast<const float4*>(zj0 + (size_t)r * XS);
-                    const float u[4] = {xi.x, xi.y, xi.z, xi.w}, v[4] = {xj.x, xj.y, xj.z, xj.w};
+                const float* zi0 = Zs + (size_t)bi[m] * kZStride;
+                const float* zj0 = Zs + (size_t)bj[m] * kZStride;
+                const size_t zc = (size_t)K * kZStride;
+#pragma unroll 2
+                for (int r = 0; r < 32; r += 4) {
+                    float4 xi[4], xj[4];
 #pragma unroll
-                    for (int p = 0; p < 4; ++p)
+                    for (int u = 0; u < 4; ++u) {
+                        xi[u] = *reinterpret_cast<const float4*>(zi0 + u * zc + r);
+                        xj[u] = *reinterpret_cast<const float4*>(zj0 + u * zc + r);
+                    }
 #pragma unroll
-                        for (int qq = 0; qq < 4; ++qq) Zg[m][4 * p + qq] = fmaf(u[p], v[qq], Zg[m][4 * p + qq]);
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            float acc = Zg[m][4 * u + v];
+                            acc = fmaf(xi[u].x, xj[v].x, acc);
+                            acc = fmaf(xi[u].y, xj[v].y, acc);
+                            acc = fmaf(xi[u].z, xj[v].z, acc);
+                            acc = fmaf(xi[u].w, xj[v].w, acc);
+                            Zg[m][4 * u + v] = acc;
+                        }
                 }
             }
         }
@@ -431,8 +494,9 @@ void combine(const pwa_handle* h, const double* theta, const double* sum, int NW
             for (int u = 0; u < 4; ++u)
                 for (int v = 0; v < 4; ++v) {
                     const double x = sum[off + 16 * b + 4 * u + v];
-                    Gm[(size_t)(4 * bi + u) * C + 4 * bj + v] = x;
-                    Gm[(size_t)(4 * bj + v) * C + 4 * bi + u] = x;
+                    const int ca = bi + u * K, cb = bj + v * K;
+                    Gm[(size_t)ca * C + cb] = x;
+                    Gm[(size_t)cb * C + ca] = x;
                 }
         }
         return Gm;
@@ -444,16 +508,15 @@ void combine(const pwa_handle* h, const double* theta, const double* sum, int NW
         const double* r1 = R.data() + (size_t)(2 * c + 1) * C;
         return cplx(r0[2 * cp] + r1[2 * cp + 1], r0[2 * cp + 1] - r1[2 * cp]);
     };
-    const int offQ = 48 * nb, offS = offQ + 12 * NW * K;
+    const int offQ = 48 * nb, offS = offQ + 12 * K;
     std::vector<cplx> Q[2][3];
     for (int smp = 0; smp < 2; ++smp)
         for (int pp = 0; pp < 3; ++pp) Q[smp][pp].assign(K, cplx(0, 0));
     for (int smp = 0; smp < 2; ++smp)
-        for (int w = 0; w < NW; ++w)
-            for (int k = 0; k < K; ++k) {
-                const double* qq = sum + offQ + ((size_t)(smp * NW + w) * K + k) * 6;
-                for (int pp = 0; pp < 3; ++pp) Q[smp][pp][k] += cplx(qq[2 * pp], qq[2 * pp + 1]);
-            }
+        for (int k = 0; k < K; ++k) {
+            const double* qq = sum + offQ + ((size_t)smp * K + k) * 6;
+            for (int pp = 0; pp < 3; ++pp) Q[smp][pp][k] = cplx(qq[2 * pp], qq[2 * pp + 1]);
+        }
     double SlnI = 0.0, Gm = 0.0;
     for (int w = 0; w < NW; ++w) {
         SlnI += sum[offS + 2 * w];
@@ -563,8 +626,10 @@ pwa_status hessian_device(pwa_handle* h, const double* theta, double* nll, doubl
     if (!fn) return set_error(h, PWA_EINVAL, "no Hessian kernel for this S");
     const Tiling& t = h->tiling;
     const uint32_t stage = (uint32_t)((std::max(h->tile_bytes[0], h->tile_bytes[1]) + 127) / 128 * 128);
-    const int C = 4 * K, XS = C + 4;
-    const size_t smem = 2 * (size_t)stage + sizeof(KConst) * K + sizeof(float) * (size_t)(kE * S + kE) * XS + 16;
+    const int C = 4 * K;
+    const int NWp = NT / 32;
+    const size_t smem = 2 * (size_t)stage + sizeof(KConst) * K +
+                        sizeof(float) * ((size_t)C * (x_stride(S) + kZStride) + (size_t)NWp * 2 * S * 32) + 16;
     HessState& hs = h->hess;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -16,7 +16,9 @@
 // with cudaGetSymbolAddress (on the first call made on that device, with that
 // device current) and passed to the kernel.  All calls share the array and it
 // keeps the last call's contents, so the counters are cleared at every call
-// and calls whose kernels overlap on the GPU race on it.
+// and calls whose kernels overlap on the GPU race on it.  The looked-up
+// address is kept for the life of the process; after a cudaDeviceReset it
+// belongs to a destroyed context, so the entry point must not be used then.
 #include <cuda_runtime.h>
 
 #include <mutex>

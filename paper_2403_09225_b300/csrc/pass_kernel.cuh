@@ -44,8 +44,11 @@ constexpr int kNScal = 3;      // per-set scalars: data (sum w ln I, -, -), MC (
 constexpr int kWindow = 64;    // tiles between FP32 -> FP64 folds
 constexpr int kMaxThreads = 512;
 
-enum { MODE_NLL = 0, MODE_GRAD = 1, MODE_HVP = 2 };
-enum { ERR_TIMEOUT = 1, ERR_NONFINITE = 2 };
+// MODE_HVP_REUSE: H v at the theta of the last full HVP pass, taking the
+// per-resonance Q sums, G and the data NLL sum from that pass (they do not
+// depend on v) and accumulating only P1 and P2
+enum { MODE_NLL = 0, MODE_GRAD = 1, MODE_HVP = 2, MODE_HVP_REUSE = 3 };
+enum { ERR_TIMEOUT = 1, ERR_NONFINITE = 2, ERR_STALE = 4 };
 
 struct ResParam {       // parameter map of one resonance
     int idx[4];         // theta index of rho, phi, M, Gamma; -1 when fixed
@@ -106,6 +109,13 @@ struct PassArgs {
     long long timeout_cycles;
     const int* skip = nullptr;  // when set and non-zero at launch, the pass does nothing
     int* err_vec = nullptr;     // when set: per-vector error words [B] (besides err)
+    // [rec_len] totals then [P] theta of the last full HVP pass: written by a
+    // single-vector MODE_HVP pass, read (and checked against theta) by MODE_HVP_REUSE
+    double* cache = nullptr;
+    // events per warp of the tiling the tile records were laid out for (their
+    // resonance rotation, tile_shift); a kernel instance with H lanes per
+    // event reads them when 16 / ev divides H (always for H = 4 and 8)
+    int ev = 8;
 };
 
 // ---------------------------------------------------------------------------
@@ -280,16 +290,21 @@ __device__ __forceinline__ void load_row(const float2* row, float2 (&fv)[S])
 // sweep lane l handles event l and warp w owns resonances [w KPW, (w+1) KPW).
 constexpr int kTileE = 32;
 
+// The pass for one block: vector bt of the batch, block gb of the a.Gb blocks
+// that share that vector's events (tiles gb, gb + Gb, ...).  pass_kernel runs
+// it for every block of one handle; multi_pass_kernel (multi.cu) for blocks
+// of several handles in one launch.
 template <int MODE, int S, int W, int KPW>
-__global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
+__device__ __forceinline__ void pass_body(const PassArgs& a, const int bt, const int gb, unsigned char* smem)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
-    constexpr bool HV = MODE == MODE_HVP;
+    constexpr bool HV = MODE >= MODE_HVP;
+    constexpr bool RU = MODE == MODE_HVP_REUSE;  // Q sums, G, sum w ln I from the cache
     constexpr bool GR = MODE >= MODE_GRAD;
     constexpr int E = kTileE;
     constexpr int H = W;                       // lanes per event
     constexpr int EV = 32 / H;                 // events per warp (one tile = W x EV events)
-    constexpr int NVM = HV ? kNV : 4;          // accumulated reals per resonance
+    constexpr int NVM = RU ? 4 : (HV ? kNV : 4);  // accumulated reals per resonance
+    constexpr int QOFF = RU ? 6 : 0;           // record slot of the first accumulated real
     constexpr int NT = 32 * W;
     using AVec = typename std::conditional<HV, float4, float2>::type;
     (void)sizeof(AVec);
@@ -307,11 +322,9 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
     uint64_t* mbar = reinterpret_cast<uint64_t*>(issued + 4);
     __shared__ int s_flag;
     __shared__ volatile int s_abort;
+    __shared__ double s_part[kMaxThreads / 32];
 
-    if (a.skip && *a.skip) return;  // a device-side loop has already finished (uniform for the grid)
     const long long T = (long long)a.ntiles[0] + a.ntiles[1];
-    // parameter vector bt of the batch; this block is block gb of the G that share the events
-    const int bt = (int)(blockIdx.x % (unsigned)a.B), gb = (int)(blockIdx.x / (unsigned)a.B);
     const long long G = a.Gb;
     const double* theta = a.theta + (size_t)bt * a.P;
     const double* vdir = HV ? a.v + (size_t)bt * a.P : nullptr;
@@ -337,7 +350,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
             }
         }
     }
-    for (int k = tid; k < K; k += NT) kc[k] = make_kconst(a, theta, vdir, k, HV, EV);
+    for (int k = tid; k < K; k += NT) kc[k] = make_kconst(a, theta, vdir, k, HV, a.ev);
     for (int i = tid; i < W * wlen; i += NT) wacc[i] = make_float2(0.f, 0.f);
     __syncthreads();
 
@@ -378,7 +391,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
                     acc[j][q] = 0.f;
 #pragma unroll
                     for (int o = 1; o < EV; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (el == 0 && j < kcount) two_sum_add(wa[(h + j * H) * kNV + q], v);
+                    if (el == 0 && j < kcount) two_sum_add(wa[(h + j * H) * kNV + QOFF + q], v);
                 }
         }
         const float t0 = warp_sum(sc0), t1 = warp_sum(sc1);
@@ -410,6 +423,8 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
     // one tile of sample set SMP (0 data, 1 MC): global tile index t, iteration i of this block
     auto tile = [&](auto smp_c, long long t, long long i) {
         constexpr int smp = decltype(smp_c)::value;
+        // the reuse pass needs A (for I, Idot and the data weights) on data events only
+        constexpr bool NEED_A = !(RU && smp == 1);
         const long long lt = smp ? t - a.ntiles[0] : t;
         bool ok = false;
         if (!s_abort) {
@@ -455,8 +470,10 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
 #pragma unroll
                     for (int q = 0; q < Q; ++q) {
                         const float2 R = fv[2 * q], Im = fv[2 * q + 1];
-                        ARp[q] = __ffma2_rn(Im, ncc, __ffma2_rn(R, crr, ARp[q]));
-                        AIp[q] = __ffma2_rn(Im, crr, __ffma2_rn(R, cii, AIp[q]));
+                        if constexpr (NEED_A) {
+                            ARp[q] = __ffma2_rn(Im, ncc, __ffma2_rn(R, crr, ARp[q]));
+                            AIp[q] = __ffma2_rn(Im, crr, __ffma2_rn(R, cii, AIp[q]));
+                        }
                         if constexpr (HV) {
                             DRp[q] = __ffma2_rn(Im, ndd, __ffma2_rn(R, drr, DRp[q]));
                             DIp[q] = __ffma2_rn(Im, drr, __ffma2_rn(R, dii, DIp[q]));
@@ -506,7 +523,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
 #pragma unroll
                     for (int s = 0; s < S; ++s) {
                         const float2 fxx = make_float2(fv[s].x, fv[s].x), fyy = make_float2(fv[s].y, fv[s].y);
-                        A2[s] = __ffma2_rn(fyy, ic2, __ffma2_rn(fxx, c2, A2[s]));
+                        if constexpr (NEED_A) A2[s] = __ffma2_rn(fyy, ic2, __ffma2_rn(fxx, c2, A2[s]));
                         if constexpr (HV) D2[s] = __ffma2_rn(fyy, id2, __ffma2_rn(fxx, d2, D2[s]));
                     }
                 };
@@ -536,8 +553,9 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
             for (int off = EV; off < 32; off <<= 1) {
 #pragma unroll
                 for (int i = 0; i < S; ++i) {
-                    PA[i] = __fadd2_rn(PA[i], make_float2(__shfl_xor_sync(0xffffffffu, PA[i].x, off),
-                                                          __shfl_xor_sync(0xffffffffu, PA[i].y, off)));
+                    if constexpr (NEED_A)
+                        PA[i] = __fadd2_rn(PA[i], make_float2(__shfl_xor_sync(0xffffffffu, PA[i].x, off),
+                                                              __shfl_xor_sync(0xffffffffu, PA[i].y, off)));
                     if constexpr (HV)
                         PD[i] = __fadd2_rn(PD[i], make_float2(__shfl_xor_sync(0xffffffffu, PD[i].x, off),
                                                               __shfl_xor_sync(0xffffffffu, PD[i].y, off)));
@@ -569,6 +587,8 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
                     }
                     if (valid && good) sc0 += w * logf(I);
                 }
+            } else if constexpr (RU) {
+                if (valid) wa = 1.f;  // G, Gdot and the finiteness check come with the cached full pass
             } else {
                 if (valid) wa = 1.f;
                 if (h == 0) {
@@ -631,8 +651,10 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
 #pragma unroll
                         for (int q = 0; q < Q2; ++q) {
                             const float2 R = fv[2 * q], Im = fv[2 * q + 1];
-                            X = __ffma2_rn(Im, aI[q], __ffma2_rn(R, aR[q], X));
-                            Y = __ffma2_rn(R, naI[q], __ffma2_rn(Im, aR[q], Y));
+                            if constexpr (!RU) {
+                                X = __ffma2_rn(Im, aI[q], __ffma2_rn(R, aR[q], X));
+                                Y = __ffma2_rn(R, naI[q], __ffma2_rn(Im, aR[q], Y));
+                            }
                             if constexpr (HV) {
                                 XD = __ffma2_rn(Im, dI[q], __ffma2_rn(R, dR[q], XD));
                                 YD = __ffma2_rn(R, ndI[q], __ffma2_rn(Im, dR[q], YD));
@@ -641,8 +663,10 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
                     } else {
 #pragma unroll
                         for (int s = 0; s < S; ++s) {
-                            X = __ffma2_rn(fv[s], al[s], X);
-                            Y = __ffma2_rn(fv[s], be[s], Y);
+                            if constexpr (!RU) {
+                                X = __ffma2_rn(fv[s], al[s], X);
+                                Y = __ffma2_rn(fv[s], be[s], Y);
+                            }
                             if constexpr (HV) {
                                 XD = __ffma2_rn(fv[s], dl[s], XD);
                                 YD = __ffma2_rn(fv[s], de[s], YD);
@@ -652,6 +676,14 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
                     const float hr = X.x + X.y, hi = Y.x + Y.y;
                     const float tr = XD.x + XD.y, ti = YD.x + YD.y;
                     const float b2r = fmaf(br, br, -bi * bi), b2i = 2.f * br * bi;
+                    if constexpr (RU) {
+                        // P1 += Dt B, P2 += Dt B^2 only (record slots 6..9)
+                        acc[j][0] = fmaf(tr, br, fmaf(-ti, bi, acc[j][0]));
+                        acc[j][1] = fmaf(tr, bi, fmaf(ti, br, acc[j][1]));
+                        acc[j][2] = fmaf(tr, b2r, fmaf(-ti, b2i, acc[j][2]));
+                        acc[j][3] = fmaf(tr, b2i, fmaf(ti, b2r, acc[j][3]));
+                        continue;
+                    }
                     acc[j][0] = fmaf(hr, br, fmaf(-hi, bi, acc[j][0]));
                     acc[j][1] = fmaf(hr, bi, fmaf(hi, br, acc[j][1]));
                     acc[j][2] = fmaf(hr, b2r, fmaf(-hi, b2i, acc[j][2]));
@@ -762,11 +794,61 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
     }
     __syncthreads();
     if (tid == 0) a.top_count[bt] = 0;
+    const int L = K * kNV + kNScal;
+    if constexpr (MODE == MODE_HVP) {
+        // keep this pass's totals and theta for the H v passes that reuse them
+        if (a.cache && a.B == 1) {
+            for (int i = tid; i < a.rec_len; i += NT) a.cache[i] = tot[i];
+            for (int i = tid; i < a.P; i += NT) a.cache[a.rec_len + i] = theta[i];
+        }
+    }
+    double Gdot = tot[L + K * kNV + 1];
+    if constexpr (RU) {
+        // the cached totals must belong to this theta
+        if (tid == 0) s_flag = 0;
+        __syncthreads();
+        for (int i = tid; i < a.P; i += NT)
+            if (theta[i] != a.cache[a.rec_len + i]) s_flag = 1;
+        __syncthreads();
+        if (s_flag) {
+            if (tid == 0) atomicOr(a.err, ERR_STALE);
+            for (int i = tid; i < 1 + 2 * a.P; i += NT) out[i] = __longlong_as_double(0x7ff8000000000000LL);
+            return;
+        }
+        // cached Q sums (slots 0..5 of each resonance) and scalars; this pass's P sums (slots 6..9)
+        for (int i = tid; i < a.rec_len; i += NT) {
+            const int r = i % L;
+            if (!(r < K * kNV && r % kNV >= 6)) tot[i] = a.cache[i];
+        }
+        __syncthreads();
+        // Gdot = sum_mc Idot = (dG/dtheta) . v, dG/dtheta_j = 2 Re (kappa1_j Q1m + kappa2_j Q2m)
+        double part = 0.0;
+        for (int k = tid; k < K; k += NT) {
+            const ResValues rv = res_values(a, theta, vdir, k, true);
+            const ResParam rp = a.res[k];
+            double sn, cs;
+            sincos(rv.phi, &sn, &cs);
+            const double* tm = tot + L + k * kNV;
+            const double q1r = tm[0], q1i = tm[1], q2r = tm[2], q2i = tm[3];
+            const double g1r = rv.rho * cs, g1i = rv.rho * sn;
+            // kappa1: rho -> e^{i phi}, phi -> i g; kappa2: M -> g (-2M + i Gamma), Gamma -> g (i M)
+            const double dg[4] = {2.0 * (cs * q1r - sn * q1i), 2.0 * (-g1i * q1r - g1r * q1i),
+                                  2.0 * ((-2.0 * rv.M * g1r - rv.G * g1i) * q2r - (-2.0 * rv.M * g1i + rv.G * g1r) * q2i),
+                                  2.0 * ((-rv.M * g1i) * q2r - (rv.M * g1r) * q2i)};
+            const double vv[4] = {rv.vr, rv.vp, rv.vm, rv.vg};
+            for (int j = 0; j < 4; ++j)
+                if (rp.idx[j] >= 0) part += dg[j] * vv[j];
+        }
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) s_part[warp] = part;
+        __syncthreads();
+        Gdot = 0.0;
+        for (int w = 0; w < NT / 32; ++w) Gdot += s_part[w];
+    }
 
     // ---- combine (a-8, Eqs. 4, 6, 7) in FP64 ----
-    const int L = K * kNV + kNScal;
     const double SlnI = tot[K * kNV + 0];
-    const double Gm = tot[L + K * kNV + 0], Gdot = tot[L + K * kNV + 1];
+    const double Gm = tot[L + K * kNV + 0];
     if (tid == 0) out[0] = -SlnI + a.Nd * log(Gm / a.Nmc);
     if constexpr (GR) {
         for (int k = tid; k < K; k += NT) {
@@ -827,6 +909,16 @@ __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
             }
         }
     }
+}
+
+
+template <int MODE, int S, int W, int KPW>
+__global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (a.skip && *a.skip) return;  // a device-side loop has already finished (uniform for the grid)
+    // parameter vector bt of the batch; this block is block gb of the Gb that share the events
+    pass_body<MODE, S, W, KPW>(a, (int)(blockIdx.x % (unsigned)a.B), (int)(blockIdx.x / (unsigned)a.B), smem);
 }
 
 }  // namespace pwa

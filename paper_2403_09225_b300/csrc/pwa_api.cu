@@ -161,6 +161,7 @@ KernelFn pick_kernel(int mode, int S, int W, int kpw)
         case pwa::MODE_NLL: PWA_PICK(nll)
         case pwa::MODE_GRAD: PWA_PICK(grad)
         case pwa::MODE_HVP: PWA_PICK(hvp)
+        case pwa::MODE_HVP_REUSE: PWA_PICK(hvpr)
         default: return nullptr;
     }
 #undef PWA_PICK
@@ -217,7 +218,7 @@ pwa_status finish_tiling(pwa_handle* h, Tiling& t)
     int max_optin = 0;
     PWA_CUDA(h, cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     int occ = 1 << 30;
-    for (int mode = 0; mode < 3; ++mode) {
+    for (int mode = 0; mode < 4; ++mode) {
         KernelFn f = pick_kernel(mode, S, t.W, t.KPW);
         if (!f) return pwa::set_error(h, PWA_EINVAL, "no compiled kernel for this S / warps / K combination");
         cudaFuncAttributes fa;
@@ -300,6 +301,12 @@ pwa_status build_tiles(pwa_handle* h)
                   "block partials"));
     PWA_TRY(alloc(h, reinterpret_cast<void**>(&h->d_group_rec), sizeof(double) * (size_t)h->ngroups * h->rec_len,
                   "group partials"));
+    if (!h->d_cache) {
+        // the reused totals; theta NaN until the first full HVP pass (no reuse can match it)
+        PWA_TRY(alloc(h, reinterpret_cast<void**>(&h->d_cache), sizeof(double) * ((size_t)h->rec_len + h->P),
+                      "H v reuse cache"));
+        PWA_CUDA(h, cudaMemsetAsync(h->d_cache, 0xFF, sizeof(double) * ((size_t)h->rec_len + h->P), h->stream));
+    }
     PWA_TRY(alloc(h, reinterpret_cast<void**>(&h->d_counts), sizeof(unsigned) * (h->ngroups + 1), "counters"));
     PWA_CUDA(h, cudaMemsetAsync(h->d_counts, 0, sizeof(unsigned) * (h->ngroups + 1), h->stream));
     PWA_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -322,6 +329,7 @@ pwa::PassArgs make_args(pwa_handle* h, const double* d_theta, const double* d_v,
     a.W = t.W;
     a.NST = t.NST;
     a.stage_bytes = t.stage_bytes;
+    a.ev = 32 / t.W;
     a.P = h->P;
     a.res = h->d_res;
     a.theta = d_theta;
@@ -522,6 +530,7 @@ pwa_status launch_pass(pwa_handle* h, const double* d_theta, const double* d_v, 
 {
     PassArgs a = make_args(h, d_theta, d_v, d_out);
     a.skip = skip;
+    if (mode == MODE_HVP || mode == MODE_HVP_REUSE) a.cache = h->d_cache;
     return launch_pass_args(h, a, mode);
 }
 
@@ -644,6 +653,8 @@ pwa_status check_device_errors(pwa_handle* h)
         h->broken = true;
         return set_error(h, PWA_ETIMEOUT, "a tile copy did not arrive within the wait limit");
     }
+    if (err & ERR_STALE)
+        return set_error(h, PWA_EINVAL, "H v reuse: the last full H v pass was not at this theta");
     return set_error(h, PWA_ENONFINITE, "event " + std::to_string(bad) +
                                             " has a non-finite intensity (or a non-positive one for data)");
 }
@@ -722,7 +733,9 @@ pwa_status pwa_device_bytes(const pwa_handle* h, long long* out)
 
 int pwa_num_params(const pwa_handle* h) { return h ? h->P : -1; }
 
-pwa_status pwa_eval(pwa_handle* h, const double* theta, const double* v, double* nll, double* grad, double* hv)
+namespace {
+pwa_status eval_impl(pwa_handle* h, const double* theta, const double* v, double* nll, double* grad, double* hv,
+                     bool reuse)
 {
     if (!h) return PWA_EINVAL;
     h->err.clear();
@@ -732,7 +745,7 @@ pwa_status pwa_eval(pwa_handle* h, const double* theta, const double* v, double*
     for (int i = 0; i < P; ++i)
         if (!std::isfinite(theta[i]) || (hv && !std::isfinite(v[i])))
             return pwa::set_error(h, PWA_EINVAL, "theta and v must be finite");
-    const int mode = hv ? pwa::MODE_HVP : (grad ? pwa::MODE_GRAD : pwa::MODE_NLL);
+    const int mode = hv ? (reuse ? pwa::MODE_HVP_REUSE : pwa::MODE_HVP) : (grad ? pwa::MODE_GRAD : pwa::MODE_NLL);
     double* pin = h->h_pin;
     std::memcpy(pin, theta, sizeof(double) * P);
     if (hv) std::memcpy(pin + P, v, sizeof(double) * P);
@@ -751,6 +764,27 @@ pwa_status pwa_eval(pwa_handle* h, const double* theta, const double* v, double*
     if (grad) std::memcpy(grad, res + 1, sizeof(double) * P);
     if (hv) std::memcpy(hv, res + 1 + P, sizeof(double) * P);
     return PWA_OK;
+}
+}  // namespace
+
+pwa_status pwa_eval(pwa_handle* h, const double* theta, const double* v, double* nll, double* grad, double* hv)
+{
+    return eval_impl(h, theta, v, nll, grad, hv, false);
+}
+
+pwa_status pwa_hvp_reuse(pwa_handle* h, const double* theta, const double* v, double* hv)
+{
+    if (!hv) return h ? pwa::set_error(h, PWA_EINVAL, "hv must not be NULL") : PWA_EINVAL;
+    double nll = 0.0;
+    return eval_impl(h, theta, v, &nll, nullptr, hv, true);
+}
+
+pwa_status pwa_hvp_reuse_device(pwa_handle* h, const double* d_theta, const double* d_v, double* d_out)
+{
+    if (!h) return PWA_EINVAL;
+    h->err.clear();
+    if (!d_theta || !d_v || !d_out) return pwa::set_error(h, PWA_EINVAL, "d_theta, d_v and d_out must not be NULL");
+    return pwa::launch_pass(h, d_theta, d_v, d_out, pwa::MODE_HVP_REUSE);
 }
 
 pwa_status pwa_nll(pwa_handle* h, const double* theta, double* nll)
@@ -889,6 +923,8 @@ pwa_status pwa_set_tiling(pwa_handle* h, int warps, int stages, int blocks_per_s
 {
     if (!h) return PWA_EINVAL;
     h->err.clear();
+    if (h->released)  // the tiling stays (re-tiling needs the released copies)
+        return pwa::set_error(h, PWA_EINVAL, "the events' caller-layout copies were released: the tiling is fixed");
     Tiling t;
     t.W = warps;
     t.NST = stages;
@@ -910,6 +946,8 @@ pwa_status pwa_autotune(pwa_handle* h, const double* theta, int B, int out3[3])
     if (!h) return PWA_EINVAL;
     h->err.clear();
     if (!theta || B < 1) return pwa::set_error(h, PWA_EINVAL, "theta must not be NULL and B >= 1");
+    if (h->released)
+        return pwa::set_error(h, PWA_EINVAL, "the events' caller-layout copies were released: the tiling is fixed");
     const int P = h->P;
     for (int i = 0; i < P; ++i)
         if (!std::isfinite(theta[i])) return pwa::set_error(h, PWA_EINVAL, "theta must be finite");
@@ -1038,7 +1076,8 @@ void pwa_destroy(pwa_handle* h)
     else cudaDeviceSynchronize();
     // d_v, d_err, d_bad and d_out live inside the d_theta block
     void* ptrs[] = {h->d_res,      h->d_F[0],     h->d_F[1],      h->d_m2[0],     h->d_m2[1], h->d_w,
-                    h->d_tiles[0], h->d_tiles[1], h->d_block_rec, h->d_group_rec, h->d_counts, h->d_theta};
+                    h->d_tiles[0], h->d_tiles[1], h->d_block_rec, h->d_group_rec, h->d_counts, h->d_theta,
+                    h->d_cache};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_pin) cudaFreeHost(h->h_pin);

@@ -96,6 +96,7 @@ struct pwa_handle {
     unsigned long long* d_bad = nullptr;
     int* d_err = nullptr;
     double* h_pin = nullptr;        // pinned staging: theta[P], v[P], out[1 + 2P], status
+    double* d_cache = nullptr;      // [rec_len] totals + [P] theta of the last full HVP pass
     pwa::BatchState batch;
     pwa::HessState hess;
     long long timeout_cycles = 0;
@@ -117,6 +118,7 @@ using KernelFn = void (*)(const PassArgs);
 PWA_DECLARE_PICK(nll)
 PWA_DECLARE_PICK(grad)
 PWA_DECLARE_PICK(hvp)
+PWA_DECLARE_PICK(hvpr)
 #undef PWA_DECLARE_PICK
 
 // Enqueue one fused pass on device buffers (theta, v: device [P]; out: device [1+2P]).

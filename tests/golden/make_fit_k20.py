@@ -8,9 +8,15 @@ numpy's default_rng(8).  The fit is the oracle's textbook Newton-CG
 (Nocedal & Wright Alg. 7.1 with a strong-Wolfe line search, xtol 1e-10);
 its inner products H v come from the oracle's full Hessian (Eq. 7) at each
 outer point, summed over event shards in worker processes (Eqs. 4-5).
-Only the oracle runs here.  Stored: theta0, the minimum, its NLL, the
-parameter errors sqrt(diag(H^-1)) there, the status, and a SHA-256 of the
-sample's bytes (the test checks that it regenerates the same events).
+That path takes some 180 Newton iterations across a multimodal surface, so
+where it ends depends on rounding (an FP32 evaluation of the same path can
+end in another local minimum).  The parity start is therefore a second one,
+theta1 = minimum + 0.2 sigma N(0, 1) (default_rng(9)), inside the minimum's
+basin; the oracle fit from theta1 gives the stored minimum.
+Only the oracle runs here.  Stored: theta0, theta1, the minimum from theta1,
+its NLL, the parameter errors sqrt(diag(H^-1)) there, the statuses, and a
+SHA-256 of the sample's bytes (the test checks that it regenerates the same
+events).
 
 Usage: python tests/golden/make_fit_k20.py   (about 5 minutes on 8 cores)
 """
@@ -41,6 +47,11 @@ def start(wl, P):
     return wl.theta_true * (1 + 0.01 * rng.standard_normal(P))
 
 
+def basin_start(theta_min, sigma):
+    rng = np.random.default_rng(9)
+    return theta_min + 0.2 * sigma * rng.standard_normal(theta_min.size)
+
+
 def main():
     import oracle
     from oracle import newton_cg as ncg
@@ -59,11 +70,16 @@ def main():
             return cache[key]
 
         fg = lambda x: oracle.sharded_nll_grad_hvp(model, x, None, wl.data, wl.mc, pool=pool, shard=10000)[:2]
-        ref = ncg.newton_cg(fg, lambda x, v: hess(x) @ v, th0, xtol=1e-10, maxiter=400)
+        hp = lambda x, v: hess(x) @ v
+        ref0 = ncg.newton_cg(fg, hp, th0, xtol=1e-10, maxiter=400)
+        th1 = basin_start(ref0.x, oracle.parameter_errors(hess(ref0.x)))
+        ref = ncg.newton_cg(fg, hp, th1, xtol=1e-10, maxiter=400)
         sig = oracle.parameter_errors(hess(ref.x))
-        np.savez(os.path.join(HERE, "fit_k20.npz"), theta0=th0, theta_min=ref.x, nll=ref.fun, sigma=sig,
-                 status=ref.status_name, iters=ref.iters, sample_sha256=sample_hash(wl), n_data=N_DATA, n_mc=N_MC)
-        print("status", ref.status_name, "iters", ref.iters, "nll", ref.fun)
+        np.savez(os.path.join(HERE, "fit_k20.npz"), theta0=th0, theta1=th1, theta_min=ref.x, nll=ref.fun,
+                 sigma=sig, status0=ref0.status_name, iters0=ref0.iters, nll0=ref0.fun, status=ref.status_name,
+                 iters=ref.iters, sample_sha256=sample_hash(wl), n_data=N_DATA, n_mc=N_MC)
+        print("from theta0:", ref0.status_name, ref0.iters, ref0.fun)
+        print("from theta1:", ref.status_name, ref.iters, ref.fun)
     finally:
         pool.shutdown()
 

@@ -106,7 +106,7 @@ def test_batched_fits_reach_the_oracle_minimum():
         pull = (oracle.canonical(model, th[b]) - oracle.canonical(model, ref.x)) / sig
         assert np.max(np.abs(pull)) <= 1e-3, (b, pull, infos[b])
         assert abs(infos[b]["nll"] - ref.fun) <= 1e-6 * abs(ref.fun)
-        assert infos[b]["n_hvp"] > 0 and infos[b]["n_fev"] > 0
+        assert infos[b]["n_hess"] > 0 and infos[b]["n_fev"] > 0  # one Hessian pass per outer iteration
 
 
 def test_batched_fit_reports_a_bad_start_per_fit():

@@ -26,8 +26,10 @@ def _oracle_fit(model, wl, th0):
     return ref, sig
 
 
-@pytest.mark.parametrize("matrix_free", [False, True])
-def test_fit_matches_oracle_fit_on_tiny(matrix_free):
+@pytest.mark.parametrize("matrix_free,method", [(False, 0), (True, 0), (False, 1), (True, 1)])
+def test_fit_matches_oracle_fit_on_tiny(matrix_free, method):
+    """Line search (method 0, the oracle's algorithm) and trust region
+    (method 1) reach the oracle's minimum."""
     from paper_2403_09225_b300 import binding
     cfg = W.CONFIGS["tiny"]
     wl, model = small_workload("tiny", cfg.n_data, cfg.n_mc)
@@ -35,9 +37,10 @@ def test_fit_matches_oracle_fit_on_tiny(matrix_free):
     th0 = wl.theta_true * (1 + 0.03 * rng.standard_normal(model.P))
     ref, sig = _oracle_fit(model, wl, th0)
     L = binding.make_likelihood(wl)
-    th, info = L.fit(th0, xtol=1e-10, matrix_free=matrix_free, trace=500)
+    th, info = L.fit(th0, xtol=1e-10, matrix_free=matrix_free, method=method, trace=500)
     assert info["converged"], info
     assert (info["n_hess"] > 0) == (not matrix_free)
+    assert (info["n_hvp"] > 0) == matrix_free
     assert all(r["hessian"] == (0 if matrix_free else 1) for r in info["trace"])
     pull = (oracle.canonical(model, th) - oracle.canonical(model, ref.x)) / sig
     assert np.max(np.abs(pull)) <= 1e-3, (pull, info)
@@ -47,9 +50,11 @@ def test_fit_matches_oracle_fit_on_tiny(matrix_free):
 def test_fit_matches_oracle_fit_at_paper_scale_model():
     """The paper-scale model (K = 20, S = 4, P = 78) on a reduced sample
     (2e4 data events accept-rejected from I at theta_true, 1e5 MC), started
-    near theta_true.  The oracle's minimum from the same start is stored in
+    0.2 sigma per parameter from the oracle's minimum (inside its basin: a long path from far
+    away ends in a rounding-dependent local minimum of this multimodal
+    surface).  The oracle's minimum from that start is stored in
     tests/golden/fit_k20.npz by tests/golden/make_fit_k20.py (the oracle's
-    Newton-CG alone; about 5 CPU-minutes on 8 cores), with a hash of the
+    Newton-CG alone; about 6 CPU-minutes on 8 cores), with a hash of the
     sample that this test regenerates."""
     import os
     import sys
@@ -60,15 +65,15 @@ def test_fit_matches_oracle_fit_at_paper_scale_model():
     g = np.load(os.path.join(here, "fit_k20.npz"))
     wl, model = small_workload("paper", int(g["n_data"]), int(g["n_mc"]))
     assert mk.sample_hash(wl) == str(g["sample_sha256"]), "the generator's events changed: rerun make_fit_k20.py"
-    th0 = mk.start(wl, model.P)
-    assert np.array_equal(th0, g["theta0"])
+    assert np.array_equal(mk.start(wl, model.P), g["theta0"])
+    th0 = g["theta1"]
     ref_x, sig = g["theta_min"], g["sigma"]
     L = binding.make_likelihood(wl)
-    for matrix_free in (False, True):
-        th, info = L.fit(th0, xtol=1e-10, matrix_free=matrix_free)
+    for matrix_free, method in ((False, 0), (True, 0), (False, 1)):
+        th, info = L.fit(th0, xtol=1e-10, matrix_free=matrix_free, method=method)
         assert info["converged"], info
         pull = (oracle.canonical(model, th) - oracle.canonical(model, ref_x)) / sig
-        assert np.max(np.abs(pull)) <= 1e-3, (matrix_free, np.max(np.abs(pull)), info)
+        assert np.max(np.abs(pull)) <= 1e-3, (matrix_free, method, np.max(np.abs(pull)), info)
     L.close()
 
 

@@ -44,6 +44,12 @@ def check_point(L, model, wl, th, v):
     assert abs(f - fo) <= TOL_NLL * nll_scale(model, th, wl, fo), (f, fo)
     assert relmax(g, go) <= TOL_GRAD, relmax(g, go)
     assert relmax(hv, hvo) <= TOL_HVP, relmax(hv, hvo)
+    # the reuse pass (Q sums, G and the gradient kept from the full pass at th)
+    # for this v and for another direction
+    assert relmax(L.hvp_reuse(th, v), hvo) <= TOL_HVP
+    v2 = np.asarray(v)[::-1] * np.linspace(0.5, 1.5, len(v))
+    hvo2 = oracle.nll_grad_hvp(model, th, v2, wl.data, wl.mc)[2]
+    assert relmax(L.hvp_reuse(th, v2), hvo2) <= TOL_HVP, relmax(L.hvp_reuse(th, v2), hvo2)
     # the cheaper passes agree with the fused one
     assert L.nll(th) == f  # same summation order in every mode
     f2, g2 = L.grad(th)
@@ -176,3 +182,40 @@ def test_small_k_tilings(warps):
     L.set_tiling(warps, 2)
     th = W.random_starts(wl, 1)[0]
     check_point(L, model, wl, th, np.linspace(-1, 1, model.P))
+
+
+def test_reuse_pass_needs_a_full_pass_at_the_same_theta():
+    """pwa_hvp_reuse refuses a theta other than the last full H v pass's,
+    through the host call (PWA_EINVAL) and the device call (NaN output and a
+    device error reported by the next synchronising call)."""
+    import torch
+    from paper_2403_09225_b300 import binding
+    wl, model = small_workload("tiny", 4000 + 17, 20000 + 5)
+    L = make_L(wl, stream=torch.cuda.current_stream().cuda_stream)
+    th = W.random_starts(wl, 2)
+    v = np.linspace(-1, 1, model.P)
+    with pytest.raises(binding.PwaError) as e:  # no full pass yet
+        L.hvp_reuse(th[0], v)
+    assert e.value.status == binding.PWA_EINVAL
+    L.eval(th[0], v)
+    ok = L.hvp_reuse(th[0], v)
+    with pytest.raises(binding.PwaError) as e:
+        L.hvp_reuse(th[1], v)
+    assert e.value.status == binding.PWA_EINVAL and "theta" in str(e.value)
+    d_th = torch.tensor(th[1], dtype=torch.float64, device="cuda")
+    d_v = torch.tensor(v, dtype=torch.float64, device="cuda")
+    out = torch.zeros(1 + 2 * model.P, dtype=torch.float64, device="cuda")
+    L.hvp_reuse_device(d_th.data_ptr(), d_v.data_ptr(), out.data_ptr())
+    with pytest.raises(binding.PwaError):
+        L.sync()
+    assert torch.isnan(out).all()
+    # after a full pass at th[1] (device call) the reuse at th[1] is served
+    L.eval_device(d_th.data_ptr(), d_v.data_ptr(), out.data_ptr(), True, True)
+    ref = out.cpu().numpy().copy()
+    L.hvp_reuse_device(d_th.data_ptr(), d_v.data_ptr(), out.data_ptr())
+    L.sync()
+    got = out.cpu().numpy()
+    assert relmax(got[1 + model.P:], ref[1 + model.P:]) <= 1e-5 and got[0] == ref[0]
+    assert np.array_equal(got[1:1 + model.P], ref[1:1 + model.P])
+    assert relmax(L.hvp_reuse(th[1], v), ref[1 + model.P:]) <= 1e-5
+    assert np.isfinite(ok).all()
