@@ -145,7 +145,9 @@ typedef enum {
     PWA_FIT_TIME_LIMIT = 3,  /* time_limit_s reached (early stopping)              */
     PWA_FIT_LINESEARCH = 4,  /* no step satisfied the Wolfe conditions             */
     PWA_FIT_PRECISION = 5,   /* converged: predicted decrease below the NLL's
-                                resolution, no further step can be resolved        */
+                                resolution, no further step can be resolved, or
+                                |grad| stalled at its rounding floor (no 1 %
+                                improvement in 25 outer iterations)                */
     PWA_FIT_ERROR = 6        /* stopped on an error (e.g. a non-finite NLL at its
                                 start point); only pwa_newton_cg_fit_batch reports
                                 it per fit, pwa_newton_cg_fit returns the error    */
@@ -323,6 +325,25 @@ pwa_status pwa_newton_cg_fit_batch(pwa_handle* h, int B, const double* theta0,
                                    const pwa_fit_opts* opts, double* theta_out,
                                    pwa_fit_result* results);
 
+/* One launch of the batched pass over several handles (no counterpart in the
+ * paper, which fits its samples one after another): handle i evaluates B[i]
+ * parameter vectors d_theta[i] ([B[i]][P_i], device) and writes d_out[i]
+ * ([B[i]][1 + 2 P_i], device) as pwa_eval_batch_device does, with d_v[i]
+ * ([B[i]][P_i]) when want_hv.  The work list of the launch is every (handle,
+ * vector, block) of those batched passes; persistent CTAs walk it, running
+ * one compiled instance per S with K a runtime value, so toys of different
+ * sizes, K and S share one launch.  Every handle needs K <= 32 and a handle
+ * may appear once.  Enqueued on `stream` (a cudaStream_t, NULL = default)
+ * after the handles' earlier work on it; errors found on the device (per
+ * vector and per handle) are reported by pwa_sync(handle) once the stream
+ * has been synchronised.  Grows each handle's batch scratch as
+ * pwa_eval_batch_device does.  want_grad or want_hv must be set.
+ * pwa_newton_cg_fit_multi uses this launch for its rounds when every handle
+ * has K <= 32. */
+pwa_status pwa_eval_multi_device(int n, pwa_handle* const* handles, const int* B, const double* const* d_theta,
+                                 const double* const* d_v, double* const* d_out, int want_grad, int want_hv,
+                                 void* stream);
+
 /* Lockstep fits over several handles (toy fits: different event samples,
  * sizes, K and S), B[i] fits on handles[i].  Every round issues one batched
  * pass per handle, each on a private stream of that handle, so the handles'
@@ -331,7 +352,10 @@ pwa_status pwa_newton_cg_fit_batch(pwa_handle* h, int B, const double* theta0,
  * it per handle).  theta0[i], theta_out[i]: host [B[i]][P_i]; results[i]: host
  * [B[i]] (results may be NULL).  A handle may appear only once.  Returns as
  * pwa_newton_cg_fit_batch; an error on one handle (its pwa_last_error says
- * which) stops all fits. */
+ * which) stops all fits.  With two or more handles, all with K <= 32, every
+ * round is one pwa_eval_multi_device launch over all handles (captured into
+ * a CUDA graph once its shape repeats); otherwise one batched launch per
+ * handle, each on its own stream. */
 pwa_status pwa_newton_cg_fit_multi(int n_handles, pwa_handle* const* handles, const int* B,
                                    const double* const* theta0, const pwa_fit_opts* opts,
                                    double* const* theta_out, pwa_fit_result* const* results);

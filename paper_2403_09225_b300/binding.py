@@ -85,7 +85,7 @@ class PwaError(RuntimeError):
 
 
 #: every symbol include/pwa.h declares
-EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "pwa_grad", "pwa_hvp", "pwa_hessian", "pwa_hvp_reuse", "pwa_hvp_reuse_device", "pwa_release_event_copies",
+EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "pwa_grad", "pwa_hvp", "pwa_hessian", "pwa_hvp_reuse", "pwa_hvp_reuse_device", "pwa_eval_multi_device", "pwa_release_event_copies",
            "pwa_device_bytes",
            "pwa_eval", "pwa_eval_device", "pwa_eval_device_noalloc", "pwa_eval_batch", "pwa_eval_batch_device",
            "pwa_sync", "pwa_event_intensity", "pwa_newton_cg_fit", "pwa_newton_cg_fit_batch",
@@ -119,6 +119,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pwa_eval": (st, [H, dp, dp, dp, dp, dp]),
         "pwa_hessian": (st, [H, dp, dp, dp, dp]),
         "pwa_hvp_reuse": (st, [H, dp, dp, dp]),
+        "pwa_eval_multi_device": (st, [i, ctypes.POINTER(ctypes.c_void_p), ip, ctypes.POINTER(ctypes.c_void_p),
+                                       ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), i, i, vp]),
         "pwa_hvp_reuse_device": (st, [H, vp, vp, vp]),
         "pwa_release_event_copies": (st, [H]),
         "pwa_device_bytes": (st, [H, ctypes.POINTER(ctypes.c_longlong)]),
@@ -543,6 +545,38 @@ def fit_multi(likelihoods, thetas0, xtol: float = 1e-8, gtol: float = 0.0, maxit
     infos = [[{"nll": r.nll, "grad_max": r.grad_max, "iters": r.iters, "n_hvp": r.n_hvp, "n_fev": r.n_fev,
                "n_hess": r.n_hess, "status": FIT_STATUS_NAMES[r.status], "elapsed_s": r.elapsed_s} for r in rr] for rr in res]
     return outs, infos, st == PWA_OK
+
+
+def eval_multi(likelihoods, thetas, vs=None):
+    """One launch over several likelihoods (pwa_eval_multi_device): thetas[i]
+    [B_i, P_i] (and vs[i] for H v) -> per likelihood (nll [B_i], grad
+    [B_i, P_i], hv [B_i, P_i] or None).  Device buffers are torch tensors;
+    the launch runs on torch's current stream."""
+    import torch
+    n = len(likelihoods)
+    want_hv = vs is not None
+    th = [torch.as_tensor(np.asarray(t, dtype=np.float64).reshape(-1, L.P), device="cuda")
+          for L, t in zip(likelihoods, thetas)]
+    vv = [torch.as_tensor(np.asarray(v, dtype=np.float64).reshape(-1, L.P), device="cuda")
+          for L, v in zip(likelihoods, vs)] if want_hv else None
+    out = [torch.empty((t.shape[0], 1 + 2 * L.P), dtype=torch.float64, device="cuda") for L, t in zip(likelihoods, th)]
+    hs = (ctypes.c_void_p * n)(*[L._h.value for L in likelihoods])
+    Bs = (ctypes.c_int * n)(*[t.shape[0] for t in th])
+    ptr = lambda ts: (ctypes.c_void_p * n)(*[t.data_ptr() for t in ts])
+    stream = torch.cuda.current_stream()
+    st = lib().pwa_eval_multi_device(n, hs, Bs, ptr(th), ptr(vv) if want_hv else None, ptr(out), 1, int(want_hv),
+                                     stream.cuda_stream)
+    if st != PWA_OK:
+        msgs = "; ".join(filter(None, (lib().pwa_last_error(L._h).decode() for L in likelihoods)))
+        raise PwaError(st, msgs)
+    stream.synchronize()
+    for L in likelihoods:
+        L.sync()
+    res = []
+    for L, o in zip(likelihoods, out):
+        o = o.cpu().numpy()
+        res.append((o[:, 0].copy(), o[:, 1:1 + L.P].copy(), o[:, 1 + L.P:].copy() if want_hv else None))
+    return res
 
 
 SHAPE_CONSTANT, SHAPE_MASS_DEPENDENT, SHAPE_FLATTE = 0, 1, 2

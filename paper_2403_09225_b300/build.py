@@ -19,7 +19,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libpwa.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
-SOURCES = ["pwa_api.cu", "fit.cu", "hessian.cu", "noalloc.cu", "coupling.cu", "mlp.cu", "generate.cu", "variant.cu"]
+SOURCES = ["pwa_api.cu", "fit.cu", "hessian.cu", "multi.cu", "noalloc.cu", "coupling.cu", "mlp.cu", "generate.cu", "variant.cu"]
 HEADERS = ["pass_kernel.cuh", "pwa_internal.h", "tcgen05.cuh"]
 
 #: compiled shapes of the fused pass: S (projections) x W (warps per block) x

@@ -15,7 +15,9 @@
 //  * the sufficient-decrease test allows an increase up to eps_f = 1e-7 |f|
 //    (the "approximate Wolfe" idea of Hager & Zhang, 2005);
 //  * a failed line search whose predicted decrease |g.p| is below
-//    1e-7 (1 + |f|) ends the fit as converged at the precision limit.
+//    1e-7 (1 + |f|) ends the fit as converged at the precision limit;
+//  * so does a gradient norm that has not improved by 1 % for 25 outer
+//    iterations (the noise floor of the FP32-summed gradient).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -305,6 +307,9 @@ struct FitState {
     double* rH = nullptr;        // HESS: the Hessian [P][P] at rx
     double cg_eps = 0.0;         // CG: solve H p = -g at (x, g) to |r| < cg_eps into p
     pwa_status req_status = PWA_OK;
+    // noise floor: the best |g| so far and the outer iteration that last improved it by 1 %
+    double g_best = INFINITY;
+    int k_best = 0;
     // per-iteration records (opts.trace); cur_it is the one being filled
     std::vector<pwa_fit_iter> trace;
     pwa_fit_iter cur_it{};
@@ -351,6 +356,23 @@ struct Suspend {
 void push_iter(FitState& s)
 {
     if ((int)s.trace.size() < s.o.trace_cap) s.trace.push_back(s.cur_it);
+}
+
+// Stagnation at the FP32 noise floor: |g| has not improved by 1 % over its
+// best for kStall outer iterations.  Near the minimum the gradient of the
+// FP32-summed NLL is dominated by rounding and the steps wander at that
+// level without ever meeting xtol; the fit has then converged as far as the
+// evaluation resolves.
+constexpr int kStall = 25;
+bool stalled(FitState& s, int k)
+{
+    const double gn = std::sqrt(dot(s.g, s.g));
+    if (gn < 0.99 * s.g_best) {
+        s.g_best = gn;
+        s.k_best = k;
+        return false;
+    }
+    return k - s.k_best > kStall;
 }
 
 FitTask newton_cg(FitState& s)
@@ -578,6 +600,10 @@ FitTask newton_cg(FitState& s)
             s.status = PWA_FIT_XTOL;
             break;
         }
+        if (stalled(s, k)) {
+            s.status = PWA_FIT_PRECISION;
+            break;
+        }
         if (s.o.time_limit_s > 0 && s.since_start() > s.o.time_limit_s) {
             s.status = PWA_FIT_TIME_LIMIT;
             break;
@@ -764,6 +790,10 @@ FitTask newton_cg_tr(FitState& s)
                 s.status = PWA_FIT_XTOL;
                 break;
             }
+            if (stalled(s, k)) {
+                s.status = PWA_FIT_PRECISION;
+                break;
+            }
         } else {
             push_iter(s);
             if (delta < 1e-12 * (1.0 + std::sqrt(dot(s.x, s.x))) ||
@@ -918,26 +948,41 @@ struct HandleRounds final : RoundEvaluator {
         *v = h->batch.h_io + (size_t)nb * h->P;
         return PWA_OK;
     }
-    // the round's operations, enqueued on the handle's stream
-    pwa_status enqueue(int nb, bool any_hv)
+    // upload of the rows' theta (and v) from the pinned staging
+    pwa_status copy_in(int nb, bool any_hv, cudaStream_t s)
+    {
+        pwa::BatchState& bs = h->batch;
+        const size_t BP = (size_t)nb * h->P;
+        cudaError_t e = cudaMemcpyAsync(bs.d_io, bs.h_io, sizeof(double) * (any_hv ? 2 * BP : BP),
+                                        cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return pwa::cuda_error(h, e, "batch upload");
+        return PWA_OK;
+    }
+    // download of the results and the error words into the pinned staging
+    pwa_status copy_out(int nb, cudaStream_t s)
     {
         pwa::BatchState& bs = h->batch;
         const size_t BP = (size_t)nb * h->P;
         const size_t ow = (size_t)nb * (1 + 2 * (size_t)h->P);
         double* pin = bs.h_io;
-        double* d_th = bs.d_io;
-        cudaError_t e = cudaMemcpyAsync(d_th, pin, sizeof(double) * (any_hv ? 2 * BP : BP), cudaMemcpyHostToDevice,
-                                        h->stream);
-        if (e != cudaSuccess) return pwa::cuda_error(h, e, "batch upload");
-        pwa_status st = pwa::launch_batch(h, nb, d_th, any_hv ? bs.d_io + BP : nullptr, bs.d_io + 2 * BP,
-                                          any_hv ? pwa::MODE_HVP : pwa::MODE_GRAD, true);
-        if (st != PWA_OK) return st;
         int* errw = reinterpret_cast<int*>(pin + 2 * BP + ow);  // [nb] per-vector words, then the shared one
-        e = cudaMemcpyAsync(pin + 2 * BP, bs.d_io + 2 * BP, sizeof(double) * ow, cudaMemcpyDeviceToHost, h->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(errw, bs.d_err_vec, sizeof(int) * nb, cudaMemcpyDeviceToHost, h->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(errw + nb, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+        cudaError_t e = cudaMemcpyAsync(pin + 2 * BP, bs.d_io + 2 * BP, sizeof(double) * ow, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(errw, bs.d_err_vec, sizeof(int) * nb, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(errw + nb, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return pwa::cuda_error(h, e, "batch download");
         return PWA_OK;
+    }
+    // the round's operations, enqueued on the handle's stream
+    pwa_status enqueue(int nb, bool any_hv)
+    {
+        pwa::BatchState& bs = h->batch;
+        const size_t BP = (size_t)nb * h->P;
+        pwa_status st = copy_in(nb, any_hv, h->stream);
+        if (st != PWA_OK) return st;
+        st = pwa::launch_batch(h, nb, bs.d_io, any_hv ? bs.d_io + BP : nullptr, bs.d_io + 2 * BP,
+                               any_hv ? pwa::MODE_HVP : pwa::MODE_GRAD, true);
+        if (st != PWA_OK) return st;
+        return copy_out(nb, h->stream);
     }
     bool same_state(const Captured& c) const
     {
@@ -1147,10 +1192,12 @@ pwa_status open_group(FitGroup& g, std::unique_ptr<RoundEvaluator> ev, int B, co
 
 // Enqueue the group's round: its unfinished fits' requests as one batched
 // evaluation (H v for all when any asks for it, with v = 0 for the f, g requests).
-pwa_status issue_round(FitGroup& g)
+// Serve the group's Hessian requests (one Hessian pass each, synchronous;
+// each such fit then runs its CG on the host and posts its next request),
+// then collect the fits that wait for f, g or H v.  Returns whether any of
+// those wants H v.
+bool collect_round(FitGroup& g)
 {
-    // Hessian requests first, one Hessian pass each (synchronous); each such
-    // fit then runs its CG on the host and posts its next request
     for (int b = 0; b < g.B; ++b) {
         FitState& s = g.fits[b];
         while (!g.tasks[b].h.done() && s.req == Req::HESS) {
@@ -1163,10 +1210,16 @@ pwa_status issue_round(FitGroup& g)
     g.live.clear();
     for (int b = 0; b < g.B; ++b)
         if (!g.tasks[b].h.done()) g.live.push_back(b);
-    if (g.live.empty()) return PWA_OK;
-    const int P = g.P, nb = (int)g.live.size();
     bool any_hv = false;
     for (int b : g.live) any_hv |= g.fits[b].req == Req::HV;
+    return any_hv;
+}
+
+// The live fits' rows (theta, and v when any_hv; zero v for f, g requests)
+// into the evaluator's staging.
+pwa_status stage_rows(FitGroup& g, bool any_hv)
+{
+    const int P = g.P, nb = (int)g.live.size();
     double *th = nullptr, *v = nullptr;
     pwa_status st = g.ev->reserve(nb, &th, &v);
     if (st != PWA_OK) return st;
@@ -1175,7 +1228,16 @@ pwa_status issue_round(FitGroup& g)
         std::memcpy(th + (size_t)i * P, s.rx, sizeof(double) * P);
         if (any_hv) std::memcpy(v + (size_t)i * P, s.req == Req::HV ? s.rv : g.zero.data(), sizeof(double) * P);
     }
-    return g.ev->issue(nb, any_hv);
+    return PWA_OK;
+}
+
+pwa_status issue_round(FitGroup& g)
+{
+    const bool any_hv = collect_round(g);
+    if (g.live.empty()) return PWA_OK;
+    pwa_status st = stage_rows(g, any_hv);
+    if (st != PWA_OK) return st;
+    return g.ev->issue((int)g.live.size(), any_hv);
 }
 
 // Wait for the group's round and resume its fits with their results.
@@ -1220,6 +1282,161 @@ pwa_status run_lockstep(std::vector<std::unique_ptr<FitGroup>>& groups)
         }
     }
 }
+
+// Lockstep rounds of several likelihood handles with one launch per round
+// (pwa::launch_multi): the rows of every handle with live fits are uploaded,
+// one pass over all those handles runs (H v mode when any fit anywhere asks
+// for H v), and the results come back, all on one stream.  The third time a
+// round of the same shape (which handles, how many rows each, the mode) comes
+// up it is captured into a CUDA graph and replayed from then on; a graph is
+// dropped when a buffer it points at has changed.
+struct MultiRounds {
+    struct Captured {
+        std::vector<int> key;  // any_hv, then (group, rows) pairs
+        cudaGraphExec_t exec = nullptr;
+        int uses = 0;
+        std::vector<const void*> ptrs;  // the buffers its nodes point at
+        // the launch arguments' staging of this graph alone: its copy node
+        // replays from it, so no other round may write it
+        pwa::MultiScratch ms;
+    };
+    std::vector<std::unique_ptr<FitGroup>>& groups;
+    cudaStream_t stream = nullptr;
+    pwa::MultiScratch eager;  // staging of the rounds that run without a graph
+    std::vector<std::unique_ptr<Captured>> cache;
+    explicit MultiRounds(std::vector<std::unique_ptr<FitGroup>>& g) : groups(g) {}
+    ~MultiRounds()
+    {
+        if (stream) cudaStreamSynchronize(stream);
+        for (auto& c : cache)
+            if (c->exec) cudaGraphExecDestroy(c->exec);
+        cache.clear();
+        if (stream) cudaStreamDestroy(stream);
+        cudaGetLastError();
+    }
+    HandleRounds* hr(int i) { return static_cast<HandleRounds*>(groups[i]->ev.get()); }
+    std::vector<const void*> buffers(const std::vector<int>& gs, const pwa::MultiScratch& ms)
+    {
+        std::vector<const void*> p{ms.d_args, ms.d_first, ms.h_stage};
+        for (int i : gs) {
+            const pwa::BatchState& bs = hr(i)->h->batch;
+            p.insert(p.end(), {bs.d_io, bs.h_io, bs.d_block_rec, bs.d_group_rec, bs.d_counts});
+        }
+        return p;
+    }
+    pwa_status enqueue(const std::vector<int>& gs, bool any_hv, pwa::MultiScratch& ms)
+    {
+        const int n = (int)gs.size();
+        std::vector<pwa_handle*> hs(n);
+        std::vector<int> B(n);
+        std::vector<const double*> th(n), v(n);
+        std::vector<double*> out(n);
+        for (int k = 0; k < n; ++k) {
+            HandleRounds* r = hr(gs[k]);
+            const int nb = (int)groups[gs[k]]->live.size();
+            pwa_status st = r->copy_in(nb, any_hv, stream);
+            if (st != PWA_OK) return st;
+            const pwa::BatchState& bs = r->h->batch;
+            const size_t BP = (size_t)nb * r->h->P;
+            hs[k] = r->h;
+            B[k] = nb;
+            th[k] = bs.d_io;
+            v[k] = bs.d_io + BP;
+            out[k] = bs.d_io + 2 * BP;
+        }
+        pwa_status st = pwa::launch_multi(n, hs.data(), B.data(), th.data(), v.data(), out.data(),
+                                          any_hv ? pwa::MODE_HVP : pwa::MODE_GRAD, true, stream, ms);
+        if (st != PWA_OK) return st;
+        for (int k = 0; k < n; ++k) {
+            st = hr(gs[k])->copy_out(B[k], stream);
+            if (st != PWA_OK) return st;
+        }
+        return PWA_OK;
+    }
+    pwa_status issue(const std::vector<int>& gs, bool any_hv)
+    {
+        std::vector<int> key{any_hv ? 1 : 0};
+        for (int i : gs) key.insert(key.end(), {i, (int)groups[i]->live.size()});
+        Captured* c = nullptr;
+        for (auto& x : cache)
+            if (x->key == key) c = x.get();
+        if (!c) {
+            cache.push_back(std::make_unique<Captured>());
+            c = cache.back().get();
+            c->key = key;
+        }
+        if (c->exec && c->ptrs != buffers(gs, c->ms)) {
+            cudaGraphExecDestroy(c->exec);
+            c->exec = nullptr;
+            c->uses = 0;
+        }
+        if (c->exec) {
+            cudaError_t e = cudaGraphLaunch(c->exec, stream);
+            if (e != cudaSuccess) return pwa::cuda_error(hr(gs[0])->h, e, "multi round graph launch");
+            return PWA_OK;
+        }
+        if (++c->uses < 3) return enqueue(gs, any_hv, eager);
+        // the graph's own staging, allocated outside the capture (enqueue then reuses it)
+        pwa_status st = pwa::launch_multi_reserve(hr(gs[0])->h, (int)gs.size(), c->ms);
+        if (st != PWA_OK) return st;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return enqueue(gs, any_hv, eager);
+        }
+        st = enqueue(gs, any_hv, c->ms);
+        e = cudaStreamEndCapture(stream, &g);
+        if (st != PWA_OK || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            for (int i : gs) hr(i)->h->err.clear();
+            c->uses = -1000000;  // this shape stays eager
+            return enqueue(gs, any_hv, eager);
+        }
+        e = cudaGraphInstantiate(&c->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->exec = nullptr;
+            c->uses = -1000000;
+            return enqueue(gs, any_hv, eager);
+        }
+        c->ptrs = buffers(gs, c->ms);
+        e = cudaGraphLaunch(c->exec, stream);
+        if (e != cudaSuccess) return pwa::cuda_error(hr(gs[0])->h, e, "multi round graph launch");
+        return PWA_OK;
+    }
+    pwa_status run()
+    {
+        if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            stream = nullptr;
+            return pwa::set_error(hr(0)->h, PWA_ECUDA, "cannot create the multi-round stream");
+        }
+        while (true) {
+            bool any_hv = false;
+            std::vector<int> gs;
+            for (int i = 0; i < (int)groups.size(); ++i) {
+                any_hv |= collect_round(*groups[i]);
+                if (!groups[i]->live.empty()) gs.push_back(i);
+            }
+            if (gs.empty()) return PWA_OK;
+            for (int i : gs) {
+                pwa_status st = stage_rows(*groups[i], any_hv);
+                if (st != PWA_OK) return st;
+            }
+            pwa_status st = issue(gs, any_hv);
+            if (st != PWA_OK) return st;
+            cudaError_t e = cudaStreamSynchronize(stream);
+            if (e != cudaSuccess) return pwa::cuda_error(hr(gs[0])->h, e, "multi round");
+            for (int i : gs) {
+                st = finish_round(*groups[i]);
+                if (st != PWA_OK) return st;
+            }
+        }
+    }
+};
 
 // Results of a group; all_ok stays true when every fit converged or hit its time limit.
 pwa_status close_group(FitGroup& g, double* theta_out, pwa_fit_result* results, bool& all_ok, int trace_row0 = 0)
@@ -1331,12 +1548,20 @@ extern "C" pwa_status pwa_newton_cg_fit_multi(int n_handles, pwa_handle* const* 
                 return pwa::set_error(handles[i], PWA_EINVAL, "a handle appears twice; put its fits in one group");
     }
     std::vector<std::unique_ptr<FitGroup>> groups;
+    bool multi = n_handles >= 2;  // one launch per round over all handles (each K <= 32)
     for (int i = 0; i < n_handles; ++i) {
+        multi &= handles[i]->K <= pwa::kMaxKMulti;
         groups.push_back(std::make_unique<FitGroup>());
         pwa_status st = open_group(*groups.back(), std::make_unique<HandleRounds>(handles[i]), B[i], theta0[i], opts);
         if (st != PWA_OK) return st;
     }
-    pwa_status st = run_lockstep(groups);
+    pwa_status st;
+    if (multi) {
+        MultiRounds mr(groups);
+        st = mr.run();
+    } else {
+        st = run_lockstep(groups);
+    }
     if (st != PWA_OK) return st;
     bool all_ok = true;
     int row0 = 0;  // trace rows run over the fits of all handles in order

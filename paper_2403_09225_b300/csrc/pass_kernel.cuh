@@ -116,6 +116,7 @@ struct PassArgs {
     // resonance rotation, tile_shift); a kernel instance with H lanes per
     // event reads them when 16 / ev divides H (always for H = 4 and 8)
     int ev = 8;
+    int S = 0;  // projections (the instance is compiled for S; a launch over several handles dispatches on it)
 };
 
 // ---------------------------------------------------------------------------
@@ -130,6 +131,11 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p)
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_inval(uint64_t* bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 __device__ __forceinline__ void fence_mbar_init()
@@ -911,6 +917,17 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bt, const
     }
 }
 
+
+// The mbarriers of pass_body in the block's shared memory (its layout for
+// W warps and the arguments' K, NST and stage size).
+__device__ __forceinline__ uint64_t* pass_mbarriers(unsigned char* smem, const PassArgs& a, int W)
+{
+    const KConst* kc = reinterpret_cast<const KConst*>(smem + (size_t)a.NST * a.stage_bytes);
+    const float2* wacc = reinterpret_cast<const float2*>(kc + a.K);
+    const unsigned* stage_cnt = reinterpret_cast<const unsigned*>(wacc + W * (a.K * kNV + 2));
+    const long long* issued = reinterpret_cast<const long long*>(stage_cnt + 4);
+    return const_cast<uint64_t*>(reinterpret_cast<const uint64_t*>(issued + 4));
+}
 
 template <int MODE, int S, int W, int KPW>
 __global__ void __launch_bounds__(32 * W, 16 / W) pass_kernel(const PassArgs a)

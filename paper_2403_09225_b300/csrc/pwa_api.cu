@@ -330,6 +330,7 @@ pwa::PassArgs make_args(pwa_handle* h, const double* d_theta, const double* d_v,
     a.NST = t.NST;
     a.stage_bytes = t.stage_bytes;
     a.ev = 32 / t.W;
+    a.S = h->S;
     a.P = h->P;
     a.res = h->d_res;
     a.theta = d_theta;
@@ -575,13 +576,18 @@ pwa_status batch_io(pwa_handle* h, int B)
     return PWA_OK;
 }
 
-pwa_status launch_batch(pwa_handle* h, int B, const double* d_theta, const double* d_v, double* d_out, int mode,
-                        bool err_vec)
+size_t pass_smem_bytes(const pwa_handle* h, int W)
+{
+    Tiling t = h->tiling;
+    t.W = W;
+    return smem_bytes(t, h->K, h->S);
+}
+
+pwa_status prepare_batch(pwa_handle* h, int B, const double* d_theta, const double* d_v, double* d_out,
+                         bool err_vec, cudaStream_t stream, PassArgs& a)
 {
     if (h->broken) return set_error(h, PWA_ETIMEOUT, "handle is unusable after a device-side timeout");
     if (B < 1) return set_error(h, PWA_EINVAL, "the batch needs at least one parameter vector");
-    KernelFn fn = pick_kernel(mode, h->S, h->tiling.W, h->tiling.KPW);
-    if (!fn) return set_error(h, PWA_EINVAL, "no kernel for this shape");
     int Gb = 0, ngroups = 0;
     batch_geometry(h, B, Gb, ngroups);
     if ((long long)B * Gb > 0x7fffffffLL) return set_error(h, PWA_EINVAL, "batch too large for one launch");
@@ -591,6 +597,7 @@ pwa_status launch_batch(pwa_handle* h, int B, const double* d_theta, const doubl
         // grow the scratch (block records, group records, counters); the
         // counters start at zero and every completed pass leaves them at zero
         PWA_CUDA(h, cudaStreamSynchronize(h->stream));
+        PWA_CUDA(h, cudaStreamSynchronize(stream));
         if (bs.d_block_rec) cudaFree(bs.d_block_rec);
         if (bs.d_group_rec) cudaFree(bs.d_group_rec);
         if (bs.d_counts) cudaFree(bs.d_counts);
@@ -604,13 +611,13 @@ pwa_status launch_batch(pwa_handle* h, int B, const double* d_theta, const doubl
         PWA_TRY(alloc(h, reinterpret_cast<void**>(&bs.d_group_rec), sizeof(double) * cg * h->rec_len,
                       "batch group partials"));
         PWA_TRY(alloc(h, reinterpret_cast<void**>(&bs.d_counts), sizeof(unsigned) * (cg + 2 * ct), "batch counters"));
-        PWA_CUDA(h, cudaMemsetAsync(bs.d_counts, 0, sizeof(unsigned) * (cg + 2 * ct), h->stream));
+        PWA_CUDA(h, cudaMemsetAsync(bs.d_counts, 0, sizeof(unsigned) * (cg + 2 * ct), stream));
         bs.d_err_vec = reinterpret_cast<int*>(bs.d_counts + cg + ct);
         bs.cap_blocks = cb;
         bs.cap_groups = cg;
         bs.cap_top = ct;
     }
-    PassArgs a = make_args(h, d_theta, d_v, d_out);
+    a = make_args(h, d_theta, d_v, d_out);
     a.B = B;
     a.Gb = Gb;
     a.block_rec = bs.d_block_rec;
@@ -619,9 +626,20 @@ pwa_status launch_batch(pwa_handle* h, int B, const double* d_theta, const doubl
     a.top_count = bs.d_counts + bs.cap_groups;
     a.ngroups = ngroups;
     if (err_vec) {
-        PWA_CUDA(h, cudaMemsetAsync(bs.d_err_vec, 0, sizeof(int) * B, h->stream));
+        PWA_CUDA(h, cudaMemsetAsync(bs.d_err_vec, 0, sizeof(int) * B, stream));
         a.err_vec = bs.d_err_vec;
     }
+    return PWA_OK;
+}
+
+pwa_status launch_batch(pwa_handle* h, int B, const double* d_theta, const double* d_v, double* d_out, int mode,
+                        bool err_vec)
+{
+    KernelFn fn = pick_kernel(mode, h->S, h->tiling.W, h->tiling.KPW);
+    if (!fn) return set_error(h, PWA_EINVAL, "no kernel for this shape");
+    PassArgs a;
+    PWA_TRY(prepare_batch(h, B, d_theta, d_v, d_out, err_vec, h->stream, a));
+    const size_t blocks = (size_t)B * a.Gb;
     fn<<<(unsigned)blocks, 32 * h->tiling.W, h->tiling.smem, h->stream>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(h, e, "batched pass kernel launch");

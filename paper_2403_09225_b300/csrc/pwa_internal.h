@@ -135,6 +135,36 @@ pwa_status launch_pass_args(pwa_handle* h, const PassArgs& a, int mode);
 // err_vec: clear and fill the per-vector error words h->batch.d_err_vec [B].
 pwa_status launch_batch(pwa_handle* h, int B, const double* d_theta, const double* d_v, double* d_out, int mode,
                         bool err_vec = false);
+// The arguments of a batched pass of B vectors on h without launching it:
+// grows the handle's batch scratch (memsets on `stream`; when the scratch
+// grows, the handle's stream and `stream` are synchronised first).
+pwa_status prepare_batch(pwa_handle* h, int B, const double* d_theta, const double* d_v, double* d_out,
+                         bool err_vec, cudaStream_t stream, PassArgs& a);
+// Arguments of a launch over several handles: device copies and their pinned
+// staging (the staging must not change until the launch's copies are done --
+// a captured graph replays the copies from it).
+struct MultiScratch {
+    int cap = 0;
+    PassArgs* d_args = nullptr;
+    int* d_first = nullptr;
+    unsigned char* h_stage = nullptr;
+    MultiScratch() = default;
+    MultiScratch(const MultiScratch&) = delete;
+    MultiScratch& operator=(const MultiScratch&) = delete;
+    ~MultiScratch();
+};
+// One batched pass (mode GRAD or HVP) over several handles in one launch on
+// `stream` (multi.cu): handle i evaluates B[i] vectors d_theta[i] -> d_out[i].
+// Every handle needs K <= 32.  No synchronisation: the caller keeps ms's
+// staging unchanged until the launch's argument copies are done.
+pwa_status launch_multi(int n, pwa_handle* const* hs, const int* B, const double* const* d_theta,
+                        const double* const* d_v, double* const* d_out, int mode, bool err_vec, cudaStream_t stream,
+                        MultiScratch& ms);
+// Size ms for n handles (allocates; call outside a stream capture).
+pwa_status launch_multi_reserve(pwa_handle* h0, int n, MultiScratch& ms);
+constexpr int kMaxKMulti = 32;
+// Shared memory per block of a pass instance with W warps over the handle's tiles.
+size_t pass_smem_bytes(const pwa_handle* h, int W);
 // Device I/O buffers of the batch state for B vectors (grown when needed).
 pwa_status batch_io(pwa_handle* h, int B);
 void free_batch(pwa_handle* h);

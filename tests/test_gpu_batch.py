@@ -129,24 +129,99 @@ def test_batched_fit_reports_a_bad_start_per_fit():
     assert abs(infos[0]["nll"] - info_single["nll"]) <= 1e-6 * abs(info_single["nll"])
 
 
-def test_fits_over_several_handles_equal_each_handles_own_batch():
-    """Toy fits of different models and sample sizes (K, S, N differ) in
-    lockstep over several handles: the same results, bit for bit, as each
-    handle's own batched fits (the groups only share the rounds)."""
+def _toys():
+    """Three toy likelihoods of different K, S and sizes (ragged tiles)."""
+    wls = [small_workload("tiny", 3000 + 7, 15000 + 3), small_workload("tiny_k4", 2001, 8001),
+           small_workload("paper", 800 + 5, 3000 + 11)]
+    cfg = W.Config("k7s3", 7, 3, 0, 0, 2, False, 11)
+    wl = W.make_workload(cfg, intensity=None, n_data=1234, n_mc=5077)
+    wls.append((wl, oracle.Model.from_table(wl.table, cfg.S)))
+    return wls
+
+
+def test_one_launch_over_several_handles_matches_the_oracle():
+    """pwa_eval_multi_device: one launch over toys of K = 3, 4, 20, 7 and
+    S = 2, 2, 4, 3, two parameter vectors each (theta_true and a prior start),
+    every row at the oracle's bars; then a gradient-only launch."""
     from paper_2403_09225_b300 import binding
-    wls = [small_workload("tiny", 3000 + 7, 15000 + 3)[0], small_workload("tiny_k4", 2001, 8001)[0],
-           small_workload("paper", 800 + 5, 3000 + 11)[0]]
-    Ls = [make_L(wl) for wl in wls]
-    starts = []
-    for i, wl in enumerate(wls):
+    toys = _toys()
+    Ls = [make_L(wl) for wl, _ in toys]
+    thetas, vs = [], []
+    for wl, model in toys:
+        thetas.append(np.stack([wl.theta_true, W.random_starts(wl, 1)[0]]))
+        vs.append(np.stack([np.linspace(-1, 1, model.P), np.cos(np.arange(model.P))]))
+    res = binding.eval_multi(Ls, thetas, vs)
+    for (wl, model), th, v, (f, g, hv) in zip(toys, thetas, vs, res):
+        for b in range(2):
+            fo, go, hvo = oracle.nll_grad_hvp(model, th[b], v[b], wl.data, wl.mc)
+            assert abs(f[b] - fo) <= TOL_NLL * nll_scale(model, th[b], wl, fo), (f[b], fo)
+            assert relmax(g[b], go) <= TOL_GRAD, relmax(g[b], go)
+            assert relmax(hv[b], hvo) <= TOL_HVP, relmax(hv[b], hvo)
+    res2 = binding.eval_multi(Ls, thetas)
+    for (f, g, _), (f2, g2, hv2) in zip(res, res2):
+        assert hv2 is None and np.allclose(f2, f, rtol=1e-12, atol=0) and relmax(g2, g) <= 1e-6
+
+
+def test_one_launch_over_many_handles_sharing_ctas():
+    """Ten toys of K 5..30 and S 2..4, eight vectors each: the work list is
+    several times longer than the CTAs that fit on the GPU, so CTAs run
+    entries of different handles one after another (different shared-memory
+    layouts).  Every row agrees with the handle's own batched pass."""
+    from paper_2403_09225_b300 import binding
+    rng = np.random.default_rng(31)
+    toys, Ls = [], []
+    for i, (K, S) in enumerate(((5, 2), (30, 3), (12, 4), (26, 2), (8, 3), (22, 4), (17, 4), (13, 2), (25, 4),
+                                (7, 2))):
+        cfg = W.Config("t%d" % i, K, S, 0, 0, 4, False, 200 + i)
+        wl = W.make_workload(cfg, intensity=None, n_data=int(rng.integers(2000, 9000)),
+                             n_mc=int(rng.integers(8000, 30000)))
+        toys.append(wl)
+        Ls.append(make_L(wl))
+    thetas = [W.random_starts(wl, 8) for wl in toys]
+    vs = [np.tile(np.linspace(-1, 1, L.P), (8, 1)) for L in Ls]
+    res = binding.eval_multi(Ls, thetas, vs)
+    for L, th, v, (f, g, hv) in zip(Ls, thetas, vs, res):
+        f2, g2, hv2 = L.eval_batch(th, v)
+        assert np.all(np.isfinite(f)) and np.all(np.isfinite(hv))
+        assert np.max(np.abs(f - f2) / np.maximum(np.abs(f2), 1.0)) <= 1e-6
+        for b in range(8):
+            assert relmax(g[b], g2[b]) <= 1e-5 and relmax(hv[b], hv2[b]) <= 1e-4
+
+
+def test_fits_over_several_handles_reach_the_oracle_minima():
+    """Toy fits of different models and sample sizes (K, S, N differ) in
+    lockstep over several handles -- one launch per round over all of them
+    (pwa_eval_multi_device, its rounds captured into CUDA graphs) -- reach,
+    toy by toy, the minimum the oracle's textbook Newton-CG finds, within
+    1e-3 of the oracle's parameter errors.  Each toy's data are drawn from its
+    own model and its starts lie 0.2 sigma per parameter from the oracle's
+    minimum (inside the basin: paths from far away can end in different
+    local minima under different FP32 rounding)."""
+    from paper_2403_09225_b300 import binding
+    toys = [small_workload("tiny", 3000 + 7, 15000 + 3), small_workload("tiny_k4", 2001, 8001)]
+    for K, S, seed in ((5, 3, 13), (6, 2, 17)):
+        cfg = W.Config("k%ds%d" % (K, S), K, S, 0, 0, 2, False, seed)
+        model = oracle.Model.from_table(W.make_table(cfg), S)
+        fn = lambda m2, F, cfg=cfg, model=model: oracle.intensity_full(cfg.K, cfg.S, model.channels, model.par0, m2, F)
+        toys.append((W.make_workload(cfg, intensity=fn, n_data=6001, n_mc=24001), model))
+    refs, starts = [], []
+    for i, (wl, model) in enumerate(toys):
+        fg = lambda x, wl=wl, model=model: oracle.nll_grad(model, x, wl.data, wl.mc)
+        hp = lambda x, v, wl=wl, model=model: oracle.nll_grad_hvp(model, x, v, wl.data, wl.mc)[2]
+        ref = ncg.newton_cg(fg, hp, wl.theta_true, xtol=1e-10, maxiter=300)
+        assert ref.status in ncg.CONVERGED, ref.status_name
+        sig = oracle.parameter_errors(oracle.hessian(model, ref.x, wl.data, wl.mc))
+        refs.append((ref.x, sig))
         rng = np.random.default_rng(20 + i)
-        starts.append(wl.theta_true * (1 + 0.02 * rng.standard_normal((3, wl.theta_true.size))))
-    outs, infos, _ = binding.fit_multi(Ls, starts, xtol=1e-8, maxiter=20)
-    for L, st, o, inf in zip(Ls, starts, outs, infos):
-        o2, inf2, _ = L.fit_batch(st, xtol=1e-8, maxiter=20)
-        assert np.array_equal(o, o2)
-        assert [r["nll"] for r in inf] == [r["nll"] for r in inf2]
-        assert [r["status"] for r in inf] == [r["status"] for r in inf2]
+        starts.append(ref.x + 0.2 * sig * rng.standard_normal((3, ref.x.size)))
+    Ls = [make_L(wl) for wl, _ in toys]
+    for matrix_free in (False, True):
+        outs, infos, ok = binding.fit_multi(Ls, starts, xtol=1e-10, matrix_free=matrix_free)
+        assert ok, infos
+        for (wl, model), (x_ref, sig), o in zip(toys, refs, outs):
+            for th in o:
+                pull = (oracle.canonical(model, th) - oracle.canonical(model, x_ref)) / sig
+                assert np.max(np.abs(pull)) <= 1e-3, (matrix_free, np.max(np.abs(pull)))
 
 
 def test_autotune_keeps_results_within_tolerance():
