@@ -280,10 +280,12 @@ def batching_metric(n_toys: int, n_starts: int, time_limit: float, seed: int = 7
     with data sizes capped at 1e5 to keep a run to minutes), accept-rejects its
     data from I at its own generating point, and is fitted from n_starts
     random starts.  Plain: every fit of every toy one after another.  Batched:
-    all fits of all toys in lockstep (pwa_newton_cg_fit_multi; one batched
-    pass per toy per round, the toys' passes on concurrent streams).  A fit
+    all fits of all toys in lockstep (pwa_newton_cg_fit_multi: every round is
+    one persistent launch over all toys, captured into a CUDA graph once its
+    shape repeats), with one Hessian pass per fit and outer iteration, or
+    matrix-free (every inner CG product a row of the shared launch).  A fit
     reaches the global minimum when its NLL is within 0.01 of the best NLL of
-    its toy (over both arms and a fit from the generating point)."""
+    its toy (over all arms and a fit from the generating point)."""
     from paper_2403_09225_b300 import binding
     from paper_2403_09225_b300 import workload as W
     rng = np.random.default_rng(seed)
@@ -308,8 +310,14 @@ def batching_metric(n_toys: int, n_starts: int, time_limit: float, seed: int = 7
         t0 = time.perf_counter()
         _, batched, _ = binding.fit_multi(Ls, starts, xtol=1e-8, time_limit_s=time_limit * n_toys * n_starts)
         t_batched = time.perf_counter() - t0
+        # matrix-free lockstep: every inner CG product of every fit of every toy in one launch per round
+        t0 = time.perf_counter()
+        _, batched_mf, _ = binding.fit_multi(Ls, starts, xtol=1e-8, time_limit_s=time_limit * n_toys * n_starts,
+                                             matrix_free=True)
+        t_batched_mf = time.perf_counter() - t0
         for i in range(n_toys):
-            best[i] = min([best[i]] + [r["nll"] for r in plain[i]] + [r["nll"] for r in batched[i]])
+            best[i] = min([best[i]] + [r["nll"] for r in plain[i]] + [r["nll"] for r in batched[i]] +
+                          [r["nll"] for r in batched_mf[i]])
 
         def arm(results, seconds):
             ok = sum(1 for i in range(n_toys) for r in results[i] if r["nll"] <= best[i] + 0.01)
@@ -319,7 +327,13 @@ def batching_metric(n_toys: int, n_starts: int, time_limit: float, seed: int = 7
                     "statuses": sorted({r["status"] for rr in results for r in rr})}
         return {"toys": n_toys, "starts_per_toy": n_starts, "time_limit_s_per_fit": time_limit,
                 "K": [wl.K for wl in toys], "S": [wl.S for wl in toys], "n_data": [wl.data.n for wl in toys],
-                "plain": arm(plain, t_plain), "batched": arm(batched, t_batched)}
+                "plain": arm(plain, t_plain), "batched": arm(batched, t_batched),
+                "batched_matrix_free": arm(batched_mf, t_batched_mf),
+                "arms": {"plain": "one fit after another, one Hessian pass per outer iteration",
+                         "batched": "all fits of all toys in lockstep, one launch over every toy per f, g round, "
+                                    "Hessian passes one per fit",
+                         "batched_matrix_free": "the same with every inner CG product an H v row of the shared "
+                                                "launch"}}
     finally:
         for L in Ls:
             L.close()
@@ -548,6 +562,32 @@ def variant_metric(wl, reps: int = 10):
     return out
 
 
+def hessian_metric(L, wl, reps: int = 10):
+    """The Hessian pass (pwa_hessian: NLL, gradient and the full P x P
+    Hessian from one pass over F) on the benchmark's workload: host calls
+    timed with CUDA events on the handle's stream, plus the Gram-matrix
+    flops it performs (X^T X over the (event, projection) rows of 4K
+    columns for data and MC, z^T z over the data events)."""
+    import torch
+    th = wl.theta_true
+    for _ in range(2):
+        L.hessian(th)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        L.hessian(th)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    C = 4 * wl.K
+    rows = (wl.data.n + wl.mc.n) * wl.S
+    flops = 2.0 * rows * C * (C + 1) / 2 + 2.0 * wl.data.n * C * (C + 1) / 2
+    return {"ms_per_call": ms, "P": L.P, "gram_flops_per_call": flops,
+            "gram_tflops": flops / (ms * 1e-3) / 1e12, "fused_passes_per_hessian": None}
+
+
 def diff_metric(reps: int = 20):
     """The differentiation configuration at full size: K = 40, S = 4, 2e6
     data + 1e7 MC phase-space events (15.4 GB of F), its caller-layout copy
@@ -648,9 +688,9 @@ def main():
     ap.add_argument("--no-diff", action="store_true", help="skip the full-size differentiation configuration leg")
     ap.add_argument("--mlp-timing", action="store_true",
                     help="also time the learned proposal's network (gradient step at batches 128, 512, 1024)")
-    ap.add_argument("--batching", default="12,4", metavar="TOYS,STARTS",
+    ap.add_argument("--batching", default="12,16", metavar="TOYS,STARTS",
                     help="uneven-size toy-fit comparison (plain vs batched); 0 to skip")
-    ap.add_argument("--learned", default="4096,24,16", metavar="TRAIN,EVAL,STARTS",
+    ap.add_argument("--learned", default="8192,48,16", metavar="TRAIN,EVAL,STARTS",
                     help="train and evaluate the learned starting-point proposal; 0 to skip")
     ap.add_argument("--learned-time-limit", type=float, default=20.0, help="seconds per fit call in the learned leg")
     ap.add_argument("--learned-polish", action="store_true",
@@ -746,6 +786,11 @@ def main():
     e2e_dt = time.perf_counter() - t0
     e2e_value, e2e_ms = aggregate_replicas(e2e_dt / e2e_steps * 1e3, units, dist)
 
+    hess = None
+    if rank == 0:
+        hess = hessian_metric(L, wl)
+        hess["fused_passes_per_hessian"] = hess["ms_per_call"] / ms
+
     fit = None
     if args.fits > 0 and rank == 0:
         t0 = time.perf_counter()
@@ -809,6 +854,8 @@ def main():
             "clocks": clk.summary(),
         }
         res["hvp_reuse"] = reuse
+        if hess is not None:
+            res["hessian"] = hess
         if cpu is not None:
             res["cpu_baseline"] = cpu
         if fit is not None:

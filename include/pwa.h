@@ -146,8 +146,9 @@ typedef enum {
     PWA_FIT_LINESEARCH = 4,  /* no step satisfied the Wolfe conditions             */
     PWA_FIT_PRECISION = 5,   /* converged: predicted decrease below the NLL's
                                 resolution, no further step can be resolved, or
-                                |grad| stalled at its rounding floor (no 1 %
-                                improvement in 25 outer iterations)                */
+                                the fit stalled at its rounding floor (25 outer
+                                iterations without a 1 % lower |grad| or an NLL
+                                drop above ten times its resolution)               */
     PWA_FIT_ERROR = 6        /* stopped on an error (e.g. a non-finite NLL at its
                                 start point); only pwa_newton_cg_fit_batch reports
                                 it per fit, pwa_newton_cg_fit returns the error    */

@@ -16,8 +16,9 @@
 //    (the "approximate Wolfe" idea of Hager & Zhang, 2005);
 //  * a failed line search whose predicted decrease |g.p| is below
 //    1e-7 (1 + |f|) ends the fit as converged at the precision limit;
-//  * so does a gradient norm that has not improved by 1 % for 25 outer
-//    iterations (the noise floor of the FP32-summed gradient).
+//  * so do 25 outer iterations in which neither the gradient norm improved
+//    by 1 % nor the NLL dropped by more than ten times its resolution (the
+//    noise floor of the FP32 sums).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -307,8 +308,10 @@ struct FitState {
     double* rH = nullptr;        // HESS: the Hessian [P][P] at rx
     double cg_eps = 0.0;         // CG: solve H p = -g at (x, g) to |r| < cg_eps into p
     pwa_status req_status = PWA_OK;
-    // noise floor: the best |g| so far and the outer iteration that last improved it by 1 %
-    double g_best = INFINITY;
+    // noise floor: the best |g| so far, the NLL and the outer iteration of
+    // the last real progress (|g| 1 % below its best, or the NLL lower by
+    // more than ten times its resolution)
+    double g_best = INFINITY, f_mark = INFINITY;
     int k_best = 0;
     // per-iteration records (opts.trace); cur_it is the one being filled
     std::vector<pwa_fit_iter> trace;
@@ -358,17 +361,20 @@ void push_iter(FitState& s)
     if ((int)s.trace.size() < s.o.trace_cap) s.trace.push_back(s.cur_it);
 }
 
-// Stagnation at the FP32 noise floor: |g| has not improved by 1 % over its
-// best for kStall outer iterations.  Near the minimum the gradient of the
-// FP32-summed NLL is dominated by rounding and the steps wander at that
-// level without ever meeting xtol; the fit has then converged as far as the
-// evaluation resolves.
+// Stagnation at the FP32 noise floor: for kStall outer iterations neither has
+// |g| improved by 1 % over its best nor has the NLL dropped by more than ten
+// times its resolution.  Near the minimum the gradient of the FP32-summed
+// NLL is dominated by rounding and the steps wander at that level without
+// ever meeting xtol; the fit has then converged as far as the evaluation
+// resolves.  (A long descent keeps lowering the NLL and is not cut short.)
 constexpr int kStall = 25;
 bool stalled(FitState& s, int k)
 {
     const double gn = std::sqrt(dot(s.g, s.g));
-    if (gn < 0.99 * s.g_best) {
-        s.g_best = gn;
+    const double resolution = 1e-7 * (1.0 + std::fabs(s.f));
+    if (gn < 0.99 * s.g_best || s.f < s.f_mark - 10.0 * resolution) {
+        s.g_best = std::min(s.g_best, gn);
+        s.f_mark = s.f;
         s.k_best = k;
         return false;
     }
