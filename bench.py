@@ -282,10 +282,11 @@ def batching_metric(n_toys: int, n_starts: int, time_limit: float, seed: int = 7
     random starts.  Plain: every fit of every toy one after another.  Batched:
     all fits of all toys in lockstep (pwa_newton_cg_fit_multi: every round is
     one persistent launch over all toys, captured into a CUDA graph once its
-    shape repeats), with one Hessian pass per fit and outer iteration, or
-    matrix-free (every inner CG product a row of the shared launch).  A fit
-    reaches the global minimum when its NLL is within 0.01 of the best NLL of
-    its toy (over all arms and a fit from the generating point)."""
+    shape repeats), with one Hessian pass per fit and outer iteration.  (A
+    matrix-free lockstep, every inner CG product a row of the shared launch,
+    took 7x the GPU time in a measured run: fit_multi(..., matrix_free=True).)  A
+    fit reaches the global minimum when its NLL is within 0.01 of the best NLL
+    of its toy (over both arms and a fit from the generating point)."""
     from paper_2403_09225_b300 import binding
     from paper_2403_09225_b300 import workload as W
     rng = np.random.default_rng(seed)
@@ -310,14 +311,8 @@ def batching_metric(n_toys: int, n_starts: int, time_limit: float, seed: int = 7
         t0 = time.perf_counter()
         _, batched, _ = binding.fit_multi(Ls, starts, xtol=1e-8, time_limit_s=time_limit * n_toys * n_starts)
         t_batched = time.perf_counter() - t0
-        # matrix-free lockstep: every inner CG product of every fit of every toy in one launch per round
-        t0 = time.perf_counter()
-        _, batched_mf, _ = binding.fit_multi(Ls, starts, xtol=1e-8, time_limit_s=time_limit * n_toys * n_starts,
-                                             matrix_free=True)
-        t_batched_mf = time.perf_counter() - t0
         for i in range(n_toys):
-            best[i] = min([best[i]] + [r["nll"] for r in plain[i]] + [r["nll"] for r in batched[i]] +
-                          [r["nll"] for r in batched_mf[i]])
+            best[i] = min([best[i]] + [r["nll"] for r in plain[i]] + [r["nll"] for r in batched[i]])
 
         def arm(results, seconds):
             ok = sum(1 for i in range(n_toys) for r in results[i] if r["nll"] <= best[i] + 0.01)
@@ -328,12 +323,9 @@ def batching_metric(n_toys: int, n_starts: int, time_limit: float, seed: int = 7
         return {"toys": n_toys, "starts_per_toy": n_starts, "time_limit_s_per_fit": time_limit,
                 "K": [wl.K for wl in toys], "S": [wl.S for wl in toys], "n_data": [wl.data.n for wl in toys],
                 "plain": arm(plain, t_plain), "batched": arm(batched, t_batched),
-                "batched_matrix_free": arm(batched_mf, t_batched_mf),
                 "arms": {"plain": "one fit after another, one Hessian pass per outer iteration",
                          "batched": "all fits of all toys in lockstep, one launch over every toy per f, g round, "
-                                    "Hessian passes one per fit",
-                         "batched_matrix_free": "the same with every inner CG product an H v row of the shared "
-                                                "launch"}}
+                                    "Hessian passes one per fit"}}
     finally:
         for L in Ls:
             L.close()
@@ -570,22 +562,39 @@ def hessian_metric(L, wl, reps: int = 10):
     columns for data and MC, z^T z over the data events)."""
     import torch
     th = wl.theta_true
-    for _ in range(2):
-        L.hessian(th)
     stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(reps):
-        L.hessian(th)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
+
+    def timed():
+        for _ in range(2):
+            L.hessian(th)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            L.hessian(th)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
     C = 4 * wl.K
     rows = (wl.data.n + wl.mc.n) * wl.S
-    flops = 2.0 * rows * C * (C + 1) / 2 + 2.0 * wl.data.n * C * (C + 1) / 2
-    return {"ms_per_call": ms, "P": L.P, "gram_flops_per_call": flops,
-            "gram_tflops": flops / (ms * 1e-3) / 1e12, "fused_passes_per_hessian": None}
+    # useful flops of the Gram matrices (full C x C: what the contraction computes)
+    flops = 2.0 * rows * C * C + 2.0 * wl.data.n * C * C
+    ms = timed()
+    L.set_hessian_cuda_cores(True)
+    ms_cc = timed()
+    L.set_hessian_cuda_cores(False)
+    peak, kind = bf16_peak()
+    out = {"ms_per_call": ms, "P": L.P, "gram_flops_per_call": flops, "cuda_cores_ms_per_call": ms_cc,
+           "fused_passes_per_hessian": None}
+    if wl.K <= 32:
+        out["gram_tflops"] = flops / (ms * 1e-3) / 1e12
+        out["roofline"] = {"bound": "tensor", "achieved": out["gram_tflops"], "unit": "TFLOP/s", "peak": peak,
+                           "frac": out["gram_tflops"] / peak, "peak_kind": kind,
+                           "note": "useful Gram flops over the host call's time; the BF16 hi/lo split issues 3 "
+                                   "products per useful one, and the event phase (Breit-Wigner, coherent sums, "
+                                   "operand split) runs on the CUDA cores between the tiles' MMAs"}
+    return out
 
 
 def diff_metric(reps: int = 20):

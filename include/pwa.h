@@ -212,9 +212,18 @@ pwa_status pwa_hvp(pwa_handle* h, const double* theta, const double* v, double* 
  * projection) and of the adjoint terms B^p D_k, plus the resonance-diagonal
  * second-derivative sums; the host combines them in FP64.  theta: host [P];
  * nll, grad: host (either may be NULL); hess: host [P][P] row-major,
- * symmetric.  Supported for K <= 44.  Errors: PWA_EINVAL (K > 44, non-finite
- * theta), PWA_ENOMEM, PWA_ECUDA, PWA_ENONFINITE, PWA_ETIMEOUT. */
+ * symmetric.  For K <= 32 the Gram matrices are contractions on the tensor
+ * cores (tcgen05, BF16 hi/lo splits of the FP32 columns, three products per
+ * 16 rows, a fresh TMEM accumulator per 32-event tile, FP32 then FP64 sums
+ * across tiles); for 32 < K <= 44 on the CUDA cores in FP32.  Supported for
+ * K <= 44.  Errors: PWA_EINVAL (K > 44, non-finite theta), PWA_ENOMEM,
+ * PWA_ECUDA, PWA_ENONFINITE, PWA_ETIMEOUT. */
 pwa_status pwa_hessian(pwa_handle* h, const double* theta, double* nll, double* grad, double* hess);
+
+/* Run the Hessian pass's Gram matrices on the CUDA cores (cuda_cores = 1)
+ * even where the tensor-core kernel applies (K <= 32), for comparisons;
+ * 0 restores the default. */
+pwa_status pwa_set_hessian_cuda_cores(pwa_handle* h, int cuda_cores);
 
 /* The fused pass: NLL, gradient and H v from one read of F.  Any of grad,
  * hv may be NULL (then the cheaper pass without them runs); v is required

@@ -85,7 +85,9 @@ class PwaError(RuntimeError):
 
 
 #: every symbol include/pwa.h declares
-EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "pwa_grad", "pwa_hvp", "pwa_hessian", "pwa_hvp_reuse", "pwa_hvp_reuse_device", "pwa_eval_multi_device", "pwa_release_event_copies",
+EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "pwa_grad", "pwa_hvp", "pwa_hessian",
+           "pwa_hvp_reuse", "pwa_hvp_reuse_device", "pwa_eval_multi_device", "pwa_set_hessian_cuda_cores",
+           "pwa_release_event_copies",
            "pwa_device_bytes",
            "pwa_eval", "pwa_eval_device", "pwa_eval_device_noalloc", "pwa_eval_batch", "pwa_eval_batch_device",
            "pwa_sync", "pwa_event_intensity", "pwa_newton_cg_fit", "pwa_newton_cg_fit_batch",
@@ -123,6 +125,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                        ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), i, i, vp]),
         "pwa_hvp_reuse_device": (st, [H, vp, vp, vp]),
         "pwa_release_event_copies": (st, [H]),
+        "pwa_set_hessian_cuda_cores": (st, [H, i]),
         "pwa_device_bytes": (st, [H, ctypes.POINTER(ctypes.c_longlong)]),
         "pwa_eval_device": (st, [H, vp, vp, vp, i, i]),
         "pwa_eval_device_noalloc": (st, [H, vp, vp, vp, i, i]),
@@ -297,6 +300,10 @@ class Likelihood:
         hv = np.empty(self.P)
         self._check(lib().pwa_hvp(self._h, _dptr(th), _dptr(vv), _dptr(hv)))
         return hv
+
+    def set_hessian_cuda_cores(self, on: bool):
+        """Hessian Gram matrices on the CUDA cores even where tensor cores apply."""
+        self._check(lib().pwa_set_hessian_cuda_cores(self._h, int(on)))
 
     def release_event_copies(self):
         """Free the caller-layout event copies (the tiling becomes fixed)."""

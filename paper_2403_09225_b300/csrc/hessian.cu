@@ -43,7 +43,10 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "pwa_internal.h"
+#include "tcgen05.cuh"
 
 namespace {
 
@@ -51,6 +54,7 @@ using pwa::KConst;
 constexpr int kE = pwa::kTileE;  // events per tile
 constexpr int kFold = 16;        // tiles between FP32 -> FP64 folds
 constexpr int kMaxKHess = pwa::kMaxKHessian;  // K (K + 1) / 2 Gram blocks fit 2 per thread of 512
+constexpr int kMaxKTensor = 32;                // 4K columns fit the M = 128 tensor-core tile
 
 struct HessArgs {
     const unsigned char* tiles[2];  // data, MC tile records (the handle's layout)
@@ -448,6 +452,453 @@ __global__ void __launch_bounds__(NT, 1) hess_kernel(const HessArgs a)
     fold(cur_smp);
 }
 
+
+// ---------------------------------------------------------------------------
+// The Gram matrices on the tensor cores (K <= 32: 4K <= 128 columns)
+// ---------------------------------------------------------------------------
+//
+// The same event phase as hess_kernel, but X and z go to shared memory as
+// BF16 pairs (x = hi + lo, each the nearest BF16 of what is left: 16
+// significant bits) in the canonical K-major layout of a tcgen05 operand:
+// element (column m, row k) in 8 x 16-byte core matrices, rows k along the
+// MMA's K dimension (X row e S + s: an event's projections are adjacent, so
+// a lane writes them in one store; the Gram does not depend on the order).  The same buffer is the A operand (M = 128 columns, the
+// ones past 4K zero) and the B operand (N = 4K rounded up to 16) of
+// D = X^T X, so one thread issues, per 16 rows, three kind::f16 MMAs
+// (hi hi, hi lo, lo hi; lo lo is below 2^-16 of the product) into a TMEM
+// accumulator that starts fresh at every tile (one tile's sum stays short,
+// so the tensor core's FP32 accumulation loses nothing), and the z Gram of
+// the data events likewise.  After each tile the eight warps read the
+// accumulators back (warp w: TMEM lanes 32 (w mod 4) + l, half w / 4 of
+// the columns) and add them to FP32 registers, folded into FP64 every kFold
+// tiles like the other sums.  Per-CTA record: the full data X Gram, the data
+// z Gram and the MC X Gram (C x C each, row-major), then Q [2][K][6] and the
+// scalars [8][2].
+
+constexpr uint32_t kTcLbo = 144;  // core-matrix stride along the rows (16 B of padding: phase 1's
+                                  // stores from 32 lanes spread over the banks)
+constexpr int kTcCols = 128;      // M of the MMA: the columns of X padded to 128
+constexpr int kTcTmemCols = 256;  // X Gram at TMEM columns [0, 128), z Gram at [128, 256)
+constexpr int kTcNT = 256;  // 8 warps (16 were slower: the cross-warp sums of the event phase grow)
+constexpr int kTcKW = 4;    // resonances per warp in the event phase: K <= 8 x 4 = 32
+
+__host__ __device__ inline uint32_t tc_sbo(int rows) { return (uint32_t)(rows / 8) * kTcLbo; }
+__host__ __device__ inline uint32_t tc_part(int rows) { return (uint32_t)(kTcCols / 8) * tc_sbo(rows); }
+__host__ __device__ inline int hess_tc_rec_len(int K) { return 3 * 16 * K * K + 12 * K + 2 * (kTcNT / 32); }
+// byte offset of (column m, row k) in a K-major BF16 operand part with stride sbo between 8-column groups
+__host__ __device__ inline uint32_t tc_off(int m, int k, uint32_t sbo)
+{
+    return (uint32_t)(m >> 3) * sbo + (uint32_t)(k >> 3) * kTcLbo + (uint32_t)(m & 7) * 16 + (uint32_t)(k & 7) * 2;
+}
+__host__ inline size_t hess_tc_smem(int K, int S, uint32_t stage)
+{
+    return 2 * (size_t)tc_part(32 * S) + 2 * (size_t)tc_part(32) + 2 * (size_t)stage + sizeof(KConst) * K +
+           sizeof(float) * (size_t)(kTcNT / 32) * 2 * S * 32 + 3 * 8 + 16;
+}
+
+__device__ __forceinline__ void store_split(unsigned char* part0, uint32_t part_bytes, uint32_t off, float x)
+{
+    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+    *reinterpret_cast<__nv_bfloat16*>(part0 + off) = hi;
+    *reinterpret_cast<__nv_bfloat16*>(part0 + part_bytes + off) = lo;
+}
+
+// 4 consecutive 32-bit columns of this thread's TMEM lane (valid after tmem_wait)
+__device__ __forceinline__ void tmem_ld4(uint32_t addr, uint32_t (&r)[4])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+// The S consecutive rows (e S .. e S + S - 1) of one column: hi and lo parts,
+// one 4- or 8-byte store per part for S = 2, 4 (the rows share a 16-byte core row)
+template <int S>
+__device__ __forceinline__ void store_rows(unsigned char* part0, uint32_t part_bytes, uint32_t off, const float (&x)[S])
+{
+    unsigned short hb[S], lb[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x[s]);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(x[s] - __bfloat162float(hi));
+        hb[s] = __bfloat16_as_ushort(hi);
+        lb[s] = __bfloat16_as_ushort(lo);
+    }
+    if constexpr (S == 4) {
+        *reinterpret_cast<uint2*>(part0 + off) = make_uint2(hb[0] | ((uint32_t)hb[1] << 16), hb[2] | ((uint32_t)hb[3] << 16));
+        *reinterpret_cast<uint2*>(part0 + part_bytes + off) =
+            make_uint2(lb[0] | ((uint32_t)lb[1] << 16), lb[2] | ((uint32_t)lb[3] << 16));
+    } else if constexpr (S == 2) {
+        *reinterpret_cast<uint32_t*>(part0 + off) = hb[0] | ((uint32_t)hb[1] << 16);
+        *reinterpret_cast<uint32_t*>(part0 + part_bytes + off) = lb[0] | ((uint32_t)lb[1] << 16);
+    } else {
+        // odd S: the rows may cross a 16-byte core row; one 2-byte store each
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int r = (int)((off >> 1) & 7) + s;  // row within its core row, from the first's offset
+            const uint32_t o = off + (uint32_t)(r >> 3) * kTcLbo + (uint32_t)((r & 7) - ((off >> 1) & 7)) * 2;
+            *reinterpret_cast<unsigned short*>(part0 + o) = hb[s];
+            *reinterpret_cast<unsigned short*>(part0 + part_bytes + o) = lb[s];
+        }
+    }
+}
+
+template <int S, int NCH>  // NCH = (4K rounded up to 16) / 16
+__global__ void __launch_bounds__(kTcNT, 1) hess_tc_kernel(const HessArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    constexpr int NT = kTcNT, NW = NT / 32, R = 32 * S, Cp = NCH * 16;
+    constexpr int CPT = Cp / (NW / 4);  // Gram columns per thread: the warps of a TMEM lane quarter split them
+    static_assert(kTcKW * NW >= 32, "the event phase must cover K <= 32");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int K = a.K, C = 4 * K;
+    const uint32_t SBOX = tc_sbo(R), PBX = tc_part(R), SBOZ = tc_sbo(32), PBZ = tc_part(32);
+
+    // shared memory: X operand [hi | lo] | z operand [hi | lo] | stages[2] | KConst[K] |
+    // partial A [NW][2S][32] | mbarriers (TMA stages 0, 1; MMA done) | TMEM address
+    unsigned char* xop = smem;
+    unsigned char* zop = xop + 2 * PBX;
+    unsigned char* stages = zop + 2 * PBZ;
+    KConst* kc = reinterpret_cast<KConst*>(stages + 2 * (size_t)a.stage_bytes);
+    float* PA = reinterpret_cast<float*>(kc + K);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(PA + NW * 2 * S * 32);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 3);
+    __shared__ long long issued[2];
+    __shared__ int s_abort;
+
+    const int G = gridDim.x;
+    const long long T = (long long)a.ntiles[0] + a.ntiles[1];
+    auto tile_src = [&](long long t, int& smp, long long& lt) {
+        smp = t < a.ntiles[0] ? 0 : 1;
+        lt = smp ? t - a.ntiles[0] : t;
+    };
+    if (tid == 0) {
+        s_abort = 0;
+        for (int s = 0; s < 3; ++s) pwa::mbar_init(&mbar[s], 1);
+        issued[0] = issued[1] = -1;
+        pwa::fence_mbar_init();
+        for (int i = 0; i < 2; ++i) {
+            const long long t = blockIdx.x + (long long)i * G;
+            if (t < T) {
+                int smp;
+                long long lt;
+                tile_src(t, smp, lt);
+                pwa::tma_load_tile(stages + (size_t)i * a.stage_bytes, a.tiles[smp] + (size_t)lt * a.tile_bytes[smp],
+                                   a.tile_bytes[smp], &mbar[i]);
+                issued[i] = i;
+            }
+        }
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(pwa::tc::sa(tslot)),
+                     "r"(kTcTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    {
+        pwa::PassArgs pa;
+        pa.res = a.res;
+        for (int k = tid; k < K; k += NT) kc[k] = pwa::make_kconst(pa, a.theta, nullptr, k, false, a.ev);
+        // the operands' padding columns (and everything else) start at zero
+        uint4* z4 = reinterpret_cast<uint4*>(xop);
+        for (uint32_t i = tid; i < (2 * PBX + 2 * PBZ) / 16; i += NT) z4[i] = make_uint4(0, 0, 0, 0);
+    }
+    pwa::fence_proxy_async();
+    pwa::tc::fence_before();
+    __syncthreads();
+    pwa::tc::fence_after();
+    const uint32_t tm = *tslot;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Cp >> 3) << 17) | ((128u >> 4) << 24);
+    const uint32_t xa = pwa::tc::sa(xop), za = pwa::tc::sa(zop);
+
+    // this thread's Gram entries: row m = 32 (warp mod 4) + lane, columns c0 .. c0 + CPT - 1
+    // (the warps w, w + 4, ... share TMEM lane quarter w mod 4 and split its columns)
+    const int qd = warp & 3, m = 32 * qd + lane, c0 = (warp >> 2) * CPT;
+    const uint32_t tlane = (uint32_t)(32 * qd) << 16;
+    float ax[CPT], az[CPT];
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) ax[j] = az[j] = 0.f;
+    float q[kTcKW][6];
+#pragma unroll
+    for (int j = 0; j < kTcKW; ++j)
+#pragma unroll
+        for (int u = 0; u < 6; ++u) q[j][u] = 0.f;
+    float sc = 0.f;
+
+    double* rec = a.rec + (size_t)blockIdx.x * a.rec_len;
+    const int CC = C * C;
+    const int offQ = 3 * CC, offS = offQ + 12 * K;
+    auto fold = [&](int smp) {
+        double* rx = rec + (smp == 0 ? 0 : 2 * CC);
+        double* rz = rec + CC;
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+            const int c = c0 + j;
+            if (m < C && c < C) {
+                rx[m * C + c] += (double)ax[j];
+                if (smp == 0) rz[m * C + c] += (double)az[j];
+            }
+            ax[j] = az[j] = 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < kTcKW; ++j) {
+            const int k = warp + j * NW;
+#pragma unroll
+            for (int u = 0; u < 6; ++u) {
+                const float v = pwa::warp_sum(q[j][u]);
+                q[j][u] = 0.f;
+                if (lane == 0 && k < K) rec[offQ + ((size_t)smp * K + k) * 6 + u] += (double)v;
+            }
+        }
+        const float v = pwa::warp_sum(sc);
+        sc = 0.f;
+        if (lane == 0) rec[offS + 2 * warp + smp] += (double)v;
+    };
+
+    int st = 0;
+    uint32_t ph = 0, mph = 0;
+    int n_mma = 0;  // commits issued on mbar[2]
+    int win = 0;
+    int cur_smp = 0;
+    long long i = 0;
+    for (long long t = blockIdx.x; t < T; t += G, ++i) {
+        int smp;
+        long long lt;
+        tile_src(t, smp, lt);
+        if (smp != cur_smp) {
+            fold(0);
+            win = 0;
+            cur_smp = smp;
+        }
+        const bool ok = pwa::mbar_wait(&mbar[st], ph, a.timeout_cycles);
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) s_abort = 1;
+            break;
+        }
+        const float* Ft = reinterpret_cast<const float*>(stages + (size_t)st * a.stage_bytes);
+        const float* m2s = Ft + (size_t)2 * K * S * kE;
+        const long long e_base = lt * kE;
+        const int e = lane;
+        const bool valid = e < (int)min((long long)kE, a.nev[smp] - e_base);
+
+        // ---- event phase (as hess_kernel) ----
+        float br[kTcKW], bim[kTcKW], fr[kTcKW][S], fi[kTcKW][S];
+        float Ar[S], Ai[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) Ar[s] = Ai[s] = 0.f;
+#pragma unroll
+        for (int j = 0; j < kTcKW; ++j) {
+            const int k = warp + j * NW;
+            br[j] = bim[j] = 0.f;
+#pragma unroll
+            for (int s = 0; s < S; ++s) fr[j][s] = fi[j][s] = 0.f;
+            if (k < K) {
+                const KConst c = kc[k];
+                pwa::breit_wigner(c, m2s[c.ch * kE + e], br[j], bim[j]);
+                const float cr = c.gre * br[j] - c.gim * bim[j], ci = c.gre * bim[j] + c.gim * br[j];
+                const int p = (e + c.shift) & (kE - 1);
+                if constexpr (S % 2 == 0) {
+#pragma unroll
+                    for (int qq = 0; qq < S / 2; ++qq) {
+                        const float4 f4 = *reinterpret_cast<const float4*>(Ft + 4 * ((k * (S / 2) + qq) * kE + p));
+                        fr[j][2 * qq] = f4.x;
+                        fr[j][2 * qq + 1] = f4.y;
+                        fi[j][2 * qq] = f4.z;
+                        fi[j][2 * qq + 1] = f4.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+                        const float2 f2 = *reinterpret_cast<const float2*>(Ft + 2 * ((k * S + s) * kE + p));
+                        fr[j][s] = f2.x;
+                        fi[j][s] = f2.y;
+                    }
+                }
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    Ar[s] += cr * fr[j][s] - ci * fi[j][s];
+                    Ai[s] += cr * fi[j][s] + ci * fr[j][s];
+                }
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            PA[(warp * 2 * S + 2 * s) * 32 + e] = Ar[s];
+            PA[(warp * 2 * S + 2 * s + 1) * 32 + e] = Ai[s];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            float xr = 0.f, xi = 0.f;
+            for (int w = 0; w < NW; ++w) {
+                xr += PA[(w * 2 * S + 2 * s) * 32 + e];
+                xi += PA[(w * 2 * S + 2 * s + 1) * 32 + e];
+            }
+            Ar[s] = xr;
+            Ai[s] = xi;
+        }
+        float I = 0.f;
+#pragma unroll
+        for (int s = 0; s < S; ++s) I += Ar[s] * Ar[s] + Ai[s] * Ai[s];
+        float aw = 0.f, sqa = 0.f, zw = 0.f;
+        if (smp == 0) {
+            const float w = m2s[3 * kE + e];
+            const bool good = I > 0.f && I < INFINITY;
+            if (valid && good) {
+                aw = w / I;
+                sqa = sqrtf(aw);
+                zw = sqrtf(w) / I;
+                if (warp == 0) sc += w * logf(I);
+            } else if (valid && warp == 0) {
+                atomicMin(a.bad, (unsigned long long)(e_base + e));
+                atomicOr(a.err, pwa::ERR_NONFINITE);
+            }
+        } else {
+            const bool good = I < INFINITY;
+            if (valid && good) {
+                aw = 1.f;
+                sqa = 1.f;
+                if (warp == 0) sc += I;
+            } else if (valid && warp == 0) {
+                atomicMin(a.bad, (unsigned long long)(a.nev[0] + e_base + e));
+                atomicOr(a.err, pwa::ERR_NONFINITE);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kTcKW; ++j) {
+            const int k = warp + j * NW;
+            if (k >= K) continue;
+            const float b1r = br[j], b1i = bim[j];
+            const float b2r = b1r * b1r - b1i * b1i, b2i = 2.f * b1r * b1i;
+            const float b3r = b2r * b1r - b2i * b1i, b3i = b2r * b1i + b2i * b1r;
+            float Dr = 0.f, Di = 0.f;
+            const int c1 = 2 * k, c2 = 2 * (K + k);  // columns of Re (B F), Re (B^2 F); Im at + 1
+            // the event's S rows are consecutive (row e S + s): one store per column and part for even S
+            float v[4][S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                Dr += Ar[s] * fr[j][s] + Ai[s] * fi[j][s];
+                Di += Ar[s] * fi[j][s] - Ai[s] * fr[j][s];
+                v[0][s] = sqa * (b1r * fr[j][s] - b1i * fi[j][s]);
+                v[1][s] = sqa * (b1r * fi[j][s] + b1i * fr[j][s]);
+                v[2][s] = sqa * (b2r * fr[j][s] - b2i * fi[j][s]);
+                v[3][s] = sqa * (b2r * fi[j][s] + b2i * fr[j][s]);
+            }
+            const int cols[4] = {c1, c1 + 1, c2, c2 + 1};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) store_rows<S>(xop, PBX, tc_off(cols[u], e * S, SBOX), v[u]);
+            const float z1r = b1r * Dr - b1i * Di, z1i = b1r * Di + b1i * Dr;
+            const float z2r = b2r * Dr - b2i * Di, z2i = b2r * Di + b2i * Dr;
+            const float z3r = b3r * Dr - b3i * Di, z3i = b3r * Di + b3i * Dr;
+            if (smp == 0) {
+                store_split(zop, PBZ, tc_off(c1, e, SBOZ), zw * z1r);
+                store_split(zop, PBZ, tc_off(c1 + 1, e, SBOZ), zw * z1i);
+                store_split(zop, PBZ, tc_off(c2, e, SBOZ), zw * z2r);
+                store_split(zop, PBZ, tc_off(c2 + 1, e, SBOZ), zw * z2i);
+            }
+            q[j][0] = fmaf(aw, z1r, q[j][0]);
+            q[j][1] = fmaf(aw, z1i, q[j][1]);
+            q[j][2] = fmaf(aw, z2r, q[j][2]);
+            q[j][3] = fmaf(aw, z2i, q[j][3]);
+            q[j][4] = fmaf(aw, z3r, q[j][4]);
+            q[j][5] = fmaf(aw, z3i, q[j][5]);
+        }
+        // the operands are complete (generic writes, read by the tensor cores' async proxy)
+        pwa::fence_proxy_async();
+        pwa::tc::fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            const long long tn = t + 2LL * G;
+            if (tn < T) {
+                int s2;
+                long long lt2;
+                tile_src(tn, s2, lt2);
+                issued[st] = i + 2;
+                pwa::tma_load_tile(stages + (size_t)st * a.stage_bytes, a.tiles[s2] + (size_t)lt2 * a.tile_bytes[s2],
+                                   a.tile_bytes[s2], &mbar[st]);
+            }
+            pwa::tc::fence_after();
+            // D = X^T X over the tile's rows: per 16 rows hi hi, hi lo, lo hi
+#pragma unroll 1
+            for (int ks = 0; ks < R / 16; ++ks) {
+                const uint64_t dh = pwa::tc::sdesc(xa + ks * 2 * kTcLbo, kTcLbo, SBOX);
+                const uint64_t dl = pwa::tc::sdesc(xa + PBX + ks * 2 * kTcLbo, kTcLbo, SBOX);
+                pwa::tc::mma_bf16(tm, dh, dh, idesc, ks > 0);
+                pwa::tc::mma_bf16(tm, dh, dl, idesc, 1);
+                pwa::tc::mma_bf16(tm, dl, dh, idesc, 1);
+            }
+            if (smp == 0) {
+#pragma unroll 1
+                for (int ks = 0; ks < 2; ++ks) {
+                    const uint64_t dh = pwa::tc::sdesc(za + ks * 2 * kTcLbo, kTcLbo, SBOZ);
+                    const uint64_t dl = pwa::tc::sdesc(za + PBZ + ks * 2 * kTcLbo, kTcLbo, SBOZ);
+                    pwa::tc::mma_bf16(tm + 128, dh, dh, idesc, ks > 0);
+                    pwa::tc::mma_bf16(tm + 128, dh, dl, idesc, 1);
+                    pwa::tc::mma_bf16(tm + 128, dl, dh, idesc, 1);
+                }
+            }
+            pwa::tc::mma_commit(&mbar[2]);
+        }
+        ++n_mma;
+        // ---- the tile's Gram sums from TMEM into registers ----
+        const bool done = pwa::mbar_wait(&mbar[2], mph, a.timeout_cycles);
+        mph ^= 1u;
+        if (!__syncthreads_and(done)) {
+            if (tid == 0) s_abort = 1;
+            break;
+        }
+        pwa::tc::fence_after();
+        // this thread's columns in 4-column loads, all in flight before one wait
+        {
+            uint32_t v[CPT / 4][4];
+#pragma unroll
+            for (int ch = 0; ch < CPT / 4; ++ch) tmem_ld4(tm + tlane + c0 + 4 * ch, v[ch]);
+            pwa::tc::tmem_wait();
+#pragma unroll
+            for (int ch = 0; ch < CPT / 4; ++ch)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) ax[4 * ch + u] += __uint_as_float(v[ch][u]);
+        }
+        if (smp == 0) {
+            uint32_t v[CPT / 4][4];
+#pragma unroll
+            for (int ch = 0; ch < CPT / 4; ++ch) tmem_ld4(tm + 128 + tlane + c0 + 4 * ch, v[ch]);
+            pwa::tc::tmem_wait();
+#pragma unroll
+            for (int ch = 0; ch < CPT / 4; ++ch)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) az[4 * ch + u] += __uint_as_float(v[ch][u]);
+        }
+        if (++win == kFold) {
+            fold(smp);
+            win = 0;
+        }
+        if (++st == 2) {
+            st = 0;
+            ph ^= 1u;
+        }
+        pwa::tc::fence_before();
+        __syncthreads();  // TMEM read and operands consumed before the next tile rewrites them
+    }
+    if (s_abort) {
+        // a copy or the tile's MMAs never completed: report it, wait (bounded)
+        // for what is still in flight, free TMEM
+        if (tid == 0) {
+            atomicOr(a.err, pwa::ERR_TIMEOUT);
+            for (int s = 0; s < 2; ++s)
+                if (issued[s] >= 0) (void)pwa::mbar_wait(&mbar[s], (uint32_t)((issued[s] / 2) & 1), a.timeout_cycles);
+            if (n_mma > 0) (void)pwa::mbar_wait(&mbar[2], (uint32_t)((n_mma - 1) & 1), a.timeout_cycles);
+        }
+    } else {
+        fold(cur_smp);
+    }
+    pwa::tc::fence_before();
+    __syncthreads();
+    pwa::tc::fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kTcTmemCols));
+}
+
 // Fixed-order sum of the per-CTA records.
 __global__ void hess_reduce_kernel(const double* __restrict__ rec, int grid, int rec_len, double* __restrict__ out)
 {
@@ -477,17 +928,52 @@ KernelH pick_hess(int S, int NT)
     }
 }
 
+template <int S>
+KernelH pick_tc_s(int nch)
+{
+    switch (nch) {
+        case 1: return hess_tc_kernel<S, 1>;
+        case 2: return hess_tc_kernel<S, 2>;
+        case 3: return hess_tc_kernel<S, 3>;
+        case 4: return hess_tc_kernel<S, 4>;
+        case 5: return hess_tc_kernel<S, 5>;
+        case 6: return hess_tc_kernel<S, 6>;
+        case 7: return hess_tc_kernel<S, 7>;
+        case 8: return hess_tc_kernel<S, 8>;
+        default: return nullptr;
+    }
+}
+
+KernelH pick_tc(int S, int K)
+{
+    const int nch = (4 * K + 15) / 16;
+    switch (S) {
+        case 1: return pick_tc_s<1>(nch);
+        case 2: return pick_tc_s<2>(nch);
+        case 3: return pick_tc_s<3>(nch);
+        case 4: return pick_tc_s<4>(nch);
+        default: return nullptr;
+    }
+}
+
 using cplx = std::complex<double>;
 
 // Combine the summed records into NLL, gradient and Hessian in the free
 // parameters (FP64, host).
-void combine(const pwa_handle* h, const double* theta, const double* sum, int NW, double* nll, double* grad,
-             double* hess)
+void combine(const pwa_handle* h, const double* theta, const double* sum, int NW, bool tc, double* nll,
+             double* grad, double* hess)
 {
     const int K = h->K, P = h->P, nb = K * (K + 1) / 2, C = 4 * K;
-    // full symmetric 4K x 4K Gram matrices from the upper-triangle blocks
+    // full symmetric 4K x 4K Gram matrices: from the upper-triangle blocks of
+    // hess_kernel, or symmetrised from the full matrices of hess_tc_kernel
     auto gram = [&](int off) {
         std::vector<double> Gm((size_t)C * C);
+        if (tc) {
+            const double* x = sum + (size_t)off;
+            for (int i = 0; i < C; ++i)
+                for (int j = 0; j < C; ++j) Gm[(size_t)i * C + j] = 0.5 * (x[(size_t)i * C + j] + x[(size_t)j * C + i]);
+            return Gm;
+        }
         for (int b = 0; b < nb; ++b) {
             int bi, bj;
             block_of(b, K, bi, bj);
@@ -501,14 +987,15 @@ void combine(const pwa_handle* h, const double* theta, const double* sum, int NW
         }
         return Gm;
     };
-    const std::vector<double> RD = gram(0), ZD = gram(16 * nb), RM = gram(32 * nb);
+    const int CC = C * C;
+    const std::vector<double> RD = gram(0), ZD = gram(tc ? CC : 16 * nb), RM = gram(tc ? 2 * CC : 32 * nb);
     // C[c][c'] = sum a sum_s conj(V_c) V_c', c = p K + k
     auto cgram = [&](const std::vector<double>& R, int c, int cp) {
         const double* r0 = R.data() + (size_t)(2 * c) * C;
         const double* r1 = R.data() + (size_t)(2 * c + 1) * C;
         return cplx(r0[2 * cp] + r1[2 * cp + 1], r0[2 * cp + 1] - r1[2 * cp]);
     };
-    const int offQ = 48 * nb, offS = offQ + 12 * K;
+    const int offQ = tc ? 3 * CC : 48 * nb, offS = offQ + 12 * K;
     std::vector<cplx> Q[2][3];
     for (int smp = 0; smp < 2; ++smp)
         for (int pp = 0; pp < 3; ++pp) Q[smp][pp].assign(K, cplx(0, 0));
@@ -620,16 +1107,18 @@ pwa_status hessian_device(pwa_handle* h, const double* theta, double* nll, doubl
         return set_error(h, PWA_EINVAL, "the Hessian pass supports K <= " + std::to_string(kMaxKHess));
     if (h->broken) return set_error(h, PWA_ETIMEOUT, "handle is unusable after a device-side timeout");
     const int nblk = K * (K + 1) / 2;
-    const int NT = nblk <= 256 ? 256 : 512;
+    // the tensor-core Gram for K <= 32 (unless the CUDA-core kernel is asked for), else the CUDA-core one
+    const bool tc = K <= kMaxKTensor && !h->hess_cuda_cores;
+    const int NT = tc ? kTcNT : (nblk <= 256 ? 256 : 512);
     const int NW = NT / 32;
-    KernelH fn = pick_hess(S, NT);
+    KernelH fn = tc ? pick_tc(S, K) : pick_hess(S, NT);
     if (!fn) return set_error(h, PWA_EINVAL, "no Hessian kernel for this S");
     const Tiling& t = h->tiling;
     const uint32_t stage = (uint32_t)((std::max(h->tile_bytes[0], h->tile_bytes[1]) + 127) / 128 * 128);
     const int C = 4 * K;
-    const int NWp = NT / 32;
-    const size_t smem = 2 * (size_t)stage + sizeof(KConst) * K +
-                        sizeof(float) * ((size_t)C * (x_stride(S) + kZStride) + (size_t)NWp * 2 * S * 32) + 16;
+    const size_t smem = tc ? hess_tc_smem(K, S, stage)
+                           : 2 * (size_t)stage + sizeof(KConst) * K +
+                                 sizeof(float) * ((size_t)C * (x_stride(S) + kZStride) + (size_t)NW * 2 * S * 32) + 16;
     HessState& hs = h->hess;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -655,7 +1144,7 @@ pwa_status hessian_device(pwa_handle* h, const double* theta, double* nll, doubl
         if (occ < 1) return set_error(h, PWA_EINVAL, "the Hessian pass does not fit on an SM");
         const long long T = (long long)h->ntiles[0] + h->ntiles[1];
         const int grid = (int)std::max(1LL, std::min((long long)h->num_sms * occ, T));
-        const int rec_len = hess_rec_len(K, nblk, NW);
+        const int rec_len = tc ? hess_tc_rec_len(K) : hess_rec_len(K, nblk, NW);
         const size_t need = sizeof(double) * ((size_t)grid * rec_len + rec_len);
         if (need > hs.cap_bytes) {
             if (hs.d_rec) cudaFree(hs.d_rec);
@@ -722,7 +1211,7 @@ pwa_status hessian_device(pwa_handle* h, const double* theta, double* nll, doubl
         if (st != PWA_OK) return st;
     }
     double f = 0.0;
-    combine(h, theta, hs.h_sum, NW, &f, grad, hess);
+    combine(h, theta, hs.h_sum, NW, tc, &f, grad, hess);
     if (nll) *nll = f;
     return PWA_OK;
 }
@@ -735,6 +1224,14 @@ void free_hessian(pwa_handle* h)
 }
 
 }  // namespace pwa
+
+extern "C" pwa_status pwa_set_hessian_cuda_cores(pwa_handle* h, int cuda_cores)
+{
+    if (!h) return PWA_EINVAL;
+    h->err.clear();
+    h->hess_cuda_cores = cuda_cores != 0;
+    return PWA_OK;
+}
 
 extern "C" pwa_status pwa_hessian(pwa_handle* h, const double* theta, double* nll, double* grad, double* hess)
 {

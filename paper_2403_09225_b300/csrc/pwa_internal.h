@@ -102,6 +102,7 @@ struct pwa_handle {
     long long timeout_cycles = 0;
     bool broken = false;
     bool released = false;  // d_F, d_m2, d_w freed (pwa_release_event_copies)
+    bool hess_cuda_cores = false;  // the Hessian pass's Gram matrices on the CUDA cores even for K <= 32
     std::string err;
 };
 

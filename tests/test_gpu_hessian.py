@@ -74,6 +74,24 @@ def test_hessian_k40_fixed_parameters_and_tilings():
     L.close()
 
 
+@pytest.mark.parametrize("K,S", [(30, 3), (28, 4), (25, 2)])
+def test_hessian_tensor_core_path_above_k24(K, S):
+    """K = 25..32 on the tensor-core path (every event-phase warp owns up to
+    four resonances), against the oracle, and against the CUDA-core path."""
+    from paper_2403_09225_b300 import binding
+    cfg = W.Config("k%ds%d" % (K, S), K, S, 0, 0, 4, False, 40 + K)
+    wl = W.make_workload(cfg, intensity=None, n_data=1500 + K, n_mc=4000 + 3 * K)
+    model = oracle.Model.from_table(wl.table, S)
+    L = binding.make_likelihood(wl)
+    th = W.random_starts(wl, 1)[0]
+    _check(L, model, wl, th)
+    _, _, H = L.hessian(th)
+    L.set_hessian_cuda_cores(True)
+    _, _, Hc = L.hessian(th)
+    assert relmax(H, Hc) <= TOL_HVP, relmax(H, Hc)
+    L.close()
+
+
 def test_hessian_is_reproducible_and_refuses_large_k():
     from paper_2403_09225_b300 import binding
     wl, model = small_workload("paper", 1500 + 3, 6000 + 29)
