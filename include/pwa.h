@@ -220,6 +220,17 @@ pwa_status pwa_hvp(pwa_handle* h, const double* theta, const double* v, double* 
  * PWA_ECUDA, PWA_ENONFINITE, PWA_ETIMEOUT. */
 pwa_status pwa_hessian(pwa_handle* h, const double* theta, double* nll, double* grad, double* hess);
 
+/* pwa_hessian for B parameter vectors in one launch (Eq. 7 as above, for
+ * each vector): the vectors share one wave of CTAs, each CTA working for one
+ * vector on its share of the tiles.  theta: host [B][P]; nll: host [B] or
+ * NULL; grad: host [B][P] or NULL; hess: host [B][P][P].  status: host [B]
+ * or NULL; when given, a vector with a non-finite intensity gets
+ * PWA_ENONFINITE there (its outputs are left untouched) and the others are
+ * still combined; when NULL such a vector fails the call.  Errors as
+ * pwa_hessian, plus PWA_EINVAL for B < 1. */
+pwa_status pwa_hessian_batch(pwa_handle* h, int B, const double* theta, double* nll, double* grad, double* hess,
+                             pwa_status* status);
+
 /* Run the Hessian pass's Gram matrices on the CUDA cores (cuda_cores = 1)
  * even where the tensor-core kernel applies (K <= 32), for comparisons;
  * 0 restores the default. */

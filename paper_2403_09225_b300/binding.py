@@ -86,6 +86,7 @@ class PwaError(RuntimeError):
 
 #: every symbol include/pwa.h declares
 EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "pwa_grad", "pwa_hvp", "pwa_hessian",
+           "pwa_hessian_batch",
            "pwa_hvp_reuse", "pwa_hvp_reuse_device", "pwa_eval_multi_device", "pwa_set_hessian_cuda_cores",
            "pwa_release_event_copies",
            "pwa_device_bytes",
@@ -120,6 +121,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pwa_hvp": (st, [H, dp, dp, dp]),
         "pwa_eval": (st, [H, dp, dp, dp, dp, dp]),
         "pwa_hessian": (st, [H, dp, dp, dp, dp]),
+        "pwa_hessian_batch": (st, [H, i, dp, dp, dp, dp, ip]),
         "pwa_hvp_reuse": (st, [H, dp, dp, dp]),
         "pwa_eval_multi_device": (st, [i, ctypes.POINTER(ctypes.c_void_p), ip, ctypes.POINTER(ctypes.c_void_p),
                                        ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), i, i, vp]),
@@ -333,6 +335,21 @@ class Likelihood:
         H = np.empty((self.P, self.P))
         self._check(lib().pwa_hessian(self._h, _dptr(th), ctypes.byref(f), _dptr(g), _dptr(H)))
         return f.value, g, H
+
+    def hessian_batch(self, thetas):
+        """(NLL [B], gradient [B, P], Hessian [B, P, P], status [B]) of B
+        parameter vectors from one batched Hessian pass; status[b] is
+        PWA_ENONFINITE for a vector with a non-finite intensity (its rows are
+        then not written)."""
+        th = np.ascontiguousarray(np.asarray(thetas, dtype=np.float64).reshape(-1, self.P))
+        B = th.shape[0]
+        f = np.full(B, np.nan)
+        g = np.full((B, self.P), np.nan)
+        H = np.full((B, self.P, self.P), np.nan)
+        stat = np.zeros(B, dtype=np.int32)
+        self._check(lib().pwa_hessian_batch(self._h, B, _dptr(th), _dptr(f), _dptr(g), _dptr(H),
+                                            stat.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return f, g, H, stat
 
     def eval(self, theta, v=None):
         """(NLL, grad, H v) from one fused pass; H v is None when v is None."""

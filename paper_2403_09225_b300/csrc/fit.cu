@@ -907,9 +907,24 @@ struct RoundEvaluator {
     virtual pwa_status reserve(int nb, double** theta, double** v) = 0;
     virtual pwa_status issue(int nb, bool any_hv) = 0;                      // asynchronous
     virtual pwa_status finish(int nb, const double** out, const int** err) = 0;  // waits
-    // the full Hessian at one point (synchronous), where the evaluator has a Hessian pass
+    // full Hessians at nb points [nb][P], where the evaluator has a Hessian
+    // pass: issue enqueues the batched pass, finish waits and writes H
+    // [nb][P][P] and a status per point
     virtual bool has_hessian() const { return false; }
-    virtual pwa_status hessian(const double* theta, double* H) { (void)theta; (void)H; return PWA_EINVAL; }
+    virtual pwa_status hessian_issue(int nb, const double* theta)
+    {
+        (void)nb;
+        (void)theta;
+        return PWA_EINVAL;
+    }
+    virtual pwa_status hessian_finish(int nb, const double* theta, double* H, pwa_status* st)
+    {
+        (void)nb;
+        (void)theta;
+        (void)H;
+        (void)st;
+        return PWA_EINVAL;
+    }
 };
 
 // a likelihood handle: pwa_eval_batch_device's pass on the handle's batch buffers.
@@ -940,11 +955,12 @@ struct HandleRounds final : RoundEvaluator {
     int P() const override { return h->P; }
     pwa_handle* handle() const override { return h; }
     bool has_hessian() const override { return h->K <= pwa::kMaxKHessian; }
-    pwa_status hessian(const double* theta, double* H) override
+    pwa_status hessian_issue(int nb, const double* theta) override { return pwa::hessian_issue(h, nb, theta); }
+    pwa_status hessian_finish(int nb, const double* theta, double* H, pwa_status* st) override
     {
-        pwa_status st = pwa::hessian_device(h, theta, nullptr, nullptr, H);
-        if (st == PWA_ENONFINITE) h->err.clear();
-        return st;
+        pwa_status r = pwa::hessian_finish(h, nb, theta, nullptr, nullptr, H, st);
+        if (r == PWA_OK) h->err.clear();  // a non-finite point is reported in its own status
+        return r;
     }
     pwa_status reserve(int nb, double** theta, double** v) override
     {
@@ -1167,6 +1183,11 @@ struct FitGroup {
     std::vector<FitTask> tasks;
     std::vector<int> live;
     std::vector<double> zero;
+    // the round's Hessian requests: fits, their points [n][P], Hessians [n][P][P], statuses
+    std::vector<int> hrows;
+    std::vector<double> htheta, hH;
+    std::vector<pwa_status> hst;
+    pwa_status hissue = PWA_OK;
 };
 
 pwa_status open_group(FitGroup& g, std::unique_ptr<RoundEvaluator> ev, int B, const double* theta0,
@@ -1196,23 +1217,55 @@ pwa_status open_group(FitGroup& g, std::unique_ptr<RoundEvaluator> ev, int B, co
     return PWA_OK;
 }
 
-// Enqueue the group's round: its unfinished fits' requests as one batched
-// evaluation (H v for all when any asks for it, with v = 0 for the f, g requests).
-// Serve the group's Hessian requests (one Hessian pass each, synchronous;
-// each such fit then runs its CG on the host and posts its next request),
-// then collect the fits that wait for f, g or H v.  Returns whether any of
-// those wants H v.
-bool collect_round(FitGroup& g)
+// Serve the groups' Hessian requests: one batched Hessian pass per group
+// over all of its fits that ask for one, every group's pass enqueued before
+// the first is waited for (so the host's combination and CG for one group
+// overlap the passes of the next); each served fit runs its CG on the host
+// and posts its next request.  Repeats while any fit asks for a Hessian.
+void serve_hessians(const std::vector<FitGroup*>& gs)
 {
-    for (int b = 0; b < g.B; ++b) {
-        FitState& s = g.fits[b];
-        while (!g.tasks[b].h.done() && s.req == Req::HESS) {
-            ++s.n_hess;
-            s.req_status = g.ev->hessian(s.rx, s.rH);
-            g.tasks[b].h.resume();
-            if (g.tasks[b].h.done()) s.elapsed = s.since_start();
+    while (true) {
+        bool any = false;
+        for (FitGroup* g : gs) {
+            g->hrows.clear();
+            for (int b = 0; b < g->B; ++b)
+                if (!g->tasks[b].h.done() && g->fits[b].req == Req::HESS) g->hrows.push_back(b);
+            if (g->hrows.empty()) continue;
+            any = true;
+            const int P = g->P, nb = (int)g->hrows.size();
+            g->htheta.resize((size_t)nb * P);
+            for (int i = 0; i < nb; ++i)
+                std::memcpy(g->htheta.data() + (size_t)i * P, g->fits[g->hrows[i]].rx, sizeof(double) * P);
+            g->hissue = g->ev->hessian_issue(nb, g->htheta.data());
+        }
+        if (!any) return;
+        for (FitGroup* g : gs) {
+            if (g->hrows.empty()) continue;
+            const int P = g->P, nb = (int)g->hrows.size();
+            g->hH.resize((size_t)nb * P * P);
+            g->hst.assign(nb, PWA_OK);
+            pwa_status st = g->hissue;
+            if (st == PWA_OK) st = g->ev->hessian_finish(nb, g->htheta.data(), g->hH.data(), g->hst.data());
+            for (int i = 0; i < nb; ++i) {
+                const int b = g->hrows[i];
+                FitState& s = g->fits[b];
+                ++s.n_hess;
+                s.req_status = st != PWA_OK ? st : g->hst[i];
+                if (s.req_status == PWA_OK)
+                    std::memcpy(s.rH, g->hH.data() + (size_t)i * P * P, sizeof(double) * P * P);
+                g->tasks[b].h.resume();
+                if (g->tasks[b].h.done()) s.elapsed = s.since_start();
+            }
         }
     }
+}
+
+// Enqueue the group's round: its unfinished fits' requests as one batched
+// evaluation (H v for all when any asks for it, with v = 0 for the f, g requests).
+// Collects the fits that wait for f, g or H v (the Hessian requests are
+// served before, by serve_hessians).  Returns whether any of those wants H v.
+bool collect_round(FitGroup& g)
+{
     g.live.clear();
     for (int b = 0; b < g.B; ++b)
         if (!g.tasks[b].h.done()) g.live.push_back(b);
@@ -1274,7 +1327,10 @@ pwa_status finish_round(FitGroup& g)
 
 pwa_status run_lockstep(std::vector<std::unique_ptr<FitGroup>>& groups)
 {
+    std::vector<FitGroup*> all;
+    for (auto& g : groups) all.push_back(g.get());
     while (true) {
+        serve_hessians(all);
         bool any = false;
         for (auto& g : groups) {
             pwa_status st = issue_round(*g);
@@ -1420,7 +1476,10 @@ struct MultiRounds {
             stream = nullptr;
             return pwa::set_error(hr(0)->h, PWA_ECUDA, "cannot create the multi-round stream");
         }
+        std::vector<FitGroup*> all;
+        for (auto& g : groups) all.push_back(g.get());
         while (true) {
+            serve_hessians(all);
             bool any_hv = false;
             std::vector<int> gs;
             for (int i = 0; i < (int)groups.size(); ++i) {

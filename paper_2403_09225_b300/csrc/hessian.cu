@@ -65,12 +65,17 @@ struct HessArgs {
     int ev;                // events per warp of the tiling the records were laid out for
     uint32_t stage_bytes;  // shared bytes per stage (16-byte multiple >= both tile records)
     const pwa::ResParam* res;
-    const double* theta;   // device [P]
+    const double* theta;   // device [B][P]
+    int P;
+    // B parameter vectors per launch: CTA c works for vector c mod B and is CTA
+    // c / B of the Gb that share that vector's tiles (tiles gb, gb + Gb, ...)
+    int B, Gb;
     int nblk;              // 4 x 4 blocks in the upper triangle of the 4K x 4K Gram: K (K + 1) / 2
-    double* rec;           // [grid][rec_len] per-CTA FP64 sums (zeroed before the launch)
+    double* rec;           // [B Gb][rec_len] per-CTA FP64 sums (zeroed before the launch)
     int rec_len;
     unsigned long long* bad;
     int* err;
+    int* err_vec;          // [B] per-vector error words (zeroed before the launch)
     long long timeout_cycles;
 };
 
@@ -126,7 +131,7 @@ __global__ void __launch_bounds__(NT, 1) hess_kernel(const HessArgs a)
     __shared__ long long issued[2];
     __shared__ int s_abort;
 
-    const int G = gridDim.x;
+    const int bt = (int)(blockIdx.x % (unsigned)a.B), gb = (int)(blockIdx.x / (unsigned)a.B), G = a.Gb;
     const long long T = (long long)a.ntiles[0] + a.ntiles[1];
     auto tile_src = [&](long long t, int& smp, long long& lt) {
         smp = t < a.ntiles[0] ? 0 : 1;
@@ -140,7 +145,7 @@ __global__ void __launch_bounds__(NT, 1) hess_kernel(const HessArgs a)
         }
         pwa::fence_mbar_init();
         for (int i = 0; i < 2; ++i) {
-            const long long t = blockIdx.x + (long long)i * G;
+            const long long t = gb + (long long)i * G;
             if (t < T) {
                 int smp;
                 long long lt;
@@ -154,7 +159,7 @@ __global__ void __launch_bounds__(NT, 1) hess_kernel(const HessArgs a)
     {
         pwa::PassArgs pa;
         pa.res = a.res;
-        for (int k = tid; k < K; k += NT) kc[k] = pwa::make_kconst(pa, a.theta, nullptr, k, false, a.ev);
+        for (int k = tid; k < K; k += NT) kc[k] = pwa::make_kconst(pa, a.theta + (size_t)bt * a.P, nullptr, k, false, a.ev);
     }
     __syncthreads();
 
@@ -218,7 +223,7 @@ __global__ void __launch_bounds__(NT, 1) hess_kernel(const HessArgs a)
     int win = 0;
     int cur_smp = 0;
     long long i = 0;
-    for (long long t = blockIdx.x; t < T; t += G, ++i) {
+    for (long long t = gb; t < T; t += G, ++i) {
         int smp;
         long long lt;
         tile_src(t, smp, lt);
@@ -311,6 +316,7 @@ __global__ void __launch_bounds__(NT, 1) hess_kernel(const HessArgs a)
             } else if (valid && warp == 0) {
                 atomicMin(a.bad, (unsigned long long)(e_base + e));
                 atomicOr(a.err, pwa::ERR_NONFINITE);
+                atomicOr(a.err_vec + bt, pwa::ERR_NONFINITE);
             }
         } else {
             const bool good = I < INFINITY;
@@ -321,6 +327,7 @@ __global__ void __launch_bounds__(NT, 1) hess_kernel(const HessArgs a)
             } else if (valid && warp == 0) {
                 atomicMin(a.bad, (unsigned long long)(a.nev[0] + e_base + e));
                 atomicOr(a.err, pwa::ERR_NONFINITE);
+                atomicOr(a.err_vec + bt, pwa::ERR_NONFINITE);
             }
         }
         // ---- phase 1c: the warp's columns of X and z for this event, its Q sums ----
@@ -567,7 +574,7 @@ __global__ void __launch_bounds__(kTcNT, 1) hess_tc_kernel(const HessArgs a)
     __shared__ long long issued[2];
     __shared__ int s_abort;
 
-    const int G = gridDim.x;
+    const int bt = (int)(blockIdx.x % (unsigned)a.B), gb = (int)(blockIdx.x / (unsigned)a.B), G = a.Gb;
     const long long T = (long long)a.ntiles[0] + a.ntiles[1];
     auto tile_src = [&](long long t, int& smp, long long& lt) {
         smp = t < a.ntiles[0] ? 0 : 1;
@@ -579,7 +586,7 @@ __global__ void __launch_bounds__(kTcNT, 1) hess_tc_kernel(const HessArgs a)
         issued[0] = issued[1] = -1;
         pwa::fence_mbar_init();
         for (int i = 0; i < 2; ++i) {
-            const long long t = blockIdx.x + (long long)i * G;
+            const long long t = gb + (long long)i * G;
             if (t < T) {
                 int smp;
                 long long lt;
@@ -598,7 +605,7 @@ __global__ void __launch_bounds__(kTcNT, 1) hess_tc_kernel(const HessArgs a)
     {
         pwa::PassArgs pa;
         pa.res = a.res;
-        for (int k = tid; k < K; k += NT) kc[k] = pwa::make_kconst(pa, a.theta, nullptr, k, false, a.ev);
+        for (int k = tid; k < K; k += NT) kc[k] = pwa::make_kconst(pa, a.theta + (size_t)bt * a.P, nullptr, k, false, a.ev);
         // the operands' padding columns (and everything else) start at zero
         uint4* z4 = reinterpret_cast<uint4*>(xop);
         for (uint32_t i = tid; i < (2 * PBX + 2 * PBZ) / 16; i += NT) z4[i] = make_uint4(0, 0, 0, 0);
@@ -661,7 +668,7 @@ __global__ void __launch_bounds__(kTcNT, 1) hess_tc_kernel(const HessArgs a)
     int win = 0;
     int cur_smp = 0;
     long long i = 0;
-    for (long long t = blockIdx.x; t < T; t += G, ++i) {
+    for (long long t = gb; t < T; t += G, ++i) {
         int smp;
         long long lt;
         tile_src(t, smp, lt);
@@ -752,6 +759,7 @@ __global__ void __launch_bounds__(kTcNT, 1) hess_tc_kernel(const HessArgs a)
             } else if (valid && warp == 0) {
                 atomicMin(a.bad, (unsigned long long)(e_base + e));
                 atomicOr(a.err, pwa::ERR_NONFINITE);
+                atomicOr(a.err_vec + bt, pwa::ERR_NONFINITE);
             }
         } else {
             const bool good = I < INFINITY;
@@ -762,6 +770,7 @@ __global__ void __launch_bounds__(kTcNT, 1) hess_tc_kernel(const HessArgs a)
             } else if (valid && warp == 0) {
                 atomicMin(a.bad, (unsigned long long)(a.nev[0] + e_base + e));
                 atomicOr(a.err, pwa::ERR_NONFINITE);
+                atomicOr(a.err_vec + bt, pwa::ERR_NONFINITE);
             }
         }
 #pragma unroll
@@ -899,13 +908,17 @@ __global__ void __launch_bounds__(kTcNT, 1) hess_tc_kernel(const HessArgs a)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kTcTmemCols));
 }
 
-// Fixed-order sum of the per-CTA records.
-__global__ void hess_reduce_kernel(const double* __restrict__ rec, int grid, int rec_len, double* __restrict__ out)
+// Fixed-order sum of the per-CTA records of each vector: out[bt] = sum over
+// gb of the record of CTA gb B + bt.
+__global__ void hess_reduce_kernel(const double* __restrict__ rec, int B, int Gb, int rec_len,
+                                   double* __restrict__ out)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rec_len; i += gridDim.x * blockDim.x) {
+    const long long n = (long long)B * rec_len;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+        const int bt = (int)(j / rec_len), i = (int)(j % rec_len);
         double s = 0.0;
-        for (int b = 0; b < grid; ++b) s += rec[(size_t)b * rec_len + i];
-        out[i] = s;
+        for (int g = 0; g < Gb; ++g) s += rec[((size_t)g * B + bt) * rec_len + i];
+        out[j] = s;
     }
 }
 
@@ -1100,12 +1113,16 @@ void combine(const pwa_handle* h, const double* theta, const double* sum, int NW
 
 namespace pwa {
 
-pwa_status hessian_device(pwa_handle* h, const double* theta, double* nll, double* grad, double* hess)
+// Enqueue the Hessian pass of B parameter vectors (host theta [B][P]) on the
+// handle's stream: theta upload, the pass, the per-vector reduction and the
+// download of the sums and error words.  hessian_finish waits and combines.
+pwa_status hessian_issue(pwa_handle* h, int B, const double* theta)
 {
-    const int K = h->K, S = h->S;
+    const int K = h->K, S = h->S, P = h->P;
     if (K > kMaxKHess)
         return set_error(h, PWA_EINVAL, "the Hessian pass supports K <= " + std::to_string(kMaxKHess));
     if (h->broken) return set_error(h, PWA_ETIMEOUT, "handle is unusable after a device-side timeout");
+    if (B < 1) return set_error(h, PWA_EINVAL, "B must be at least 1");
     const int nblk = K * (K + 1) / 2;
     // the tensor-core Gram for K <= 32 (unless the CUDA-core kernel is asked for), else the CUDA-core one
     const bool tc = K <= kMaxKTensor && !h->hess_cuda_cores;
@@ -1120,12 +1137,11 @@ pwa_status hessian_device(pwa_handle* h, const double* theta, double* nll, doubl
                            : 2 * (size_t)stage + sizeof(KConst) * K +
                                  sizeof(float) * ((size_t)C * (x_stride(S) + kZStride) + (size_t)NW * 2 * S * 32) + 16;
     HessState& hs = h->hess;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_error(h, e, "cudaGetDevice");
+    cudaError_t e = cudaSuccess;
     if (hs.fn != reinterpret_cast<const void*>(fn) || hs.smem != smem) {
-        int max_optin = 0;
-        e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        int dev = 0, max_optin = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (e != cudaSuccess) return cuda_error(h, e, "cudaDeviceGetAttribute");
         cudaFuncAttributes fa;
         e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(fn));
@@ -1142,30 +1158,35 @@ pwa_status hessian_device(pwa_handle* h, const double* theta, double* nll, doubl
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reinterpret_cast<const void*>(fn), NT, smem);
         if (e != cudaSuccess) return cuda_error(h, e, "occupancy");
         if (occ < 1) return set_error(h, PWA_EINVAL, "the Hessian pass does not fit on an SM");
-        const long long T = (long long)h->ntiles[0] + h->ntiles[1];
-        const int grid = (int)std::max(1LL, std::min((long long)h->num_sms * occ, T));
-        const int rec_len = tc ? hess_tc_rec_len(K) : hess_rec_len(K, nblk, NW);
-        const size_t need = sizeof(double) * ((size_t)grid * rec_len + rec_len);
-        if (need > hs.cap_bytes) {
-            if (hs.d_rec) cudaFree(hs.d_rec);
-            if (hs.h_sum) cudaFreeHost(hs.h_sum);
-            hs.d_rec = nullptr;
-            hs.h_sum = nullptr;
-            hs.cap_bytes = 0;
-            if (cudaMalloc(reinterpret_cast<void**>(&hs.d_rec), need) != cudaSuccess) {
-                cudaGetLastError();
-                return set_error(h, PWA_ENOMEM, "cudaMalloc failed for the Hessian records");
-            }
-            if (cudaMallocHost(reinterpret_cast<void**>(&hs.h_sum), sizeof(double) * rec_len) != cudaSuccess) {
-                cudaGetLastError();
-                return set_error(h, PWA_ENOMEM, "pinned allocation failed for the Hessian sums");
-            }
-            hs.cap_bytes = need;
-        }
         hs.fn = reinterpret_cast<const void*>(fn);
         hs.smem = smem;
-        hs.grid = grid;
-        hs.rec_len = rec_len;
+        hs.resident = h->num_sms * occ;
+        hs.rec_len = tc ? hess_tc_rec_len(K) : hess_rec_len(K, nblk, NW);
+    }
+    // CTAs per vector: the vectors share one wave of resident CTAs (at least one each)
+    const long long T = (long long)h->ntiles[0] + h->ntiles[1];
+    const int Gb = (int)std::max(1LL, std::min((long long)std::max(1, hs.resident / B), T));
+    const size_t rl = (size_t)hs.rec_len;
+    const size_t need = sizeof(double) * ((size_t)B * Gb * rl + (size_t)B * rl + (size_t)B * P) + sizeof(int) * B;
+    const size_t need_h = sizeof(double) * ((size_t)B * rl + (size_t)B * P) + sizeof(int) * B;
+    if (need > hs.cap_bytes || need_h > hs.cap_host) {
+        if (hs.d_rec) cudaFree(hs.d_rec);
+        if (hs.h_buf) cudaFreeHost(hs.h_buf);
+        hs.d_rec = nullptr;
+        hs.h_buf = nullptr;
+        hs.cap_bytes = hs.cap_host = 0;
+        if (cudaMalloc(reinterpret_cast<void**>(&hs.d_rec), need) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(h, PWA_ENOMEM, "cudaMalloc failed for the Hessian records");
+        }
+        if (cudaMallocHost(reinterpret_cast<void**>(&hs.h_buf), need_h) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(hs.d_rec);
+            hs.d_rec = nullptr;
+            return set_error(h, PWA_ENOMEM, "pinned allocation failed for the Hessian sums");
+        }
+        hs.cap_bytes = need;
+        hs.cap_host = need_h;
     }
     HessArgs a;
     for (int s = 0; s < 2; ++s) {
@@ -1176,50 +1197,96 @@ pwa_status hessian_device(pwa_handle* h, const double* theta, double* nll, doubl
         if (h->tile_bytes[s] > stage || h->tile_bytes[s] % 16 != 0 || (long long)h->ntiles[s] * kE < h->n[s])
             return set_error(h, PWA_EINVAL, "inconsistent tile geometry");
     }
+    // device: records [B Gb][rl] | sums [B][rl] | theta [B][P] | error words [B]
+    double* d_sum = hs.d_rec + (size_t)B * Gb * rl;
+    double* d_th = d_sum + (size_t)B * rl;
+    int* d_ev = reinterpret_cast<int*>(d_th + (size_t)B * P);
+    // host (pinned): sums [B][rl] | theta [B][P] | error words [B]
+    double* h_th = hs.h_buf + (size_t)B * rl;
+    int* h_ev = reinterpret_cast<int*>(h_th + (size_t)B * P);
     a.K = K;
     a.ev = 32 / t.W;
     a.stage_bytes = stage;
     a.res = h->d_res;
-    a.theta = h->d_theta;
+    a.theta = d_th;
+    a.P = P;
+    a.B = B;
+    a.Gb = Gb;
     a.nblk = nblk;
     a.rec = hs.d_rec;
     a.rec_len = hs.rec_len;
     a.bad = h->d_bad;
     a.err = h->d_err;
+    a.err_vec = d_ev;
     a.timeout_cycles = h->timeout_cycles;
-    double* d_sum = hs.d_rec + (size_t)hs.grid * hs.rec_len;
 
-    std::memcpy(h->h_pin, theta, sizeof(double) * h->P);
-    e = cudaMemcpyAsync(h->d_theta, h->h_pin, sizeof(double) * h->P, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(hs.d_rec, 0, sizeof(double) * (size_t)hs.grid * hs.rec_len, h->stream);
+    std::memcpy(h_th, theta, sizeof(double) * (size_t)B * P);
+    e = cudaMemcpyAsync(d_th, h_th, sizeof(double) * (size_t)B * P, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hs.d_rec, 0, sizeof(double) * (size_t)B * Gb * rl, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_ev, 0, sizeof(int) * B, h->stream);
     if (e != cudaSuccess) return cuda_error(h, e, "Hessian inputs");
-    fn<<<hs.grid, NT, smem, h->stream>>>(a);
+    fn<<<B * Gb, NT, smem, h->stream>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(h, e, "Hessian kernel launch");
-    hess_reduce_kernel<<<(hs.rec_len + 255) / 256, 256, 0, h->stream>>>(hs.d_rec, hs.grid, hs.rec_len, d_sum);
+    const long long nred = (long long)B * rl;
+    const int rgrid = (int)std::min<long long>((nred + 255) / 256, 4LL * h->num_sms);
+    hess_reduce_kernel<<<rgrid, 256, 0, h->stream>>>(hs.d_rec, B, Gb, hs.rec_len, d_sum);
     e = cudaGetLastError();
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(hs.h_sum, d_sum, sizeof(double) * hs.rec_len, cudaMemcpyDeviceToHost, h->stream);
-    int errw = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_pin + h->P, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        e = cudaMemcpyAsync(hs.h_buf, d_sum, sizeof(double) * (size_t)B * rl, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_ev, d_ev, sizeof(int) * B, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_pin + P, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_error(h, e, "Hessian pass");
-    std::memcpy(&errw, h->h_pin + h->P, sizeof(int));
-    if (errw) {
-        pwa_status st = check_device_errors(h);
-        if (st != PWA_OK) return st;
-    }
-    double f = 0.0;
-    combine(h, theta, hs.h_sum, NW, tc, &f, grad, hess);
-    if (nll) *nll = f;
+    hs.B = B;
+    hs.NW = NW;
+    hs.tc = tc;
     return PWA_OK;
+}
+
+// Wait for the pass that hessian_issue enqueued for these B vectors and
+// combine each vector's sums.  status[b] (when given) receives PWA_OK or
+// PWA_ENONFINITE per vector; without it a non-finite vector fails the call.
+// nll, grad may be NULL; hess [B][P][P].
+pwa_status hessian_finish(pwa_handle* h, int B, const double* theta, double* nll, double* grad, double* hess,
+                          pwa_status* status)
+{
+    HessState& hs = h->hess;
+    if (B != hs.B) return set_error(h, PWA_EINVAL, "hessian_finish does not match the issued batch");
+    const int P = h->P;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_error(h, e, "Hessian pass");
+    const size_t rl = (size_t)hs.rec_len;
+    const int* h_ev = reinterpret_cast<const int*>(hs.h_buf + (size_t)B * rl + (size_t)B * P);
+    int errw = 0;
+    std::memcpy(&errw, h->h_pin + P, sizeof(int));
+    if (errw) {
+        // a timeout fails the batch; non-finite intensities fail only their vectors
+        pwa_status st = check_device_errors(h);
+        if (st != PWA_OK && st != PWA_ENONFINITE) return st;
+        if (st == PWA_ENONFINITE && !status) return st;
+    }
+    for (int b = 0; b < B; ++b) {
+        if (status) status[b] = h_ev[b] ? PWA_ENONFINITE : PWA_OK;
+        if (h_ev[b]) continue;
+        double f = 0.0;
+        combine(h, theta + (size_t)b * P, hs.h_buf + (size_t)b * rl, hs.NW, hs.tc, &f,
+                grad ? grad + (size_t)b * P : nullptr, hess + (size_t)b * P * P);
+        if (nll) nll[b] = f;
+    }
+    return PWA_OK;
+}
+
+pwa_status hessian_device(pwa_handle* h, const double* theta, double* nll, double* grad, double* hess)
+{
+    pwa_status st = hessian_issue(h, 1, theta);
+    if (st != PWA_OK) return st;
+    return hessian_finish(h, 1, theta, nll, grad, hess, nullptr);
 }
 
 void free_hessian(pwa_handle* h)
 {
     if (h->hess.d_rec) cudaFree(h->hess.d_rec);
-    if (h->hess.h_sum) cudaFreeHost(h->hess.h_sum);
+    if (h->hess.h_buf) cudaFreeHost(h->hess.h_buf);
     h->hess = HessState();
 }
 
@@ -1241,4 +1308,17 @@ extern "C" pwa_status pwa_hessian(pwa_handle* h, const double* theta, double* nl
     for (int i = 0; i < h->P; ++i)
         if (!std::isfinite(theta[i])) return pwa::set_error(h, PWA_EINVAL, "theta must be finite");
     return pwa::hessian_device(h, theta, nll, grad, hess);
+}
+
+extern "C" pwa_status pwa_hessian_batch(pwa_handle* h, int B, const double* theta, double* nll, double* grad,
+                                        double* hess, pwa_status* status)
+{
+    if (!h) return PWA_EINVAL;
+    h->err.clear();
+    if (B < 1 || !theta || !hess) return pwa::set_error(h, PWA_EINVAL, "B >= 1, theta and hess are required");
+    for (size_t i = 0; i < (size_t)B * h->P; ++i)
+        if (!std::isfinite(theta[i])) return pwa::set_error(h, PWA_EINVAL, "theta must be finite");
+    pwa_status st = pwa::hessian_issue(h, B, theta);
+    if (st != PWA_OK) return st;
+    return pwa::hessian_finish(h, B, theta, nll, grad, hess, status);
 }

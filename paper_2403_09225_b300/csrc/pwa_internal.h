@@ -61,10 +61,14 @@ namespace pwa {
 struct HessState {
     const void* fn = nullptr;  // kernel instance the geometry below belongs to
     size_t smem = 0;
-    int grid = 0, rec_len = 0;
-    size_t cap_bytes = 0;
-    double* d_rec = nullptr;   // [grid][rec_len] records, then [rec_len] sums
-    double* h_sum = nullptr;   // [rec_len] pinned
+    int resident = 0, rec_len = 0;  // CTAs resident on the GPU at once; FP64 record length
+    size_t cap_bytes = 0, cap_host = 0;
+    // device: [B Gb][rec_len] records | [B][rec_len] sums | theta [B][P] | error words [B]
+    double* d_rec = nullptr;
+    // pinned: [B][rec_len] sums | theta [B][P] | error words [B]
+    double* h_buf = nullptr;
+    int B = 0, NW = 0;  // the batch in flight (hessian_issue -> hessian_finish)
+    bool tc = false;
 };
 }  // namespace pwa
 
@@ -188,6 +192,9 @@ constexpr int kMaxKHessian = 44;
 // The full Hessian of NLL at host theta (plus NLL and gradient; either may be
 // null) from one Hessian pass; synchronous.  hess: host [P][P].
 pwa_status hessian_device(pwa_handle* h, const double* theta, double* nll, double* grad, double* hess);
+pwa_status hessian_issue(pwa_handle* h, int B, const double* theta);
+pwa_status hessian_finish(pwa_handle* h, int B, const double* theta, double* nll, double* grad, double* hess,
+                          pwa_status* status);
 void free_hessian(pwa_handle* h);
 // Read back and clear the device error flags; turns them into a status + message.
 pwa_status check_device_errors(pwa_handle* h);

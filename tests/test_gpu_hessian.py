@@ -92,6 +92,42 @@ def test_hessian_tensor_core_path_above_k24(K, S):
     L.close()
 
 
+@pytest.mark.parametrize("name,nd,nm,B", [("tiny", 2001, 8003, 5), ("tiny_k4", 1500, 6001, 200),
+                                           ("paper", 1203, 4099, 3)])
+def test_hessian_batch_matches_oracle_and_single_calls(name, nd, nm, B):
+    """B vectors in one launch (B = 200 exceeds the resident CTAs: one CTA per
+    vector) against the oracle and against single-vector calls; a vector whose
+    intensity overflows is flagged in its status while the others are still
+    combined."""
+    from paper_2403_09225_b300 import binding
+    wl, model = small_workload(name, nd, nm)
+    L = binding.make_likelihood(wl)
+    ths = np.array(W.random_starts(wl, B))
+    bad = wl.theta_true.copy()
+    bad[0] = 1e30  # the first free magnitude (magnitudes lead theta): I overflows FP32
+    ths[1 % B] = bad if B > 1 else ths[0]
+    f, g, H, st = L.hessian_batch(ths)
+    for b in range(B):
+        if B > 1 and b == 1:
+            assert st[b] == binding.PWA_ENONFINITE
+            assert np.all(np.isnan(H[b]))
+            continue
+        assert st[b] == binding.PWA_OK
+        if b < 3:
+            fo, go = oracle.nll_grad(model, ths[b], wl.data, wl.mc)
+            Ho = oracle.hessian(model, ths[b], wl.data, wl.mc)
+            assert abs(f[b] - fo) <= TOL_NLL * nll_scale(model, ths[b], wl, fo), (b, f[b], fo)
+            assert relmax(g[b], go) <= TOL_GRAD, (b, relmax(g[b], go))
+            assert relmax(H[b], Ho) <= TOL_HVP, (b, relmax(H[b], Ho))
+        f1, g1, H1 = L.hessian(ths[b])
+        assert relmax(H[b], H1) <= 1e-5 and relmax(g[b], g1) <= 1e-6, (b, relmax(H[b], H1))
+        assert np.array_equal(H[b], H[b].T)
+    # the handle stays usable and a single call after the flagged batch is clean
+    f1, g1, H1 = L.hessian(ths[0])
+    assert np.isfinite(H1).all()
+    L.close()
+
+
 def test_hessian_is_reproducible_and_refuses_large_k():
     from paper_2403_09225_b300 import binding
     wl, model = small_workload("paper", 1500 + 3, 6000 + 29)
