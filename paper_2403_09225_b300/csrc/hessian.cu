@@ -53,6 +53,7 @@ namespace {
 using pwa::KConst;
 constexpr int kE = pwa::kTileE;  // events per tile
 constexpr int kFold = 16;        // tiles between FP32 -> FP64 folds
+constexpr int kFoldG = 32;       // the same for the tensor-core kernel's Gram sums (FP32 adds of per-tile sums)
 constexpr int kMaxKHess = pwa::kMaxKHessian;  // K (K + 1) / 2 Gram blocks fit 2 per thread of 512
 constexpr int kMaxKTensor = 32;                // 4K columns fit the M = 128 tensor-core tile
 
@@ -115,7 +116,7 @@ constexpr int kZStride = 36;
 template <int S, int NT, int NB>
 __global__ void __launch_bounds__(NT, 1) hess_kernel(const HessArgs a)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int NW = NT / 32;
     constexpr int RS = 32 * S + 4;  // x_stride(S)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -469,84 +470,128 @@ __global__ void __launch_bounds__(NT, 1) hess_kernel(const HessArgs a)
 // significant bits) in the canonical K-major layout of a tcgen05 operand:
 // element (column m, row k) in 8 x 16-byte core matrices, rows k along the
 // MMA's K dimension (X row e S + s: an event's projections are adjacent, so
-// a lane writes them in one store; the Gram does not depend on the order).  The same buffer is the A operand (M = 128 columns, the
-// ones past 4K zero) and the B operand (N = 4K rounded up to 16) of
-// D = X^T X, so one thread issues, per 16 rows, three kind::f16 MMAs
-// (hi hi, hi lo, lo hi; lo lo is below 2^-16 of the product) into a TMEM
-// accumulator that starts fresh at every tile (one tile's sum stays short,
-// so the tensor core's FP32 accumulation loses nothing), and the z Gram of
-// the data events likewise.  After each tile the eight warps read the
-// accumulators back (warp w: TMEM lanes 32 (w mod 4) + l, half w / 4 of
-// the columns) and add them to FP32 registers, folded into FP64 every kFold
-// tiles like the other sums.  Per-CTA record: the full data X Gram, the data
-// z Gram and the MC X Gram (C x C each, row-major), then Q [2][K][6] and the
-// scalars [8][2].
+// a lane writes them in one store; the Gram does not depend on the order).
+// The hi part is the A operand (M = 128 columns: the MMA reads past the 4K
+// rounded up to 16 columns the buffer holds, into rows of D that are never
+// read) and, with the lo part stored as 2 lo, the B operand (N = 4K rounded
+// up to 16): per 16 rows one thread issues two kind::f16 MMAs, D += hi^T hi
+// + hi^T (2 lo), whose symmetric part is hi^T hi + hi^T lo + lo^T hi (lo^T lo
+// is below 2^-16 of the product; the host symmetrises).  Each tile's sums
+// start in a fresh TMEM accumulator (one tile's sum stays short, so the
+// tensor core's FP32 accumulation loses nothing), and the data events' z
+// Gram likewise.  The tiles are pipelined over two operand buffers and two
+// accumulator sets: tile i's MMAs run while the warps read tile i - 1's
+// accumulators back (warp w: TMEM lanes 32 (w mod 4) + l, half w / 4 of the
+// columns) into FP32 registers and build tile i + 1's operands; the FP32
+// sums are folded into FP64 every kFold tiles like the other sums.  (For
+// S = 4 and K > 28 the two buffers do not fit in shared memory: one buffer,
+// each tile read back before the next is built.)  Per-CTA record: the full
+// data X Gram, the data z Gram and the MC X Gram (C x C each, row-major, not
+// yet symmetric), then Q [2][K][6] and the scalars [8][2].
 
 constexpr uint32_t kTcLbo = 144;  // core-matrix stride along the rows (16 B of padding: phase 1's
                                   // stores from 32 lanes spread over the banks)
-constexpr int kTcCols = 128;      // M of the MMA: the columns of X padded to 128
-constexpr int kTcTmemCols = 256;  // X Gram at TMEM columns [0, 128), z Gram at [128, 256)
 constexpr int kTcNT = 256;  // 8 warps (16 were slower: the cross-warp sums of the event phase grow)
 constexpr int kTcKW = 4;    // resonances per warp in the event phase: K <= 8 x 4 = 32
 
 __host__ __device__ inline uint32_t tc_sbo(int rows) { return (uint32_t)(rows / 8) * kTcLbo; }
-__host__ __device__ inline uint32_t tc_part(int rows) { return (uint32_t)(kTcCols / 8) * tc_sbo(rows); }
 __host__ __device__ inline int hess_tc_rec_len(int K) { return 3 * 16 * K * K + 12 * K + 2 * (kTcNT / 32); }
+// operand buffers per kernel instance (S, NCH = (4K rounded up to 16) / 16): two where they fit
+__host__ __device__ constexpr int tc_nbuf(int S, int nch) { return (S == 4 && nch == 8) ? 1 : 2; }
+// TMEM columns: per accumulator set the X Gram at [0, 128) and the z Gram at [128, 256)
+__host__ __device__ constexpr int tc_tmem_cols(int nbuf) { return 256 * nbuf; }
 // byte offset of (column m, row k) in a K-major BF16 operand part with stride sbo between 8-column groups
 __host__ __device__ inline uint32_t tc_off(int m, int k, uint32_t sbo)
 {
     return (uint32_t)(m >> 3) * sbo + (uint32_t)(k >> 3) * kTcLbo + (uint32_t)(m & 7) * 16 + (uint32_t)(k & 7) * 2;
 }
-__host__ inline size_t hess_tc_smem(int K, int S, uint32_t stage)
-{
-    return 2 * (size_t)tc_part(32 * S) + 2 * (size_t)tc_part(32) + 2 * (size_t)stage + sizeof(KConst) * K +
-           sizeof(float) * (size_t)(kTcNT / 32) * 2 * S * 32 + 3 * 8 + 16;
-}
 
-__device__ __forceinline__ void store_split(unsigned char* part0, uint32_t part_bytes, uint32_t off, float x)
+// Shared-memory layout of hess_tc_kernel (byte offsets): X operand buffers
+// [nbuf] (hi part, then the 2 lo part, each 4K rounded up to 16 columns) |
+// z operand buffers [nbuf] | TMA stages [2] | KConst [K] | partial A
+// [8 warps][2S][32] | total A [2S][32] | mbarriers (TMA 0, 1; MMA sets 0, 1)
+// | TMEM address.  total covers the A operands' reads of 128 columns.
+struct TcLayout {
+    uint32_t sbox, sboz, pbx, pbz;  // 8-column group strides and part sizes of X and z
+    uint32_t x[2], z[2], stages, kc, pa, pt, mbar, tslot, total;
+};
+__host__ __device__ inline TcLayout tc_layout(int K, int S, int nch, uint32_t stage_bytes)
+{
+    const int nbuf = tc_nbuf(S, nch), NW = kTcNT / 32;
+    TcLayout L{};
+    L.sbox = tc_sbo(32 * S);
+    L.sboz = tc_sbo(32);
+    L.pbx = (uint32_t)(2 * nch) * L.sbox;
+    L.pbz = (uint32_t)(2 * nch) * L.sboz;
+    L.x[0] = 0;
+    L.x[1] = nbuf == 2 ? 2 * L.pbx : 0;
+    uint32_t o = (uint32_t)nbuf * 2 * L.pbx;
+    L.z[0] = o;
+    L.z[1] = nbuf == 2 ? o + 2 * L.pbz : o;
+    o += (uint32_t)nbuf * 2 * L.pbz;
+    L.stages = o;  // a multiple of 16 (the parts are multiples of 144 = 9 x 16)
+    o += 2 * stage_bytes;
+    L.kc = o;
+    o += (uint32_t)(sizeof(KConst) * K);
+    L.pa = o;
+    o += (uint32_t)(sizeof(float) * NW * 2 * S * 32);
+    L.pt = o;
+    o += (uint32_t)(sizeof(float) * 2 * S * 32);
+    o = (o + 15u) & ~15u;
+    L.mbar = o;
+    o += 4 * 8;
+    L.tslot = o;
+    o += 16;
+    const uint32_t ax = L.x[nbuf - 1] + 16 * L.sbox, az = L.z[nbuf - 1] + 16 * L.sboz;
+    L.total = o > ax ? (o > az ? o : az) : (ax > az ? ax : az);
+    return L;
+}
+__host__ inline size_t hess_tc_smem(int K, int S, uint32_t stage) { return tc_layout(K, S, (4 * K + 15) / 16, stage).total; }
+
+// x as a BF16 hi part and the BF16 of 2 (x - hi) (x - hi is exact in FP32)
+__device__ __forceinline__ void store_split(unsigned char* hi0, uint32_t part_bytes, uint32_t off, float x)
 {
     const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-    *reinterpret_cast<__nv_bfloat16*>(part0 + off) = hi;
-    *reinterpret_cast<__nv_bfloat16*>(part0 + part_bytes + off) = lo;
+    const __nv_bfloat16 lo2 = __float2bfloat16_rn(2.f * (x - __bfloat162float(hi)));
+    *reinterpret_cast<__nv_bfloat16*>(hi0 + off) = hi;
+    *reinterpret_cast<__nv_bfloat16*>(hi0 + part_bytes + off) = lo2;
 }
 
-// 4 consecutive 32-bit columns of this thread's TMEM lane (valid after tmem_wait)
-__device__ __forceinline__ void tmem_ld4(uint32_t addr, uint32_t (&r)[4])
+// the same for a pair of adjacent rows, as packed BF16 pairs (the first row in the low half)
+__device__ __forceinline__ void split2(float2 x, uint32_t& hi, uint32_t& lo2)
 {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(addr));
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x.x, x.y);
+    const float2 hf = __bfloat1622float2(h);
+    const float2 d = __ffma2_rn(hf, make_float2(-2.f, -2.f), __fmul2_rn(x, make_float2(2.f, 2.f)));  // exact
+    const __nv_bfloat162 l = __floats2bfloat162_rn(d.x, d.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo2 = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// The S consecutive rows (e S .. e S + S - 1) of one column: hi and lo parts,
-// one 4- or 8-byte store per part for S = 2, 4 (the rows share a 16-byte core row)
+// The S consecutive rows (e S .. e S + S - 1) of one column, hi and 2 lo
+// parts: one 8- (S = 4) or 4-byte (S = 2) store per part (the rows share a
+// 16-byte core row); odd S one 2-byte store per row and part.
 template <int S>
-__device__ __forceinline__ void store_rows(unsigned char* part0, uint32_t part_bytes, uint32_t off, const float (&x)[S])
+__device__ __forceinline__ void store_rows(unsigned char* hi0, uint32_t part_bytes, uint32_t off, const float (&x)[S])
 {
-    unsigned short hb[S], lb[S];
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-        const __nv_bfloat16 hi = __float2bfloat16_rn(x[s]);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(x[s] - __bfloat162float(hi));
-        hb[s] = __bfloat16_as_ushort(hi);
-        lb[s] = __bfloat16_as_ushort(lo);
-    }
     if constexpr (S == 4) {
-        *reinterpret_cast<uint2*>(part0 + off) = make_uint2(hb[0] | ((uint32_t)hb[1] << 16), hb[2] | ((uint32_t)hb[3] << 16));
-        *reinterpret_cast<uint2*>(part0 + part_bytes + off) =
-            make_uint2(lb[0] | ((uint32_t)lb[1] << 16), lb[2] | ((uint32_t)lb[3] << 16));
+        uint32_t h0, l0, h1, l1;
+        split2(make_float2(x[0], x[1]), h0, l0);
+        split2(make_float2(x[2], x[3]), h1, l1);
+        *reinterpret_cast<uint2*>(hi0 + off) = make_uint2(h0, h1);
+        *reinterpret_cast<uint2*>(hi0 + part_bytes + off) = make_uint2(l0, l1);
     } else if constexpr (S == 2) {
-        *reinterpret_cast<uint32_t*>(part0 + off) = hb[0] | ((uint32_t)hb[1] << 16);
-        *reinterpret_cast<uint32_t*>(part0 + part_bytes + off) = lb[0] | ((uint32_t)lb[1] << 16);
+        uint32_t h0, l0;
+        split2(make_float2(x[0], x[1]), h0, l0);
+        *reinterpret_cast<uint32_t*>(hi0 + off) = h0;
+        *reinterpret_cast<uint32_t*>(hi0 + part_bytes + off) = l0;
     } else {
-        // odd S: the rows may cross a 16-byte core row; one 2-byte store each
+        // odd S: the rows may cross a 16-byte core row
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             const int r = (int)((off >> 1) & 7) + s;  // row within its core row, from the first's offset
             const uint32_t o = off + (uint32_t)(r >> 3) * kTcLbo + (uint32_t)((r & 7) - ((off >> 1) & 7)) * 2;
-            *reinterpret_cast<unsigned short*>(part0 + o) = hb[s];
-            *reinterpret_cast<unsigned short*>(part0 + part_bytes + o) = lb[s];
+            store_split(hi0, part_bytes, o, x[s]);
         }
     }
 }
@@ -556,33 +601,28 @@ __global__ void __launch_bounds__(kTcNT, 1) hess_tc_kernel(const HessArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int NT = kTcNT, NW = NT / 32, R = 32 * S, Cp = NCH * 16;
+    constexpr int NBUF = tc_nbuf(S, NCH);
     constexpr int CPT = Cp / (NW / 4);  // Gram columns per thread: the warps of a TMEM lane quarter split them
-    static_assert(kTcKW * NW >= 32, "the event phase must cover K <= 32");
+    static_assert(kTcKW * NW >= 32 && CPT % 8 == 0 && 2 * S <= NW, "tile shape");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = a.K, C = 4 * K;
-    const uint32_t SBOX = tc_sbo(R), PBX = tc_part(R), SBOZ = tc_sbo(32), PBZ = tc_part(32);
-
-    // shared memory: X operand [hi | lo] | z operand [hi | lo] | stages[2] | KConst[K] |
-    // partial A [NW][2S][32] | mbarriers (TMA stages 0, 1; MMA done) | TMEM address
-    unsigned char* xop = smem;
-    unsigned char* zop = xop + 2 * PBX;
-    unsigned char* stages = zop + 2 * PBZ;
-    KConst* kc = reinterpret_cast<KConst*>(stages + 2 * (size_t)a.stage_bytes);
-    float* PA = reinterpret_cast<float*>(kc + K);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(PA + NW * 2 * S * 32);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 3);
-    __shared__ long long issued[2];
-    __shared__ int s_abort;
-
     const int bt = (int)(blockIdx.x % (unsigned)a.B), gb = (int)(blockIdx.x / (unsigned)a.B), G = a.Gb;
+    const TcLayout L = tc_layout(K, S, NCH, a.stage_bytes);
+    unsigned char* stages = smem + L.stages;
+    KConst* kc = reinterpret_cast<KConst*>(smem + L.kc);
+    float* PA = reinterpret_cast<float*>(smem + L.pa);
+    float* PT = reinterpret_cast<float*>(smem + L.pt);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.mbar);  // TMA stages 0, 1; MMA sets 0, 1
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.tslot);
+    __shared__ long long issued[2];
+
     const long long T = (long long)a.ntiles[0] + a.ntiles[1];
     auto tile_src = [&](long long t, int& smp, long long& lt) {
         smp = t < a.ntiles[0] ? 0 : 1;
         lt = smp ? t - a.ntiles[0] : t;
     };
     if (tid == 0) {
-        s_abort = 0;
-        for (int s = 0; s < 3; ++s) pwa::mbar_init(&mbar[s], 1);
+        for (int s = 0; s < 4; ++s) pwa::mbar_init(&mbar[s], 1);
         issued[0] = issued[1] = -1;
         pwa::fence_mbar_init();
         for (int i = 0; i < 2; ++i) {
@@ -599,16 +639,16 @@ __global__ void __launch_bounds__(kTcNT, 1) hess_tc_kernel(const HessArgs a)
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(pwa::tc::sa(tslot)),
-                     "r"(kTcTmemCols));
+                     "r"(tc_tmem_cols(NBUF)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     {
         pwa::PassArgs pa;
         pa.res = a.res;
         for (int k = tid; k < K; k += NT) kc[k] = pwa::make_kconst(pa, a.theta + (size_t)bt * a.P, nullptr, k, false, a.ev);
-        // the operands' padding columns (and everything else) start at zero
-        uint4* z4 = reinterpret_cast<uint4*>(xop);
-        for (uint32_t i = tid; i < (2 * PBX + 2 * PBZ) / 16; i += NT) z4[i] = make_uint4(0, 0, 0, 0);
+        // the operands start at zero (columns past 4K only ever meet D entries that are not read)
+        uint4* z4 = reinterpret_cast<uint4*>(smem);
+        for (uint32_t i = tid; i < L.stages / 16; i += NT) z4[i] = make_uint4(0, 0, 0, 0);
     }
     pwa::fence_proxy_async();
     pwa::tc::fence_before();
@@ -616,10 +656,8 @@ __global__ void __launch_bounds__(kTcNT, 1) hess_tc_kernel(const HessArgs a)
     pwa::tc::fence_after();
     const uint32_t tm = *tslot;
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Cp >> 3) << 17) | ((128u >> 4) << 24);
-    const uint32_t xa = pwa::tc::sa(xop), za = pwa::tc::sa(zop);
 
     // this thread's Gram entries: row m = 32 (warp mod 4) + lane, columns c0 .. c0 + CPT - 1
-    // (the warps w, w + 4, ... share TMEM lane quarter w mod 4 and split its columns)
     const int qd = warp & 3, m = 32 * qd + lane, c0 = (warp >> 2) * CPT;
     const uint32_t tlane = (uint32_t)(32 * qd) << 16;
     float ax[CPT], az[CPT];
@@ -635,7 +673,8 @@ __global__ void __launch_bounds__(kTcNT, 1) hess_tc_kernel(const HessArgs a)
     double* rec = a.rec + (size_t)blockIdx.x * a.rec_len;
     const int CC = C * C;
     const int offQ = 3 * CC, offS = offQ + 12 * K;
-    auto fold = [&](int smp) {
+    // FP32 Gram sums of sample set smp into the FP64 record
+    auto fold_g = [&](int smp) {
         double* rx = rec + (smp == 0 ? 0 : 2 * CC);
         double* rz = rec + CC;
 #pragma unroll
@@ -647,6 +686,9 @@ __global__ void __launch_bounds__(kTcNT, 1) hess_tc_kernel(const HessArgs a)
             }
             ax[j] = az[j] = 0.f;
         }
+    };
+    // FP32 Q and scalar sums of sample set smp into the FP64 record
+    auto fold_q = [&](int smp) {
 #pragma unroll
         for (int j = 0; j < kTcKW; ++j) {
             const int k = warp + j * NW;
@@ -661,92 +703,147 @@ __global__ void __launch_bounds__(kTcNT, 1) hess_tc_kernel(const HessArgs a)
         sc = 0.f;
         if (lane == 0) rec[offS + 2 * warp + smp] += (double)v;
     };
+    // accumulator set sb (a finished tile's MMAs) into the FP32 sums; z only for data tiles
+    auto read_back = [&](int sb, bool with_z) {
+        const uint32_t base = tm + (uint32_t)(256 * sb) + tlane + (uint32_t)c0;
+        {
+            uint32_t v[CPT / 8][8];
+#pragma unroll
+            for (int ch = 0; ch < CPT / 8; ++ch) pwa::tc::tmem_ld8(base + 8 * ch, v[ch]);
+            pwa::tc::tmem_wait();
+#pragma unroll
+            for (int ch = 0; ch < CPT / 8; ++ch)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) ax[8 * ch + u] += __uint_as_float(v[ch][u]);
+        }
+        if (with_z) {
+            uint32_t v[CPT / 8][8];
+#pragma unroll
+            for (int ch = 0; ch < CPT / 8; ++ch) pwa::tc::tmem_ld8(base + 128 + 8 * ch, v[ch]);
+            pwa::tc::tmem_wait();
+#pragma unroll
+            for (int ch = 0; ch < CPT / 8; ++ch)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) az[8 * ch + u] += __uint_as_float(v[ch][u]);
+        }
+    };
 
     int st = 0;
-    uint32_t ph = 0, mph = 0;
-    int n_mma = 0;  // commits issued on mbar[2]
-    int win = 0;
-    int cur_smp = 0;
+    uint32_t ph = 0;
+    int win_q = 0, win_g = 0;
+    int cur_q = 0, cur_g = 0;  // sample sets of the Q/scalar sums and of the Gram sums in registers
+    int pend_smp = -1;         // two buffers: sample set of the tile whose read-back is pending (-1: none)
     long long i = 0;
+    bool aborted = false;      // the same in every thread (decided at a barrier)
+    bool failed = false;       // this thread's last wait gave up
+    long long last_mma = -1;   // the last tile whose MMAs were issued
+    const bool issuer = tid == NT - 32;  // lane 0 of the last warp (the fewest resonances) issues copies and MMAs
+    // this thread's wait for tile j's MMAs (accumulator set j mod NBUF, the (j / NBUF)-th commit there)
+    auto wait_mma = [&](long long j) -> bool {
+        const int sb = NBUF == 2 ? (int)(j & 1) : 0;
+        const uint32_t par = (uint32_t)((NBUF == 2 ? (j >> 1) : j) & 1);
+        return pwa::mbar_wait(&mbar[2 + sb], par, a.timeout_cycles);
+    };
+    // tile j's accumulators (sample set smp) into the FP32 sums, once its MMAs are done
+    auto finish_tile = [&](long long j, int smp) {
+        failed |= !wait_mma(j);
+        pwa::tc::fence_after();
+        if (smp != cur_g) {
+            fold_g(cur_g);
+            win_g = 0;
+            cur_g = smp;
+        }
+        read_back(NBUF == 2 ? (int)(j & 1) : 0, smp == 0);
+        if (++win_g == kFoldG) {
+            fold_g(cur_g);
+            win_g = 0;
+        }
+        pwa::tc::fence_before();
+    };
     for (long long t = gb; t < T; t += G, ++i) {
         int smp;
         long long lt;
         tile_src(t, smp, lt);
-        if (smp != cur_smp) {
-            fold(0);
-            win = 0;
-            cur_smp = smp;
+        if (smp != cur_q) {
+            fold_q(cur_q);
+            win_q = 0;
+            cur_q = smp;
         }
-        const bool ok = pwa::mbar_wait(&mbar[st], ph, a.timeout_cycles);
-        if (!__syncthreads_and(ok)) {
-            if (tid == 0) s_abort = 1;
-            break;
-        }
+        // the tile's copy (each thread waits; a failure is acted on at the next barrier)
+        failed |= !pwa::mbar_wait(&mbar[st], ph, a.timeout_cycles);
+        const int b = NBUF == 2 ? (int)(i & 1) : 0;
+        unsigned char* xo = smem + (b ? L.x[1] : L.x[0]);
+        unsigned char* zo = smem + (b ? L.z[1] : L.z[0]);
         const float* Ft = reinterpret_cast<const float*>(stages + (size_t)st * a.stage_bytes);
         const float* m2s = Ft + (size_t)2 * K * S * kE;
         const long long e_base = lt * kE;
         const int e = lane;
         const bool valid = e < (int)min((long long)kE, a.nev[smp] - e_base);
 
-        // ---- event phase (as hess_kernel) ----
-        float br[kTcKW], bim[kTcKW], fr[kTcKW][S], fi[kTcKW][S];
-        float Ar[S], Ai[S];
+        // ---- event phase: BW and the coherent sums A_s over this warp's resonances ----
+        float br[kTcKW], bim[kTcKW];
+        // even S: F as packed pairs over two projections, fv[j][2q] = (Re F_2q, Re F_2q+1),
+        // fv[j][2q+1] = (Im F_2q, Im F_2q+1), and A likewise; odd S: fv[j][s] = (Re F_s, Im F_s)
+        float2 fv[kTcKW][S];
+        float2 Ap[S];
 #pragma unroll
-        for (int s = 0; s < S; ++s) Ar[s] = Ai[s] = 0.f;
+        for (int s = 0; s < S; ++s) Ap[s] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < kTcKW; ++j) {
             const int k = warp + j * NW;
             br[j] = bim[j] = 0.f;
 #pragma unroll
-            for (int s = 0; s < S; ++s) fr[j][s] = fi[j][s] = 0.f;
+            for (int s = 0; s < S; ++s) fv[j][s] = make_float2(0.f, 0.f);
             if (k < K) {
                 const KConst c = kc[k];
                 pwa::breit_wigner(c, m2s[c.ch * kE + e], br[j], bim[j]);
                 const float cr = c.gre * br[j] - c.gim * bim[j], ci = c.gre * bim[j] + c.gim * br[j];
                 const int p = (e + c.shift) & (kE - 1);
                 if constexpr (S % 2 == 0) {
+                    const float2 crr = make_float2(cr, cr), cii = make_float2(ci, ci), ncc = make_float2(-ci, -ci);
 #pragma unroll
                     for (int qq = 0; qq < S / 2; ++qq) {
                         const float4 f4 = *reinterpret_cast<const float4*>(Ft + 4 * ((k * (S / 2) + qq) * kE + p));
-                        fr[j][2 * qq] = f4.x;
-                        fr[j][2 * qq + 1] = f4.y;
-                        fi[j][2 * qq] = f4.z;
-                        fi[j][2 * qq + 1] = f4.w;
+                        const float2 R2 = make_float2(f4.x, f4.y), I2 = make_float2(f4.z, f4.w);
+                        fv[j][2 * qq] = R2;
+                        fv[j][2 * qq + 1] = I2;
+                        Ap[2 * qq] = __ffma2_rn(I2, ncc, __ffma2_rn(R2, crr, Ap[2 * qq]));
+                        Ap[2 * qq + 1] = __ffma2_rn(I2, crr, __ffma2_rn(R2, cii, Ap[2 * qq + 1]));
                     }
                 } else {
 #pragma unroll
                     for (int s = 0; s < S; ++s) {
                         const float2 f2 = *reinterpret_cast<const float2*>(Ft + 2 * ((k * S + s) * kE + p));
-                        fr[j][s] = f2.x;
-                        fi[j][s] = f2.y;
+                        fv[j][s] = f2;
+                        Ap[s].x += cr * f2.x - ci * f2.y;
+                        Ap[s].y += cr * f2.y + ci * f2.x;
                     }
                 }
-#pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    Ar[s] += cr * fr[j][s] - ci * fi[j][s];
-                    Ai[s] += cr * fi[j][s] + ci * fr[j][s];
-                }
             }
         }
+        // the warps' partial sums: warp c < 2S adds up component c over the warps (fixed order)
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            PA[(warp * 2 * S + 2 * s) * 32 + e] = Ar[s];
-            PA[(warp * 2 * S + 2 * s + 1) * 32 + e] = Ai[s];
+            PA[(warp * 2 * S + 2 * s) * 32 + e] = Ap[s].x;
+            PA[(warp * 2 * S + 2 * s + 1) * 32 + e] = Ap[s].y;
+        }
+        if (__syncthreads_or(failed)) {  // a copy or the previous tile's MMAs never completed
+            aborted = true;
+            break;
+        }
+        if (warp < 2 * S) {
+            float x = 0.f;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) x += PA[(w * 2 * S + warp) * 32 + e];
+            PT[warp * 32 + e] = x;
         }
         __syncthreads();
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            float xr = 0.f, xi = 0.f;
-            for (int w = 0; w < NW; ++w) {
-                xr += PA[(w * 2 * S + 2 * s) * 32 + e];
-                xi += PA[(w * 2 * S + 2 * s + 1) * 32 + e];
-            }
-            Ar[s] = xr;
-            Ai[s] = xi;
-        }
         float I = 0.f;
 #pragma unroll
-        for (int s = 0; s < S; ++s) I += Ar[s] * Ar[s] + Ai[s] * Ai[s];
+        for (int s = 0; s < S; ++s) {
+            Ap[s] = make_float2(PT[(2 * s) * 32 + e], PT[(2 * s + 1) * 32 + e]);
+            I += Ap[s].x * Ap[s].x + Ap[s].y * Ap[s].y;
+        }
         float aw = 0.f, sqa = 0.f, zw = 0.f;
         if (smp == 0) {
             const float w = m2s[3 * kE + e];
@@ -773,6 +870,12 @@ __global__ void __launch_bounds__(kTcNT, 1) hess_tc_kernel(const HessArgs a)
                 atomicOr(a.err_vec + bt, pwa::ERR_NONFINITE);
             }
         }
+        // ---- per resonance: the X columns (sqrt a (B F, B^2 F)), D, the z columns and Q ----
+        float2 nAi[S];  // even S: minus the imaginary pairs of A (for Im D)
+        if constexpr (S % 2 == 0) {
+#pragma unroll
+            for (int qq = 0; qq < S / 2; ++qq) nAi[qq] = make_float2(-Ap[2 * qq + 1].x, -Ap[2 * qq + 1].y);
+        }
 #pragma unroll
         for (int j = 0; j < kTcKW; ++j) {
             const int k = warp + j * NW;
@@ -780,30 +883,57 @@ __global__ void __launch_bounds__(kTcNT, 1) hess_tc_kernel(const HessArgs a)
             const float b1r = br[j], b1i = bim[j];
             const float b2r = b1r * b1r - b1i * b1i, b2i = 2.f * b1r * b1i;
             const float b3r = b2r * b1r - b2i * b1i, b3i = b2r * b1i + b2i * b1r;
-            float Dr = 0.f, Di = 0.f;
+            const float p1r = sqa * b1r, p1i = sqa * b1i, p2r = sqa * b2r, p2i = sqa * b2i;
             const int c1 = 2 * k, c2 = 2 * (K + k);  // columns of Re (B F), Re (B^2 F); Im at + 1
-            // the event's S rows are consecutive (row e S + s): one store per column and part for even S
             float v[4][S];
+            float Dr, Di;
+            if constexpr (S % 2 == 0) {
+                float2 DR = make_float2(0.f, 0.f), DI = DR;
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                Dr += Ar[s] * fr[j][s] + Ai[s] * fi[j][s];
-                Di += Ar[s] * fi[j][s] - Ai[s] * fr[j][s];
-                v[0][s] = sqa * (b1r * fr[j][s] - b1i * fi[j][s]);
-                v[1][s] = sqa * (b1r * fi[j][s] + b1i * fr[j][s]);
-                v[2][s] = sqa * (b2r * fr[j][s] - b2i * fi[j][s]);
-                v[3][s] = sqa * (b2r * fi[j][s] + b2i * fr[j][s]);
+                for (int qq = 0; qq < S / 2; ++qq) {
+                    const float2 R2 = fv[j][2 * qq], I2 = fv[j][2 * qq + 1];
+                    // D = sum_s conj(A_s) F_s
+                    DR = __ffma2_rn(Ap[2 * qq + 1], I2, __ffma2_rn(Ap[2 * qq], R2, DR));
+                    DI = __ffma2_rn(nAi[qq], R2, __ffma2_rn(Ap[2 * qq], I2, DI));
+                    const float2 x0 = __ffma2_rn(I2, make_float2(-p1i, -p1i), __fmul2_rn(R2, make_float2(p1r, p1r)));
+                    const float2 x1 = __ffma2_rn(I2, make_float2(p1r, p1r), __fmul2_rn(R2, make_float2(p1i, p1i)));
+                    const float2 x2 = __ffma2_rn(I2, make_float2(-p2i, -p2i), __fmul2_rn(R2, make_float2(p2r, p2r)));
+                    const float2 x3 = __ffma2_rn(I2, make_float2(p2r, p2r), __fmul2_rn(R2, make_float2(p2i, p2i)));
+                    v[0][2 * qq] = x0.x;
+                    v[0][2 * qq + 1] = x0.y;
+                    v[1][2 * qq] = x1.x;
+                    v[1][2 * qq + 1] = x1.y;
+                    v[2][2 * qq] = x2.x;
+                    v[2][2 * qq + 1] = x2.y;
+                    v[3][2 * qq] = x3.x;
+                    v[3][2 * qq + 1] = x3.y;
+                }
+                Dr = DR.x + DR.y;
+                Di = DI.x + DI.y;
+            } else {
+                Dr = Di = 0.f;
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    const float fr = fv[j][s].x, fi = fv[j][s].y;
+                    Dr += Ap[s].x * fr + Ap[s].y * fi;
+                    Di += Ap[s].x * fi - Ap[s].y * fr;
+                    v[0][s] = p1r * fr - p1i * fi;
+                    v[1][s] = p1r * fi + p1i * fr;
+                    v[2][s] = p2r * fr - p2i * fi;
+                    v[3][s] = p2r * fi + p2i * fr;
+                }
             }
             const int cols[4] = {c1, c1 + 1, c2, c2 + 1};
 #pragma unroll
-            for (int u = 0; u < 4; ++u) store_rows<S>(xop, PBX, tc_off(cols[u], e * S, SBOX), v[u]);
+            for (int u = 0; u < 4; ++u) store_rows<S>(xo, L.pbx, tc_off(cols[u], e * S, L.sbox), v[u]);
             const float z1r = b1r * Dr - b1i * Di, z1i = b1r * Di + b1i * Dr;
             const float z2r = b2r * Dr - b2i * Di, z2i = b2r * Di + b2i * Dr;
             const float z3r = b3r * Dr - b3i * Di, z3i = b3r * Di + b3i * Dr;
             if (smp == 0) {
-                store_split(zop, PBZ, tc_off(c1, e, SBOZ), zw * z1r);
-                store_split(zop, PBZ, tc_off(c1 + 1, e, SBOZ), zw * z1i);
-                store_split(zop, PBZ, tc_off(c2, e, SBOZ), zw * z2r);
-                store_split(zop, PBZ, tc_off(c2 + 1, e, SBOZ), zw * z2i);
+                store_split(zo, L.pbz, tc_off(c1, e, L.sboz), zw * z1r);
+                store_split(zo, L.pbz, tc_off(c1 + 1, e, L.sboz), zw * z1i);
+                store_split(zo, L.pbz, tc_off(c2, e, L.sboz), zw * z2r);
+                store_split(zo, L.pbz, tc_off(c2 + 1, e, L.sboz), zw * z2i);
             }
             q[j][0] = fmaf(aw, z1r, q[j][0]);
             q[j][1] = fmaf(aw, z1i, q[j][1]);
@@ -816,7 +946,7 @@ __global__ void __launch_bounds__(kTcNT, 1) hess_tc_kernel(const HessArgs a)
         pwa::fence_proxy_async();
         pwa::tc::fence_before();
         __syncthreads();
-        if (tid == 0) {
+        if (issuer) {
             const long long tn = t + 2LL * G;
             if (tn < T) {
                 int s2;
@@ -827,85 +957,66 @@ __global__ void __launch_bounds__(kTcNT, 1) hess_tc_kernel(const HessArgs a)
                                    a.tile_bytes[s2], &mbar[st]);
             }
             pwa::tc::fence_after();
-            // D = X^T X over the tile's rows: per 16 rows hi hi, hi lo, lo hi
+            // D = hi^T hi + hi^T (2 lo) over the tile's rows, 16 rows per step
+            const uint32_t xa = pwa::tc::sa(xo), za = pwa::tc::sa(zo), dx = tm + (uint32_t)(256 * b);
 #pragma unroll 1
             for (int ks = 0; ks < R / 16; ++ks) {
-                const uint64_t dh = pwa::tc::sdesc(xa + ks * 2 * kTcLbo, kTcLbo, SBOX);
-                const uint64_t dl = pwa::tc::sdesc(xa + PBX + ks * 2 * kTcLbo, kTcLbo, SBOX);
-                pwa::tc::mma_bf16(tm, dh, dh, idesc, ks > 0);
-                pwa::tc::mma_bf16(tm, dh, dl, idesc, 1);
-                pwa::tc::mma_bf16(tm, dl, dh, idesc, 1);
+                const uint64_t dh = pwa::tc::sdesc(xa + ks * 2 * kTcLbo, kTcLbo, L.sbox);
+                const uint64_t dl = pwa::tc::sdesc(xa + L.pbx + ks * 2 * kTcLbo, kTcLbo, L.sbox);
+                pwa::tc::mma_bf16(dx, dh, dh, idesc, ks > 0);
+                pwa::tc::mma_bf16(dx, dh, dl, idesc, 1);
             }
             if (smp == 0) {
 #pragma unroll 1
                 for (int ks = 0; ks < 2; ++ks) {
-                    const uint64_t dh = pwa::tc::sdesc(za + ks * 2 * kTcLbo, kTcLbo, SBOZ);
-                    const uint64_t dl = pwa::tc::sdesc(za + PBZ + ks * 2 * kTcLbo, kTcLbo, SBOZ);
-                    pwa::tc::mma_bf16(tm + 128, dh, dh, idesc, ks > 0);
-                    pwa::tc::mma_bf16(tm + 128, dh, dl, idesc, 1);
-                    pwa::tc::mma_bf16(tm + 128, dl, dh, idesc, 1);
+                    const uint64_t dh = pwa::tc::sdesc(za + ks * 2 * kTcLbo, kTcLbo, L.sboz);
+                    const uint64_t dl = pwa::tc::sdesc(za + L.pbz + ks * 2 * kTcLbo, kTcLbo, L.sboz);
+                    pwa::tc::mma_bf16(dx + 128, dh, dh, idesc, ks > 0);
+                    pwa::tc::mma_bf16(dx + 128, dh, dl, idesc, 1);
                 }
             }
-            pwa::tc::mma_commit(&mbar[2]);
+            pwa::tc::mma_commit(&mbar[2 + b]);
         }
-        ++n_mma;
-        // ---- the tile's Gram sums from TMEM into registers ----
-        const bool done = pwa::mbar_wait(&mbar[2], mph, a.timeout_cycles);
-        mph ^= 1u;
-        if (!__syncthreads_and(done)) {
-            if (tid == 0) s_abort = 1;
-            break;
-        }
-        pwa::tc::fence_after();
-        // this thread's columns in 4-column loads, all in flight before one wait
-        {
-            uint32_t v[CPT / 4][4];
-#pragma unroll
-            for (int ch = 0; ch < CPT / 4; ++ch) tmem_ld4(tm + tlane + c0 + 4 * ch, v[ch]);
-            pwa::tc::tmem_wait();
-#pragma unroll
-            for (int ch = 0; ch < CPT / 4; ++ch)
-#pragma unroll
-                for (int u = 0; u < 4; ++u) ax[4 * ch + u] += __uint_as_float(v[ch][u]);
-        }
-        if (smp == 0) {
-            uint32_t v[CPT / 4][4];
-#pragma unroll
-            for (int ch = 0; ch < CPT / 4; ++ch) tmem_ld4(tm + 128 + tlane + c0 + 4 * ch, v[ch]);
-            pwa::tc::tmem_wait();
-#pragma unroll
-            for (int ch = 0; ch < CPT / 4; ++ch)
-#pragma unroll
-                for (int u = 0; u < 4; ++u) az[4 * ch + u] += __uint_as_float(v[ch][u]);
-        }
-        if (++win == kFold) {
-            fold(smp);
-            win = 0;
+        last_mma = i;
+        if (++win_q == kFold) {
+            fold_q(cur_q);
+            win_q = 0;
         }
         if (++st == 2) {
             st = 0;
             ph ^= 1u;
         }
-        pwa::tc::fence_before();
-        __syncthreads();  // TMEM read and operands consumed before the next tile rewrites them
+        // read back: two buffers, the previous tile's accumulators (this tile's MMAs
+        // meanwhile run); one buffer, this tile's.  Each thread waits for the MMAs
+        // itself, so its next operand writes and the next MMAs into the set it
+        // read (issued after the next barriers) follow its loads.
+        if constexpr (NBUF == 2) {
+            if (pend_smp >= 0) finish_tile(i - 1, pend_smp);
+            pend_smp = smp;
+        } else {
+            finish_tile(i, smp);
+        }
     }
-    if (s_abort) {
-        // a copy or the tile's MMAs never completed: report it, wait (bounded)
+    if (!aborted && NBUF == 2 && pend_smp >= 0) finish_tile(i - 1, pend_smp);
+    if (__syncthreads_or(failed)) aborted = true;
+    if (aborted) {
+        // a copy or a tile's MMAs never completed: report it, wait (bounded)
         // for what is still in flight, free TMEM
         if (tid == 0) {
             atomicOr(a.err, pwa::ERR_TIMEOUT);
             for (int s = 0; s < 2; ++s)
                 if (issued[s] >= 0) (void)pwa::mbar_wait(&mbar[s], (uint32_t)((issued[s] / 2) & 1), a.timeout_cycles);
-            if (n_mma > 0) (void)pwa::mbar_wait(&mbar[2], (uint32_t)((n_mma - 1) & 1), a.timeout_cycles);
+            for (long long j = last_mma; j >= 0 && j > last_mma - 2; --j) (void)wait_mma(j);
         }
     } else {
-        fold(cur_smp);
+        fold_g(cur_g);
+        fold_q(cur_q);
     }
     pwa::tc::fence_before();
     __syncthreads();
     pwa::tc::fence_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kTcTmemCols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(tc_tmem_cols(NBUF)));
 }
 
 // Fixed-order sum of the per-CTA records of each vector: out[bt] = sum over

@@ -102,18 +102,21 @@ def test_hessian_batch_matches_oracle_and_single_calls(name, nd, nm, B):
     from paper_2403_09225_b300 import binding
     wl, model = small_workload(name, nd, nm)
     L = binding.make_likelihood(wl)
-    ths = np.array(W.random_starts(wl, B))
+    # the oracle-checked rows at theta_true and an offset from it (as the
+    # parity tests); random starts of the prior for the rest
+    pts = points(wl, n_random=1)
+    ths = np.array([pts[0]] + [pts[0]] + [pts[1]] + list(W.random_starts(wl, B)))[:B]
     bad = wl.theta_true.copy()
     bad[0] = 1e30  # the first free magnitude (magnitudes lead theta): I overflows FP32
-    ths[1 % B] = bad if B > 1 else ths[0]
+    ths[1] = bad
     f, g, H, st = L.hessian_batch(ths)
     for b in range(B):
-        if B > 1 and b == 1:
+        if b == 1:
             assert st[b] == binding.PWA_ENONFINITE
             assert np.all(np.isnan(H[b]))
             continue
         assert st[b] == binding.PWA_OK
-        if b < 3:
+        if b in (0, 2):
             fo, go = oracle.nll_grad(model, ths[b], wl.data, wl.mc)
             Ho = oracle.hessian(model, ths[b], wl.data, wl.mc)
             assert abs(f[b] - fo) <= TOL_NLL * nll_scale(model, ths[b], wl, fo), (b, f[b], fo)
