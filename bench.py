@@ -591,9 +591,9 @@ def hessian_metric(L, wl, reps: int = 10):
         out["gram_tflops"] = flops / (ms * 1e-3) / 1e12
         out["roofline"] = {"bound": "tensor", "achieved": out["gram_tflops"], "unit": "TFLOP/s", "peak": peak,
                            "frac": out["gram_tflops"] / peak, "peak_kind": kind,
-                           "note": "useful Gram flops over the host call's time; the BF16 hi/lo split issues 3 "
-                                   "products per useful one, and the event phase (Breit-Wigner, coherent sums, "
-                                   "operand split) runs on the CUDA cores between the tiles' MMAs"}
+                           "note": "useful Gram flops over the host call's time; the BF16 hi/lo split issues 2 "
+                                   "products per useful one (hi^T hi, hi^T 2lo), and the event phase (Breit-Wigner, "
+                                   "coherent sums, operand split) runs on the CUDA cores while the tiles' MMAs run"}
     return out
 
 
