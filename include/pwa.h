@@ -483,6 +483,17 @@ int pwa_variant_num_params(const pwa_variant* v);
 pwa_status pwa_variant_eval(pwa_variant* v, const double* theta, const double* dir, double* nll,
                             double* grad, double* hv);
 
+/* pwa_variant_eval for B parameter vectors in one launch (each vector runs
+ * the single evaluation's blocks, so its results equal pwa_variant_eval's).
+ * theta, dir: host [B][P] (dir required when hv is non-NULL); nll: host [B];
+ * grad, hv: host [B][P] or NULL.  status: host [B], per vector PWA_OK,
+ * PWA_EINVAL (outside the model's domain, e.g. a mass below its pair
+ * threshold) or PWA_ENONFINITE; such a vector's outputs are not written.
+ * The call itself fails with PWA_EINVAL (B < 1, NULL or non-finite inputs),
+ * PWA_ENOMEM or PWA_ECUDA. */
+pwa_status pwa_variant_eval_batch(pwa_variant* v, int B, const double* theta, const double* dir, double* nll,
+                                  double* grad, double* hv, pwa_status* status);
+
 /* B Newton-CG fits (rows of theta0 [B][P]) in lockstep on the variant
  * likelihood; results as pwa_newton_cg_fit_batch. */
 pwa_status pwa_variant_fit(pwa_variant* v, int B, const double* theta0, const pwa_fit_opts* opts,

@@ -99,7 +99,7 @@ EXPORTS = ("pwa_create", "pwa_last_create_error", "pwa_num_params", "pwa_nll", "
            "pwa_mlp_gradients", "pwa_mlp_train_step", "pwa_mlp_params", "pwa_mlp_gemm_check",
            "pwa_mlp_last_error", "pwa_mlp_destroy", "pwa_accept_reject", "pwa_dalitz_histogram",
            "pwa_gather_events", "pwa_last_generate_error", "pwa_variant_create", "pwa_variant_num_params",
-           "pwa_variant_eval", "pwa_variant_fit", "pwa_variant_set_shapes", "pwa_variant_coupling_num_params",
+           "pwa_variant_eval", "pwa_variant_eval_batch", "pwa_variant_fit", "pwa_variant_set_shapes", "pwa_variant_coupling_num_params",
            "pwa_variant_coupling_eval", "pwa_variant_coupling_fit", "pwa_variant_last_error", "pwa_variant_destroy")
 
 
@@ -173,6 +173,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                     ctypes.POINTER(pwa_lineshape), i, i, i, vp]),
         "pwa_variant_num_params": (i, [vp]),
         "pwa_variant_eval": (st, [vp, dp, dp, dp, dp, dp]),
+        "pwa_variant_eval_batch": (st, [vp, i, dp, dp, dp, dp, dp, ip]),
         "pwa_variant_fit": (st, [vp, i, dp, ctypes.POINTER(pwa_fit_opts), dp, ctypes.POINTER(pwa_fit_result)]),
         "pwa_variant_set_shapes": (st, [vp, dp, dp]),
         "pwa_variant_coupling_num_params": (i, [vp]),
@@ -669,6 +670,25 @@ class Variant:
         hv = np.empty(self.P)
         self._check(lib().pwa_variant_eval(self._h, _dptr(th), _dptr(vv), ctypes.byref(f), _dptr(g), _dptr(hv)))
         return f.value, g, hv
+
+    def eval_batch(self, thetas, vs=None):
+        """(NLL [B], grad [B, P], H v [B, P] or None, status [B]) of B
+        parameter vectors in one launch; a vector outside the model's domain
+        or with a non-finite intensity has a non-zero status (its rows are NaN)."""
+        th = np.ascontiguousarray(np.asarray(thetas, dtype=np.float64).reshape(-1, self.P))
+        B = th.shape[0]
+        f = np.full(B, np.nan)
+        g = np.full((B, self.P), np.nan)
+        stat = np.zeros(B, dtype=np.int32)
+        sp = stat.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        if vs is None:
+            self._check(lib().pwa_variant_eval_batch(self._h, B, _dptr(th), None, _dptr(f), _dptr(g), None, sp))
+            return f, g, None, stat
+        vv = np.ascontiguousarray(np.asarray(vs, dtype=np.float64).reshape(B, self.P))
+        hv = np.full((B, self.P), np.nan)
+        self._check(lib().pwa_variant_eval_batch(self._h, B, _dptr(th), _dptr(vv), _dptr(f), _dptr(g), _dptr(hv),
+                                                 sp))
+        return f, g, hv, stat
 
     def fit(self, thetas0, xtol: float = 1e-8, gtol: float = 0.0, maxiter: int = 0, cg_maxiter: int = 0,
             time_limit_s: float = 0.0):

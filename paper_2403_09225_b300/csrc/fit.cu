@@ -1126,6 +1126,8 @@ struct VariantRounds final : RoundEvaluator {
     pwa_handle* h;
     int Pv;
     std::vector<double> th, vv, res;
+    std::vector<double> bf, bg, bh;  // batched evaluation: NLL [nb], gradient and H v [nb][P]
+    std::vector<pwa_status> bst;
     std::vector<int> errw;
     bool couplings_only;
     VariantRounds(pwa_variant* vr, int p, bool conly = false)
@@ -1147,13 +1149,35 @@ struct VariantRounds final : RoundEvaluator {
         const size_t ow = 1 + 2 * (size_t)Pv;
         res.assign((size_t)nb * ow, 0.0);
         errw.assign(nb, 0);
+        if (!couplings_only) {
+            // every row in one launch
+            bf.assign(nb, 0.0);
+            bg.assign((size_t)nb * Pv, 0.0);
+            bh.assign(any_hv ? (size_t)nb * Pv : 0, 0.0);
+            bst.assign(nb, PWA_OK);
+            pwa_status st = pwa::variant_eval_batch(v, nb, th.data(), any_hv ? vv.data() : nullptr, bf.data(),
+                                                    bg.data(), any_hv ? bh.data() : nullptr, bst.data());
+            if (st != PWA_OK) return st;
+            for (int b = 0; b < nb; ++b) {
+                double* r = res.data() + b * ow;
+                if (bst[b] != PWA_OK) {
+                    // a point outside the model's domain (non-finite intensity, a mass below its
+                    // threshold): the fit sees an error for this row and backs off
+                    errw[b] = 1;
+                    r[0] = std::numeric_limits<double>::infinity();
+                    continue;
+                }
+                r[0] = bf[b];
+                std::memcpy(r + 1, bg.data() + (size_t)b * Pv, sizeof(double) * Pv);
+                if (any_hv) std::memcpy(r + 1 + Pv, bh.data() + (size_t)b * Pv, sizeof(double) * Pv);
+            }
+            return PWA_OK;
+        }
         for (int b = 0; b < nb; ++b) {
             double* r = res.data() + b * ow;
             const double* tb = th.data() + (size_t)b * Pv;
             const double* vb = any_hv ? vv.data() + (size_t)b * Pv : nullptr;
-            pwa_status st = couplings_only
-                                ? pwa::variant_coupling_eval(v, tb, vb, r, r + 1, any_hv ? r + 1 + Pv : nullptr)
-                                : pwa::variant_eval(v, tb, vb, r, r + 1, any_hv ? r + 1 + Pv : nullptr);
+            pwa_status st = pwa::variant_coupling_eval(v, tb, vb, r, r + 1, any_hv ? r + 1 + Pv : nullptr);
             if (st == PWA_ENONFINITE || st == PWA_EINVAL) {
                 // a point outside the model's domain (non-finite intensity, a mass below its threshold):
                 // the fit sees an error for this row and backs off

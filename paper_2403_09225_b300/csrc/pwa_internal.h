@@ -183,6 +183,9 @@ pwa_handle* coupling_handle(const pwa_coupling* cp);
 // stream and the error text.
 pwa_status variant_eval(pwa_variant* v, const double* theta, const double* dir, double* nll, double* grad,
                         double* hv);
+// B evaluations in one launch (theta, dir [B][P]); status [B] per vector
+pwa_status variant_eval_batch(pwa_variant* v, int B, const double* theta, const double* dir, double* nll,
+                              double* grad, double* hv, pwa_status* status);
 pwa_handle* variant_base(pwa_variant* v);
 // The same with the couplings only, at the line shapes of the last pwa_variant_set_shapes.
 pwa_status variant_coupling_eval(pwa_variant* v, const double* theta_c, const double* dir_c, double* nll,

@@ -70,11 +70,14 @@ struct VarArgs {
     const float* w;         // data weights or null
     long long n[2];
     int K;
-    int blocks0;            // blocks of the data sample (the rest take the MC sample)
-    const VarRes* res;
-    double* rec;            // [warps][rec_len] per sample, data warps first
+    // B parameter vectors per launch: block i works for vector i / nbv, as
+    // block i mod nbv of that vector's nbv blocks
+    int nbv;
+    int blocks0;            // blocks of the data sample per vector (the rest take the MC sample)
+    const VarRes* res;      // [B][K]
+    double* rec;            // [B][nbv warps][rec_len], per vector data warps first
     int rec_len;
-    int* err;
+    int* err;               // [B]
 };
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
@@ -248,13 +251,14 @@ __global__ void __launch_bounds__(32 * kVarWarps) variant_kernel(const VarArgs a
     double* acc = reinterpret_cast<double*>(var_smem + ((32 * sizeof(VarRes) + 15) / 16) * 16 +
                                             kVarWarps * (NV * 33 * sizeof(float))) + warp * (32 * NV);
     const int K = a.K;
-    for (int i = threadIdx.x; i < K; i += blockDim.x) sres[i] = a.res[i];
+    const int vec = blockIdx.x / a.nbv, bx = blockIdx.x - vec * a.nbv;
+    for (int i = threadIdx.x; i < K; i += blockDim.x) sres[i] = a.res[(size_t)vec * K + i];
     for (int i = lane; i < 32 * NV; i += 32) acc[i] = 0.0;
     __syncthreads();
 
-    const int sample = blockIdx.x < a.blocks0 ? 0 : 1;
-    const int blk = sample ? blockIdx.x - a.blocks0 : blockIdx.x;
-    const int nblk = sample ? gridDim.x - a.blocks0 : a.blocks0;
+    const int sample = bx < a.blocks0 ? 0 : 1;
+    const int blk = sample ? bx - a.blocks0 : bx;
+    const int nblk = sample ? a.nbv - a.blocks0 : a.blocks0;
     const int wg = blk * kVarWarps + warp, nw = nblk * kVarWarps;
     const long long n = a.n[sample];
     const long long ntiles = (n + kVarE - 1) / kVarE;
@@ -377,13 +381,13 @@ __global__ void __launch_bounds__(32 * kVarWarps) variant_kernel(const VarArgs a
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
     }
     __syncwarp();
-    double* rec = a.rec + ((long long)(sample ? a.blocks0 * kVarWarps : 0) + wg) * a.rec_len;
+    double* rec = a.rec + ((long long)vec * a.nbv * kVarWarps + (sample ? a.blocks0 * kVarWarps : 0) + wg) * a.rec_len;
     for (int i = lane; i < 32 * NV; i += 32) rec[i] = acc[i];
     if (lane == 0) {
         rec[32 * NV] = s0;
         rec[32 * NV + 1] = s1;
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, 1);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err + vec, 1);
 }
 
 // Integral matrices of the MC sample at fixed line shapes:
@@ -483,11 +487,14 @@ __global__ void variant_tile_kernel(const float2* __restrict__ F, long long n, i
 // out[sample][j] = sum over the sample's warps of rec[warp][j], in a fixed order:
 // block x takes 32 consecutive slots (threadIdx.x, coalesced reads), and
 // thread row y sums the warps y, y + 32, ...; the 32 row sums are then added
-// in row order.
+// in row order.  Vector blockIdx.y: records [warps0 + warps1][rec_len] from
+// rec + y (warps0 + warps1) rec_len, sums [2 rec_len] at out + y 2 rec_len.
 __global__ void __launch_bounds__(1024) variant_reduce_kernel(const double* __restrict__ rec, int rec_len, int warps0,
                                                               int warps1, double* __restrict__ out)
 {
     __shared__ double part[32][33];
+    rec += (size_t)blockIdx.y * (warps0 + warps1) * rec_len;
+    out += (size_t)blockIdx.y * 2 * rec_len;
     const int j = blockIdx.x * 32 + threadIdx.x;
     const bool ok = j < 2 * rec_len;
     const int sample = ok ? j / rec_len : 0, slot = ok ? j % rec_len : 0;
@@ -589,13 +596,14 @@ struct pwa_variant {
     float* d_m2[2] = {nullptr, nullptr};
     float2* d_F[2] = {nullptr, nullptr};
     float* d_w = nullptr;
-    VarRes* d_res = nullptr;
-    double* d_rec = nullptr;
-    double* d_sums = nullptr;
-    int* d_err = nullptr;
-    double* h_sums = nullptr;  // pinned: 2 rec_len sums + the error word
-    int rec_len = 0, blocks0 = 0, blocks1 = 0;
-    VarRes* h_res = nullptr;   // pinned
+    // per-vector buffers, room for vcap parameter vectors (one pass evaluates up to vcap)
+    VarRes* d_res = nullptr;   // [vcap][K]
+    double* d_rec = nullptr;   // [vcap][(blocks0 + blocks1) warps][rec_len]
+    double* d_sums = nullptr;  // [vcap][2 rec_len]
+    int* d_err = nullptr;      // [vcap]
+    double* h_sums = nullptr;  // pinned: [vcap][2 rec_len] sums, then vcap error words
+    int rec_len = 0, blocks0 = 0, blocks1 = 0, vcap = 0;
+    VarRes* h_res = nullptr;   // pinned [vcap][K]
     // coupling-only evaluation at fixed line shapes: the shape parameters and
     // the MC integral matrices Phi [S][K][K] (complex FP64, host)
     int Pc = 0;                       // coupling parameters at the head of theta
@@ -622,9 +630,42 @@ pwa_status vfail(pwa_variant* v, pwa_status st, const std::string& msg) { return
 
 int NC_of(const pwa_variant* v) { return v->per_projection ? v->base.S : 1; }
 
-// host: per-resonance constants for theta (and direction v, may be null)
-pwa_status fill_res(pwa_variant* vv, const double* theta, const double* dir)
+// room for B parameter vectors in the per-vector buffers (grown, never shrunk;
+// the error words start at zero)
+pwa_status reserve_vectors(pwa_variant* v, int B)
 {
+    if (B <= v->vcap) return PWA_OK;
+    cudaStream_t st = v->base.stream;
+    VAR_CUDA(v, cudaStreamSynchronize(st));
+    if (v->d_rec) cudaFree(v->d_rec);
+    if (v->d_sums) cudaFree(v->d_sums);
+    if (v->d_res) cudaFree(v->d_res);
+    if (v->d_err) cudaFree(v->d_err);
+    if (v->h_sums) cudaFreeHost(v->h_sums);
+    if (v->h_res) cudaFreeHost(v->h_res);
+    v->d_rec = v->d_sums = v->h_sums = nullptr;
+    v->d_res = v->h_res = nullptr;
+    v->d_err = nullptr;
+    v->vcap = 0;
+    const int K = v->base.K;
+    const size_t warps = (size_t)(v->blocks0 + v->blocks1) * kVarWarps, rl = (size_t)v->rec_len;
+    VAR_CUDA(v, cudaMalloc(&v->d_rec, sizeof(double) * B * warps * rl));
+    VAR_CUDA(v, cudaMalloc(&v->d_sums, sizeof(double) * B * 2 * rl));
+    VAR_CUDA(v, cudaMalloc(&v->d_res, sizeof(VarRes) * B * K));
+    VAR_CUDA(v, cudaMalloc(&v->d_err, sizeof(int) * B));
+    VAR_CUDA(v, cudaMemsetAsync(v->d_err, 0, sizeof(int) * B, st));
+    VAR_CUDA(v, cudaMallocHost(&v->h_sums, sizeof(double) * B * (2 * rl + 1)));
+    VAR_CUDA(v, cudaMallocHost(&v->h_res, sizeof(VarRes) * B * K));
+    VAR_CUDA(v, cudaStreamSynchronize(st));
+    v->vcap = B;
+    return PWA_OK;
+}
+
+// host: per-resonance constants for theta (and direction v, may be null) into
+// out [K] (the first vector's slot when null)
+pwa_status fill_res(pwa_variant* vv, const double* theta, const double* dir, VarRes* out = nullptr)
+{
+    if (!out) out = vv->h_res;
     const int K = vv->base.K, S = vv->base.S, NC = NC_of(vv);
     std::vector<double> mag((size_t)K * NC), ph((size_t)K * NC), M(K), w1(K), w2(K);
     std::vector<double> vmag((size_t)K * NC, 0.0), vph((size_t)K * NC, 0.0), vM(K, 0.0), vw1(K, 0.0), vw2(K, 0.0);
@@ -649,7 +690,7 @@ pwa_status fill_res(pwa_variant* vv, const double* theta, const double* dir)
         }
     }
     for (int k = 0; k < K; ++k) {
-        VarRes& r = vv->h_res[k];
+        VarRes& r = out[k];
         std::memset(&r, 0, sizeof(r));
         const pwa_lineshape& sh = vv->shapes[k];
         r.ch = vv->table[k].channel;
@@ -886,14 +927,7 @@ pwa_status create_impl(pwa_variant* v, const pwa_events* data, const pwa_events*
     v->blocks1 = (int)b1;
     const int NP = 2 * NC + 3;
     v->rec_len = 32 * 2 * NP + 2;
-    VAR_CUDA(v, cudaMalloc(&v->d_rec, sizeof(double) * (size_t)(b0 + b1) * kVarWarps * v->rec_len));
-    VAR_CUDA(v, cudaMalloc(&v->d_sums, sizeof(double) * 2 * (size_t)v->rec_len));
-    VAR_CUDA(v, cudaMalloc(&v->d_res, sizeof(VarRes) * K));
-    VAR_CUDA(v, cudaMalloc(&v->d_err, sizeof(int)));
-    VAR_CUDA(v, cudaMemsetAsync(v->d_err, 0, sizeof(int), v->base.stream));
-    VAR_CUDA(v, cudaMallocHost(&v->h_sums, sizeof(double) * (2 * (size_t)v->rec_len + 1)));
-    VAR_CUDA(v, cudaMallocHost(&v->h_res, sizeof(VarRes) * K));
-    VAR_CUDA(v, cudaStreamSynchronize(v->base.stream));
+    VAR_TRY(reserve_vectors(v, 1));
     return PWA_OK;
 }
 
@@ -901,15 +935,29 @@ pwa_status create_impl(pwa_variant* v, const pwa_events* data, const pwa_events*
 
 namespace pwa {
 
-// One pass of the variant kernel at host theta (and direction dir when hv):
-// the data sample, and the MC sample unless data_only; leaves the summed
-// records in v->h_sums (data, then MC).
-static pwa_status run_pass(pwa_variant* v, const double* theta, const double* dir, bool hv, bool data_only)
+// One pass of the variant kernel for B parameter vectors (host theta [B][P],
+// direction dir [B][P] when hv): the data sample, and the MC sample unless
+// data_only; leaves the summed records in v->h_sums (per vector: data, then
+// MC) and a per-vector error word (non-finite intensity) in bad[B].  A vector
+// whose parameters are outside the model's domain (fill_res fails) gets
+// PWA_EINVAL in vstat and the constants of another vector (its sums are not
+// used); vstat [B] receives PWA_OK, PWA_EINVAL or PWA_ENONFINITE.
+static pwa_status run_pass_b(pwa_variant* v, int B, const double* theta, const double* dir, bool hv, bool data_only,
+                             pwa_status* vstat)
 {
-    const int K = v->base.K, S = v->base.S;
-    VAR_TRY(fill_res(v, theta, hv ? dir : nullptr));
+    const int K = v->base.K, S = v->base.S, P = v->base.P;
+    VAR_TRY(reserve_vectors(v, B));
+    int valid = -1;
+    for (int b = 0; b < B; ++b) {
+        vstat[b] = fill_res(v, theta + (size_t)b * P, hv ? dir + (size_t)b * P : nullptr, v->h_res + (size_t)b * K);
+        if (vstat[b] == PWA_OK && valid < 0) valid = b;
+    }
+    if (valid < 0) return vstat[0];
+    for (int b = 0; b < B; ++b)
+        if (vstat[b] != PWA_OK) std::memcpy(v->h_res + (size_t)b * K, v->h_res + (size_t)valid * K, sizeof(VarRes) * K);
+    v->base.err.clear();
     cudaStream_t st = v->base.stream;
-    VAR_CUDA(v, cudaMemcpyAsync(v->d_res, v->h_res, sizeof(VarRes) * K, cudaMemcpyHostToDevice, st));
+    VAR_CUDA(v, cudaMemcpyAsync(v->d_res, v->h_res, sizeof(VarRes) * K * B, cudaMemcpyHostToDevice, st));
     VarArgs a{};
     a.m2[0] = v->d_m2[0];
     a.m2[1] = v->d_m2[1];
@@ -922,6 +970,7 @@ static pwa_status run_pass(pwa_variant* v, const double* theta, const double* di
     // data only: the whole grid takes the data sample (the records hold that many warps)
     const int blocks0 = data_only ? v->blocks0 + v->blocks1 : v->blocks0;
     const int blocks1 = data_only ? 0 : v->blocks1;
+    a.nbv = blocks0 + blocks1;
     a.blocks0 = blocks0;
     a.res = v->d_res;
     a.rec = v->d_rec;
@@ -931,29 +980,39 @@ static pwa_status run_pass(pwa_variant* v, const double* theta, const double* di
     if (!fn) return vfail(v, PWA_EINVAL, "no variant kernel for this S");
     const size_t smem = var_smem_for(S, v->per_projection != 0);
     VAR_CUDA(v, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    fn<<<blocks0 + blocks1, 32 * kVarWarps, smem, st>>>(a);
+    fn<<<a.nbv * B, 32 * kVarWarps, smem, st>>>(a);
     VAR_CUDA(v, cudaGetLastError());
-    variant_reduce_kernel<<<(2 * v->rec_len + 31) / 32, dim3(32, 32), 0, st>>>(
+    variant_reduce_kernel<<<dim3((2 * v->rec_len + 31) / 32, B), dim3(32, 32), 0, st>>>(
         v->d_rec, v->rec_len, blocks0 * kVarWarps, blocks1 * kVarWarps, v->d_sums);
     VAR_CUDA(v, cudaGetLastError());
-    VAR_CUDA(v, cudaMemcpyAsync(v->h_sums, v->d_sums, sizeof(double) * 2 * v->rec_len, cudaMemcpyDeviceToHost, st));
-    VAR_CUDA(v, cudaMemcpyAsync(v->h_sums + 2 * v->rec_len, v->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    VAR_CUDA(v, cudaMemsetAsync(v->d_err, 0, sizeof(int), st));
+    const size_t ns = (size_t)B * 2 * v->rec_len;
+    int* h_err = reinterpret_cast<int*>(v->h_sums + ns);
+    VAR_CUDA(v, cudaMemcpyAsync(v->h_sums, v->d_sums, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
+    VAR_CUDA(v, cudaMemcpyAsync(h_err, v->d_err, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+    VAR_CUDA(v, cudaMemsetAsync(v->d_err, 0, sizeof(int) * B, st));
     VAR_CUDA(v, cudaStreamSynchronize(st));
-    int errw = 0;
-    std::memcpy(&errw, v->h_sums + 2 * v->rec_len, sizeof(int));
-    if (errw) return vfail(v, PWA_ENONFINITE, "an event's intensity is not finite, or not positive for a data event");
+    for (int b = 0; b < B; ++b)
+        if (vstat[b] == PWA_OK && h_err[b]) vstat[b] = PWA_ENONFINITE;
     return PWA_OK;
 }
 
-// One evaluation (NLL, and the gradient and H v when asked) at host theta, v.
-pwa_status variant_eval(pwa_variant* v, const double* theta, const double* dir, double* nll, double* grad, double* hv)
+// The single-vector pass: an error status (with its message) when the vector failed.
+static pwa_status run_pass(pwa_variant* v, const double* theta, const double* dir, bool hv, bool data_only)
+{
+    pwa_status vs = PWA_OK;
+    VAR_TRY(run_pass_b(v, 1, theta, dir, hv, data_only, &vs));
+    if (vs == PWA_ENONFINITE)
+        return vfail(v, PWA_ENONFINITE, "an event's intensity is not finite, or not positive for a data event");
+    if (vs != PWA_OK) return fill_res(v, theta, hv ? dir : nullptr);  // repeats the domain error with its message
+    return PWA_OK;
+}
+
+// Eqs. 3, 6, 7 from one vector's sums (data sd, MC sm: per resonance
+// [G NP][H NP], then sum w ln I for data and sum I, sum Idot for MC).
+static pwa_status combine_sums(pwa_variant* v, const double* sd, const double* sm, double* nll, double* grad,
+                               double* hv)
 {
     const int P = v->base.P, NC = NC_of(v), NP = 2 * NC + 3;
-    VAR_TRY(run_pass(v, theta, dir, hv != nullptr, false));
-    // Eqs. 3, 6, 7 from the sums
-    const double* sd = v->h_sums;                 // data: per resonance [G NP][H NP], then sum w ln I
-    const double* sm = v->h_sums + v->rec_len;    // MC: per resonance [G NP][H NP], then sum I, sum Idot
     const double SL = sd[32 * 2 * NP], G = sm[32 * 2 * NP], Gd = sm[32 * 2 * NP + 1];
     if (!(G > 0.0) || !std::isfinite(SL)) return vfail(v, PWA_ENONFINITE, "the MC normalisation is not positive");
     const double Nd = v->base.Nd;
@@ -968,6 +1027,34 @@ pwa_status variant_eval(pwa_variant* v, const double* theta, const double* dir, 
             if (hv) hv[i] = -hD + Nd * (hM / G - gM * Gd / (G * G));
         }
     }
+    return PWA_OK;
+}
+
+// One evaluation (NLL, and the gradient and H v when asked) at host theta, v.
+pwa_status variant_eval(pwa_variant* v, const double* theta, const double* dir, double* nll, double* grad, double* hv)
+{
+    VAR_TRY(run_pass(v, theta, dir, hv != nullptr, false));
+    return combine_sums(v, v->h_sums, v->h_sums + v->rec_len, nll, grad, hv);
+}
+
+// B evaluations in one launch (theta, dir [B][P]; nll [B]; grad, hv [B][P] or
+// null): each vector runs the single pass's blocks, so its results equal
+// variant_eval's.  status [B]: PWA_OK, PWA_EINVAL (outside the model's
+// domain) or PWA_ENONFINITE per vector; the call fails only on CUDA or
+// allocation errors.
+pwa_status variant_eval_batch(pwa_variant* v, int B, const double* theta, const double* dir, double* nll,
+                              double* grad, double* hv, pwa_status* status)
+{
+    const int P = v->base.P;
+    VAR_TRY(run_pass_b(v, B, theta, dir, hv != nullptr, false, status));
+    const size_t rl = (size_t)v->rec_len;
+    for (int b = 0; b < B; ++b) {
+        if (status[b] != PWA_OK) continue;
+        const double* sd = v->h_sums + (size_t)b * 2 * rl;
+        status[b] = combine_sums(v, sd, sd + rl, nll + b, grad ? grad + (size_t)b * P : nullptr,
+                                 hv ? hv + (size_t)b * P : nullptr);
+    }
+    v->base.err.clear();
     return PWA_OK;
 }
 
@@ -1168,6 +1255,19 @@ pwa_status pwa_variant_eval(pwa_variant* v, const double* theta, const double* d
         grad = g_tmp.data();
     }
     return pwa::variant_eval(v, theta, dir, nll, grad, hv);
+}
+
+pwa_status pwa_variant_eval_batch(pwa_variant* v, int B, const double* theta, const double* dir, double* nll,
+                                  double* grad, double* hv, pwa_status* status)
+{
+    if (!v) return PWA_EINVAL;
+    v->base.err.clear();
+    if (B < 1 || !theta || !nll || !status) return vfail(v, PWA_EINVAL, "B >= 1, theta, nll and status are required");
+    if (hv && !dir) return vfail(v, PWA_EINVAL, "v is required for hv");
+    for (size_t i = 0; i < (size_t)B * v->base.P; ++i)
+        if (!std::isfinite(theta[i]) || (hv && !std::isfinite(dir[i])))
+            return vfail(v, PWA_EINVAL, "theta and v must be finite");
+    return pwa::variant_eval_batch(v, B, theta, dir, nll, grad, hv, status);
 }
 
 pwa_status pwa_variant_set_shapes(pwa_variant* v, const double* theta, double* phi_out)

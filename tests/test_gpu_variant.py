@@ -125,6 +125,38 @@ def test_variant_rejects_a_mass_below_its_threshold():
     Lv.close()
 
 
+@pytest.mark.parametrize("name,per_projection", [("tiny", False), ("k7s3", True)])
+def test_variant_batch_equals_single_evaluations(name, per_projection):
+    """B vectors in one launch: every vector runs the single evaluation's
+    blocks, so NLL, gradient and H v equal pwa_variant_eval's bit for bit; a
+    vector with a mass below its pair threshold gets PWA_EINVAL and one with
+    an overflowing intensity PWA_ENONFINITE, without disturbing the others."""
+    from paper_2403_09225_b300 import binding
+    cfg, table, vm, wl = variant_case(name, per_projection)
+    Lv = make_variant(cfg, table, vm, wl)
+    rng = np.random.default_rng(3)
+    P = vm.P
+    ths = np.array([vm.theta0() * (1 + 0.02 * rng.standard_normal(P)) for _ in range(6)])
+    vs = rng.standard_normal((6, P))
+    lay = vm.layout()
+    k_md = [k for k, sh in enumerate(vm.shapes) if sh.kind == V.KIND_MASS_DEPENDENT][0]
+    i_m = [j for j, (n, k, _) in enumerate(lay) if n == "mass" and k == k_md][0]
+    i_mag = [j for j, (n, _, _) in enumerate(lay) if n == "mag"][0]
+    sh = vm.shapes[k_md]
+    ths[2, i_m] = max(sh.ma, sh.mb)  # between |ma - mb| and ma + mb: q^2 < 0, outside the model's domain
+    ths[4, i_mag] = 1e30  # the intensity overflows FP32
+    for with_v in (False, True):
+        f, g, hv, st = Lv.eval_batch(ths, vs if with_v else None)
+        assert st[2] == binding.PWA_EINVAL and st[4] == binding.PWA_ENONFINITE
+        for b in (0, 1, 3, 5):
+            assert st[b] == binding.PWA_OK
+            f1, g1, hv1 = Lv.eval(ths[b], vs[b] if with_v else None)
+            assert f[b] == f1 and np.array_equal(g[b], g1)
+            if with_v:
+                assert np.array_equal(hv[b], hv1)
+    Lv.close()
+
+
 def _canonical(vm, th):
     th = np.array(th, dtype=float)
     lay = vm.layout()
