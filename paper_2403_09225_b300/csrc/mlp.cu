@@ -10,6 +10,7 @@
 // operands it needs with explicit transpose kernels.  Loss: squared error on
 // the standardised outputs, 1 - cos(difference) on outputs flagged periodic
 // (phases); Adam on FP32 master weights, whose BF16 copies the products read.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -27,10 +28,12 @@ namespace {
 
 // ---------------------------------------------------------------------------
 // GEMM: 128 x 64 output tile per CTA, K in chunks of 64 staged in shared memory
+// by TMA tensor copies, kGStages chunks in flight
 // ---------------------------------------------------------------------------
 
 constexpr int kGM = 128, kGN = 64, kGK = 64;  // tile; K chunk (four MMAs of K = 16)
 constexpr int kGThreads = 128;                // 4 warps: one per TMEM lane quarter
+constexpr int kGStages = 4;                   // K chunks in flight
 
 using pwa::tc::mma_bf16;
 using pwa::tc::mma_commit;
@@ -38,17 +41,23 @@ using pwa::tc::sa;
 using pwa::tc::sdesc;
 
 // C = A B^T: A [M][K], B [N][K] BF16 row-major with leading dimensions lda, ldb
-// (elements); C [M][N] FP32 with ldc.  M % 128 == 0, N % 64 == 0, K % 64 == 0,
-// leading dimensions multiples of 8.  Split K: CTA z of gridDim.z takes the
-// K chunks [z n / Z, (z + 1) n / Z) of the n = K / 64 and writes its partial
-// product to C + z split_stride (a workspace the caller reduces in fixed order).
-constexpr int kGStageBytes = (kGM + kGN) * kGK * 2;  // one K chunk of A and B: 24 KB
-constexpr int kGSmem = 2 * kGStageBytes + 1024;         // two stages + alignment slack
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
+// (elements), read through tensor maps (tmA, tmB: 2D, K innermost, boxes of
+// 8 K x 128 rows and 8 K x 64 rows); C [M][N] FP32 with ldc.  M % 128 == 0,
+// N % 64 == 0, K % 64 == 0, leading dimensions multiples of 8.  Split K: CTA z
+// of gridDim.z takes the K chunks [z n / Z, (z + 1) n / Z) of the n = K / 64
+// and writes its partial product to C + z split_stride (a workspace the
+// caller reduces in fixed order).
+//
+// Shared memory per stage: the A chunk as eight 8-K slices of 128 rows x 16
+// bytes (slice j at j 2048: element (r, k) at (k >> 3) 2048 + r 16 + (k & 7) 2),
+// then the B chunk likewise with 64 rows (slice stride 1024).  That is the
+// canonical K-major layout without swizzle, core matrices of 8 rows x 16
+// bytes: LBO (between core matrices along K) = rows x 16, SBO (between 8-row
+// groups) = 128.  Each slice is one TMA tensor copy (16 per chunk, issued by
+// one thread with the stage's transaction count).
+constexpr int kGABytes = kGM * kGK * 2, kGBBytes = kGN * kGK * 2;
+constexpr int kGStageBytes = kGABytes + kGBBytes;         // 24 KB
+constexpr int kGSmem = kGStages * kGStageBytes + 1024;     // stages + alignment slack
 
 // Bounded wait for phase `parity` of an mbarrier; false when the limit ran out.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long timeout)
@@ -71,27 +80,40 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     }
 }
 
-__global__ void __launch_bounds__(kGThreads, 1) gemm_bf16_kernel(const __nv_bfloat16* __restrict__ A, int lda,
-                                                                const __nv_bfloat16* __restrict__ B, int ldb,
+// one 2D tensor-map box (x = K element, y = row) into shared memory, counted on bar
+__device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(kGThreads, 1) gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                const __grid_constant__ CUtensorMap tmB,
                                                                 float* __restrict__ C, int ldc,
                                                                 long long split_stride, int K,
                                                                 long long timeout, int* err)
 {
-    // per stage: A chunk 128 rows x 64 K (16 8-row groups of 8 core matrices, SBO 1024),
-    // then B chunk 64 rows (SBO 1024); element (r, k) of a chunk at (r >> 3) 1024 + (k >> 3) 128 + (r & 7) 16
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t full[kGStages], empty[kGStages];  // chunk landed / its MMAs done
     __shared__ uint32_t tslot;
+    __shared__ int s_ok;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * kGM, n0 = blockIdx.x * kGN;
     const int nchunk = K / kGK, z = blockIdx.z, Z = gridDim.z;
     const int cbeg = (int)((long long)z * nchunk / Z), cend = (int)((long long)(z + 1) * nchunk / Z);
+    const int n = cend - cbeg;
     C += (long long)z * split_stride;
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(&bar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(&bar[1])));
+        for (int s = 0; s < kGStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(&full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(&empty[s])));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_ok = 1;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(sa(&tslot)));
@@ -104,64 +126,68 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_bf16_kernel(const __nv_bflo
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kGN >> 3) << 17) | ((uint32_t)(kGM >> 4) << 24);
     const uint32_t s0 = sa(smem);
 
-    // 16-byte pieces of chunk c into stage st: A 8 per thread, B 4 per thread, all in flight together
-    auto load_chunk = [&](int c, int st) {
-        const int k0 = c * kGK;
-        const uint32_t dA = s0 + st * kGStageBytes, dB = dA + kGM * kGK * 2;
+    if (tid == 0) {
+        // chunk i (of this CTA's n) goes to stage i mod kGStages, its (i / kGStages)-th use
+        auto issue = [&](int i) {
+            const int st = i % kGStages, k0 = (cbeg + i) * kGK;
+            const uint32_t dA = s0 + st * kGStageBytes, dB = dA + kGABytes, fb = sa(&full[st]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kGStageBytes)
+                         : "memory");
 #pragma unroll
-        for (int i = 0; i < kGM * (kGK / 8) / kGThreads; ++i) {
-            const int p = tid + i * kGThreads, r = p >> 3, q = p & 7;
-            cp_async16(dA + (r >> 3) * 1024 + q * 128 + (r & 7) * 16, A + (size_t)(m0 + r) * lda + k0 + 8 * q);
-        }
-#pragma unroll
-        for (int i = 0; i < kGN * (kGK / 8) / kGThreads; ++i) {
-            const int p = tid + i * kGThreads, r = p >> 3, q = p & 7;
-            cp_async16(dB + (r >> 3) * 1024 + q * 128 + (r & 7) * 16, B + (size_t)(n0 + r) * ldb + k0 + 8 * q);
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-
-    bool ok = true;
-    uint32_t ph = 0u;  // bit b: parity of the next phase of bar[b] to wait for
-    if (cbeg < cend) load_chunk(cbeg, 0);
-    for (int c = cbeg; c < cend; ++c) {
-        const int i = c - cbeg, st = i & 1;
-        if (c + 1 < cend) {
-            // stage st ^ 1 was read by the MMAs of chunk c - 1: wait for them before refilling it
-            if (i >= 1) {
-                ok = mbar_wait_bounded(sa(&bar[st ^ 1]), (ph >> (st ^ 1)) & 1u, timeout);
-                ph ^= 1u << (st ^ 1);
+            for (int j = 0; j < kGK / 8; ++j) {
+                tma_box(dA + j * (kGM * 16), &tmA, k0 + 8 * j, m0, fb);
+                tma_box(dB + j * (kGN * 16), &tmB, k0 + 8 * j, n0, fb);
             }
-            ok = __syncthreads_and(ok);
+        };
+        // chunks whose copies were issued / whose MMAs were committed
+        int issued = 0, committed = 0;
+        bool ok = true;
+        for (; issued < n && issued < kGStages; ++issued) issue(issued);
+        while (committed < n) {
+            const int c = committed, st = c % kGStages;
+            ok = mbar_wait_bounded(sa(&full[st]), (uint32_t)((c / kGStages) & 1), timeout);
             if (!ok) break;
-            load_chunk(c + 1, st ^ 1);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) {
-            const uint32_t dA = s0 + st * kGStageBytes, dB = dA + kGM * kGK * 2;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t dA = s0 + st * kGStageBytes, dB = dA + kGABytes;
 #pragma unroll
             for (int ks = 0; ks < kGK / 16; ++ks) {
-                const uint64_t ad = sdesc(dA + ks * 256, 128, 1024), bd = sdesc(dB + ks * 256, 128, 1024);
-                mma_bf16(tm, ad, bd, idesc, (i > 0 || ks > 0) ? 1u : 0u);
+                const uint64_t ad = sdesc(dA + ks * 2 * (kGM * 16), kGM * 16, 128);
+                const uint64_t bd = sdesc(dB + ks * 2 * (kGN * 16), kGN * 16, 128);
+                mma_bf16(tm, ad, bd, idesc, (c > 0 || ks > 0) ? 1u : 0u);
             }
-            mma_commit(&bar[st]);
+            mma_commit(&empty[st]);
+            ++committed;
+            // refill the stage of chunk c - 1 (issued = c - 1 + kGStages) once its MMAs have read
+            // it; chunk c's MMAs are queued meanwhile, so the tensor cores keep working
+            if (c >= 1 && issued < n) {
+                const int sp = (c - 1) % kGStages;
+                ok = mbar_wait_bounded(sa(&empty[sp]), (uint32_t)(((c - 1) / kGStages) & 1), timeout);
+                if (!ok) break;
+                issue(issued++);
+            }
+        }
+        // the last chunk's MMAs (and with them every earlier one) before the accumulator is read
+        if (ok && n > 0) ok = mbar_wait_bounded(sa(&empty[(n - 1) % kGStages]), (uint32_t)(((n - 1) / kGStages) & 1), timeout);
+        if (!ok) {
+            // wait (bounded) for the copies and MMAs still in flight: each stage's last armed phase
+            for (int s = 0; s < kGStages; ++s) {
+                if (issued > s) {
+                    const int last = issued - 1 - (issued - 1 - s) % kGStages;  // last chunk copied into stage s
+                    (void)mbar_wait_bounded(sa(&full[s]), (uint32_t)((last / kGStages) & 1), timeout);
+                }
+                if (committed > s) {
+                    const int last = committed - 1 - (committed - 1 - s) % kGStages;  // last chunk computed from s
+                    (void)mbar_wait_bounded(sa(&empty[s]), (uint32_t)((last / kGStages) & 1), timeout);
+                }
+            }
+            s_ok = 0;
         }
     }
-    // the last chunk's MMAs (and with them every earlier one) before the accumulator is read
-    if (ok && cend > cbeg) {
-        const int st = (cend - 1 - cbeg) & 1;
-        ok = mbar_wait_bounded(sa(&bar[st]), (ph >> st) & 1u, timeout);
-    }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    ok = __syncthreads_and(ok);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok && cend > cbeg) {
+    const bool ok = s_ok != 0;
+    if (ok && n > 0) {
         // row m0 + 32 warp + lane of C from TMEM lane 32 warp + lane
         const int m = m0 + 32 * warp + lane;
         for (int c0 = 0; c0 < kGN; c0 += 16) {
@@ -396,23 +422,63 @@ int k_splits(int M, int N, int K)
     return std::max(1, std::min(z, chunks / 2));
 }
 
+// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point query
+// (no link against the driver library); null when the driver does not offer it
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled()
+{
+    static const EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (EncodeTiledFn) nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// 2D map of a row-major BF16 matrix [rows][K] (leading dimension ld elements):
+// K innermost, boxes of 8 K x box_rows rows, no swizzle
+bool bf16_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int K, int ld, int box_rows)
+{
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {8, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // C[M][N] = A[M][K] B[N][K]^T on the tensor cores (split K through the workspace when it pays)
 pwa_status gemm(pwa_mlp* m, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, float* C, int ldc, int M,
                 int N, int K)
 {
-    if (M % kGM || N % kGN || K % kGK || lda % 8 || ldb % 8)
+    if (M % kGM || N % kGN || K % kGK || lda % 8 || ldb % 8 || lda < K || ldb < K)
         return mlp_fail(m, PWA_EINVAL, "internal: GEMM shape not tile-aligned");
+    if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) % 16)
+        return mlp_fail(m, PWA_EINVAL, "internal: GEMM operands not 16-byte aligned");
+    CUtensorMap tmA, tmB;
+    if (!bf16_map(&tmA, A, M, K, lda, kGM) || !bf16_map(&tmB, B, N, K, ldb, kGN))
+        return mlp_fail(m, PWA_ECUDA, "tensor map encoding failed for a GEMM operand");
     const int Z = k_splits(M, N, K);
     if (Z > 1 && (size_t)Z * M * N > m->ws_floats) return mlp_fail(m, PWA_EINVAL, "internal: split-K workspace too small");
     dim3 grid(N / kGN, M / kGM, Z);
     if (Z == 1) {
-        gemm_bf16_kernel<<<grid, kGThreads, kGSmem, m->stream>>>(A, lda, B, ldb, C, ldc, 0, K, m->timeout, m->d_err);
+        gemm_bf16_kernel<<<grid, kGThreads, kGSmem, m->stream>>>(tmA, tmB, C, ldc, 0, K, m->timeout, m->d_err);
         MLP_CUDA(m, cudaGetLastError());
         return PWA_OK;
     }
     const long long stride = (long long)M * N;
-    gemm_bf16_kernel<<<grid, kGThreads, kGSmem, m->stream>>>(A, lda, B, ldb, m->ws, N, stride, K, m->timeout,
-                                                             m->d_err);
+    gemm_bf16_kernel<<<grid, kGThreads, kGSmem, m->stream>>>(tmA, tmB, m->ws, N, stride, K, m->timeout, m->d_err);
     MLP_CUDA(m, cudaGetLastError());
     split_reduce_kernel<<<blocks_for(stride), 256, 0, m->stream>>>(m->ws, N, stride, Z, M, N, C, ldc);
     MLP_CUDA(m, cudaGetLastError());
