@@ -136,6 +136,12 @@ typedef struct {
     pwa_fit_iter* trace;  /* host [fits][trace_cap] or NULL: per-iteration record;
                              fits are numbered in the order of theta0 (over all
                              handles in order for pwa_newton_cg_fit_multi)     */
+    int one_launch;       /* pwa_newton_cg_fit_multi only: 1: every f, g round is
+                             one pwa_eval_multi_device launch over all handles
+                             (when each has K <= 32); 0 (default): one batched
+                             launch per handle, each on its own stream (faster
+                             on the measured toys: the per-handle instances
+                             are tuned for their K, S)                        */
 } pwa_fit_opts;
 
 typedef enum {
@@ -359,8 +365,8 @@ pwa_status pwa_newton_cg_fit_batch(pwa_handle* h, int B, const double* theta0,
  * vector and per handle) are reported by pwa_sync(handle) once the stream
  * has been synchronised.  Grows each handle's batch scratch as
  * pwa_eval_batch_device does.  want_grad or want_hv must be set.
- * pwa_newton_cg_fit_multi uses this launch for its rounds when every handle
- * has K <= 32. */
+ * pwa_newton_cg_fit_multi uses this launch for its rounds when asked to
+ * (pwa_fit_opts.one_launch) and every handle has K <= 32. */
 pwa_status pwa_eval_multi_device(int n, pwa_handle* const* handles, const int* B, const double* const* d_theta,
                                  const double* const* d_v, double* const* d_out, int want_grad, int want_hv,
                                  void* stream);
@@ -373,10 +379,11 @@ pwa_status pwa_eval_multi_device(int n, pwa_handle* const* handles, const int* B
  * it per handle).  theta0[i], theta_out[i]: host [B[i]][P_i]; results[i]: host
  * [B[i]] (results may be NULL).  A handle may appear only once.  Returns as
  * pwa_newton_cg_fit_batch; an error on one handle (its pwa_last_error says
- * which) stops all fits.  With two or more handles, all with K <= 32, every
- * round is one pwa_eval_multi_device launch over all handles (captured into
- * a CUDA graph once its shape repeats); otherwise one batched launch per
- * handle, each on its own stream. */
+ * which) stops all fits.  A round's f, g requests are one batched launch per
+ * handle, each on its own stream; with opts->one_launch and every handle at
+ * K <= 32 they are instead one pwa_eval_multi_device launch over all handles
+ * (captured into a CUDA graph once its shape repeats).  Either way, each
+ * handle's Hessian requests of a round are one batched Hessian pass. */
 pwa_status pwa_newton_cg_fit_multi(int n_handles, pwa_handle* const* handles, const int* B,
                                    const double* const* theta0, const pwa_fit_opts* opts,
                                    double* const* theta_out, pwa_fit_result* const* results);

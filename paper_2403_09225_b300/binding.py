@@ -44,7 +44,8 @@ class pwa_fit_iter(ctypes.Structure):
 class pwa_fit_opts(ctypes.Structure):
     _fields_ = [("xtol", ctypes.c_double), ("gtol", ctypes.c_double), ("maxiter", ctypes.c_int),
                 ("cg_maxiter", ctypes.c_int), ("time_limit_s", ctypes.c_double), ("matrix_free", ctypes.c_int),
-                ("method", ctypes.c_int), ("trace_cap", ctypes.c_int), ("trace", ctypes.POINTER(pwa_fit_iter))]
+                ("method", ctypes.c_int), ("trace_cap", ctypes.c_int), ("trace", ctypes.POINTER(pwa_fit_iter)),
+                ("one_launch", ctypes.c_int)]
 
 
 class pwa_lineshape(ctypes.Structure):
@@ -548,9 +549,11 @@ class Coupling:
 
 
 def fit_multi(likelihoods, thetas0, xtol: float = 1e-8, gtol: float = 0.0, maxiter: int = 0,
-              cg_maxiter: int = 0, time_limit_s: float = 0.0, matrix_free: bool = False, method: int = 0):
+              cg_maxiter: int = 0, time_limit_s: float = 0.0, matrix_free: bool = False, method: int = 0,
+              one_launch: bool = False):
     """Lockstep fits over several likelihoods (one group of starts per
-    likelihood; their batched passes run concurrently).  thetas0[i]: [B_i, P_i].
+    likelihood; their batched passes run concurrently, or with one_launch as
+    one launch over all likelihoods per round).  thetas0[i]: [B_i, P_i].
     Returns ([theta [B_i, P_i]], [[info per fit]], all converged-or-time-limit)."""
     n = len(likelihoods)
     ths = [_f64(t).reshape(-1, L.P) for L, t in zip(likelihoods, thetas0)]
@@ -563,6 +566,7 @@ def fit_multi(likelihoods, thetas0, xtol: float = 1e-8, gtol: float = 0.0, maxit
     out_p = (dpp * n)(*[_dptr(o) for o in outs])
     res_p = (ctypes.POINTER(pwa_fit_result) * n)(*[ctypes.cast(r, ctypes.POINTER(pwa_fit_result)) for r in res])
     opts = pwa_fit_opts(xtol, gtol, maxiter, cg_maxiter, time_limit_s, int(matrix_free), int(method))
+    opts.one_launch = int(one_launch)
     st = lib().pwa_newton_cg_fit_multi(n, hs, Bs, th_p, ctypes.byref(opts), out_p, res_p)
     if st not in (PWA_OK, PWA_ENOCONV):
         msgs = "; ".join(filter(None, (lib().pwa_last_error(L._h).decode() for L in likelihoods)))

@@ -1556,6 +1556,7 @@ extern "C" void pwa_fit_opts_default(pwa_fit_opts* o)
     o->method = 0;
     o->trace_cap = 0;
     o->trace = nullptr;
+    o->one_launch = 0;
 }
 
 extern "C" pwa_status pwa_newton_cg_fit(pwa_handle* h, const double* theta0, const pwa_fit_opts* opts_in,
@@ -1637,7 +1638,8 @@ extern "C" pwa_status pwa_newton_cg_fit_multi(int n_handles, pwa_handle* const* 
                 return pwa::set_error(handles[i], PWA_EINVAL, "a handle appears twice; put its fits in one group");
     }
     std::vector<std::unique_ptr<FitGroup>> groups;
-    bool multi = n_handles >= 2;  // one launch per round over all handles (each K <= 32)
+    // one launch per round over all handles (each K <= 32) when asked for
+    bool multi = n_handles >= 2 && opts && opts->one_launch;
     for (int i = 0; i < n_handles; ++i) {
         multi &= handles[i]->K <= pwa::kMaxKMulti;
         groups.push_back(std::make_unique<FitGroup>());

@@ -215,13 +215,13 @@ def test_fits_over_several_handles_reach_the_oracle_minima():
         rng = np.random.default_rng(20 + i)
         starts.append(ref.x + 0.2 * sig * rng.standard_normal((3, ref.x.size)))
     Ls = [make_L(wl) for wl, _ in toys]
-    for matrix_free in (False, True):
-        outs, infos, ok = binding.fit_multi(Ls, starts, xtol=1e-10, matrix_free=matrix_free)
+    for matrix_free, one_launch in ((False, False), (False, True), (True, True)):
+        outs, infos, ok = binding.fit_multi(Ls, starts, xtol=1e-10, matrix_free=matrix_free, one_launch=one_launch)
         assert ok, infos
         for (wl, model), (x_ref, sig), o in zip(toys, refs, outs):
             for th in o:
                 pull = (oracle.canonical(model, th) - oracle.canonical(model, x_ref)) / sig
-                assert np.max(np.abs(pull)) <= 1e-3, (matrix_free, np.max(np.abs(pull)))
+                assert np.max(np.abs(pull)) <= 1e-3, (matrix_free, one_launch, np.max(np.abs(pull)))
 
 
 def test_autotune_keeps_results_within_tolerance():
