@@ -219,8 +219,9 @@ pwa_status pwa_hvp(pwa_handle* h, const double* theta, const double* v, double* 
  * second-derivative sums; the host combines them in FP64.  theta: host [P];
  * nll, grad: host (either may be NULL); hess: host [P][P] row-major,
  * symmetric.  For K <= 32 the Gram matrices are contractions on the tensor
- * cores (tcgen05, BF16 hi/lo splits of the FP32 columns, three products per
- * 16 rows, a fresh TMEM accumulator per 32-event tile, FP32 then FP64 sums
+ * cores (tcgen05, BF16 hi/lo splits of the FP32 columns, two products per
+ * 16 rows (hi^T hi + hi^T 2lo, symmetrised), a fresh TMEM accumulator per
+ * 32-event tile, tiles pipelined over two buffers, FP32 then FP64 sums
  * across tiles); for 32 < K <= 44 on the CUDA cores in FP32.  Supported for
  * K <= 44.  Errors: PWA_EINVAL (K > 44, non-finite theta), PWA_ENOMEM,
  * PWA_ECUDA, PWA_ENONFINITE, PWA_ETIMEOUT. */

@@ -26,13 +26,17 @@
 //
 // Work split (one CTA of NT threads streams tiles of 32 events, the records
 // pwa_create lays out, by TMA bulk copies into two shared stages):
-//   phase 1: a warp per event, a lane per resonance: B, the coherent sums by a
-//            warp reduction, I, the weights; the lane writes its resonance's
-//            columns of X and z into shared memory and accumulates its Q sums;
-//   phase 2: every thread owns NB 4 x 4 blocks of the upper triangle of the
-//            4K x 4K Gram matrices and accumulates them over the tile's rows
-//            in FP32 registers.
-// FP32 sums are folded into per-CTA FP64 records every kFold tiles; a second
+//   event phase: a lane per event, each warp owning every NW-th resonance: B,
+//            the warp's partial coherent sums, summed over the warps through
+//            shared memory, I, the weights; the lane writes its resonances'
+//            columns of X and z into shared memory and accumulates their Q
+//            sums;
+//   Gram phase: CUDA cores (hess_kernel): every thread owns NB 4 x 4 blocks of
+//            the upper triangle of the 4K x 4K Gram matrices and accumulates
+//            them over the tile's rows in FP32 registers; tensor cores
+//            (hess_tc_kernel, K <= 32): MMAs on BF16 splits of X and z into
+//            TMEM, read back into FP32 registers (described below).
+// FP32 sums are folded into per-CTA FP64 records every few tiles; a second
 // kernel adds the records in a fixed order (run-to-run bit-identical).
 #include <cuda_runtime.h>
 
@@ -483,7 +487,7 @@ __global__ void __launch_bounds__(NT, 1) hess_kernel(const HessArgs a)
 // accumulator sets: tile i's MMAs run while the warps read tile i - 1's
 // accumulators back (warp w: TMEM lanes 32 (w mod 4) + l, half w / 4 of the
 // columns) into FP32 registers and build tile i + 1's operands; the FP32
-// sums are folded into FP64 every kFold tiles like the other sums.  (For
+// sums are folded into FP64 every kFoldG tiles (the Q sums every kFold).  (For
 // S = 4 and K > 28 the two buffers do not fit in shared memory: one buffer,
 // each tile read back before the next is built.)  Per-CTA record: the full
 // data X Gram, the data z Gram and the MC X Gram (C x C each, row-major, not
