@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "NLL+grad+HVP event-amplitude evaluations/s (fused pass)"
 #: identifies the kernel version the committed DRAM-traffic summary was taken on
-KERNEL_REVISION = "paired-projection tiles, paired butterfly, twosum folds"
+KERNEL_REVISION = "paired-projection tiles, paired butterfly, twosum folds, shared block body"
 UNIT = "event*amp/s"
 CONFIG_NAME = "paper"
 
