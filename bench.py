@@ -386,14 +386,20 @@ def coupling_metric(L, wl, reps: int = 20):
 
 
 def learned_metric(n_train: int, n_eval: int, n_random: int, time_limit: float, pool: int = 10_000_000,
-                   n_events: int = 100_000, n_mc: int = 500_000, epochs: int = 60, polish: bool = False):
+                   n_events: int = 100_000, n_mc: int = 500_000, epochs: int = 60, polish: bool = False,
+                   main=None):
     """The learned starting-point proposal on the paper-scale model (K = 20,
     S = 4, 78 parameters): n_train pseudo-experiments (theta from the prior,
     up to n_events events accept-rejected from a pool of phase-space events,
     labels from capped Newton-CG fits started at theta), the 4096 -> 3 x 512
     -> 78 network trained with the library's BF16 kernels, then n_eval
     held-out experiments fitted from the network's start and from n_random
-    prior starts (one batched call) with the same options."""
+    prior starts (one batched call) with the same options.  With main =
+    (likelihood, workload, best NLL of the fit leg or None, fit time limit,
+    the fit leg's line-search record or None), also the benchmark's own
+    paper-scale workload (1e6 data events): the network's start for its data
+    histogram, fitted alone and as a batch with three draws around it,
+    against the fit leg's random starts."""
     import torch
     from paper_2403_09225_b300 import proposal, workload as W
     cfg = W.CONFIGS["paper"]
@@ -430,8 +436,11 @@ def learned_metric(n_train: int, n_eval: int, n_random: int, time_limit: float, 
         recs, summ = proposal.evaluate(gen, net, codec, n_eval, n_events, n_random, seed=999,
                                        fit_opts=dict(time_limit_s=time_limit), polish=polish)
         eval_s = time.perf_counter() - t0
+        paper_scale = None
+        if main is not None:
+            paper_scale = _learned_paper_scale(net, codec, gen, *main)
         net.close()
-        return {"model": "paper-scale table: K=20, S=4, P=78", "train_experiments": n_train,
+        return {"paper_scale": paper_scale, "model": "paper-scale table: K=20, S=4, P=78", "train_experiments": n_train,
                 "eval_experiments": n_eval, "events_per_experiment": n_events, "pool_events": pool,
                 "mc_events": n_mc, "kept_events_min_mean": [int(ex.n_events.min()), float(ex.n_events.mean())],
                 "label_fit_s": ex.fit_s, "generate_s": ex.gen_s, "setup_s": gen_setup_s, "make_s": make_s,
@@ -444,6 +453,42 @@ def learned_metric(n_train: int, n_eval: int, n_random: int, time_limit: float, 
                                                "peak_kind": kind}}}
     finally:
         gen.close()
+
+
+def _learned_paper_scale(net, codec, gen, L, wl, best_fit, time_limit, random_runs):
+    """The trained network on the benchmark's own workload: its start for the
+    data sample's histogram, one fit from it and one batched call from it and
+    three draws around it (the learned leg's batched form); a fit reaches the
+    global minimum when its NLL is within 0.01 of the best NLL seen (these
+    fits, the fit leg's random starts and its fits from theta_true)."""
+    import torch
+    from paper_2403_09225_b300 import binding, proposal
+    m2 = torch.from_numpy(np.ascontiguousarray(wl.data.m2, dtype=np.float32)).cuda()
+    idx = torch.arange(wl.data.n, dtype=torch.int32, device="cuda")
+    X = binding.dalitz_histogram(m2, idx, gen.nb, gen.bounds, log_scale=True)[None]
+    start = proposal.propose(net, codec, X)[0]
+    t0 = time.perf_counter()
+    _, info = L.fit(start, xtol=1e-8, time_limit_s=time_limit)
+    t_one = time.perf_counter() - t0
+    starts = proposal.perturbed_starts(codec, start, 4, np.random.default_rng(5))
+    t0 = time.perf_counter()
+    _, infos, _ = L.fit_batch(starts, xtol=1e-8, time_limit_s=time_limit * 4)
+    t_batch = time.perf_counter() - t0
+    nll_b = [d["nll"] for d in infos]
+    best = min([info["nll"]] + nll_b + ([best_fit] if best_fit is not None else []))
+    out = {"events": int(wl.data.n + wl.mc.n), "nll_learned": info["nll"], "t_learned": t_one,
+           "status_learned": info["status"], "nll_learned_batch": nll_b, "t_learned_batch": t_batch,
+           "best_nll": best, "learned_hit": bool(info["nll"] <= best + 0.01),
+           "learned_batch_hit": bool(min(nll_b) <= best + 0.01)}
+    if random_runs is not None:
+        hits = sum(1 for f in random_runs["nll"] if f <= best + 0.01)
+        out["random"] = {"starts": len(random_runs["nll"]), "gpu_seconds": random_runs["gpu_seconds"],
+                         "hits": hits}
+    out["fits_to_global_min_per_s"] = {
+        "learned": (1.0 if out["learned_hit"] else 0.0) / t_one,
+        "learned_batch": (1.0 if out["learned_batch_hit"] else 0.0) / t_batch,
+        "random": (out["random"]["hits"] / out["random"]["gpu_seconds"]) if random_runs else None}
+    return out
 
 
 def mlp_step_metric(batches=(128, 512, 1024), reps: int = 50):
@@ -843,8 +888,10 @@ def main():
     if args.learned not in ("", "0") and rank == 0:
         n_train, n_eval, n_rand = (int(x) for x in args.learned.split(","))
         t0 = time.perf_counter()
+        main = (L, wl, fit["paper"]["best_nll"] if fit else None, args.fit_time_limit,
+                fit["paper"]["line_search"] if fit else None)
         learned = learned_metric(n_train, n_eval, n_rand, time_limit=args.learned_time_limit,
-                                 polish=args.learned_polish)
+                                 polish=args.learned_polish, main=main)
         learned["leg_s"] = time.perf_counter() - t0
 
     cpu = None
