@@ -259,6 +259,26 @@ double dot(const std::vector<double>& a, const std::vector<double>& b)
     return s;
 }
 
+// y = H x for the explicit Hessian H [n][n] (host FP64).  Four partial sums
+// per row in a fixed order: independent chains the compiler can vectorise,
+// instead of one dependent chain of n additions.
+void hess_times(const double* H, int n, const double* x, double* y)
+{
+    for (int i = 0; i < n; ++i) {
+        const double* Hi = H + (size_t)i * n;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int l = 0;
+        for (; l + 4 <= n; l += 4) {
+            a0 += Hi[l] * x[l];
+            a1 += Hi[l + 1] * x[l + 1];
+            a2 += Hi[l + 2] * x[l + 2];
+            a3 += Hi[l + 3] * x[l + 3];
+        }
+        for (; l < n; ++l) a0 += Hi[l] * x[l];
+        y[i] = (a0 + a1) + (a2 + a3);
+    }
+}
+
 struct LinePoint {
     double a = 0.0, f = 0.0, df = 0.0;
     std::vector<double> x, g;
@@ -441,12 +461,7 @@ FitTask newton_cg(FitState& s)
             double rr = dot(r, r);
             for (int j = 0;; ++j) {
                 if (s.explicit_h) {
-                    for (int i = 0; i < n; ++i) {
-                        const double* Hi = s.H.data() + (size_t)i * n;
-                        double acc = 0.0;
-                        for (int l = 0; l < n; ++l) acc += Hi[l] * d[l];
-                        Hd[i] = acc;
-                    }
+                    hess_times(s.H.data(), n, d.data(), Hd.data());
                 } else {
                     s.req = Req::HV;
                     s.rx = s.x.data();
@@ -689,12 +704,7 @@ FitTask newton_cg_tr(FitState& s)
         double rr = dot(r, r);
         for (int j = 0;; ++j) {
             if (s.explicit_h) {
-                for (int i = 0; i < n; ++i) {
-                    const double* Hi = s.H.data() + (size_t)i * n;
-                    double acc = 0.0;
-                    for (int l = 0; l < n; ++l) acc += Hi[l] * d[l];
-                    Hd[i] = acc;
-                }
+                hess_times(s.H.data(), n, d.data(), Hd.data());
             } else {
                 s.req = Req::HV;
                 s.rx = s.x.data();
