@@ -483,7 +483,9 @@ def _learned_paper_scale(net, codec, gen, L, wl, best_fit, time_limit, random_ru
     if random_runs is not None:
         hits = sum(1 for f in random_runs["nll"] if f <= best + 0.01)
         out["random"] = {"starts": len(random_runs["nll"]), "gpu_seconds": random_runs["gpu_seconds"],
-                         "hits": hits}
+                         "hits": hits, "dnll_closest": min(random_runs["nll"]) - best}
+    # how close each form came (the 0.01 criterion is finer than an FP32 pass resolves at |NLL| ~ 1.5e6)
+    out["dnll_closest"] = {"learned": info["nll"] - best, "learned_batch": min(nll_b) - best}
     out["fits_to_global_min_per_s"] = {
         "learned": (1.0 if out["learned_hit"] else 0.0) / t_one,
         "learned_batch": (1.0 if out["learned_batch_hit"] else 0.0) / t_batch,
