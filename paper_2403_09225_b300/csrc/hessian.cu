@@ -1092,36 +1092,40 @@ void combine(const pwa_handle* h, const double* theta, const double* sum, int NW
              double* grad, double* hess)
 {
     const int K = h->K, P = h->P, nb = K * (K + 1) / 2, C = 4 * K;
-    // full symmetric 4K x 4K Gram matrices: from the upper-triangle blocks of
-    // hess_kernel, or symmetrised from the full matrices of hess_tc_kernel
-    auto gram = [&](int off) {
-        std::vector<double> Gm((size_t)C * C);
-        if (tc) {
-            const double* x = sum + (size_t)off;
-            for (int i = 0; i < C; ++i)
-                for (int j = 0; j < C; ++j) Gm[(size_t)i * C + j] = 0.5 * (x[(size_t)i * C + j] + x[(size_t)j * C + i]);
-            return Gm;
-        }
-        for (int b = 0; b < nb; ++b) {
-            int bi, bj;
-            block_of(b, K, bi, bj);
-            for (int u = 0; u < 4; ++u)
-                for (int v = 0; v < 4; ++v) {
-                    const double x = sum[off + 16 * b + 4 * u + v];
-                    const int ca = bi + u * K, cb = bj + v * K;
-                    Gm[(size_t)ca * C + cb] = x;
-                    Gm[(size_t)cb * C + ca] = x;
-                }
-        }
-        return Gm;
-    };
+    // the three symmetric 4K x 4K Gram matrices (0: data X, 1: data z, 2: MC X):
+    // the tensor-core records hold each full and not yet symmetric, read as
+    // (x_ab + x_ba) / 2 in place; the CUDA-core records hold upper-triangle
+    // blocks, expanded once
     const int CC = C * C;
-    const std::vector<double> RD = gram(0), ZD = gram(tc ? CC : 16 * nb), RM = gram(tc ? 2 * CC : 32 * nb);
-    // C[c][c'] = sum a sum_s conj(V_c) V_c', c = p K + k
-    auto cgram = [&](const std::vector<double>& R, int c, int cp) {
-        const double* r0 = R.data() + (size_t)(2 * c) * C;
-        const double* r1 = R.data() + (size_t)(2 * c + 1) * C;
-        return cplx(r0[2 * cp] + r1[2 * cp + 1], r0[2 * cp + 1] - r1[2 * cp]);
+    std::vector<double> Gx[3];
+    if (!tc) {
+        const int offs[3] = {0, 16 * nb, 32 * nb};
+        for (int m = 0; m < 3; ++m) {
+            Gx[m].assign((size_t)C * C, 0.0);
+            for (int b = 0; b < nb; ++b) {
+                int bi, bj;
+                block_of(b, K, bi, bj);
+                for (int u = 0; u < 4; ++u)
+                    for (int v = 0; v < 4; ++v) {
+                        const double x = sum[offs[m] + 16 * b + 4 * u + v];
+                        const int ca = bi + u * K, cb = bj + v * K;
+                        Gx[m][(size_t)ca * C + cb] = x;
+                        Gx[m][(size_t)cb * C + ca] = x;
+                    }
+            }
+        }
+    }
+    auto at = [&](int m, int a, int b) -> double {
+        if (tc) {
+            const double* x = sum + (size_t)m * CC;
+            return 0.5 * (x[(size_t)a * C + b] + x[(size_t)b * C + a]);
+        }
+        return Gx[m][(size_t)a * C + b];
+    };
+    // C[c][c'] = sum a sum_s conj(V_c) V_c', c = p K + k, from Gram matrix m (0 data, 2 MC)
+    auto cgram = [&](int m, int c, int cp) {
+        return cplx(at(m, 2 * c, 2 * cp) + at(m, 2 * c + 1, 2 * cp + 1),
+                    at(m, 2 * c, 2 * cp + 1) - at(m, 2 * c + 1, 2 * cp));
     };
     const int offQ = tc ? 3 * CC : 48 * nb, offS = offQ + 12 * K;
     std::vector<cplx> Q[2][3];
@@ -1203,14 +1207,14 @@ void combine(const pwa_handle* h, const double* theta, const double* sum, int NW
                 for (int pp = 0; pp < 2; ++pp) {
                     if (ka[p] == 0.0 || kb[pp] == 0.0) continue;
                     const int c = p * K + a.k, cp = pp * K + b.k;
-                    s2d += 2.0 * std::real(std::conj(ka[p]) * kb[pp] * cgram(RD, c, cp));
-                    s2m += 2.0 * std::real(std::conj(ka[p]) * kb[pp] * cgram(RM, c, cp));
+                    s2d += 2.0 * std::real(std::conj(ka[p]) * kb[pp] * cgram(0, c, cp));
+                    s2m += 2.0 * std::real(std::conj(ka[p]) * kb[pp] * cgram(2, c, cp));
                     // c_a^T Zg c_b with c = (2 Re kappa, -2 Im kappa) at the z columns of (p, k)
                     const double ca[2] = {2.0 * ka[p].real(), -2.0 * ka[p].imag()};
                     const double cb[2] = {2.0 * kb[pp].real(), -2.0 * kb[pp].imag()};
                     for (int u = 0; u < 2; ++u)
                         for (int v = 0; v < 2; ++v)
-                            jg += ca[u] * cb[v] * ZD[(size_t)(2 * c + u) * C + 2 * cp + v];
+                            jg += ca[u] * cb[v] * at(1, 2 * c + u, 2 * cp + v);
                 }
             if (a.k == b.k) {
                 cplx m1, m2, m3;
