@@ -1251,46 +1251,54 @@ pwa_status open_group(FitGroup& g, std::unique_ptr<RoundEvaluator> ev, int B, co
     return PWA_OK;
 }
 
-// Serve the groups' Hessian requests: one batched Hessian pass per group
-// over all of its fits that ask for one, every group's pass enqueued before
-// the first is waited for (so the host's combination and CG for one group
-// overlap the passes of the next); each served fit runs its CG on the host
-// and posts its next request.  Repeats while any fit asks for a Hessian.
+// A group's Hessian requests: hess_issue enqueues one batched Hessian pass
+// over all of its fits that ask for one (returns whether there were any);
+// hess_finish waits for it and resumes those fits (each runs its CG on the
+// host and posts its next request).
+bool hess_issue(FitGroup& g)
+{
+    g.hrows.clear();
+    for (int b = 0; b < g.B; ++b)
+        if (!g.tasks[b].h.done() && g.fits[b].req == Req::HESS) g.hrows.push_back(b);
+    if (g.hrows.empty()) return false;
+    const int P = g.P, nb = (int)g.hrows.size();
+    g.htheta.resize((size_t)nb * P);
+    for (int i = 0; i < nb; ++i)
+        std::memcpy(g.htheta.data() + (size_t)i * P, g.fits[g.hrows[i]].rx, sizeof(double) * P);
+    g.hissue = g.ev->hessian_issue(nb, g.htheta.data());
+    return true;
+}
+
+void hess_finish(FitGroup& g)
+{
+    if (g.hrows.empty()) return;
+    const int P = g.P, nb = (int)g.hrows.size();
+    g.hH.resize((size_t)nb * P * P);
+    g.hst.assign(nb, PWA_OK);
+    pwa_status st = g.hissue;
+    if (st == PWA_OK) st = g.ev->hessian_finish(nb, g.htheta.data(), g.hH.data(), g.hst.data());
+    for (int i = 0; i < nb; ++i) {
+        const int b = g.hrows[i];
+        FitState& s = g.fits[b];
+        ++s.n_hess;
+        s.req_status = st != PWA_OK ? st : g.hst[i];
+        if (s.req_status == PWA_OK) std::memcpy(s.rH, g.hH.data() + (size_t)i * P * P, sizeof(double) * P * P);
+        g.tasks[b].h.resume();
+        if (g.tasks[b].h.done()) s.elapsed = s.since_start();
+    }
+    g.hrows.clear();
+}
+
+// Serve the groups' Hessian requests: every group's pass enqueued before the
+// first is waited for (the host's combination and CG for one group overlap
+// the passes of the next); repeats while any fit asks for a Hessian.
 void serve_hessians(const std::vector<FitGroup*>& gs)
 {
     while (true) {
         bool any = false;
-        for (FitGroup* g : gs) {
-            g->hrows.clear();
-            for (int b = 0; b < g->B; ++b)
-                if (!g->tasks[b].h.done() && g->fits[b].req == Req::HESS) g->hrows.push_back(b);
-            if (g->hrows.empty()) continue;
-            any = true;
-            const int P = g->P, nb = (int)g->hrows.size();
-            g->htheta.resize((size_t)nb * P);
-            for (int i = 0; i < nb; ++i)
-                std::memcpy(g->htheta.data() + (size_t)i * P, g->fits[g->hrows[i]].rx, sizeof(double) * P);
-            g->hissue = g->ev->hessian_issue(nb, g->htheta.data());
-        }
+        for (FitGroup* g : gs) any |= hess_issue(*g);
         if (!any) return;
-        for (FitGroup* g : gs) {
-            if (g->hrows.empty()) continue;
-            const int P = g->P, nb = (int)g->hrows.size();
-            g->hH.resize((size_t)nb * P * P);
-            g->hst.assign(nb, PWA_OK);
-            pwa_status st = g->hissue;
-            if (st == PWA_OK) st = g->ev->hessian_finish(nb, g->htheta.data(), g->hH.data(), g->hst.data());
-            for (int i = 0; i < nb; ++i) {
-                const int b = g->hrows[i];
-                FitState& s = g->fits[b];
-                ++s.n_hess;
-                s.req_status = st != PWA_OK ? st : g->hst[i];
-                if (s.req_status == PWA_OK)
-                    std::memcpy(s.rH, g->hH.data() + (size_t)i * P * P, sizeof(double) * P * P);
-                g->tasks[b].h.resume();
-                if (g->tasks[b].h.done()) s.elapsed = s.since_start();
-            }
-        }
+        for (FitGroup* g : gs) hess_finish(*g);
     }
 }
 
@@ -1302,7 +1310,7 @@ bool collect_round(FitGroup& g)
 {
     g.live.clear();
     for (int b = 0; b < g.B; ++b)
-        if (!g.tasks[b].h.done()) g.live.push_back(b);
+        if (!g.tasks[b].h.done() && g.fits[b].req != Req::HESS) g.live.push_back(b);
     bool any_hv = false;
     for (int b : g.live) any_hv |= g.fits[b].req == Req::HV;
     return any_hv;
@@ -1359,17 +1367,23 @@ pwa_status finish_round(FitGroup& g)
     return PWA_OK;
 }
 
+// Lockstep rounds, one batched launch per group on its own stream: every
+// group's Hessian pass is enqueued first; then, group by group, its Hessian
+// is waited for, its fits run their CG on the host, and its f, g / H v round
+// is enqueued at once, so that the GPU works on that round (and on the later
+// groups' Hessians) while the host serves the next group.  A fit that asks
+// for a Hessian again is served in the next round.
 pwa_status run_lockstep(std::vector<std::unique_ptr<FitGroup>>& groups)
 {
-    std::vector<FitGroup*> all;
-    for (auto& g : groups) all.push_back(g.get());
     while (true) {
-        serve_hessians(all);
+        for (auto& g : groups) hess_issue(*g);
         bool any = false;
         for (auto& g : groups) {
+            hess_finish(*g);
             pwa_status st = issue_round(*g);
             if (st != PWA_OK) return st;
             any |= !g->live.empty();
+            for (int b = 0; b < g->B && !any; ++b) any |= !g->tasks[b].h.done();
         }
         if (!any) return PWA_OK;
         for (auto& g : groups) {
