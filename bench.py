@@ -199,10 +199,53 @@ def cpu_baseline_leg():
         oracle.nll_grad_hvp(model, th, v, wl.data, wl.mc)
         reps += 1
         dt = time.perf_counter() - t0
-    return {"value": reps * (nd + nm) * cfg.K / dt, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
-            "kind": "oracle",
-            "sample": "%d data + %d MC events (1/60 of the workload), K=%d, S=%d, %d fused evaluations, "
-                      "%.1f s" % (nd, nm, cfg.K, cfg.S, reps, dt)}
+    out = {"value": reps * (nd + nm) * cfg.K / dt, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+           "kind": "oracle", "pass_s_sample": dt / reps,
+           "sample": "%d data + %d MC events (1/60 of the workload), K=%d, S=%d, %d fused evaluations, "
+                     "%.1f s" % (nd, nm, cfg.K, cfg.S, reps, dt)}
+    out["other_configs"] = _oracle_other_configs()
+    return out
+
+
+def _oracle_eval_rate(name: str, frac: float):
+    """One oracle NLL + gradient + H v evaluation on (a fraction of) a configuration."""
+    import oracle
+    from paper_2403_09225_b300 import workload as W
+    cfg = W.CONFIGS[name]
+    model = oracle.Model.from_table(W.make_table(cfg), cfg.S)
+    nd, nm = max(1, int(cfg.n_data * frac)), max(1, int(cfg.n_mc * frac))
+    wl = W.make_workload(cfg, intensity=None, n_data=nd, n_mc=nm)
+    th = W.random_starts(wl, 1)[0]
+    v = np.linspace(-1.0, 1.0, model.P)
+    t0 = time.perf_counter()
+    oracle.nll_grad_hvp(model, th, v, wl.data, wl.mc)
+    dt = time.perf_counter() - t0
+    return {"events": nd + nm, "fraction_of_config": frac, "K": cfg.K, "S": cfg.S, "eval_s": dt,
+            "event_amps_per_s": (nd + nm) * cfg.K / dt}
+
+
+def _oracle_other_configs():
+    """The oracle on the other configurations (single core): one fused
+    evaluation on the full tiny configuration and on 1/600 of the
+    differentiation one, and a full Newton-CG fit (its own FP64 iteration,
+    matrix-free) on 1/4 of tiny, data accept-rejected from the model."""
+    import oracle
+    from oracle import newton_cg as ncg
+    from paper_2403_09225_b300 import workload as W
+    out = {"tiny": _oracle_eval_rate("tiny", 1.0), "diff": _oracle_eval_rate("diff", 1.0 / 600)}
+    cfg = W.CONFIGS["tiny"]
+    table = W.make_table(cfg)
+    model = oracle.Model.from_table(table, cfg.S)
+    fn = lambda m2, F: oracle.intensity_full(cfg.K, cfg.S, model.channels, model.par0, m2, F)
+    nd, nm = cfg.n_data // 4, cfg.n_mc // 4
+    wl = W.make_workload(cfg, intensity=fn, n_data=nd, n_mc=nm)
+    x0 = W.random_starts(wl, 1)[0]
+    fg = lambda x: oracle.nll_grad(model, x, wl.data, wl.mc)
+    hp = lambda x, v: oracle.nll_grad_hvp(model, x, v, wl.data, wl.mc)[2]
+    r = ncg.newton_cg(fg, hp, x0, xtol=1e-8, time_limit=30.0)
+    out["tiny_fit"] = {"events": nd + nm, "fraction_of_config": 0.25, "seconds": r.elapsed, "iters": r.iters,
+                       "n_fev": r.n_fev, "n_hvp": r.n_hvp, "status": r.status_name, "time_limit_s": 30.0}
+    return out
 
 
 def _fit_runs(L, wl, starts, time_limit: float, batched: bool = False, method: int = 0,
@@ -900,6 +943,16 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_leg()
+        if fit is not None:
+            # the oracle on a paper-scale fit of the GPU fits' length, extrapolated: its full-scale
+            # pass time (the 1/60 sample's x 60) times the GPU fits' f, g evaluations per fit (a
+            # lower bound: the oracle's matrix-free CG adds one H v pass per inner iteration)
+            ls = fit["paper"]["line_search"]
+            fev = (ls["passes"] - ls["hessian_passes"]) / max(1, ls["starts"])
+            cpu["paper_fit_extrapolated"] = {"pass_s_full_scale": 60.0 * cpu["pass_s_sample"],
+                                             "fg_evaluations_per_gpu_fit": fev,
+                                             "seconds_lower_bound": fev * 60.0 * cpu["pass_s_sample"],
+                                             "gpu_seconds_per_fit": ls["gpu_seconds"] / max(1, ls["starts"])}
 
     til = L.get_tiling()
     traffic = measured_traffic(til)
