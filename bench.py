@@ -262,6 +262,7 @@ def _fit_runs(L, wl, starts, time_limit: float, batched: bool = False, method: i
         results = [L.fit(s, **kw)[1] for s in starts]
     total = time.perf_counter() - t0
     return {"starts": len(starts), "gpu_seconds": total, "nll": [r["nll"] for r in results],
+            "grad_max": [r["grad_max"] for r in results], "status_per_fit": [r["status"] for r in results],
             "iters": [r["iters"] for r in results], "statuses": sorted({r["status"] for r in results}),
             "passes": int(sum(r["n_fev"] + r["n_hvp"] + r["n_hess"] for r in results)),
             "hessian_passes": int(sum(r["n_hess"] for r in results)), "time_limit_s": time_limit,
@@ -290,13 +291,16 @@ def fit_metric(L, wl, n_starts: int, time_limit: float):
     from paper_2403_09225_b300 import binding
     from paper_2403_09225_b300 import workload as W
     starts = W.random_starts(wl, n_starts)
-    refs = [L.fit(wl.theta_true, xtol=1e-8, time_limit_s=time_limit, method=m)[1]["nll"] for m in (0, 1)]
+    ref_infos = [L.fit(wl.theta_true, xtol=1e-8, time_limit_s=time_limit, method=m)[1] for m in (0, 1)]
+    refs = [r["nll"] for r in ref_infos]
     paper = {"line_search": _fit_runs(L, wl, starts, time_limit),
              "trust_region": _fit_runs(L, wl, starts[:max(1, n_starts // 2)], time_limit, method=1)}
     best = min(refs + [f for a in paper.values() for f in a["nll"]])
     _score(paper, best)
     paper["best_nll"] = best
     paper["nll_from_theta_true"] = refs
+    paper["from_theta_true"] = [{"method": m, "nll": r["nll"], "grad_max": r["grad_max"], "iters": r["iters"],
+                                 "status": r["status"]} for m, r in zip(("line-search", "trust-region"), ref_infos)]
     out = {"xtol": 1e-8, "paper": paper}
     cfg = W.CONFIGS["tiny"]
     table = W.make_table(cfg)
