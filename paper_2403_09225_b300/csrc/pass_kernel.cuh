@@ -615,8 +615,9 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bt, const
                 //      F = (ReF, ImF) pairs, Re Dh = sum (ReF a_r + ImF a_i), Im Dh = sum (ImF a_r - ReF a_i);
                 //      the same for Dt with (a Adot - b A) ----
                 constexpr int Q2 = S % 2 == 0 ? S / 2 : 1;
-                float2 aR[Q2], aI[Q2], naI[Q2], dR[Q2], dI[Q2], ndI[Q2];
-                float2 al[S], be[S], dl[S], de[S];
+                // (each mode uses a subset: the unused ones are compiled away)
+                [[maybe_unused]] float2 aR[Q2], aI[Q2], naI[Q2], dR[Q2], dI[Q2], ndI[Q2];
+                [[maybe_unused]] float2 al[S], be[S], dl[S], de[S];
                 const float2 waa = make_float2(wa, wa), nwaa = make_float2(-wa, -wa);
                 const float2 wbb = make_float2(wb, wb), nwbb = make_float2(-wb, -wb);
                 if constexpr (S % 2 == 0) {
@@ -679,8 +680,8 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bt, const
                             }
                         }
                     }
-                    const float hr = X.x + X.y, hi = Y.x + Y.y;
-                    const float tr = XD.x + XD.y, ti = YD.x + YD.y;
+                    [[maybe_unused]] const float hr = X.x + X.y, hi = Y.x + Y.y;
+                    [[maybe_unused]] const float tr = XD.x + XD.y, ti = YD.x + YD.y;
                     const float b2r = fmaf(br, br, -bi * bi), b2i = 2.f * br * bi;
                     if constexpr (RU) {
                         // P1 += Dt B, P2 += Dt B^2 only (record slots 6..9)
