@@ -65,8 +65,11 @@ def test_two_symmetrised_products_reach_the_gram_matrix():
     X = (rng.standard_normal((4096, 40)) * np.exp(rng.uniform(-6, 6, (4096, 1)))).astype(np.float32)
     err = scaled_error(gram_scheme(X), X)
     assert err <= 4 * 2.0 ** -16, err
-    # the same accuracy as the three-product form it replaces
-    assert err <= 2 * scaled_error(gram_scheme(X, products=3), X) + 2.0 ** -20
+    # the same result as the three-product form it replaces (hi^T hi + hi^T lo + lo^T hi)
+    three = gram_scheme(X, lo_factor=1.0, products=3)
+    assert abs(err - scaled_error(three, X)) <= 2.0 ** -30
+    mag = np.abs(X.astype(np.float64)).T @ np.abs(X.astype(np.float64))
+    assert np.max(np.abs(gram_scheme(X) - three) / mag) <= 2.0 ** -40
 
 
 def test_the_scheme_fails_without_its_pieces():
